@@ -1,0 +1,141 @@
+"""Seeded synthetic inputs for the multigrid workloads.
+
+This module is shared by the oracle checks and the CUDA path and therefore holds none of
+the solver's arithmetic: only grid generation (max_grid_size chopping, Sec. "Regridding")
+and the random coefficient / right-hand-side fields.  Dense arrays are float64 with shape
+(nz, ny, nx), x fastest.
+
+Workload shapes follow the paper's solver study (Sec. "Linear Solvers": variable
+coefficient alpha/beta problem, 256^3 cells per node):
+
+  poisson32   32^3 periodic, 8 boxes of 16^3, beta = 1, rhs = sin(2 pi x) sin(2 pi y) sin(2 pi z)
+  abec256     256^3 Dirichlet, 64 boxes of 64^3, beta log-normal smoothed, rhs N(0,1)
+  abec512     512^3 Dirichlet, 64 boxes of 128^3, same recipe
+  batch64     64 solves with edges drawn from {32,48,64,96,128,160}, boxes of at most 32^3
+  amr2        two-level composite: 128^3 periodic + ratio-2 patch over coarse [32,96)^3
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PERIODIC = 0
+DIRICHLET = 1
+
+SEEDS = {"poisson32": 12010, "abec256": 12011, "abec512": 12012, "batch64": 12013, "amr2": 12014}
+BATCH_EDGES = (32, 48, 64, 96, 128, 160)
+
+
+def chop(lo, hi, max_grid_size):
+    """Cut the box [lo, hi] into chunks of max_grid_size cells per axis from the low end,
+    the remainder last (48 -> 32 + 16 for max_grid_size 32).  Box order: x fastest."""
+    cuts = []
+    for d in range(3):
+        c = []
+        s = lo[d]
+        while s <= hi[d]:
+            e = min(s + max_grid_size - 1, hi[d])
+            c.append((s, e))
+            s = e + 1
+        cuts.append(c)
+    boxes = []
+    for (zl, zh) in cuts[2]:
+        for (yl, yh) in cuts[1]:
+            for (xl, xh) in cuts[0]:
+                boxes.append(((xl, yl, zl), (xh, yh, zh)))
+    return boxes
+
+
+def cell_centres(n, lo=0.0, hi=1.0):
+    h = (hi - lo) / n
+    return lo + (np.arange(n) + 0.5) * h
+
+
+def sin_product(shape, mode=(2, 2, 2), kind="periodic"):
+    """prod_d sin(m_d * pi * x_d) at cell centres of the unit cube (kind='dirichlet'),
+    or prod_d sin(2 pi x_d) (kind='periodic', mode ignored)."""
+    nz, ny, nx = shape
+    xs = [cell_centres(nx), cell_centres(ny), cell_centres(nz)]
+    if kind == "periodic":
+        fx, fy, fz = (np.sin(2 * np.pi * x) for x in xs)
+    else:
+        fx, fy, fz = (np.sin(m * np.pi * x) for m, x in zip(mode, xs))
+    return fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+
+
+def box_mean_filter(a, periodic):
+    """3x3x3 mean of a cell field: periodic wrap, or a window truncated at the domain edge
+    (mean over the in-domain neighbours only).  Applied separably."""
+    out = np.array(a, dtype=np.float64, copy=True)
+    cnt = np.ones_like(out) if not periodic else None
+    for ax in range(3):
+        if periodic:
+            out = np.roll(out, 1, axis=ax) + out + np.roll(out, -1, axis=ax)
+        else:
+            s = out.copy()
+            c = cnt.copy()
+            sl_lo = [slice(None)] * 3
+            sl_hi = [slice(None)] * 3
+            sl_lo[ax] = slice(0, -1)
+            sl_hi[ax] = slice(1, None)
+            s[tuple(sl_hi)] += out[tuple(sl_lo)]
+            s[tuple(sl_lo)] += out[tuple(sl_hi)]
+            c[tuple(sl_hi)] += cnt[tuple(sl_lo)]
+            c[tuple(sl_lo)] += cnt[tuple(sl_hi)]
+            out, cnt = s, c
+    return out / 27.0 if periodic else out / cnt
+
+
+def lognormal_beta(rng, shape, periodic):
+    """beta = exp(N(0,1)) per cell, smoothed by one 3x3x3 mean filter."""
+    return box_mean_filter(np.exp(rng.standard_normal(shape)), periodic)
+
+
+def poisson32():
+    n = 32
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    return dict(name="poisson32", domain=dom, boxes=chop(*dom, 16), bc_lo=[PERIODIC] * 3, bc_hi=[PERIODIC] * 3,
+                a=0.0, b=1.0, alpha=None, beta=None, rhs=sin_product((n, n, n), kind="periodic"))
+
+
+def abec(n, max_grid_size, seed, bc=DIRICHLET, name=None):
+    """Variable-beta problem (a = 0, b = 1) on n^3: log-normal smoothed beta, N(0,1) rhs."""
+    rng = np.random.default_rng(seed)
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    shape = (n, n, n)
+    beta = lognormal_beta(rng, shape, periodic=(bc == PERIODIC))
+    rhs = rng.standard_normal(shape)
+    if bc == PERIODIC:
+        rhs -= rhs.mean()
+    return dict(name=name or f"abec{n}", domain=dom, boxes=chop(*dom, max_grid_size), bc_lo=[bc] * 3,
+                bc_hi=[bc] * 3, a=0.0, b=1.0, alpha=None, beta=beta, rhs=rhs)
+
+
+def abec256():
+    return abec(256, 64, SEEDS["abec256"], name="abec256")
+
+
+def abec512():
+    return abec(512, 128, SEEDS["abec512"], name="abec512")
+
+
+def batch_sizes(nsolves=64, seed=None):
+    rng = np.random.default_rng(SEEDS["batch64"] if seed is None else seed)
+    return [tuple(int(v) for v in rng.choice(BATCH_EDGES, size=3)) for _ in range(nsolves)]
+
+
+def batch_problem(size, index, seed=None, max_grid_size=32):
+    """One member of the batched workload: edges size=(nx, ny, nz), Dirichlet walls."""
+    base = SEEDS["batch64"] if seed is None else seed
+    rng = np.random.default_rng(base + 1 + index)
+    nx, ny, nz = size
+    dom = ((0, 0, 0), (nx - 1, ny - 1, nz - 1))
+    shape = (nz, ny, nx)
+    beta = lognormal_beta(rng, shape, periodic=False)
+    rhs = rng.standard_normal(shape)
+    return dict(name=f"batch{index}", domain=dom, boxes=chop(*dom, max_grid_size), bc_lo=[DIRICHLET] * 3,
+                bc_hi=[DIRICHLET] * 3, a=0.0, b=1.0, alpha=None, beta=beta, rhs=rhs,
+                prob_hi=(nx / 64.0, ny / 64.0, nz / 64.0))
+
+
+def batch64(nsolves=64, seed=None):
+    return [batch_problem(s, i, seed) for i, s in enumerate(batch_sizes(nsolves, seed))]
