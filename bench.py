@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 multigrid solve to 1e-10 relative residual on the abec256 workload.
+
+Workload (the paper's solver study, Sec. "Linear Solvers": 256^3 cells per node, variable
+coefficients): 256^3 cells, Dirichlet walls, 64 boxes of 64^3, a = 0, b = 1, beta =
+exp(N(0,1)) smoothed by one 3x3x3 mean filter (harmonic faces), rhs N(0,1), seed 12011.
+
+A step is one whole solve from phi = 0 to ||r||_inf <= 1e-10 ||rhs||_inf: every V-cycle
+step of the hot path (ghost exchange, red-black Gauss-Seidel, residual, average-down,
+prolongation, BiCGStab bottom) and the outer FP64 residual loop.
+
+  value  = Mcell-updates/s = sum over smoothed levels of cells x (nu1 + nu2) x V-cycles
+           / time to tolerance, device-timed (CUDA events) with inputs resident in HBM;
+  e2e    = the same metric through the public API with host buffers: pinned rhs copied
+           in, packed, solved, unpacked and copied back inside the timed region;
+  mixed  = the same solve with the float and bfloat16-storage V-cycles inside FP64
+           iterative refinement (time, Mcell-updates/s, error against the FP64 solve);
+  roofline: the finest-level smoother kernel (dominant), its algorithmic bytes per launch
+           over its average launch time, CUDA events recorded around each launch inside
+           the timed solves;
+  cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload.
+
+--impl reference times the oracle itself (each step: one V-cycle iteration of the
+workload on the host cores).  Multi-GPU: independent replicas (the solve does not shard
+in this version), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solve time to 1e-10 rel. residual & Mcell-updates/s; mixed vs FP64"
+UNIT = "Mcell-updates/s"
+WORKLOAD = ("abec256: 256^3 ABecLaplacian a=0 b=1, Dirichlet walls, 64 boxes of 64^3, beta log-normal "
+            "(3x3x3 mean filter, harmonic faces), rhs N(0,1) seed 12011; V(2,2) red-black GS, "
+            "BiCGStab bottom at 2^3, FP64, tol 1e-10")
+SMOOTH_BYTES_PER_CELL = 56  # one colour pass: phi, rhs, 3 face weights, 1/D read, phi written (8 B each)
+TOL = 1e-10
+
+
+def mcell_updates_per_vcycle(ctx, nu):
+    """sum over smoothed levels (all but the bottom) of cells x smoothing sweeps"""
+    tot = 0
+    for m in range(ctx.nlevels - 1):
+        nz, ny, nx = ctx.level_shape(m)
+        tot += nx * ny * nz * nu
+    return tot
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the kernel
+    source it was measured on is the current one (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    src = os.path.join(ROOT, "paper_2009_12009_gb300", "csrc", rec.get("source", "kernels.cu"))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != rec.get("source_sha256_16"):
+        return None
+    return rec.get("dram_bytes_per_launch_full_size")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(cfg, iters=2):
+    """The FP64 oracle, single-threaded, on the full workload for `iters` V-cycle
+    iterations (a bounded sample of the solve)."""
+    from oracle import oracle as O
+
+    P = O.Problem(cfg["domain"], cfg["boxes"], cfg["bc_lo"], cfg["bc_hi"])
+    P.set_coeffs(cfg["a"], cfg["b"], alpha=cfg["alpha"], beta=cfg["beta"])
+    cells = 0
+    for m in range(P.nlevels - 1):
+        nz, ny, nx = P.level_shape(m)
+        cells += nx * ny * nz * 4
+    t0 = time.perf_counter()
+    _, it, _, _ = P.solve(cfg["rhs"], tol_rel=0.0, maxit=iters)
+    dt = time.perf_counter() - t0
+    return {"value": cells * it / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{it} V-cycle iterations of the abec256 solve (FP64 oracle, 1 thread), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2009_12009_gb300 import inputs as I
+    from oracle import oracle as O
+
+    cfg = I.abec256()
+    P = O.Problem(cfg["domain"], cfg["boxes"], cfg["bc_lo"], cfg["bc_hi"])
+    P.set_coeffs(cfg["a"], cfg["b"], alpha=cfg["alpha"], beta=cfg["beta"])
+    cells = sum(P.level_shape(m)[0] * P.level_shape(m)[1] * P.level_shape(m)[2] * 4 for m in range(P.nlevels - 1))
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        P.solve(cfg["rhs"], tol_rel=0.0, maxit=1)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = cells * len(times) / tot / 1e6
+    sample = f"each step: 1 V-cycle iteration of the abec256 solve (FP64 oracle, 1 thread)"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+                      "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2009_12009_gb300 import gmg
+    from paper_2009_12009_gb300 import inputs as I
+
+    cfg = I.abec256()
+    stream = torch.cuda.current_stream()
+    ctx = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"], stream=stream.cuda_stream)
+    ctx.allocate(gmg.MIXED_FP32)
+    ctx.set_scalars(cfg["a"], cfg["b"])
+    ctx.set_beta(torch.from_numpy(cfg["beta"]))
+    rhs = ctx.pack(torch.from_numpy(cfg["rhs"]))
+    phi = ctx.field(0)
+    ncells = int(np.prod(ctx.level_shape(0)))
+    nu = 4
+    upd_per_vc = mcell_updates_per_vcycle(ctx, nu)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_solves(precision, steps, warmup, profile=0):
+        for _ in range(warmup):
+            ctx.solve(rhs, phi, tol_rel=TOL, precision=precision)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(stream)
+        for _ in range(steps):
+            _, info = ctx.solve(rhs, phi, tol_rel=TOL, precision=precision, profile=profile)
+            infos.append(info)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms, infos = timed_solves(gmg.FP64, args.steps, args.warmup, profile=1)
+    clk = clocks.stop()
+    its = [i.iterations for i in infos]
+    assert all(i.status == gmg.OK for i in infos), [i.status for i in infos]
+    updates = sum(upd_per_vc * k for k in its) * world
+    value = updates / (ms * 1e-3) / 1e6
+    phi64 = ctx.unpack(phi).clone()
+
+    # roofline of the dominant kernel: finest-level red-black smoother
+    sm_ms = sum(i.smooth0_ms for i in infos)
+    sm_n = sum(i.smooth0_launches for i in infos)
+    launch_s = sm_ms * 1e-3 / max(sm_n, 1)
+    alg_bytes = SMOOTH_BYTES_PER_CELL * ncells
+    achieved = alg_bytes / launch_s / 1e9
+    peak, peak_kind = peaks()
+    rs_ms = sum(i.resid0_ms for i in infos)
+    rs_n = sum(i.resid0_launches for i in infos)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "time_to_tol_ms": ms / args.steps,
+           "iterations": its[0], "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "cells": ncells, "mg_levels": ctx.nlevels,
+                      "cell_updates_per_vcycle": upd_per_vc, "parallelism": f"replicas x{world}",
+                      "l2": "inputs larger than L2 (finest-level working set ~1.2 GB of fields and coefficients)"},
+           "gpu_launches": int(sum(i.kernel_launches for i in infos)),
+           "roofline": {"bound": "hbm", "kernel": "k_smooth<double> (finest level, one colour)",
+                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_kind": peak_kind, "traffic": kernel_traffic("k_smooth_f64"),
+                        "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": launch_s * 1e6,
+                        "launches_timed": sm_n},
+           "outer_residual": {"kernel": "k_residual<double> (finest level, FP64)", "avg_launch_us":
+                              1e3 * rs_ms / max(rs_n, 1), "launches_timed": rs_n},
+           "clocks": clk}
+
+    if not args.no_mixed:
+        mixed = {}
+        for name, prec in (("fp32", gmg.MIXED_FP32), ("bf16", gmg.MIXED_BF16)):
+            ms_m, inf_m = timed_solves(prec, max(3, args.steps // 2), 2)
+            itm = inf_m[0].iterations
+            upd = sum(upd_per_vc * i.iterations for i in inf_m) * world
+            err = float((ctx.unpack(phi) - phi64).abs().max() / phi64.abs().max())
+            mixed[name] = {"time_to_tol_ms": ms_m / len(inf_m), "value": upd / (ms_m * 1e-3) / 1e6, "unit": UNIT,
+                           "iterations": itm, "final_rel_resid": inf_m[-1].final_resid / inf_m[-1].rhs_norm,
+                           "rel_err_vs_fp64_solve": err,
+                           "speedup_vs_fp64": (ms / args.steps) / (ms_m / len(inf_m))}
+        out["mixed"] = mixed
+
+    if not args.no_e2e:
+        host_rhs = torch.from_numpy(cfg["rhs"]).pin_memory()
+        host_out = torch.empty(ctx.level_shape(0), dtype=torch.float64).pin_memory()
+        dense = torch.empty(ctx.level_shape(0), dtype=torch.float64, device=dev)
+        nsteps = max(3, args.steps // 2)
+        barrier()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tot_upd = 0
+        for _ in range(nsteps):
+            dense.copy_(host_rhs, non_blocking=True)
+            r = ctx.pack(dense, out=rhs)
+            _, info = ctx.solve(r, phi, tol_rel=TOL)
+            host_out.copy_(ctx.unpack(phi), non_blocking=True)
+            tot_upd += upd_per_vc * info.iterations
+        e1.record(stream)
+        barrier()
+        ms_e = e0.elapsed_time(e1)
+        out["e2e"] = {"value": tot_upd * world / (ms_e * 1e-3) / 1e6, "unit": UNIT,
+                      "h2d_bytes_per_step": 8 * ncells, "d2h_bytes_per_step": 8 * ncells,
+                      "wall_ms_per_step": 1e3 * (time.perf_counter() - t0) / nsteps}
+
+    if not args.no_cpu and rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(cfg)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * gmg.h -- C ABI of the GB300 (sm_103a) cell-centred geometric multigrid library.
+ *
+ * The library solves the variable-coefficient equation of the paper's linear-solver
+ * section (AMReX, arXiv 2009.12009, Sec. "Linear Solvers"):
+ *
+ *        a * alpha * phi - b * div(beta grad phi) = rhs,
+ *
+ * phi, rhs and alpha at cell centres, beta on cell faces, on a BoxArray (Sec. "Basic
+ * data structures") with one ghost cell per box (Sec. "Containers for mesh data").  The
+ * solver is a multigrid V-cycle: ghost-cell exchange (Sec. "Operations on a level",
+ * fused into one gather kernel as in Sec. "Communication"), red-black Gauss-Seidel
+ * smoothing, residual, average-down restriction and piecewise-constant interpolation
+ * (Sec. "Operations between levels"), box aggregation on coarse levels and a BiCGStab
+ * bottom solve (Sec. "Linear Solvers").
+ *
+ * Conventions
+ *   - Every pointer to field data is a DEVICE pointer.  Pointers to index lists, scalars,
+ *     parameter and info structs are HOST pointers.
+ *   - The caller owns all device memory: the fields it passes and one workspace buffer
+ *     (gmg_workspace_size / gmg_set_workspace).  The library never allocates device
+ *     memory; it keeps the workspace pointer until it is replaced or the context is
+ *     destroyed, and borrows field pointers for the duration of a call only.
+ *   - All device work is ordered on the stream given to gmg_create.  Calls that return a
+ *     host-visible result (norms, iteration counts) synchronise that stream.
+ *   - Field layout ("boxed layout"): per MG level and element type, each box is a
+ *     ghosted 3-D block, x fastest.  Valid cell (i,j,k), i in [0,nx), lives at element
+ *         box_offset + (gx + i) + sx * ((j + 1) + (ny + 2) * (k + 1)),
+ *     with gx = 8 for every element type (so the first valid cell of a row is 16-byte
+ *     aligned for bfloat16, 32-byte for float, 64-byte for double) and sx = the row
+ *     stride returned by gmg_mg_layout (a multiple of 16 elements).  Offsets count
+ *     elements, so buffers of different element types on one level share offsets.  Ghost cells sit at
+ *     i = -1, i = nx, j = -1, ... .  Face arrays use the same layout: slot i holds the
+ *     face at i - 1/2, i in [0, nx].  gmg_pack / gmg_unpack convert to and from a dense
+ *     array over the level's domain.
+ *   - Errors: every call returns a gmg_status.  Negative values are errors; the message
+ *     of the last failing call on a context is returned by gmg_last_error.  No call
+ *     aborts the process or traps on the device.
+ */
+#ifndef GMG_H
+#define GMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmg_ctx gmg_ctx;
+
+typedef enum {
+  GMG_OK = 0,
+  GMG_ERR_BAD_INPUT = -1,      /* invalid arguments, geometry or unsolvable singular rhs */
+  GMG_ERR_NOT_CONVERGED = -2,  /* max_iter reached; the last iterate is returned */
+  GMG_ERR_DIVERGED = -3,       /* non-finite residual */
+  GMG_ERR_CUDA = -4,           /* a CUDA runtime call failed */
+  GMG_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait ran out */
+  GMG_ERR_NO_WORKSPACE = -6,   /* workspace missing or too small for the request */
+  GMG_ERR_STATE = -7           /* call out of order (e.g. solve before coefficients) */
+} gmg_status;
+
+/* Boundary condition of one domain side (Sec. "Basic data structures": BCRec). */
+typedef enum { GMG_BC_PERIODIC = 0, GMG_BC_DIRICHLET0 = 1 } gmg_bc;
+
+/* Arithmetic of the V-cycle.  FP64: everything in double.  MIXED_FP32: the V-cycle
+   (smoothing, residual, restriction, interpolation) runs in float inside an FP64
+   iterative-refinement loop (FP64 outer residual and solution update, FP64 bottom
+   solve).  MIXED_BF16: as MIXED_FP32 with the V-cycle's correction and residual
+   stored as bfloat16 (float arithmetic, float coefficients). */
+typedef enum { GMG_FP64 = 0, GMG_MIXED_FP32 = 1, GMG_MIXED_BF16 = 2 } gmg_precision;
+
+/* Element types of boxed-layout buffers. */
+typedef enum { GMG_DT_F64 = 0, GMG_DT_F32 = 1, GMG_DT_BF16 = 2 } gmg_dtype;
+
+typedef struct {
+  int nu1;              /* pre-smoothing sweeps (red + black), default 2 */
+  int nu2;              /* post-smoothing sweeps, default 2 */
+  int max_iter;         /* outer iterations, default 100 */
+  int bottom_max_iter;  /* BiCGStab iterations, default 200 */
+  double bottom_tol;    /* BiCGStab relative L-inf tolerance, default 1e-4 */
+  int precision;        /* gmg_precision, default GMG_FP64 */
+  int project_mean;     /* singular (all periodic, a = 0): project a nonzero-mean rhs
+                           instead of returning GMG_ERR_BAD_INPUT; default 0 */
+  int use_graph;        /* replay the V-cycle as a captured CUDA graph, default 1 */
+  int profile;          /* record CUDA events around every finest-level smoother and
+                           outer-residual launch (inside the graph too); default 0 */
+} gmg_params;
+
+typedef struct {
+  int iterations;        /* outer (V-cycle) iterations taken */
+  int status;            /* gmg_status of the solve */
+  double rhs_norm;       /* ||rhs||_inf (after mean projection for singular problems) */
+  double initial_resid;  /* ||r_0||_inf */
+  double final_resid;    /* ||r||_inf at exit, FP64 residual */
+  int hist_len;          /* entries in resid_hist */
+  double resid_hist[256];/* ||r||_inf after each iteration (index 0 = initial) */
+  int bottom_iters;      /* BiCGStab iterations of the last bottom solve */
+  double solve_ms;       /* wall time of the solve call (host clock) */
+  long long kernel_launches; /* kernels launched by the call (graph nodes counted per replay) */
+  double smooth0_ms;     /* with profile: summed device time of finest-level smoother launches */
+  int smooth0_launches;  /* ... and their number */
+  double resid0_ms;      /* with profile: summed device time of the outer FP64 residual launches */
+  int resid0_launches;
+} gmg_solve_info;
+
+/* ---------------------------------------------------------------- context */
+
+gmg_status gmg_default_params(gmg_params* p);
+
+/* Create a context bound to a CUDA stream (cudaStream_t passed as void*; NULL = the
+   legacy default stream).  *out receives the context. */
+gmg_status gmg_create(gmg_ctx** out, void* cuda_stream);
+gmg_status gmg_destroy(gmg_ctx* ctx);
+/* Message of the last error on ctx ("" if none).  ctx may be NULL (creation errors). */
+const char* gmg_last_error(const gmg_ctx* ctx);
+
+/* ---------------------------------------------------------------- geometry */
+
+/* Problem domain (Sec. "Basic data structures": Geometry + BCRec): inclusive cell-index
+   box [lo, hi], physical extent [prob_lo, prob_hi], one boundary condition per side.
+   A periodic direction must be periodic on both sides. */
+gmg_status gmg_define_domain(gmg_ctx* ctx, const int lo[3], const int hi[3], const double prob_lo[3],
+                             const double prob_hi[3], const int bc_lo[3], const int bc_hi[3]);
+
+/* BoxArray of AMR level `lev` (only lev = 0 in this version): nboxes boxes given as
+   box_lohi[6*b + 0..2] = lo, [6*b + 3..5] = hi (inclusive).  Boxes must be disjoint and
+   cover the domain.  Builds the multigrid hierarchy (per-box coarsening, then
+   aggregation into one box, Sec. "Linear Solvers"). */
+gmg_status gmg_define_level(gmg_ctx* ctx, int lev, int nboxes, const int* box_lohi, int ref_ratio);
+
+/* Convenience: BoxArray of level `lev` = the domain chopped into boxes of at most
+   max_grid_size cells per axis (Sec. "Regridding": max_grid_size). */
+gmg_status gmg_chop_domain(gmg_ctx* ctx, int lev, int max_grid_size);
+
+/* Number of multigrid levels of the hierarchy (level 0 = the user's BoxArray). */
+gmg_status gmg_mg_nlevels(const gmg_ctx* ctx, int* nlevels);
+
+/* MG level m: number of boxes and domain (dom[0..2] = lo, dom[3..5] = hi). */
+gmg_status gmg_mg_level_info(const gmg_ctx* ctx, int m, int* nboxes, int* dom);
+
+/* MG level m: boxes (6 ints each) and, for each box, the box of level m+1 that holds its
+   coarsened image (-1 on the bottom level).  Either pointer may be NULL. */
+gmg_status gmg_mg_level_boxes(const gmg_ctx* ctx, int m, int* box_lohi, int* parents);
+
+/* Boxed layout of MG level m for element type dt: total elements, per-box element
+   offsets (nboxes entries, may be NULL) and row strides sx (nboxes entries, may be
+   NULL). */
+gmg_status gmg_mg_layout(const gmg_ctx* ctx, int m, int dt, int64_t* nelems, int64_t* box_offsets, int* row_strides);
+
+/* Level-0 FP64 layout (same as gmg_mg_layout(ctx, 0, GMG_DT_F64, ...)). */
+gmg_status gmg_layout(const gmg_ctx* ctx, int lev, int64_t* nelems, int64_t* box_offsets);
+
+/* Dense (nz, ny, nx) FP64 device array over MG level m's domain <-> boxed layout of
+   element type dt.  pack writes valid cells only (ghosts untouched); unpack reads
+   valid cells only. */
+gmg_status gmg_pack(gmg_ctx* ctx, int m, int dt, const double* dense, void* boxed);
+gmg_status gmg_unpack(gmg_ctx* ctx, int m, int dt, const void* boxed, double* dense);
+
+/* ------------------------------------------------------------- coefficients */
+
+/* Scalars a and b of the operator equation. */
+gmg_status gmg_set_scalars(gmg_ctx* ctx, double a, double b);
+
+/* Cell-centred alpha of level lev (FP64, level-0 boxed layout, device).  Not calling it
+   means alpha = 1. */
+gmg_status gmg_set_acoef(gmg_ctx* ctx, int lev, const double* alpha_cc);
+
+/* Cell-centred beta (FP64, boxed layout, device); face beta = harmonic mean of the two
+   cells, the interior cell's value on a wall face.  Builds the coefficients of every
+   MG level (coarse alpha = mean of 8 children, coarse face beta = mean of the 4 fine
+   faces).  Needs the workspace. */
+gmg_status gmg_set_bcoef_cell(gmg_ctx* ctx, int lev, const double* beta_cc);
+
+/* Face beta given directly: three FP64 face arrays in the boxed layout (slot i = face
+   i - 1/2).  Builds every MG level's coefficients.  Needs the workspace. */
+gmg_status gmg_set_bcoef_face(gmg_ctx* ctx, int lev, const double* bx, const double* by, const double* bz);
+
+/* Scaled face weights w_d = b * beta_d / h_d^2 and diagonal D = a*alpha + sum of the six
+   weights of MG level m, copied into caller buffers of element type dt (NULL to skip). */
+gmg_status gmg_get_coeffs(gmg_ctx* ctx, int m, int dt, void* wx, void* wy, void* wz, void* diag);
+
+/* ---------------------------------------------------------------- workspace */
+
+/* Bytes of device workspace needed for solves with parameters p (NULL = defaults; a
+   mixed precision needs its float buffers in addition to the FP64 ones). */
+gmg_status gmg_workspace_size(const gmg_ctx* ctx, const gmg_params* p, size_t* bytes);
+
+/* Hand the library a device buffer of at least gmg_workspace_size bytes, 256-byte
+   aligned.  Uploads the index tables.  The buffer stays in use until replaced. */
+gmg_status gmg_set_workspace(gmg_ctx* ctx, void* dptr, size_t bytes);
+
+/* ------------------------------------------------------------------- solve */
+
+/* Solve A phi = rhs on level 0 from phi = 0 (phi's input content is ignored) until
+   ||rhs - A phi||_inf <= max(tol_rel * ||rhs||_inf, tol_abs) or p->max_iter outer
+   iterations.  phi, rhs: FP64 device arrays in the level-0 layout (phi[0], rhs[0]; the
+   arrays of pointers leave room for AMR levels).  info may be NULL.  Returns GMG_OK,
+   GMG_ERR_NOT_CONVERGED (phi holds the last iterate), GMG_ERR_DIVERGED or
+   GMG_ERR_BAD_INPUT (nonzero-mean rhs of a singular problem without project_mean). */
+gmg_status gmg_solve(gmg_ctx* ctx, void* const* phi, const void* const* rhs, double tol_rel, double tol_abs,
+                     const gmg_params* p, gmg_solve_info* info);
+
+/* out = A phi on level 0 (FP64; phi's ghost cells are overwritten). */
+gmg_status gmg_apply(gmg_ctx* ctx, void* const* out, void* const* phi);
+
+/* ------------------------------------------------ individual hot-path steps */
+/* Each step acts on MG level m with caller buffers of element type dt in that level's
+   boxed layout.  Coefficients come from the last gmg_set_bcoef_* call (float copies
+   for GMG_DT_F32 / GMG_DT_BF16 fields need a mixed-precision workspace). */
+
+/* FillBoundary: copy every face ghost cell from the box that owns it (periodic images
+   included) or apply the homogeneous Dirichlet reflection.  colour = 0 or 1 fills only
+   the ghosts whose global (i+j+k) parity is that colour; -1 fills all. */
+gmg_status gmg_fill_boundary(gmg_ctx* ctx, int m, int dt, void* field, int colour);
+
+/* One red-black Gauss-Seidel half sweep of colour 0 (red, i+j+k even) or 1 (black),
+   preceded by the ghost fill it needs. */
+gmg_status gmg_smooth(gmg_ctx* ctx, int m, int dt, void* phi, const void* rhs, int colour);
+
+/* r = rhs - A phi (ghosts of phi filled first).  r has element type rdt.  If norm is
+   non-NULL, *norm receives ||r||_inf (synchronises the stream). */
+gmg_status gmg_residual(gmg_ctx* ctx, int m, int dt, void* phi, const void* rhs, int rdt, void* r, double* norm);
+
+/* Average-down restriction of a cell field from MG level m to m+1 (mean of 8 children). */
+gmg_status gmg_restrict(gmg_ctx* ctx, int m, int dt, const void* fine, void* coarse);
+
+/* fine += piecewise-constant interpolation of coarse (MG level m+1 -> m). */
+gmg_status gmg_prolong_add(gmg_ctx* ctx, int m, int dt, const void* coarse, void* fine);
+
+/* BiCGStab on the bottom level: x = A_bottom^-1 rhs to bottom_tol (FP64 arithmetic,
+   buffers of type dt).  *iters (host, may be NULL) receives the iteration count. */
+gmg_status gmg_bottom_solve(gmg_ctx* ctx, int dt, const void* rhs, void* x, const gmg_params* p, int* iters);
+
+/* One V-cycle on the correction equation of MG level 0: e = V(r), element type dt. */
+gmg_status gmg_vcycle(gmg_ctx* ctx, int dt, void* e, const void* r, const gmg_params* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMG_H */

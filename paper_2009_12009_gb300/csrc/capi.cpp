@@ -1,0 +1,962 @@
+// capi.cpp -- C ABI (include/gmg.h) and the host driver of the V-cycle / outer loop.
+//
+// The host side owns only metadata: the hierarchy, the cached exchange tables and the
+// carve-up of the caller's workspace.  Every step of the solve runs in the kernels of
+// kernels.cu / bottom.cu; the host decides the launch order and reads back one norm per
+// outer iteration.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/gmg.h"
+#include "kernels.h"
+#include "meta.h"
+
+using namespace gmg;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+size_t dt_size(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
+
+struct LevelBufs {
+  // FP64 coefficients
+  double *acoef = nullptr, *wx = nullptr, *wy = nullptr, *wz = nullptr, *D = nullptr, *invD = nullptr;
+  // float coefficients (mixed precision)
+  float *fwx = nullptr, *fwy = nullptr, *fwz = nullptr, *fD = nullptr, *finvD = nullptr;
+  // V-cycle correction and right-hand side per element type
+  void* e[NDT] = {nullptr, nullptr, nullptr};
+  void* r[NDT] = {nullptr, nullptr, nullptr};
+  // bottom work vectors (7 doubles per element) if a bottom problem lives here
+  double* bot_work = nullptr;
+};
+
+// bump allocator over the caller's workspace; run once with base = nullptr to size
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  void* take(size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    void* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+}  // namespace
+
+struct gmg_ctx {
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  std::string err;
+
+  bool have_domain = false;
+  SolveGeom geom0;
+  double prob_lo[3] = {0, 0, 0}, prob_hi[3] = {1, 1, 1};
+  std::vector<LevelMeta> L;  // multigrid levels, 0 = user's BoxArray
+  double a = 0.0, b = 1.0;
+
+  // workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool mixed = false;  // float buffers present
+  std::vector<LevelDev> dev;
+  std::vector<LevelBufs> buf;
+  double *alpha0 = nullptr, *bx0 = nullptr, *by0 = nullptr, *bz0 = nullptr, *tmp0 = nullptr;
+  unsigned long long* normbits = nullptr;  // [0]: residual norm of the outer loop; [1..]: scratch
+  double* partials = nullptr;
+  double* scal = nullptr;  // [0]: rhs mean, [1]: phi mean, [2..]: scratch
+  int* bot_iters = nullptr;
+  int max_cell_chunks = 0;
+
+  bool have_beta = false, have_alpha = false;
+  bool coefs_dirty = true;
+
+  // pinned host mirror of a few device scalars
+  unsigned long long* h_bits = nullptr;
+  double* h_scal = nullptr;
+  int* h_iters = nullptr;
+
+  // graphs of one outer iteration, keyed by (phi, rhs, precision, nu1, nu2, bottom, profile)
+  std::map<std::tuple<void*, const void*, int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+
+  // profiling events (pairs around finest-level smoother / outer residual launches)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_smooth, ev_resid;
+  int n_ev_smooth = 0, n_ev_resid = 0;
+};
+
+#define SETERR(ctx, code, msg) \
+  do {                          \
+    (ctx)->err = (msg);         \
+    return (code);              \
+  } while (0)
+
+#define CK(ctx, call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
+      return GMG_ERR_CUDA;                                                                \
+    }                                                                                     \
+  } while (0)
+
+namespace {
+
+void drop_graphs(gmg_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  c->graphs.clear();
+}
+
+// event pair k of a list (created on first use)
+cudaEvent_t* ev_pair(std::vector<cudaEvent_t>& v, int k) {
+  while ((int)v.size() < 2 * (k + 1)) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    v.push_back(e);
+  }
+  return &v[2 * k];
+}
+
+bool singular(const gmg_ctx* c) { return c->geom0.all_periodic() && c->a == 0.0; }
+
+int nlev(const gmg_ctx* c) { return (int)c->L.size(); }
+
+Coefs coefs_of(const gmg_ctx* c, int m, int dt) {
+  const LevelBufs& B = c->buf[m];
+  Coefs k;
+  if (dt == DT_F64) {
+    k.wx = B.wx; k.wy = B.wy; k.wz = B.wz; k.D = B.D; k.invD = B.invD;
+  } else {
+    k.wx = B.fwx; k.wy = B.fwy; k.wz = B.fwz; k.D = B.fD; k.invD = B.finvD;
+  }
+  return k;
+}
+
+Coefs coefs64(const gmg_ctx* c, int m) { return coefs_of(c, m, DT_F64); }
+
+gmg_status check_level(gmg_ctx* c, int m, int dt) {
+  if (c->L.empty()) SETERR(c, GMG_ERR_STATE, "no BoxArray defined");
+  if (m < 0 || m >= nlev(c)) SETERR(c, GMG_ERR_BAD_INPUT, "MG level out of range");
+  if (dt < 0 || dt >= NDT) SETERR(c, GMG_ERR_BAD_INPUT, "bad element type");
+  if (!c->ws) SETERR(c, GMG_ERR_NO_WORKSPACE, "no workspace set");
+  if (dt != DT_F64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace has no float buffers (size it for a mixed precision)");
+  return GMG_OK;
+}
+
+// Carve the workspace (base = nullptr: size only).  Returns bytes.
+size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
+  Carver cv(base);
+  const int n = nlev(c);
+  if (fill) {
+    c->dev.assign(n, LevelDev());
+    c->buf.assign(n, LevelBufs());
+  }
+  int maxchunks = 1;
+  for (int m = 0; m < n; ++m) {
+    const LevelMeta& M = c->L[m];
+    const size_t ne = (size_t)M.nelem;
+    LevelDev D;
+    LevelBufs B;
+    D.nelem = M.nelem;
+    D.boxes = (const DevBox*)cv.take(sizeof(DevBox) * M.dbox.size());
+    D.geoms = (const DevGeom*)cv.take(sizeof(DevGeom) * M.geoms.size());
+    D.ghosts = (const GhostRect*)cv.take(sizeof(GhostRect) * M.ghosts.size());
+    D.ghost_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.ghost_chunks.size());
+    D.n_ghost_chunks = (int)M.ghost_chunks.size();
+    D.pair_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.pair_chunks.size());
+    D.n_pair_chunks = (int)M.pair_chunks.size();
+    D.pair_all_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.pair_all_chunks.size());
+    D.n_pair_all_chunks = (int)M.pair_all_chunks.size();
+    D.cell_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.cell_chunks.size());
+    D.n_cell_chunks = (int)M.cell_chunks.size();
+    D.coarse_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.coarse_chunks.size());
+    D.n_coarse_chunks = (int)M.coarse_chunks.size();
+    D.parent = (const int*)cv.take(sizeof(int) * M.parent.size());
+    D.bot_cells = (const BotCell*)cv.take(sizeof(BotCell) * M.bot_cells.size());
+    D.bot_ghosts = (const BotGhost*)cv.take(sizeof(BotGhost) * M.bot_ghosts.size());
+    D.bot_descs = (const BotDesc*)cv.take(sizeof(BotDesc) * M.bot_descs.size());
+    D.n_bot = (int)M.bot_descs.size();
+    maxchunks = std::max(maxchunks, D.n_cell_chunks);
+    B.acoef = (double*)cv.take(8 * ne);
+    B.wx = (double*)cv.take(8 * ne);
+    B.wy = (double*)cv.take(8 * ne);
+    B.wz = (double*)cv.take(8 * ne);
+    B.D = (double*)cv.take(8 * ne);
+    B.invD = (double*)cv.take(8 * ne);
+    B.e[DT_F64] = cv.take(8 * ne);
+    B.r[DT_F64] = cv.take(8 * ne);
+    if (mixed) {
+      B.fwx = (float*)cv.take(4 * ne);
+      B.fwy = (float*)cv.take(4 * ne);
+      B.fwz = (float*)cv.take(4 * ne);
+      B.fD = (float*)cv.take(4 * ne);
+      B.finvD = (float*)cv.take(4 * ne);
+      B.e[DT_F32] = cv.take(4 * ne);
+      B.r[DT_F32] = cv.take(4 * ne);
+      B.e[DT_BF16] = cv.take(2 * ne);
+      B.r[DT_BF16] = cv.take(2 * ne);
+    }
+    if (!M.bot_descs.empty()) B.bot_work = (double*)cv.take(8 * 7 * ne);
+    if (fill) {
+      c->dev[m] = D;
+      c->buf[m] = B;
+    }
+  }
+  const size_t ne0 = c->L.empty() ? 0 : (size_t)c->L[0].nelem;
+  double* alpha0 = (double*)cv.take(8 * ne0);
+  double* bx0 = (double*)cv.take(8 * ne0);
+  double* by0 = (double*)cv.take(8 * ne0);
+  double* bz0 = (double*)cv.take(8 * ne0);
+  double* tmp0 = (double*)cv.take(8 * ne0);
+  unsigned long long* nb = (unsigned long long*)cv.take(8 * 64);
+  double* partials = (double*)cv.take(8 * (size_t)maxchunks);
+  double* scal = (double*)cv.take(8 * 64);
+  int* iters = (int*)cv.take(4 * (c->L.empty() ? 1 : c->L[0].geoms.size()));
+  if (fill) {
+    c->alpha0 = alpha0; c->bx0 = bx0; c->by0 = by0; c->bz0 = bz0; c->tmp0 = tmp0;
+    c->normbits = nb; c->partials = partials; c->scal = scal; c->bot_iters = iters;
+    c->max_cell_chunks = maxchunks;
+  }
+  return cv.off + 256;
+}
+
+template <class V>
+gmg_status upload(gmg_ctx* c, const void* dst, const std::vector<V>& v) {
+  if (v.empty()) return GMG_OK;
+  CK(c, cudaMemcpyAsync((void*)dst, v.data(), sizeof(V) * v.size(), cudaMemcpyHostToDevice, c->stream));
+  return GMG_OK;
+}
+
+std::vector<DevGeom> dev_geoms(const LevelMeta& M) {
+  std::vector<DevGeom> g(M.geoms.size());
+  for (size_t s = 0; s < g.size(); ++s) {
+    const SolveGeom& G = M.geoms[s];
+    for (int d = 0; d < 3; ++d) {
+      g[s].dlo[d] = G.domain.lo[d];
+      g[s].dhi[d] = G.domain.hi[d];
+      g[s].wall_lo[d] = G.bclo[d] != 0;
+      g[s].wall_hi[d] = G.bchi[d] != 0;
+      g[s].ih2[d] = 1.0 / (G.h[d] * G.h[d]);
+    }
+  }
+  return g;
+}
+
+gmg_status upload_tables(gmg_ctx* c) {
+  for (int m = 0; m < nlev(c); ++m) {
+    const LevelMeta& M = c->L[m];
+    const LevelDev& D = c->dev[m];
+    gmg_status st;
+    if ((st = upload(c, D.boxes, M.dbox))) return st;
+    if ((st = upload(c, D.geoms, dev_geoms(M)))) return st;
+    if ((st = upload(c, D.ghosts, M.ghosts))) return st;
+    if ((st = upload(c, D.ghost_chunks, M.ghost_chunks))) return st;
+    if ((st = upload(c, D.pair_chunks, M.pair_chunks))) return st;
+    if ((st = upload(c, D.pair_all_chunks, M.pair_all_chunks))) return st;
+    if ((st = upload(c, D.cell_chunks, M.cell_chunks))) return st;
+    if ((st = upload(c, D.coarse_chunks, M.coarse_chunks))) return st;
+    if ((st = upload(c, D.parent, M.parent))) return st;
+    if ((st = upload(c, D.bot_cells, M.bot_cells))) return st;
+    if ((st = upload(c, D.bot_ghosts, M.bot_ghosts))) return st;
+    if ((st = upload(c, D.bot_descs, M.bot_descs))) return st;
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return GMG_OK;
+}
+
+// Build the multigrid hierarchy from level-0 boxes.
+gmg_status build_hierarchy(gmg_ctx* c, const std::vector<Box>& boxes) {
+  std::string e = validate_boxes(boxes, c->geom0.domain, true);
+  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, e);
+  drop_graphs(c);
+  c->L.clear();
+  c->ws = nullptr;
+  c->ws_bytes = 0;
+  c->have_beta = c->have_alpha = false;
+  c->coefs_dirty = true;
+  LevelMeta L0;
+  L0.boxes = boxes;
+  L0.box_solve.assign(boxes.size(), 0);
+  L0.geoms = {c->geom0};
+  L0.solve_present = {1};
+  L0.solve_bottom = {0};
+  c->L.push_back(L0);
+  for (int m = 0; m < 64; ++m) {
+    LevelMeta C;
+    bool more = make_coarse(c->L[m], C);
+    e = finalize_level(c->L[m]);
+    if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, e);
+    if (!more) break;
+    c->L.push_back(C);
+  }
+  return GMG_OK;
+}
+
+// Coefficients of every level from the stored level-0 alpha and face beta.
+gmg_status build_coefs(gmg_ctx* c) {
+  if (!c->coefs_dirty) return GMG_OK;
+  if (!c->have_beta) SETERR(c, GMG_ERR_STATE, "beta not set (gmg_set_bcoef_cell / gmg_set_bcoef_face)");
+  cudaStream_t s = c->stream;
+  launch_acoef(c->dev[0], c->a, c->have_alpha ? c->alpha0 : nullptr, c->buf[0].acoef, s);
+  launch_faces_scale(c->dev[0], c->b, c->bx0, c->by0, c->bz0, c->buf[0].wx, c->buf[0].wy, c->buf[0].wz, s);
+  for (int m = 0; m + 1 < nlev(c); ++m) {
+    const LevelBufs& F = c->buf[m];
+    const LevelBufs& C = c->buf[m + 1];
+    launch_coarsen_coefs(c->dev[m], c->dev[m + 1], F.acoef, F.wx, F.wy, F.wz, C.acoef, C.wx, C.wy, C.wz, s);
+  }
+  for (int m = 0; m < nlev(c); ++m) {
+    const LevelBufs& B = c->buf[m];
+    launch_diag(c->dev[m], B.acoef, B.wx, B.wy, B.wz, B.D, B.invD, s);
+    if (c->mixed) {
+      const int64_t n = c->L[m].nelem;
+      launch_convert(DT_F64, DT_F32, B.wx, B.fwx, n, s);
+      launch_convert(DT_F64, DT_F32, B.wy, B.fwy, n, s);
+      launch_convert(DT_F64, DT_F32, B.wz, B.fwz, n, s);
+      launch_convert(DT_F64, DT_F32, B.D, B.fD, n, s);
+      launch_convert(DT_F64, DT_F32, B.invD, B.finvD, n, s);
+    }
+  }
+  // singular flag of the bottom problems
+  for (int m = 0; m < nlev(c); ++m) {
+    LevelMeta& M = c->L[m];
+    for (auto& d : M.bot_descs) d.singular = singular(c) ? 1 : 0;
+    gmg_status st = upload(c, c->dev[m].bot_descs, M.bot_descs);
+    if (st) return st;
+  }
+  CK(c, cudaGetLastError());
+  c->coefs_dirty = false;
+  return GMG_OK;
+}
+
+// Fill coefficient buffers' ghost-free regions: face arrays need their high faces and the
+// diagonal its valid cells; fields are zeroed once so that untouched padding is finite.
+gmg_status zero_workspace(gmg_ctx* c) {
+  CK(c, cudaMemsetAsync(c->ws, 0, c->ws_bytes, c->stream));
+  return GMG_OK;
+}
+
+void smooth_colour(gmg_ctx* c, int dt, int m, int colour, cudaStream_t s) {
+  const LevelDev& D = c->dev[m];
+  const LevelBufs& B = c->buf[m];
+  launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
+  const bool prof = c->profiling && m == 0;
+  cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
+  // external event-record nodes when captured, so that the events carry timestamps
+  if (prof) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  launch_smooth(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s);
+  if (prof) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+}
+
+void smooth_sweeps(gmg_ctx* c, int dt, int m, int nsweep, cudaStream_t s) {
+  for (int it = 0; it < nsweep; ++it) {
+    smooth_colour(c, dt, m, 0, s);
+    smooth_colour(c, dt, m, 1, s);
+  }
+}
+
+// V-cycle on the correction equation of level m: e_m = V(r_m), e_m zeroed first.
+void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
+  const LevelDev& D = c->dev[m];
+  const LevelBufs& B = c->buf[m];
+  cudaMemsetAsync(B.e[dt], 0, dt_size(dt) * (size_t)c->L[m].nelem, s);
+  if (D.n_bot) {
+    BottomArgs a{p.bottom_max_iter, p.bottom_tol, B.bot_work, c->bot_iters};
+    launch_bottom(dt, D, B.r[dt], B.e[dt], coefs64(c, m), a, s);
+  }
+  if (m + 1 >= nlev(c) || D.n_pair_chunks == 0) return;
+  smooth_sweeps(c, dt, m, p.nu1, s);
+  launch_fill(dt, D, B.e[dt], -1, 0, s);
+  launch_resid_restrict(dt, D, c->dev[m + 1], B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
+  vcycle(c, dt, m + 1, p, s);
+  launch_prolong_add(dt, D, c->dev[m + 1], c->buf[m + 1].e[dt], B.e[dt], s);
+  smooth_sweeps(c, dt, m, p.nu2, s);
+}
+
+// One outer iteration: e = V(r); phi += e; r = rhs - A phi with ||r||_inf into normbits[0].
+void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const gmg_params& p, cudaStream_t s) {
+  vcycle(c, dt, 0, p, s);
+  launch_add_correction(dt, c->dev[0], phi, c->buf[0].e[dt], s);
+  launch_fill(DT_F64, c->dev[0], phi, -1, 0, s);
+  cudaMemsetAsync(c->normbits, 0, 8, s);
+  cudaEvent_t* ev = c->profiling ? ev_pair(c->ev_resid, c->n_ev_resid++) : nullptr;
+  if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  launch_residual(DT_F64, dt, c->dev[0], phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits,
+                  singular(c) ? c->scal : nullptr, s);
+  if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+  cudaMemcpyAsync(c->h_bits, c->normbits, 8, cudaMemcpyDeviceToHost, s);
+}
+
+// summed elapsed time (ms) of the first n event pairs of a list
+double pair_ms(const std::vector<cudaEvent_t>& v, int n) {
+  double t = 0.0;
+  for (int k = 0; k < n; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, v[2 * k], v[2 * k + 1]) == cudaSuccess) t += ms;
+    else cudaGetLastError();  // a missing timestamp is not an error of the solve
+  }
+  return t;
+}
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  memcpy(&d, &b, 8);
+  return d;
+}
+
+int dt_of_precision(int prec) { return prec == GMG_MIXED_FP32 ? DT_F32 : (prec == GMG_MIXED_BF16 ? DT_BF16 : DT_F64); }
+
+gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
+  if (p.nu1 < 0 || p.nu2 < 0 || p.nu1 + p.nu2 == 0 || p.max_iter < 0 || p.bottom_max_iter < 1 || !(p.bottom_tol > 0))
+    SETERR(c, GMG_ERR_BAD_INPUT, "invalid parameters");
+  if (p.precision < GMG_FP64 || p.precision > GMG_MIXED_BF16) SETERR(c, GMG_ERR_BAD_INPUT, "invalid precision");
+  if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
+  return GMG_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+gmg_status gmg_default_params(gmg_params* p) {
+  if (!p) return GMG_ERR_BAD_INPUT;
+  p->nu1 = 2;
+  p->nu2 = 2;
+  p->max_iter = 100;
+  p->bottom_max_iter = 200;
+  p->bottom_tol = 1e-4;
+  p->precision = GMG_FP64;
+  p->project_mean = 0;
+  p->use_graph = 1;
+  p->profile = 0;
+  return GMG_OK;
+}
+
+gmg_status gmg_create(gmg_ctx** out, void* stream) {
+  if (!out) return GMG_ERR_BAD_INPUT;
+  *out = nullptr;
+  gmg_ctx* c = new gmg_ctx();
+  c->stream = (cudaStream_t)stream;
+  *out = c;
+  return GMG_OK;
+}
+
+gmg_status gmg_destroy(gmg_ctx* c) {
+  if (!c) return GMG_OK;
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->h_bits) cudaFreeHost(c->h_bits);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->h_iters) cudaFreeHost(c->h_iters);
+  delete c;
+  return GMG_OK;
+}
+
+const char* gmg_last_error(const gmg_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+gmg_status gmg_define_domain(gmg_ctx* c, const int lo[3], const int hi[3], const double plo[3], const double phi[3],
+                             const int bclo[3], const int bchi[3]) {
+  if (!c || !lo || !hi || !plo || !phi || !bclo || !bchi) return GMG_ERR_BAD_INPUT;
+  SolveGeom G;
+  for (int d = 0; d < 3; ++d) {
+    if (hi[d] < lo[d]) SETERR(c, GMG_ERR_BAD_INPUT, "empty domain");
+    if (!(phi[d] > plo[d])) SETERR(c, GMG_ERR_BAD_INPUT, "prob_hi must exceed prob_lo");
+    if ((bclo[d] != GMG_BC_PERIODIC && bclo[d] != GMG_BC_DIRICHLET0) ||
+        (bchi[d] != GMG_BC_PERIODIC && bchi[d] != GMG_BC_DIRICHLET0))
+      SETERR(c, GMG_ERR_BAD_INPUT, "unknown boundary condition");
+    if ((bclo[d] == GMG_BC_PERIODIC) != (bchi[d] == GMG_BC_PERIODIC))
+      SETERR(c, GMG_ERR_BAD_INPUT, "a periodic direction must be periodic on both sides");
+    G.domain.lo[d] = lo[d];
+    G.domain.hi[d] = hi[d];
+    G.bclo[d] = bclo[d];
+    G.bchi[d] = bchi[d];
+    G.h[d] = (phi[d] - plo[d]) / (double)(hi[d] - lo[d] + 1);
+    c->prob_lo[d] = plo[d];
+    c->prob_hi[d] = phi[d];
+  }
+  c->geom0 = G;
+  c->have_domain = true;
+  c->L.clear();
+  c->ws = nullptr;
+  drop_graphs(c);
+  c->err.clear();
+  return GMG_OK;
+}
+
+gmg_status gmg_define_level(gmg_ctx* c, int lev, int nboxes, const int* lohi, int ref_ratio) {
+  (void)ref_ratio;
+  if (!c) return GMG_ERR_BAD_INPUT;
+  if (!c->have_domain) SETERR(c, GMG_ERR_STATE, "define the domain first");
+  if (lev != 0) SETERR(c, GMG_ERR_BAD_INPUT, "only AMR level 0 is supported by gmg_define_level");
+  if (nboxes <= 0 || !lohi) SETERR(c, GMG_ERR_BAD_INPUT, "no boxes");
+  std::vector<Box> boxes(nboxes);
+  for (int b = 0; b < nboxes; ++b)
+    for (int d = 0; d < 3; ++d) {
+      boxes[b].lo[d] = lohi[6 * b + d];
+      boxes[b].hi[d] = lohi[6 * b + 3 + d];
+    }
+  return build_hierarchy(c, boxes);
+}
+
+gmg_status gmg_chop_domain(gmg_ctx* c, int lev, int mgs) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  if (!c->have_domain) SETERR(c, GMG_ERR_STATE, "define the domain first");
+  if (lev != 0) SETERR(c, GMG_ERR_BAD_INPUT, "only AMR level 0 is supported by gmg_chop_domain");
+  if (mgs < 1) SETERR(c, GMG_ERR_BAD_INPUT, "max_grid_size must be positive");
+  return build_hierarchy(c, chop(c->geom0.domain, mgs));
+}
+
+gmg_status gmg_mg_nlevels(const gmg_ctx* c, int* n) {
+  if (!c || !n) return GMG_ERR_BAD_INPUT;
+  *n = (int)c->L.size();
+  return GMG_OK;
+}
+
+gmg_status gmg_mg_level_info(const gmg_ctx* c, int m, int* nboxes, int* dom) {
+  if (!c || m < 0 || m >= (int)c->L.size()) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = c->L[m];
+  if (nboxes) *nboxes = (int)M.boxes.size();
+  if (dom)
+    for (int d = 0; d < 3; ++d) {
+      dom[d] = M.geoms[0].domain.lo[d];
+      dom[3 + d] = M.geoms[0].domain.hi[d];
+    }
+  return GMG_OK;
+}
+
+gmg_status gmg_mg_level_boxes(const gmg_ctx* c, int m, int* lohi, int* parents) {
+  if (!c || m < 0 || m >= (int)c->L.size()) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = c->L[m];
+  for (size_t b = 0; b < M.boxes.size(); ++b) {
+    if (lohi)
+      for (int d = 0; d < 3; ++d) {
+        lohi[6 * b + d] = M.boxes[b].lo[d];
+        lohi[6 * b + 3 + d] = M.boxes[b].hi[d];
+      }
+    if (parents) parents[b] = M.parent[b];
+  }
+  return GMG_OK;
+}
+
+gmg_status gmg_mg_layout(const gmg_ctx* c, int m, int dt, int64_t* nelems, int64_t* offs, int* sx) {
+  if (!c || m < 0 || m >= (int)c->L.size() || dt < 0 || dt >= NDT) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = c->L[m];
+  if (nelems) *nelems = M.nelem;
+  for (size_t b = 0; b < M.dbox.size(); ++b) {
+    if (offs) offs[b] = M.dbox[b].off;
+    if (sx) sx[b] = M.dbox[b].sx;
+  }
+  return GMG_OK;
+}
+
+gmg_status gmg_layout(const gmg_ctx* c, int lev, int64_t* nelems, int64_t* offs) {
+  if (lev != 0) return GMG_ERR_BAD_INPUT;
+  return gmg_mg_layout(c, 0, DT_F64, nelems, offs, nullptr);
+}
+
+gmg_status gmg_pack(gmg_ctx* c, int m, int dt, const double* dense, void* boxed) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, m, dt);
+  if (st) return st;
+  const SolveGeom& G = c->L[m].geoms[0];
+  int dn[3] = {G.domain.n(0), G.domain.n(1), G.domain.n(2)};
+  launch_pack(dt, c->dev[m], G.domain.lo, dn, dense, boxed, c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_unpack(gmg_ctx* c, int m, int dt, const void* boxed, double* dense) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, m, dt);
+  if (st) return st;
+  const SolveGeom& G = c->L[m].geoms[0];
+  int dn[3] = {G.domain.n(0), G.domain.n(1), G.domain.n(2)};
+  launch_unpack(dt, c->dev[m], G.domain.lo, dn, boxed, dense, c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_set_scalars(gmg_ctx* c, double a, double b) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  if (!std::isfinite(a) || !std::isfinite(b) || b == 0.0) SETERR(c, GMG_ERR_BAD_INPUT, "a must be finite and b finite and nonzero");
+  c->a = a;
+  c->b = b;
+  c->coefs_dirty = true;
+  drop_graphs(c);
+  return GMG_OK;
+}
+
+gmg_status gmg_set_acoef(gmg_ctx* c, int lev, const double* alpha) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if (lev != 0 || !alpha) SETERR(c, GMG_ERR_BAD_INPUT, "alpha: only level 0, non-null");
+  CK(c, cudaMemcpyAsync(c->alpha0, alpha, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, c->stream));
+  c->have_alpha = true;
+  c->coefs_dirty = true;
+  return GMG_OK;
+}
+
+gmg_status gmg_set_bcoef_cell(gmg_ctx* c, int lev, const double* beta) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if (lev != 0 || !beta) SETERR(c, GMG_ERR_BAD_INPUT, "beta: only level 0, non-null");
+  cudaStream_t s = c->stream;
+  CK(c, cudaMemcpyAsync(c->tmp0, beta, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, s));
+  launch_fill(DT_F64, c->dev[0], c->tmp0, -1, 1, s);
+  launch_faces_from_cell(c->dev[0], c->tmp0, c->bx0, c->by0, c->bz0, s);
+  CK(c, cudaGetLastError());
+  c->have_beta = true;
+  c->coefs_dirty = true;
+  return build_coefs(c);
+}
+
+gmg_status gmg_set_bcoef_face(gmg_ctx* c, int lev, const double* bx, const double* by, const double* bz) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if (lev != 0 || !bx || !by || !bz) SETERR(c, GMG_ERR_BAD_INPUT, "beta faces: only level 0, non-null");
+  const size_t n = 8 * (size_t)c->L[0].nelem;
+  CK(c, cudaMemcpyAsync(c->bx0, bx, n, cudaMemcpyDeviceToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(c->by0, by, n, cudaMemcpyDeviceToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(c->bz0, bz, n, cudaMemcpyDeviceToDevice, c->stream));
+  c->have_beta = true;
+  c->coefs_dirty = true;
+  return build_coefs(c);
+}
+
+gmg_status gmg_get_coeffs(gmg_ctx* c, int m, int dt, void* wx, void* wy, void* wz, void* diag) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, m, dt);
+  if (st) return st;
+  if ((st = build_coefs(c))) return st;
+  const LevelBufs& B = c->buf[m];
+  const int64_t n = c->L[m].nelem;
+  const int src = (dt == DT_F64) ? DT_F64 : DT_F32;
+  const Coefs k = coefs_of(c, m, src);
+  if (wx) launch_convert(src, dt, k.wx, wx, n, c->stream);
+  if (wy) launch_convert(src, dt, k.wy, wy, n, c->stream);
+  if (wz) launch_convert(src, dt, k.wz, wz, n, c->stream);
+  if (diag) launch_convert(src, dt, k.D, diag, n, c->stream);
+  (void)B;
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_workspace_size(const gmg_ctx* cc, const gmg_params* p, size_t* bytes) {
+  gmg_ctx* c = (gmg_ctx*)cc;
+  if (!c || !bytes) return GMG_ERR_BAD_INPUT;
+  if (c->L.empty()) SETERR(c, GMG_ERR_STATE, "no BoxArray defined");
+  const bool mixed = p && p->precision != GMG_FP64;
+  *bytes = carve(c, nullptr, mixed, false);
+  return GMG_OK;
+}
+
+gmg_status gmg_set_workspace(gmg_ctx* c, void* dptr, size_t bytes) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  if (c->L.empty()) SETERR(c, GMG_ERR_STATE, "no BoxArray defined");
+  if (!dptr || ((uintptr_t)dptr & 255)) SETERR(c, GMG_ERR_BAD_INPUT, "workspace must be non-null and 256-byte aligned");
+  const size_t need64 = carve(c, nullptr, false, false);
+  const size_t needmx = carve(c, nullptr, true, false);
+  bool mixed;
+  if (bytes >= needmx) mixed = true;
+  else if (bytes >= need64) mixed = false;
+  else SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace too small");
+  drop_graphs(c);
+  if (!c->cap_stream) CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (!c->h_bits) CK(c, cudaHostAlloc((void**)&c->h_bits, 64 * sizeof(unsigned long long), cudaHostAllocDefault));
+  if (!c->h_scal) CK(c, cudaHostAlloc((void**)&c->h_scal, 64 * sizeof(double), cudaHostAllocDefault));
+  if (!c->h_iters) CK(c, cudaHostAlloc((void**)&c->h_iters, 4096 * sizeof(int), cudaHostAllocDefault));
+  c->ws = dptr;
+  c->ws_bytes = bytes;
+  c->mixed = mixed;
+  carve(c, dptr, mixed, true);
+  gmg_status st = zero_workspace(c);
+  if (st) return st;
+  st = upload_tables(c);
+  if (st) return st;
+  c->have_beta = c->have_alpha = false;
+  c->coefs_dirty = true;
+  return GMG_OK;
+}
+
+gmg_status gmg_fill_boundary(gmg_ctx* c, int m, int dt, void* f, int colour) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, m, dt);
+  if (st) return st;
+  if (colour < -1 || colour > 1) SETERR(c, GMG_ERR_BAD_INPUT, "colour must be -1, 0 or 1");
+  launch_fill(dt, c->dev[m], f, colour, 0, c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_smooth(gmg_ctx* c, int m, int dt, void* phi, const void* rhs, int colour) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, m, dt);
+  if (st) return st;
+  if (colour < 0 || colour > 1) SETERR(c, GMG_ERR_BAD_INPUT, "colour must be 0 or 1");
+  if ((st = build_coefs(c))) return st;
+  // the smoother's work list skips bottom boxes; for a test of the bottom level smooth
+  // over every box
+  LevelDev D = c->dev[m];
+  if (D.n_pair_chunks == 0) {
+    D.pair_chunks = D.pair_all_chunks;
+    D.n_pair_chunks = D.n_pair_all_chunks;
+  }
+  launch_fill(dt, D, phi, 1 - colour, 0, c->stream);
+  launch_smooth(dt, D, phi, rhs, coefs_of(c, m, dt), colour, c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_residual(gmg_ctx* c, int m, int dt, void* phi, const void* rhs, int rdt, void* r, double* norm) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, m, dt);
+  if (st) return st;
+  if (rdt < 0 || rdt >= NDT) SETERR(c, GMG_ERR_BAD_INPUT, "bad residual type");
+  if (dt != DT_F64 && rdt == DT_F64) SETERR(c, GMG_ERR_BAD_INPUT, "a float residual pass cannot write double");
+  if ((st = build_coefs(c))) return st;
+  cudaStream_t s = c->stream;
+  launch_fill(dt, c->dev[m], phi, -1, 0, s);
+  unsigned long long* nb = c->normbits + 1;
+  CK(c, cudaMemsetAsync(nb, 0, 8, s));
+  launch_residual(dt, rdt, c->dev[m], phi, rhs, coefs_of(c, m, dt), r, norm ? nb : nullptr, nullptr, s);
+  CK(c, cudaGetLastError());
+  if (norm) {
+    CK(c, cudaMemcpyAsync(c->h_bits + 1, nb, 8, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    *norm = bits_to_double(c->h_bits[1]);
+  }
+  return GMG_OK;
+}
+
+gmg_status gmg_restrict(gmg_ctx* c, int m, int dt, const void* fine, void* coarse) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, m, dt);
+  if (st) return st;
+  if (m + 1 >= nlev(c)) SETERR(c, GMG_ERR_BAD_INPUT, "no coarser level");
+  launch_restrict(dt, c->dev[m], c->dev[m + 1], fine, coarse, c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_prolong_add(gmg_ctx* c, int m, int dt, const void* coarse, void* fine) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, m, dt);
+  if (st) return st;
+  if (m + 1 >= nlev(c)) SETERR(c, GMG_ERR_BAD_INPUT, "no coarser level");
+  launch_prolong_add(dt, c->dev[m], c->dev[m + 1], coarse, fine, c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_bottom_solve(gmg_ctx* c, int dt, const void* rhs, void* x, const gmg_params* pp, int* iters) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_params p;
+  gmg_default_params(&p);
+  if (pp) p = *pp;
+  gmg_status st = check_level(c, 0, dt);
+  if (st) return st;
+  if ((st = build_coefs(c))) return st;
+  const int m = nlev(c) - 1;
+  BottomArgs a{p.bottom_max_iter, p.bottom_tol, c->buf[m].bot_work, c->bot_iters};
+  launch_bottom(dt, c->dev[m], rhs, x, coefs64(c, m), a, c->stream);
+  CK(c, cudaGetLastError());
+  if (iters) {
+    CK(c, cudaMemcpyAsync(c->h_iters, c->bot_iters, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *iters = c->h_iters[0];
+  }
+  return GMG_OK;
+}
+
+gmg_status gmg_vcycle(gmg_ctx* c, int dt, void* e, const void* r, const gmg_params* pp) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_params p;
+  gmg_default_params(&p);
+  if (pp) p = *pp;
+  gmg_status st = check_level(c, 0, dt);
+  if (st) return st;
+  if ((st = build_coefs(c))) return st;
+  const size_t n = dt_size(dt) * (size_t)c->L[0].nelem;
+  CK(c, cudaMemcpyAsync(c->buf[0].r[dt], r, n, cudaMemcpyDeviceToDevice, c->stream));
+  vcycle(c, dt, 0, p, c->stream);
+  CK(c, cudaGetLastError());
+  CK(c, cudaMemcpyAsync(e, c->buf[0].e[dt], n, cudaMemcpyDeviceToDevice, c->stream));
+  return GMG_OK;
+}
+
+gmg_status gmg_apply(gmg_ctx* c, void* const* out, void* const* phi) {
+  if (!c || !out || !phi || !out[0] || !phi[0]) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if ((st = build_coefs(c))) return st;
+  cudaStream_t s = c->stream;
+  // out = -(0 - A phi): the residual pass with a zero right-hand side, negated
+  launch_fill(DT_F64, c->dev[0], phi[0], -1, 0, s);
+  CK(c, cudaMemsetAsync(c->tmp0, 0, 8 * (size_t)c->L[0].nelem, s));
+  launch_residual(DT_F64, DT_F64, c->dev[0], phi[0], c->tmp0, coefs64(c, 0), out[0], nullptr, nullptr, s);
+  launch_scale_valid(c->dev[0], (double*)out[0], -1.0, s);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_solve(gmg_ctx* c, void* const* phiv, const void* const* rhsv, double tol_rel, double tol_abs,
+                     const gmg_params* pp, gmg_solve_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!c || !phiv || !rhsv || !phiv[0] || !rhsv[0]) return GMG_ERR_BAD_INPUT;
+  gmg_params p;
+  gmg_default_params(&p);
+  if (pp) p = *pp;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if ((st = params_ok(c, p))) return st;
+  if ((st = build_coefs(c))) return st;
+  double* phi = (double*)phiv[0];
+  const double* rhs = (const double*)rhsv[0];
+  const int dt = dt_of_precision(p.precision);
+  cudaStream_t s = c->stream;
+  const LevelDev& D0 = c->dev[0];
+  const int64_t ne0 = c->L[0].nelem;
+  const bool sing = singular(c);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+  }
+  const int64_t l_pro = kernel_launch_count();
+  // ||rhs||_inf and, for a singular problem, mean(rhs)
+  CK(c, cudaMemsetAsync(c->normbits, 0, 16, s));
+  launch_norm_max(D0, rhs, c->normbits + 1, s);
+  if (sing) launch_sum(D0, rhs, c->partials, c->scal, s);
+  CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 16, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  const double rhsnorm = bits_to_double(c->h_bits[1]);
+  if (!std::isfinite(rhsnorm)) SETERR(c, GMG_ERR_BAD_INPUT, "rhs is not finite");
+  if (sing) {
+    const double mean = c->h_scal[0] / (double)c->L[0].ncells;
+    c->h_scal[1] = mean;
+    if (std::fabs(mean) > 1e-12 * rhsnorm && !p.project_mean) {
+      if (info) info->status = GMG_ERR_BAD_INPUT;
+      SETERR(c, GMG_ERR_BAD_INPUT, "singular problem with a nonzero-mean rhs (set project_mean)");
+    }
+    CK(c, cudaMemcpyAsync(c->scal, c->h_scal + 1, 8, cudaMemcpyHostToDevice, s));
+  }
+  double target = tol_rel * rhsnorm;
+  if (tol_abs > target) target = tol_abs;
+  // phi = 0; r = (rhs - mean) - A 0
+  CK(c, cudaMemsetAsync(phi, 0, 8 * (size_t)ne0, s));
+  CK(c, cudaMemsetAsync(c->normbits, 0, 8, s));
+  launch_residual(DT_F64, dt, D0, phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits, sing ? c->scal : nullptr, s);
+  CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 8, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  double rn = bits_to_double(c->h_bits[0]);
+  std::vector<double> hist{rn};
+  const int64_t prologue_launches = kernel_launch_count() - l_pro;
+  int it = 0;
+  gmg_status result = GMG_OK;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t per_iter = 0;
+  c->profiling = p.profile != 0;
+  if (c->profiling) {  // events are created outside any capture
+    ev_pair(c->ev_smooth, 2 * (p.nu1 + p.nu2) - 1);
+    ev_pair(c->ev_resid, 0);
+  }
+  double sm_ms = 0.0, rs_ms = 0.0;
+  int sm_n = 0, rs_n = 0;
+  if (p.use_graph) {
+    auto key = std::make_tuple(phiv[0], rhsv[0], p.precision, p.nu1, p.nu2, p.bottom_max_iter, p.bottom_tol,
+                               p.profile);
+    auto itg = c->graphs.find(key);
+    if (itg != c->graphs.end()) {
+      gexec = itg->second.first;
+      per_iter = itg->second.second;
+      c->n_ev_smooth = 2 * (p.nu1 + p.nu2);
+      c->n_ev_resid = 1;
+    } else {
+      cudaGraph_t g;
+      const int64_t l0 = kernel_launch_count();
+      c->n_ev_smooth = c->n_ev_resid = 0;
+      CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      outer_iteration(c, dt, phi, rhs, p, c->cap_stream);
+      cudaError_t e1 = cudaStreamEndCapture(c->cap_stream, &g);
+      if (e1 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+      cudaError_t e2 = cudaGraphInstantiate(&gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+      per_iter = kernel_launch_count() - l0;
+      count_launches((int)-per_iter);  // captured, not launched
+      c->graphs[key] = {gexec, per_iter};
+    }
+  }
+  int64_t launched = 0;
+  while (!(rn <= target) && it < p.max_iter) {
+    if (gexec) {
+      CK(c, cudaGraphLaunch(gexec, s));
+      launched += per_iter;
+    } else {
+      const int64_t l0 = kernel_launch_count();
+      c->n_ev_smooth = c->n_ev_resid = 0;
+      outer_iteration(c, dt, phi, rhs, p, s);
+      launched += kernel_launch_count() - l0;
+    }
+    CK(c, cudaStreamSynchronize(s));
+    CK(c, cudaGetLastError());
+    if (c->profiling) {
+      sm_ms += pair_ms(c->ev_smooth, c->n_ev_smooth);
+      sm_n += c->n_ev_smooth;
+      rs_ms += pair_ms(c->ev_resid, c->n_ev_resid);
+      rs_n += c->n_ev_resid;
+    }
+    rn = bits_to_double(c->h_bits[0]);
+    ++it;
+    hist.push_back(rn);
+    if (!std::isfinite(rn)) {
+      result = GMG_ERR_DIVERGED;
+      break;
+    }
+  }
+  c->profiling = false;
+  if (result == GMG_OK && !(rn <= target)) result = GMG_ERR_NOT_CONVERGED;
+  const int64_t l_epi = kernel_launch_count();
+  if (sing) {
+    // phi -= mean(phi)
+    launch_sum(D0, phi, c->partials, c->scal + 1, s);
+    launch_add_scalar(D0, phi, c->scal + 1, -1.0 / (double)c->L[0].ncells, s);
+    CK(c, cudaGetLastError());
+  }
+  CK(c, cudaMemcpyAsync(c->h_iters, c->bot_iters, 4, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  if (info) {
+    info->iterations = it;
+    info->status = result;
+    info->rhs_norm = rhsnorm;
+    info->initial_resid = hist[0];
+    info->final_resid = rn;
+    info->hist_len = (int)std::min<size_t>(hist.size(), 256);
+    for (int i = 0; i < info->hist_len; ++i) info->resid_hist[i] = hist[i];
+    info->bottom_iters = c->h_iters[0];
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->kernel_launches = launched + prologue_launches + (kernel_launch_count() - l_epi);
+    info->smooth0_ms = sm_ms;
+    info->smooth0_launches = sm_n;
+    info->resid0_ms = rs_ms;
+    info->resid0_launches = rs_n;
+  }
+  if (result == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
+  if (result == GMG_ERR_DIVERGED) c->err = "residual is not finite";
+  return result;
+}
+
+}  // extern "C"

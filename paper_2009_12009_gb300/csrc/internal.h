@@ -1,0 +1,85 @@
+// internal.h -- shared host/device definitions of the GB300 multigrid library.
+//
+// Data model (Sec. "Basic data structures", Sec. "Containers for mesh data"): a level is
+// a list of disjoint boxes; every field on a level is one flat device buffer holding one
+// ghosted block per box.  All element types share one layout per level (offsets are
+// counted in elements), so a float field, a bfloat16 field and a double coefficient
+// array of the same level are indexed with the same numbers.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace gmg {
+
+enum { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2, NDT = 3 };
+
+// Valid cell i of a row sits at element GX + i; GX elements = 16 B for bfloat16, 32 B for
+// float, 64 B for double, so the first valid cell of every row is 16-byte aligned.
+constexpr int GX = 8;
+// Row strides are multiples of this many elements (32 B for bfloat16).
+constexpr int ROW_ALIGN = 16;
+// Box offsets are multiples of this many elements.
+constexpr int BOX_ALIGN = 64;
+
+// Threads per block of the cell/pair kernels and items per block.
+constexpr int BLOCK = 256;
+// Ghost elements handled by one block of the ghost-exchange kernel.
+constexpr int GHOST_CHUNK = 1024;
+
+struct DevBox {
+  int64_t off;   // element offset of the box's ghosted block
+  int64_t sy;    // plane stride (elements) = sx * (ny + 2)
+  int nx, ny, nz;
+  int sx;        // row stride (elements)
+  int lo[3];     // global index of the box's first valid cell on its level
+  int solve;     // index of the independent solve this box belongs to (batched form)
+};
+
+// One rectangle of face ghost cells of box dst_box and where its values come from.
+struct GhostRect {
+  int dst_box, src_box;
+  int dst[3];    // local coordinates of the rectangle's first ghost cell
+  int src[3];    // local coordinates (in src_box) of its source cell
+  int d1, d2;    // tangential axes iterated by u (fastest) and v
+  int n1, n2;    // extents along d1, d2
+  int sign;      // +1: copy; -1: homogeneous Dirichlet reflection
+  int par0;      // global (i+j+k) parity of the first ghost cell
+  int kind;      // 0: copy from a box of the same level (periodic images included); 1: wall
+};
+
+// Generic work-list entry: block b handles items [start, start + per-block) of `item`.
+struct Chunk {
+  int item;
+  int start;
+};
+
+// A valid cell of the bottom level (for the single-block BiCGStab kernel).
+struct BotCell {
+  int64_t q;     // element offset
+  int64_t sy;    // plane stride of its box
+  int sx;        // row stride of its box
+  int pad;
+};
+
+// Ghost assignment of the bottom level, flattened: f[dst] = sign * f[src].
+struct BotGhost {
+  int64_t dst, src;
+  double sign;
+};
+
+// One bottom problem (one per independent solve in the batched form).
+struct BotDesc {
+  int cell0, ncell;     // range in the BotCell list
+  int ghost0, nghost;   // range in the BotGhost list
+  int singular;         // project onto zero mean
+  int solve;
+};
+
+__host__ __device__ inline int64_t elem_index(const DevBox& B, int i, int j, int k) {
+  return B.off + GX + i + (int64_t)B.sx * (j + 1) + B.sy * (k + 1);
+}
+
+}  // namespace gmg

@@ -1,0 +1,694 @@
+// kernels.cu -- sm_103a kernels of the multigrid V-cycle.
+//
+// Every kernel reads a work list of Chunk entries (box, first item) built once on the
+// host, so one launch covers all boxes of a level (the fused launch of Sec.
+// "Communication" applied to every step, not only to ghost exchange).  Arithmetic is
+// double for double fields and float for float / bfloat16 fields.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace gmg {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+template <class T> struct Arith { using type = float; };
+template <> struct Arith<double> { using type = double; };
+template <class T> struct CoefOf { using type = float; };
+template <> struct CoefOf<double> { using type = double; };
+
+__device__ __forceinline__ double ld(const double* p) { return *p; }
+__device__ __forceinline__ float ld(const float* p) { return *p; }
+__device__ __forceinline__ float ld(const bf16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg(const bf16* p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ void st(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void st(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st(bf16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+
+__device__ __forceinline__ int64_t axis_stride(const DevBox& B, int d) {
+  return d == 0 ? 1 : (d == 1 ? (int64_t)B.sx : B.sy);
+}
+
+// |v| as ordered bits: for non-negative doubles the IEEE bit pattern is monotone, and a
+// NaN (all exponent bits set, nonzero mantissa) compares above +inf, so the max of the
+// bits is the max of |v| with NaN propagating.  Integer max keeps the FP64 pipe free.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+__device__ __forceinline__ void block_max_atomic(unsigned long long v, unsigned long long* out) {
+  __shared__ unsigned long long red[BLOCK / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_down_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (BLOCK / 32) ? red[threadIdx.x] : 0ULL;
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long w = __shfl_down_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
+    if (threadIdx.x == 0 && v) atomicMax(out, v);
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[BLOCK / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < BLOCK / 32; ++w) s += red[w];
+  return s;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------- ghost exchange
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_fill(const DevBox* __restrict__ boxes, const GhostRect* __restrict__ rects,
+                                                const Chunk* __restrict__ chunks, T* f, int colour, int copy_mode) {
+  const Chunk ch = chunks[blockIdx.x];
+  const GhostRect g = rects[ch.item];
+  if (copy_mode && g.kind == 1) return;
+  const DevBox Bd = boxes[g.dst_box];
+  const DevBox Bs = boxes[g.src_box];
+  const int64_t d0 = elem_index(Bd, g.dst[0], g.dst[1], g.dst[2]);
+  const int64_t s0 = elem_index(Bs, g.src[0], g.src[1], g.src[2]);
+  const int64_t du = axis_stride(Bd, g.d1), dv = axis_stride(Bd, g.d2);
+  const int64_t su = axis_stride(Bs, g.d1), sv = axis_stride(Bs, g.d2);
+  const int n = g.n1 * g.n2;
+  const int end = min(n, ch.start + GHOST_CHUNK);
+  for (int e = ch.start + threadIdx.x; e < end; e += BLOCK) {
+    const int u = e % g.n1, v = e / g.n1;
+    if (colour >= 0 && ((g.par0 + u + v) & 1) != colour) continue;
+    const auto val = ld(f + s0 + u * su + v * sv);
+    st(f + d0 + u * du + v * dv, g.sign < 0 ? -val : val);
+  }
+}
+
+// decode a pair item of box B into (i0, j, k); i0 even
+__device__ __forceinline__ void pair_decode(const DevBox& B, int t, int& i0, int& j, int& k) {
+  const int npx = (B.nx + 1) >> 1;
+  const int p = t % npx;
+  const int r = t / npx;
+  j = r % B.ny;
+  k = r / B.ny;
+  i0 = 2 * p;
+}
+
+// ------------------------------------------------------------ red-black smoother
+
+// One colour of Gauss-Seidel: each thread owns a pair of x-adjacent cells and updates
+// the one whose global (i+j+k) parity is `colour`:
+//   phi = invD * (rhs + sum_f w_f phi_nbr)          (7 FMA-pipe operations)
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                  T* phi, const T* __restrict__ rhs,
+                                                  const typename CoefOf<T>::type* __restrict__ wx,
+                                                  const typename CoefOf<T>::type* __restrict__ wy,
+                                                  const typename CoefOf<T>::type* __restrict__ wz,
+                                                  const typename CoefOf<T>::type* __restrict__ invD, int colour) {
+  using A = typename Arith<T>::type;
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= ((B.nx + 1) >> 1) * B.ny * B.nz) return;
+  int i, j, k;
+  pair_decode(B, t, i, j, k);
+  i += (B.lo[0] + B.lo[1] + B.lo[2] + j + k + colour) & 1;
+  if (i >= B.nx) return;
+  const int64_t q = elem_index(B, i, j, k);
+  const int64_t sx = B.sx, sy = B.sy;
+  A s = ldg(rhs + q);
+  s = fma((A)ldg(wx + q), (A)ld(phi + q - 1), s);
+  s = fma((A)ldg(wx + q + 1), (A)ld(phi + q + 1), s);
+  s = fma((A)ldg(wy + q), (A)ld(phi + q - sx), s);
+  s = fma((A)ldg(wy + q + sx), (A)ld(phi + q + sx), s);
+  s = fma((A)ldg(wz + q), (A)ld(phi + q - sy), s);
+  s = fma((A)ldg(wz + q + sy), (A)ld(phi + q + sy), s);
+  st(phi + q, s * (A)ldg(invD + q));
+}
+
+// ------------------------------------------------------------------- residual
+
+template <class T, class C>
+__device__ __forceinline__ typename Arith<T>::type resid_at(const T* phi, const T* rhs, const C* wx, const C* wy,
+                                                           const C* wz, const C* D, int64_t q, int64_t sx, int64_t sy,
+                                                           typename Arith<T>::type shift) {
+  using A = typename Arith<T>::type;
+  A v = (A)ldg(rhs + q) - shift;
+  v = fma(-(A)ldg(D + q), (A)ld(phi + q), v);
+  v = fma((A)ldg(wx + q), (A)ld(phi + q - 1), v);
+  v = fma((A)ldg(wx + q + 1), (A)ld(phi + q + 1), v);
+  v = fma((A)ldg(wy + q), (A)ld(phi + q - sx), v);
+  v = fma((A)ldg(wy + q + sx), (A)ld(phi + q + sx), v);
+  v = fma((A)ldg(wz + q), (A)ld(phi + q - sy), v);
+  v = fma((A)ldg(wz + q + sy), (A)ld(phi + q + sy), v);
+  return v;
+}
+
+template <class T, class R>
+__global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                    const T* __restrict__ phi, const T* __restrict__ rhs,
+                                                    const typename CoefOf<T>::type* __restrict__ wx,
+                                                    const typename CoefOf<T>::type* __restrict__ wy,
+                                                    const typename CoefOf<T>::type* __restrict__ wz,
+                                                    const typename CoefOf<T>::type* __restrict__ D, R* r,
+                                                    unsigned long long* maxbits, const double* shift_p) {
+  using A = typename Arith<T>::type;
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  const A shift = shift_p ? (A)*shift_p : (A)0;
+  unsigned long long mx = 0;
+  if (t < ((B.nx + 1) >> 1) * B.ny * B.nz) {
+    int i0, j, k;
+    pair_decode(B, t, i0, j, k);
+    const int64_t q0 = elem_index(B, i0, j, k);
+    for (int c = 0; c < 2; ++c) {
+      if (i0 + c >= B.nx) break;
+      const A v = resid_at(phi, rhs, wx, wy, wz, D, q0 + c, B.sx, B.sy, shift);
+      if (r) st(r + q0 + c, v);
+      const unsigned long long bb = abs_bits((double)v);
+      mx = bb > mx ? bb : mx;
+    }
+  }
+  if (maxbits) block_max_atomic(mx, maxbits);
+}
+
+// residual of the 8 children of one coarse cell, averaged into the coarse level
+template <class T, class R>
+__global__ void __launch_bounds__(BLOCK)
+    k_resid_restrict(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes,
+                     const int* __restrict__ parent, const Chunk* __restrict__ chunks, const T* __restrict__ phi,
+                     const T* __restrict__ rhs, const typename CoefOf<T>::type* __restrict__ wx,
+                     const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
+                     const typename CoefOf<T>::type* __restrict__ D, R* rc) {
+  using A = typename Arith<T>::type;
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox F = fboxes[ch.item];
+  const DevBox P = cboxes[parent[ch.item]];
+  const int ncx = F.nx >> 1, ncy = F.ny >> 1, ncz = F.nz >> 1;
+  const int t = ch.start + threadIdx.x;
+  if (t >= ncx * ncy * ncz) return;
+  const int ci = t % ncx, cj = (t / ncx) % ncy, ck = t / (ncx * ncy);
+  A s = 0;
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj) {
+      const int64_t q = elem_index(F, 2 * ci, 2 * cj + dj, 2 * ck + dk);
+      s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0);
+      s += resid_at(phi, rhs, wx, wy, wz, D, q + 1, F.sx, F.sy, (A)0);
+    }
+  const int I = (F.lo[0] >> 1) + ci - P.lo[0];
+  const int J = (F.lo[1] >> 1) + cj - P.lo[1];
+  const int K = (F.lo[2] >> 1) + ck - P.lo[2];
+  st(rc + elem_index(P, I, J, K), s * (A)0.125);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK)
+    k_restrict(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes, const int* __restrict__ parent,
+               const Chunk* __restrict__ chunks, const T* __restrict__ fine, T* coarse) {
+  using A = typename Arith<T>::type;
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox F = fboxes[ch.item];
+  const DevBox P = cboxes[parent[ch.item]];
+  const int ncx = F.nx >> 1, ncy = F.ny >> 1, ncz = F.nz >> 1;
+  const int t = ch.start + threadIdx.x;
+  if (t >= ncx * ncy * ncz) return;
+  const int ci = t % ncx, cj = (t / ncx) % ncy, ck = t / (ncx * ncy);
+  A s = 0;
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj) {
+      const int64_t q = elem_index(F, 2 * ci, 2 * cj + dj, 2 * ck + dk);
+      s += (A)ld(fine + q);
+      s += (A)ld(fine + q + 1);
+    }
+  const int I = (F.lo[0] >> 1) + ci - P.lo[0];
+  const int J = (F.lo[1] >> 1) + cj - P.lo[1];
+  const int K = (F.lo[2] >> 1) + ck - P.lo[2];
+  st(coarse + elem_index(P, I, J, K), s * (A)0.125);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK)
+    k_prolong_add(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes, const int* __restrict__ parent,
+                  const Chunk* __restrict__ chunks, const T* __restrict__ coarse, T* fine) {
+  using A = typename Arith<T>::type;
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox F = fboxes[ch.item];
+  const DevBox P = cboxes[parent[ch.item]];
+  const int ncx = F.nx >> 1, ncy = F.ny >> 1, ncz = F.nz >> 1;
+  const int t = ch.start + threadIdx.x;
+  if (t >= ncx * ncy * ncz) return;
+  const int ci = t % ncx, cj = (t / ncx) % ncy, ck = t / (ncx * ncy);
+  const int I = (F.lo[0] >> 1) + ci - P.lo[0];
+  const int J = (F.lo[1] >> 1) + cj - P.lo[1];
+  const int K = (F.lo[2] >> 1) + ck - P.lo[2];
+  const A e = ld(coarse + elem_index(P, I, J, K));
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj) {
+      const int64_t q = elem_index(F, 2 * ci, 2 * cj + dj, 2 * ck + dk);
+      st(fine + q, (A)ld(fine + q) + e);
+      st(fine + q + 1, (A)ld(fine + q + 1) + e);
+    }
+}
+
+// ----------------------------------------------------------- cell-wise helpers
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_add_correction(const DevBox* __restrict__ boxes,
+                                                          const Chunk* __restrict__ chunks, double* phi,
+                                                          const T* __restrict__ e) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+  const int64_t q = elem_index(B, i, j, k);
+  phi[q] += (double)ld(e + q);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_pack(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                int3 dlo, int3 dn, const double* __restrict__ dense, T* boxed) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+  const int64_t g = (int64_t)(B.lo[0] + i - dlo.x) + (int64_t)dn.x * ((B.lo[1] + j - dlo.y) + (int64_t)dn.y * (B.lo[2] + k - dlo.z));
+  st(boxed + elem_index(B, i, j, k), dense[g]);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_unpack(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                  int3 dlo, int3 dn, const T* __restrict__ boxed, double* dense) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+  const int64_t g = (int64_t)(B.lo[0] + i - dlo.x) + (int64_t)dn.x * ((B.lo[1] + j - dlo.y) + (int64_t)dn.y * (B.lo[2] + k - dlo.z));
+  dense[g] = (double)ld(boxed + elem_index(B, i, j, k));
+}
+
+__global__ void __launch_bounds__(BLOCK) k_norm_max(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                    const double* __restrict__ x, unsigned long long* maxbits) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  unsigned long long mx = 0;
+  if (t < B.nx * B.ny * B.nz) {
+    const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+    mx = abs_bits(x[elem_index(B, i, j, k)]);
+  }
+  block_max_atomic(mx, maxbits);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_sum_partial(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                       const double* __restrict__ x, double* partials) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  double v = 0.0;
+  if (t < B.nx * B.ny * B.nz) {
+    const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+    v = x[elem_index(B, i, j, k)];
+  }
+  const double s = block_sum(v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_sum_final(const double* __restrict__ partials, int n, double* out) {
+  // fixed order: thread t adds partials t, t + BLOCK, ...; then a fixed tree
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += BLOCK) v += partials[i];
+  const double s = block_sum(v);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_add_scalar(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                      double* x, const double* c, double scale) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+  x[elem_index(B, i, j, k)] += scale * *c;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_scale_valid(const DevBox* __restrict__ boxes,
+                                                       const Chunk* __restrict__ chunks, double* x, double scale) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+  x[elem_index(B, i, j, k)] *= scale;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_copy_valid(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                      double* dst, const double* __restrict__ src) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+  const int64_t q = elem_index(B, i, j, k);
+  dst[q] = src[q];
+}
+
+// ------------------------------------------------------------- coefficients
+
+__global__ void __launch_bounds__(BLOCK) k_acoef(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                 double a, const double* __restrict__ alpha, double* acoef) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+  const int64_t q = elem_index(B, i, j, k);
+  acoef[q] = alpha ? a * alpha[q] : a;
+}
+
+// Face beta from cell beta (Sec. "Linear Solvers": beta on faces): harmonic mean of the
+// two cells; on a Dirichlet wall face the interior cell's value.  Each thread writes the
+// low face of its cell in every direction and, for the last cell of a row/column, the
+// high face too.  The ghosts of beta must hold the neighbouring boxes' values.
+__global__ void __launch_bounds__(BLOCK)
+    k_faces_from_cell(const DevBox* __restrict__ boxes, const DevGeom* __restrict__ geoms,
+                      const Chunk* __restrict__ chunks, const double* __restrict__ beta, double* bx, double* by,
+                      double* bz) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const DevGeom G = geoms[B.solve];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int loc[3] = {t % B.nx, (t / B.nx) % B.ny, t / (B.nx * B.ny)};
+  const int n[3] = {B.nx, B.ny, B.nz};
+  const int64_t q = elem_index(B, loc[0], loc[1], loc[2]);
+  double* w[3] = {bx, by, bz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int64_t st_d = d == 0 ? 1 : (d == 1 ? (int64_t)B.sx : B.sy);
+    for (int side = 0; side < 2; ++side) {
+      if (side == 1 && loc[d] != n[d] - 1) continue;
+      const int64_t qf = q + side * st_d;         // face slot (low face of cell qf)
+      const int gf = B.lo[d] + loc[d] + side;      // global face index
+      const double bl = beta[qf - st_d], br = beta[qf];
+      double v;
+      if (G.wall_lo[d] && gf == G.dlo[d]) v = br;
+      else if (G.wall_hi[d] && gf == G.dhi[d] + 1) v = bl;
+      else v = 2.0 * bl * br / (bl + br);
+      w[d][qf] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(BLOCK)
+    k_faces_scale(const DevBox* __restrict__ boxes, const DevGeom* __restrict__ geoms, const Chunk* __restrict__ chunks,
+                  double b, const double* __restrict__ bx, const double* __restrict__ by, const double* __restrict__ bz,
+                  double* wx, double* wy, double* wz) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const DevGeom G = geoms[B.solve];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int loc[3] = {t % B.nx, (t / B.nx) % B.ny, t / (B.nx * B.ny)};
+  const int n[3] = {B.nx, B.ny, B.nz};
+  const int64_t q = elem_index(B, loc[0], loc[1], loc[2]);
+  const double* src[3] = {bx, by, bz};
+  double* w[3] = {wx, wy, wz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int64_t st_d = d == 0 ? 1 : (d == 1 ? (int64_t)B.sx : B.sy);
+    for (int side = 0; side < 2; ++side) {
+      if (side == 1 && loc[d] != n[d] - 1) continue;
+      const int64_t qf = q + side * st_d;
+      w[d][qf] = b * src[d][qf] * G.ih2[d];
+    }
+  }
+}
+
+// Coarse coefficients (Sec. "Operations between levels": average of fine data): coarse
+// a*alpha = mean of the 8 children; coarse beta face = mean of the 4 fine faces, i.e.
+// coarse w = (sum of the 4 fine w) / 16 because h doubles.
+__global__ void __launch_bounds__(BLOCK)
+    k_coarsen_coefs(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes, const int* __restrict__ parent,
+                    const Chunk* __restrict__ chunks, const double* __restrict__ acf, const double* __restrict__ wxf,
+                    const double* __restrict__ wyf, const double* __restrict__ wzf, double* acc, double* wxc,
+                    double* wyc, double* wzc) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox F = fboxes[ch.item];
+  const DevBox P = cboxes[parent[ch.item]];
+  const int nc[3] = {F.nx >> 1, F.ny >> 1, F.nz >> 1};
+  const int t = ch.start + threadIdx.x;
+  if (t >= nc[0] * nc[1] * nc[2]) return;
+  const int c[3] = {t % nc[0], (t / nc[0]) % nc[1], t / (nc[0] * nc[1])};
+  const int64_t qc = elem_index(P, (F.lo[0] >> 1) + c[0] - P.lo[0], (F.lo[1] >> 1) + c[1] - P.lo[1],
+                                (F.lo[2] >> 1) + c[2] - P.lo[2]);
+  const int64_t qf = elem_index(F, 2 * c[0], 2 * c[1], 2 * c[2]);
+  const int64_t fs[3] = {1, (int64_t)F.sx, F.sy};
+  const int64_t cs[3] = {1, (int64_t)P.sx, P.sy};
+  double s = 0.0;
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) s += acf[qf + di + dj * fs[1] + dk * fs[2]];
+  acc[qc] = s * 0.125;
+  const double* wf[3] = {wxf, wyf, wzf};
+  double* wc[3] = {wxc, wyc, wzc};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+    for (int side = 0; side < 2; ++side) {
+      if (side == 1 && c[d] != nc[d] - 1) continue;
+      const int64_t f0 = qf + 2 * side * fs[d];
+      const double v = wf[d][f0] + wf[d][f0 + fs[d1]] + wf[d][f0 + fs[d2]] + wf[d][f0 + fs[d1] + fs[d2]];
+      wc[d][qc + side * cs[d]] = v * 0.0625;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(BLOCK) k_diag(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                const double* __restrict__ acoef, const double* __restrict__ wx,
+                                                const double* __restrict__ wy, const double* __restrict__ wz,
+                                                double* D, double* invD) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+  const int64_t q = elem_index(B, i, j, k);
+  const double s = ((wx[q] + wx[q + 1]) + (wy[q] + wy[q + B.sx])) + (wz[q] + wz[q + B.sy]);
+  const double d = acoef[q] + s;
+  D[q] = d;
+  invD[q] = 1.0 / d;
+}
+
+template <class S, class T>
+__global__ void k_convert(const S* __restrict__ src, T* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    st(dst + i, ld(src + i));
+}
+
+inline unsigned grid_of(int n) { return (unsigned)(n > 0 ? n : 0); }
+
+}  // namespace
+
+static int64_t g_launches = 0;
+int64_t kernel_launch_count() { return g_launches; }
+void count_launches(int n) { g_launches += n; }
+
+// ================================================================= launchers
+
+#define GMG_DISPATCH(dt, KERNEL_CALL)                  \
+  switch (dt) {                                         \
+    case DT_F64: { using T = double; KERNEL_CALL; } break; \
+    case DT_F32: { using T = float; KERNEL_CALL; } break;  \
+    default: { using T = bf16; KERNEL_CALL; } break;       \
+  }
+
+void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, cudaStream_t s) {
+  if (!L.n_ghost_chunks) return;
+  ++g_launches;
+  GMG_DISPATCH(dt, (k_fill<T><<<grid_of(L.n_ghost_chunks), BLOCK, 0, s>>>(L.boxes, L.ghosts, L.ghost_chunks,
+                                                                           (T*)f, colour, copy_mode)));
+}
+
+void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour, cudaStream_t s) {
+  if (!L.n_pair_chunks) return;
+  ++g_launches;
+  GMG_DISPATCH(dt, (k_smooth<T><<<grid_of(L.n_pair_chunks), BLOCK, 0, s>>>(
+                       L.boxes, L.pair_chunks, (T*)phi, (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
+                       (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
+                       (const typename CoefOf<T>::type*)c.invD, colour)));
+}
+
+// residual work list: pair items over every box (the bottom level included)
+void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const void* rhs, const Coefs& c, void* r,
+                     unsigned long long* maxbits, const double* shift, cudaStream_t s) {
+  if (!L.n_pair_all_chunks) return;
+  ++g_launches;
+#define GMG_RESID(TR)                                                                                     \
+  GMG_DISPATCH(dt, (k_residual<T, TR><<<grid_of(L.n_pair_all_chunks), BLOCK, 0, s>>>(                     \
+                       L.boxes, L.pair_all_chunks, (const T*)phi, (const T*)rhs,                              \
+                       (const typename CoefOf<T>::type*)c.wx, (const typename CoefOf<T>::type*)c.wy,      \
+                       (const typename CoefOf<T>::type*)c.wz, (const typename CoefOf<T>::type*)c.D, (TR*)r, \
+                       maxbits, shift)))
+  switch (rdt) {
+    case DT_F64: GMG_RESID(double); break;
+    case DT_F32: GMG_RESID(float); break;
+    default: GMG_RESID(bf16); break;
+  }
+#undef GMG_RESID
+}
+
+void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* phi, const void* rhs,
+                           const Coefs& cf, void* rc, cudaStream_t s) {
+  if (!f.n_coarse_chunks) return;
+  ++g_launches;
+  GMG_DISPATCH(dt, (k_resid_restrict<T, T><<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(
+                       f.boxes, c.boxes, f.parent, f.coarse_chunks, (const T*)phi, (const T*)rhs,
+                       (const typename CoefOf<T>::type*)cf.wx, (const typename CoefOf<T>::type*)cf.wy,
+                       (const typename CoefOf<T>::type*)cf.wz, (const typename CoefOf<T>::type*)cf.D, (T*)rc)));
+}
+
+void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s) {
+  if (!f.n_coarse_chunks) return;
+  ++g_launches;
+  GMG_DISPATCH(dt, (k_restrict<T><<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(f.boxes, c.boxes, f.parent,
+                                                                                 f.coarse_chunks, (const T*)fine,
+                                                                                 (T*)coarse)));
+}
+
+void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine, cudaStream_t s) {
+  if (!f.n_coarse_chunks) return;
+  ++g_launches;
+  GMG_DISPATCH(dt, (k_prolong_add<T><<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(f.boxes, c.boxes, f.parent,
+                                                                                    f.coarse_chunks, (const T*)coarse,
+                                                                                    (T*)fine)));
+}
+
+void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  GMG_DISPATCH(dt, (k_add_correction<T><<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, phi,
+                                                                                     (const T*)e)));
+}
+
+void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const double* dense, void* boxed,
+                 cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  int3 lo = make_int3(dlo[0], dlo[1], dlo[2]), n = make_int3(dn[0], dn[1], dn[2]);
+  GMG_DISPATCH(dt, (k_pack<T><<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, lo, n, dense,
+                                                                          (T*)boxed)));
+}
+
+void launch_unpack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const void* boxed, double* dense,
+                   cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  int3 lo = make_int3(dlo[0], dlo[1], dlo[2]), n = make_int3(dn[0], dn[1], dn[2]);
+  GMG_DISPATCH(dt, (k_unpack<T><<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, lo, n,
+                                                                            (const T*)boxed, dense)));
+}
+
+void launch_norm_max(const LevelDev& L, const double* x, unsigned long long* maxbits, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  k_norm_max<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, x, maxbits);
+}
+
+void launch_sum(const LevelDev& L, const double* x, double* partials, double* out, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  ++g_launches;
+  k_sum_partial<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, x, partials);
+  k_sum_final<<<1, BLOCK, 0, s>>>(partials, L.n_cell_chunks, out);
+}
+
+void launch_add_scalar(const LevelDev& L, double* x, const double* c, double scale, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  k_add_scalar<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, x, c, scale);
+}
+
+void launch_scale_valid(const LevelDev& L, double* x, double scale, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  k_scale_valid<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, x, scale);
+}
+
+void launch_copy_valid(const LevelDev& L, double* dst, const double* src, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  k_copy_valid<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, dst, src);
+}
+
+void launch_acoef(const LevelDev& L, double a, const double* alpha, double* acoef, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  k_acoef<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, a, alpha, acoef);
+}
+
+void launch_faces_from_cell(const LevelDev& L, const double* beta, double* bx, double* by, double* bz, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  k_faces_from_cell<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.geoms, L.cell_chunks, beta, bx, by, bz);
+}
+
+void launch_faces_scale(const LevelDev& L, double b, const double* bx, const double* by, const double* bz, double* wx,
+                        double* wy, double* wz, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  k_faces_scale<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.geoms, L.cell_chunks, b, bx, by, bz, wx, wy,
+                                                           wz);
+}
+
+void launch_coarsen_coefs(const LevelDev& f, const LevelDev& c, const double* acf, const double* wxf,
+                          const double* wyf, const double* wzf, double* acc, double* wxc, double* wyc, double* wzc,
+                          cudaStream_t s) {
+  if (!f.n_coarse_chunks) return;
+  ++g_launches;
+  k_coarsen_coefs<<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(f.boxes, c.boxes, f.parent, f.coarse_chunks, acf, wxf,
+                                                               wyf, wzf, acc, wxc, wyc, wzc);
+}
+
+void launch_diag(const LevelDev& L, const double* acoef, const double* wx, const double* wy, const double* wz,
+                 double* D, double* invD, cudaStream_t s) {
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  k_diag<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, acoef, wx, wy, wz, D, invD);
+}
+
+void launch_convert(int dt, int dt2, const void* src, void* dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  ++g_launches;
+  const unsigned g = (unsigned)std::min<int64_t>((n + BLOCK - 1) / BLOCK, 152 * 16);
+#define GMG_CVT(TD) GMG_DISPATCH(dt, (k_convert<T, TD><<<g, BLOCK, 0, s>>>((const T*)src, (TD*)dst, n)))
+  switch (dt2) {
+    case DT_F64: GMG_CVT(double); break;
+    case DT_F32: GMG_CVT(float); break;
+    default: GMG_CVT(bf16); break;
+  }
+#undef GMG_CVT
+}
+
+void launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s) {
+  launch_convert(DT_F64, DT_F32, src, dst, n, s);
+}
+
+}  // namespace gmg

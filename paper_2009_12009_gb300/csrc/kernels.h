@@ -1,0 +1,118 @@
+// kernels.h -- launch wrappers of the sm_103a kernels (kernels.cu, bottom.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace gmg {
+
+// Per-solve geometry of one level, as the coefficient kernels see it.
+struct DevGeom {
+  int dlo[3], dhi[3];
+  int wall_lo[3], wall_hi[3];  // 1: homogeneous Dirichlet wall on that side
+  double ih2[3];               // 1 / h_d^2
+};
+
+// Device view of one level: its tables (uploaded once into the workspace).
+struct LevelDev {
+  const DevBox* boxes = nullptr;
+  const DevGeom* geoms = nullptr;
+  const GhostRect* ghosts = nullptr;
+  const Chunk* ghost_chunks = nullptr;
+  int n_ghost_chunks = 0;
+  const Chunk* pair_chunks = nullptr;  // boxes that smooth on this level, 2 cells per item
+  int n_pair_chunks = 0;
+  const Chunk* pair_all_chunks = nullptr;  // every box, 2 cells per item
+  int n_pair_all_chunks = 0;
+  const Chunk* cell_chunks = nullptr;
+  int n_cell_chunks = 0;
+  const Chunk* coarse_chunks = nullptr;
+  int n_coarse_chunks = 0;
+  const int* parent = nullptr;
+  const BotCell* bot_cells = nullptr;
+  const BotGhost* bot_ghosts = nullptr;
+  const BotDesc* bot_descs = nullptr;
+  int n_bot = 0;
+  int64_t nelem = 0;
+};
+
+// Coefficients of one level in one element type (double for FP64 fields, float for
+// float and bfloat16 fields): scaled face weights w = b*beta/h^2, diagonal
+// D = a*alpha + sum of the six weights, and 1/D.
+struct Coefs {
+  const void* wx = nullptr;
+  const void* wy = nullptr;
+  const void* wz = nullptr;
+  const void* D = nullptr;
+  const void* invD = nullptr;
+};
+
+// ghost exchange; colour -1 = all ghosts; copy_mode: skip wall rectangles (coefficient
+// fills, where the wall face is handled by the face kernel)
+void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, cudaStream_t s);
+// one red-black colour (no ghost fill)
+void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour,
+                   cudaStream_t s);
+// r = (rhs - shift) - A phi on valid cells (ghosts of phi must be filled); rdt = type of r;
+// maxbits (may be null): atomic max of |r| as IEEE bits; shift (may be null): device scalar
+void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const void* rhs, const Coefs& c,
+                     void* r, unsigned long long* maxbits, const double* shift, cudaStream_t s);
+// coarse r = restriction of (rhs - A phi) (ghosts of phi filled)
+void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* phi, const void* rhs,
+                           const Coefs& cf, void* rc, cudaStream_t s);
+void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s);
+void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine,
+                        cudaStream_t s);
+// phi (double) += e (type dt) on valid cells
+void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s);
+// dense (nz,ny,nx) double over the level's (single-solve) domain <-> boxed type dt
+void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const double* dense, void* boxed,
+                 cudaStream_t s);
+void launch_unpack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const void* boxed, double* dense,
+                   cudaStream_t s);
+// |x|_inf of a double field (atomic max into maxbits)
+void launch_norm_max(const LevelDev& L, const double* x, unsigned long long* maxbits, cudaStream_t s);
+// deterministic sum of valid cells of a double field: partial sums per block, then one
+// block adds them in order; result in *out (device)
+void launch_sum(const LevelDev& L, const double* x, double* partials, double* out, cudaStream_t s);
+// x += c (device scalar, multiplied by `scale`) on valid cells
+void launch_add_scalar(const LevelDev& L, double* x, const double* c, double scale, cudaStream_t s);
+// x *= scale on valid cells
+void launch_scale_valid(const LevelDev& L, double* x, double scale, cudaStream_t s);
+void launch_copy_valid(const LevelDev& L, double* dst, const double* src, cudaStream_t s);
+
+// ---- coefficients (FP64) ----
+// acoef = a * alpha (alpha null: a)
+void launch_acoef(const LevelDev& L, double a, const double* alpha, double* acoef, cudaStream_t s);
+// face beta = harmonic mean of the two cells (wall faces: interior cell) from cell beta
+// whose ghosts hold the neighbouring boxes' values
+void launch_faces_from_cell(const LevelDev& L, const double* beta, double* bx, double* by, double* bz, cudaStream_t s);
+// w_d = b * beta_d / h_d^2 from face arrays
+void launch_faces_scale(const LevelDev& L, double b, const double* bx, const double* by, const double* bz, double* wx,
+                        double* wy, double* wz, cudaStream_t s);
+// coarse acoef = mean of 8; coarse w = (sum of 4 fine w) / 16
+void launch_coarsen_coefs(const LevelDev& f, const LevelDev& c, const double* acf, const double* wxf,
+                          const double* wyf, const double* wzf, double* acc, double* wxc, double* wyc, double* wzc,
+                          cudaStream_t s);
+void launch_diag(const LevelDev& L, const double* acoef, const double* wx, const double* wy, const double* wz,
+                 double* D, double* invD, cudaStream_t s);
+void launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s);
+// copy a field of type dt into type dt2 (same layout, every element)
+void launch_convert(int dt, int dt2, const void* src, void* dst, int64_t n, cudaStream_t s);
+
+// number of kernel launches issued through these wrappers (host counter)
+int64_t kernel_launch_count();
+void count_launches(int n);
+
+// ---- bottom solve (bottom.cu) ----
+struct BottomArgs {
+  int maxit;
+  double tol;
+  double* work;        // 7 double vectors of the bottom level's layout
+  int* iters;          // device: iterations per bottom problem
+};
+void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Coefs& c64, const BottomArgs& a,
+                   cudaStream_t s);
+
+}  // namespace gmg

@@ -1,0 +1,288 @@
+// meta.cpp -- multigrid hierarchy and cached exchange tables (host).
+#include "meta.h"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace gmg {
+
+Box intersect(const Box& a, const Box& b) {
+  Box r;
+  for (int d = 0; d < 3; ++d) {
+    r.lo[d] = std::max(a.lo[d], b.lo[d]);
+    r.hi[d] = std::min(a.hi[d], b.hi[d]);
+  }
+  return r;
+}
+
+Box shifted(const Box& a, int d, int s) {
+  Box r = a;
+  r.lo[d] += s;
+  r.hi[d] += s;
+  return r;
+}
+
+static int pmod2(int a) { return ((a % 2) + 2) % 2; }
+
+std::string validate_boxes(const std::vector<Box>& boxes, const Box& domain, bool must_cover) {
+  int64_t vol = 0;
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    const Box& B = boxes[b];
+    if (B.empty()) return "empty box " + std::to_string(b);
+    for (int d = 0; d < 3; ++d)
+      if (B.lo[d] < domain.lo[d] || B.hi[d] > domain.hi[d]) return "box " + std::to_string(b) + " outside the domain";
+    vol += B.volume();
+  }
+  // pairwise disjointness: sort by lo.x and sweep
+  std::vector<int> idx(boxes.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return boxes[a].lo[0] < boxes[b].lo[0]; });
+  for (size_t a = 0; a < idx.size(); ++a)
+    for (size_t b = a + 1; b < idx.size(); ++b) {
+      if (boxes[idx[b]].lo[0] > boxes[idx[a]].hi[0]) break;
+      if (!intersect(boxes[idx[a]], boxes[idx[b]]).empty())
+        return "boxes " + std::to_string(idx[a]) + " and " + std::to_string(idx[b]) + " overlap";
+    }
+  if (must_cover && vol != domain.volume()) return "boxes do not cover the domain";
+  return "";
+}
+
+std::vector<Box> chop(const Box& dom, int mgs) {
+  std::vector<std::pair<int, int>> cuts[3];
+  for (int d = 0; d < 3; ++d)
+    for (int s = dom.lo[d]; s <= dom.hi[d]; s += mgs) cuts[d].push_back({s, std::min(s + mgs - 1, dom.hi[d])});
+  std::vector<Box> out;
+  for (auto& z : cuts[2])
+    for (auto& y : cuts[1])
+      for (auto& x : cuts[0]) {
+        Box b;
+        b.lo[0] = x.first; b.hi[0] = x.second;
+        b.lo[1] = y.first; b.hi[1] = y.second;
+        b.lo[2] = z.first; b.hi[2] = z.second;
+        out.push_back(b);
+      }
+  return out;
+}
+
+// Face ghost rectangles of every box (Sec. "Operations on a level").  For each face slab
+// of each box, the slab is intersected with every box of the same solve (and with its
+// periodic images along the face normal); the part outside a Dirichlet wall becomes a
+// reflection rectangle.  Edge and corner ghosts are not needed by the 7-point stencil.
+static std::string build_ghosts(LevelMeta& L) {
+  L.ghosts.clear();
+  const int nb = (int)L.boxes.size();
+  // boxes per solve
+  std::vector<std::vector<int>> members(L.geoms.size());
+  for (int b = 0; b < nb; ++b) members[L.box_solve[b]].push_back(b);
+  for (int b = 0; b < nb; ++b) {
+    const Box& B = L.boxes[b];
+    const SolveGeom& G = L.geoms[L.box_solve[b]];
+    for (int d = 0; d < 3; ++d) {
+      int d1 = (d == 0) ? 1 : 0;
+      int d2 = (d == 2) ? 1 : 2;
+      for (int side = 0; side < 2; ++side) {
+        Box slab = B;
+        int gd = side ? B.hi[d] + 1 : B.lo[d] - 1;
+        slab.lo[d] = slab.hi[d] = gd;
+        bool outside = gd < G.domain.lo[d] || gd > G.domain.hi[d];
+        int bc = side ? G.bchi[d] : G.bclo[d];
+        if (outside && bc != 0) {
+          GhostRect r{};
+          r.dst_box = r.src_box = b;
+          for (int q = 0; q < 3; ++q) r.dst[q] = r.src[q] = 0;
+          r.dst[d] = side ? B.n(d) : -1;
+          r.src[d] = side ? B.n(d) - 1 : 0;
+          r.d1 = d1; r.d2 = d2;
+          r.n1 = B.n(d1); r.n2 = B.n(d2);
+          r.sign = -1;
+          r.par0 = pmod2(B.lo[0] + B.lo[1] + B.lo[2] + r.dst[0] + r.dst[1] + r.dst[2]);
+          r.kind = 1;
+          L.ghosts.push_back(r);
+          continue;
+        }
+        int64_t covered = 0;
+        int len = G.domain.n(d);
+        int shifts[3] = {0, 0, 0};
+        int nsh = 1;
+        if (G.periodic(d)) { shifts[1] = len; shifts[2] = -len; nsh = 3; }
+        for (int ob : members[L.box_solve[b]]) {
+          for (int s = 0; s < nsh; ++s) {
+            Box img = shifted(L.boxes[ob], d, shifts[s]);
+            Box I = intersect(slab, img);
+            if (I.empty()) continue;
+            GhostRect r{};
+            r.dst_box = b;
+            r.src_box = ob;
+            for (int q = 0; q < 3; ++q) {
+              r.dst[q] = I.lo[q] - B.lo[q];
+              r.src[q] = I.lo[q] - img.lo[q];
+            }
+            r.d1 = d1; r.d2 = d2;
+            r.n1 = I.n(d1); r.n2 = I.n(d2);
+            r.sign = 1;
+            r.par0 = pmod2(I.lo[0] + I.lo[1] + I.lo[2]);
+            r.kind = 0;
+            L.ghosts.push_back(r);
+            covered += I.volume();
+          }
+        }
+        if (covered != slab.volume())
+          return "ghost cells of box " + std::to_string(b) + " are not covered by the level (coarse/fine boundary)";
+      }
+    }
+  }
+  L.ghost_chunks.clear();
+  for (int g = 0; g < (int)L.ghosts.size(); ++g) {
+    int n = L.ghosts[g].n1 * L.ghosts[g].n2;
+    for (int s = 0; s < n; s += GHOST_CHUNK) L.ghost_chunks.push_back({g, s});
+  }
+  return "";
+}
+
+static void build_bottom(LevelMeta& L) {
+  L.bot_cells.clear();
+  L.bot_ghosts.clear();
+  L.bot_descs.clear();
+  for (int s = 0; s < (int)L.geoms.size(); ++s) {
+    if (!L.solve_present[s] || !L.solve_bottom[s]) continue;
+    BotDesc D{};
+    D.cell0 = (int)L.bot_cells.size();
+    D.ghost0 = (int)L.bot_ghosts.size();
+    D.solve = s;
+    for (int b = 0; b < (int)L.boxes.size(); ++b) {
+      if (L.box_solve[b] != s) continue;
+      const DevBox& B = L.dbox[b];
+      for (int k = 0; k < B.nz; ++k)
+        for (int j = 0; j < B.ny; ++j)
+          for (int i = 0; i < B.nx; ++i) L.bot_cells.push_back({elem_index(B, i, j, k), B.sy, B.sx, 0});
+    }
+    for (const GhostRect& g : L.ghosts) {
+      if (L.box_solve[g.dst_box] != s) continue;
+      const DevBox& Bd = L.dbox[g.dst_box];
+      const DevBox& Bs = L.dbox[g.src_box];
+      for (int v = 0; v < g.n2; ++v)
+        for (int u = 0; u < g.n1; ++u) {
+          int dl[3] = {g.dst[0], g.dst[1], g.dst[2]};
+          int sl[3] = {g.src[0], g.src[1], g.src[2]};
+          dl[g.d1] += u; dl[g.d2] += v;
+          sl[g.d1] += u; sl[g.d2] += v;
+          L.bot_ghosts.push_back({elem_index(Bd, dl[0], dl[1], dl[2]), elem_index(Bs, sl[0], sl[1], sl[2]), (double)g.sign});
+        }
+    }
+    D.ncell = (int)L.bot_cells.size() - D.cell0;
+    D.nghost = (int)L.bot_ghosts.size() - D.ghost0;
+    D.singular = 0;  // set from the operator's scalars at coefficient time
+    L.bot_descs.push_back(D);
+  }
+}
+
+std::string finalize_level(LevelMeta& L) {
+  const int nb = (int)L.boxes.size();
+  L.dbox.resize(nb);
+  int64_t off = 0;
+  L.ncells = 0;
+  for (int b = 0; b < nb; ++b) {
+    const Box& B = L.boxes[b];
+    DevBox& D = L.dbox[b];
+    D.nx = B.n(0); D.ny = B.n(1); D.nz = B.n(2);
+    D.sx = ((GX + D.nx + 1 + ROW_ALIGN - 1) / ROW_ALIGN) * ROW_ALIGN;
+    D.sy = (int64_t)D.sx * (D.ny + 2);
+    for (int d = 0; d < 3; ++d) D.lo[d] = B.lo[d];
+    D.solve = L.box_solve[b];
+    D.off = off;
+    off += ((D.sy * (D.nz + 2) + BOX_ALIGN - 1) / BOX_ALIGN) * BOX_ALIGN;
+    L.ncells += B.volume();
+  }
+  L.nelem = off;
+  if (L.parent.size() != (size_t)nb) L.parent.assign(nb, -1);
+  std::string err = build_ghosts(L);
+  if (!err.empty()) return err;
+  L.pair_chunks.clear();
+  L.pair_all_chunks.clear();
+  L.cell_chunks.clear();
+  for (int b = 0; b < nb; ++b) {
+    const DevBox& D = L.dbox[b];
+    int64_t ncell = (int64_t)D.nx * D.ny * D.nz;
+    for (int64_t s = 0; s < ncell; s += BLOCK) L.cell_chunks.push_back({b, (int)s});
+    int64_t npair = (int64_t)((D.nx + 1) / 2) * D.ny * D.nz;
+    for (int64_t s = 0; s < npair; s += BLOCK) L.pair_all_chunks.push_back({b, (int)s});
+    if (L.solve_bottom[L.box_solve[b]]) continue;
+    for (int64_t s = 0; s < npair; s += BLOCK) L.pair_chunks.push_back({b, (int)s});
+  }
+  L.coarse_chunks.clear();
+  for (int b = 0; b < nb; ++b) {
+    if (L.parent[b] < 0) continue;
+    const DevBox& D = L.dbox[b];
+    int64_t nc = (int64_t)(D.nx / 2) * (D.ny / 2) * (D.nz / 2);
+    for (int64_t s = 0; s < nc; s += BLOCK) L.coarse_chunks.push_back({b, (int)s});
+  }
+  build_bottom(L);
+  return "";
+}
+
+bool make_coarse(LevelMeta& f, LevelMeta& c) {
+  const int nb = (int)f.boxes.size();
+  const int ns = (int)f.geoms.size();
+  f.parent.assign(nb, -1);
+  f.solve_bottom.assign(ns, 0);
+  c = LevelMeta();
+  c.geoms = f.geoms;
+  c.solve_present.assign(ns, 0);
+  c.solve_bottom.assign(ns, 0);
+  bool any = false;
+  for (int s = 0; s < ns; ++s) {
+    if (!f.solve_present[s]) continue;
+    std::vector<int> mem;
+    for (int b = 0; b < nb; ++b)
+      if (f.box_solve[b] == s) mem.push_back(b);
+    bool per_box = true, evenly = true;
+    int64_t vol = 0;
+    for (int b : mem) {
+      const Box& B = f.boxes[b];
+      vol += B.volume();
+      for (int d = 0; d < 3; ++d) {
+        if (pmod2(B.lo[d]) != 0 || B.n(d) % 2 != 0) { evenly = false; per_box = false; }
+        if (B.n(d) < 4) per_box = false;
+      }
+    }
+    const SolveGeom& G = f.geoms[s];
+    bool agg = false;
+    if (!per_box && evenly && vol == G.domain.volume()) {
+      agg = true;
+      for (int d = 0; d < 3; ++d)
+        if (G.domain.n(d) % 2 != 0 || G.domain.n(d) < 4 || pmod2(G.domain.lo[d]) != 0) agg = false;
+    }
+    if (!per_box && !agg) {
+      f.solve_bottom[s] = 1;
+      continue;
+    }
+    any = true;
+    c.solve_present[s] = 1;
+    SolveGeom& CG = c.geoms[s];
+    for (int d = 0; d < 3; ++d) {
+      CG.domain.lo[d] = G.domain.lo[d] / 2;
+      CG.domain.hi[d] = (G.domain.hi[d] + 1) / 2 - 1;
+      CG.h[d] = 2.0 * G.h[d];
+    }
+    if (per_box) {
+      for (int b : mem) {
+        Box cb;
+        for (int d = 0; d < 3; ++d) {
+          cb.lo[d] = f.boxes[b].lo[d] / 2;
+          cb.hi[d] = (f.boxes[b].hi[d] + 1) / 2 - 1;
+        }
+        f.parent[b] = (int)c.boxes.size();
+        c.boxes.push_back(cb);
+        c.box_solve.push_back(s);
+      }
+    } else {
+      int P = (int)c.boxes.size();
+      c.boxes.push_back(CG.domain);
+      c.box_solve.push_back(s);
+      for (int b : mem) f.parent[b] = P;
+    }
+  }
+  return any;
+}
+
+}  // namespace gmg

@@ -1,0 +1,82 @@
+// meta.h -- host-side index-space metadata: boxes, BoxArrays, the multigrid hierarchy
+// and the cached ghost-exchange / work tables (Sec. "Basic data structures",
+// Sec. "Communication": box intersections are computed once and cached).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace gmg {
+
+struct Box {
+  int lo[3] = {0, 0, 0};
+  int hi[3] = {-1, -1, -1};
+  int n(int d) const { return hi[d] - lo[d] + 1; }
+  bool empty() const { return n(0) <= 0 || n(1) <= 0 || n(2) <= 0; }
+  int64_t volume() const { return empty() ? 0 : (int64_t)n(0) * n(1) * n(2); }
+};
+
+Box intersect(const Box& a, const Box& b);
+Box shifted(const Box& a, int d, int s);
+
+// Geometry of one independent problem on one level (Sec. "Basic data structures":
+// Geometry, BCRec).
+struct SolveGeom {
+  Box domain;
+  double h[3] = {1, 1, 1};
+  int bclo[3] = {0, 0, 0};
+  int bchi[3] = {0, 0, 0};
+  bool periodic(int d) const { return bclo[d] == 0; }
+  bool all_periodic() const { return bclo[0] == 0 && bclo[1] == 0 && bclo[2] == 0; }
+};
+
+// One multigrid level of one or several independent problems.
+struct LevelMeta {
+  std::vector<Box> boxes;
+  std::vector<int> box_solve;       // per box: index into geoms
+  std::vector<SolveGeom> geoms;     // per solve (indexed by solve id)
+  std::vector<char> solve_present;  // per solve: has boxes on this level
+  std::vector<char> solve_bottom;   // per solve: this level is its bottom
+  std::vector<int> parent;          // per box: box on the next coarser level (-1: none)
+
+  // layout (shared by every element type)
+  std::vector<DevBox> dbox;
+  int64_t nelem = 0;
+  int64_t ncells = 0;
+
+  // cached tables
+  std::vector<GhostRect> ghosts;
+  std::vector<Chunk> ghost_chunks;
+  std::vector<Chunk> pair_chunks;    // boxes of solves that smooth on this level, 2 cells per item
+  std::vector<Chunk> pair_all_chunks;  // every box, 2 cells per item
+  std::vector<Chunk> cell_chunks;    // every box, 1 cell per item
+  std::vector<Chunk> coarse_chunks;  // boxes with a parent, 1 coarse cell per item
+  std::vector<BotCell> bot_cells;    // bottom problems on this level
+  std::vector<BotGhost> bot_ghosts;
+  std::vector<BotDesc> bot_descs;
+};
+
+// Checks that boxes are non-empty, inside the domain and pairwise disjoint; with
+// must_cover, that they cover it.  Returns "" or an error message.
+std::string validate_boxes(const std::vector<Box>& boxes, const Box& domain, bool must_cover);
+
+// Chop a box into pieces of at most max_grid_size cells per axis (low end first).
+std::vector<Box> chop(const Box& dom, int max_grid_size);
+
+// Layout, ghost rectangles and work tables of a level whose boxes, box_solve, geoms and
+// solve_present/solve_bottom are set.  Returns "" or an error message.
+std::string finalize_level(LevelMeta& L);
+
+// Multigrid coarsening with aggregation (Sec. "Linear Solvers"), per solve:
+//  - every box of the solve has even lo, even size and size >= 4: coarsen each box;
+//  - else every box has even lo and even size, the boxes cover the solve's domain and
+//    every domain edge is even and >= 4: the coarse level holds the coarsened domain as
+//    one box (aggregation);
+//  - else the solve's bottom is this level.
+// Fills f.parent and f.solve_bottom, and c's boxes/geoms.  Returns false if no solve
+// continues to a coarser level.
+bool make_coarse(LevelMeta& f, LevelMeta& c);
+
+}  // namespace gmg

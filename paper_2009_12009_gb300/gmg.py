@@ -1,0 +1,363 @@
+"""Python binding of the GB300 multigrid library (libgmg.so, C ABI in include/gmg.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels.
+PyTorch supplies device memory (fields and the workspace) and the CUDA stream.  There is
+no CPU fallback: if the library cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, BAD_INPUT, NOT_CONVERGED, DIVERGED, CUDA_ERR, DEVICE_TIMEOUT, NO_WORKSPACE, STATE = 0, -1, -2, -3, -4, -5, -6, -7
+PERIODIC, DIRICHLET0 = 0, 1
+FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
+DT_F64, DT_F32, DT_BF16 = 0, 1, 2
+GX = 8  # first valid cell of a row sits at element GX (16-byte aligned for every type)
+
+PRECISION = {"fp64": FP64, "fp32": MIXED_FP32, "mixed_fp32": MIXED_FP32, "bf16": MIXED_BF16, "mixed_bf16": MIXED_BF16}
+
+# every symbol declared in include/gmg.h
+EXPORTS = [
+    "gmg_default_params", "gmg_create", "gmg_destroy", "gmg_last_error", "gmg_define_domain", "gmg_define_level",
+    "gmg_chop_domain", "gmg_mg_nlevels", "gmg_mg_level_info", "gmg_mg_level_boxes", "gmg_mg_layout", "gmg_layout",
+    "gmg_pack", "gmg_unpack", "gmg_set_scalars", "gmg_set_acoef", "gmg_set_bcoef_cell", "gmg_set_bcoef_face",
+    "gmg_get_coeffs", "gmg_workspace_size", "gmg_set_workspace", "gmg_solve", "gmg_apply", "gmg_fill_boundary",
+    "gmg_smooth", "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_bottom_solve", "gmg_vcycle",
+]
+
+
+class Params(C.Structure):
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_iter", C.c_int), ("bottom_max_iter", C.c_int),
+                ("bottom_tol", C.c_double), ("precision", C.c_int), ("project_mean", C.c_int),
+                ("use_graph", C.c_int), ("profile", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rhs_norm", C.c_double),
+                ("initial_resid", C.c_double), ("final_resid", C.c_double), ("hist_len", C.c_int),
+                ("resid_hist", C.c_double * 256), ("bottom_iters", C.c_int), ("solve_ms", C.c_double),
+                ("kernel_launches", C.c_longlong), ("smooth0_ms", C.c_double), ("smooth0_launches", C.c_int),
+                ("resid0_ms", C.c_double), ("resid0_launches", C.c_int)]
+
+    def history(self):
+        return [self.resid_hist[i] for i in range(self.hist_len)]
+
+
+class GmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"gmg status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libgmg.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libgmg.so is missing and could not be built")
+        L = C.CDLL(path)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, i32p, i64p, f64p = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    sig = {
+        "gmg_default_params": [C.POINTER(Params)],
+        "gmg_create": [C.POINTER(C.c_void_p), vp],
+        "gmg_destroy": [vp],
+        "gmg_define_domain": [vp, i32p, i32p, f64p, f64p, i32p, i32p],
+        "gmg_define_level": [vp, C.c_int, C.c_int, i32p, C.c_int],
+        "gmg_chop_domain": [vp, C.c_int, C.c_int],
+        "gmg_mg_nlevels": [vp, i32p],
+        "gmg_mg_level_info": [vp, C.c_int, i32p, i32p],
+        "gmg_mg_level_boxes": [vp, C.c_int, i32p, i32p],
+        "gmg_mg_layout": [vp, C.c_int, C.c_int, i64p, i64p, i32p],
+        "gmg_layout": [vp, C.c_int, i64p, i64p],
+        "gmg_pack": [vp, C.c_int, C.c_int, vp, vp],
+        "gmg_unpack": [vp, C.c_int, C.c_int, vp, vp],
+        "gmg_set_scalars": [vp, C.c_double, C.c_double],
+        "gmg_set_acoef": [vp, C.c_int, vp],
+        "gmg_set_bcoef_cell": [vp, C.c_int, vp],
+        "gmg_set_bcoef_face": [vp, C.c_int, vp, vp, vp],
+        "gmg_get_coeffs": [vp, C.c_int, C.c_int, vp, vp, vp, vp],
+        "gmg_workspace_size": [vp, C.POINTER(Params), C.POINTER(C.c_size_t)],
+        "gmg_set_workspace": [vp, vp, C.c_size_t],
+        "gmg_solve": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_double, C.c_double, C.POINTER(Params),
+                      C.POINTER(SolveInfo)],
+        "gmg_apply": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)],
+        "gmg_fill_boundary": [vp, C.c_int, C.c_int, vp, C.c_int],
+        "gmg_smooth": [vp, C.c_int, C.c_int, vp, vp, C.c_int],
+        "gmg_residual": [vp, C.c_int, C.c_int, vp, vp, C.c_int, vp, f64p],
+        "gmg_restrict": [vp, C.c_int, C.c_int, vp, vp],
+        "gmg_prolong_add": [vp, C.c_int, C.c_int, vp, vp],
+        "gmg_bottom_solve": [vp, C.c_int, vp, vp, C.POINTER(Params), i32p],
+        "gmg_vcycle": [vp, C.c_int, vp, vp, C.POINTER(Params)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.gmg_last_error.argtypes = [vp]
+    L.gmg_last_error.restype = C.c_char_p
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().gmg_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        setattr(p, k, v)
+    return p
+
+
+def _arr(vals, ct):
+    a = (ct * len(vals))()
+    for i, v in enumerate(vals):
+        a[i] = v
+    return a
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+_TORCH_DT = {}
+
+
+def torch_dtype(dt):
+    import torch
+    return {DT_F64: torch.float64, DT_F32: torch.float32, DT_BF16: torch.bfloat16}[dt]
+
+
+class Context:
+    """One gmg context: a domain, its BoxArray, the multigrid hierarchy and (after
+    allocate()) a torch-owned device workspace."""
+
+    def __init__(self, domain, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0), prob_hi=(1.0, 1.0, 1.0), boxes=None,
+                 max_grid_size=None, stream=None):
+        self.L = lib()
+        h = C.c_void_p()
+        self._check(self.L.gmg_create(C.byref(h), C.c_void_p(stream or 0)), None)
+        self.h = h
+        lo, hi = domain
+        self._check(self.L.gmg_define_domain(self.h, _arr(lo, C.c_int), _arr(hi, C.c_int), _arr(prob_lo, C.c_double),
+                                             _arr(prob_hi, C.c_double), _arr(bc_lo, C.c_int), _arr(bc_hi, C.c_int)))
+        if boxes is not None:
+            flat = [v for b in boxes for v in (list(b[0]) + list(b[1]))]
+            self._check(self.L.gmg_define_level(self.h, 0, len(boxes), _arr(flat, C.c_int), 1))
+        else:
+            self._check(self.L.gmg_chop_domain(self.h, 0, int(max_grid_size)))
+        self.domain = (tuple(lo), tuple(hi))
+        self.workspace = None
+        self._keep = []
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.L.gmg_destroy(self.h)
+            self.h = None
+
+    def _check(self, st, h=-1):
+        if st != OK:
+            msg = self.L.gmg_last_error(self.h if h == -1 else h)
+            raise GmgError(st, (msg or b"").decode())
+        return st
+
+    # ---- hierarchy / layout -------------------------------------------------
+    @property
+    def nlevels(self):
+        n = C.c_int()
+        self._check(self.L.gmg_mg_nlevels(self.h, C.byref(n)))
+        return n.value
+
+    def level_info(self, m):
+        nb = C.c_int()
+        dom = (C.c_int * 6)()
+        self._check(self.L.gmg_mg_level_info(self.h, m, C.byref(nb), dom))
+        return nb.value, (tuple(dom[:3]), tuple(dom[3:]))
+
+    def level_boxes(self, m):
+        nb, _ = self.level_info(m)
+        lohi = (C.c_int * (6 * nb))()
+        par = (C.c_int * nb)()
+        self._check(self.L.gmg_mg_level_boxes(self.h, m, lohi, par))
+        boxes = [(tuple(lohi[6 * b:6 * b + 3]), tuple(lohi[6 * b + 3:6 * b + 6])) for b in range(nb)]
+        return boxes, list(par)
+
+    def layout(self, m, dt=DT_F64):
+        nb, _ = self.level_info(m)
+        ne = C.c_int64()
+        offs = (C.c_int64 * nb)()
+        sx = (C.c_int * nb)()
+        self._check(self.L.gmg_mg_layout(self.h, m, dt, C.byref(ne), offs, sx))
+        return ne.value, list(offs), list(sx)
+
+    def level_shape(self, m):
+        _, (lo, hi) = self.level_info(m)
+        return (hi[2] - lo[2] + 1, hi[1] - lo[1] + 1, hi[0] - lo[0] + 1)
+
+    # ---- workspace ------------------------------------------------------------
+    def workspace_bytes(self, precision=FP64):
+        n = C.c_size_t()
+        p = default_params(precision=precision)
+        self._check(self.L.gmg_workspace_size(self.h, C.byref(p), C.byref(n)))
+        return n.value
+
+    def allocate(self, precision=FP64, device="cuda"):
+        import torch
+        nbytes = self.workspace_bytes(precision)
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = ws.data_ptr()
+        off = (-base) % 256
+        self._check(self.L.gmg_set_workspace(self.h, C.c_void_p(base + off), C.c_size_t(nbytes)))
+        self.workspace = ws
+        return self
+
+    def field(self, m=0, dt=DT_F64, device="cuda"):
+        import torch
+        ne, _, _ = self.layout(m, dt)
+        return torch.zeros(ne, dtype=torch_dtype(dt), device=device)
+
+    def box_views(self, buf, m=0):
+        """Ghosted (nz+2, ny+2, nx+2) views of every box of a boxed-layout tensor."""
+        boxes, _ = self.level_boxes(m)
+        _, offs, sxs = self.layout(m)
+        out = []
+        for (lo, hi), off, sx in zip(boxes, offs, sxs):
+            n = [hi[d] - lo[d] + 1 for d in range(3)]
+            blk = buf[off:off + sx * (n[1] + 2) * (n[2] + 2)].view(n[2] + 2, n[1] + 2, sx)
+            out.append(blk[:, :, GX - 1:GX + n[0] + 1])
+        return out
+
+    # ---- dense <-> boxed --------------------------------------------------------
+    def pack(self, dense, m=0, dt=DT_F64, out=None):
+        import torch
+        dense = torch.as_tensor(dense, dtype=torch.float64, device="cuda").contiguous()
+        assert tuple(dense.shape) == self.level_shape(m), (dense.shape, self.level_shape(m))
+        out = self.field(m, dt) if out is None else out
+        self._check(self.L.gmg_pack(self.h, m, dt, _ptr(dense), _ptr(out)))
+        self._keep = [dense]
+        return out
+
+    def unpack(self, boxed, m=0, dt=DT_F64):
+        import torch
+        out = torch.zeros(self.level_shape(m), dtype=torch.float64, device=boxed.device)
+        self._check(self.L.gmg_unpack(self.h, m, dt, _ptr(boxed), _ptr(out)))
+        return out
+
+    # ---- coefficients -------------------------------------------------------------
+    def set_scalars(self, a, b):
+        self._check(self.L.gmg_set_scalars(self.h, float(a), float(b)))
+
+    def set_alpha(self, alpha_dense):
+        buf = self.pack(alpha_dense)
+        self._check(self.L.gmg_set_acoef(self.h, 0, _ptr(buf)))
+
+    def set_beta(self, beta_dense=None):
+        import torch
+        if beta_dense is None:
+            beta_dense = torch.ones(self.level_shape(0), dtype=torch.float64)
+        buf = self.pack(beta_dense)
+        self._check(self.L.gmg_set_bcoef_cell(self.h, 0, _ptr(buf)))
+
+    def set_beta_faces(self, bx, by, bz):
+        self._check(self.L.gmg_set_bcoef_face(self.h, 0, _ptr(bx), _ptr(by), _ptr(bz)))
+
+    def coeffs(self, m, dt=DT_F64):
+        wx, wy, wz, d = (self.field(m, dt) for _ in range(4))
+        self._check(self.L.gmg_get_coeffs(self.h, m, dt, _ptr(wx), _ptr(wy), _ptr(wz), _ptr(d)))
+        return wx, wy, wz, d
+
+    # ---- solve ------------------------------------------------------------------------
+    def solve(self, rhs, phi=None, tol_rel=1e-10, tol_abs=0.0, raise_on_error=True, **params):
+        """rhs, phi: FP64 boxed-layout tensors of level 0.  Returns (phi, info)."""
+        phi = self.field(0) if phi is None else phi
+        p = default_params(**params)
+        info = SolveInfo()
+        pa = (C.c_void_p * 1)(phi.data_ptr())
+        ra = (C.c_void_p * 1)(rhs.data_ptr())
+        st = self.L.gmg_solve(self.h, pa, ra, tol_rel, tol_abs, C.byref(p), C.byref(info))
+        if st not in (OK, NOT_CONVERGED) and raise_on_error:
+            self._check(st)
+        return phi, info
+
+    def apply(self, phi, out=None):
+        out = self.field(0) if out is None else out
+        pa = (C.c_void_p * 1)(phi.data_ptr())
+        oa = (C.c_void_p * 1)(out.data_ptr())
+        self._check(self.L.gmg_apply(self.h, oa, pa))
+        return out
+
+    # ---- individual steps ----------------------------------------------------------------
+    def fill_boundary(self, f, m=0, dt=DT_F64, colour=-1):
+        self._check(self.L.gmg_fill_boundary(self.h, m, dt, _ptr(f), colour))
+
+    def smooth(self, phi, rhs, m=0, dt=DT_F64, colour=0):
+        self._check(self.L.gmg_smooth(self.h, m, dt, _ptr(phi), _ptr(rhs), colour))
+
+    def residual(self, phi, rhs, m=0, dt=DT_F64, rdt=None, norm=False):
+        rdt = dt if rdt is None else rdt
+        r = self.field(m, rdt)
+        nv = C.c_double()
+        self._check(self.L.gmg_residual(self.h, m, dt, _ptr(phi), _ptr(rhs), rdt, _ptr(r),
+                                        C.byref(nv) if norm else None))
+        return (r, nv.value) if norm else r
+
+    def restrict(self, fine, m=0, dt=DT_F64):
+        c = self.field(m + 1, dt)
+        self._check(self.L.gmg_restrict(self.h, m, dt, _ptr(fine), _ptr(c)))
+        return c
+
+    def prolong_add(self, coarse, fine, m=0, dt=DT_F64):
+        self._check(self.L.gmg_prolong_add(self.h, m, dt, _ptr(coarse), _ptr(fine)))
+
+    def bottom_solve(self, rhs, dt=DT_F64, **params):
+        x = self.field(self.nlevels - 1, dt)
+        p = default_params(**params)
+        it = C.c_int()
+        self._check(self.L.gmg_bottom_solve(self.h, dt, _ptr(rhs), _ptr(x), C.byref(p), C.byref(it)))
+        return x, it.value
+
+    def vcycle(self, r, dt=DT_F64, **params):
+        e = self.field(0, dt)
+        p = default_params(**params)
+        self._check(self.L.gmg_vcycle(self.h, dt, _ptr(e), _ptr(r), C.byref(p)))
+        return e
+
+
+class Poisson:
+    """Convenience front end for dense problems: a*alpha*phi - b*div(beta grad phi) = rhs
+    on an (nz, ny, nx) grid chopped into boxes of at most max_grid_size cells."""
+
+    def __init__(self, shape_xyz, bc="dirichlet", max_grid_size=64, boxes=None, prob_hi=None, precision="fp64",
+                 a=0.0, b=1.0, alpha=None, beta=None):
+        import torch
+        nx, ny, nz = shape_xyz
+        bcv = PERIODIC if bc == "periodic" else DIRICHLET0
+        self.ctx = Context(((0, 0, 0), (nx - 1, ny - 1, nz - 1)), [bcv] * 3, [bcv] * 3,
+                           prob_hi=prob_hi or (1.0, 1.0, 1.0), boxes=boxes, max_grid_size=max_grid_size,
+                           stream=torch.cuda.current_stream().cuda_stream)
+        self.precision = PRECISION[precision] if isinstance(precision, str) else precision
+        self.ctx.allocate(self.precision)
+        self.ctx.set_scalars(a, b)
+        if alpha is not None:
+            self.ctx.set_alpha(alpha)
+        self.ctx.set_beta(beta)
+
+    def solve(self, rhs_dense, tol_rel=1e-10, **params):
+        rhs = self.ctx.pack(rhs_dense)
+        params.setdefault("precision", self.precision)
+        phi, info = self.ctx.solve(rhs, tol_rel=tol_rel, **params)
+        return self.ctx.unpack(phi), info

@@ -1,0 +1,104 @@
+"""Host-side checks of the CUDA library that need no GPU: the C ABI loads and exports
+every symbol of include/gmg.h, the multigrid hierarchy and its box metadata match the
+oracle's, the boxed layout keeps every row's first valid cell 16-byte aligned, and bad
+input is refused with an error code.  No compute call is made here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2009_12009_gb300 import gmg
+from paper_2009_12009_gb300 import inputs as I
+from tests import cases
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_exports_match_header():
+    src = open(os.path.join(ROOT, "include", "gmg.h")).read()
+    declared = sorted(set(re.findall(r"\b(gmg_[a-z0-9_]+)\s*\(", src)))
+    L = gmg.lib()
+    missing = [n for n in declared if not hasattr(L, n)]
+    assert not missing, missing
+    assert len(set(gmg.EXPORTS)) == len(gmg.EXPORTS)
+    assert set(declared) == set(gmg.EXPORTS)
+
+
+HIER_CASES = [
+    ("poisson32", None),
+    ("uneven", None),
+    ("periodic", None),
+    ("helmholtz", None),
+    ("oddlo", None),
+    ("batch", ((0, 0, 0), (47, 159, 95))),
+    ("odd12", ((0, 0, 0), (11, 11, 11))),
+]
+
+
+@pytest.mark.parametrize("name,dom", HIER_CASES)
+def test_hierarchy_matches_oracle(orc, name, dom):
+    """Per-box coarsening, then aggregation into one box (Sec. "Linear Solvers"): the
+    library builds the same levels, boxes and parent links as the oracle."""
+    if dom is None:
+        c = cases.make(name)
+        dom, boxes, bl, bh = c["domain"], c["boxes"], c["bc_lo"], c["bc_hi"]
+    else:
+        boxes = I.chop(*dom, 32 if name == "batch" else 6)
+        bl = bh = [I.DIRICHLET] * 3
+    P = orc.Problem(dom, boxes, bl, bh)
+    Cx = gmg.Context(dom, bl, bh, boxes=boxes)
+    assert Cx.nlevels == P.nlevels
+    for m in range(P.nlevels):
+        cb, par = Cx.level_boxes(m)
+        assert cb == P.level_boxes(m)
+        assert Cx.level_info(m)[1] == P.level_domain(m)
+        assert par == P.level_parents(m)
+
+
+def test_chop_matches_inputs():
+    dom = ((0, 0, 0), (47, 159, 95))
+    Cx = gmg.Context(dom, [1] * 3, [1] * 3, max_grid_size=32)
+    assert Cx.level_boxes(0)[0] == I.chop(*dom, 32)
+
+
+@pytest.mark.parametrize("name", ["uneven", "poisson32", "oddlo"])
+def test_layout_alignment(name):
+    c = cases.make(name)
+    Cx = gmg.Context(c["domain"], c["bc_lo"], c["bc_hi"], boxes=c["boxes"])
+    for m in range(Cx.nlevels):
+        boxes, _ = Cx.level_boxes(m)
+        for dt, es in ((gmg.DT_F64, 8), (gmg.DT_F32, 4), (gmg.DT_BF16, 2)):
+            ne, offs, sxs = Cx.layout(m, dt)
+            prev_end = 0
+            for (lo, hi), off, sx in zip(boxes, offs, sxs):
+                n = [hi[d] - lo[d] + 1 for d in range(3)]
+                assert off >= prev_end and (off * es) % 16 == 0
+                assert ((off + gmg.GX) * es) % 16 == 0 and (sx * es) % 16 == 0
+                assert sx >= gmg.GX + n[0] + 1
+                prev_end = off + sx * (n[1] + 2) * (n[2] + 2)
+            assert prev_end <= ne
+
+
+def test_bad_input_refused():
+    dom = ((0, 0, 0), (7, 7, 7))
+    with pytest.raises(gmg.GmgError) as e:
+        gmg.Context(dom, [0, 1, 1], [1, 1, 1], max_grid_size=4)  # half-periodic axis
+    assert e.value.status == gmg.BAD_INPUT
+    with pytest.raises(gmg.GmgError) as e:
+        gmg.Context(dom, [1] * 3, [1] * 3, boxes=[((0, 0, 0), (7, 7, 7)), ((4, 4, 4), (7, 7, 7))])  # overlap
+    assert e.value.status == gmg.BAD_INPUT
+    with pytest.raises(gmg.GmgError) as e:
+        gmg.Context(dom, [1] * 3, [1] * 3, boxes=[((0, 0, 0), (3, 7, 7))])  # does not cover
+    assert e.value.status == gmg.BAD_INPUT
+    with pytest.raises(gmg.GmgError) as e:
+        gmg.Context(dom, [1] * 3, [1] * 3, boxes=[((0, 0, 0), (8, 7, 7))])  # outside
+    assert e.value.status == gmg.BAD_INPUT
+    Cx = gmg.Context(dom, [1] * 3, [1] * 3, max_grid_size=4)
+    st = Cx.L.gmg_fill_boundary(Cx.h, 0, gmg.DT_F64, None, -1)
+    assert st == gmg.NO_WORKSPACE
+    st = Cx.L.gmg_set_workspace(Cx.h, C.c_void_p(256), C.c_size_t(16))
+    assert st == gmg.NO_WORKSPACE
+    st = Cx.L.gmg_set_workspace(Cx.h, C.c_void_p(257), C.c_size_t(1 << 40))
+    assert st == gmg.BAD_INPUT
+    assert Cx.L.gmg_set_scalars(Cx.h, 0.0, 0.0) == gmg.BAD_INPUT
