@@ -235,6 +235,42 @@ gmg_status gmg_bottom_solve(gmg_ctx* ctx, int dt, const void* rhs, void* x, cons
 /* One V-cycle on the correction equation of MG level 0: e = V(r), element type dt. */
 gmg_status gmg_vcycle(gmg_ctx* ctx, int dt, void* e, const void* r, const gmg_params* p);
 
+/* ------------------------------------------------- allocation-free box solve */
+
+/* BiCGStab solve of one box that allocates nothing (the paper has no counterpart to this
+   entry point).  It is for callers that cannot allocate device memory when they solve:
+   an operator inside another framework that is handed only its input and output
+   tensors, code running while its own stream is being captured into a CUDA graph
+   (cudaMalloc is not allowed during capture), or a host that forbids allocation after
+   start-up.  Such callers cannot provide a workspace, so no context is used: inputs and
+   output are plain dense device arrays (x fastest) and the seven BiCGStab vectors live
+   in one static device array of the library.
+
+   Solves A x = rhs on an nx * ny * nz box with A = diag - (weighted neighbours):
+     (A x)_c = diag_c x_c - sum over the six faces f of c of w_f x_nbr(f),
+   the same operator and the same BiCGStab iteration as gmg_bottom_solve (x0 = 0, stop
+   at ||r||_inf <= tol ||r0||_inf, after max_iter iterations, or on breakdown; FP64).
+     wx: (nx+1)*ny*nz face weights, face i-1/2 of cell (i,j,k) at i + (nx+1)*(j + ny*k);
+     wy: nx*(ny+1)*nz, face j-1/2 at i + nx*(j + (ny+1)*k);
+     wz: nx*ny*(nz+1), face k-1/2 at i + nx*(j + ny*k);
+     diag, rhs, x: nx*ny*nz.  All device pointers; x is written.
+   bc_lo/bc_hi: GMG_BC_PERIODIC (both sides; wraps inside the box) or GMG_BC_DIRICHLET0
+   (ghost = minus the adjacent cell).  singular != 0 projects rhs and x onto zero mean.
+   iters: device int receiving the iteration count, or NULL.
+
+   Limit: (nx+2)(ny+2)(nz+2) <= 65536; larger boxes return GMG_ERR_BAD_INPUT.  The static
+   scratch (65536 * 7 doubles = 3.5 MiB) is held by every GPU that loads the library until
+   the process exits.  All calls share it and it keeps the previous call's contents (the
+   kernel initialises what it reads); calls whose kernels overlap on the GPU race on it
+   and must be serialised by the caller.  The first call on a device resolves the scratch
+   address (cudaGetSymbolAddress) with that device current; make that first call before
+   any stream capture.  Work is enqueued on cuda_stream; errors are reported through the
+   return value and gmg_last_error(NULL). */
+gmg_status gmg_box_bicgstab_noalloc(void* cuda_stream, int nx, int ny, int nz, const int bc_lo[3], const int bc_hi[3],
+                                    int singular, const double* wx, const double* wy, const double* wz,
+                                    const double* diag, const double* rhs, double* x, int max_iter, double tol,
+                                    int* iters);
+
 #ifdef __cplusplus
 }
 #endif

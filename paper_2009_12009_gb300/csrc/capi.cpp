@@ -52,6 +52,11 @@ struct Carver {
 
 }  // namespace
 
+namespace gmg {
+// errors of calls that have no context; read back through gmg_last_error(NULL)
+void set_thread_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace gmg
+
 struct gmg_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs

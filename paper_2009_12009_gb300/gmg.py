@@ -28,6 +28,7 @@ EXPORTS = [
     "gmg_pack", "gmg_unpack", "gmg_set_scalars", "gmg_set_acoef", "gmg_set_bcoef_cell", "gmg_set_bcoef_face",
     "gmg_get_coeffs", "gmg_workspace_size", "gmg_set_workspace", "gmg_solve", "gmg_apply", "gmg_fill_boundary",
     "gmg_smooth", "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_bottom_solve", "gmg_vcycle",
+    "gmg_box_bicgstab_noalloc",
 ]
 
 
@@ -103,6 +104,8 @@ def _declare(L):
         "gmg_prolong_add": [vp, C.c_int, C.c_int, vp, vp],
         "gmg_bottom_solve": [vp, C.c_int, vp, vp, C.POINTER(Params), i32p],
         "gmg_vcycle": [vp, C.c_int, vp, vp, C.POINTER(Params)],
+        "gmg_box_bicgstab_noalloc": [vp, C.c_int, C.c_int, C.c_int, i32p, i32p, C.c_int, vp, vp, vp, vp, vp, vp,
+                                     C.c_int, C.c_double, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
