@@ -1,8 +1,8 @@
 #!/usr/bin/env python
 """Benchmark: FP64 multigrid solve to 1e-10 relative residual on the abec256 workload.
 
-Workload (the paper's solver study, Sec. "Linear Solvers": 256^3 cells per node, variable
-coefficients): 256^3 cells, Dirichlet walls, 64 boxes of 64^3, a = 0, b = 1, beta =
+Workload (shaped like the solver study of Sec. "Linear Solvers", which runs 256^3 cells on
+each node with variable coefficients): 256^3 cells, Dirichlet walls, 64 boxes of 64^3, a = 0, b = 1, beta =
 exp(N(0,1)) smoothed by one 3x3x3 mean filter (harmonic faces), rhs N(0,1), seed 12011.
 
 A step is one whole solve from phi = 0 to ||r||_inf <= 1e-10 ||rhs||_inf: every V-cycle
@@ -210,7 +210,7 @@ def main():
     cfg = I.abec256()
     stream = torch.cuda.current_stream()
     ctx = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"], stream=stream.cuda_stream)
-    ctx.allocate(gmg.MIXED_FP32)
+    ctx.allocate(gmg.FP64 if args.no_mixed else gmg.MIXED_FP32)
     ctx.set_scalars(cfg["a"], cfg["b"])
     ctx.set_beta(torch.from_numpy(cfg["beta"]))
     rhs = ctx.pack(torch.from_numpy(cfg["rhs"]))

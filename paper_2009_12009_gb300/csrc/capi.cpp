@@ -348,16 +348,22 @@ gmg_status zero_workspace(gmg_ctx* c) {
   return GMG_OK;
 }
 
+// A timing event: inside a capture it must be an external event-record node (a plain
+// record becomes a dependency edge without a timestamp); outside, a plain record.
+void record_timing_event(gmg_ctx* c, cudaEvent_t e, cudaStream_t s) {
+  if (s == c->cap_stream) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
+
 void smooth_colour(gmg_ctx* c, int dt, int m, int colour, cudaStream_t s) {
   const LevelDev& D = c->dev[m];
   const LevelBufs& B = c->buf[m];
   launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
   const bool prof = c->profiling && m == 0;
   cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
-  // external event-record nodes when captured, so that the events carry timestamps
-  if (prof) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  if (prof) record_timing_event(c, ev[0], s);
   launch_smooth(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s);
-  if (prof) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+  if (prof) record_timing_event(c, ev[1], s);
 }
 
 void smooth_sweeps(gmg_ctx* c, int dt, int m, int nsweep, cudaStream_t s) {
@@ -392,10 +398,10 @@ void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const g
   launch_fill(DT_F64, c->dev[0], phi, -1, 0, s);
   cudaMemsetAsync(c->normbits, 0, 8, s);
   cudaEvent_t* ev = c->profiling ? ev_pair(c->ev_resid, c->n_ev_resid++) : nullptr;
-  if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  if (ev) record_timing_event(c, ev[0], s);
   launch_residual(DT_F64, dt, c->dev[0], phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits,
                   singular(c) ? c->scal : nullptr, s);
-  if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+  if (ev) record_timing_event(c, ev[1], s);
   cudaMemcpyAsync(c->h_bits, c->normbits, 8, cudaMemcpyDeviceToHost, s);
 }
 

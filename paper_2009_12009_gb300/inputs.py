@@ -5,8 +5,8 @@ the solver's arithmetic: only grid generation (max_grid_size chopping, Sec. "Reg
 and the random coefficient / right-hand-side fields.  Dense arrays are float64 with shape
 (nz, ny, nx), x fastest.
 
-Workload shapes follow the paper's solver study (Sec. "Linear Solvers": variable
-coefficient alpha/beta problem, 256^3 cells per node):
+Workload shapes follow the solver study of Sec. "Linear Solvers" (a variable-coefficient
+alpha/beta problem with 256^3 cells on each node):
 
   poisson32   32^3 periodic, 8 boxes of 16^3, beta = 1, rhs = sin(2 pi x) sin(2 pi y) sin(2 pi z)
   abec256     256^3 Dirichlet, 64 boxes of 64^3, beta log-normal smoothed, rhs N(0,1)
