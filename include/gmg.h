@@ -235,6 +235,42 @@ gmg_status gmg_bottom_solve(gmg_ctx* ctx, int dt, const void* rhs, void* x, cons
 /* One V-cycle on the correction equation of MG level 0: e = V(r), element type dt. */
 gmg_status gmg_vcycle(gmg_ctx* ctx, int dt, void* e, const void* r, const gmg_params* p);
 
+/* ------------------------------------------------------------ batched form */
+
+/* Several independent problems in one context (the batched form of the solve: many
+   solves with boxes of uneven sizes run as one set of launches per V-cycle step).
+   Problem s has domain dom_lohi[6s..6s+5] (lo, hi inclusive), physical extent
+   prob_lo[3s..], prob_hi[3s..], boundary conditions bc_lo[3s..], bc_hi[3s..] and
+   nboxes[s] boxes; box_lohi lists the boxes of problem 0, then of problem 1, ... (6 ints
+   each).  Every problem's boxes must be disjoint and cover its domain.  Each problem
+   gets its own multigrid hierarchy (Sec. "Linear Solvers": per-box coarsening, then
+   aggregation) and its own bottom level; MG level m of the context is the union of level
+   m of every problem that still has one.  Replaces any previous definition. */
+gmg_status gmg_define_batch(gmg_ctx* ctx, int nsolves, const int* dom_lohi, const double* prob_lo,
+                            const double* prob_hi, const int* bc_lo, const int* bc_hi, const int* nboxes,
+                            const int* box_lohi);
+
+/* Number of independent problems in the context (1 after gmg_define_domain). */
+gmg_status gmg_num_solves(const gmg_ctx* ctx, int* nsolves);
+
+/* Boxes of problem `solve` on MG level m: index of its first box and count (-1, 0 if the
+   problem has no boxes on that level). */
+gmg_status gmg_solve_boxes(const gmg_ctx* ctx, int m, int solve, int* first, int* count);
+
+/* gmg_pack / gmg_unpack for one problem: dense (nz, ny, nx) FP64 array over that
+   problem's domain on MG level m <-> its boxes in the level's boxed layout. */
+gmg_status gmg_pack_solve(gmg_ctx* ctx, int m, int dt, int solve, const double* dense, void* boxed);
+gmg_status gmg_unpack_solve(gmg_ctx* ctx, int m, int dt, int solve, const void* boxed, double* dense);
+
+/* Solve every problem of the context from phi = 0: phi and rhs are FP64 level-0 boxed
+   buffers holding all problems.  Each problem stops at its own tolerance
+   max(tol_rel * ||rhs_s||_inf, tol_abs) (or max_iter); problems that have converged are
+   masked out of the remaining V-cycles, so each one performs exactly the iterations a
+   solve of it alone would.  infos: nsolves entries (may be NULL).  Returns GMG_OK when all
+   converged, else the worst status (GMG_ERR_DIVERGED before GMG_ERR_NOT_CONVERGED). */
+gmg_status gmg_batch_solve(gmg_ctx* ctx, void* phi, const void* rhs, double tol_rel, double tol_abs,
+                           const gmg_params* p, gmg_solve_info* infos);
+
 /* ------------------------------------------------- allocation-free box solve */
 
 /* BiCGStab solve of one box that allocates nothing (the paper has no counterpart to this

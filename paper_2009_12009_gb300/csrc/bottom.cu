@@ -103,9 +103,11 @@ __global__ void __launch_bounds__(BT) k_bottom(const BotDesc* __restrict__ descs
                                                const BotGhost* __restrict__ ghosts, const T* __restrict__ rhs, T* xout,
                                                const double* __restrict__ wx, const double* __restrict__ wy,
                                                const double* __restrict__ wz, const double* __restrict__ D,
-                                               double* work, int64_t nelem, int maxit, double tol, int* iters) {
+                                               double* work, int64_t nelem, int maxit, double tol, int* iters,
+                                               const int* __restrict__ active) {
   __shared__ double sh[BT / 32 + 1];
   const BotDesc P = descs[blockIdx.x];
+  if (active && !active[P.solve]) return;
   BotCtx c{cells + P.cell0, ghosts + P.ghost0, P.ncell, P.nghost, wx, wy, wz, D};
   double* r = work;
   double* rh = work + nelem;
@@ -197,15 +199,15 @@ void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Co
   switch (dt) {
     case DT_F64:
       k_bottom<double><<<L.n_bot, BT, 0, s>>>(L.bot_descs, L.bot_cells, L.bot_ghosts, (const double*)rhs, (double*)x, wx,
-                                              wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters);
+                                              wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
       break;
     case DT_F32:
       k_bottom<float><<<L.n_bot, BT, 0, s>>>(L.bot_descs, L.bot_cells, L.bot_ghosts, (const float*)rhs, (float*)x, wx,
-                                             wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters);
+                                             wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
       break;
     default:
       k_bottom<bf16><<<L.n_bot, BT, 0, s>>>(L.bot_descs, L.bot_cells, L.bot_ghosts, (const bf16*)rhs, (bf16*)x, wx, wy,
-                                            wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters);
+                                            wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
       break;
   }
 }

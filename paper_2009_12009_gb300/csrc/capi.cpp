@@ -3,7 +3,13 @@
 // The host side owns only metadata: the hierarchy, the cached exchange tables and the
 // carve-up of the caller's workspace.  Every step of the solve runs in the kernels of
 // kernels.cu / bottom.cu; the host decides the launch order and reads back one norm per
-// outer iteration.
+// problem per outer iteration.
+//
+// A context holds one problem (gmg_define_domain + gmg_define_level / gmg_chop_domain) or
+// several independent problems (gmg_define_batch).  Either way each MG level is ONE list
+// of boxes over all problems, so one launch per step covers every problem; a device mask
+// of still-active problems makes converged ones skip their work.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -63,9 +69,8 @@ struct gmg_ctx {
   std::string err;
 
   bool have_domain = false;
-  SolveGeom geom0;
-  double prob_lo[3] = {0, 0, 0}, prob_hi[3] = {1, 1, 1};
-  std::vector<LevelMeta> L;  // multigrid levels, 0 = user's BoxArray
+  std::vector<SolveGeom> geoms;  // level-0 geometry per independent problem
+  std::vector<LevelMeta> L;      // multigrid levels, 0 = the user's BoxArray(s)
   double a = 0.0, b = 1.0;
 
   // workspace
@@ -75,19 +80,23 @@ struct gmg_ctx {
   std::vector<LevelDev> dev;
   std::vector<LevelBufs> buf;
   double *alpha0 = nullptr, *bx0 = nullptr, *by0 = nullptr, *bz0 = nullptr, *tmp0 = nullptr;
-  unsigned long long* normbits = nullptr;  // [0]: residual norm of the outer loop; [1..]: scratch
+  // per-problem device scalars
+  unsigned long long* normbits = nullptr;  // [0, ns): outer residual norms; [ns, 2ns): rhs / step norms
   double* partials = nullptr;
-  double* scal = nullptr;  // [0]: rhs mean, [1]: phi mean, [2..]: scratch
+  double* scal = nullptr;  // [0, ns): rhs means; [ns, 2ns): phi means
   int* bot_iters = nullptr;
+  int* active = nullptr;  // per problem: 1 while it iterates
   int max_cell_chunks = 0;
 
   bool have_beta = false, have_alpha = false;
   bool coefs_dirty = true;
 
-  // pinned host mirror of a few device scalars
+  // pinned host mirrors
   unsigned long long* h_bits = nullptr;
   double* h_scal = nullptr;
   int* h_iters = nullptr;
+  int* h_active = nullptr;
+  size_t h_cap = 0;
 
   // graphs of one outer iteration, keyed by (phi, rhs, precision, nu1, nu2, bottom, profile)
   std::map<std::tuple<void*, const void*, int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
@@ -96,6 +105,8 @@ struct gmg_ctx {
   bool profiling = false;
   std::vector<cudaEvent_t> ev_smooth, ev_resid;
   int n_ev_smooth = 0, n_ev_resid = 0;
+
+  int ns() const { return (int)geoms.size(); }
 };
 
 #define SETERR(ctx, code, msg) \
@@ -104,13 +115,13 @@ struct gmg_ctx {
     return (code);              \
   } while (0)
 
-#define CK(ctx, call)                                                                     \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess) {                                                              \
-      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
-      return GMG_ERR_CUDA;                                                                \
-    }                                                                                     \
+#define CK(ctx, call)                                                  \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) {                                           \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+      return GMG_ERR_CUDA;                                             \
+    }                                                                  \
   } while (0)
 
 namespace {
@@ -120,7 +131,7 @@ void drop_graphs(gmg_ctx* c) {
   c->graphs.clear();
 }
 
-// event pair k of a list (created on first use)
+// event pair k of a list (created on first use, outside any capture)
 cudaEvent_t* ev_pair(std::vector<cudaEvent_t>& v, int k) {
   while ((int)v.size() < 2 * (k + 1)) {
     cudaEvent_t e;
@@ -130,7 +141,12 @@ cudaEvent_t* ev_pair(std::vector<cudaEvent_t>& v, int k) {
   return &v[2 * k];
 }
 
-bool singular(const gmg_ctx* c) { return c->geom0.all_periodic() && c->a == 0.0; }
+bool singular(const gmg_ctx* c, int s) { return c->geoms[s].all_periodic() && c->a == 0.0; }
+bool any_singular(const gmg_ctx* c) {
+  for (int s = 0; s < c->ns(); ++s)
+    if (singular(c, s)) return true;
+  return false;
+}
 
 int nlev(const gmg_ctx* c) { return (int)c->L.size(); }
 
@@ -160,10 +176,12 @@ gmg_status check_level(gmg_ctx* c, int m, int dt) {
 size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
   Carver cv(base);
   const int n = nlev(c);
+  const size_t ns = (size_t)std::max(1, c->ns());
   if (fill) {
     c->dev.assign(n, LevelDev());
     c->buf.assign(n, LevelBufs());
   }
+  int* active = (int*)cv.take(4 * ns);
   int maxchunks = 1;
   for (int m = 0; m < n; ++m) {
     const LevelMeta& M = c->L[m];
@@ -171,6 +189,8 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     LevelDev D;
     LevelBufs B;
     D.nelem = M.nelem;
+    D.nsolves = (int)ns;
+    D.active = active;
     D.boxes = (const DevBox*)cv.take(sizeof(DevBox) * M.dbox.size());
     D.geoms = (const DevGeom*)cv.take(sizeof(DevGeom) * M.geoms.size());
     D.ghosts = (const GhostRect*)cv.take(sizeof(GhostRect) * M.ghosts.size());
@@ -189,6 +209,8 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.bot_ghosts = (const BotGhost*)cv.take(sizeof(BotGhost) * M.bot_ghosts.size());
     D.bot_descs = (const BotDesc*)cv.take(sizeof(BotDesc) * M.bot_descs.size());
     D.n_bot = (int)M.bot_descs.size();
+    D.solve_chunk_range = (const int*)cv.take(sizeof(int) * M.solve_chunk_range.size());
+    D.inv_count = (const double*)cv.take(sizeof(double) * M.inv_count.size());
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
     B.acoef = (double*)cv.take(8 * ne);
     B.wx = (double*)cv.take(8 * ne);
@@ -221,13 +243,14 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
   double* by0 = (double*)cv.take(8 * ne0);
   double* bz0 = (double*)cv.take(8 * ne0);
   double* tmp0 = (double*)cv.take(8 * ne0);
-  unsigned long long* nb = (unsigned long long*)cv.take(8 * 64);
+  unsigned long long* nb = (unsigned long long*)cv.take(8 * (2 * ns + 8));
   double* partials = (double*)cv.take(8 * (size_t)maxchunks);
-  double* scal = (double*)cv.take(8 * 64);
-  int* iters = (int*)cv.take(4 * (c->L.empty() ? 1 : c->L[0].geoms.size()));
+  double* scal = (double*)cv.take(8 * (2 * ns + 8));
+  int* iters = (int*)cv.take(4 * ns);
   if (fill) {
     c->alpha0 = alpha0; c->bx0 = bx0; c->by0 = by0; c->bz0 = bz0; c->tmp0 = tmp0;
     c->normbits = nb; c->partials = partials; c->scal = scal; c->bot_iters = iters;
+    c->active = active;
     c->max_cell_chunks = maxchunks;
   }
   return cv.off + 256;
@@ -272,32 +295,48 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.bot_cells, M.bot_cells))) return st;
     if ((st = upload(c, D.bot_ghosts, M.bot_ghosts))) return st;
     if ((st = upload(c, D.bot_descs, M.bot_descs))) return st;
+    if ((st = upload(c, D.solve_chunk_range, M.solve_chunk_range))) return st;
+    if ((st = upload(c, D.inv_count, M.inv_count))) return st;
   }
+  std::vector<int> ones(c->ns(), 1);
+  gmg_status st = upload(c, c->active, ones);
+  if (st) return st;
   CK(c, cudaStreamSynchronize(c->stream));
   return GMG_OK;
 }
 
-// Build the multigrid hierarchy from level-0 boxes.
-gmg_status build_hierarchy(gmg_ctx* c, const std::vector<Box>& boxes) {
-  std::string e = validate_boxes(boxes, c->geom0.domain, true);
-  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, e);
+void reset_problem(gmg_ctx* c) {
   drop_graphs(c);
   c->L.clear();
   c->ws = nullptr;
   c->ws_bytes = 0;
   c->have_beta = c->have_alpha = false;
   c->coefs_dirty = true;
+}
+
+// Build the multigrid hierarchy from level-0 boxes (stored problem by problem).
+gmg_status build_hierarchy(gmg_ctx* c, const std::vector<Box>& boxes, const std::vector<int>& box_solve) {
+  const int ns = c->ns();
+  for (int s = 0; s < ns; ++s) {
+    std::vector<Box> mine;
+    for (size_t b = 0; b < boxes.size(); ++b)
+      if (box_solve[b] == s) mine.push_back(boxes[b]);
+    if (mine.empty()) SETERR(c, GMG_ERR_BAD_INPUT, "problem " + std::to_string(s) + " has no boxes");
+    std::string e = validate_boxes(mine, c->geoms[s].domain, true);
+    if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, (ns > 1 ? "problem " + std::to_string(s) + ": " : std::string()) + e);
+  }
+  reset_problem(c);
   LevelMeta L0;
   L0.boxes = boxes;
-  L0.box_solve.assign(boxes.size(), 0);
-  L0.geoms = {c->geom0};
-  L0.solve_present = {1};
-  L0.solve_bottom = {0};
+  L0.box_solve = box_solve;
+  L0.geoms = c->geoms;
+  L0.solve_present.assign(ns, 1);
+  L0.solve_bottom.assign(ns, 0);
   c->L.push_back(L0);
   for (int m = 0; m < 64; ++m) {
     LevelMeta C;
     bool more = make_coarse(c->L[m], C);
-    e = finalize_level(c->L[m]);
+    std::string e = finalize_level(c->L[m]);
     if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, e);
     if (!more) break;
     c->L.push_back(C);
@@ -332,19 +371,12 @@ gmg_status build_coefs(gmg_ctx* c) {
   // singular flag of the bottom problems
   for (int m = 0; m < nlev(c); ++m) {
     LevelMeta& M = c->L[m];
-    for (auto& d : M.bot_descs) d.singular = singular(c) ? 1 : 0;
+    for (auto& d : M.bot_descs) d.singular = singular(c, d.solve) ? 1 : 0;
     gmg_status st = upload(c, c->dev[m].bot_descs, M.bot_descs);
     if (st) return st;
   }
   CK(c, cudaGetLastError());
   c->coefs_dirty = false;
-  return GMG_OK;
-}
-
-// Fill coefficient buffers' ghost-free regions: face arrays need their high faces and the
-// diagonal its valid cells; fields are zeroed once so that untouched padding is finite.
-gmg_status zero_workspace(gmg_ctx* c) {
-  CK(c, cudaMemsetAsync(c->ws, 0, c->ws_bytes, c->stream));
   return GMG_OK;
 }
 
@@ -373,7 +405,9 @@ void smooth_sweeps(gmg_ctx* c, int dt, int m, int nsweep, cudaStream_t s) {
   }
 }
 
-// V-cycle on the correction equation of level m: e_m = V(r_m), e_m zeroed first.
+// V-cycle on the correction equation of level m: e_m = V(r_m), e_m zeroed first.  Problems
+// whose bottom is this level are solved here by BiCGStab; the others smooth, restrict,
+// recurse, interpolate and smooth again.
 void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
   const LevelDev& D = c->dev[m];
   const LevelBufs& B = c->buf[m];
@@ -391,18 +425,20 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
   smooth_sweeps(c, dt, m, p.nu2, s);
 }
 
-// One outer iteration: e = V(r); phi += e; r = rhs - A phi with ||r||_inf into normbits[0].
+// One outer iteration: e = V(r); phi += e; r = rhs - A phi with per-problem ||r||_inf into
+// normbits[0, ns), copied to the pinned host mirror.
 void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const gmg_params& p, cudaStream_t s) {
+  const int ns = c->ns();
   vcycle(c, dt, 0, p, s);
   launch_add_correction(dt, c->dev[0], phi, c->buf[0].e[dt], s);
   launch_fill(DT_F64, c->dev[0], phi, -1, 0, s);
-  cudaMemsetAsync(c->normbits, 0, 8, s);
+  cudaMemsetAsync(c->normbits, 0, 8 * (size_t)ns, s);
   cudaEvent_t* ev = c->profiling ? ev_pair(c->ev_resid, c->n_ev_resid++) : nullptr;
   if (ev) record_timing_event(c, ev[0], s);
   launch_residual(DT_F64, dt, c->dev[0], phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits,
-                  singular(c) ? c->scal : nullptr, s);
+                  any_singular(c) ? c->scal : nullptr, s);
   if (ev) record_timing_event(c, ev[1], s);
-  cudaMemcpyAsync(c->h_bits, c->normbits, 8, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(c->h_bits, c->normbits, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s);
 }
 
 // summed elapsed time (ms) of the first n event pairs of a list
@@ -429,6 +465,231 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
     SETERR(c, GMG_ERR_BAD_INPUT, "invalid parameters");
   if (p.precision < GMG_FP64 || p.precision > GMG_MIXED_BF16) SETERR(c, GMG_ERR_BAD_INPUT, "invalid precision");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
+  return GMG_OK;
+}
+
+// the level's cell work list restricted to one problem's boxes
+LevelDev solve_view(const gmg_ctx* c, int m, int s) {
+  LevelDev D = c->dev[m];
+  const LevelMeta& M = c->L[m];
+  D.cell_chunks += M.solve_chunk_range[s];
+  D.n_cell_chunks = M.solve_chunk_range[s + 1] - M.solve_chunk_range[s];
+  return D;
+}
+
+// Solve every problem of the context from phi = 0; infos[s] per problem (may be null).
+gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel, double tol_abs, const gmg_params& p,
+                      gmg_solve_info* infos) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int ns = c->ns();
+  const int dt = dt_of_precision(p.precision);
+  cudaStream_t s = c->stream;
+  const LevelDev& D0 = c->dev[0];
+  const int64_t ne0 = c->L[0].nelem;
+  const bool sing = any_singular(c);
+  if (infos) memset(infos, 0, sizeof(gmg_solve_info) * (size_t)ns);
+  const int64_t l_pro = kernel_launch_count();
+  // ||rhs||_inf per problem and, for singular problems, mean(rhs)
+  CK(c, cudaMemsetAsync(c->normbits, 0, 8 * (size_t)(2 * ns), s));
+  launch_norm_max(D0, rhs, c->normbits + ns, s);
+  if (sing) launch_sum(D0, rhs, c->partials, c->scal, s);
+  CK(c, cudaMemcpyAsync(c->h_bits + ns, c->normbits + ns, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  std::vector<double> rhsnorm(ns), target(ns);
+  for (int q = 0; q < ns; ++q) {
+    rhsnorm[q] = bits_to_double(c->h_bits[ns + q]);
+    if (!std::isfinite(rhsnorm[q])) SETERR(c, GMG_ERR_BAD_INPUT, "rhs of problem " + std::to_string(q) + " is not finite");
+    if (sing && singular(c, q)) {
+      const double mean = c->h_scal[q];
+      if (std::fabs(mean) > 1e-12 * rhsnorm[q] && !p.project_mean) {
+        if (infos) infos[q].status = GMG_ERR_BAD_INPUT;
+        SETERR(c, GMG_ERR_BAD_INPUT, "singular problem with a nonzero-mean rhs (set project_mean)");
+      }
+    } else {
+      c->h_scal[q] = 0.0;  // no shift for nonsingular problems
+    }
+    target[q] = std::max(tol_rel * rhsnorm[q], tol_abs);
+  }
+  if (sing) CK(c, cudaMemcpyAsync(c->scal, c->h_scal, 8 * (size_t)ns, cudaMemcpyHostToDevice, s));
+  // phi = 0; r = (rhs - mean) - A 0
+  CK(c, cudaMemsetAsync(phi, 0, 8 * (size_t)ne0, s));
+  CK(c, cudaMemsetAsync(c->normbits, 0, 8 * (size_t)ns, s));
+  launch_residual(DT_F64, dt, D0, phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits, sing ? c->scal : nullptr, s);
+  CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  std::vector<std::vector<double>> hist(ns);
+  std::vector<int> its(ns, 0), status(ns, GMG_OK);
+  std::vector<char> live(ns, 0);
+  int nlive = 0;
+  for (int q = 0; q < ns; ++q) {
+    const double rn = bits_to_double(c->h_bits[q]);
+    hist[q].push_back(rn);
+    live[q] = !(rn <= target[q]);
+    if (live[q] && p.max_iter == 0) {
+      status[q] = GMG_ERR_NOT_CONVERGED;
+      live[q] = 0;
+    }
+    nlive += live[q];
+    c->h_active[q] = live[q];
+  }
+  if (ns > 1) CK(c, cudaMemcpyAsync(c->active, c->h_active, 4 * (size_t)ns, cudaMemcpyHostToDevice, s));
+  const int64_t prologue_launches = kernel_launch_count() - l_pro;
+
+  cudaGraphExec_t gexec = nullptr;
+  int64_t per_iter = 0;
+  c->profiling = p.profile != 0;
+  if (c->profiling) {  // events are created outside any capture
+    ev_pair(c->ev_smooth, 2 * (p.nu1 + p.nu2) - 1);
+    ev_pair(c->ev_resid, 0);
+  }
+  double sm_ms = 0.0, rs_ms = 0.0;
+  int sm_n = 0, rs_n = 0;
+  if (p.use_graph && nlive) {
+    auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
+                               p.bottom_tol, p.profile);
+    auto itg = c->graphs.find(key);
+    if (itg != c->graphs.end()) {
+      gexec = itg->second.first;
+      per_iter = itg->second.second;
+      c->n_ev_smooth = 2 * (p.nu1 + p.nu2);
+      c->n_ev_resid = 1;
+    } else {
+      cudaGraph_t g;
+      const int64_t l0 = kernel_launch_count();
+      c->n_ev_smooth = c->n_ev_resid = 0;
+      CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      outer_iteration(c, dt, phi, rhs, p, c->cap_stream);
+      cudaError_t e1 = cudaStreamEndCapture(c->cap_stream, &g);
+      if (e1 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+      cudaError_t e2 = cudaGraphInstantiate(&gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+      per_iter = kernel_launch_count() - l0;
+      count_launches((int)-per_iter);  // captured, not launched
+      c->graphs[key] = {gexec, per_iter};
+    }
+  }
+  int64_t launched = 0;
+  while (nlive) {
+    if (gexec) {
+      CK(c, cudaGraphLaunch(gexec, s));
+      launched += per_iter;
+    } else {
+      const int64_t l0 = kernel_launch_count();
+      c->n_ev_smooth = c->n_ev_resid = 0;
+      outer_iteration(c, dt, phi, rhs, p, s);
+      launched += kernel_launch_count() - l0;
+    }
+    CK(c, cudaStreamSynchronize(s));
+    CK(c, cudaGetLastError());
+    if (c->profiling) {
+      sm_ms += pair_ms(c->ev_smooth, c->n_ev_smooth);
+      sm_n += c->n_ev_smooth;
+      rs_ms += pair_ms(c->ev_resid, c->n_ev_resid);
+      rs_n += c->n_ev_resid;
+    }
+    bool changed = false;
+    for (int q = 0; q < ns; ++q) {
+      if (!live[q]) continue;
+      const double rn = bits_to_double(c->h_bits[q]);
+      ++its[q];
+      hist[q].push_back(rn);
+      if (!std::isfinite(rn)) status[q] = GMG_ERR_DIVERGED;
+      else if (rn <= target[q]) status[q] = GMG_OK;
+      else if (its[q] >= p.max_iter) status[q] = GMG_ERR_NOT_CONVERGED;
+      else continue;
+      live[q] = 0;
+      c->h_active[q] = 0;
+      --nlive;
+      changed = true;
+    }
+    if (changed && nlive && ns > 1)
+      CK(c, cudaMemcpyAsync(c->active, c->h_active, 4 * (size_t)ns, cudaMemcpyHostToDevice, s));
+  }
+  c->profiling = false;
+  const int64_t l_epi = kernel_launch_count();
+  // every problem active again for later calls
+  if (ns > 1) {
+    for (int q = 0; q < ns; ++q) c->h_active[q] = 1;
+    CK(c, cudaMemcpyAsync(c->active, c->h_active, 4 * (size_t)ns, cudaMemcpyHostToDevice, s));
+  }
+  if (sing) {  // singular problems: phi -= mean(phi); the others keep a zero shift
+    launch_sum(D0, phi, c->partials, c->scal + ns, s);
+    for (int q = 0; q < ns; ++q)
+      if (!singular(c, q)) CK(c, cudaMemsetAsync(c->scal + ns + q, 0, 8, s));
+    launch_add_scalar(D0, phi, c->scal + ns, -1.0, s);
+    CK(c, cudaGetLastError());
+  }
+  CK(c, cudaMemcpyAsync(c->h_iters, c->bot_iters, 4 * (size_t)ns, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  gmg_status worst = GMG_OK;
+  for (int q = 0; q < ns; ++q)
+    if (status[q] != GMG_OK && (worst == GMG_OK || status[q] == GMG_ERR_DIVERGED)) worst = (gmg_status)status[q];
+  if (infos) {
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const int64_t tot = launched + prologue_launches + (kernel_launch_count() - l_epi);
+    for (int q = 0; q < ns; ++q) {
+      gmg_solve_info& I = infos[q];
+      I.iterations = its[q];
+      I.status = status[q];
+      I.rhs_norm = rhsnorm[q];
+      I.initial_resid = hist[q][0];
+      I.final_resid = hist[q].back();
+      I.hist_len = (int)std::min<size_t>(hist[q].size(), 256);
+      for (int i = 0; i < I.hist_len; ++i) I.resid_hist[i] = hist[q][i];
+      I.bottom_iters = c->h_iters[q];
+      I.solve_ms = ms;
+      I.kernel_launches = tot;
+      I.smooth0_ms = sm_ms;
+      I.smooth0_launches = sm_n;
+      I.resid0_ms = rs_ms;
+      I.resid0_launches = rs_n;
+    }
+  }
+  if (worst == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
+  if (worst == GMG_ERR_DIVERGED) c->err = "residual is not finite";
+  return worst;
+}
+
+gmg_status ensure_pinned(gmg_ctx* c) {
+  const size_t need = (size_t)std::max(1, c->ns()) * 3 + 16;
+  if (c->h_cap >= need) return GMG_OK;
+  if (c->h_bits) cudaFreeHost(c->h_bits);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->h_iters) cudaFreeHost(c->h_iters);
+  if (c->h_active) cudaFreeHost(c->h_active);
+  c->h_bits = nullptr;
+  c->h_scal = nullptr;
+  c->h_iters = nullptr;
+  c->h_active = nullptr;
+  c->h_cap = 0;
+  CK(c, cudaHostAlloc((void**)&c->h_bits, need * sizeof(unsigned long long), cudaHostAllocDefault));
+  CK(c, cudaHostAlloc((void**)&c->h_scal, need * sizeof(double), cudaHostAllocDefault));
+  CK(c, cudaHostAlloc((void**)&c->h_iters, need * sizeof(int), cudaHostAllocDefault));
+  CK(c, cudaHostAlloc((void**)&c->h_active, need * sizeof(int), cudaHostAllocDefault));
+  c->h_cap = need;
+  return GMG_OK;
+}
+
+gmg_status set_domain_geom(gmg_ctx* c, SolveGeom& G, const int lo[3], const int hi[3], const double plo[3],
+                           const double phi[3], const int bclo[3], const int bchi[3]) {
+  for (int d = 0; d < 3; ++d) {
+    if (hi[d] < lo[d]) SETERR(c, GMG_ERR_BAD_INPUT, "empty domain");
+    if (!(phi[d] > plo[d])) SETERR(c, GMG_ERR_BAD_INPUT, "prob_hi must exceed prob_lo");
+    if ((bclo[d] != GMG_BC_PERIODIC && bclo[d] != GMG_BC_DIRICHLET0) ||
+        (bchi[d] != GMG_BC_PERIODIC && bchi[d] != GMG_BC_DIRICHLET0))
+      SETERR(c, GMG_ERR_BAD_INPUT, "unknown boundary condition");
+    if ((bclo[d] == GMG_BC_PERIODIC) != (bchi[d] == GMG_BC_PERIODIC))
+      SETERR(c, GMG_ERR_BAD_INPUT, "a periodic direction must be periodic on both sides");
+    G.domain.lo[d] = lo[d];
+    G.domain.hi[d] = hi[d];
+    G.bclo[d] = bclo[d];
+    G.bchi[d] = bchi[d];
+    G.h[d] = (phi[d] - plo[d]) / (double)(hi[d] - lo[d] + 1);
+  }
   return GMG_OK;
 }
 
@@ -464,10 +725,13 @@ gmg_status gmg_create(gmg_ctx** out, void* stream) {
 gmg_status gmg_destroy(gmg_ctx* c) {
   if (!c) return GMG_OK;
   drop_graphs(c);
+  for (cudaEvent_t e : c->ev_smooth) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_resid) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->h_bits) cudaFreeHost(c->h_bits);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_iters) cudaFreeHost(c->h_iters);
+  if (c->h_active) cudaFreeHost(c->h_active);
   delete c;
   return GMG_OK;
 }
@@ -478,27 +742,11 @@ gmg_status gmg_define_domain(gmg_ctx* c, const int lo[3], const int hi[3], const
                              const int bclo[3], const int bchi[3]) {
   if (!c || !lo || !hi || !plo || !phi || !bclo || !bchi) return GMG_ERR_BAD_INPUT;
   SolveGeom G;
-  for (int d = 0; d < 3; ++d) {
-    if (hi[d] < lo[d]) SETERR(c, GMG_ERR_BAD_INPUT, "empty domain");
-    if (!(phi[d] > plo[d])) SETERR(c, GMG_ERR_BAD_INPUT, "prob_hi must exceed prob_lo");
-    if ((bclo[d] != GMG_BC_PERIODIC && bclo[d] != GMG_BC_DIRICHLET0) ||
-        (bchi[d] != GMG_BC_PERIODIC && bchi[d] != GMG_BC_DIRICHLET0))
-      SETERR(c, GMG_ERR_BAD_INPUT, "unknown boundary condition");
-    if ((bclo[d] == GMG_BC_PERIODIC) != (bchi[d] == GMG_BC_PERIODIC))
-      SETERR(c, GMG_ERR_BAD_INPUT, "a periodic direction must be periodic on both sides");
-    G.domain.lo[d] = lo[d];
-    G.domain.hi[d] = hi[d];
-    G.bclo[d] = bclo[d];
-    G.bchi[d] = bchi[d];
-    G.h[d] = (phi[d] - plo[d]) / (double)(hi[d] - lo[d] + 1);
-    c->prob_lo[d] = plo[d];
-    c->prob_hi[d] = phi[d];
-  }
-  c->geom0 = G;
+  gmg_status st = set_domain_geom(c, G, lo, hi, plo, phi, bclo, bchi);
+  if (st) return st;
+  reset_problem(c);
+  c->geoms = {G};
   c->have_domain = true;
-  c->L.clear();
-  c->ws = nullptr;
-  drop_graphs(c);
   c->err.clear();
   return GMG_OK;
 }
@@ -506,7 +754,7 @@ gmg_status gmg_define_domain(gmg_ctx* c, const int lo[3], const int hi[3], const
 gmg_status gmg_define_level(gmg_ctx* c, int lev, int nboxes, const int* lohi, int ref_ratio) {
   (void)ref_ratio;
   if (!c) return GMG_ERR_BAD_INPUT;
-  if (!c->have_domain) SETERR(c, GMG_ERR_STATE, "define the domain first");
+  if (!c->have_domain || c->ns() != 1) SETERR(c, GMG_ERR_STATE, "define one domain first (gmg_define_domain)");
   if (lev != 0) SETERR(c, GMG_ERR_BAD_INPUT, "only AMR level 0 is supported by gmg_define_level");
   if (nboxes <= 0 || !lohi) SETERR(c, GMG_ERR_BAD_INPUT, "no boxes");
   std::vector<Box> boxes(nboxes);
@@ -515,15 +763,66 @@ gmg_status gmg_define_level(gmg_ctx* c, int lev, int nboxes, const int* lohi, in
       boxes[b].lo[d] = lohi[6 * b + d];
       boxes[b].hi[d] = lohi[6 * b + 3 + d];
     }
-  return build_hierarchy(c, boxes);
+  return build_hierarchy(c, boxes, std::vector<int>(boxes.size(), 0));
 }
 
 gmg_status gmg_chop_domain(gmg_ctx* c, int lev, int mgs) {
   if (!c) return GMG_ERR_BAD_INPUT;
-  if (!c->have_domain) SETERR(c, GMG_ERR_STATE, "define the domain first");
+  if (!c->have_domain || c->ns() != 1) SETERR(c, GMG_ERR_STATE, "define one domain first (gmg_define_domain)");
   if (lev != 0) SETERR(c, GMG_ERR_BAD_INPUT, "only AMR level 0 is supported by gmg_chop_domain");
   if (mgs < 1) SETERR(c, GMG_ERR_BAD_INPUT, "max_grid_size must be positive");
-  return build_hierarchy(c, chop(c->geom0.domain, mgs));
+  std::vector<Box> boxes = chop(c->geoms[0].domain, mgs);
+  return build_hierarchy(c, boxes, std::vector<int>(boxes.size(), 0));
+}
+
+gmg_status gmg_define_batch(gmg_ctx* c, int n, const int* dom_lohi, const double* prob_lo, const double* prob_hi,
+                            const int* bc_lo, const int* bc_hi, const int* nboxes, const int* box_lohi) {
+  if (!c || n < 1 || !dom_lohi || !prob_lo || !prob_hi || !bc_lo || !bc_hi || !nboxes || !box_lohi)
+    return GMG_ERR_BAD_INPUT;
+  std::vector<SolveGeom> geoms(n);
+  std::vector<Box> boxes;
+  std::vector<int> owner;
+  int64_t k = 0;
+  for (int s = 0; s < n; ++s) {
+    gmg_status st = set_domain_geom(c, geoms[s], dom_lohi + 6 * s, dom_lohi + 6 * s + 3, prob_lo + 3 * s,
+                                    prob_hi + 3 * s, bc_lo + 3 * s, bc_hi + 3 * s);
+    if (st) return st;
+    if (nboxes[s] < 1) SETERR(c, GMG_ERR_BAD_INPUT, "every problem needs at least one box");
+    for (int b = 0; b < nboxes[s]; ++b, ++k) {
+      Box B;
+      for (int d = 0; d < 3; ++d) {
+        B.lo[d] = box_lohi[6 * k + d];
+        B.hi[d] = box_lohi[6 * k + 3 + d];
+      }
+      boxes.push_back(B);
+      owner.push_back(s);
+    }
+  }
+  reset_problem(c);
+  c->geoms = geoms;
+  c->have_domain = true;
+  c->err.clear();
+  return build_hierarchy(c, boxes, owner);
+}
+
+gmg_status gmg_num_solves(const gmg_ctx* c, int* n) {
+  if (!c || !n) return GMG_ERR_BAD_INPUT;
+  *n = c->ns();
+  return GMG_OK;
+}
+
+gmg_status gmg_solve_boxes(const gmg_ctx* c, int m, int solve, int* first, int* count) {
+  if (!c || m < 0 || m >= (int)c->L.size() || solve < 0 || solve >= c->ns()) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = c->L[m];
+  int f = -1, n = 0;
+  for (int b = 0; b < (int)M.boxes.size(); ++b)
+    if (M.box_solve[b] == solve) {
+      if (f < 0) f = b;
+      ++n;
+    }
+  if (first) *first = f;
+  if (count) *count = n;
+  return GMG_OK;
 }
 
 gmg_status gmg_mg_nlevels(const gmg_ctx* c, int* n) {
@@ -574,26 +873,38 @@ gmg_status gmg_layout(const gmg_ctx* c, int lev, int64_t* nelems, int64_t* offs)
   return gmg_mg_layout(c, 0, DT_F64, nelems, offs, nullptr);
 }
 
-gmg_status gmg_pack(gmg_ctx* c, int m, int dt, const double* dense, void* boxed) {
+gmg_status gmg_pack_solve(gmg_ctx* c, int m, int dt, int solve, const double* dense, void* boxed) {
   if (!c) return GMG_ERR_BAD_INPUT;
   gmg_status st = check_level(c, m, dt);
   if (st) return st;
-  const SolveGeom& G = c->L[m].geoms[0];
+  if (solve < 0 || solve >= c->ns()) SETERR(c, GMG_ERR_BAD_INPUT, "problem index out of range");
+  if (!c->L[m].solve_present[solve]) SETERR(c, GMG_ERR_BAD_INPUT, "problem has no boxes on this MG level");
+  const SolveGeom& G = c->L[m].geoms[solve];
   int dn[3] = {G.domain.n(0), G.domain.n(1), G.domain.n(2)};
-  launch_pack(dt, c->dev[m], G.domain.lo, dn, dense, boxed, c->stream);
+  launch_pack(dt, solve_view(c, m, solve), G.domain.lo, dn, dense, boxed, c->stream);
   CK(c, cudaGetLastError());
   return GMG_OK;
 }
 
-gmg_status gmg_unpack(gmg_ctx* c, int m, int dt, const void* boxed, double* dense) {
+gmg_status gmg_unpack_solve(gmg_ctx* c, int m, int dt, int solve, const void* boxed, double* dense) {
   if (!c) return GMG_ERR_BAD_INPUT;
   gmg_status st = check_level(c, m, dt);
   if (st) return st;
-  const SolveGeom& G = c->L[m].geoms[0];
+  if (solve < 0 || solve >= c->ns()) SETERR(c, GMG_ERR_BAD_INPUT, "problem index out of range");
+  if (!c->L[m].solve_present[solve]) SETERR(c, GMG_ERR_BAD_INPUT, "problem has no boxes on this MG level");
+  const SolveGeom& G = c->L[m].geoms[solve];
   int dn[3] = {G.domain.n(0), G.domain.n(1), G.domain.n(2)};
-  launch_unpack(dt, c->dev[m], G.domain.lo, dn, boxed, dense, c->stream);
+  launch_unpack(dt, solve_view(c, m, solve), G.domain.lo, dn, boxed, dense, c->stream);
   CK(c, cudaGetLastError());
   return GMG_OK;
+}
+
+gmg_status gmg_pack(gmg_ctx* c, int m, int dt, const double* dense, void* boxed) {
+  return gmg_pack_solve(c, m, dt, 0, dense, boxed);
+}
+
+gmg_status gmg_unpack(gmg_ctx* c, int m, int dt, const void* boxed, double* dense) {
+  return gmg_unpack_solve(c, m, dt, 0, boxed, dense);
 }
 
 gmg_status gmg_set_scalars(gmg_ctx* c, double a, double b) {
@@ -651,7 +962,6 @@ gmg_status gmg_get_coeffs(gmg_ctx* c, int m, int dt, void* wx, void* wy, void* w
   gmg_status st = check_level(c, m, dt);
   if (st) return st;
   if ((st = build_coefs(c))) return st;
-  const LevelBufs& B = c->buf[m];
   const int64_t n = c->L[m].nelem;
   const int src = (dt == DT_F64) ? DT_F64 : DT_F32;
   const Coefs k = coefs_of(c, m, src);
@@ -659,7 +969,6 @@ gmg_status gmg_get_coeffs(gmg_ctx* c, int m, int dt, void* wx, void* wy, void* w
   if (wy) launch_convert(src, dt, k.wy, wy, n, c->stream);
   if (wz) launch_convert(src, dt, k.wz, wz, n, c->stream);
   if (diag) launch_convert(src, dt, k.D, diag, n, c->stream);
-  (void)B;
   CK(c, cudaGetLastError());
   return GMG_OK;
 }
@@ -685,15 +994,13 @@ gmg_status gmg_set_workspace(gmg_ctx* c, void* dptr, size_t bytes) {
   else SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace too small");
   drop_graphs(c);
   if (!c->cap_stream) CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-  if (!c->h_bits) CK(c, cudaHostAlloc((void**)&c->h_bits, 64 * sizeof(unsigned long long), cudaHostAllocDefault));
-  if (!c->h_scal) CK(c, cudaHostAlloc((void**)&c->h_scal, 64 * sizeof(double), cudaHostAllocDefault));
-  if (!c->h_iters) CK(c, cudaHostAlloc((void**)&c->h_iters, 4096 * sizeof(int), cudaHostAllocDefault));
+  gmg_status st = ensure_pinned(c);
+  if (st) return st;
   c->ws = dptr;
   c->ws_bytes = bytes;
   c->mixed = mixed;
   carve(c, dptr, mixed, true);
-  gmg_status st = zero_workspace(c);
-  if (st) return st;
+  CK(c, cudaMemsetAsync(c->ws, 0, c->ws_bytes, c->stream));
   st = upload_tables(c);
   if (st) return st;
   c->have_beta = c->have_alpha = false;
@@ -717,13 +1024,10 @@ gmg_status gmg_smooth(gmg_ctx* c, int m, int dt, void* phi, const void* rhs, int
   if (st) return st;
   if (colour < 0 || colour > 1) SETERR(c, GMG_ERR_BAD_INPUT, "colour must be 0 or 1");
   if ((st = build_coefs(c))) return st;
-  // the smoother's work list skips bottom boxes; for a test of the bottom level smooth
-  // over every box
+  // the smoother's work list skips bottom boxes; a single step smooths every box
   LevelDev D = c->dev[m];
-  if (D.n_pair_chunks == 0) {
-    D.pair_chunks = D.pair_all_chunks;
-    D.n_pair_chunks = D.n_pair_all_chunks;
-  }
+  D.pair_chunks = D.pair_all_chunks;
+  D.n_pair_chunks = D.n_pair_all_chunks;
   launch_fill(dt, D, phi, 1 - colour, 0, c->stream);
   launch_smooth(dt, D, phi, rhs, coefs_of(c, m, dt), colour, c->stream);
   CK(c, cudaGetLastError());
@@ -738,15 +1042,18 @@ gmg_status gmg_residual(gmg_ctx* c, int m, int dt, void* phi, const void* rhs, i
   if (dt != DT_F64 && rdt == DT_F64) SETERR(c, GMG_ERR_BAD_INPUT, "a float residual pass cannot write double");
   if ((st = build_coefs(c))) return st;
   cudaStream_t s = c->stream;
+  const int ns = c->ns();
   launch_fill(dt, c->dev[m], phi, -1, 0, s);
-  unsigned long long* nb = c->normbits + 1;
-  CK(c, cudaMemsetAsync(nb, 0, 8, s));
+  unsigned long long* nb = c->normbits + ns;  // per-problem slots; the maximum is taken here
+  CK(c, cudaMemsetAsync(nb, 0, 8 * (size_t)ns, s));
   launch_residual(dt, rdt, c->dev[m], phi, rhs, coefs_of(c, m, dt), r, norm ? nb : nullptr, nullptr, s);
   CK(c, cudaGetLastError());
   if (norm) {
-    CK(c, cudaMemcpyAsync(c->h_bits + 1, nb, 8, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaMemcpyAsync(c->h_bits + ns, nb, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s));
     CK(c, cudaStreamSynchronize(s));
-    *norm = bits_to_double(c->h_bits[1]);
+    double v = 0.0;
+    for (int q = 0; q < ns; ++q) v = std::max(v, bits_to_double(c->h_bits[ns + q]));
+    *norm = v;
   }
   return GMG_OK;
 }
@@ -779,6 +1086,7 @@ gmg_status gmg_bottom_solve(gmg_ctx* c, int dt, const void* rhs, void* x, const 
   gmg_status st = check_level(c, 0, dt);
   if (st) return st;
   if ((st = build_coefs(c))) return st;
+  if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "gmg_bottom_solve needs a single-problem context");
   const int m = nlev(c) - 1;
   BottomArgs a{p.bottom_max_iter, p.bottom_tol, c->buf[m].bot_work, c->bot_iters};
   launch_bottom(dt, c->dev[m], rhs, x, coefs64(c, m), a, c->stream);
@@ -824,8 +1132,21 @@ gmg_status gmg_apply(gmg_ctx* c, void* const* out, void* const* phi) {
 
 gmg_status gmg_solve(gmg_ctx* c, void* const* phiv, const void* const* rhsv, double tol_rel, double tol_abs,
                      const gmg_params* pp, gmg_solve_info* info) {
-  const auto t0 = std::chrono::steady_clock::now();
   if (!c || !phiv || !rhsv || !phiv[0] || !rhsv[0]) return GMG_ERR_BAD_INPUT;
+  gmg_params p;
+  gmg_default_params(&p);
+  if (pp) p = *pp;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "context holds several problems: use gmg_batch_solve");
+  if ((st = params_ok(c, p))) return st;
+  if ((st = build_coefs(c))) return st;
+  return solve_impl(c, (double*)phiv[0], (const double*)rhsv[0], tol_rel, tol_abs, p, info);
+}
+
+gmg_status gmg_batch_solve(gmg_ctx* c, void* phi, const void* rhs, double tol_rel, double tol_abs,
+                           const gmg_params* pp, gmg_solve_info* infos) {
+  if (!c || !phi || !rhs) return GMG_ERR_BAD_INPUT;
   gmg_params p;
   gmg_default_params(&p);
   if (pp) p = *pp;
@@ -833,141 +1154,7 @@ gmg_status gmg_solve(gmg_ctx* c, void* const* phiv, const void* const* rhsv, dou
   if (st) return st;
   if ((st = params_ok(c, p))) return st;
   if ((st = build_coefs(c))) return st;
-  double* phi = (double*)phiv[0];
-  const double* rhs = (const double*)rhsv[0];
-  const int dt = dt_of_precision(p.precision);
-  cudaStream_t s = c->stream;
-  const LevelDev& D0 = c->dev[0];
-  const int64_t ne0 = c->L[0].nelem;
-  const bool sing = singular(c);
-  if (info) {
-    memset(info, 0, sizeof(*info));
-  }
-  const int64_t l_pro = kernel_launch_count();
-  // ||rhs||_inf and, for a singular problem, mean(rhs)
-  CK(c, cudaMemsetAsync(c->normbits, 0, 16, s));
-  launch_norm_max(D0, rhs, c->normbits + 1, s);
-  if (sing) launch_sum(D0, rhs, c->partials, c->scal, s);
-  CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 16, cudaMemcpyDeviceToHost, s));
-  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8, cudaMemcpyDeviceToHost, s));
-  CK(c, cudaStreamSynchronize(s));
-  CK(c, cudaGetLastError());
-  const double rhsnorm = bits_to_double(c->h_bits[1]);
-  if (!std::isfinite(rhsnorm)) SETERR(c, GMG_ERR_BAD_INPUT, "rhs is not finite");
-  if (sing) {
-    const double mean = c->h_scal[0] / (double)c->L[0].ncells;
-    c->h_scal[1] = mean;
-    if (std::fabs(mean) > 1e-12 * rhsnorm && !p.project_mean) {
-      if (info) info->status = GMG_ERR_BAD_INPUT;
-      SETERR(c, GMG_ERR_BAD_INPUT, "singular problem with a nonzero-mean rhs (set project_mean)");
-    }
-    CK(c, cudaMemcpyAsync(c->scal, c->h_scal + 1, 8, cudaMemcpyHostToDevice, s));
-  }
-  double target = tol_rel * rhsnorm;
-  if (tol_abs > target) target = tol_abs;
-  // phi = 0; r = (rhs - mean) - A 0
-  CK(c, cudaMemsetAsync(phi, 0, 8 * (size_t)ne0, s));
-  CK(c, cudaMemsetAsync(c->normbits, 0, 8, s));
-  launch_residual(DT_F64, dt, D0, phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits, sing ? c->scal : nullptr, s);
-  CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 8, cudaMemcpyDeviceToHost, s));
-  CK(c, cudaStreamSynchronize(s));
-  CK(c, cudaGetLastError());
-  double rn = bits_to_double(c->h_bits[0]);
-  std::vector<double> hist{rn};
-  const int64_t prologue_launches = kernel_launch_count() - l_pro;
-  int it = 0;
-  gmg_status result = GMG_OK;
-  cudaGraphExec_t gexec = nullptr;
-  int64_t per_iter = 0;
-  c->profiling = p.profile != 0;
-  if (c->profiling) {  // events are created outside any capture
-    ev_pair(c->ev_smooth, 2 * (p.nu1 + p.nu2) - 1);
-    ev_pair(c->ev_resid, 0);
-  }
-  double sm_ms = 0.0, rs_ms = 0.0;
-  int sm_n = 0, rs_n = 0;
-  if (p.use_graph) {
-    auto key = std::make_tuple(phiv[0], rhsv[0], p.precision, p.nu1, p.nu2, p.bottom_max_iter, p.bottom_tol,
-                               p.profile);
-    auto itg = c->graphs.find(key);
-    if (itg != c->graphs.end()) {
-      gexec = itg->second.first;
-      per_iter = itg->second.second;
-      c->n_ev_smooth = 2 * (p.nu1 + p.nu2);
-      c->n_ev_resid = 1;
-    } else {
-      cudaGraph_t g;
-      const int64_t l0 = kernel_launch_count();
-      c->n_ev_smooth = c->n_ev_resid = 0;
-      CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-      outer_iteration(c, dt, phi, rhs, p, c->cap_stream);
-      cudaError_t e1 = cudaStreamEndCapture(c->cap_stream, &g);
-      if (e1 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
-      cudaError_t e2 = cudaGraphInstantiate(&gexec, g, 0);
-      cudaGraphDestroy(g);
-      if (e2 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
-      per_iter = kernel_launch_count() - l0;
-      count_launches((int)-per_iter);  // captured, not launched
-      c->graphs[key] = {gexec, per_iter};
-    }
-  }
-  int64_t launched = 0;
-  while (!(rn <= target) && it < p.max_iter) {
-    if (gexec) {
-      CK(c, cudaGraphLaunch(gexec, s));
-      launched += per_iter;
-    } else {
-      const int64_t l0 = kernel_launch_count();
-      c->n_ev_smooth = c->n_ev_resid = 0;
-      outer_iteration(c, dt, phi, rhs, p, s);
-      launched += kernel_launch_count() - l0;
-    }
-    CK(c, cudaStreamSynchronize(s));
-    CK(c, cudaGetLastError());
-    if (c->profiling) {
-      sm_ms += pair_ms(c->ev_smooth, c->n_ev_smooth);
-      sm_n += c->n_ev_smooth;
-      rs_ms += pair_ms(c->ev_resid, c->n_ev_resid);
-      rs_n += c->n_ev_resid;
-    }
-    rn = bits_to_double(c->h_bits[0]);
-    ++it;
-    hist.push_back(rn);
-    if (!std::isfinite(rn)) {
-      result = GMG_ERR_DIVERGED;
-      break;
-    }
-  }
-  c->profiling = false;
-  if (result == GMG_OK && !(rn <= target)) result = GMG_ERR_NOT_CONVERGED;
-  const int64_t l_epi = kernel_launch_count();
-  if (sing) {
-    // phi -= mean(phi)
-    launch_sum(D0, phi, c->partials, c->scal + 1, s);
-    launch_add_scalar(D0, phi, c->scal + 1, -1.0 / (double)c->L[0].ncells, s);
-    CK(c, cudaGetLastError());
-  }
-  CK(c, cudaMemcpyAsync(c->h_iters, c->bot_iters, 4, cudaMemcpyDeviceToHost, s));
-  CK(c, cudaStreamSynchronize(s));
-  if (info) {
-    info->iterations = it;
-    info->status = result;
-    info->rhs_norm = rhsnorm;
-    info->initial_resid = hist[0];
-    info->final_resid = rn;
-    info->hist_len = (int)std::min<size_t>(hist.size(), 256);
-    for (int i = 0; i < info->hist_len; ++i) info->resid_hist[i] = hist[i];
-    info->bottom_iters = c->h_iters[0];
-    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    info->kernel_launches = launched + prologue_launches + (kernel_launch_count() - l_epi);
-    info->smooth0_ms = sm_ms;
-    info->smooth0_launches = sm_n;
-    info->resid0_ms = rs_ms;
-    info->resid0_launches = rs_n;
-  }
-  if (result == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
-  if (result == GMG_ERR_DIVERGED) c->err = "residual is not finite";
-  return result;
+  return solve_impl(c, (double*)phi, (const double*)rhs, tol_rel, tol_abs, p, infos);
 }
 
 }  // extern "C"

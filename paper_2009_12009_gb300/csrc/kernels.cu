@@ -77,11 +77,13 @@ __device__ __forceinline__ double block_sum(double v) {
 
 template <class T>
 __global__ void __launch_bounds__(BLOCK) k_fill(const DevBox* __restrict__ boxes, const GhostRect* __restrict__ rects,
-                                                const Chunk* __restrict__ chunks, T* f, int colour, int copy_mode) {
+                                                const Chunk* __restrict__ chunks, T* f, int colour, int copy_mode,
+                                                const int* __restrict__ active) {
   const Chunk ch = chunks[blockIdx.x];
   const GhostRect g = rects[ch.item];
   if (copy_mode && g.kind == 1) return;
   const DevBox Bd = boxes[g.dst_box];
+  if (active && !active[Bd.solve]) return;
   const DevBox Bs = boxes[g.src_box];
   const int64_t d0 = elem_index(Bd, g.dst[0], g.dst[1], g.dst[2]);
   const int64_t s0 = elem_index(Bs, g.src[0], g.src[1], g.src[2]);
@@ -118,10 +120,12 @@ __global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ box
                                                   const typename CoefOf<T>::type* __restrict__ wx,
                                                   const typename CoefOf<T>::type* __restrict__ wy,
                                                   const typename CoefOf<T>::type* __restrict__ wz,
-                                                  const typename CoefOf<T>::type* __restrict__ invD, int colour) {
+                                                  const typename CoefOf<T>::type* __restrict__ invD, int colour,
+                                                  const int* __restrict__ active) {
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
+  if (active && !active[B.solve]) return;
   const int t = ch.start + threadIdx.x;
   if (t >= ((B.nx + 1) >> 1) * B.ny * B.nz) return;
   int i, j, k;
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ b
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
   const int t = ch.start + threadIdx.x;
-  const A shift = shift_p ? (A)*shift_p : (A)0;
+  const A shift = shift_p ? (A)shift_p[B.solve] : (A)0;
   unsigned long long mx = 0;
   if (t < ((B.nx + 1) >> 1) * B.ny * B.nz) {
     int i0, j, k;
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ b
       mx = bb > mx ? bb : mx;
     }
   }
-  if (maxbits) block_max_atomic(mx, maxbits);
+  if (maxbits) block_max_atomic(mx, maxbits + B.solve);
 }
 
 // residual of the 8 children of one coarse cell, averaged into the coarse level
@@ -194,10 +198,11 @@ __global__ void __launch_bounds__(BLOCK)
                      const int* __restrict__ parent, const Chunk* __restrict__ chunks, const T* __restrict__ phi,
                      const T* __restrict__ rhs, const typename CoefOf<T>::type* __restrict__ wx,
                      const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
-                     const typename CoefOf<T>::type* __restrict__ D, R* rc) {
+                     const typename CoefOf<T>::type* __restrict__ D, R* rc, const int* __restrict__ active) {
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox F = fboxes[ch.item];
+  if (active && !active[F.solve]) return;
   const DevBox P = cboxes[parent[ch.item]];
   const int ncx = F.nx >> 1, ncy = F.ny >> 1, ncz = F.nz >> 1;
   const int t = ch.start + threadIdx.x;
@@ -244,10 +249,12 @@ __global__ void __launch_bounds__(BLOCK)
 template <class T>
 __global__ void __launch_bounds__(BLOCK)
     k_prolong_add(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes, const int* __restrict__ parent,
-                  const Chunk* __restrict__ chunks, const T* __restrict__ coarse, T* fine) {
+                  const Chunk* __restrict__ chunks, const T* __restrict__ coarse, T* fine,
+                  const int* __restrict__ active) {
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox F = fboxes[ch.item];
+  if (active && !active[F.solve]) return;
   const DevBox P = cboxes[parent[ch.item]];
   const int ncx = F.nx >> 1, ncy = F.ny >> 1, ncz = F.nz >> 1;
   const int t = ch.start + threadIdx.x;
@@ -270,9 +277,10 @@ __global__ void __launch_bounds__(BLOCK)
 template <class T>
 __global__ void __launch_bounds__(BLOCK) k_add_correction(const DevBox* __restrict__ boxes,
                                                           const Chunk* __restrict__ chunks, double* phi,
-                                                          const T* __restrict__ e) {
+                                                          const T* __restrict__ e, const int* __restrict__ active) {
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
+  if (active && !active[B.solve]) return;
   const int t = ch.start + threadIdx.x;
   if (t >= B.nx * B.ny * B.nz) return;
   const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
@@ -314,7 +322,7 @@ __global__ void __launch_bounds__(BLOCK) k_norm_max(const DevBox* __restrict__ b
     const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
     mx = abs_bits(x[elem_index(B, i, j, k)]);
   }
-  block_max_atomic(mx, maxbits);
+  block_max_atomic(mx, maxbits + B.solve);
 }
 
 __global__ void __launch_bounds__(BLOCK) k_sum_partial(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
@@ -331,12 +339,16 @@ __global__ void __launch_bounds__(BLOCK) k_sum_partial(const DevBox* __restrict_
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(BLOCK) k_sum_final(const double* __restrict__ partials, int n, double* out) {
-  // fixed order: thread t adds partials t, t + BLOCK, ...; then a fixed tree
+// block s reduces the partial sums of solve s's chunk range [range[s], range[s+1]) in a
+// fixed order and writes the mean (sum * inv_count[s])
+__global__ void __launch_bounds__(BLOCK) k_sum_final(const double* __restrict__ partials,
+                                                     const int* __restrict__ range,
+                                                     const double* __restrict__ inv_count, double* out) {
+  const int s = blockIdx.x;
   double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += BLOCK) v += partials[i];
-  const double s = block_sum(v);
-  if (threadIdx.x == 0) *out = s;
+  for (int i = range[s] + threadIdx.x; i < range[s + 1]; i += BLOCK) v += partials[i];
+  const double t = block_sum(v);
+  if (threadIdx.x == 0) out[s] = t * inv_count[s];
 }
 
 __global__ void __launch_bounds__(BLOCK) k_add_scalar(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
@@ -346,7 +358,7 @@ __global__ void __launch_bounds__(BLOCK) k_add_scalar(const DevBox* __restrict__
   const int t = ch.start + threadIdx.x;
   if (t >= B.nx * B.ny * B.nz) return;
   const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
-  x[elem_index(B, i, j, k)] += scale * *c;
+  x[elem_index(B, i, j, k)] += scale * c[B.solve];
 }
 
 __global__ void __launch_bounds__(BLOCK) k_scale_valid(const DevBox* __restrict__ boxes,
@@ -524,7 +536,7 @@ void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, 
   if (!L.n_ghost_chunks) return;
   ++g_launches;
   GMG_DISPATCH(dt, (k_fill<T><<<grid_of(L.n_ghost_chunks), BLOCK, 0, s>>>(L.boxes, L.ghosts, L.ghost_chunks,
-                                                                           (T*)f, colour, copy_mode)));
+                                                                           (T*)f, colour, copy_mode, L.active)));
 }
 
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour, cudaStream_t s) {
@@ -533,7 +545,7 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
   GMG_DISPATCH(dt, (k_smooth<T><<<grid_of(L.n_pair_chunks), BLOCK, 0, s>>>(
                        L.boxes, L.pair_chunks, (T*)phi, (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
                        (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
-                       (const typename CoefOf<T>::type*)c.invD, colour)));
+                       (const typename CoefOf<T>::type*)c.invD, colour, L.active)));
 }
 
 // residual work list: pair items over every box (the bottom level included)
@@ -562,7 +574,8 @@ void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const v
   GMG_DISPATCH(dt, (k_resid_restrict<T, T><<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(
                        f.boxes, c.boxes, f.parent, f.coarse_chunks, (const T*)phi, (const T*)rhs,
                        (const typename CoefOf<T>::type*)cf.wx, (const typename CoefOf<T>::type*)cf.wy,
-                       (const typename CoefOf<T>::type*)cf.wz, (const typename CoefOf<T>::type*)cf.D, (T*)rc)));
+                       (const typename CoefOf<T>::type*)cf.wz, (const typename CoefOf<T>::type*)cf.D, (T*)rc,
+                       f.active)));
 }
 
 void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s) {
@@ -578,14 +591,14 @@ void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void
   ++g_launches;
   GMG_DISPATCH(dt, (k_prolong_add<T><<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(f.boxes, c.boxes, f.parent,
                                                                                     f.coarse_chunks, (const T*)coarse,
-                                                                                    (T*)fine)));
+                                                                                    (T*)fine, f.active)));
 }
 
 void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s) {
   if (!L.n_cell_chunks) return;
   ++g_launches;
   GMG_DISPATCH(dt, (k_add_correction<T><<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, phi,
-                                                                                     (const T*)e)));
+                                                                                     (const T*)e, L.active)));
 }
 
 void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const double* dense, void* boxed,
@@ -617,7 +630,7 @@ void launch_sum(const LevelDev& L, const double* x, double* partials, double* ou
   ++g_launches;
   ++g_launches;
   k_sum_partial<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, x, partials);
-  k_sum_final<<<1, BLOCK, 0, s>>>(partials, L.n_cell_chunks, out);
+  k_sum_final<<<grid_of(L.nsolves), BLOCK, 0, s>>>(partials, L.solve_chunk_range, L.inv_count, out);
 }
 
 void launch_add_scalar(const LevelDev& L, double* x, const double* c, double scale, cudaStream_t s) {

@@ -35,6 +35,11 @@ struct LevelDev {
   const BotDesc* bot_descs = nullptr;
   int n_bot = 0;
   int64_t nelem = 0;
+  // per-solve data (batched form; one solve otherwise)
+  int nsolves = 1;
+  const int* active = nullptr;             // per solve: 0 = converged, its boxes are skipped; null = all
+  const int* solve_chunk_range = nullptr;  // cell_chunks of solve s are [range[s], range[s+1])
+  const double* inv_count = nullptr;       // per solve: 1 / number of cells on this level
 };
 
 // Coefficients of one level in one element type (double for FP64 fields, float for
@@ -54,8 +59,9 @@ void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, 
 // one red-black colour (no ghost fill)
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour,
                    cudaStream_t s);
-// r = (rhs - shift) - A phi on valid cells (ghosts of phi must be filled); rdt = type of r;
-// maxbits (may be null): atomic max of |r| as IEEE bits; shift (may be null): device scalar
+// r = (rhs - shift[solve]) - A phi on valid cells (ghosts of phi must be filled); rdt =
+// type of r; maxbits (may be null): per-solve atomic max of |r| as IEEE bits; shift (may be
+// null): per-solve device scalars
 void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const void* rhs, const Coefs& c,
                      void* r, unsigned long long* maxbits, const double* shift, cudaStream_t s);
 // coarse r = restriction of (rhs - A phi) (ghosts of phi filled)
@@ -71,12 +77,12 @@ void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], c
                  cudaStream_t s);
 void launch_unpack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const void* boxed, double* dense,
                    cudaStream_t s);
-// |x|_inf of a double field (atomic max into maxbits)
+// |x|_inf of a double field per solve (atomic max into maxbits[solve])
 void launch_norm_max(const LevelDev& L, const double* x, unsigned long long* maxbits, cudaStream_t s);
-// deterministic sum of valid cells of a double field: partial sums per block, then one
-// block adds them in order; result in *out (device)
+// deterministic per-solve mean of the valid cells of a double field: partial sums per
+// block, then one block per solve adds its partials in order; out[s] = mean of solve s
 void launch_sum(const LevelDev& L, const double* x, double* partials, double* out, cudaStream_t s);
-// x += c (device scalar, multiplied by `scale`) on valid cells
+// x += scale * c[solve] on valid cells
 void launch_add_scalar(const LevelDev& L, double* x, const double* c, double scale, cudaStream_t s);
 // x *= scale on valid cells
 void launch_scale_valid(const LevelDev& L, double* x, double scale, cudaStream_t s);

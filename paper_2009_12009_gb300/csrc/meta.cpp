@@ -209,6 +209,15 @@ std::string finalize_level(LevelMeta& L) {
     if (L.solve_bottom[L.box_solve[b]]) continue;
     for (int64_t s = 0; s < npair; s += BLOCK) L.pair_chunks.push_back({b, (int)s});
   }
+  // boxes are stored solve by solve, so each solve's cell chunks are contiguous
+  const int ns = (int)L.geoms.size();
+  L.solve_chunk_range.assign(ns + 1, 0);
+  std::vector<int64_t> cells(ns, 0);
+  for (const Chunk& ch : L.cell_chunks) L.solve_chunk_range[L.box_solve[ch.item] + 1]++;
+  for (int q = 0; q < ns; ++q) L.solve_chunk_range[q + 1] += L.solve_chunk_range[q];
+  for (int b = 0; b < nb; ++b) cells[L.box_solve[b]] += L.boxes[b].volume();
+  L.inv_count.assign(ns, 0.0);
+  for (int q = 0; q < ns; ++q) L.inv_count[q] = cells[q] ? 1.0 / (double)cells[q] : 0.0;
   L.coarse_chunks.clear();
   for (int b = 0; b < nb; ++b) {
     if (L.parent[b] < 0) continue;

@@ -56,6 +56,8 @@ struct LevelMeta {
   std::vector<BotCell> bot_cells;    // bottom problems on this level
   std::vector<BotGhost> bot_ghosts;
   std::vector<BotDesc> bot_descs;
+  std::vector<int> solve_chunk_range;  // cell_chunks of solve s: [range[s], range[s+1])
+  std::vector<double> inv_count;       // per solve: 1 / cells of the solve on this level (0 if absent)
 };
 
 // Checks that boxes are non-empty, inside the domain and pairwise disjoint; with

@@ -28,7 +28,8 @@ EXPORTS = [
     "gmg_pack", "gmg_unpack", "gmg_set_scalars", "gmg_set_acoef", "gmg_set_bcoef_cell", "gmg_set_bcoef_face",
     "gmg_get_coeffs", "gmg_workspace_size", "gmg_set_workspace", "gmg_solve", "gmg_apply", "gmg_fill_boundary",
     "gmg_smooth", "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_bottom_solve", "gmg_vcycle",
-    "gmg_box_bicgstab_noalloc",
+    "gmg_box_bicgstab_noalloc", "gmg_define_batch", "gmg_num_solves", "gmg_solve_boxes", "gmg_pack_solve",
+    "gmg_unpack_solve", "gmg_batch_solve",
 ]
 
 
@@ -106,6 +107,12 @@ def _declare(L):
         "gmg_vcycle": [vp, C.c_int, vp, vp, C.POINTER(Params)],
         "gmg_box_bicgstab_noalloc": [vp, C.c_int, C.c_int, C.c_int, i32p, i32p, C.c_int, vp, vp, vp, vp, vp, vp,
                                      C.c_int, C.c_double, vp],
+        "gmg_define_batch": [vp, C.c_int, i32p, f64p, f64p, i32p, i32p, i32p, i32p],
+        "gmg_num_solves": [vp, i32p],
+        "gmg_solve_boxes": [vp, C.c_int, C.c_int, i32p, i32p],
+        "gmg_pack_solve": [vp, C.c_int, C.c_int, C.c_int, vp, vp],
+        "gmg_unpack_solve": [vp, C.c_int, C.c_int, C.c_int, vp, vp],
+        "gmg_batch_solve": [vp, vp, vp, C.c_double, C.c_double, C.POINTER(Params), C.POINTER(SolveInfo)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -338,6 +345,75 @@ class Context:
         p = default_params(**params)
         self._check(self.L.gmg_vcycle(self.h, dt, _ptr(e), _ptr(r), C.byref(p)))
         return e
+
+
+class BatchContext(Context):
+    """Several independent problems solved together (one launch per step covers them all).
+
+    problems: list of dicts with keys domain ((lo), (hi)), boxes [(lo, hi), ...], bc_lo, bc_hi
+    and optional prob_lo / prob_hi."""
+
+    def __init__(self, problems, stream=None):
+        self.L = lib()
+        h = C.c_void_p()
+        self._check(self.L.gmg_create(C.byref(h), C.c_void_p(stream or 0)), None)
+        self.h = h
+        n = len(problems)
+        dom, plo, phi, bl, bh, nb, bx = [], [], [], [], [], [], []
+        for p in problems:
+            dom += list(p["domain"][0]) + list(p["domain"][1])
+            plo += list(p.get("prob_lo", (0.0, 0.0, 0.0)))
+            phi += list(p.get("prob_hi", (1.0, 1.0, 1.0)))
+            bl += list(p["bc_lo"])
+            bh += list(p["bc_hi"])
+            nb.append(len(p["boxes"]))
+            for b in p["boxes"]:
+                bx += list(b[0]) + list(b[1])
+        self._check(self.L.gmg_define_batch(self.h, n, _arr(dom, C.c_int), _arr(plo, C.c_double),
+                                            _arr(phi, C.c_double), _arr(bl, C.c_int), _arr(bh, C.c_int),
+                                            _arr(nb, C.c_int), _arr(bx, C.c_int)))
+        self.problems = problems
+        self.nsolves = n
+        self.workspace = None
+        self._keep = []
+
+    def solve_shape(self, s, m=0):
+        lo, hi = self.problems[s]["domain"]
+        f = 2 ** m
+        return tuple((hi[d] - lo[d] + 1) // f for d in (2, 1, 0))
+
+    def pack_solve(self, s, dense, out, m=0, dt=DT_F64):
+        import torch
+        dense = torch.as_tensor(dense, dtype=torch.float64, device="cuda").contiguous()
+        self._check(self.L.gmg_pack_solve(self.h, m, dt, s, _ptr(dense), _ptr(out)))
+        self._keep.append(dense)
+        return out
+
+    def unpack_solve(self, s, boxed, m=0, dt=DT_F64):
+        import torch
+        out = torch.zeros(self.solve_shape(s, m), dtype=torch.float64, device=boxed.device)
+        self._check(self.L.gmg_unpack_solve(self.h, m, dt, s, _ptr(boxed), _ptr(out)))
+        return out
+
+    def pack_all(self, dense_list, m=0, dt=DT_F64):
+        out = self.field(m, dt)
+        self._keep = []
+        for s, d in enumerate(dense_list):
+            self.pack_solve(s, d, out, m, dt)
+        return out
+
+    def set_beta_all(self, betas):
+        buf = self.pack_all(betas)
+        self._check(self.L.gmg_set_bcoef_cell(self.h, 0, _ptr(buf)))
+
+    def batch_solve(self, rhs, phi=None, tol_rel=1e-10, tol_abs=0.0, **params):
+        phi = self.field(0) if phi is None else phi
+        p = default_params(**params)
+        infos = (SolveInfo * self.nsolves)()
+        st = self.L.gmg_batch_solve(self.h, _ptr(phi), _ptr(rhs), tol_rel, tol_abs, C.byref(p), infos)
+        if st not in (OK, NOT_CONVERGED):
+            self._check(st)
+        return phi, list(infos)
 
 
 class Poisson:
