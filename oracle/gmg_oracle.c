@@ -808,3 +808,665 @@ void orc_apply(void* vp, const double* phi_dense, double* out_dense) {
   orc_boxed_to_dense(vp, 0, out, out_dense);
   free(phi); free(out);
 }
+
+/* =====================================================================
+ * Two-level composite problem (Sec. "Operations between levels", Sec. "Linear
+ * Solvers": multi-AMR-level geometric multigrid).  Level 0 (coarse) covers the domain;
+ * level 1 (fine, refinement ratio 2) covers part of it.  The unknowns are the fine cells
+ * and the coarse cells NOT covered by fine cells.
+ *
+ * Readings used (the paper names interpolation, restriction and refluxing but gives no
+ * formulas):
+ *   - a fine ghost g across a coarse/fine face normal to d is the quadratic through the
+ *     coarse value interpolated tangentially to g's position (phi_c*, at the coarse cell
+ *     centre one fine cell beyond g) and the first two fine cells inward:
+ *       phi_g = 8/15 phi_c* + 2/3 phi_f1 - 1/5 phi_f2,
+ *       phi_c* = phi_C + sum over the two tangential axes t of
+ *                s_t (phi_{C+t} - phi_{C-t}) / 2 + s_t^2 (phi_{C+t} - 2 phi_C + phi_{C-t}) / 2,
+ *     with s_t = +-1/4 the ghost's offset from the coarse centre in coarse cells;
+ *   - a fine face on the coarse/fine boundary takes the adjacent fine cell's beta;
+ *   - refluxing (Sec. "Operations between levels"): an uncovered coarse cell uses, on a
+ *     face shared with a covered cell, the mean of the 4 fine fluxes through that face
+ *     instead of its own coarse flux;
+ *   - covered coarse values are the average of their 8 fine children.
+ * The operator is written row by row as (unknown, coefficient) terms, each coefficient
+ * that carries a face beta tagged with that face, so that the same row code gives
+ * A x, A^T y and the derivative lambda^T (dA/dbeta) phi.
+ * ===================================================================== */
+
+typedef struct {
+  int64_t dst;       /* ghost slot in the fine boxed layout */
+  int64_t f1, f2;    /* first and second fine cells inward */
+  int64_t cq[5];     /* coarse cells C, C+t1, C-t1, C+t2, C-t2 (coarse boxed layout) */
+  double cw[5];      /* weights of phi_c* */
+} ocfghost;
+
+typedef struct {
+  oprob* C;          /* coarse level + its multigrid hierarchy */
+  oprob* F;          /* fine level (its own hierarchy is not used) */
+  char* covered;     /* coarse boxed layout: 1 where fine cells lie above */
+  int64_t ncf;
+  ocfghost* cf;      /* coarse/fine ghosts of the fine level */
+  int64_t* cfidx;    /* fine boxed layout -> index into cf, or -1 */
+  int64_t* gentry;   /* fine boxed layout -> fine ghost-map entry, or -1 */
+  double a, b;
+  int nu1, nu2;
+} oamr;
+
+static int64_t coarse_at(const olev* c, const int g_in[3]) {
+  int g[3] = {g_in[0], g_in[1], g_in[2]};
+  for (int d = 0; d < 3; ++d)
+    if (c->bclo[d] == ORC_PERIODIC) {
+      int len = c->dhi[d] - c->dlo[d] + 1;
+      g[d] = c->dlo[d] + pmod(g[d] - c->dlo[d], len);
+    }
+  int b = find_box(c, g);
+  if (b < 0) return -1;
+  return IX(c, b, g[0] - c->lo[3 * b], g[1] - c->lo[3 * b + 1], g[2] - c->lo[3 * b + 2]);
+}
+
+static int box_of_index(const olev* l, int64_t q) {
+  int b = 0;
+  while (!(q >= l->off[b] && q < l->off[b + 1])) ++b;
+  return b;
+}
+
+void* orc_amr_create(const int* dlo, const int* dhi, const int* bclo, const int* bchi, const double* plo,
+                     const double* phi_, int nbc, const int* cboxes, int nbf, const int* fboxes) {
+  oamr* A = (oamr*)calloc(1, sizeof(oamr));
+  A->C = (oprob*)orc_create(dlo, dhi, bclo, bchi, plo, phi_, nbc, cboxes);
+  int fdlo[3], fdhi[3];
+  for (int d = 0; d < 3; ++d) { fdlo[d] = 2 * dlo[d]; fdhi[d] = 2 * dhi[d] + 1; }
+  A->F = A->C ? (oprob*)orc_create(fdlo, fdhi, bclo, bchi, plo, phi_, nbf, fboxes) : NULL;
+  if (!A->C || !A->F) { orc_destroy(A->C); orc_destroy(A->F); free(A); return NULL; }
+  olev* c = &A->C->L[0];
+  olev* f = &A->F->L[0];
+  /* fine boxes must be ratio-2 aligned and at least 2 cells wide */
+  for (int b = 0; b < f->nb; ++b)
+    for (int d = 0; d < 3; ++d)
+      if (pmod(f->lo[3 * b + d], 2) || pmod(f->hi[3 * b + d] + 1, 2) || bn(f, b, d) < 2) {
+        orc_destroy(A->C); orc_destroy(A->F); free(A); return NULL;
+      }
+  A->covered = (char*)calloc(c->ntot, 1);
+  for (int b = 0; b < c->nb; ++b)
+    for (int k = 0; k < bn(c, b, 2); ++k)
+      for (int j = 0; j < bn(c, b, 1); ++j)
+        for (int i = 0; i < bn(c, b, 0); ++i) {
+          int g[3] = {2 * (c->lo[3 * b] + i), 2 * (c->lo[3 * b + 1] + j), 2 * (c->lo[3 * b + 2] + k)};
+          A->covered[IX(c, b, i, j, k)] = find_box(f, g) >= 0;
+        }
+  A->gentry = (int64_t*)malloc(sizeof(int64_t) * f->ntot);
+  A->cfidx = (int64_t*)malloc(sizeof(int64_t) * f->ntot);
+  for (int64_t q = 0; q < f->ntot; ++q) A->gentry[q] = A->cfidx[q] = -1;
+  for (int64_t e = 0; e < f->ng; ++e) A->gentry[f->gdst[e]] = e;
+  /* coarse/fine ghosts: the fine ghost-map entries that no fine box fills */
+  A->cf = (ocfghost*)calloc(f->ng + 1, sizeof(ocfghost));
+  int64_t n = 0;
+  for (int64_t e = 0; e < f->ng; ++e) {
+    if (f->gsrc[e] >= 0) continue;
+    int64_t gq = f->gdst[e];
+    int b = box_of_index(f, gq);
+    int64_t nx = bn(f, b, 0) + 2, ny = bn(f, b, 1) + 2;
+    int64_t rel = gq - f->off[b];
+    int loc[3] = {(int)(rel % nx) - 1, (int)((rel / nx) % ny) - 1, (int)(rel / (nx * ny)) - 1};
+    int d = -1, side = 0;
+    for (int q = 0; q < 3; ++q) {
+      if (loc[q] < 0) { d = q; side = 0; }
+      if (loc[q] >= bn(f, b, q)) { d = q; side = 1; }
+    }
+    int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    ocfghost* G = &A->cf[n];
+    G->dst = gq;
+    int in1[3] = {loc[0], loc[1], loc[2]}, in2[3] = {loc[0], loc[1], loc[2]};
+    in1[d] = side ? bn(f, b, d) - 1 : 0;
+    in2[d] = side ? bn(f, b, d) - 2 : 1;
+    G->f1 = IX(f, b, in1[0], in1[1], in1[2]);
+    G->f2 = IX(f, b, in2[0], in2[1], in2[2]);
+    int g[3], C[3];
+    double s[3];
+    for (int q = 0; q < 3; ++q) {
+      g[q] = f->lo[3 * b + q] + loc[q];
+      C[q] = (g[q] - pmod(g[q], 2)) / 2;
+      s[q] = (pmod(g[q], 2) == 0) ? -0.25 : 0.25;
+    }
+    int t[2] = {d1, d2};
+    G->cq[0] = coarse_at(c, C);
+    G->cw[0] = 1.0;
+    for (int e2 = 0; e2 < 2; ++e2) {
+      int Cp[3] = {C[0], C[1], C[2]}, Cm[3] = {C[0], C[1], C[2]};
+      Cp[t[e2]] += 1;
+      Cm[t[e2]] -= 1;
+      double st = s[t[e2]];
+      G->cq[1 + 2 * e2] = coarse_at(c, Cp);
+      G->cq[2 + 2 * e2] = coarse_at(c, Cm);
+      G->cw[1 + 2 * e2] = 0.5 * st + 0.5 * st * st;
+      G->cw[2 + 2 * e2] = -0.5 * st + 0.5 * st * st;
+      G->cw[0] -= st * st;
+    }
+    for (int e2 = 0; e2 < 5; ++e2)
+      if (G->cq[e2] < 0 || A->covered[G->cq[e2]]) { /* interpolation must use uncovered coarse cells */
+        orc_destroy(A->C); orc_destroy(A->F); free(A->covered); free(A->cf); free(A->cfidx); free(A->gentry); free(A);
+        return NULL;
+      }
+    A->cfidx[gq] = n;
+    ++n;
+  }
+  A->ncf = n;
+  A->a = 0.0;
+  A->b = 1.0;
+  A->nu1 = 2;
+  A->nu2 = 2;
+  return A;
+}
+
+void orc_amr_destroy(void* vp) {
+  oamr* A = (oamr*)vp;
+  if (!A) return;
+  orc_destroy(A->C);
+  orc_destroy(A->F);
+  free(A->covered); free(A->cf); free(A->cfidx); free(A->gentry);
+  free(A);
+}
+
+void* orc_amr_coarse(void* vp) { return ((oamr*)vp)->C; }
+void* orc_amr_fine(void* vp) { return ((oamr*)vp)->F; }
+int64_t orc_amr_ncf(void* vp) { return ((oamr*)vp)->ncf; }
+void orc_amr_covered(void* vp, char* out) { memcpy(out, ((oamr*)vp)->covered, ((oamr*)vp)->C->L[0].ntot); }
+
+/* Coefficients: dense cell alpha/beta over the coarse domain and over the FINE domain
+   (only the fine boxes' cells are read).  Fine faces on the coarse/fine boundary take the
+   adjacent fine cell's beta. */
+int orc_amr_set_coeffs(void* vp, double a, double bsc, const double* alpha_c, const double* beta_c,
+                       const double* alpha_f, const double* beta_f) {
+  oamr* A = (oamr*)vp;
+  A->a = a;
+  A->b = bsc;
+  orc_set_coeffs(A->C, a, bsc, alpha_c, beta_c);
+  orc_set_coeffs(A->F, a, bsc, alpha_f, beta_f);
+  olev* f = &A->F->L[0];
+  double* face[3] = {f->bx, f->by, f->bz};
+  for (int64_t q = 0; q < A->ncf; ++q) {
+    const ocfghost* G = &A->cf[q];
+    int b = box_of_index(f, G->dst);
+    int64_t nx = bn(f, b, 0) + 2, ny = bn(f, b, 1) + 2;
+    int64_t diff = G->f1 - G->dst;
+    int d = (diff == 1 || diff == -1) ? 0 : ((diff == nx || diff == -nx) ? 1 : 2);
+    int64_t slot = diff > 0 ? G->f1 : G->dst; /* face slot i holds the face at i - 1/2 */
+    int64_t rel = G->f1 - f->off[b];
+    int g[3] = {f->lo[3 * b] + (int)(rel % nx) - 1, f->lo[3 * b + 1] + (int)((rel / nx) % ny) - 1,
+                f->lo[3 * b + 2] + (int)(rel / (nx * ny)) - 1};
+    face[d][slot] = beta_f ? dense_at(f, beta_f, g) : 1.0;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ rows */
+
+typedef struct {
+  int mode;               /* 0: apply, 1: transpose, 2: beta gradient */
+  const double *xc, *xf;  /* apply / gradient: the vector A acts on */
+  double *yc, *yf;        /* transpose: output */
+  double yrow;            /* transpose / gradient: the row's value of y (lambda) */
+  double acc;             /* apply: the row value */
+  double *gc[3], *gf[3];  /* gradient: per-face accumulators, coarse and fine */
+} orow;
+
+/* a term coef * x[which][q] with coef = c * beta(face) when fw >= 0 (fw: 0 coarse, 1 fine
+   face array of direction fd, slot fs), else coef = c */
+static void term(const oamr* A, orow* R, int which, int64_t q, double c, int fw, int fd, int64_t fs) {
+  double beta = 1.0;
+  if (fw >= 0) {
+    const olev* l = fw ? &A->F->L[0] : &A->C->L[0];
+    const double* fa = fd == 0 ? l->bx : (fd == 1 ? l->by : l->bz);
+    beta = fa[fs];
+  }
+  if (R->mode == 0) {
+    R->acc += c * beta * (which ? R->xf[q] : R->xc[q]);
+  } else if (R->mode == 1) {
+    if (which) R->yf[q] += c * beta * R->yrow;
+    else R->yc[q] += c * beta * R->yrow;
+  } else if (fw >= 0) {
+    double* g = fw ? R->gf[fd] : R->gc[fd];
+    g[fs] -= R->yrow * c * (which ? R->xf[q] : R->xc[q]);
+  }
+}
+
+/* the value of fine ghost slot gq as terms, scaled by c (face tag passed through) */
+static void fine_ghost_terms(const oamr* A, orow* R, int64_t gq, double c, int fw, int fd, int64_t fs) {
+  const olev* f = &A->F->L[0];
+  int64_t cfi = A->cfidx[gq];
+  if (cfi >= 0) {
+    const ocfghost* G = &A->cf[cfi];
+    for (int e = 0; e < 5; ++e) term(A, R, 0, G->cq[e], c * (8.0 / 15.0) * G->cw[e], fw, fd, fs);
+    term(A, R, 1, G->f1, c * (2.0 / 3.0), fw, fd, fs);
+    term(A, R, 1, G->f2, c * (-0.2), fw, fd, fs);
+    return;
+  }
+  int64_t e = A->gentry[gq];
+  term(A, R, 1, f->gsrc[e], c * f->gfac[e], fw, fd, fs);
+}
+
+/* fine row: a alpha phi - b sum_d [beta+(phi+ - phi) - beta-(phi - phi-)] / h_d^2 */
+static void fine_row(const oamr* A, orow* R, int b, int i, int j, int k) {
+  const olev* f = &A->F->L[0];
+  int64_t q = IX(f, b, i, j, k);
+  int loc[3] = {i, j, k};
+  term(A, R, 1, q, A->a * f->alpha[q], -1, 0, 0);
+  for (int d = 0; d < 3; ++d) {
+    double ih2 = A->b / (f->h[d] * f->h[d]);
+    for (int side = 0; side < 2; ++side) {
+      int nl[3] = {loc[0], loc[1], loc[2]};
+      nl[d] += side ? 1 : -1;
+      int fl[3] = {loc[0], loc[1], loc[2]};
+      if (side) fl[d] += 1;
+      int64_t fs = IX(f, b, fl[0], fl[1], fl[2]);
+      term(A, R, 1, q, ih2, 1, d, fs);
+      int64_t nq = IX(f, b, nl[0], nl[1], nl[2]);
+      if (nl[d] >= 0 && nl[d] < bn(f, b, d)) term(A, R, 1, nq, -ih2, 1, d, fs);
+      else fine_ghost_terms(A, R, nq, -ih2, 1, d, fs);
+    }
+  }
+}
+
+/* coarse row of an uncovered coarse cell; on a face shared with a covered cell the flux is
+   the mean of the 4 fine fluxes beta_f (phi_fine - phi_ghost) / h_f through that face */
+static void coarse_row(const oamr* A, orow* R, int b, int i, int j, int k) {
+  const olev* c = &A->C->L[0];
+  const olev* f = &A->F->L[0];
+  int64_t q = IX(c, b, i, j, k);
+  int loc[3] = {i, j, k};
+  term(A, R, 0, q, A->a * c->alpha[q], -1, 0, 0);
+  for (int d = 0; d < 3; ++d) {
+    double hc = c->h[d], hf = f->h[d];
+    int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    int gl[3] = {c->lo[3 * b] + i, c->lo[3 * b + 1] + j, c->lo[3 * b + 2] + k};
+    for (int side = 0; side < 2; ++side) {
+      int gn[3] = {gl[0], gl[1], gl[2]};
+      gn[d] += side ? 1 : -1;
+      int64_t nq = coarse_at(c, gn);
+      if (nq >= 0 && A->covered[nq]) {
+        for (int u = 0; u < 2; ++u)
+          for (int v = 0; v < 2; ++v) {
+            int fg[3];
+            fg[d] = side ? 2 * gn[d] : 2 * gn[d] + 1; /* fine cell next to the face */
+            fg[d1] = 2 * gl[d1] + u;
+            fg[d2] = 2 * gl[d2] + v;
+            for (int t = 0; t < 3; ++t)
+              if (f->bclo[t] == ORC_PERIODIC) {
+                int len = f->dhi[t] - f->dlo[t] + 1;
+                fg[t] = f->dlo[t] + pmod(fg[t] - f->dlo[t], len);
+              }
+            int fb = find_box(f, fg);
+            int fl[3] = {fg[0] - f->lo[3 * fb], fg[1] - f->lo[3 * fb + 1], fg[2] - f->lo[3 * fb + 2]};
+            int64_t fq = IX(f, fb, fl[0], fl[1], fl[2]);
+            int ghl[3] = {fl[0], fl[1], fl[2]};
+            ghl[d] += side ? -1 : 1;
+            int64_t gq = IX(f, fb, ghl[0], ghl[1], ghl[2]);
+            int sl[3] = {fl[0], fl[1], fl[2]};
+            if (!side) sl[d] += 1;
+            int64_t fs = IX(f, fb, sl[0], sl[1], sl[2]);
+            /* high side: -b F / hc with F = beta (phi_f - phi_g) / hf;
+               low side:  +b F / hc with F = beta (phi_g - phi_f) / hf: the same terms */
+            double cf = A->b * 0.25 / (hf * hc);
+            term(A, R, 1, fq, -cf, 1, d, fs);
+            fine_ghost_terms(A, R, gq, cf, 1, d, fs);
+          }
+        continue;
+      }
+      int fl[3] = {loc[0], loc[1], loc[2]};
+      if (side) fl[d] += 1;
+      int64_t fs = IX(c, b, fl[0], fl[1], fl[2]);
+      double w = A->b / (hc * hc);
+      term(A, R, 0, q, w, 0, d, fs);
+      if (nq < 0) term(A, R, 0, q, w, 0, d, fs); /* homogeneous Dirichlet: ghost = -phi */
+      else term(A, R, 0, nq, -w, 0, d, fs);
+    }
+  }
+}
+
+typedef void (*row_fn)(const oamr*, orow*, int, int, int, int);
+
+static void amr_sweep(const oamr* A, orow* R, double* yc, double* yf, const double* ycin, const double* yfin) {
+  const olev* c = &A->C->L[0];
+  const olev* f = &A->F->L[0];
+  for (int b = 0; b < f->nb; ++b)
+    for (int k = 0; k < bn(f, b, 2); ++k)
+      for (int j = 0; j < bn(f, b, 1); ++j)
+        for (int i = 0; i < bn(f, b, 0); ++i) {
+          int64_t q = IX(f, b, i, j, k);
+          R->acc = 0.0;
+          if (yfin) R->yrow = yfin[q];
+          fine_row(A, R, b, i, j, k);
+          if (yf) yf[q] = R->acc;
+        }
+  for (int b = 0; b < c->nb; ++b)
+    for (int k = 0; k < bn(c, b, 2); ++k)
+      for (int j = 0; j < bn(c, b, 1); ++j)
+        for (int i = 0; i < bn(c, b, 0); ++i) {
+          int64_t q = IX(c, b, i, j, k);
+          if (A->covered[q]) continue;
+          R->acc = 0.0;
+          if (ycin) R->yrow = ycin[q];
+          coarse_row(A, R, b, i, j, k);
+          if (yc) yc[q] = R->acc;
+        }
+}
+
+/* y = A x (composite), boxed layouts; covered coarse entries of y are 0 */
+void orc_amr_apply_boxed(void* vp, const double* xc, const double* xf, double* yc, double* yf) {
+  oamr* A = (oamr*)vp;
+  orow R;
+  memset(&R, 0, sizeof(R));
+  R.mode = 0;
+  R.xc = xc;
+  R.xf = xf;
+  memset(yc, 0, sizeof(double) * A->C->L[0].ntot);
+  memset(yf, 0, sizeof(double) * A->F->L[0].ntot);
+  amr_sweep(A, &R, yc, yf, NULL, NULL);
+}
+
+/* x = A^T y; covered coarse entries of y are ignored */
+void orc_amr_apply_transpose_boxed(void* vp, const double* yc, const double* yf, double* xc, double* xf) {
+  oamr* A = (oamr*)vp;
+  orow R;
+  memset(&R, 0, sizeof(R));
+  R.mode = 1;
+  R.yc = xc;
+  R.yf = xf;
+  memset(xc, 0, sizeof(double) * A->C->L[0].ntot);
+  memset(xf, 0, sizeof(double) * A->F->L[0].ntot);
+  amr_sweep(A, &R, NULL, NULL, yc, yf);
+}
+
+/* dL/dbeta_face = -lambda^T (dA/dbeta_face) phi for every coarse and fine face (boxed
+   face layouts, zeroed first) */
+void orc_amr_grad_faces(void* vp, const double* phic, const double* phif, const double* lamc, const double* lamf,
+                        double* gcx, double* gcy, double* gcz, double* gfx, double* gfy, double* gfz) {
+  oamr* A = (oamr*)vp;
+  orow R;
+  memset(&R, 0, sizeof(R));
+  R.mode = 2;
+  R.xc = phic;
+  R.xf = phif;
+  double* gc[3] = {gcx, gcy, gcz};
+  double* gf[3] = {gfx, gfy, gfz};
+  for (int d = 0; d < 3; ++d) {
+    R.gc[d] = gc[d];
+    R.gf[d] = gf[d];
+    memset(gc[d], 0, sizeof(double) * A->C->L[0].ntot);
+    memset(gf[d], 0, sizeof(double) * A->F->L[0].ntot);
+  }
+  amr_sweep(A, &R, NULL, NULL, lamc, lamf);
+}
+
+/* ------------------------------------------------------------------ solve */
+
+/* coarse/fine ghosts of the fine field from coarse values cx (NULL: zero) */
+static void amr_fill_cf(const oamr* A, double* fx, const double* cx) {
+  for (int64_t q = 0; q < A->ncf; ++q) {
+    const ocfghost* G = &A->cf[q];
+    double cs = 0.0;
+    if (cx)
+      for (int e = 0; e < 5; ++e) cs += G->cw[e] * cx[G->cq[e]];
+    fx[G->dst] = (8.0 / 15.0) * cs + (2.0 / 3.0) * fx[G->f1] - 0.2 * fx[G->f2];
+  }
+}
+
+/* covered coarse cells := mean of their 8 fine children */
+static void amr_average_down(const oamr* A, const double* fx, double* cx) {
+  const olev* c = &A->C->L[0];
+  const olev* f = &A->F->L[0];
+  for (int b = 0; b < f->nb; ++b)
+    for (int K = f->lo[3 * b + 2] / 2; K <= (f->hi[3 * b + 2] + 1) / 2 - 1; ++K)
+      for (int J = f->lo[3 * b + 1] / 2; J <= (f->hi[3 * b + 1] + 1) / 2 - 1; ++J)
+        for (int I = f->lo[3 * b] / 2; I <= (f->hi[3 * b] + 1) / 2 - 1; ++I) {
+          double s = 0.0;
+          for (int dk = 0; dk < 2; ++dk)
+            for (int dj = 0; dj < 2; ++dj)
+              for (int di = 0; di < 2; ++di)
+                s += fx[IX(f, b, 2 * I + di - f->lo[3 * b], 2 * J + dj - f->lo[3 * b + 1], 2 * K + dk - f->lo[3 * b + 2])];
+          int G[3] = {I, J, K};
+          cx[coarse_at(c, G)] = s / 8.0;
+        }
+}
+
+/* one red-black colour on the fine level, coarse/fine ghosts from cx */
+static void amr_fine_colour(oamr* A, double* ef, const double* rf, const double* cx, int colour) {
+  amr_fill_cf(A, ef, cx);
+  orc_smooth_colour(A->F, 0, ef, rf, colour); /* fills the fine/fine ghosts, keeps the C/F ones */
+}
+
+/* volume-weighted composite sum and volume (fine cells h_f^3, uncovered coarse h_c^3) */
+static void amr_vsum(const oamr* A, const double* xc, const double* xf, double* s, double* v) {
+  const olev* c = &A->C->L[0];
+  const olev* f = &A->F->L[0];
+  double vc = c->h[0] * c->h[1] * c->h[2], vf = f->h[0] * f->h[1] * f->h[2];
+  *s = 0.0;
+  *v = 0.0;
+  for (int b = 0; b < f->nb; ++b)
+    for (int k = 0; k < bn(f, b, 2); ++k)
+      for (int j = 0; j < bn(f, b, 1); ++j)
+        for (int i = 0; i < bn(f, b, 0); ++i) { *s += vf * xf[IX(f, b, i, j, k)]; *v += vf; }
+  for (int b = 0; b < c->nb; ++b)
+    for (int k = 0; k < bn(c, b, 2); ++k)
+      for (int j = 0; j < bn(c, b, 1); ++j)
+        for (int i = 0; i < bn(c, b, 0); ++i) {
+          int64_t q = IX(c, b, i, j, k);
+          if (A->covered[q]) continue;
+          *s += vc * xc[q];
+          *v += vc;
+        }
+}
+
+static void amr_add_const(const oamr* A, double* xc, double* xf, double k) {
+  lev_add_const(&A->C->L[0], xc, k);
+  lev_add_const(&A->F->L[0], xf, k);
+}
+
+static double amr_norminf(const oamr* A, const double* xc, const double* xf) {
+  const olev* c = &A->C->L[0];
+  double m = lev_norminf(&A->F->L[0], xf);
+  for (int b = 0; b < c->nb; ++b)
+    for (int k = 0; k < bn(c, b, 2); ++k)
+      for (int j = 0; j < bn(c, b, 1); ++j)
+        for (int i = 0; i < bn(c, b, 0); ++i) {
+          int64_t q = IX(c, b, i, j, k);
+          if (A->covered[q]) continue;
+          double v = fabs(xc[q]);
+          if (v > m || v != v) m = v;
+        }
+  return m;
+}
+
+/* composite residual r = rhs - A phi (covered coarse entries 0) */
+static void amr_residual(oamr* A, const double* rc_in, const double* rf_in, const double* pc, const double* pf,
+                         double* rc, double* rf) {
+  olev* c = &A->C->L[0];
+  olev* f = &A->F->L[0];
+  orc_amr_apply_boxed(A, pc, pf, rc, rf);
+  for (int64_t q = 0; q < f->ntot; ++q) rf[q] = rf_in[q] - rf[q];
+  for (int64_t q = 0; q < c->ntot; ++q) rc[q] = A->covered[q] ? 0.0 : rc_in[q] - rc[q];
+}
+
+/* Composite multigrid solve (the two-level iteration of the multi-level solver):
+   1. r = composite residual;
+   2. fine correction e_f from 0 by nu1 red-black sweeps with homogeneous coarse/fine
+      ghosts (coarse correction 0);
+   3. coarse right-hand side: on covered cells the average of the fine correction
+      residual r_f - A_f e_f, on uncovered cells r_c minus the change of their composite
+      row by e_f (the fine correction's reflux);
+   4. one V-cycle of the coarse level's own hierarchy gives e_c;
+   5. e_f += piecewise-constant interpolation of e_c;
+   6. nu2 fine sweeps with coarse/fine ghosts interpolated from e_c;
+   7. covered e_c := average of e_f; phi += e.
+   Stops at ||r||_inf <= max(tol_rel ||rhs||_inf, tol_abs) over the composite unknowns.
+   Singular (all periodic, a = 0): rhs projected to zero volume-weighted mean; phi returned
+   with zero volume-weighted mean.  Dense arrays: coarse over the coarse domain, fine over
+   the fine domain (cells outside fine boxes ignored; covered coarse cells of phi_c hold the
+   average of the fine solution on return). */
+int orc_amr_solve(void* vp, const double* rhsc_d, const double* rhsf_d, double* phic_d, double* phif_d, double tol_rel,
+                  double tol_abs, int maxit, double* hist, int* status) {
+  oamr* A = (oamr*)vp;
+  olev* c = &A->C->L[0];
+  olev* f = &A->F->L[0];
+  int64_t nc = c->ntot, nf = f->ntot;
+  double *rhc = calloc(nc, 8), *rhf = calloc(nf, 8), *pc = calloc(nc, 8), *pf = calloc(nf, 8);
+  double *rc = calloc(nc, 8), *rf = calloc(nf, 8), *ec = calloc(nc, 8), *ef = calloc(nf, 8);
+  double *yc = calloc(nc, 8), *yf = calloc(nf, 8), *cr = calloc(nc, 8);
+  orc_dense_to_boxed(A->C, 0, rhsc_d, rhc);
+  orc_dense_to_boxed(A->F, 0, rhsf_d, rhf);
+  for (int64_t q = 0; q < nc; ++q)
+    if (A->covered[q]) rhc[q] = 0.0;
+  double rn0 = amr_norminf(A, rhc, rhf);
+  int sing = A->C->singular;
+  if (sing) {
+    double s, v;
+    amr_vsum(A, rhc, rhf, &s, &v);
+    amr_add_const(A, rhc, rhf, -s / v);
+    for (int64_t q = 0; q < nc; ++q)
+      if (A->covered[q]) rhc[q] = 0.0;
+  }
+  double target = tol_rel * rn0 > tol_abs ? tol_rel * rn0 : tol_abs;
+  amr_residual(A, rhc, rhf, pc, pf, rc, rf);
+  double rn = amr_norminf(A, rc, rf);
+  if (hist) hist[0] = rn;
+  int it = 0;
+  *status = 0;
+  while (!(rn <= target) && it < maxit) {
+    memset(ef, 0, 8 * nf);
+    memset(ec, 0, 8 * nc);
+    for (int s = 0; s < A->nu1; ++s) {
+      amr_fine_colour(A, ef, rf, NULL, 0);
+      amr_fine_colour(A, ef, rf, NULL, 1);
+    }
+    orc_amr_apply_boxed(A, ec, ef, yc, yf); /* A(0, e_f): fine rows and the reflux change */
+    memset(cr, 0, 8 * nc);
+    for (int64_t q = 0; q < nf; ++q) yf[q] = rf[q] - yf[q];
+    amr_average_down(A, yf, cr);
+    for (int64_t q = 0; q < nc; ++q)
+      if (!A->covered[q]) cr[q] = rc[q] - yc[q];
+    orc_vcycle(A->C, 0, ec, cr);
+    /* piecewise-constant interpolation of e_c into e_f */
+    for (int b = 0; b < f->nb; ++b)
+      for (int k = 0; k < bn(f, b, 2); ++k)
+        for (int j = 0; j < bn(f, b, 1); ++j)
+          for (int i = 0; i < bn(f, b, 0); ++i) {
+            int G[3] = {(f->lo[3 * b] + i) >> 1, (f->lo[3 * b + 1] + j) >> 1, (f->lo[3 * b + 2] + k) >> 1};
+            ef[IX(f, b, i, j, k)] += ec[coarse_at(c, G)];
+          }
+    for (int s = 0; s < A->nu2; ++s) {
+      amr_fine_colour(A, ef, rf, ec, 0);
+      amr_fine_colour(A, ef, rf, ec, 1);
+    }
+    amr_average_down(A, ef, ec);
+    for (int64_t q = 0; q < nf; ++q) pf[q] += ef[q];
+    for (int64_t q = 0; q < nc; ++q) pc[q] += ec[q];
+    amr_average_down(A, pf, pc);
+    amr_residual(A, rhc, rhf, pc, pf, rc, rf);
+    rn = amr_norminf(A, rc, rf);
+    ++it;
+    if (hist) hist[it] = rn;
+    if (!(rn == rn) || isinf(rn)) { *status = -3; break; }
+  }
+  if (*status == 0 && !(rn <= target)) *status = -2;
+  if (sing) {
+    double s, v;
+    amr_vsum(A, pc, pf, &s, &v);
+    amr_add_const(A, pc, pf, -s / v);
+    amr_average_down(A, pf, pc);
+  }
+  orc_boxed_to_dense(A->C, 0, pc, phic_d);
+  orc_boxed_to_dense(A->F, 0, pf, phif_d);
+  free(rhc); free(rhf); free(pc); free(pf); free(rc); free(rf); free(ec); free(ef); free(yc); free(yf); free(cr);
+  return it;
+}
+
+/* dense wrappers (coarse dense over the coarse domain, fine dense over the fine domain) */
+void orc_amr_apply(void* vp, const double* xc_d, const double* xf_d, double* yc_d, double* yf_d, int transpose) {
+  oamr* A = (oamr*)vp;
+  int64_t nc = A->C->L[0].ntot, nf = A->F->L[0].ntot;
+  double *xc = calloc(nc, 8), *xf = calloc(nf, 8), *yc = calloc(nc, 8), *yf = calloc(nf, 8);
+  orc_dense_to_boxed(A->C, 0, xc_d, xc);
+  orc_dense_to_boxed(A->F, 0, xf_d, xf);
+  if (transpose) orc_amr_apply_transpose_boxed(A, xc, xf, yc, yf);
+  else orc_amr_apply_boxed(A, xc, xf, yc, yf);
+  orc_boxed_to_dense(A->C, 0, yc, yc_d);
+  orc_boxed_to_dense(A->F, 0, yf, yf_d);
+  free(xc); free(xf); free(yc); free(yf);
+}
+
+/* dL/dbeta at cells (dense) from the face gradients: a face between two cells of the same
+   level took the harmonic mean 2 bL bR / (bL + bR) (d/dbL = 2 bR^2 / (bL + bR)^2); a wall
+   face or a coarse/fine fine face took the one adjacent cell's beta (d = 1). */
+void orc_amr_grad_beta_cells(void* vp, const double* phic_d, const double* phif_d, const double* lamc_d,
+                             const double* lamf_d, const double* betac_d, const double* betaf_d, double* gc_d,
+                             double* gf_d) {
+  oamr* A = (oamr*)vp;
+  oprob* P[2] = {A->C, A->F};
+  int64_t nn[2] = {A->C->L[0].ntot, A->F->L[0].ntot};
+  double* v[2][2];
+  double* g[2][3];
+  for (int w = 0; w < 2; ++w) {
+    v[w][0] = calloc(nn[w], 8);
+    v[w][1] = calloc(nn[w], 8);
+    for (int d = 0; d < 3; ++d) g[w][d] = calloc(nn[w], 8);
+  }
+  orc_dense_to_boxed(A->C, 0, phic_d, v[0][0]);
+  orc_dense_to_boxed(A->C, 0, lamc_d, v[0][1]);
+  orc_dense_to_boxed(A->F, 0, phif_d, v[1][0]);
+  orc_dense_to_boxed(A->F, 0, lamf_d, v[1][1]);
+  /* lambda is zero on covered coarse cells (not unknowns) */
+  for (int64_t q = 0; q < nn[0]; ++q)
+    if (A->covered[q]) v[0][1][q] = 0.0;
+  orc_amr_grad_faces(A, v[0][0], v[1][0], v[0][1], v[1][1], g[0][0], g[0][1], g[0][2], g[1][0], g[1][1], g[1][2]);
+  const double* beta_d[2] = {betac_d, betaf_d};
+  double* out_d[2] = {gc_d, gf_d};
+  for (int w = 0; w < 2; ++w) {
+    const olev* l = &P[w]->L[0];
+    int64_t nx = l->dhi[0] - l->dlo[0] + 1, ny = l->dhi[1] - l->dlo[1] + 1, nz = l->dhi[2] - l->dlo[2] + 1;
+    memset(out_d[w], 0, sizeof(double) * nx * ny * nz);
+    for (int b = 0; b < l->nb; ++b)
+      for (int d = 0; d < 3; ++d) {
+        int ext[3] = {bn(l, b, 0), bn(l, b, 1), bn(l, b, 2)};
+        ext[d] += 1;
+        for (int k = 0; k < ext[2]; ++k)
+          for (int j = 0; j < ext[1]; ++j)
+            for (int i = 0; i < ext[0]; ++i) {
+              int loc[3] = {i, j, k};
+              double gface = g[w][d][IX(l, b, i, j, k)];
+              if (gface == 0.0) continue;
+              /* a face shared by two boxes has a slot in each; each slot carries the part
+                 of dL/dbeta of the rows that read it, so every slot is mapped to its cells */
+              int gR[3], gL[3];
+              for (int q = 0; q < 3; ++q) gR[q] = gL[q] = l->lo[3 * b + q] + loc[q];
+              gL[d] -= 1;
+              int per = l->bclo[d] == ORC_PERIODIC;
+              int len = l->dhi[d] - l->dlo[d] + 1;
+              int Lw[3] = {gL[0], gL[1], gL[2]}, Rw[3] = {gR[0], gR[1], gR[2]};
+              if (per) {
+                Lw[d] = l->dlo[d] + pmod(Lw[d] - l->dlo[d], len);
+                Rw[d] = l->dlo[d] + pmod(Rw[d] - l->dlo[d], len);
+              }
+              int Lin = (per || (gL[d] >= l->dlo[d])) && find_box(l, Lw) >= 0;
+              int Rin = (per || (gR[d] <= l->dhi[d])) && find_box(l, Rw) >= 0;
+              int64_t iL = (Lw[0] - l->dlo[0]) + nx * ((Lw[1] - l->dlo[1]) + ny * (int64_t)(Lw[2] - l->dlo[2]));
+              int64_t iR = (Rw[0] - l->dlo[0]) + nx * ((Rw[1] - l->dlo[1]) + ny * (int64_t)(Rw[2] - l->dlo[2]));
+              if (Lin && Rin) {
+                double bl = beta_d[w][iL], br = beta_d[w][iR], s2 = (bl + br) * (bl + br);
+                out_d[w][iL] += gface * 2.0 * br * br / s2;
+                out_d[w][iR] += gface * 2.0 * bl * bl / s2;
+              } else if (Rin) {
+                out_d[w][iR] += gface;
+              } else if (Lin) {
+                out_d[w][iL] += gface;
+              }
+              (void)nz;
+            }
+      }
+  }
+  for (int w = 0; w < 2; ++w) {
+    free(v[w][0]);
+    free(v[w][1]);
+    for (int d = 0; d < 3; ++d) free(g[w][d]);
+  }
+}

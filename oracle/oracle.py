@@ -17,7 +17,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["gmg_oracle.c", "gmg_oracle_amr.c"]
+SOURCES = ["gmg_oracle.c"]
 LIB = os.path.join(BUILD, "liboracle.so")
 
 PERIODIC = 0
@@ -264,3 +264,124 @@ class Problem:
         out = np.zeros(self.level_shape(0))
         lib().orc_apply(self.h, _dp(phi), _dp(out))
         return out
+
+
+def _declare_amr(L):
+    vp = C.c_void_p
+    L.orc_amr_create.restype = vp
+    L.orc_amr_create.argtypes = [_i32p, _i32p, _i32p, _i32p, _f64p, _f64p, C.c_int, _i32p, C.c_int, _i32p]
+    L.orc_amr_destroy.argtypes = [vp]
+    L.orc_amr_coarse.restype = vp
+    L.orc_amr_coarse.argtypes = [vp]
+    L.orc_amr_fine.restype = vp
+    L.orc_amr_fine.argtypes = [vp]
+    L.orc_amr_ncf.restype = C.c_int64
+    L.orc_amr_ncf.argtypes = [vp]
+    L.orc_amr_covered.argtypes = [vp, C.c_char_p]
+    L.orc_amr_set_coeffs.argtypes = [vp, C.c_double, C.c_double, _f64p, _f64p, _f64p, _f64p]
+    L.orc_amr_apply.argtypes = [vp, _f64p, _f64p, _f64p, _f64p, C.c_int]
+    L.orc_amr_solve.restype = C.c_int
+    L.orc_amr_solve.argtypes = [vp, _f64p, _f64p, _f64p, _f64p, C.c_double, C.c_double, C.c_int, _f64p, _i32p]
+    L.orc_amr_grad_beta_cells.argtypes = [vp, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+
+
+class AmrProblem:
+    """Two-level composite problem: a coarse level covering the domain and a ratio-2 fine
+    level over part of it.  Coarse dense arrays are (nz, ny, nx) over the coarse domain;
+    fine dense arrays are over the whole FINE-resolution domain (only cells inside fine
+    boxes are used)."""
+
+    def __init__(self, domain, coarse_boxes, fine_boxes, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0),
+                 prob_hi=(1.0, 1.0, 1.0)):
+        L = lib()
+        if not hasattr(L, "_amr_declared"):
+            _declare_amr(L)
+            L._amr_declared = True
+        dlo, dhi = _i32(domain[0]), _i32(domain[1])
+        cb = _i32([list(b[0]) + list(b[1]) for b in coarse_boxes]).reshape(-1)
+        fb = _i32([list(b[0]) + list(b[1]) for b in fine_boxes]).reshape(-1)
+        self._keep = [_i32(bc_lo), _i32(bc_hi), _f64(prob_lo), _f64(prob_hi)]
+        self.h = L.orc_amr_create(_ip(dlo), _ip(dhi), _ip(self._keep[0]), _ip(self._keep[1]), _dp(self._keep[2]),
+                                  _dp(self._keep[3]), len(coarse_boxes), _ip(cb), len(fine_boxes), _ip(fb))
+        if not self.h:
+            raise ValueError("oracle: invalid two-level layout")
+        self.coarse_shape = tuple(int(dhi[d] - dlo[d] + 1) for d in (2, 1, 0))
+        self.fine_shape = tuple(2 * n for n in self.coarse_shape)
+        self.fine_boxes = fine_boxes
+        self.C = Problem.__new__(Problem)
+        self.C.h = L.orc_amr_coarse(self.h)
+        self.F = Problem.__new__(Problem)
+        self.F.h = L.orc_amr_fine(self.h)
+        # masks of the composite unknowns
+        self.fine_mask = np.zeros(self.fine_shape, dtype=bool)
+        for lo, hi in fine_boxes:
+            self.fine_mask[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] = True
+        cov = self.fine_mask.reshape(self.coarse_shape[0], 2, self.coarse_shape[1], 2, self.coarse_shape[2], 2)
+        self.covered = cov.all(axis=(1, 3, 5))
+        self.coarse_mask = ~self.covered
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            # the coarse/fine sub-problems are owned by the composite handle
+            self.C.h = None
+            self.F.h = None
+            lib().orc_amr_destroy(self.h)
+            self.h = None
+
+    @property
+    def ncf(self):
+        return int(lib().orc_amr_ncf(self.h))
+
+    def set_coeffs(self, a=0.0, b=1.0, alpha_c=None, beta_c=None, alpha_f=None, beta_f=None):
+        self._coef = [None if x is None else _f64(x) for x in (alpha_c, beta_c, alpha_f, beta_f)]
+        lib().orc_amr_set_coeffs(self.h, a, b, *(_dp(x) for x in self._coef))
+
+    def apply(self, xc, xf, transpose=False):
+        xc, xf = _f64(xc), _f64(xf)
+        yc, yf = np.zeros(self.coarse_shape), np.zeros(self.fine_shape)
+        lib().orc_amr_apply(self.h, _dp(xc), _dp(xf), _dp(yc), _dp(yf), int(transpose))
+        return yc * self.coarse_mask, yf * self.fine_mask
+
+    def solve(self, rhs_c, rhs_f, tol_rel=1e-10, tol_abs=0.0, maxit=100):
+        rc, rf = _f64(rhs_c), _f64(rhs_f)
+        pc, pf = np.zeros(self.coarse_shape), np.zeros(self.fine_shape)
+        hist = np.zeros(maxit + 1)
+        st = np.zeros(1, dtype=np.int32)
+        it = lib().orc_amr_solve(self.h, _dp(rc), _dp(rf), _dp(pc), _dp(pf), tol_rel, tol_abs, maxit, _dp(hist),
+                                 _ip(st))
+        return pc, pf * self.fine_mask, int(it), hist[:it + 1].copy(), int(st[0])
+
+    def grad_beta(self, phi_c, phi_f, lam_c, lam_f, beta_c, beta_f):
+        """dL/dbeta at coarse and fine cells from dL/dbeta_face = -lambda^T dA/dbeta_face phi."""
+        args = [_f64(x) for x in (phi_c, phi_f, lam_c, lam_f, beta_c, beta_f)]
+        gc, gf = np.zeros(self.coarse_shape), np.zeros(self.fine_shape)
+        lib().orc_amr_grad_beta_cells(self.h, *(_dp(x) for x in args), _dp(gc), _dp(gf))
+        return gc, gf
+
+    # composite-vector helpers ---------------------------------------------------------------
+    def pack(self, xc, xf):
+        return np.concatenate([np.asarray(xc)[self.coarse_mask], np.asarray(xf)[self.fine_mask]])
+
+    def unpack(self, v):
+        nc = int(self.coarse_mask.sum())
+        xc, xf = np.zeros(self.coarse_shape), np.zeros(self.fine_shape)
+        xc[self.coarse_mask] = v[:nc]
+        xf[self.fine_mask] = v[nc:]
+        return xc, xf
+
+    def volumes(self):
+        nz, ny, nx = self.coarse_shape
+        plo, phi = self._keep[2], self._keep[3]
+        vc = np.prod([(phi[d] - plo[d]) / n for d, n in zip(range(3), (nx, ny, nz))])
+        return self.pack(np.full(self.coarse_shape, vc), np.full(self.fine_shape, vc / 8.0))
+
+    def matrix(self):
+        """Dense composite matrix (small problems only), columns = composite unknowns."""
+        n = int(self.coarse_mask.sum() + self.fine_mask.sum())
+        M = np.zeros((n, n))
+        e = np.zeros(n)
+        for j in range(n):
+            e[:] = 0.0
+            e[j] = 1.0
+            M[:, j] = self.pack(*self.apply(*self.unpack(e)))
+        return M
