@@ -123,10 +123,17 @@ const char* gmg_last_error(const gmg_ctx* ctx);
 gmg_status gmg_define_domain(gmg_ctx* ctx, const int lo[3], const int hi[3], const double prob_lo[3],
                              const double prob_hi[3], const int bc_lo[3], const int bc_hi[3]);
 
-/* BoxArray of AMR level `lev` (only lev = 0 in this version): nboxes boxes given as
-   box_lohi[6*b + 0..2] = lo, [6*b + 3..5] = hi (inclusive).  Boxes must be disjoint and
-   cover the domain.  Builds the multigrid hierarchy (per-box coarsening, then
-   aggregation into one box, Sec. "Linear Solvers"). */
+/* BoxArray of AMR level `lev`: nboxes boxes given as box_lohi[6*b + 0..2] = lo,
+   [6*b + 3..5] = hi (inclusive), disjoint.
+   lev 0: the boxes cover the domain; builds the multigrid hierarchy (per-box coarsening,
+     then aggregation into one box, Sec. "Linear Solvers").  Resets any level 1.
+   lev 1 (two-level composite form, Sec. "Basic data structures": refinement ratio;
+     Sec. "Operations between levels"): ref_ratio must be 2; boxes in the fine index space,
+     aligned to the ratio, each coarsened box inside one level-0 box, faces either shared
+     with another level-1 box or wholly on the coarse/fine boundary, and at least one
+     uncovered coarse cell between the fine level and any other fine box or wall (the
+     coarse/fine interpolation reads coarse neighbours).  Call after level 0 and before
+     gmg_workspace_size; the workspace then holds both levels. */
 gmg_status gmg_define_level(gmg_ctx* ctx, int lev, int nboxes, const int* box_lohi, int ref_ratio);
 
 /* Convenience: BoxArray of level `lev` = the domain chopped into boxes of at most
@@ -148,8 +155,16 @@ gmg_status gmg_mg_level_boxes(const gmg_ctx* ctx, int m, int* box_lohi, int* par
    NULL). */
 gmg_status gmg_mg_layout(const gmg_ctx* ctx, int m, int dt, int64_t* nelems, int64_t* box_offsets, int* row_strides);
 
-/* Level-0 FP64 layout (same as gmg_mg_layout(ctx, 0, GMG_DT_F64, ...)). */
+/* FP64 boxed layout of AMR level lev (0: MG level 0; 1: the fine level). */
 gmg_status gmg_layout(const gmg_ctx* ctx, int lev, int64_t* nelems, int64_t* box_offsets);
+
+/* Boxes of AMR level lev (count, 6 ints each, row strides); NULL pointers are skipped. */
+gmg_status gmg_amr_level_boxes(const gmg_ctx* ctx, int lev, int* nboxes, int* box_lohi, int* row_strides);
+
+/* Dense (nz, ny, nx) FP64 array over the bounding box of AMR level lev's boxes (level 0:
+   the domain) <-> FP64 boxed layout of that level (valid cells only). */
+gmg_status gmg_pack_amr(gmg_ctx* ctx, int lev, const double* dense, double* boxed);
+gmg_status gmg_unpack_amr(gmg_ctx* ctx, int lev, const double* boxed, double* dense);
 
 /* Dense (nz, ny, nx) FP64 device array over MG level m's domain <-> boxed layout of
    element type dt.  pack writes valid cells only (ghosts untouched); unpack reads
@@ -162,14 +177,15 @@ gmg_status gmg_unpack(gmg_ctx* ctx, int m, int dt, const void* boxed, double* de
 /* Scalars a and b of the operator equation. */
 gmg_status gmg_set_scalars(gmg_ctx* ctx, double a, double b);
 
-/* Cell-centred alpha of level lev (FP64, level-0 boxed layout, device).  Not calling it
-   means alpha = 1. */
+/* Cell-centred alpha of AMR level lev (FP64, that level's boxed layout, device).  Not
+   calling it means alpha = 1. */
 gmg_status gmg_set_acoef(gmg_ctx* ctx, int lev, const double* alpha_cc);
 
-/* Cell-centred beta (FP64, boxed layout, device); face beta = harmonic mean of the two
-   cells, the interior cell's value on a wall face.  Builds the coefficients of every
-   MG level (coarse alpha = mean of 8 children, coarse face beta = mean of the 4 fine
-   faces).  Needs the workspace. */
+/* Cell-centred beta of AMR level lev (FP64, that level's boxed layout, device); face
+   beta = harmonic mean of the two cells, the interior cell's value on a wall face and
+   (level 1) on a coarse/fine face.  Builds the coefficients of every MG level (coarse
+   alpha = mean of 8 children, coarse face beta = mean of the 4 fine faces) once every
+   defined AMR level has its beta.  Needs the workspace. */
 gmg_status gmg_set_bcoef_cell(gmg_ctx* ctx, int lev, const double* beta_cc);
 
 /* Face beta given directly: three FP64 face arrays in the boxed layout (slot i = face
@@ -192,17 +208,50 @@ gmg_status gmg_set_workspace(gmg_ctx* ctx, void* dptr, size_t bytes);
 
 /* ------------------------------------------------------------------- solve */
 
-/* Solve A phi = rhs on level 0 from phi = 0 (phi's input content is ignored) until
+/* Solve A phi = rhs from phi = 0 (phi's input content is ignored) until
    ||rhs - A phi||_inf <= max(tol_rel * ||rhs||_inf, tol_abs) or p->max_iter outer
-   iterations.  phi, rhs: FP64 device arrays in the level-0 layout (phi[0], rhs[0]; the
-   arrays of pointers leave room for AMR levels).  info may be NULL.  Returns GMG_OK,
+   iterations.  phi[l], rhs[l]: FP64 device arrays in AMR level l's layout.  One level:
+   the multigrid V-cycle iteration.  Two levels: A is the composite operator on the fine
+   cells and the uncovered coarse cells (fine ghosts on the coarse/fine boundary by
+   quadratic interpolation, coarse cells next to the fine level refluxed: the mean of the 4
+   fine fluxes replaces the coarse flux on a shared face), solved by the two-level
+   composite multigrid iteration (fine smoothing, coarse V-cycle on level 0's hierarchy);
+   on return covered coarse cells of phi[0] hold the average of the fine solution, and the
+   rhs entries of covered cells are ignored; FP64 only.  info may be NULL.  Returns GMG_OK,
    GMG_ERR_NOT_CONVERGED (phi holds the last iterate), GMG_ERR_DIVERGED or
-   GMG_ERR_BAD_INPUT (nonzero-mean rhs of a singular problem without project_mean). */
+   GMG_ERR_BAD_INPUT (nonzero-mean rhs of a singular problem without project_mean; for
+   two levels the mean is volume-weighted over the composite cells). */
 gmg_status gmg_solve(gmg_ctx* ctx, void* const* phi, const void* const* rhs, double tol_rel, double tol_abs,
                      const gmg_params* p, gmg_solve_info* info);
 
-/* out = A phi on level 0 (FP64; phi's ghost cells are overwritten). */
+/* out = A phi (FP64; phi's ghost cells are overwritten).  Two levels: the composite
+   operator; covered coarse entries of out are 0. */
 gmg_status gmg_apply(gmg_ctx* ctx, void* const* out, void* const* phi);
+
+/* out = A^T y.  One level: A is symmetric (same as gmg_apply).  Two levels: the transpose
+   of the composite operator (the transposed interpolation and reflux couplings); covered
+   coarse entries of y are taken as 0 and those of out are 0. */
+gmg_status gmg_apply_transpose(gmg_ctx* ctx, void* const* out, void* const* y);
+
+/* Adjoint solve A^T lambda = g (FP64), so that lambda = dL/d(rhs) for a loss L(phi) with
+   dL/dphi = g.  One level: a forward solve (A symmetric).  Two levels: BiCGStab on A^T,
+   right-preconditioned by the composite multigrid correction of A, to ||g - A^T lambda||_inf
+   <= tol_rel ||g||_inf (max_iter Krylov iterations).  Singular problems (all periodic,
+   a = 0): g is projected onto the range of A^T (g - V sum(g)/sum(V), V the cell volumes;
+   one level: g minus its mean) and lambda returned with zero sum.  lambda, g as in
+   gmg_solve; covered coarse entries of g are ignored and those of lambda are 0. */
+gmg_status gmg_solve_adjoint(gmg_ctx* ctx, void* const* lambda, const void* const* g, double tol_rel,
+                             const gmg_params* p, gmg_solve_info* info);
+
+/* Gradient of a loss with respect to the cell-centred beta of each level, given the
+   solution phi and the adjoint lambda:  per face, dL/dbeta_face = -lambda^T (dA/dbeta_face) phi
+   (-(b/h^2)(phi_R - phi_L)(lambda_R - lambda_L) on an interior face; on a coarse/fine face
+   also the reflux row's share), then through the rule that made the face value from cell
+   beta (harmonic mean: d/dbeta_L = 2 beta_R^2 / (beta_L + beta_R)^2; wall and coarse/fine
+   faces: 1 for the adjacent cell).  Uses the beta last passed to gmg_set_bcoef_cell.
+   dbeta[l]: FP64 output in level l's layout (covered coarse cells get 0).  phi's and
+   lambda's ghosts are overwritten. */
+gmg_status gmg_beta_grad(gmg_ctx* ctx, void* const* dbeta, void* const* phi, void* const* lambda);
 
 /* ------------------------------------------------ individual hot-path steps */
 /* Each step acts on MG level m with caller buffers of element type dt in that level's

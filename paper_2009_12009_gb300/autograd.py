@@ -1,0 +1,110 @@
+"""Differentiable solves: torch.autograd.Function wrappers of the library's solve.
+
+Forward:  phi = A(beta)^-1 rhs by the multigrid solve (one level, or the two-level
+          composite form of Sec. "Operations between levels").
+Backward: lambda = A^-T dL/dphi by the adjoint solve (gmg_solve_adjoint), then
+          dL/drhs = lambda and dL/dbeta = -lambda^T (dA/dbeta) phi by the face-flux gradient
+          kernel (gmg_beta_grad), through the harmonic face mean to the cell beta.
+Both run in the library's kernels; this module only marshals tensors.
+
+Singular problems (all periodic, a = 0): the forward projects rhs onto the operator's range
+and returns phi with zero (volume-weighted) mean; the backward projects accordingly, so the
+gradients are those of that projected map.  Two levels: phi on coarse cells under the fine
+level is returned as 0 (those cells are not unknowns of the composite problem), and the
+rhs of those cells does not influence phi (its gradient is 0).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import gmg
+
+
+class _AmrSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, solver, rhs_c, rhs_f, beta_c, beta_f):
+        C = solver.ctx
+        C.set_coeffs(solver.a, solver.b, beta_c=beta_c.detach(), beta_f=beta_f.detach())
+        rc = C.pack_level(0, rhs_c.detach())
+        rf = C.pack_level(1, rhs_f.detach())
+        pc, pf, info = C.solve2(rc, rf, tol_rel=solver.tol, max_iter=solver.max_iter, project_mean=1)
+        if info.status != gmg.OK:
+            raise gmg.GmgError(info.status, "forward solve did not converge")
+        ctx.solver = solver
+        ctx.state = (pc, pf)
+        mask = torch.as_tensor(~C.covered, device=rhs_c.device, dtype=torch.float64)
+        ctx.mask = mask
+        solver.last_info = info
+        return C.unpack_level(0, pc) * mask, C.unpack_level(1, pf)
+
+    @staticmethod
+    def backward(ctx, g_c, g_f):
+        solver = ctx.solver
+        C = solver.ctx
+        pc, pf = ctx.state
+        gc = C.pack_level(0, (g_c * ctx.mask).contiguous())
+        gf = C.pack_level(1, g_f.contiguous())
+        lc, lf, info = C.solve_adjoint2(gc, gf, tol_rel=solver.tol, max_iter=solver.max_iter)
+        if info.status != gmg.OK:
+            raise gmg.GmgError(info.status, "adjoint solve did not converge")
+        solver.last_adjoint_info = info
+        dc, df = C.beta_grad2(pc, pf, lc, lf)
+        lam_c = C.unpack_level(0, lc) * ctx.mask
+        lam_f = C.unpack_level(1, lf)
+        return None, lam_c, lam_f, C.unpack_level(0, dc), C.unpack_level(1, df)
+
+
+class AmrSolve:
+    """phi_c, phi_f = AmrSolve(...)(rhs_c, rhs_f, beta_c, beta_f), differentiable in rhs and
+    beta.  Dense float64 CUDA tensors: coarse over the level-0 domain (nz, ny, nx), fine over
+    the bounding box of the fine boxes."""
+
+    def __init__(self, domain, coarse_boxes, fine_boxes, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0),
+                 prob_hi=(1.0, 1.0, 1.0), a=0.0, b=1.0, tol=1e-10, max_iter=100):
+        self.ctx = gmg.AmrContext(domain, coarse_boxes, fine_boxes, bc_lo, bc_hi, prob_lo, prob_hi,
+                                  stream=torch.cuda.current_stream().cuda_stream)
+        self.ctx.allocate(gmg.FP64)
+        self.a, self.b, self.tol, self.max_iter = a, b, tol, max_iter
+
+    def __call__(self, rhs_c, rhs_f, beta_c, beta_f):
+        return _AmrSolve.apply(self, rhs_c, rhs_f, beta_c, beta_f)
+
+
+class _Solve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, solver, rhs, beta):
+        C = solver.ctx
+        C.set_beta(beta.detach())
+        phi, info = C.solve(C.pack(rhs.detach()), tol_rel=solver.tol, max_iter=solver.max_iter, project_mean=1)
+        if info.status != gmg.OK:
+            raise gmg.GmgError(info.status, "forward solve did not converge")
+        ctx.solver = solver
+        ctx.phi = phi
+        return C.unpack(phi)
+
+    @staticmethod
+    def backward(ctx, g):
+        solver = ctx.solver
+        C = solver.ctx
+        lam, info = C.solve_adjoint(C.pack(g.contiguous()), tol_rel=solver.tol, max_iter=solver.max_iter)
+        if info.status != gmg.OK:
+            raise gmg.GmgError(info.status, "adjoint solve did not converge")
+        d = C.beta_grad(ctx.phi, lam)
+        return None, C.unpack(lam), C.unpack(d)
+
+
+class Solve:
+    """phi = Solve(...)(rhs, beta) on one level, differentiable in rhs and beta."""
+
+    def __init__(self, shape_xyz, bc="dirichlet", max_grid_size=64, prob_hi=(1.0, 1.0, 1.0), a=0.0, b=1.0,
+                 tol=1e-10, max_iter=100):
+        nx, ny, nz = shape_xyz
+        bcv = gmg.PERIODIC if bc == "periodic" else gmg.DIRICHLET0
+        self.ctx = gmg.Context(((0, 0, 0), (nx - 1, ny - 1, nz - 1)), [bcv] * 3, [bcv] * 3, prob_hi=prob_hi,
+                               max_grid_size=max_grid_size, stream=torch.cuda.current_stream().cuda_stream)
+        self.ctx.allocate(gmg.FP64)
+        self.ctx.set_scalars(a, b)
+        self.tol, self.max_iter = tol, max_iter
+
+    def __call__(self, rhs, beta):
+        return _Solve.apply(self, rhs, beta)

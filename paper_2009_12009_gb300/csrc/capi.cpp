@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/gmg.h"
+#include "amr_meta.h"
 #include "kernels.h"
 #include "meta.h"
 
@@ -105,6 +106,22 @@ struct gmg_ctx {
   bool profiling = false;
   std::vector<cudaEvent_t> ev_smooth, ev_resid;
   int n_ev_smooth = 0, n_ev_resid = 0;
+
+  // cell beta of level 0 as last set (ghosts filled), for beta gradients
+  double* betac_cell = nullptr;
+
+  // two-level composite form: AMR level 1 (ratio 2) over part of level 0
+  bool amr = false;
+  LevelMeta F;          // the fine level (one MG level; its coarse correction is level 0)
+  AmrHost amr_host;
+  AmrDev amrd;
+  LevelDev devf;
+  LevelBufs buff;       // fine coefficients and work fields
+  double *alphaf = nullptr, *bxf = nullptr, *byf = nullptr, *bzf = nullptr, *betaf_cell = nullptr;
+  double *crhs = nullptr, *frhs = nullptr, *cres = nullptr, *fres = nullptr;  // projected rhs, residual
+  double *ctmp = nullptr, *ftmp = nullptr, *czero = nullptr, *fzero = nullptr;
+  double *kc[9] = {}, *kf[9] = {};  // adjoint BiCGStab vectors
+  bool have_beta_f = false, have_alpha_f = false;
 
   int ns() const { return (int)geoms.size(); }
 };
@@ -243,6 +260,77 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
   double* by0 = (double*)cv.take(8 * ne0);
   double* bz0 = (double*)cv.take(8 * ne0);
   double* tmp0 = (double*)cv.take(8 * ne0);
+  double* betac = (double*)cv.take(8 * ne0);
+  if (fill) c->betac_cell = betac;
+  if (c->amr) {
+    const LevelMeta& M = c->F;
+    const AmrHost& H = c->amr_host;
+    const size_t nf = (size_t)M.nelem;
+    LevelDev D;
+    LevelBufs B;
+    D.nelem = M.nelem;
+    D.nsolves = 1;
+    D.active = active;
+    D.boxes = (const DevBox*)cv.take(sizeof(DevBox) * M.dbox.size());
+    D.geoms = (const DevGeom*)cv.take(sizeof(DevGeom) * M.geoms.size());
+    D.ghosts = (const GhostRect*)cv.take(sizeof(GhostRect) * M.ghosts.size());
+    D.ghost_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.ghost_chunks.size());
+    D.n_ghost_chunks = (int)M.ghost_chunks.size();
+    D.pair_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.pair_chunks.size());
+    D.n_pair_chunks = (int)M.pair_chunks.size();
+    D.pair_all_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.pair_all_chunks.size());
+    D.n_pair_all_chunks = (int)M.pair_all_chunks.size();
+    D.cell_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.cell_chunks.size());
+    D.n_cell_chunks = (int)M.cell_chunks.size();
+    D.coarse_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.coarse_chunks.size());
+    D.n_coarse_chunks = (int)M.coarse_chunks.size();
+    D.parent = (const int*)cv.take(sizeof(int) * M.parent.size());
+    D.solve_chunk_range = (const int*)cv.take(sizeof(int) * M.solve_chunk_range.size());
+    D.inv_count = (const double*)cv.take(sizeof(double) * M.inv_count.size());
+    maxchunks = std::max(maxchunks, D.n_cell_chunks);
+    B.acoef = (double*)cv.take(8 * nf);
+    B.wx = (double*)cv.take(8 * nf);
+    B.wy = (double*)cv.take(8 * nf);
+    B.wz = (double*)cv.take(8 * nf);
+    B.D = (double*)cv.take(8 * nf);
+    B.invD = (double*)cv.take(8 * nf);
+    B.e[DT_F64] = cv.take(8 * nf);
+    B.r[DT_F64] = cv.take(8 * nf);
+    AmrDev A;
+    A.cf = (const CfGhost*)cv.take(sizeof(CfGhost) * H.cf.size());
+    A.ncf = (int)H.cf.size();
+    A.rcells = (const RefluxCell*)cv.take(sizeof(RefluxCell) * H.rcells.size());
+    A.nrcell = (int)H.rcells.size();
+    A.rfaces = (const RefluxFace*)cv.take(sizeof(RefluxFace) * H.rfaces.size());
+    A.covered_list = (const int64_t*)cv.take(sizeof(int64_t) * H.covered_list.size());
+    A.ncov = (int)H.covered_list.size();
+    A.covered = (const unsigned char*)cv.take(H.covered.size());
+    A.cfidx = (const int*)cv.take(sizeof(int) * H.cfidx.size());
+    A.hf_over_hc = 0.5;
+    double* f5[5];
+    for (int q = 0; q < 5; ++q) f5[q] = (double*)cv.take(8 * nf);
+    double* cc[4];
+    for (int q = 0; q < 4; ++q) cc[q] = (double*)cv.take(8 * ne0);
+    double* ff[5];
+    for (int q = 0; q < 5; ++q) ff[q] = (double*)cv.take(8 * nf);
+    double *kc[9], *kf[9];
+    for (int q = 0; q < 9; ++q) {
+      kc[q] = (double*)cv.take(8 * ne0);
+      kf[q] = (double*)cv.take(8 * nf);
+    }
+    if (fill) {
+      c->devf = D;
+      c->buff = B;
+      c->amrd = A;
+      c->alphaf = f5[0]; c->bxf = f5[1]; c->byf = f5[2]; c->bzf = f5[3]; c->betaf_cell = f5[4];
+      c->crhs = cc[0]; c->cres = cc[1]; c->ctmp = cc[2]; c->czero = cc[3];
+      c->frhs = ff[0]; c->fres = ff[1]; c->ftmp = ff[2]; c->fzero = ff[3];
+      for (int q = 0; q < 9; ++q) {
+        c->kc[q] = kc[q];
+        c->kf[q] = kf[q];
+      }
+    }
+  }
   unsigned long long* nb = (unsigned long long*)cv.take(8 * (2 * ns + 8));
   double* partials = (double*)cv.take(8 * (size_t)maxchunks);
   double* scal = (double*)cv.take(8 * (2 * ns + 8));
@@ -298,6 +386,30 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.solve_chunk_range, M.solve_chunk_range))) return st;
     if ((st = upload(c, D.inv_count, M.inv_count))) return st;
   }
+  if (c->amr) {
+    const LevelMeta& M = c->F;
+    const LevelDev& D = c->devf;
+    const AmrHost& H = c->amr_host;
+    const AmrDev& A = c->amrd;
+    gmg_status st;
+    if ((st = upload(c, D.boxes, M.dbox))) return st;
+    if ((st = upload(c, D.geoms, dev_geoms(M)))) return st;
+    if ((st = upload(c, D.ghosts, M.ghosts))) return st;
+    if ((st = upload(c, D.ghost_chunks, M.ghost_chunks))) return st;
+    if ((st = upload(c, D.pair_chunks, M.pair_chunks))) return st;
+    if ((st = upload(c, D.pair_all_chunks, M.pair_all_chunks))) return st;
+    if ((st = upload(c, D.cell_chunks, M.cell_chunks))) return st;
+    if ((st = upload(c, D.coarse_chunks, M.coarse_chunks))) return st;
+    if ((st = upload(c, D.parent, M.parent))) return st;
+    if ((st = upload(c, D.solve_chunk_range, M.solve_chunk_range))) return st;
+    if ((st = upload(c, D.inv_count, M.inv_count))) return st;
+    if ((st = upload(c, A.cf, H.cf))) return st;
+    if ((st = upload(c, A.rcells, H.rcells))) return st;
+    if ((st = upload(c, A.rfaces, H.rfaces))) return st;
+    if ((st = upload(c, A.covered_list, H.covered_list))) return st;
+    if ((st = upload(c, A.covered, H.covered))) return st;
+    if ((st = upload(c, A.cfidx, H.cfidx))) return st;
+  }
   std::vector<int> ones(c->ns(), 1);
   gmg_status st = upload(c, c->active, ones);
   if (st) return st;
@@ -312,6 +424,10 @@ void reset_problem(gmg_ctx* c) {
   c->ws_bytes = 0;
   c->have_beta = c->have_alpha = false;
   c->coefs_dirty = true;
+  c->amr = false;
+  c->F = LevelMeta();
+  c->amr_host = AmrHost();
+  c->have_beta_f = c->have_alpha_f = false;
 }
 
 // Build the multigrid hierarchy from level-0 boxes (stored problem by problem).
@@ -367,6 +483,13 @@ gmg_status build_coefs(gmg_ctx* c) {
       launch_convert(DT_F64, DT_F32, B.D, B.fD, n, s);
       launch_convert(DT_F64, DT_F32, B.invD, B.finvD, n, s);
     }
+  }
+  if (c->amr) {
+    if (!c->have_beta_f) SETERR(c, GMG_ERR_STATE, "beta of AMR level 1 not set");
+    const LevelBufs& B = c->buff;
+    launch_acoef(c->devf, c->a, c->have_alpha_f ? c->alphaf : nullptr, B.acoef, s);
+    launch_faces_scale(c->devf, c->b, c->bxf, c->byf, c->bzf, B.wx, B.wy, B.wz, s);
+    launch_diag(c->devf, B.acoef, B.wx, B.wy, B.wz, B.D, B.invD, s);
   }
   // singular flag of the bottom problems
   for (int m = 0; m < nlev(c); ++m) {
@@ -654,6 +777,372 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   return worst;
 }
 
+// ------------------------------------------------------------ two-level composite
+
+Coefs coefs_fine(const gmg_ctx* c) {
+  Coefs k;
+  k.wx = c->buff.wx; k.wy = c->buff.wy; k.wz = c->buff.wz; k.D = c->buff.D; k.invD = c->buff.invD;
+  return k;
+}
+
+// fine ghosts: copies between fine boxes, then the coarse/fine ghosts (interpolated from
+// coarse field `cx`, or zero coarse data when cx is null)
+void fine_fill(gmg_ctx* c, double* f, const double* cx, int mode, cudaStream_t s) {
+  launch_fill(DT_F64, c->devf, f, -1, 0, s);
+  launch_cf_fill(c->amrd, f, cx, mode, s);
+}
+
+// composite residual r = rhs - A phi (fine cells, uncovered coarse cells; covered 0) and
+// ||r||_inf of each level into normbits[0] (fine) and normbits[1] (coarse)
+void comp_residual(gmg_ctx* c, double* pc, double* pf, const double* rc_in, const double* rf_in, double* rc,
+                   double* rf, unsigned long long* nb, cudaStream_t s) {
+  fine_fill(c, pf, pc, CF_INTERP, s);
+  launch_fill(DT_F64, c->dev[0], pc, -1, 0, s);
+  if (nb) cudaMemsetAsync(nb, 0, 16, s);
+  launch_residual(DT_F64, DT_F64, c->devf, pf, rf_in, coefs_fine(c), rf, nb, nullptr, s);
+  launch_residual(DT_F64, DT_F64, c->dev[0], pc, rc_in, coefs64(c, 0), rc, nullptr, nullptr, s);
+  launch_reflux(c->amrd, coefs64(c, 0), coefs_fine(c), pc, pf, rc, rc, 1, s);
+  launch_zero_covered(c->amrd, rc, s);
+  if (nb) launch_norm_max(c->dev[0], rc, nb + 1, s);
+}
+
+// one composite multigrid correction from residual (rc, rf): e_c in buf[0].e, e_f in buff.e
+void comp_correction(gmg_ctx* c, const gmg_params& p, const double* rc, const double* rf, cudaStream_t s) {
+  double* ef = (double*)c->buff.e[DT_F64];
+  double* ec = (double*)c->buf[0].e[DT_F64];
+  double* crhs = (double*)c->buf[0].r[DT_F64];
+  cudaMemsetAsync(ef, 0, 8 * (size_t)c->F.nelem, s);
+  for (int it = 0; it < p.nu1; ++it)
+    for (int colour = 0; colour < 2; ++colour) {
+      fine_fill(c, ef, nullptr, CF_INTERP, s);  // coarse correction 0
+      launch_smooth(DT_F64, c->devf, ef, rf, coefs_fine(c), colour, s);
+    }
+  fine_fill(c, ef, nullptr, CF_INTERP, s);
+  cudaMemcpyAsync(crhs, rc, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, s);
+  // covered cells: average of the fine correction residual r_f - A_f e_f
+  launch_resid_restrict(DT_F64, c->devf, c->dev[0], ef, rf, coefs_fine(c), crhs, s);
+  // uncovered cells next to the fine level: minus the fine correction's reflux
+  launch_reflux(c->amrd, coefs64(c, 0), coefs_fine(c), crhs, ef, crhs, crhs, 0, s);
+  vcycle(c, DT_F64, 0, p, s);
+  launch_prolong_add(DT_F64, c->devf, c->dev[0], ec, ef, s);
+  for (int it = 0; it < p.nu2; ++it)
+    for (int colour = 0; colour < 2; ++colour) {
+      fine_fill(c, ef, ec, CF_INTERP, s);
+      launch_smooth(DT_F64, c->devf, ef, rf, coefs_fine(c), colour, s);
+    }
+  launch_restrict(DT_F64, c->devf, c->dev[0], ef, ec, s);  // covered e_c := average of e_f
+}
+
+struct CompSums {
+  double vc, vf;  // cell volumes
+  double ncell_c, ncov, ncell_f;
+};
+
+CompSums comp_sizes(const gmg_ctx* c) {
+  CompSums z;
+  const SolveGeom& G = c->geoms[0];
+  z.vc = G.h[0] * G.h[1] * G.h[2];
+  z.vf = z.vc / 8.0;
+  z.ncell_c = (double)c->L[0].ncells;
+  z.ncov = (double)c->amr_host.covered_list.size();
+  z.ncell_f = (double)c->F.ncells;
+  return z;
+}
+
+// per-level sums of the valid cells of (xc, xf) (covered coarse entries must be zero)
+gmg_status comp_level_sums(gmg_ctx* c, const double* xc, const double* xf, double* sc, double* sf) {
+  cudaStream_t s = c->stream;
+  launch_sum(c->dev[0], xc, c->partials, c->scal, s);
+  launch_sum(c->devf, xf, c->partials, c->scal + 1, s);  // same stream: after the first
+  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 16, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  const CompSums z = comp_sizes(c);
+  *sc = c->h_scal[0] * z.ncell_c;  // launch_sum returns means over every cell of the level
+  *sf = c->h_scal[1] * z.ncell_f;
+  return GMG_OK;
+}
+
+// x_c (uncovered) += kc, x_f += kf  (covered coarse entries cleared afterwards)
+gmg_status comp_add_const(gmg_ctx* c, double* xc, double* xf, double kc, double kf) {
+  cudaStream_t s = c->stream;
+  c->h_scal[2] = kc;
+  c->h_scal[3] = kf;
+  CK(c, cudaMemcpyAsync(c->scal + 2, c->h_scal + 2, 16, cudaMemcpyHostToDevice, s));
+  launch_add_scalar(c->dev[0], xc, c->scal + 2, 1.0, s);
+  launch_add_scalar(c->devf, xf, c->scal + 3, 1.0, s);
+  launch_zero_covered(c->amrd, xc, s);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status read_norms(gmg_ctx* c, double* rn) {
+  CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 16, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaGetLastError());
+  *rn = std::max(bits_to_double(c->h_bits[0]), bits_to_double(c->h_bits[1]));
+  if (std::isnan(bits_to_double(c->h_bits[0])) || std::isnan(bits_to_double(c->h_bits[1]))) *rn = NAN;
+  return GMG_OK;
+}
+
+// Composite multigrid solve of the two-level problem (the oracle's two-level iteration):
+// residual, fine pre-smoothing with homogeneous coarse/fine ghosts, coarse right-hand side
+// (restricted fine correction residual under the fine level, reflux-corrected residual
+// next to it), coarse V-cycle, interpolation, fine post-smoothing, average-down, update.
+gmg_status solve_amr(gmg_ctx* c, double* pc, double* pf, const double* rc_user, const double* rf_user, double tol_rel,
+                     double tol_abs, const gmg_params& p, gmg_solve_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = c->stream;
+  const int64_t l0 = kernel_launch_count();
+  if (info) memset(info, 0, sizeof(*info));
+  const size_t nc = 8 * (size_t)c->L[0].nelem, nf = 8 * (size_t)c->F.nelem;
+  CK(c, cudaMemcpyAsync(c->crhs, rc_user, nc, cudaMemcpyDeviceToDevice, s));
+  CK(c, cudaMemcpyAsync(c->frhs, rf_user, nf, cudaMemcpyDeviceToDevice, s));
+  launch_zero_covered(c->amrd, c->crhs, s);
+  CK(c, cudaMemsetAsync(c->normbits, 0, 16, s));
+  launch_norm_max(c->devf, c->frhs, c->normbits, s);
+  launch_norm_max(c->dev[0], c->crhs, c->normbits + 1, s);
+  double rhsnorm;
+  gmg_status st = read_norms(c, &rhsnorm);
+  if (st) return st;
+  if (!std::isfinite(rhsnorm)) SETERR(c, GMG_ERR_BAD_INPUT, "rhs is not finite");
+  const bool sing = singular(c, 0);
+  const CompSums z = comp_sizes(c);
+  if (sing) {  // project onto zero volume-weighted mean (the range of the composite operator)
+    double sc, sf;
+    if ((st = comp_level_sums(c, c->crhs, c->frhs, &sc, &sf))) return st;
+    const double vol = z.vf * z.ncell_f + z.vc * (z.ncell_c - z.ncov);
+    const double mean = (z.vf * sf + z.vc * sc) / vol;
+    if (std::fabs(mean) > 1e-12 * rhsnorm && !p.project_mean)
+      SETERR(c, GMG_ERR_BAD_INPUT, "singular problem with a nonzero-mean rhs (set project_mean)");
+    if ((st = comp_add_const(c, c->crhs, c->frhs, -mean, -mean))) return st;
+  }
+  const double target = std::max(tol_rel * rhsnorm, tol_abs);
+  CK(c, cudaMemsetAsync(pc, 0, nc, s));
+  CK(c, cudaMemsetAsync(pf, 0, nf, s));
+  comp_residual(c, pc, pf, c->crhs, c->frhs, c->cres, c->fres, c->normbits, s);
+  double rn;
+  if ((st = read_norms(c, &rn))) return st;
+  std::vector<double> hist{rn};
+  int it = 0;
+  gmg_status result = GMG_OK;
+  while (!(rn <= target) && it < p.max_iter) {
+    comp_correction(c, p, c->cres, c->fres, s);
+    launch_add_correction(DT_F64, c->devf, pf, c->buff.e[DT_F64], s);
+    launch_add_correction(DT_F64, c->dev[0], pc, c->buf[0].e[DT_F64], s);
+    launch_restrict(DT_F64, c->devf, c->dev[0], pf, pc, s);  // covered := average of fine
+    comp_residual(c, pc, pf, c->crhs, c->frhs, c->cres, c->fres, c->normbits, s);
+    if ((st = read_norms(c, &rn))) return st;
+    ++it;
+    hist.push_back(rn);
+    if (!std::isfinite(rn)) {
+      result = GMG_ERR_DIVERGED;
+      break;
+    }
+  }
+  if (result == GMG_OK && !(rn <= target)) result = GMG_ERR_NOT_CONVERGED;
+  if (sing) {  // zero volume-weighted mean over the composite unknowns
+    launch_zero_covered(c->amrd, pc, s);
+    double sc, sf;
+    if ((st = comp_level_sums(c, pc, pf, &sc, &sf))) return st;
+    const double mean = (z.vf * sf + z.vc * sc) / (z.vf * z.ncell_f + z.vc * (z.ncell_c - z.ncov));
+    if ((st = comp_add_const(c, pc, pf, -mean, -mean))) return st;
+  }
+  launch_restrict(DT_F64, c->devf, c->dev[0], pf, pc, s);
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  if (info) {
+    info->iterations = it;
+    info->status = result;
+    info->rhs_norm = rhsnorm;
+    info->initial_resid = hist[0];
+    info->final_resid = rn;
+    info->hist_len = (int)std::min<size_t>(hist.size(), 256);
+    for (int i = 0; i < info->hist_len; ++i) info->resid_hist[i] = hist[i];
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->kernel_launches = kernel_launch_count() - l0;
+  }
+  if (result == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
+  if (result == GMG_ERR_DIVERGED) c->err = "residual is not finite";
+  return result;
+}
+
+// out = A x (composite); x's ghosts are overwritten; covered coarse entries of out are 0
+void comp_apply(gmg_ctx* c, double* xc, double* xf, double* outc, double* outf, cudaStream_t s) {
+  cudaMemsetAsync(c->czero, 0, 8 * (size_t)c->L[0].nelem, s);
+  cudaMemsetAsync(c->fzero, 0, 8 * (size_t)c->F.nelem, s);
+  comp_residual(c, xc, xf, c->czero, c->fzero, outc, outf, nullptr, s);
+  launch_scale_valid(c->dev[0], outc, -1.0, s);
+  launch_scale_valid(c->devf, outf, -1.0, s);
+}
+
+// out = A^T y (composite): the level stencils (symmetric; the fine one with zero coarse/fine
+// ghosts, the coarse one with covered entries of y zero) plus the transposed
+// interpolation and reflux couplings.  y's ghosts are overwritten; yc's covered entries are
+// cleared.
+void comp_apply_transpose(gmg_ctx* c, double* yc, double* yf, double* outc, double* outf, cudaStream_t s) {
+  cudaMemsetAsync(c->czero, 0, 8 * (size_t)c->L[0].nelem, s);
+  cudaMemsetAsync(c->fzero, 0, 8 * (size_t)c->F.nelem, s);
+  launch_zero_covered(c->amrd, yc, s);
+  fine_fill(c, yf, nullptr, CF_ZERO, s);
+  launch_fill(DT_F64, c->dev[0], yc, -1, 0, s);
+  launch_residual(DT_F64, DT_F64, c->devf, yf, c->fzero, coefs_fine(c), outf, nullptr, nullptr, s);
+  launch_residual(DT_F64, DT_F64, c->dev[0], yc, c->czero, coefs64(c, 0), outc, nullptr, nullptr, s);
+  launch_scale_valid(c->dev[0], outc, -1.0, s);
+  launch_scale_valid(c->devf, outf, -1.0, s);
+  launch_composite_transpose_couplings(c->amrd, coefs64(c, 0), coefs_fine(c), yc, yf, outc, outf, s);
+  launch_zero_covered(c->amrd, outc, s);
+}
+
+gmg_status comp_dot(gmg_ctx* c, const double* xc, const double* xf, const double* yc, const double* yf, double* out) {
+  cudaStream_t s = c->stream;
+  launch_dot(c->dev[0], xc, yc, c->partials, c->scal, s);
+  launch_dot(c->devf, xf, yf, c->partials, c->scal + 1, s);  // same stream: after the first
+  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 16, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  *out = c->h_scal[0] + c->h_scal[1];
+  return GMG_OK;
+}
+
+gmg_status comp_norm(gmg_ctx* c, const double* xc, const double* xf, double* out) {
+  CK(c, cudaMemsetAsync(c->normbits, 0, 16, c->stream));
+  launch_norm_max(c->devf, xf, c->normbits, c->stream);
+  launch_norm_max(c->dev[0], xc, c->normbits + 1, c->stream);
+  return read_norms(c, out);
+}
+
+// Adjoint solve A^T lambda = g of the composite operator: BiCGStab preconditioned on the
+// right by the composite multigrid correction of A.  Singular problems: g is projected
+// onto the range of A^T (g - V sum(g)/sum(V), V = cell volumes) and lambda onto zero sum.
+gmg_status solve_adjoint_amr(gmg_ctx* c, double* lc, double* lf, const double* gc_user, const double* gf_user,
+                             double tol_rel, const gmg_params& p, gmg_solve_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = c->stream;
+  const int64_t l0 = kernel_launch_count();
+  if (info) memset(info, 0, sizeof(*info));
+  const int64_t nc = c->L[0].nelem, nf = c->F.nelem;
+  // vectors: 0 r, 1 rhat, 2 p, 3 v, 4 s, 5 t, 6 phat, 7 shat, 8 g
+  double **kc = c->kc, **kf = c->kf;
+  CK(c, cudaMemcpyAsync(kc[8], gc_user, 8 * (size_t)nc, cudaMemcpyDeviceToDevice, s));
+  CK(c, cudaMemcpyAsync(kf[8], gf_user, 8 * (size_t)nf, cudaMemcpyDeviceToDevice, s));
+  launch_zero_covered(c->amrd, kc[8], s);
+  const CompSums z = comp_sizes(c);
+  gmg_status st;
+  const bool sing = singular(c, 0);
+  if (sing) {
+    double sc, sf;
+    if ((st = comp_level_sums(c, kc[8], kf[8], &sc, &sf))) return st;
+    const double mu = (sc + sf) / (z.vf * z.ncell_f + z.vc * (z.ncell_c - z.ncov));
+    if ((st = comp_add_const(c, kc[8], kf[8], -mu * z.vc, -mu * z.vf))) return st;
+  }
+  double gnorm;
+  if ((st = comp_norm(c, kc[8], kf[8], &gnorm))) return st;
+  CK(c, cudaMemsetAsync(lc, 0, 8 * (size_t)nc, s));
+  CK(c, cudaMemsetAsync(lf, 0, 8 * (size_t)nf, s));
+  for (int q = 0; q < 8; ++q) {
+    CK(c, cudaMemsetAsync(kc[q], 0, 8 * (size_t)nc, s));
+    CK(c, cudaMemsetAsync(kf[q], 0, 8 * (size_t)nf, s));
+  }
+  launch_axpby(nc, 1.0, kc[8], 0.0, kc[8], kc[0], s);
+  launch_axpby(nf, 1.0, kf[8], 0.0, kf[8], kf[0], s);
+  launch_axpby(nc, 1.0, kc[8], 0.0, kc[8], kc[1], s);
+  launch_axpby(nf, 1.0, kf[8], 0.0, kf[8], kf[1], s);
+  const double target = tol_rel * gnorm;
+  double rho_old = 1.0, alpha = 1.0, omega = 1.0, rn = gnorm;
+  std::vector<double> hist{rn};
+  int it = 0;
+  gmg_status result = GMG_OK;
+  // Preconditioner for A^T.  The composite operator is a flux divergence per cell volume,
+  // A = V^-1 K with K nearly symmetric, so A^T = K V^-1 = V A V^-1 (exactly so away from
+  // the coarse/fine couplings).  With M the composite multigrid correction (M ~ A^-1), the
+  // preconditioner is V M V^-1: scale the fine part of the input by V_c / V_f = 8, apply M,
+  // scale the fine part of the output by 1/8.  V^-1 also maps the range of A^T (zero sum)
+  // onto the range of A (zero volume-weighted sum) for the singular problem.
+  auto precond = [&](double* inc, double* inf, double* outc, double* outf) {
+    launch_axpby(nc, 1.0, inc, 0.0, inc, c->ctmp, s);
+    launch_axpby(nf, 8.0, inf, 0.0, inf, c->ftmp, s);
+    comp_correction(c, p, c->ctmp, c->ftmp, s);
+    launch_axpby(nc, 1.0, (const double*)c->buf[0].e[DT_F64], 0.0, (const double*)c->buf[0].e[DT_F64], outc, s);
+    launch_axpby(nf, 0.125, (const double*)c->buff.e[DT_F64], 0.0, (const double*)c->buff.e[DT_F64], outf, s);
+  };
+  while (!(rn <= target) && it < p.max_iter) {
+    ++it;
+    double rho;
+    if ((st = comp_dot(c, kc[1], kf[1], kc[0], kf[0], &rho))) return st;
+    if (std::fabs(rho) < 1e-300) break;
+    const double beta = (rho / rho_old) * (alpha / omega);
+    // p = r + beta (p - omega v)
+    launch_axpby(nc, 1.0, kc[2], -omega, kc[3], kc[2], s);
+    launch_axpby(nf, 1.0, kf[2], -omega, kf[3], kf[2], s);
+    launch_axpby(nc, 1.0, kc[0], beta, kc[2], kc[2], s);
+    launch_axpby(nf, 1.0, kf[0], beta, kf[2], kf[2], s);
+    precond(kc[2], kf[2], kc[6], kf[6]);
+    launch_axpby(nc, 1.0, kc[6], 0.0, kc[6], c->ctmp, s);
+    launch_axpby(nf, 1.0, kf[6], 0.0, kf[6], c->ftmp, s);
+    comp_apply_transpose(c, c->ctmp, c->ftmp, kc[3], kf[3], s);
+    double rv;
+    if ((st = comp_dot(c, kc[1], kf[1], kc[3], kf[3], &rv))) return st;
+    if (std::fabs(rv) < 1e-300) break;
+    alpha = rho / rv;
+    launch_axpby(nc, 1.0, kc[0], -alpha, kc[3], kc[4], s);
+    launch_axpby(nf, 1.0, kf[0], -alpha, kf[3], kf[4], s);
+    double sn;
+    if ((st = comp_norm(c, kc[4], kf[4], &sn))) return st;
+    if (sn <= target) {
+      launch_axpby(nc, 1.0, lc, alpha, kc[6], lc, s);
+      launch_axpby(nf, 1.0, lf, alpha, kf[6], lf, s);
+      rn = sn;
+      hist.push_back(rn);
+      break;
+    }
+    precond(kc[4], kf[4], kc[7], kf[7]);
+    launch_axpby(nc, 1.0, kc[7], 0.0, kc[7], c->ctmp, s);
+    launch_axpby(nf, 1.0, kf[7], 0.0, kf[7], c->ftmp, s);
+    comp_apply_transpose(c, c->ctmp, c->ftmp, kc[5], kf[5], s);
+    double tt, ts;
+    if ((st = comp_dot(c, kc[5], kf[5], kc[5], kf[5], &tt))) return st;
+    if ((st = comp_dot(c, kc[5], kf[5], kc[4], kf[4], &ts))) return st;
+    if (tt == 0.0) break;
+    omega = ts / tt;
+    launch_axpby(nc, 1.0, lc, alpha, kc[6], lc, s);
+    launch_axpby(nf, 1.0, lf, alpha, kf[6], lf, s);
+    launch_axpby(nc, 1.0, lc, omega, kc[7], lc, s);
+    launch_axpby(nf, 1.0, lf, omega, kf[7], lf, s);
+    launch_axpby(nc, 1.0, kc[4], -omega, kc[5], kc[0], s);
+    launch_axpby(nf, 1.0, kf[4], -omega, kf[5], kf[0], s);
+    if ((st = comp_norm(c, kc[0], kf[0], &rn))) return st;
+    hist.push_back(rn);
+    if (!std::isfinite(rn)) {
+      result = GMG_ERR_DIVERGED;
+      break;
+    }
+    rho_old = rho;
+  }
+  if (result == GMG_OK && !(rn <= target)) result = GMG_ERR_NOT_CONVERGED;
+  launch_zero_covered(c->amrd, lc, s);
+  if (sing) {  // remove the null-space component of A^T (span of V): zero plain sum
+    double sc, sf;
+    if ((st = comp_level_sums(c, lc, lf, &sc, &sf))) return st;
+    const double a = (sc + sf) / (z.vf * z.ncell_f + z.vc * (z.ncell_c - z.ncov));
+    if ((st = comp_add_const(c, lc, lf, -a * z.vc, -a * z.vf))) return st;
+  }
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  if (info) {
+    info->iterations = it;
+    info->status = result;
+    info->rhs_norm = gnorm;
+    info->initial_resid = hist[0];
+    info->final_resid = rn;
+    info->hist_len = (int)std::min<size_t>(hist.size(), 256);
+    for (int i = 0; i < info->hist_len; ++i) info->resid_hist[i] = hist[i];
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->kernel_launches = kernel_launch_count() - l0;
+  }
+  if (result == GMG_ERR_NOT_CONVERGED) c->err = "adjoint solve not converged within max_iter";
+  return result;
+}
+
 gmg_status ensure_pinned(gmg_ctx* c) {
   const size_t need = (size_t)std::max(1, c->ns()) * 3 + 16;
   if (c->h_cap >= need) return GMG_OK;
@@ -752,10 +1241,9 @@ gmg_status gmg_define_domain(gmg_ctx* c, const int lo[3], const int hi[3], const
 }
 
 gmg_status gmg_define_level(gmg_ctx* c, int lev, int nboxes, const int* lohi, int ref_ratio) {
-  (void)ref_ratio;
   if (!c) return GMG_ERR_BAD_INPUT;
   if (!c->have_domain || c->ns() != 1) SETERR(c, GMG_ERR_STATE, "define one domain first (gmg_define_domain)");
-  if (lev != 0) SETERR(c, GMG_ERR_BAD_INPUT, "only AMR level 0 is supported by gmg_define_level");
+  if (lev != 0 && lev != 1) SETERR(c, GMG_ERR_BAD_INPUT, "AMR levels 0 and 1 are supported");
   if (nboxes <= 0 || !lohi) SETERR(c, GMG_ERR_BAD_INPUT, "no boxes");
   std::vector<Box> boxes(nboxes);
   for (int b = 0; b < nboxes; ++b)
@@ -763,7 +1251,40 @@ gmg_status gmg_define_level(gmg_ctx* c, int lev, int nboxes, const int* lohi, in
       boxes[b].lo[d] = lohi[6 * b + d];
       boxes[b].hi[d] = lohi[6 * b + 3 + d];
     }
-  return build_hierarchy(c, boxes, std::vector<int>(boxes.size(), 0));
+  if (lev == 0) return build_hierarchy(c, boxes, std::vector<int>(boxes.size(), 0));
+  // AMR level 1: ratio 2 over part of level 0 (Sec. "Basic data structures": refinement
+  // ratio between levels; proper nesting inside level 0)
+  if (c->L.empty()) SETERR(c, GMG_ERR_STATE, "define AMR level 0 first");
+  if (ref_ratio != 2) SETERR(c, GMG_ERR_BAD_INPUT, "only refinement ratio 2 is supported");
+  SolveGeom G = c->geoms[0];
+  for (int d = 0; d < 3; ++d) {
+    G.domain.lo[d] = 2 * G.domain.lo[d];
+    G.domain.hi[d] = 2 * G.domain.hi[d] + 1;
+    G.h[d] *= 0.5;
+  }
+  std::string e = validate_boxes(boxes, G.domain, false);
+  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, "level 1: " + e);
+  drop_graphs(c);
+  c->ws = nullptr;
+  c->ws_bytes = 0;
+  c->have_beta = c->have_alpha = c->have_beta_f = c->have_alpha_f = false;
+  c->coefs_dirty = true;
+  LevelMeta F;
+  F.allow_cf = true;
+  F.boxes = boxes;
+  F.box_solve.assign(boxes.size(), 0);
+  F.geoms = {G};
+  F.solve_present = {1};
+  F.solve_bottom = {0};
+  e = finalize_level(F);
+  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, "level 1: " + e);
+  AmrHost H;
+  e = build_amr(c->L[0], F, H);
+  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, "level 1: " + e);
+  c->F = F;
+  c->amr_host = H;
+  c->amr = true;
+  return GMG_OK;
 }
 
 gmg_status gmg_chop_domain(gmg_ctx* c, int lev, int mgs) {
@@ -869,8 +1390,65 @@ gmg_status gmg_mg_layout(const gmg_ctx* c, int m, int dt, int64_t* nelems, int64
 }
 
 gmg_status gmg_layout(const gmg_ctx* c, int lev, int64_t* nelems, int64_t* offs) {
-  if (lev != 0) return GMG_ERR_BAD_INPUT;
-  return gmg_mg_layout(c, 0, DT_F64, nelems, offs, nullptr);
+  if (!c) return GMG_ERR_BAD_INPUT;
+  if (lev == 0) return gmg_mg_layout(c, 0, DT_F64, nelems, offs, nullptr);
+  if (lev != 1 || !c->amr) return GMG_ERR_BAD_INPUT;
+  if (nelems) *nelems = c->F.nelem;
+  if (offs)
+    for (size_t b = 0; b < c->F.dbox.size(); ++b) offs[b] = c->F.dbox[b].off;
+  return GMG_OK;
+}
+
+gmg_status gmg_amr_level_boxes(const gmg_ctx* c, int lev, int* nboxes, int* lohi, int* row_strides) {
+  if (!c || (lev != 0 && lev != 1) || (lev == 1 && !c->amr) || c->L.empty()) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = lev ? c->F : c->L[0];
+  if (nboxes) *nboxes = (int)M.boxes.size();
+  for (size_t b = 0; b < M.boxes.size(); ++b) {
+    if (lohi)
+      for (int d = 0; d < 3; ++d) {
+        lohi[6 * b + d] = M.boxes[b].lo[d];
+        lohi[6 * b + 3 + d] = M.boxes[b].hi[d];
+      }
+    if (row_strides) row_strides[b] = M.dbox[b].sx;
+  }
+  return GMG_OK;
+}
+
+// dense (nz, ny, nx) array over the bounding box of AMR level lev's boxes <-> boxed layout
+gmg_status gmg_pack_amr(gmg_ctx* c, int lev, const double* dense, double* boxed) {
+  if (!c || (lev != 0 && lev != 1)) return GMG_ERR_BAD_INPUT;
+  if (lev == 0) return gmg_pack_solve(c, 0, DT_F64, 0, dense, boxed);
+  if (!c->amr) SETERR(c, GMG_ERR_STATE, "no AMR level 1");
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  Box bb = c->F.boxes[0];
+  for (const Box& B : c->F.boxes)
+    for (int d = 0; d < 3; ++d) {
+      bb.lo[d] = std::min(bb.lo[d], B.lo[d]);
+      bb.hi[d] = std::max(bb.hi[d], B.hi[d]);
+    }
+  int dn[3] = {bb.n(0), bb.n(1), bb.n(2)};
+  launch_pack(DT_F64, c->devf, bb.lo, dn, dense, boxed, c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_unpack_amr(gmg_ctx* c, int lev, const double* boxed, double* dense) {
+  if (!c || (lev != 0 && lev != 1)) return GMG_ERR_BAD_INPUT;
+  if (lev == 0) return gmg_unpack_solve(c, 0, DT_F64, 0, boxed, dense);
+  if (!c->amr) SETERR(c, GMG_ERR_STATE, "no AMR level 1");
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  Box bb = c->F.boxes[0];
+  for (const Box& B : c->F.boxes)
+    for (int d = 0; d < 3; ++d) {
+      bb.lo[d] = std::min(bb.lo[d], B.lo[d]);
+      bb.hi[d] = std::max(bb.hi[d], B.hi[d]);
+    }
+  int dn[3] = {bb.n(0), bb.n(1), bb.n(2)};
+  launch_unpack(DT_F64, c->devf, bb.lo, dn, boxed, dense, c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
 }
 
 gmg_status gmg_pack_solve(gmg_ctx* c, int m, int dt, int solve, const double* dense, void* boxed) {
@@ -921,7 +1499,13 @@ gmg_status gmg_set_acoef(gmg_ctx* c, int lev, const double* alpha) {
   if (!c) return GMG_ERR_BAD_INPUT;
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
-  if (lev != 0 || !alpha) SETERR(c, GMG_ERR_BAD_INPUT, "alpha: only level 0, non-null");
+  if (!alpha || lev < 0 || lev > 1 || (lev == 1 && !c->amr)) SETERR(c, GMG_ERR_BAD_INPUT, "alpha: bad level or null");
+  if (lev == 1) {
+    CK(c, cudaMemcpyAsync(c->alphaf, alpha, 8 * (size_t)c->F.nelem, cudaMemcpyDeviceToDevice, c->stream));
+    c->have_alpha_f = true;
+    c->coefs_dirty = true;
+    return GMG_OK;
+  }
   CK(c, cudaMemcpyAsync(c->alpha0, alpha, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, c->stream));
   c->have_alpha = true;
   c->coefs_dirty = true;
@@ -932,14 +1516,25 @@ gmg_status gmg_set_bcoef_cell(gmg_ctx* c, int lev, const double* beta) {
   if (!c) return GMG_ERR_BAD_INPUT;
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
-  if (lev != 0 || !beta) SETERR(c, GMG_ERR_BAD_INPUT, "beta: only level 0, non-null");
+  if (!beta || lev < 0 || lev > 1 || (lev == 1 && !c->amr)) SETERR(c, GMG_ERR_BAD_INPUT, "beta: bad level or null");
   cudaStream_t s = c->stream;
-  CK(c, cudaMemcpyAsync(c->tmp0, beta, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, s));
-  launch_fill(DT_F64, c->dev[0], c->tmp0, -1, 1, s);
-  launch_faces_from_cell(c->dev[0], c->tmp0, c->bx0, c->by0, c->bz0, s);
+  if (lev == 1) {  // coarse/fine faces take the fine cell's beta: ghost := adjacent cell
+    CK(c, cudaMemcpyAsync(c->betaf_cell, beta, 8 * (size_t)c->F.nelem, cudaMemcpyDeviceToDevice, s));
+    launch_fill(DT_F64, c->devf, c->betaf_cell, -1, 1, s);
+    launch_cf_fill(c->amrd, c->betaf_cell, nullptr, CF_COPY, s);
+    launch_faces_from_cell(c->devf, c->betaf_cell, c->bxf, c->byf, c->bzf, s);
+    CK(c, cudaGetLastError());
+    c->have_beta_f = true;
+    c->coefs_dirty = true;
+    return c->have_beta ? build_coefs(c) : GMG_OK;
+  }
+  CK(c, cudaMemcpyAsync(c->betac_cell, beta, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, s));
+  launch_fill(DT_F64, c->dev[0], c->betac_cell, -1, 1, s);
+  launch_faces_from_cell(c->dev[0], c->betac_cell, c->bx0, c->by0, c->bz0, s);
   CK(c, cudaGetLastError());
   c->have_beta = true;
   c->coefs_dirty = true;
+  if (c->amr && !c->have_beta_f) return GMG_OK;  // built once level 1's beta is set
   return build_coefs(c);
 }
 
@@ -1121,6 +1716,12 @@ gmg_status gmg_apply(gmg_ctx* c, void* const* out, void* const* phi) {
   if (st) return st;
   if ((st = build_coefs(c))) return st;
   cudaStream_t s = c->stream;
+  if (c->amr) {
+    if (!out[1] || !phi[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
+    comp_apply(c, (double*)phi[0], (double*)phi[1], (double*)out[0], (double*)out[1], s);
+    CK(c, cudaGetLastError());
+    return GMG_OK;
+  }
   // out = -(0 - A phi): the residual pass with a zero right-hand side, negated
   launch_fill(DT_F64, c->dev[0], phi[0], -1, 0, s);
   CK(c, cudaMemsetAsync(c->tmp0, 0, 8 * (size_t)c->L[0].nelem, s));
@@ -1141,6 +1742,12 @@ gmg_status gmg_solve(gmg_ctx* c, void* const* phiv, const void* const* rhsv, dou
   if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "context holds several problems: use gmg_batch_solve");
   if ((st = params_ok(c, p))) return st;
   if ((st = build_coefs(c))) return st;
+  if (c->amr) {
+    if (!phiv[1] || !rhsv[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
+    if (p.precision != GMG_FP64) SETERR(c, GMG_ERR_BAD_INPUT, "the two-level solve runs in FP64");
+    return solve_amr(c, (double*)phiv[0], (double*)phiv[1], (const double*)rhsv[0], (const double*)rhsv[1], tol_rel,
+                     tol_abs, p, info);
+  }
   return solve_impl(c, (double*)phiv[0], (const double*)rhsv[0], tol_rel, tol_abs, p, info);
 }
 
@@ -1155,6 +1762,71 @@ gmg_status gmg_batch_solve(gmg_ctx* c, void* phi, const void* rhs, double tol_re
   if ((st = params_ok(c, p))) return st;
   if ((st = build_coefs(c))) return st;
   return solve_impl(c, (double*)phi, (const double*)rhs, tol_rel, tol_abs, p, infos);
+}
+
+gmg_status gmg_apply_transpose(gmg_ctx* c, void* const* out, void* const* y) {
+  if (!c || !out || !y || !out[0] || !y[0]) return GMG_ERR_BAD_INPUT;
+  if (!c->amr) return gmg_apply(c, out, y);  // one level: A is symmetric
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if ((st = build_coefs(c))) return st;
+  if (!out[1] || !y[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
+  comp_apply_transpose(c, (double*)y[0], (double*)y[1], (double*)out[0], (double*)out[1], c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_solve_adjoint(gmg_ctx* c, void* const* lambda, const void* const* g, double tol_rel,
+                             const gmg_params* pp, gmg_solve_info* info) {
+  if (!c || !lambda || !g || !lambda[0] || !g[0]) return GMG_ERR_BAD_INPUT;
+  gmg_params p;
+  gmg_default_params(&p);
+  if (pp) p = *pp;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "adjoint: single-problem contexts only");
+  if ((st = params_ok(c, p))) return st;
+  if ((st = build_coefs(c))) return st;
+  if (!c->amr) {  // symmetric operator: the adjoint solve is a forward solve (mean projected)
+    p.project_mean = 1;
+    return solve_impl(c, (double*)lambda[0], (const double*)g[0], tol_rel, 0.0, p, info);
+  }
+  if (!lambda[1] || !g[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
+  p.precision = GMG_FP64;
+  return solve_adjoint_amr(c, (double*)lambda[0], (double*)lambda[1], (const double*)g[0], (const double*)g[1],
+                           tol_rel, p, info);
+}
+
+gmg_status gmg_beta_grad(gmg_ctx* c, void* const* dbeta, void* const* phi, void* const* lambda) {
+  if (!c || !dbeta || !phi || !lambda || !dbeta[0] || !phi[0] || !lambda[0]) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if ((st = build_coefs(c))) return st;
+  if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "beta gradient: single-problem contexts only");
+  cudaStream_t s = c->stream;
+  double* pc = (double*)phi[0];
+  double* lc = (double*)lambda[0];
+  if (c->amr) {
+    if (!dbeta[1] || !phi[1] || !lambda[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass both levels");
+    double* pf = (double*)phi[1];
+    double* lf = (double*)lambda[1];
+    launch_zero_covered(c->amrd, lc, s);
+    fine_fill(c, pf, pc, CF_INTERP, s);
+    launch_fill(DT_F64, c->devf, lf, -1, 0, s);
+    launch_fill(DT_F64, c->dev[0], pc, -1, 0, s);
+    launch_fill(DT_F64, c->dev[0], lc, -1, 0, s);
+    launch_grad_beta(c->devf, pf, lf, c->betaf_cell, c->b, c->amrd.cfidx, c->amrd.cf, lc, c->amrd.hf_over_hc,
+                     nullptr, (double*)dbeta[1], s);
+    launch_grad_beta(c->dev[0], pc, lc, c->betac_cell, c->b, nullptr, nullptr, nullptr, 0.5, c->amrd.covered,
+                     (double*)dbeta[0], s);
+  } else {
+    launch_fill(DT_F64, c->dev[0], pc, -1, 0, s);
+    launch_fill(DT_F64, c->dev[0], lc, -1, 0, s);
+    launch_grad_beta(c->dev[0], pc, lc, c->betac_cell, c->b, nullptr, nullptr, nullptr, 0.5, nullptr,
+                     (double*)dbeta[0], s);
+  }
+  CK(c, cudaGetLastError());
+  return GMG_OK;
 }
 
 }  // extern "C"

@@ -70,6 +70,7 @@ std::vector<Box> chop(const Box& dom, int mgs) {
 // reflection rectangle.  Edge and corner ghosts are not needed by the 7-point stencil.
 static std::string build_ghosts(LevelMeta& L) {
   L.ghosts.clear();
+  L.cf_slabs.clear();
   const int nb = (int)L.boxes.size();
   // boxes per solve
   std::vector<std::vector<int>> members(L.geoms.size());
@@ -126,8 +127,15 @@ static std::string build_ghosts(LevelMeta& L) {
             covered += I.volume();
           }
         }
-        if (covered != slab.volume())
-          return "ghost cells of box " + std::to_string(b) + " are not covered by the level (coarse/fine boundary)";
+        if (covered != slab.volume()) {
+          if (L.allow_cf && covered == 0) {  // a whole face on the coarse/fine boundary
+            L.cf_slabs.push_back({b, d, side});
+            continue;
+          }
+          return "ghost cells of box " + std::to_string(b) +
+                 (L.allow_cf ? " are partly covered by other boxes of the level (not supported)"
+                             : " are not covered by the level (coarse/fine boundary)");
+        }
       }
     }
   }

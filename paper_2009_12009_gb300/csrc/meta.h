@@ -33,7 +33,13 @@ struct SolveGeom {
 };
 
 // One multigrid level of one or several independent problems.
+struct CfSlab {
+  int box, d, side;  // a face of a box whose ghosts lie on the coarse/fine boundary
+};
+
 struct LevelMeta {
+  bool allow_cf = false;            // fine AMR level: uncovered face ghosts are coarse/fine
+  std::vector<CfSlab> cf_slabs;
   std::vector<Box> boxes;
   std::vector<int> box_solve;       // per box: index into geoms
   std::vector<SolveGeom> geoms;     // per solve (indexed by solve id)

@@ -29,7 +29,8 @@ EXPORTS = [
     "gmg_get_coeffs", "gmg_workspace_size", "gmg_set_workspace", "gmg_solve", "gmg_apply", "gmg_fill_boundary",
     "gmg_smooth", "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_bottom_solve", "gmg_vcycle",
     "gmg_box_bicgstab_noalloc", "gmg_define_batch", "gmg_num_solves", "gmg_solve_boxes", "gmg_pack_solve",
-    "gmg_unpack_solve", "gmg_batch_solve",
+    "gmg_unpack_solve", "gmg_batch_solve", "gmg_amr_level_boxes", "gmg_pack_amr", "gmg_unpack_amr",
+    "gmg_apply_transpose", "gmg_solve_adjoint", "gmg_beta_grad",
 ]
 
 
@@ -113,6 +114,13 @@ def _declare(L):
         "gmg_pack_solve": [vp, C.c_int, C.c_int, C.c_int, vp, vp],
         "gmg_unpack_solve": [vp, C.c_int, C.c_int, C.c_int, vp, vp],
         "gmg_batch_solve": [vp, vp, vp, C.c_double, C.c_double, C.POINTER(Params), C.POINTER(SolveInfo)],
+        "gmg_amr_level_boxes": [vp, C.c_int, i32p, i32p, i32p],
+        "gmg_pack_amr": [vp, C.c_int, vp, vp],
+        "gmg_unpack_amr": [vp, C.c_int, vp, vp],
+        "gmg_apply_transpose": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)],
+        "gmg_solve_adjoint": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_double, C.POINTER(Params),
+                              C.POINTER(SolveInfo)],
+        "gmg_beta_grad": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -310,6 +318,20 @@ class Context:
         self._check(self.L.gmg_apply(self.h, oa, pa))
         return out
 
+    def solve_adjoint(self, g, tol_rel=1e-10, **params):
+        lam = self.field(0)
+        p = default_params(**params)
+        info = SolveInfo()
+        st = self.L.gmg_solve_adjoint(self.h, _pp(lam), _pp(g), tol_rel, C.byref(p), C.byref(info))
+        if st not in (OK, NOT_CONVERGED):
+            self._check(st)
+        return lam, info
+
+    def beta_grad(self, phi, lam):
+        d = self.field(0)
+        self._check(self.L.gmg_beta_grad(self.h, _pp(d), _pp(phi), _pp(lam)))
+        return d
+
     # ---- individual steps ----------------------------------------------------------------
     def fill_boundary(self, f, m=0, dt=DT_F64, colour=-1):
         self._check(self.L.gmg_fill_boundary(self.h, m, dt, _ptr(f), colour))
@@ -345,6 +367,101 @@ class Context:
         p = default_params(**params)
         self._check(self.L.gmg_vcycle(self.h, dt, _ptr(e), _ptr(r), C.byref(p)))
         return e
+
+
+def _pp(*tensors):
+    """array of device pointers (level 0, level 1, ...)"""
+    return (C.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+
+class AmrContext(Context):
+    """Two-level composite problem: level 0 covers the domain, level 1 (ratio 2) covers the
+    fine boxes.  Dense fine arrays span the bounding box of the fine boxes."""
+
+    def __init__(self, domain, coarse_boxes, fine_boxes, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0),
+                 prob_hi=(1.0, 1.0, 1.0), stream=None):
+        super().__init__(domain, bc_lo, bc_hi, prob_lo, prob_hi, boxes=coarse_boxes, stream=stream)
+        flat = [v for b in fine_boxes for v in (list(b[0]) + list(b[1]))]
+        self._check(self.L.gmg_define_level(self.h, 1, len(fine_boxes), _arr(flat, C.c_int), 2))
+        self.fine_boxes = list(fine_boxes)
+        lo = [min(b[0][d] for b in fine_boxes) for d in range(3)]
+        hi = [max(b[1][d] for b in fine_boxes) for d in range(3)]
+        self.fine_lo = tuple(lo)
+        self.fine_shape = tuple(hi[d] - lo[d] + 1 for d in (2, 1, 0))
+        self.coarse_shape = self.level_shape(0)
+        import numpy as np
+        cov = np.zeros(self.coarse_shape, dtype=bool)
+        for b in fine_boxes:
+            cov[b[0][2] // 2:(b[1][2] + 1) // 2, b[0][1] // 2:(b[1][1] + 1) // 2, b[0][0] // 2:(b[1][0] + 1) // 2] = True
+        self.covered = cov
+
+    def nelem(self, lev):
+        ne = C.c_int64()
+        self._check(self.L.gmg_layout(self.h, lev, C.byref(ne), None))
+        return ne.value
+
+    def level_field(self, lev):
+        import torch
+        return torch.zeros(self.nelem(lev), dtype=torch.float64, device="cuda")
+
+    def pack_level(self, lev, dense, out=None):
+        import torch
+        dense = torch.as_tensor(dense, dtype=torch.float64, device="cuda").contiguous()
+        out = self.level_field(lev) if out is None else out
+        self._check(self.L.gmg_pack_amr(self.h, lev, _ptr(dense), _ptr(out)))
+        self._keep.append(dense)
+        return out
+
+    def unpack_level(self, lev, boxed):
+        import torch
+        shape = self.coarse_shape if lev == 0 else self.fine_shape
+        out = torch.zeros(shape, dtype=torch.float64, device=boxed.device)
+        self._check(self.L.gmg_unpack_amr(self.h, lev, _ptr(boxed), _ptr(out)))
+        return out
+
+    def set_coeffs(self, a=0.0, b=1.0, alpha_c=None, beta_c=None, alpha_f=None, beta_f=None):
+        import torch
+        self._keep = []
+        self.set_scalars(a, b)
+        if alpha_c is not None:
+            self._check(self.L.gmg_set_acoef(self.h, 0, _ptr(self.pack_level(0, alpha_c))))
+        if alpha_f is not None:
+            self._check(self.L.gmg_set_acoef(self.h, 1, _ptr(self.pack_level(1, alpha_f))))
+        if beta_c is None:
+            beta_c = torch.ones(self.coarse_shape, dtype=torch.float64)
+        if beta_f is None:
+            beta_f = torch.ones(self.fine_shape, dtype=torch.float64)
+        self._check(self.L.gmg_set_bcoef_cell(self.h, 0, _ptr(self.pack_level(0, beta_c))))
+        self._check(self.L.gmg_set_bcoef_cell(self.h, 1, _ptr(self.pack_level(1, beta_f))))
+
+    def solve2(self, rhs_c, rhs_f, tol_rel=1e-10, tol_abs=0.0, **params):
+        pc, pf = self.level_field(0), self.level_field(1)
+        p = default_params(**params)
+        info = SolveInfo()
+        st = self.L.gmg_solve(self.h, _pp(pc, pf), _pp(rhs_c, rhs_f), tol_rel, tol_abs, C.byref(p), C.byref(info))
+        if st not in (OK, NOT_CONVERGED):
+            self._check(st)
+        return pc, pf, info
+
+    def apply2(self, xc, xf, transpose=False):
+        oc, of = self.level_field(0), self.level_field(1)
+        fn = self.L.gmg_apply_transpose if transpose else self.L.gmg_apply
+        self._check(fn(self.h, _pp(oc, of), _pp(xc, xf)))
+        return oc, of
+
+    def solve_adjoint2(self, gc, gf, tol_rel=1e-10, **params):
+        lc, lf = self.level_field(0), self.level_field(1)
+        p = default_params(**params)
+        info = SolveInfo()
+        st = self.L.gmg_solve_adjoint(self.h, _pp(lc, lf), _pp(gc, gf), tol_rel, C.byref(p), C.byref(info))
+        if st not in (OK, NOT_CONVERGED):
+            self._check(st)
+        return lc, lf, info
+
+    def beta_grad2(self, pc, pf, lc, lf):
+        dc, df = self.level_field(0), self.level_field(1)
+        self._check(self.L.gmg_beta_grad(self.h, _pp(dc, df), _pp(pc, pf), _pp(lc, lf)))
+        return dc, df
 
 
 class BatchContext(Context):
