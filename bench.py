@@ -151,6 +151,120 @@ def cpu_baseline(cfg, iters=2):
             "sample": f"{it} V-cycle iterations of the abec256 solve (FP64 oracle, 1 thread), {dt:.1f} s"}
 
 
+def _timed(fn, steps, warmup, stream, barrier):
+    """device time (ms) per call of fn over `steps` calls after `warmup`; returns (ms, last)"""
+    import torch
+
+    last = None
+    for _ in range(warmup):
+        last = fn()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        last = fn()
+    e1.record(stream)
+    barrier()
+    return e0.elapsed_time(e1) / steps, last
+
+
+def _updates_per_vcycle_problem(ctx, s):
+    """cells x 4 sweeps over the smoothed levels of problem s of a batched context"""
+    tot, levels = 0, []
+    for m in range(ctx.nlevels):
+        boxes, _ = ctx.level_boxes(m)
+        import ctypes as C
+
+        first, count = C.c_int(), C.c_int()
+        ctx.L.gmg_solve_boxes(ctx.h, m, s, C.byref(first), C.byref(count))
+        if count.value == 0:
+            break
+        cells = sum((b[1][0] - b[0][0] + 1) * (b[1][1] - b[0][1] + 1) * (b[1][2] - b[0][2] + 1)
+                    for b in boxes[first.value:first.value + count.value])
+        levels.append(cells)
+    return 4 * sum(levels[:-1])
+
+
+def measure_forms(stream, barrier, dev):
+    """The other workloads, each at full size: abec512 in FP64 and both mixed forms, batch64
+    (64 uneven problems, batched form), amr2 (two-level composite forward + adjoint +
+    beta gradient).  Device time to 1e-10 per solve."""
+    import numpy as np
+    import torch
+
+    from paper_2009_12009_gb300 import gmg
+    from paper_2009_12009_gb300 import inputs as I
+
+    forms = {}
+    # --- abec512: FP64 vs mixed
+    cfg = I.abec512()
+    ctx = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"], stream=stream.cuda_stream)
+    ctx.allocate(gmg.MIXED_FP32)
+    ctx.set_scalars(0.0, 1.0)
+    ctx.set_beta(torch.from_numpy(cfg["beta"]))
+    rhs = ctx.pack(torch.from_numpy(cfg["rhs"]))
+    del cfg
+    phi = ctx.field(0)
+    upd = mcell_updates_per_vcycle(ctx, 4)
+    res = {"workload": "abec512: 512^3 Dirichlet, 64 boxes of 128^3, abec recipe seed 12012, tol 1e-10"}
+    ref = None
+    for name, prec in (("fp64", gmg.FP64), ("fp32", gmg.MIXED_FP32), ("bf16", gmg.MIXED_BF16)):
+        ms, info = _timed(lambda: ctx.solve(rhs, phi, tol_rel=TOL, precision=prec)[1], 3, 1, stream, barrier)
+        sol = ctx.unpack(phi)
+        if ref is None:
+            ref = sol.clone()
+        res[name] = {"time_to_tol_ms": ms, "iterations": info.iterations, "status": info.status,
+                     "value": upd * info.iterations / (ms * 1e-3) / 1e6, "unit": UNIT,
+                     "final_rel_resid": info.final_resid / info.rhs_norm,
+                     "rel_err_vs_fp64": float((sol - ref).abs().max() / ref.abs().max())}
+    res["mixed_speedup_fp32"] = res["fp64"]["time_to_tol_ms"] / res["fp32"]["time_to_tol_ms"]
+    res["mixed_speedup_bf16"] = res["fp64"]["time_to_tol_ms"] / res["bf16"]["time_to_tol_ms"]
+    forms["abec512"] = res
+    del ctx, rhs, phi, ref, sol
+    torch.cuda.empty_cache()
+    # --- batch64: 64 uneven problems in one batched context
+    probs = I.batch64()
+    bctx = gmg.BatchContext(probs, stream=stream.cuda_stream)
+    bctx.allocate(gmg.MIXED_FP32)
+    bctx.set_scalars(0.0, 1.0)
+    bctx.set_beta_all([torch.from_numpy(p["beta"]) for p in probs])
+    brhs = bctx.pack_all([torch.from_numpy(p["rhs"]) for p in probs])
+    cells = sum(int(np.prod(p["rhs"].shape)) for p in probs)
+    upd_s = [_updates_per_vcycle_problem(bctx, s) for s in range(len(probs))]
+    bphi = bctx.field(0)
+    res = {"workload": f"batch64: 64 problems, edges from {{32,...,160}}, boxes <= 32^3, {cells} cells, "
+                       f"{bctx.level_info(0)[0]} boxes, abec recipe seeds 12014+i (i = 0..63), tol 1e-10 each"}
+    for name, prec in (("fp64", gmg.FP64), ("fp32", gmg.MIXED_FP32)):
+        ms, infos = _timed(lambda: bctx.batch_solve(brhs, bphi, tol_rel=TOL, precision=prec)[1], 3, 1, stream, barrier)
+        its = [i.iterations for i in infos]
+        res[name] = {"time_to_tol_ms": ms, "iterations_min": min(its), "iterations_max": max(its),
+                     "all_converged": all(i.status == gmg.OK for i in infos),
+                     "value": sum(u * k for u, k in zip(upd_s, its)) / (ms * 1e-3) / 1e6, "unit": UNIT}
+    forms["batch64"] = res
+    del bctx, brhs, bphi
+    torch.cuda.empty_cache()
+    # --- amr2: two-level composite forward solve, adjoint solve, beta gradient
+    a = I.amr2()
+    actx = gmg.AmrContext(a["domain"], a["coarse_boxes"], a["fine_boxes"], a["bc_lo"], a["bc_hi"],
+                          stream=stream.cuda_stream)
+    actx.allocate(gmg.FP64)
+    actx.set_coeffs(0.0, 1.0, beta_c=torch.from_numpy(a["beta_c"]), beta_f=torch.from_numpy(a["beta_f"]))
+    rc, rf = actx.pack_level(0, torch.from_numpy(a["rhs_c"])), actx.pack_level(1, torch.from_numpy(a["rhs_f"]))
+    ms_f, (pc, pf, info_f) = _timed(lambda: actx.solve2(rc, rf, tol_rel=TOL), 3, 1, stream, barrier)
+    # dL/dphi of L = 0.5 |phi - phi_target|^2 over the composite cells
+    keep = torch.as_tensor(~a["covered"], device=dev, dtype=torch.float64)
+    gc = actx.pack_level(0, (actx.unpack_level(0, pc) - torch.from_numpy(a["target_c"]).to(dev)) * keep)
+    gf = actx.pack_level(1, actx.unpack_level(1, pf) - torch.from_numpy(a["target_f"]).to(dev))
+    ms_a, (lc, lf, info_a) = _timed(lambda: actx.solve_adjoint2(gc, gf, tol_rel=TOL), 3, 1, stream, barrier)
+    ms_g, _ = _timed(lambda: actx.beta_grad2(pc, pf, lc, lf), 5, 1, stream, barrier)
+    forms["amr2"] = {"workload": "amr2: 128^3 periodic level 0 (8 boxes) + ratio-2 level 1 over the central 64^3 "
+                                 "coarse cells (128^3 fine cells, 8 boxes), seed 12014, tol 1e-10",
+                     "forward": {"time_to_tol_ms": ms_f, "iterations": info_f.iterations, "status": info_f.status},
+                     "adjoint": {"time_to_tol_ms": ms_a, "iterations": info_a.iterations, "status": info_a.status},
+                     "beta_grad_ms": ms_g}
+    return forms
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -188,6 +302,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the 512^3, batched and two-level workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -316,6 +431,11 @@ def main():
         out["e2e"] = {"value": tot_upd * world / (ms_e * 1e-3) / 1e6, "unit": UNIT,
                       "h2d_bytes_per_step": 8 * ncells, "d2h_bytes_per_step": 8 * ncells,
                       "wall_ms_per_step": 1e3 * (time.perf_counter() - t0) / nsteps}
+
+    if not args.no_forms:
+        del ctx, rhs, phi
+        torch.cuda.empty_cache()
+        out["forms"] = measure_forms(stream, barrier, dev)
 
     if not args.no_cpu and rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(cfg)

@@ -976,6 +976,87 @@ void orc_amr_covered(void* vp, char* out) { memcpy(out, ((oamr*)vp)->covered, ((
 /* Coefficients: dense cell alpha/beta over the coarse domain and over the FINE domain
    (only the fine boxes' cells are read).  Fine faces on the coarse/fine boundary take the
    adjacent fine cell's beta. */
+/* fine cell g wrapped into the fine domain along periodic directions */
+static void wrap_periodic(const olev* l, int g[3]) {
+  for (int d = 0; d < 3; ++d)
+    if (l->bclo[d] == ORC_PERIODIC) g[d] = l->dlo[d] + pmod(g[d] - l->dlo[d], l->dhi[d] - l->dlo[d] + 1);
+}
+
+/* beta of the fine face at fine index g[d] - 1/2 along d, read from a fine box holding the
+   cell on its high side or on its low side; 0 when neither cell is a fine cell */
+static int fine_face_beta(const olev* f, int d, const int g_in[3], double* out) {
+  const double* ff = d == 0 ? f->bx : (d == 1 ? f->by : f->bz);
+  int g[3] = {g_in[0], g_in[1], g_in[2]};
+  wrap_periodic(f, g);
+  int b = find_box(f, g);
+  if (b >= 0) {
+    *out = ff[IX(f, b, g[0] - f->lo[3 * b], g[1] - f->lo[3 * b + 1], g[2] - f->lo[3 * b + 2])];
+    return 1;
+  }
+  int gl[3] = {g_in[0], g_in[1], g_in[2]};
+  gl[d] -= 1;
+  wrap_periodic(f, gl);
+  b = find_box(f, gl);
+  if (b < 0) return 0;
+  int loc[3] = {gl[0] - f->lo[3 * b], gl[1] - f->lo[3 * b + 1], gl[2] - f->lo[3 * b + 2]};
+  loc[d] += 1; /* the face above the low cell: slot n of that box */
+  *out = ff[IX(f, b, loc[0], loc[1], loc[2])];
+  return 1;
+}
+
+/* Sec. "Operations between levels" (average of fine data onto the coarse level) applied to
+   the face coefficients: a level-0 face tiled by fine faces (a face of a covered cell)
+   takes the mean of its 4 fine faces, the same rule as between multigrid levels.  The
+   composite operator never reads these faces (covered cells have no rows, and refluxing
+   replaces the coarse flux on the coarse/fine boundary): they shape only the coarse
+   correction operator of the composite iteration, which then sees the fine coefficients
+   instead of a coarse re-discretisation of them.  The coarser multigrid levels of level 0
+   are rebuilt from the result. */
+static void amr_average_down_faces(oamr* A) {
+  olev* c = &A->C->L[0];
+  const olev* f = &A->F->L[0];
+  double* cf[3] = {c->bx, c->by, c->bz};
+  for (int b = 0; b < c->nb; ++b)
+    for (int d = 0; d < 3; ++d) {
+      int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+      int ext[3] = {bn(c, b, 0), bn(c, b, 1), bn(c, b, 2)};
+      ext[d] += 1;
+      for (int k = 0; k < ext[2]; ++k)
+        for (int j = 0; j < ext[1]; ++j)
+          for (int i = 0; i < ext[0]; ++i) {
+            int G[3] = {c->lo[3 * b] + i, c->lo[3 * b + 1] + j, c->lo[3 * b + 2] + k};
+            double s = 0.0, v;
+            int found = 1;
+            for (int t1 = 0; t1 < 2 && found; ++t1)
+              for (int t2 = 0; t2 < 2 && found; ++t2) {
+                int g[3] = {2 * G[0], 2 * G[1], 2 * G[2]};
+                g[d1] += t1;
+                g[d2] += t2;
+                found = fine_face_beta(f, d, g, &v);
+                s += v;
+              }
+            if (found) cf[d][IX(c, b, i, j, k)] = 0.25 * s;
+          }
+    }
+  /* and a covered cell's alpha is the mean of its 8 children's */
+  for (int b = 0; b < c->nb; ++b)
+    for (int k = 0; k < bn(c, b, 2); ++k)
+      for (int j = 0; j < bn(c, b, 1); ++j)
+        for (int i = 0; i < bn(c, b, 0); ++i) {
+          int64_t q = IX(c, b, i, j, k);
+          if (!A->covered[q]) continue;
+          double s = 0.0;
+          for (int e = 0; e < 8; ++e) {
+            int g[3] = {2 * (c->lo[3 * b] + i) + (e & 1), 2 * (c->lo[3 * b + 1] + j) + ((e >> 1) & 1),
+                        2 * (c->lo[3 * b + 2] + k) + (e >> 2)};
+            int fb = find_box(f, g);
+            s += f->alpha[IX(f, fb, g[0] - f->lo[3 * fb], g[1] - f->lo[3 * fb + 1], g[2] - f->lo[3 * fb + 2])];
+          }
+          c->alpha[q] = 0.125 * s;
+        }
+  for (int m = 0; m + 1 < A->C->nlev; ++m) coarsen_coeffs(&A->C->L[m], &A->C->L[m + 1]);
+}
+
 int orc_amr_set_coeffs(void* vp, double a, double bsc, const double* alpha_c, const double* beta_c,
                        const double* alpha_f, const double* beta_f) {
   oamr* A = (oamr*)vp;
@@ -997,6 +1078,7 @@ int orc_amr_set_coeffs(void* vp, double a, double bsc, const double* alpha_c, co
                 f->lo[3 * b + 2] + (int)(rel / (nx * ny)) - 1};
     face[d][slot] = beta_f ? dense_at(f, beta_f, g) : 1.0;
   }
+  amr_average_down_faces(A);
   return 0;
 }
 

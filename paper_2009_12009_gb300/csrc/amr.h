@@ -37,6 +37,23 @@ struct RefluxCell {
   int face0, nface;
 };
 
+// a level-0 face tiled by 4 fine faces: its coefficient is their mean (restriction of the
+// coefficients between AMR levels, as between multigrid levels)
+struct AvgFace {
+  int64_t cslot;   // coarse face slot (coarse layout)
+  int64_t f0;      // first fine face slot (fine layout); the others at +s1, +s2, +s1+s2
+  int s1, s2;      // fine element strides along the two tangential directions
+  int d;           // face direction
+  int pad;
+};
+
+// a covered coarse cell and its 8 fine children (f0 + {0,1} + sx*{0,1} + sy*{0,1})
+struct AvgCell {
+  int64_t cq;
+  int64_t f0;
+  int sx, sy;
+};
+
 struct AmrDev {
   const CfGhost* cf = nullptr;
   int ncf = 0;
@@ -48,12 +65,20 @@ struct AmrDev {
   const unsigned char* covered = nullptr; // coarse layout: 1 where covered
   const int* cfidx = nullptr;             // fine layout: C/F ghost index or -1
   double hf_over_hc = 0.5;
+  const AvgFace* avg_faces = nullptr;
+  int navg_face = 0;
+  const AvgCell* avg_cells = nullptr;
+  int navg_cell = 0;
 };
 
 void launch_cf_fill(const AmrDev& A, double* f, const double* c, int mode, cudaStream_t s);
 // out = in + std_part * (coarse faces' w (c_I - c_N)) - reflux of the fine field
 void launch_reflux(const AmrDev& A, const Coefs& coarse, const Coefs& fine, const double* c, const double* f,
                    const double* in, double* out, int std_part, cudaStream_t s);
+// level-0 coefficients under the fine level from the fine ones: tiled faces' w = (sum of the
+// 4 fine w) / 16 (w = b beta / h^2, h doubling), covered cells' a*alpha = mean of 8 children
+void launch_avgdown_coefs(const AmrDev& A, const double* facoef, const double* fwx, const double* fwy,
+                          const double* fwz, double* cacoef, double* cwx, double* cwy, double* cwz, cudaStream_t s);
 void launch_zero_covered(const AmrDev& A, double* c, cudaStream_t s);
 // outc/outf += transpose of the ghost-interpolation and reflux couplings applied to y
 void launch_composite_transpose_couplings(const AmrDev& A, const Coefs& coarse, const Coefs& fine, const double* yc,

@@ -195,6 +195,41 @@ void launch_reflux(const AmrDev& A, const Coefs& cc, const Coefs& cf, const doub
                                           (const double*)cf.wz, c, f, in, out, std_part, A.hf_over_hc);
 }
 
+__global__ void __launch_bounds__(AT) k_avgdown_faces(const AvgFace* __restrict__ t, int n,
+                                                      const double* __restrict__ fwx, const double* __restrict__ fwy,
+                                                      const double* __restrict__ fwz, double* cwx, double* cwy,
+                                                      double* cwz) {
+  const int i = blockIdx.x * AT + threadIdx.x;
+  if (i >= n) return;
+  const AvgFace a = t[i];
+  const double* fw = a.d == 0 ? fwx : (a.d == 1 ? fwy : fwz);
+  double* cw = a.d == 0 ? cwx : (a.d == 1 ? cwy : cwz);
+  const double sum = fw[a.f0] + fw[a.f0 + a.s2] + fw[a.f0 + a.s1] + fw[a.f0 + a.s1 + a.s2];
+  cw[a.cslot] = sum * 0.0625;
+}
+
+__global__ void __launch_bounds__(AT) k_avgdown_cells(const AvgCell* __restrict__ t, int n,
+                                                      const double* __restrict__ fa, double* ca) {
+  const int i = blockIdx.x * AT + threadIdx.x;
+  if (i >= n) return;
+  const AvgCell a = t[i];
+  double sum = 0.0;
+  for (int e = 0; e < 8; ++e) sum += fa[a.f0 + (e & 1) + (int64_t)a.sx * ((e >> 1) & 1) + (int64_t)a.sy * (e >> 2)];
+  ca[a.cq] = 0.125 * sum;
+}
+
+void launch_avgdown_coefs(const AmrDev& A, const double* facoef, const double* fwx, const double* fwy,
+                          const double* fwz, double* cacoef, double* cwx, double* cwy, double* cwz, cudaStream_t s) {
+  if (A.navg_face) {
+    count_launches(1);
+    k_avgdown_faces<<<nblk(A.navg_face), AT, 0, s>>>(A.avg_faces, A.navg_face, fwx, fwy, fwz, cwx, cwy, cwz);
+  }
+  if (A.navg_cell) {
+    count_launches(1);
+    k_avgdown_cells<<<nblk(A.navg_cell), AT, 0, s>>>(A.avg_cells, A.navg_cell, facoef, cacoef);
+  }
+}
+
 void launch_zero_covered(const AmrDev& A, double* c, cudaStream_t s) {
   if (!A.ncov) return;
   count_launches(1);

@@ -157,6 +157,64 @@ std::string build_amr(const LevelMeta& C, LevelMeta& F, AmrHost& A) {
     for (auto& f : kv.second) A.rfaces.push_back(f);
     A.rcells.push_back(rc);
   }
+  // coefficient restriction onto level 0 under the fine level (Sec. "Operations between
+  // levels"): every level-0 face slot with a covered cell on either side, and every covered
+  // cell.  The composite operator reads none of these; the coarse correction operator does.
+  auto is_covered = [&](const int g[3]) {
+    const int gf[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+    return cell_elem(F, gf) >= 0;
+  };
+  for (int b = 0; b < (int)C.boxes.size(); ++b) {
+    const Box& B = C.boxes[b];
+    const DevBox& D = C.dbox[b];
+    for (int d = 0; d < 3; ++d) {
+      const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+      int ext[3] = {B.n(0), B.n(1), B.n(2)};
+      ext[d] += 1;
+      for (int k = 0; k < ext[2]; ++k)
+        for (int j = 0; j < ext[1]; ++j)
+          for (int i = 0; i < ext[0]; ++i) {
+            const int G[3] = {B.lo[0] + i, B.lo[1] + j, B.lo[2] + k};
+            int Gl[3] = {G[0], G[1], G[2]};
+            Gl[d] -= 1;
+            if (!is_covered(G) && !is_covered(Gl)) continue;
+            // the fine face at 2G (its tangential low corner), from the box of the fine cell
+            // above it, else from the box of the fine cell below it (slot n of that box)
+            int fg[3] = {2 * G[0], 2 * G[1], 2 * G[2]};
+            int fb = -1;
+            int64_t f0 = cell_elem(F, fg, &fb);
+            if (f0 < 0) {
+              fg[d] -= 1;
+              f0 = cell_elem(F, fg, &fb);
+              if (f0 < 0) return "covered face without fine faces (internal error)";
+              f0 += d == 0 ? 1 : (d == 1 ? (int64_t)F.dbox[fb].sx : F.dbox[fb].sy);
+            }
+            const DevBox& FD = F.dbox[fb];
+            const int64_t st[3] = {1, FD.sx, FD.sy};
+            AvgFace a{};
+            a.cslot = elem_index(D, i, j, k);
+            a.f0 = f0;
+            a.s1 = (int)st[d1];
+            a.s2 = (int)st[d2];
+            a.d = d;
+            A.avg_faces.push_back(a);
+          }
+    }
+    for (int k = 0; k < B.n(2); ++k)
+      for (int j = 0; j < B.n(1); ++j)
+        for (int i = 0; i < B.n(0); ++i) {
+          const int64_t q = elem_index(D, i, j, k);
+          if (!A.covered[q]) continue;
+          const int gf[3] = {2 * (B.lo[0] + i), 2 * (B.lo[1] + j), 2 * (B.lo[2] + k)};
+          int fb = -1;
+          AvgCell a{};
+          a.cq = q;
+          a.f0 = cell_elem(F, gf, &fb);
+          a.sx = F.dbox[fb].sx;
+          a.sy = (int)F.dbox[fb].sy;
+          A.avg_cells.push_back(a);
+        }
+  }
   // each fine box's coarsened image must lie in one coarse box (transfers use it)
   F.parent.assign(F.boxes.size(), -1);
   for (int b = 0; b < (int)F.boxes.size(); ++b) {

@@ -16,6 +16,8 @@ struct AmrHost {
   std::vector<unsigned char> covered;  // coarse level-0 layout
   std::vector<int64_t> covered_list;
   std::vector<int> cfidx;              // fine layout
+  std::vector<AvgFace> avg_faces;
+  std::vector<AvgCell> avg_cells;
 };
 
 // Tables of the composite operator for coarse level C (AMR level 0, MG level 0) and the

@@ -307,6 +307,10 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     A.covered = (const unsigned char*)cv.take(H.covered.size());
     A.cfidx = (const int*)cv.take(sizeof(int) * H.cfidx.size());
     A.hf_over_hc = 0.5;
+    A.avg_faces = (const AvgFace*)cv.take(sizeof(AvgFace) * H.avg_faces.size());
+    A.navg_face = (int)H.avg_faces.size();
+    A.avg_cells = (const AvgCell*)cv.take(sizeof(AvgCell) * H.avg_cells.size());
+    A.navg_cell = (int)H.avg_cells.size();
     double* f5[5];
     for (int q = 0; q < 5; ++q) f5[q] = (double*)cv.take(8 * nf);
     double* cc[4];
@@ -409,6 +413,8 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, A.covered_list, H.covered_list))) return st;
     if ((st = upload(c, A.covered, H.covered))) return st;
     if ((st = upload(c, A.cfidx, H.cfidx))) return st;
+    if ((st = upload(c, A.avg_faces, H.avg_faces))) return st;
+    if ((st = upload(c, A.avg_cells, H.avg_cells))) return st;
   }
   std::vector<int> ones(c->ns(), 1);
   gmg_status st = upload(c, c->active, ones);
@@ -467,6 +473,16 @@ gmg_status build_coefs(gmg_ctx* c) {
   cudaStream_t s = c->stream;
   launch_acoef(c->dev[0], c->a, c->have_alpha ? c->alpha0 : nullptr, c->buf[0].acoef, s);
   launch_faces_scale(c->dev[0], c->b, c->bx0, c->by0, c->bz0, c->buf[0].wx, c->buf[0].wy, c->buf[0].wz, s);
+  if (c->amr) {
+    // the fine level first: level 0 under it takes the restriction of its coefficients
+    if (!c->have_beta_f) SETERR(c, GMG_ERR_STATE, "beta of AMR level 1 not set");
+    const LevelBufs& B = c->buff;
+    const LevelBufs& B0 = c->buf[0];
+    launch_acoef(c->devf, c->a, c->have_alpha_f ? c->alphaf : nullptr, B.acoef, s);
+    launch_faces_scale(c->devf, c->b, c->bxf, c->byf, c->bzf, B.wx, B.wy, B.wz, s);
+    launch_diag(c->devf, B.acoef, B.wx, B.wy, B.wz, B.D, B.invD, s);
+    launch_avgdown_coefs(c->amrd, B.acoef, B.wx, B.wy, B.wz, B0.acoef, B0.wx, B0.wy, B0.wz, s);
+  }
   for (int m = 0; m + 1 < nlev(c); ++m) {
     const LevelBufs& F = c->buf[m];
     const LevelBufs& C = c->buf[m + 1];
@@ -483,13 +499,6 @@ gmg_status build_coefs(gmg_ctx* c) {
       launch_convert(DT_F64, DT_F32, B.D, B.fD, n, s);
       launch_convert(DT_F64, DT_F32, B.invD, B.finvD, n, s);
     }
-  }
-  if (c->amr) {
-    if (!c->have_beta_f) SETERR(c, GMG_ERR_STATE, "beta of AMR level 1 not set");
-    const LevelBufs& B = c->buff;
-    launch_acoef(c->devf, c->a, c->have_alpha_f ? c->alphaf : nullptr, B.acoef, s);
-    launch_faces_scale(c->devf, c->b, c->bxf, c->byf, c->bzf, B.wx, B.wy, B.wz, s);
-    launch_diag(c->devf, B.acoef, B.wx, B.wy, B.wz, B.D, B.invD, s);
   }
   // singular flag of the bottom problems
   for (int m = 0; m < nlev(c); ++m) {

@@ -139,3 +139,34 @@ def batch_problem(size, index, seed=None, max_grid_size=32):
 
 def batch64(nsolves=64, seed=None):
     return [batch_problem(s, i, seed) for i, s in enumerate(batch_sizes(nsolves, seed))]
+
+
+def amr2(n=128, seed=None):
+    """Two-level composite workload: level 0 n^3 periodic in boxes of (n/2)^3; level 1 at ratio
+    2 over the central half of the coarse domain ([n/4, 3n/4)^3 coarse -> (n)^3 fine cells in 8
+    boxes of (n/2)^3).  beta log-normal smoothed (periodic wrap on level 0, window truncated at
+    the patch edge on level 1, drawn independently), coarse cells under the patch take the
+    average of their fine children; rhs N(0,1) on the composite cells minus its
+    volume-weighted mean; phi_target N(0,1).  Fine arrays span the patch (n^3)."""
+    rng = np.random.default_rng(SEEDS["amr2"] if seed is None else seed)
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    lo, hi = n // 2, 3 * n // 2 - 1
+    fdom = ((lo, lo, lo), (hi, hi, hi))
+    cshape, fshape = (n, n, n), (n, n, n)
+    beta_c = lognormal_beta(rng, cshape, periodic=True)
+    beta_f = lognormal_beta(rng, fshape, periodic=False)
+    q = n // 4
+    avg = beta_f.reshape(n // 2, 2, n // 2, 2, n // 2, 2).mean(axis=(1, 3, 5))
+    beta_c[q:3 * q, q:3 * q, q:3 * q] = avg
+    covered = np.zeros(cshape, dtype=bool)
+    covered[q:3 * q, q:3 * q, q:3 * q] = True
+    rhs_c = rng.standard_normal(cshape) * ~covered
+    rhs_f = rng.standard_normal(fshape)
+    vc, vf = 1.0, 1.0 / 8.0
+    mean = (vc * rhs_c.sum() + vf * rhs_f.sum()) / (vc * (~covered).sum() + vf * rhs_f.size)
+    rhs_c = (rhs_c - mean) * ~covered
+    rhs_f = rhs_f - mean
+    return dict(name="amr2", domain=dom, coarse_boxes=chop(*dom, n // 2), fine_boxes=chop(*fdom, n // 2),
+                fine_slice=(lo, hi), bc_lo=[PERIODIC] * 3, bc_hi=[PERIODIC] * 3, a=0.0, b=1.0, beta_c=beta_c,
+                beta_f=beta_f, rhs_c=rhs_c, rhs_f=rhs_f, covered=covered,
+                target_c=rng.standard_normal(cshape) * ~covered, target_f=rng.standard_normal(fshape))

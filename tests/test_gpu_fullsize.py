@@ -1,0 +1,206 @@
+"""The full-size workloads, in the launch configuration the benchmark times, checked against
+the oracle.
+
+  * abec256 (256^3, 64 boxes, FP64, graphs, V(2,2)): two V-cycle iterations element by
+    element against two oracle iterations (1e-10 relative); the converged solution's
+    residual recomputed by the oracle's operator (<= 1.01e-10 ||rhs||, the requested
+    tolerance with room for the order of the residual's additions).
+  * abec512 (512^3, 64 boxes): one FP64 iteration element by element; FP64 and both mixed
+    solves converge to a residual that the oracle's operator confirms.
+  * batch64 (64 problems, 42.3M cells, one batched context): every problem's residual by
+    the oracle's operator, in FP64 and mixed FP32; three problems (smallest, median,
+    largest) solved by the oracle alone: same iteration count, solutions within 1e-10.
+  * amr2 (two levels, 128^3 + 128^3): two composite iterations element by element; the
+    converged forward and adjoint solves' residuals by the oracle's composite operator and
+    its transpose; the beta gradient of the GPU's phi and lambda against the oracle's.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2009_12009_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2009_12009_gb300 import gmg  # noqa: E402
+
+TOL = 1e-10
+RES_BOUND = 1.01e-10
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def make_pair(cfg, precision):
+    ph = cfg.get("prob_hi", (1.0, 1.0, 1.0))
+    C = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], prob_hi=ph, boxes=cfg["boxes"], stream=stream())
+    C.allocate(precision)
+    C.set_scalars(cfg["a"], cfg["b"])
+    C.set_beta(torch.from_numpy(cfg["beta"]))
+    P = O.Problem(cfg["domain"], cfg["boxes"], cfg["bc_lo"], cfg["bc_hi"], (0.0, 0.0, 0.0), ph)
+    P.set_coeffs(cfg["a"], cfg["b"], alpha=cfg["alpha"], beta=cfg["beta"])
+    return C, P
+
+
+def oracle_rel_residual(P, phi, rhs):
+    return np.abs(rhs - P.apply(phi)).max() / np.abs(rhs).max()
+
+
+@pytest.fixture(scope="module")
+def abec256():
+    cfg = I.abec256()
+    C, P = make_pair(cfg, gmg.FP64)
+    return cfg, C, P
+
+
+def test_abec256_two_iterations_match_oracle(abec256):
+    cfg, C, P = abec256
+    want, it, hist, _ = P.solve(cfg["rhs"], tol_rel=0.0, maxit=2)
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=0.0, max_iter=2)
+    assert info.iterations == it == 2
+    got = C.unpack(phi).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    np.testing.assert_allclose(info.history(), hist, rtol=1e-8)
+
+
+def test_abec256_converged_residual(abec256):
+    cfg, C, P = abec256
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=TOL)
+    assert info.status == gmg.OK
+    rel = oracle_rel_residual(P, C.unpack(phi).cpu().numpy(), cfg["rhs"])
+    assert rel <= RES_BOUND
+    # the library's own final residual is the one the oracle's operator gives
+    assert abs(rel - info.final_resid / info.rhs_norm) <= 1e-3 * rel
+
+
+@pytest.fixture(scope="module")
+def abec512():
+    cfg = I.abec512()
+    C, P = make_pair(cfg, gmg.MIXED_FP32)
+    return cfg, C, P
+
+
+def test_abec512_one_iteration_matches_oracle(abec512):
+    cfg, C, P = abec512
+    want, it, hist, _ = P.solve(cfg["rhs"], tol_rel=0.0, maxit=1)
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=0.0, max_iter=1)
+    assert info.iterations == it == 1
+    got = C.unpack(phi).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("prec", [gmg.FP64, gmg.MIXED_FP32, gmg.MIXED_BF16], ids=["fp64", "fp32", "bf16"])
+def test_abec512_converged_residual(abec512, prec):
+    cfg, C, P = abec512
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=TOL, precision=prec)
+    assert info.status == gmg.OK
+    assert oracle_rel_residual(P, C.unpack(phi).cpu().numpy(), cfg["rhs"]) <= RES_BOUND
+
+
+@pytest.fixture(scope="module")
+def batch64():
+    probs = I.batch64()
+    B = gmg.BatchContext(probs, stream=stream())
+    B.allocate(gmg.MIXED_FP32)
+    B.set_scalars(0.0, 1.0)
+    B.set_beta_all([torch.from_numpy(p["beta"]) for p in probs])
+    rhs = B.pack_all([torch.from_numpy(p["rhs"]) for p in probs])
+    return probs, B, rhs
+
+
+def oracle_of(p):
+    P = O.Problem(p["domain"], p["boxes"], p["bc_lo"], p["bc_hi"], (0.0, 0.0, 0.0), p["prob_hi"])
+    P.set_coeffs(p["a"], p["b"], alpha=p["alpha"], beta=p["beta"])
+    return P
+
+
+@pytest.mark.parametrize("prec", [gmg.FP64, gmg.MIXED_FP32], ids=["fp64", "fp32"])
+def test_batch64_every_problem_converged(batch64, prec):
+    probs, B, rhs = batch64
+    phi, infos = B.batch_solve(rhs, tol_rel=TOL, precision=prec)
+    assert all(i.status == gmg.OK for i in infos)
+    for s, p in enumerate(probs):
+        rel = oracle_rel_residual(oracle_of(p), B.unpack_solve(s, phi).cpu().numpy(), p["rhs"])
+        assert rel <= RES_BOUND, (s, rel)
+
+
+def test_batch64_sampled_problems_match_oracle_solves(batch64):
+    probs, B, rhs = batch64
+    phi, infos = B.batch_solve(rhs, tol_rel=TOL)
+    cells = [int(np.prod(p["rhs"].shape)) for p in probs]
+    order = sorted(range(len(probs)), key=lambda s: cells[s])
+    for s in (order[0], order[len(order) // 2], order[-1]):
+        want, it, hist, st = oracle_of(probs[s]).solve(probs[s]["rhs"], tol_rel=TOL)
+        assert st == 0 and infos[s].iterations == it, (s, it, infos[s].iterations)
+        got = B.unpack_solve(s, phi).cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max(), s
+
+
+class Amr2:
+    def __init__(self):
+        a = self.cfg = I.amr2()
+        self.C = gmg.AmrContext(a["domain"], a["coarse_boxes"], a["fine_boxes"], a["bc_lo"], a["bc_hi"], stream=stream())
+        self.C.allocate(gmg.FP64)
+        self.C.set_coeffs(0.0, 1.0, beta_c=torch.from_numpy(a["beta_c"]), beta_f=torch.from_numpy(a["beta_f"]))
+        self.P = O.AmrProblem(a["domain"], a["coarse_boxes"], a["fine_boxes"], a["bc_lo"], a["bc_hi"])
+        lo, hi = a["fine_slice"]
+        self.sl = (slice(lo, hi + 1),) * 3
+        self.bf = np.ones(self.P.fine_shape)
+        self.bf[self.sl] = a["beta_f"]
+        self.P.set_coeffs(0.0, 1.0, beta_c=a["beta_c"], beta_f=self.bf)
+
+    def full_fine(self, x):
+        out = np.zeros(self.P.fine_shape)
+        out[self.sl] = x
+        return out
+
+    def to_gpu(self, xc, xf_patch):
+        return self.C.pack_level(0, torch.from_numpy(xc)), self.C.pack_level(1, torch.from_numpy(xf_patch))
+
+    def from_gpu(self, gc, gf):
+        return self.C.unpack_level(0, gc).cpu().numpy() * self.P.coarse_mask, \
+            self.full_fine(self.C.unpack_level(1, gf).cpu().numpy())
+
+
+@pytest.fixture(scope="module")
+def amr2():
+    return Amr2()
+
+
+def test_amr2_two_iterations_match_oracle(amr2):
+    a = amr2.cfg
+    pc, pf, it, hist, st = amr2.P.solve(a["rhs_c"], amr2.full_fine(a["rhs_f"]), tol_rel=0.0, maxit=2)
+    oc, of, info = amr2.C.solve2(*amr2.to_gpu(a["rhs_c"], a["rhs_f"]), tol_rel=0.0, max_iter=2)
+    assert info.iterations == it == 2
+    want = amr2.P.pack(pc, pf)
+    assert np.abs(amr2.P.pack(*amr2.from_gpu(oc, of)) - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_amr2_forward_adjoint_gradient(amr2):
+    a, P = amr2.cfg, amr2.P
+    rc, rf = a["rhs_c"], amr2.full_fine(a["rhs_f"])
+    pc, pf, info = amr2.C.solve2(*amr2.to_gpu(a["rhs_c"], a["rhs_f"]), tol_rel=TOL)
+    assert info.status == gmg.OK
+    phi = amr2.from_gpu(pc, pf)
+    r = P.pack(rc, rf) - P.pack(*P.apply(*phi))
+    assert np.abs(r).max() <= RES_BOUND * np.abs(P.pack(rc, rf)).max()
+    # adjoint of L = 0.5 |phi - phi_target|^2 over the composite cells
+    gcn = (phi[0] - a["target_c"]) * P.coarse_mask
+    gfn = phi[1][amr2.sl] - a["target_f"]
+    lc, lf, ainfo = amr2.C.solve_adjoint2(*amr2.to_gpu(gcn, gfn), tol_rel=TOL)
+    assert ainfo.status == gmg.OK
+    lam = amr2.from_gpu(lc, lf)
+    g = P.pack(gcn, amr2.full_fine(gfn))
+    V = P.volumes()
+    g = g - V * g.sum() / V.sum()
+    ra = g - P.pack(*P.apply(*lam, transpose=True))
+    assert np.abs(ra).max() <= RES_BOUND * np.abs(g).max()
+    # beta gradient of the GPU's phi and lambda
+    dc, df = amr2.C.beta_grad2(pc, pf, lc, lf)
+    got_c, got_f = amr2.from_gpu(dc, df)
+    want_c, want_f = P.grad_beta(*phi, *lam, a["beta_c"], amr2.bf)
+    scale = max(np.abs(want_c).max(), np.abs(want_f).max())
+    assert np.abs(got_c - want_c * P.coarse_mask).max() <= 1e-10 * scale
+    assert np.abs((got_f - want_f)[P.fine_mask]).max() <= 1e-10 * scale
