@@ -185,18 +185,26 @@ def _updates_per_vcycle_problem(ctx, s):
     return 4 * sum(levels[:-1])
 
 
-def measure_forms(stream, barrier, dev):
+def measure_forms(stream, barrier, dev, only=None):
     """The other workloads, each at full size: abec512 in FP64 and both mixed forms, batch64
     (64 uneven problems, batched form), amr2 (two-level composite forward + adjoint +
     beta gradient).  Device time to 1e-10 per solve."""
-    import numpy as np
+    forms = {}
+    if only in (None, "abec512"):
+        forms["abec512"] = _form_abec512(stream, barrier)
+    if only in (None, "batch64"):
+        forms["batch64"] = _form_batch64(stream, barrier)
+    if only in (None, "amr2"):
+        forms["amr2"] = _form_amr2(stream, barrier, dev)
+    return forms
+
+
+def _form_abec512(stream, barrier):
     import torch
 
     from paper_2009_12009_gb300 import gmg
     from paper_2009_12009_gb300 import inputs as I
 
-    forms = {}
-    # --- abec512: FP64 vs mixed
     cfg = I.abec512()
     ctx = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"], stream=stream.cuda_stream)
     ctx.allocate(gmg.MIXED_FP32)
@@ -219,10 +227,18 @@ def measure_forms(stream, barrier, dev):
                      "rel_err_vs_fp64": float((sol - ref).abs().max() / ref.abs().max())}
     res["mixed_speedup_fp32"] = res["fp64"]["time_to_tol_ms"] / res["fp32"]["time_to_tol_ms"]
     res["mixed_speedup_bf16"] = res["fp64"]["time_to_tol_ms"] / res["bf16"]["time_to_tol_ms"]
-    forms["abec512"] = res
     del ctx, rhs, phi, ref, sol
     torch.cuda.empty_cache()
-    # --- batch64: 64 uneven problems in one batched context
+    return res
+
+
+def _form_batch64(stream, barrier):
+    import numpy as np
+    import torch
+
+    from paper_2009_12009_gb300 import gmg
+    from paper_2009_12009_gb300 import inputs as I
+
     probs = I.batch64()
     bctx = gmg.BatchContext(probs, stream=stream.cuda_stream)
     bctx.allocate(gmg.MIXED_FP32)
@@ -240,10 +256,17 @@ def measure_forms(stream, barrier, dev):
         res[name] = {"time_to_tol_ms": ms, "iterations_min": min(its), "iterations_max": max(its),
                      "all_converged": all(i.status == gmg.OK for i in infos),
                      "value": sum(u * k for u, k in zip(upd_s, its)) / (ms * 1e-3) / 1e6, "unit": UNIT}
-    forms["batch64"] = res
     del bctx, brhs, bphi
     torch.cuda.empty_cache()
-    # --- amr2: two-level composite forward solve, adjoint solve, beta gradient
+    return res
+
+
+def _form_amr2(stream, barrier, dev):
+    import torch
+
+    from paper_2009_12009_gb300 import gmg
+    from paper_2009_12009_gb300 import inputs as I
+
     a = I.amr2()
     actx = gmg.AmrContext(a["domain"], a["coarse_boxes"], a["fine_boxes"], a["bc_lo"], a["bc_hi"],
                           stream=stream.cuda_stream)
@@ -257,12 +280,11 @@ def measure_forms(stream, barrier, dev):
     gf = actx.pack_level(1, actx.unpack_level(1, pf) - torch.from_numpy(a["target_f"]).to(dev))
     ms_a, (lc, lf, info_a) = _timed(lambda: actx.solve_adjoint2(gc, gf, tol_rel=TOL), 3, 1, stream, barrier)
     ms_g, _ = _timed(lambda: actx.beta_grad2(pc, pf, lc, lf), 5, 1, stream, barrier)
-    forms["amr2"] = {"workload": "amr2: 128^3 periodic level 0 (8 boxes) + ratio-2 level 1 over the central 64^3 "
-                                 "coarse cells (128^3 fine cells, 8 boxes), seed 12014, tol 1e-10",
-                     "forward": {"time_to_tol_ms": ms_f, "iterations": info_f.iterations, "status": info_f.status},
-                     "adjoint": {"time_to_tol_ms": ms_a, "iterations": info_a.iterations, "status": info_a.status},
-                     "beta_grad_ms": ms_g}
-    return forms
+    return {"workload": "amr2: 128^3 periodic level 0 (8 boxes) + ratio-2 level 1 over the central 64^3 "
+                        "coarse cells (128^3 fine cells, 8 boxes), seed 12014, tol 1e-10",
+            "forward": {"time_to_tol_ms": ms_f, "iterations": info_f.iterations, "status": info_f.status},
+            "adjoint": {"time_to_tol_ms": ms_a, "iterations": info_a.iterations, "status": info_a.status},
+            "beta_grad_ms": ms_g}
 
 
 def run_reference(args):
@@ -303,6 +325,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the 512^3, batched and two-level workloads")
+    ap.add_argument("--only", choices=["abec512", "batch64", "amr2"], default=None,
+                    help="run and print only this one of the other workloads (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -322,8 +346,13 @@ def main():
     from paper_2009_12009_gb300 import gmg
     from paper_2009_12009_gb300 import inputs as I
 
-    cfg = I.abec256()
     stream = torch.cuda.current_stream()
+    if args.only:
+        def sync():
+            torch.cuda.synchronize()
+        print(json.dumps({"forms": measure_forms(stream, sync, dev, only=args.only)}))
+        return
+    cfg = I.abec256()
     ctx = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"], stream=stream.cuda_stream)
     ctx.allocate(gmg.FP64 if args.no_mixed else gmg.MIXED_FP32)
     ctx.set_scalars(cfg["a"], cfg["b"])
