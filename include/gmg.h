@@ -85,6 +85,12 @@ typedef struct {
   int use_graph;        /* replay the V-cycle as a captured CUDA graph, default 1 */
   int profile;          /* record CUDA events around every finest-level smoother and
                            outer-residual launch (inside the graph too); default 0 */
+  int fused_coarse;     /* 1 (default): each problem's V-cycle levels from the first one
+                           with at most 4096 of its cells (never level 0) down to its
+                           bottom run as ONE thread block per problem (same arithmetic as
+                           the per-level launches; only the bottom solve's dot products
+                           add in another order); 0: one grid launch per step on every
+                           level */
 } gmg_params;
 
 typedef struct {

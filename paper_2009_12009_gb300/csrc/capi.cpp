@@ -100,7 +100,8 @@ struct gmg_ctx {
   size_t h_cap = 0;
 
   // graphs of one outer iteration, keyed by (phi, rhs, precision, nu1, nu2, bottom, profile)
-  std::map<std::tuple<void*, const void*, int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int>, std::pair<cudaGraphExec_t, int64_t>>
+      graphs;
 
   // profiling events (pairs around finest-level smoother / outer residual launches)
   bool profiling = false;
@@ -109,6 +110,15 @@ struct gmg_ctx {
 
   // cell beta of level 0 as last set (ghosts filled), for beta gradients
   double* betac_cell = nullptr;
+
+  // coarse ends of the problems' V-cycles, one thread block each (tail.cu)
+  TailHost tail;
+  bool tail_ok = false;  // tables built and addressable (hierarchy within TAIL_MAXLEV levels)
+  TailDesc* tdescs = nullptr;
+  TailLevel* tlevels = nullptr;
+  BotCell* tcells = nullptr;
+  BotGhost* tghosts = nullptr;
+  TailXfer* txfer = nullptr;
 
   // two-level composite form: AMR level 1 (ratio 2) over part of level 0
   bool amr = false;
@@ -228,6 +238,14 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.n_bot = (int)M.bot_descs.size();
     D.solve_chunk_range = (const int*)cv.take(sizeof(int) * M.solve_chunk_range.size());
     D.inv_count = (const double*)cv.take(sizeof(double) * M.inv_count.size());
+    D.vc_ghost_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.vc_ghost_chunks.size());
+    D.n_vc_ghost_chunks = (int)M.vc_ghost_chunks.size();
+    D.vc_pair_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.vc_pair_chunks.size());
+    D.n_vc_pair_chunks = (int)M.vc_pair_chunks.size();
+    D.vc_coarse_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.vc_coarse_chunks.size());
+    D.n_vc_coarse_chunks = (int)M.vc_coarse_chunks.size();
+    D.vc_bot_descs = (const BotDesc*)cv.take(sizeof(BotDesc) * M.vc_bot_descs.size());
+    D.n_vc_bot = (int)M.vc_bot_descs.size();
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
     B.acoef = (double*)cv.take(8 * ne);
     B.wx = (double*)cv.take(8 * ne);
@@ -262,6 +280,17 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
   double* tmp0 = (double*)cv.take(8 * ne0);
   double* betac = (double*)cv.take(8 * ne0);
   if (fill) c->betac_cell = betac;
+  {
+    const TailHost& T = c->tail;
+    TailDesc* td = (TailDesc*)cv.take(sizeof(TailDesc) * T.descs.size());
+    TailLevel* tl = (TailLevel*)cv.take(sizeof(TailLevel) * T.levels.size());
+    BotCell* tc = (BotCell*)cv.take(sizeof(BotCell) * T.cells.size());
+    BotGhost* tg = (BotGhost*)cv.take(sizeof(BotGhost) * T.ghosts.size());
+    TailXfer* tx = (TailXfer*)cv.take(sizeof(TailXfer) * T.xfer.size());
+    if (fill) {
+      c->tdescs = td; c->tlevels = tl; c->tcells = tc; c->tghosts = tg; c->txfer = tx;
+    }
+  }
   if (c->amr) {
     const LevelMeta& M = c->F;
     const AmrHost& H = c->amr_host;
@@ -389,6 +418,19 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.bot_descs, M.bot_descs))) return st;
     if ((st = upload(c, D.solve_chunk_range, M.solve_chunk_range))) return st;
     if ((st = upload(c, D.inv_count, M.inv_count))) return st;
+    if ((st = upload(c, D.vc_ghost_chunks, M.vc_ghost_chunks))) return st;
+    if ((st = upload(c, D.vc_pair_chunks, M.vc_pair_chunks))) return st;
+    if ((st = upload(c, D.vc_coarse_chunks, M.vc_coarse_chunks))) return st;
+    if ((st = upload(c, D.vc_bot_descs, M.vc_bot_descs))) return st;
+  }
+  {
+    const TailHost& T = c->tail;
+    gmg_status st;
+    if ((st = upload(c, c->tdescs, T.descs))) return st;
+    if ((st = upload(c, c->tlevels, T.levels))) return st;
+    if ((st = upload(c, c->tcells, T.cells))) return st;
+    if ((st = upload(c, c->tghosts, T.ghosts))) return st;
+    if ((st = upload(c, c->txfer, T.xfer))) return st;
   }
   if (c->amr) {
     const LevelMeta& M = c->F;
@@ -434,6 +476,8 @@ void reset_problem(gmg_ctx* c) {
   c->F = LevelMeta();
   c->amr_host = AmrHost();
   c->have_beta_f = c->have_alpha_f = false;
+  c->tail = TailHost();
+  c->tail_ok = false;
 }
 
 // Build the multigrid hierarchy from level-0 boxes (stored problem by problem).
@@ -462,6 +506,12 @@ gmg_status build_hierarchy(gmg_ctx* c, const std::vector<Box>& boxes, const std:
     if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, e);
     if (!more) break;
     c->L.push_back(C);
+  }
+  c->tail_ok = false;
+  if (nlev(c) <= TAIL_MAXLEV) {
+    std::string e = build_tail(c->L, c->tail);
+    if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, e);
+    c->tail_ok = true;
   }
   return GMG_OK;
 }
@@ -504,9 +554,13 @@ gmg_status build_coefs(gmg_ctx* c) {
   for (int m = 0; m < nlev(c); ++m) {
     LevelMeta& M = c->L[m];
     for (auto& d : M.bot_descs) d.singular = singular(c, d.solve) ? 1 : 0;
+    for (auto& d : M.vc_bot_descs) d.singular = singular(c, d.solve) ? 1 : 0;
     gmg_status st = upload(c, c->dev[m].bot_descs, M.bot_descs);
     if (st) return st;
+    if ((st = upload(c, c->dev[m].vc_bot_descs, M.vc_bot_descs))) return st;
   }
+  for (auto& d : c->tail.descs) d.singular = singular(c, d.solve) ? 1 : 0;
+  if (gmg_status st = upload(c, c->tdescs, c->tail.descs)) return st;
   CK(c, cudaGetLastError());
   c->coefs_dirty = false;
   return GMG_OK;
@@ -519,8 +573,7 @@ void record_timing_event(gmg_ctx* c, cudaEvent_t e, cudaStream_t s) {
   else cudaEventRecord(e, s);
 }
 
-void smooth_colour(gmg_ctx* c, int dt, int m, int colour, cudaStream_t s) {
-  const LevelDev& D = c->dev[m];
+void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cudaStream_t s) {
   const LevelBufs& B = c->buf[m];
   launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
   const bool prof = c->profiling && m == 0;
@@ -530,31 +583,81 @@ void smooth_colour(gmg_ctx* c, int dt, int m, int colour, cudaStream_t s) {
   if (prof) record_timing_event(c, ev[1], s);
 }
 
-void smooth_sweeps(gmg_ctx* c, int dt, int m, int nsweep, cudaStream_t s) {
+void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, cudaStream_t s) {
   for (int it = 0; it < nsweep; ++it) {
-    smooth_colour(c, dt, m, 0, s);
-    smooth_colour(c, dt, m, 1, s);
+    smooth_colour(c, D, dt, m, 0, s);
+    smooth_colour(c, D, dt, m, 1, s);
   }
+}
+
+// Level m's tables with the V-cycle's work lists of the fused coarse ends: the grid
+// launches leave out the problems whose tail covers level m.
+LevelDev vc_view(const gmg_ctx* c, int m) {
+  LevelDev D = c->dev[m];
+  D.ghost_chunks = D.vc_ghost_chunks;
+  D.n_ghost_chunks = D.n_vc_ghost_chunks;
+  D.pair_chunks = D.vc_pair_chunks;
+  D.n_pair_chunks = D.n_vc_pair_chunks;
+  D.coarse_chunks = D.vc_coarse_chunks;
+  D.n_coarse_chunks = D.n_vc_coarse_chunks;
+  D.bot_descs = D.vc_bot_descs;
+  D.n_bot = D.n_vc_bot;
+  return D;
+}
+
+// the tails that start at level m: one block per problem runs its levels m..bottom
+void launch_tails(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
+  const TailHost& T = c->tail;
+  if (m >= (int)T.count_at.size() || T.count_at[m] == 0) return;
+  TailArgs a;
+  a.descs = c->tdescs + T.first_at[m];
+  a.levels = c->tlevels;
+  a.cells = c->tcells;
+  a.ghosts = c->tghosts;
+  a.xfer = c->txfer;
+  TailLevelBufs lv[TAIL_MAXLEV];
+  for (int q = 0; q < nlev(c) && q < TAIL_MAXLEV; ++q) {
+    const LevelBufs& B = c->buf[q];
+    const Coefs k = coefs_of(c, q, dt);
+    lv[q].e = B.e[dt];
+    lv[q].r = B.r[dt];
+    lv[q].wx = k.wx; lv[q].wy = k.wy; lv[q].wz = k.wz; lv[q].D = k.D; lv[q].invD = k.invD;
+    a.wx64[q] = B.wx; a.wy64[q] = B.wy; a.wz64[q] = B.wz; a.D64[q] = B.D;
+    a.work[q] = B.bot_work;
+    a.nelem[q] = c->L[q].nelem;
+  }
+  a.nu1 = p.nu1;
+  a.nu2 = p.nu2;
+  a.maxit = p.bottom_max_iter;
+  a.tol = p.bottom_tol;
+  a.iters = c->bot_iters;
+  a.active = c->active;
+  launch_vtail(dt, T.count_at[m], a, lv, std::min(nlev(c), TAIL_MAXLEV), s);
 }
 
 // V-cycle on the correction equation of level m: e_m = V(r_m), e_m zeroed first.  Problems
 // whose bottom is this level are solved here by BiCGStab; the others smooth, restrict,
-// recurse, interpolate and smooth again.
+// recurse, interpolate and smooth again.  With fused_coarse, each problem's levels from
+// its first level of at most TAIL_MAX_CELLS cells down to its bottom run in one thread
+// block (launched when the descent reaches that level) and the grid launches skip them.
 void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
-  const LevelDev& D = c->dev[m];
+  const bool fused = p.fused_coarse && c->tail_ok;
+  const LevelDev D = fused ? vc_view(c, m) : c->dev[m];
   const LevelBufs& B = c->buf[m];
   cudaMemsetAsync(B.e[dt], 0, dt_size(dt) * (size_t)c->L[m].nelem, s);
+  if (fused) launch_tails(c, dt, m, p, s);
   if (D.n_bot) {
     BottomArgs a{p.bottom_max_iter, p.bottom_tol, B.bot_work, c->bot_iters};
     launch_bottom(dt, D, B.r[dt], B.e[dt], coefs64(c, m), a, s);
   }
   if (m + 1 >= nlev(c) || D.n_pair_chunks == 0) return;
-  smooth_sweeps(c, dt, m, p.nu1, s);
+  smooth_sweeps(c, D, dt, m, p.nu1, s);
   launch_fill(dt, D, B.e[dt], -1, 0, s);
-  launch_resid_restrict(dt, D, c->dev[m + 1], B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
+  const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
+  launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
   vcycle(c, dt, m + 1, p, s);
-  launch_prolong_add(dt, D, c->dev[m + 1], c->buf[m + 1].e[dt], B.e[dt], s);
-  smooth_sweeps(c, dt, m, p.nu2, s);
+  launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s);
+  smooth_sweeps(c, D, dt, m, p.nu2, s);
 }
 
 // One outer iteration: e = V(r); phi += e; r = rhs - A phi with per-problem ||r||_inf into
@@ -596,6 +699,7 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.nu1 < 0 || p.nu2 < 0 || p.nu1 + p.nu2 == 0 || p.max_iter < 0 || p.bottom_max_iter < 1 || !(p.bottom_tol > 0))
     SETERR(c, GMG_ERR_BAD_INPUT, "invalid parameters");
   if (p.precision < GMG_FP64 || p.precision > GMG_MIXED_BF16) SETERR(c, GMG_ERR_BAD_INPUT, "invalid precision");
+  if (p.fused_coarse != 0 && p.fused_coarse != 1) SETERR(c, GMG_ERR_BAD_INPUT, "fused_coarse must be 0 or 1");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
   return GMG_OK;
 }
@@ -681,7 +785,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   int sm_n = 0, rs_n = 0;
   if (p.use_graph && nlive) {
     auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
-                               p.bottom_tol, p.profile);
+                               p.bottom_tol, p.profile, p.fused_coarse);
     auto itg = c->graphs.find(key);
     if (itg != c->graphs.end()) {
       gexec = itg->second.first;
@@ -1208,6 +1312,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->project_mean = 0;
   p->use_graph = 1;
   p->profile = 0;
+  p->fused_coarse = 1;
   return GMG_OK;
 }
 

@@ -78,6 +78,35 @@ struct BotDesc {
   int solve;
 };
 
+// The coarse end of one problem's V-cycle run by one thread block (tail.cu): levels
+// m0..mb of that problem, mb its bottom.  Cell and ghost lists reuse BotCell / BotGhost.
+constexpr int TAIL_MAXLEV = 20;       // MG levels addressable by the tail kernel
+constexpr int TAIL_MAX_CELLS = 512;   // a problem's level joins its tail at or below this size
+constexpr int TAIL_WARP_CELLS = 128;  // bottoms up to this size run in one warp ...
+constexpr int TAIL_WARP_SPAN = 2048;  // ... if their boxes span at most this many elements
+
+struct TailLevel {
+  int cell0, ncell[2];   // colour-0 cells at [cell0, cell0 + ncell[0]), colour 1 after them
+  int ghost0, nghost[2]; // ghosts of parity 0, then parity 1 (walls included)
+  int xfer0, nxfer;      // coarse cells of level m + 1 over this level's boxes (m < mb)
+};
+
+// one coarse cell of the next level and its 8 children on this level:
+// qf + {0,1} + sx*{0,1} + sy*{0,1}
+struct TailXfer {
+  int64_t qc, qf;
+  int sx, sy;
+};
+
+struct TailDesc {
+  int solve;
+  int m0, mb;       // first tail level and bottom level (absolute MG levels)
+  int lev0;         // TailLevel of m0; level m is lev0 + m - m0
+  int singular;     // bottom projects onto zero mean
+  int bot_span;     // elements from bot_base to the end of the problem's last bottom box
+  int64_t bot_base; // first element of the problem's first bottom box
+};
+
 __host__ __device__ inline int64_t elem_index(const DevBox& B, int i, int j, int k) {
   return B.off + GX + i + (int64_t)B.sx * (j + 1) + B.sy * (k + 1);
 }

@@ -40,6 +40,15 @@ struct LevelDev {
   const int* active = nullptr;             // per solve: 0 = converged, its boxes are skipped; null = all
   const int* solve_chunk_range = nullptr;  // cell_chunks of solve s are [range[s], range[s+1])
   const double* inv_count = nullptr;       // per solve: 1 / number of cells on this level
+  // the V-cycle's work lists when each problem's coarse end runs as one block (tail.cu)
+  const Chunk* vc_ghost_chunks = nullptr;
+  int n_vc_ghost_chunks = 0;
+  const Chunk* vc_pair_chunks = nullptr;
+  int n_vc_pair_chunks = 0;
+  const Chunk* vc_coarse_chunks = nullptr;
+  int n_vc_coarse_chunks = 0;
+  const BotDesc* vc_bot_descs = nullptr;
+  int n_vc_bot = 0;
 };
 
 // Coefficients of one level in one element type (double for FP64 fields, float for
@@ -120,5 +129,32 @@ struct BottomArgs {
 };
 void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Coefs& c64, const BottomArgs& a,
                    cudaStream_t s);
+
+// ---- coarse end of the V-cycle, one block per problem (tail.cu) ----
+struct TailArgs {
+  const TailDesc* descs = nullptr;  // block b runs descs[b]
+  const TailLevel* levels = nullptr;
+  const BotCell* cells = nullptr;
+  const BotGhost* ghosts = nullptr;
+  const TailXfer* xfer = nullptr;
+  const double* wx64[TAIL_MAXLEV] = {};  // FP64 coefficients (bottom solve)
+  const double* wy64[TAIL_MAXLEV] = {};
+  const double* wz64[TAIL_MAXLEV] = {};
+  const double* D64[TAIL_MAXLEV] = {};
+  double* work[TAIL_MAXLEV] = {};  // 7 double vectors of the level's layout (bottom levels)
+  int64_t nelem[TAIL_MAXLEV] = {};
+  int nu1 = 2, nu2 = 2, maxit = 200;
+  double tol = 1e-4;
+  int* iters = nullptr;         // per solve: bottom iterations
+  const int* active = nullptr;  // per solve: 0 = skip (null: all)
+};
+// one level's V-cycle buffers in the element type of the launch (coefficients double for
+// FP64, float otherwise)
+struct TailLevelBufs {
+  void* e = nullptr;
+  void* r = nullptr;
+  const void *wx = nullptr, *wy = nullptr, *wz = nullptr, *D = nullptr, *invD = nullptr;
+};
+void launch_vtail(int dt, int nblocks, const TailArgs& a, const TailLevelBufs* lv, int nlev, cudaStream_t s);
 
 }  // namespace gmg

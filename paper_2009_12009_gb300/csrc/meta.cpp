@@ -302,4 +302,135 @@ bool make_coarse(LevelMeta& f, LevelMeta& c) {
   return any;
 }
 
+std::string build_tail(std::vector<LevelMeta>& L, TailHost& T) {
+  T = TailHost();
+  const int n = (int)L.size();
+  const int ns = n ? (int)L[0].geoms.size() : 0;
+  T.first_at.assign(n, 0);
+  T.count_at.assign(n, 0);
+  T.tail_from.assign(ns, -1);
+  // per solve: cells per level, bottom level; the tail starts at the first level >= 1 with
+  // at most TAIL_MAX_CELLS cells (sizes only shrink going down)
+  std::vector<int> bottom(ns, -1);
+  for (int s = 0; s < ns; ++s) {
+    for (int m = 0; m < n; ++m)
+      if (L[m].solve_present[s] && L[m].solve_bottom[s]) bottom[s] = m;
+    if (bottom[s] < 1 || bottom[s] >= TAIL_MAXLEV) continue;
+    for (int m = 1; m <= bottom[s]; ++m) {
+      int64_t cells = 0;
+      for (int b = 0; b < (int)L[m].boxes.size(); ++b)
+        if (L[m].box_solve[b] == s) cells += L[m].boxes[b].volume();
+      if (cells <= TAIL_MAX_CELLS) {
+        T.tail_from[s] = m;
+        break;
+      }
+    }
+  }
+  std::vector<int> order;
+  for (int s = 0; s < ns; ++s)
+    if (T.tail_from[s] >= 0) order.push_back(s);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return T.tail_from[a] < T.tail_from[b]; });
+  for (int s : order) {
+    TailDesc D{};
+    D.solve = s;
+    D.m0 = T.tail_from[s];
+    D.mb = bottom[s];
+    D.lev0 = (int)T.levels.size();
+    D.singular = 0;  // set from the operator's scalars at coefficient time
+    for (int m = D.m0; m <= D.mb; ++m) {
+      const LevelMeta& M = L[m];
+      TailLevel TL{};
+      TL.cell0 = (int)T.cells.size();
+      for (int colour = 0; colour < 2; ++colour) {
+        const int c0 = (int)T.cells.size();
+        for (int b = 0; b < (int)M.boxes.size(); ++b) {
+          if (M.box_solve[b] != s) continue;
+          const DevBox& B = M.dbox[b];
+          for (int k = 0; k < B.nz; ++k)
+            for (int j = 0; j < B.ny; ++j)
+              for (int i = 0; i < B.nx; ++i)
+                if (pmod2(B.lo[0] + B.lo[1] + B.lo[2] + i + j + k) == colour)
+                  T.cells.push_back({elem_index(B, i, j, k), B.sy, B.sx, 0});
+        }
+        TL.ncell[colour] = (int)T.cells.size() - c0;
+      }
+      TL.ghost0 = (int)T.ghosts.size();
+      for (int parity = 0; parity < 2; ++parity) {
+        const int g0 = (int)T.ghosts.size();
+        for (const GhostRect& g : M.ghosts) {
+          if (M.box_solve[g.dst_box] != s) continue;
+          const DevBox& Bd = M.dbox[g.dst_box];
+          const DevBox& Bs = M.dbox[g.src_box];
+          for (int v = 0; v < g.n2; ++v)
+            for (int u = 0; u < g.n1; ++u) {
+              if (pmod2(g.par0 + u + v) != parity) continue;
+              int dl[3] = {g.dst[0], g.dst[1], g.dst[2]};
+              int sl[3] = {g.src[0], g.src[1], g.src[2]};
+              dl[g.d1] += u; dl[g.d2] += v;
+              sl[g.d1] += u; sl[g.d2] += v;
+              T.ghosts.push_back({elem_index(Bd, dl[0], dl[1], dl[2]), elem_index(Bs, sl[0], sl[1], sl[2]),
+                                  (double)g.sign});
+            }
+        }
+        TL.nghost[parity] = (int)T.ghosts.size() - g0;
+      }
+      TL.xfer0 = (int)T.xfer.size();
+      if (m < D.mb) {
+        const LevelMeta& Cm = L[m + 1];
+        for (int b = 0; b < (int)M.boxes.size(); ++b) {
+          if (M.box_solve[b] != s) continue;
+          if (M.parent[b] < 0) return "tail: a box without a coarse parent above the bottom (internal error)";
+          const DevBox& F = M.dbox[b];
+          const DevBox& P = Cm.dbox[M.parent[b]];
+          for (int ck = 0; ck < F.nz / 2; ++ck)
+            for (int cj = 0; cj < F.ny / 2; ++cj)
+              for (int ci = 0; ci < F.nx / 2; ++ci) {
+                TailXfer x{};
+                x.qc = elem_index(P, (F.lo[0] >> 1) + ci - P.lo[0], (F.lo[1] >> 1) + cj - P.lo[1],
+                                  (F.lo[2] >> 1) + ck - P.lo[2]);
+                x.qf = elem_index(F, 2 * ci, 2 * cj, 2 * ck);
+                x.sx = F.sx;
+                x.sy = (int)F.sy;
+                T.xfer.push_back(x);
+              }
+        }
+      }
+      TL.nxfer = (int)T.xfer.size() - TL.xfer0;
+      T.levels.push_back(TL);
+    }
+    {
+      const LevelMeta& M = L[D.mb];
+      int64_t lo = -1, hi = 0;
+      for (int b = 0; b < (int)M.boxes.size(); ++b) {
+        if (M.box_solve[b] != s) continue;
+        const DevBox& B = M.dbox[b];
+        if (lo < 0 || B.off < lo) lo = B.off;
+        hi = std::max(hi, B.off + B.sy * (B.nz + 2));
+      }
+      D.bot_base = lo;
+      D.bot_span = (int)std::min<int64_t>(hi - lo, 1 << 30);
+    }
+    if (T.count_at[D.m0]++ == 0) T.first_at[D.m0] = (int)T.descs.size();
+    T.descs.push_back(D);
+  }
+  // the grid launches of the V-cycle skip what the tails do
+  for (int m = 0; m < n; ++m) {
+    LevelMeta& M = L[m];
+    auto in_tail = [&](int solve) { return T.tail_from[solve] >= 0 && T.tail_from[solve] <= m; };
+    M.vc_ghost_chunks.clear();
+    for (const Chunk& ch : M.ghost_chunks)
+      if (!in_tail(M.box_solve[M.ghosts[ch.item].dst_box])) M.vc_ghost_chunks.push_back(ch);
+    M.vc_pair_chunks.clear();
+    for (const Chunk& ch : M.pair_chunks)
+      if (!in_tail(M.box_solve[ch.item])) M.vc_pair_chunks.push_back(ch);
+    M.vc_coarse_chunks.clear();
+    for (const Chunk& ch : M.coarse_chunks)
+      if (!in_tail(M.box_solve[ch.item])) M.vc_coarse_chunks.push_back(ch);
+    M.vc_bot_descs.clear();
+    for (const BotDesc& d : M.bot_descs)
+      if (!in_tail(d.solve)) M.vc_bot_descs.push_back(d);
+  }
+  return "";
+}
+
 }  // namespace gmg

@@ -64,7 +64,28 @@ struct LevelMeta {
   std::vector<BotDesc> bot_descs;
   std::vector<int> solve_chunk_range;  // cell_chunks of solve s: [range[s], range[s+1])
   std::vector<double> inv_count;       // per solve: 1 / cells of the solve on this level (0 if absent)
+
+  // work lists of the V-cycle's grid launches when the coarse ends of the problems run as
+  // one thread block each: entries of problems whose tail covers this level are left out
+  std::vector<Chunk> vc_ghost_chunks, vc_pair_chunks, vc_coarse_chunks;
+  std::vector<BotDesc> vc_bot_descs;
 };
+
+// Tail tables: for every problem whose bottom level is small, the levels from the first
+// one with at most TAIL_MAX_CELLS of its cells (never level 0) down to its bottom.
+struct TailHost {
+  std::vector<TailDesc> descs;  // ordered by m0
+  std::vector<TailLevel> levels;
+  std::vector<BotCell> cells;
+  std::vector<BotGhost> ghosts;
+  std::vector<TailXfer> xfer;
+  std::vector<int> first_at, count_at;  // per MG level: descs whose m0 is that level
+  std::vector<int> tail_from;           // per solve: m0, or -1 (no tail)
+};
+
+// Build the tail tables and the vc_* work lists of every level (after finalize_level of
+// all levels).  Returns "" or an error message.
+std::string build_tail(std::vector<LevelMeta>& L, TailHost& T);
 
 // Checks that boxes are non-empty, inside the domain and pairwise disjoint; with
 // must_cover, that they cover it.  Returns "" or an error message.

@@ -1,0 +1,503 @@
+// tail.cu -- the coarse end of the V-cycle (Sec. "Linear Solvers": geometric multigrid
+// with a Krylov bottom solve), one thread block per problem.
+//
+// Below a few thousand cells a level's grid launches are pure latency: a ghost exchange or
+// a colour sweep moves kilobytes but costs a launch and a dependent-load chain each.  Here
+// one block runs every remaining step of its problem -- ghost fills, red-black sweeps,
+// residual restriction, the BiCGStab bottom solve, interpolation and post-smoothing --
+// with a block barrier between steps, from the first level with at most TAIL_MAX_CELLS
+// cells down to the bottom and back.  The arithmetic of every step is that of the grid
+// kernels (kernels.cu, bottom.cu), in the same order per cell; only the order of the
+// bottom solve's dot-product additions differs.
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace gmg {
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int TT = 512;  // threads of a tail block
+
+template <class T> struct Ar { using type = float; };
+template <> struct Ar<double> { using type = double; };
+template <class T> struct Cf { using type = float; };
+template <> struct Cf<double> { using type = double; };
+
+__device__ __forceinline__ double tld(const double* p) { return *p; }
+__device__ __forceinline__ float tld(const float* p) { return *p; }
+__device__ __forceinline__ float tld(const bf16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void tst(double* p, double v) { *p = v; }
+__device__ __forceinline__ void tst(float* p, float v) { *p = v; }
+__device__ __forceinline__ void tst(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void tst_d(double* p, double v) { *p = v; }
+__device__ __forceinline__ void tst_d(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void tst_d(bf16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+
+// block-wide sum / max, broadcast to every thread; fixed reduction order
+__device__ double tsum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < TT / 32 ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) sh[TT / 32] = w;
+  }
+  __syncthreads();
+  return sh[TT / 32];
+}
+
+__device__ double tmax(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < TT / 32 ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_down_sync(0xffffffffu, w, o));
+    if (threadIdx.x == 0) sh[TT / 32] = w;
+  }
+  __syncthreads();
+  return sh[TT / 32];
+}
+
+// ghosts of one parity (or both: parity -1) of field f
+template <class T>
+__device__ void t_fill(const TailLevel& L, const BotGhost* __restrict__ ghosts, T* f, int parity) {
+  const int g0 = L.ghost0 + (parity == 1 ? L.nghost[0] : 0);
+  const int n = parity < 0 ? L.nghost[0] + L.nghost[1] : L.nghost[parity];
+  for (int i = threadIdx.x; i < n; i += TT) {
+    const BotGhost G = ghosts[g0 + i];
+    const auto v = tld(f + G.src);
+    tst(f + G.dst, G.sign < 0 ? -v : v);
+  }
+}
+
+// one Gauss-Seidel colour: phi = invD * (rhs + sum_f w_f phi_nbr), as k_smooth
+template <class T>
+__device__ void t_smooth(const TailLevel& L, const BotCell* __restrict__ cells, T* phi, const T* rhs,
+                         const typename Cf<T>::type* wx, const typename Cf<T>::type* wy,
+                         const typename Cf<T>::type* wz, const typename Cf<T>::type* invD, int colour) {
+  using A = typename Ar<T>::type;
+  const int c0 = L.cell0 + (colour ? L.ncell[0] : 0);
+  for (int i = threadIdx.x; i < L.ncell[colour]; i += TT) {
+    const BotCell C = cells[c0 + i];
+    const int64_t q = C.q, sx = C.sx, sy = C.sy;
+    A s = tld(rhs + q);
+    s = fma((A)wx[q], (A)tld(phi + q - 1), s);
+    s = fma((A)wx[q + 1], (A)tld(phi + q + 1), s);
+    s = fma((A)wy[q], (A)tld(phi + q - sx), s);
+    s = fma((A)wy[q + sx], (A)tld(phi + q + sx), s);
+    s = fma((A)wz[q], (A)tld(phi + q - sy), s);
+    s = fma((A)wz[q + sy], (A)tld(phi + q + sy), s);
+    tst(phi + q, s * (A)invD[q]);
+  }
+}
+
+template <class T, class C>
+__device__ __forceinline__ typename Ar<T>::type t_resid(const T* phi, const T* rhs, const C* wx, const C* wy,
+                                                        const C* wz, const C* D, int64_t q, int64_t sx, int64_t sy) {
+  using A = typename Ar<T>::type;
+  A v = (A)tld(rhs + q);
+  v = fma(-(A)D[q], (A)tld(phi + q), v);
+  v = fma((A)wx[q], (A)tld(phi + q - 1), v);
+  v = fma((A)wx[q + 1], (A)tld(phi + q + 1), v);
+  v = fma((A)wy[q], (A)tld(phi + q - sx), v);
+  v = fma((A)wy[q + sx], (A)tld(phi + q + sx), v);
+  v = fma((A)wz[q], (A)tld(phi + q - sy), v);
+  v = fma((A)wz[q + sy], (A)tld(phi + q + sy), v);
+  return v;
+}
+
+// xor-butterfly warp reductions: every lane ends with the same bits (a + b == b + a)
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+constexpr int WS = TAIL_WARP_CELLS;  // cell slots of the warp bottom solve
+
+// Shared memory of the warp bottom solve: p and s (the vectors the operator is applied to)
+// in the problem's own element layout from bot_base, with ghosts; the other vectors, the
+// coefficients and the cell offsets per cell slot.
+struct WarpBottomSmem {
+  double p[TAIL_WARP_SPAN], s[TAIL_WARP_SPAN];
+  double D[WS], wxm[WS], wxp[WS], wym[WS], wyp[WS], wzm[WS], wzp[WS];
+  double r[WS], rh[WS], v[WS], t[WS], x[WS];
+  int q[WS], sx[WS], sy[WS];
+};
+
+// BiCGStab (van der Vorst 1992) of a small bottom problem in warp 0 (lanes own cell slots
+// lane, lane + 32, ...): the steps and stopping rules of the block version, with warp
+// barriers instead of block barriers and the operator applied from shared memory.
+template <class T>
+__device__ void warp_bottom(const TailDesc& Dd, const BotCell* __restrict__ cells, int nc,
+                            const BotGhost* __restrict__ ghosts, int ng, const double* wx, const double* wy,
+                            const double* wz, const double* Dg, const T* rhs, T* e, int maxit, double tol,
+                            int* iters, WarpBottomSmem& W) {
+  const int lane = threadIdx.x;
+  const int64_t base = Dd.bot_base;
+  for (int i = lane; i < nc; i += 32) {
+    const BotCell C = cells[i];
+    const int64_t q = C.q;
+    W.q[i] = (int)(q - base);
+    W.sx[i] = C.sx;
+    W.sy[i] = (int)C.sy;
+    W.D[i] = Dg[q];
+    W.wxm[i] = wx[q];
+    W.wxp[i] = wx[q + 1];
+    W.wym[i] = wy[q];
+    W.wyp[i] = wy[q + C.sx];
+    W.wzm[i] = wz[q];
+    W.wzp[i] = wz[q + C.sy];
+    W.r[i] = (double)tld(rhs + q);
+    W.p[W.q[i]] = 0.0;
+    W.v[i] = 0.0;
+    W.x[i] = 0.0;
+  }
+  __syncwarp();
+  auto apply = [&](double* in, double* out) {  // out[slot] = (A in)[cell]
+    __syncwarp();
+    for (int g = lane; g < ng; g += 32) {
+      const BotGhost G = ghosts[g];
+      in[G.dst - base] = G.sign * in[G.src - base];
+    }
+    __syncwarp();
+    for (int i = lane; i < nc; i += 32) {
+      const int q = W.q[i], sx = W.sx[i], sy = W.sy[i];
+      double w = W.D[i] * in[q];
+      w = fma(-W.wxm[i], in[q - 1], w);
+      w = fma(-W.wxp[i], in[q + 1], w);
+      w = fma(-W.wym[i], in[q - sx], w);
+      w = fma(-W.wyp[i], in[q + sx], w);
+      w = fma(-W.wzm[i], in[q - sy], w);
+      w = fma(-W.wzp[i], in[q + sy], w);
+      out[i] = w;
+    }
+  };
+  auto dot = [&](const double* a, const double* b) {
+    double acc = 0.0;
+    for (int i = lane; i < nc; i += 32) acc += a[i] * b[i];
+    return wsum(acc);
+  };
+  auto norm = [&](const double* a) {
+    double acc = 0.0;
+    for (int i = lane; i < nc; i += 32) acc = fmax(acc, fabs(a[i]));
+    return wmax(acc);
+  };
+  if (Dd.singular) {
+    double acc = 0.0;
+    for (int i = lane; i < nc; i += 32) acc += W.r[i];
+    const double mean = wsum(acc) / (double)nc;
+    for (int i = lane; i < nc; i += 32) W.r[i] -= mean;
+  }
+  for (int i = lane; i < nc; i += 32) W.rh[i] = W.r[i];
+  const double r0 = norm(W.r);
+  double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  int it = 0;
+  // s-values of the cells (slot order) live in W.s at the cells' element offsets
+  auto sval = [&](int i) -> double& { return W.s[W.q[i]]; };
+  auto pval = [&](int i) -> double& { return W.p[W.q[i]]; };
+  if (r0 > 0.0) {
+    for (it = 1; it <= maxit; ++it) {
+      const double rho = dot(W.rh, W.r);
+      if (fabs(rho) < 1e-300) { --it; break; }
+      const double beta = (rho / rho_old) * (alpha / omega);
+      __syncwarp();
+      for (int i = lane; i < nc; i += 32) pval(i) = W.r[i] + beta * (pval(i) - omega * W.v[i]);
+      apply(W.p, W.v);
+      const double rv = dot(W.rh, W.v);
+      if (fabs(rv) < 1e-300) { --it; break; }
+      alpha = rho / rv;
+      __syncwarp();
+      for (int i = lane; i < nc; i += 32) sval(i) = W.r[i] - alpha * W.v[i];
+      double ns = 0.0;
+      for (int i = lane; i < nc; i += 32) ns = fmax(ns, fabs(sval(i)));
+      if (wmax(ns) <= tol * r0) {
+        for (int i = lane; i < nc; i += 32) W.x[i] += alpha * pval(i);
+        break;
+      }
+      apply(W.s, W.t);
+      const double tt = dot(W.t, W.t);
+      if (tt == 0.0) {
+        for (int i = lane; i < nc; i += 32) W.x[i] += alpha * pval(i);
+        break;
+      }
+      double ts = 0.0;
+      for (int i = lane; i < nc; i += 32) ts += W.t[i] * sval(i);
+      omega = wsum(ts) / tt;
+      for (int i = lane; i < nc; i += 32) {
+        W.x[i] += alpha * pval(i) + omega * sval(i);
+        W.r[i] = sval(i) - omega * W.t[i];
+      }
+      if (norm(W.r) <= tol * r0) break;
+      rho_old = rho;
+    }
+    if (it > maxit) it = maxit;
+  }
+  double shift = 0.0;
+  if (Dd.singular) {
+    double acc = 0.0;
+    for (int i = lane; i < nc; i += 32) acc += W.x[i];
+    shift = wsum(acc) / (double)nc;
+  }
+  for (int i = lane; i < nc; i += 32) tst_d(e + (base + W.q[i]), W.x[i] - shift);
+  if (lane == 0 && iters) *iters = it;
+}
+
+// every level's buffers in the V-cycle's element type
+template <class T>
+struct TailPtrs {
+  T* e[TAIL_MAXLEV];
+  T* r[TAIL_MAXLEV];
+  const typename Cf<T>::type* wx[TAIL_MAXLEV];
+  const typename Cf<T>::type* wy[TAIL_MAXLEV];
+  const typename Cf<T>::type* wz[TAIL_MAXLEV];
+  const typename Cf<T>::type* D[TAIL_MAXLEV];
+  const typename Cf<T>::type* invD[TAIL_MAXLEV];
+};
+
+template <class T>
+__global__ void __launch_bounds__(TT) k_vtail(const TailArgs a, const TailPtrs<T> P) {
+  using A = typename Ar<T>::type;
+  __shared__ double sh[TT / 32 + 1];
+  const TailDesc Dd = a.descs[blockIdx.x];
+  if (a.active && !a.active[Dd.solve]) return;
+  // ---- down: pre-smooth, restrict the residual
+  for (int m = Dd.m0; m < Dd.mb; ++m) {
+    const TailLevel L = a.levels[Dd.lev0 + m - Dd.m0];
+    T* e = P.e[m];
+    const T* r = P.r[m];
+    for (int i = threadIdx.x; i < L.ncell[0] + L.ncell[1]; i += TT) tst(e + a.cells[L.cell0 + i].q, (A)0);
+    __syncthreads();
+    for (int it = 0; it < a.nu1; ++it)
+      for (int colour = 0; colour < 2; ++colour) {
+        t_fill(L, a.ghosts, e, 1 - colour);
+        __syncthreads();
+        t_smooth(L, a.cells, e, r, P.wx[m], P.wy[m], P.wz[m], P.invD[m], colour);
+        __syncthreads();
+      }
+    t_fill(L, a.ghosts, e, -1);
+    __syncthreads();
+    T* rc = P.r[m + 1];
+    for (int i = threadIdx.x; i < L.nxfer; i += TT) {
+      const TailXfer X = a.xfer[L.xfer0 + i];
+      A s = 0;
+      for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj) {
+          const int64_t q = X.qf + (int64_t)dj * X.sx + (int64_t)dk * X.sy;
+          s += t_resid(e, r, P.wx[m], P.wy[m], P.wz[m], P.D[m], q, X.sx, X.sy);
+          s += t_resid(e, r, P.wx[m], P.wy[m], P.wz[m], P.D[m], q + 1, X.sx, X.sy);
+        }
+      tst(rc + X.qc, s * (A)0.125);
+    }
+    __syncthreads();
+  }
+  // ---- bottom: BiCGStab (van der Vorst 1992) in FP64 on the bottom level, x0 = 0
+  __shared__ WarpBottomSmem wb;
+  const TailLevel Lb = a.levels[Dd.lev0 + Dd.mb - Dd.m0];
+  if (Lb.ncell[0] + Lb.ncell[1] <= TAIL_WARP_CELLS && Dd.bot_span <= TAIL_WARP_SPAN) {
+    const int m = Dd.mb;
+    if (threadIdx.x < 32)
+      warp_bottom(Dd, a.cells + Lb.cell0, Lb.ncell[0] + Lb.ncell[1], a.ghosts + Lb.ghost0,
+                  Lb.nghost[0] + Lb.nghost[1], a.wx64[m], a.wy64[m], a.wz64[m], a.D64[m], P.r[m], P.e[m], a.maxit,
+                  a.tol, a.iters ? a.iters + Dd.solve : nullptr, wb);
+    __syncthreads();
+  } else {
+    const int m = Dd.mb;
+    const TailLevel L = a.levels[Dd.lev0 + m - Dd.m0];
+    const BotCell* cells = a.cells + L.cell0;
+    const int nc = L.ncell[0] + L.ncell[1];
+    const BotGhost* ghosts = a.ghosts + L.ghost0;
+    const int ng = L.nghost[0] + L.nghost[1];
+    const double *wx = a.wx64[m], *wy = a.wy64[m], *wz = a.wz64[m], *D = a.D64[m];
+    const int64_t ne = a.nelem[m];
+    double* r = a.work[m];
+    double* rh = r + ne;
+    double* p = r + 2 * ne;
+    double* v = r + 3 * ne;
+    double* s = r + 4 * ne;
+    double* t = r + 5 * ne;
+    double* x = r + 6 * ne;
+    const T* rhs = P.r[m];
+    auto apply = [&](double* in, double* out) {
+      for (int g = threadIdx.x; g < ng; g += TT) {
+        const BotGhost G = ghosts[g];
+        in[G.dst] = G.sign * in[G.src];
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < nc; i += TT) {
+        const BotCell C = cells[i];
+        const int64_t q = C.q, sx = C.sx, sy = C.sy;
+        double w = D[q] * in[q];
+        w = fma(-wx[q], in[q - 1], w);
+        w = fma(-wx[q + 1], in[q + 1], w);
+        w = fma(-wy[q], in[q - sx], w);
+        w = fma(-wy[q + sx], in[q + sx], w);
+        w = fma(-wz[q], in[q - sy], w);
+        w = fma(-wz[q + sy], in[q + sy], w);
+        out[q] = w;
+      }
+      __syncthreads();
+    };
+    auto dot = [&](const double* y, const double* z) {
+      double acc = 0.0;
+      for (int i = threadIdx.x; i < nc; i += TT) acc += y[cells[i].q] * z[cells[i].q];
+      return tsum(acc, sh);
+    };
+    auto norm = [&](const double* y) {
+      double acc = 0.0;
+      for (int i = threadIdx.x; i < nc; i += TT) acc = fmax(acc, fabs(y[cells[i].q]));
+      return tmax(acc, sh);
+    };
+    auto sum = [&](const double* y) {
+      double acc = 0.0;
+      for (int i = threadIdx.x; i < nc; i += TT) acc += y[cells[i].q];
+      return tsum(acc, sh);
+    };
+    for (int i = threadIdx.x; i < nc; i += TT) {
+      const int64_t q = cells[i].q;
+      r[q] = (double)tld(rhs + q);
+      p[q] = 0.0;
+      v[q] = 0.0;
+      x[q] = 0.0;
+    }
+    __syncthreads();
+    if (Dd.singular) {
+      const double mean = sum(r) / (double)nc;
+      for (int i = threadIdx.x; i < nc; i += TT) r[cells[i].q] -= mean;
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < nc; i += TT) rh[cells[i].q] = r[cells[i].q];
+    __syncthreads();
+    const double r0 = norm(r);
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    int it = 0;
+    if (r0 > 0.0) {
+      for (it = 1; it <= a.maxit; ++it) {
+        const double rho = dot(rh, r);
+        if (fabs(rho) < 1e-300) { --it; break; }
+        const double beta = (rho / rho_old) * (alpha / omega);
+        for (int i = threadIdx.x; i < nc; i += TT) {
+          const int64_t q = cells[i].q;
+          p[q] = r[q] + beta * (p[q] - omega * v[q]);
+        }
+        __syncthreads();
+        apply(p, v);
+        const double rv = dot(rh, v);
+        if (fabs(rv) < 1e-300) { --it; break; }
+        alpha = rho / rv;
+        for (int i = threadIdx.x; i < nc; i += TT) {
+          const int64_t q = cells[i].q;
+          s[q] = r[q] - alpha * v[q];
+        }
+        __syncthreads();
+        if (norm(s) <= a.tol * r0) {
+          for (int i = threadIdx.x; i < nc; i += TT) x[cells[i].q] += alpha * p[cells[i].q];
+          __syncthreads();
+          break;
+        }
+        apply(s, t);
+        const double tt = dot(t, t);
+        if (tt == 0.0) {
+          for (int i = threadIdx.x; i < nc; i += TT) x[cells[i].q] += alpha * p[cells[i].q];
+          __syncthreads();
+          break;
+        }
+        omega = dot(t, s) / tt;
+        for (int i = threadIdx.x; i < nc; i += TT) {
+          const int64_t q = cells[i].q;
+          x[q] += alpha * p[q] + omega * s[q];
+          r[q] = s[q] - omega * t[q];
+        }
+        __syncthreads();
+        if (norm(r) <= a.tol * r0) break;
+        rho_old = rho;
+      }
+      if (it > a.maxit) it = a.maxit;
+    }
+    double shift = 0.0;
+    if (Dd.singular) shift = sum(x) / (double)nc;
+    T* e = P.e[m];
+    for (int i = threadIdx.x; i < nc; i += TT) {
+      const int64_t q = cells[i].q;
+      tst_d(e + q, x[q] - shift);
+    }
+    if (threadIdx.x == 0 && a.iters) a.iters[Dd.solve] = it;
+    __syncthreads();
+  }
+  // ---- up: interpolate, post-smooth
+  for (int m = Dd.mb - 1; m >= Dd.m0; --m) {
+    const TailLevel L = a.levels[Dd.lev0 + m - Dd.m0];
+    T* e = P.e[m];
+    const T* r = P.r[m];
+    const T* ec = P.e[m + 1];
+    for (int i = threadIdx.x; i < L.nxfer; i += TT) {
+      const TailXfer X = a.xfer[L.xfer0 + i];
+      const A c = tld(ec + X.qc);
+      for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj) {
+          const int64_t q = X.qf + (int64_t)dj * X.sx + (int64_t)dk * X.sy;
+          tst(e + q, (A)tld(e + q) + c);
+          tst(e + q + 1, (A)tld(e + q + 1) + c);
+        }
+    }
+    __syncthreads();
+    for (int it = 0; it < a.nu2; ++it)
+      for (int colour = 0; colour < 2; ++colour) {
+        t_fill(L, a.ghosts, e, 1 - colour);
+        __syncthreads();
+        t_smooth(L, a.cells, e, r, P.wx[m], P.wy[m], P.wz[m], P.invD[m], colour);
+        __syncthreads();
+      }
+  }
+}
+
+template <class T>
+void fill_ptrs(TailPtrs<T>& P, const TailLevelBufs* lv, int n) {
+  for (int m = 0; m < TAIL_MAXLEV; ++m) {
+    const bool ok = m < n;
+    P.e[m] = ok ? (T*)lv[m].e : nullptr;
+    P.r[m] = ok ? (T*)lv[m].r : nullptr;
+    P.wx[m] = ok ? (const typename Cf<T>::type*)lv[m].wx : nullptr;
+    P.wy[m] = ok ? (const typename Cf<T>::type*)lv[m].wy : nullptr;
+    P.wz[m] = ok ? (const typename Cf<T>::type*)lv[m].wz : nullptr;
+    P.D[m] = ok ? (const typename Cf<T>::type*)lv[m].D : nullptr;
+    P.invD[m] = ok ? (const typename Cf<T>::type*)lv[m].invD : nullptr;
+  }
+}
+
+}  // namespace
+
+void launch_vtail(int dt, int nblocks, const TailArgs& a, const TailLevelBufs* lv, int nlev, cudaStream_t s) {
+  if (nblocks <= 0) return;
+  count_launches(1);
+  switch (dt) {
+    case DT_F64: {
+      TailPtrs<double> P;
+      fill_ptrs(P, lv, nlev);
+      k_vtail<double><<<nblocks, TT, 0, s>>>(a, P);
+      break;
+    }
+    case DT_F32: {
+      TailPtrs<float> P;
+      fill_ptrs(P, lv, nlev);
+      k_vtail<float><<<nblocks, TT, 0, s>>>(a, P);
+      break;
+    }
+    default: {
+      TailPtrs<bf16> P;
+      fill_ptrs(P, lv, nlev);
+      k_vtail<bf16><<<nblocks, TT, 0, s>>>(a, P);
+      break;
+    }
+  }
+}
+
+}  // namespace gmg

@@ -61,10 +61,11 @@ def test_batch_hierarchy_is_union_of_problems(batch):
         assert boxes == want
 
 
+@pytest.mark.parametrize("fused", [1, 0], ids=["fused_coarse", "per_level"])
 @pytest.mark.parametrize("graph", [1, 0])
-def test_batch_fixed_iterations(batch, graph):
+def test_batch_fixed_iterations(batch, graph, fused):
     probs, ctx, rhs, oracles = batch
-    phi, infos = ctx.batch_solve(rhs, tol_rel=0.0, max_iter=4, use_graph=graph)
+    phi, infos = ctx.batch_solve(rhs, tol_rel=0.0, max_iter=4, use_graph=graph, fused_coarse=fused)
     for s, (p, P) in enumerate(zip(probs, oracles)):
         want, it, hist, st = P.solve(p["rhs"], tol_rel=0.0, maxit=4)
         got = ctx.unpack_solve(s, phi).cpu().numpy()

@@ -222,12 +222,15 @@ def test_bottom(pair, dt):
 # ---------------------------------------------------------------------------- V-cycle
 
 
+@pytest.mark.parametrize("fused", [1, 0], ids=["fused_coarse", "per_level"])
 @pytest.mark.parametrize("dt", DTS)
-def test_vcycle(pair, dt):
+def test_vcycle(pair, dt, fused):
+    """One V-cycle, with the coarse end of the cycle run by one thread block (fused) or by
+    a grid launch per step and level."""
     r = rand_level(pair, 0, 9000, dt)
     if pair.cfg["name"] == "periodic":
         r = round_to(r - r.mean(), dt)
-    e = pair.C.vcycle(pair.C.pack(torch.from_numpy(r), 0, dt), dt)
+    e = pair.C.vcycle(pair.C.pack(torch.from_numpy(r), 0, dt), dt, fused_coarse=fused)
     got = pair.C.unpack(e, 0, dt).cpu().numpy()
     want = pair.P.to_dense(0, pair.P.vcycle(0, pair.P.to_boxed(0, r)))
     tol = {gmg.DT_F64: 1e-10, gmg.DT_F32: 2e-4, gmg.DT_BF16: 6e-2}[dt]
@@ -237,14 +240,15 @@ def test_vcycle(pair, dt):
 # ------------------------------------------------------------------------- whole solve
 
 
+@pytest.mark.parametrize("fused", [1, 0], ids=["fused_coarse", "per_level"])
 @pytest.mark.parametrize("graph", [1, 0])
-def test_solve_fixed_iterations(pair, graph):
+def test_solve_fixed_iterations(pair, graph, fused):
     """Outer loop (Sec. "Linear Solvers"): the same number of V-cycles from phi = 0 gives the
     same iterate to 1e-10 relative, and the same residual history."""
     c = pair.cfg
     nit = 6
     rhs = pair.C.pack(torch.from_numpy(c["rhs"]))
-    phi, info = pair.C.solve(rhs, tol_rel=0.0, max_iter=nit, use_graph=graph)
+    phi, info = pair.C.solve(rhs, tol_rel=0.0, max_iter=nit, use_graph=graph, fused_coarse=fused)
     got = pair.C.unpack(phi).cpu().numpy()
     want, it, hist, st = pair.P.solve(c["rhs"], tol_rel=0.0, maxit=nit)
     assert info.iterations == it == nit
@@ -309,3 +313,25 @@ def test_profiled_solve_times_kernels(graph):
     assert info.smooth0_launches == 3 * 8 and info.resid0_launches == 3
     assert info.smooth0_ms > 0 and info.resid0_ms > 0
     assert info.kernel_launches > 3 * 8
+
+
+def test_fused_coarse_launches_fewer_kernels():
+    """abec-like 64^3 problem in 8 boxes: the fused coarse end replaces the per-level launches
+    of the levels at or below 4096 cells by one launch per V-cycle, and gives the same
+    iterates (the bottom's dot products add in another order: 1e-12)."""
+    from paper_2009_12009_gb300 import inputs as I
+
+    cfg = I.abec(64, 32, 4242, name="abec64")
+    C = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"],
+                    stream=torch.cuda.current_stream().cuda_stream)
+    C.allocate(gmg.FP64)
+    C.set_scalars(cfg["a"], cfg["b"])
+    C.set_beta(torch.from_numpy(cfg["beta"]))
+    rhs = C.pack(torch.from_numpy(cfg["rhs"]))
+    out = {}
+    for fused in (1, 0):
+        phi, info = C.solve(rhs, tol_rel=0.0, max_iter=5, fused_coarse=fused)
+        out[fused] = (C.unpack(phi).cpu().numpy(), info.kernel_launches)
+    a, b = out[1][0], out[0][0]
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    assert out[1][1] < out[0][1]
