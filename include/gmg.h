@@ -84,13 +84,23 @@ typedef struct {
                            instead of returning GMG_ERR_BAD_INPUT; default 0 */
   int use_graph;        /* replay the V-cycle as a captured CUDA graph, default 1 */
   int profile;          /* record CUDA events around every finest-level smoother and
-                           outer-residual launch (inside the graph too); default 0 */
+                           outer-residual launch (inside the graph too; with fused sweeps
+                           the region pass of each sweep); default 0 */
   int fused_coarse;     /* 1 (default): each problem's V-cycle levels from the first one
                            with at most 4096 of its cells (never level 0) down to its
                            bottom run as ONE thread block per problem (same arithmetic as
                            the per-level launches; only the bottom solve's dot products
                            add in another order); 0: one grid launch per step on every
                            level */
+  int fused_sweep;      /* 1: in the float and bfloat16 V-cycles, on levels with at least
+                           2^20 smoothed cells, each red-black sweep stages the planes of a
+                           box region in shared memory with TMA bulk copies and updates the
+                           red cells and the region's inner black cells in one pass; the
+                           regions' boundary black cells follow after the red ghost
+                           exchange.  Updates and results are bitwise those of the two
+                           half-sweeps.  0 (default): one pass per colour, measured faster
+                           on GB300 (the fix-up pass costs more than the halved traffic
+                           saves).  FP64 sweeps always use one pass per colour. */
 } gmg_params;
 
 typedef struct {

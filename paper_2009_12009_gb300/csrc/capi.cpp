@@ -86,6 +86,7 @@ struct gmg_ctx {
   double* partials = nullptr;
   double* scal = nullptr;  // [0, ns): rhs means; [ns, 2ns): phi means
   int* bot_iters = nullptr;
+  int* dev_err = nullptr;  // raised by a kernel whose bounded wait gave up
   int* active = nullptr;  // per problem: 1 while it iterates
   int max_cell_chunks = 0;
 
@@ -100,8 +101,12 @@ struct gmg_ctx {
   size_t h_cap = 0;
 
   // graphs of one outer iteration, keyed by (phi, rhs, precision, nu1, nu2, bottom, profile)
-  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int>, std::pair<cudaGraphExec_t, int64_t>>
-      graphs;
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    int64_t launches;
+    int n_ev_smooth, n_ev_resid;  // profiling event pairs recorded per replay
+  };
+  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int>, GraphEntry> graphs;
 
   // profiling events (pairs around finest-level smoother / outer residual launches)
   bool profiling = false;
@@ -154,7 +159,7 @@ struct gmg_ctx {
 namespace {
 
 void drop_graphs(gmg_ctx* c) {
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   c->graphs.clear();
 }
 
@@ -246,6 +251,11 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.n_vc_coarse_chunks = (int)M.vc_coarse_chunks.size();
     D.vc_bot_descs = (const BotDesc*)cv.take(sizeof(BotDesc) * M.vc_bot_descs.size());
     D.n_vc_bot = (int)M.vc_bot_descs.size();
+    D.sweep_regions = (const SweepRegion*)cv.take(sizeof(SweepRegion) * M.sweep_regions.size());
+    D.n_sweep_regions = (int)M.sweep_regions.size();
+    D.vc_sweep_regions = (const SweepRegion*)cv.take(sizeof(SweepRegion) * M.vc_sweep_regions.size());
+    D.n_vc_sweep_regions = (int)M.vc_sweep_regions.size();
+    D.sweep_cap = M.sweep_cap;
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
     B.acoef = (double*)cv.take(8 * ne);
     B.wx = (double*)cv.take(8 * ne);
@@ -367,10 +377,11 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
   unsigned long long* nb = (unsigned long long*)cv.take(8 * (2 * ns + 8));
   double* partials = (double*)cv.take(8 * (size_t)maxchunks);
   double* scal = (double*)cv.take(8 * (2 * ns + 8));
-  int* iters = (int*)cv.take(4 * ns);
+  int* iters = (int*)cv.take(4 * (ns + 1));  // bottom iterations per problem, then the device error flag
   if (fill) {
     c->alpha0 = alpha0; c->bx0 = bx0; c->by0 = by0; c->bz0 = bz0; c->tmp0 = tmp0;
     c->normbits = nb; c->partials = partials; c->scal = scal; c->bot_iters = iters;
+    c->dev_err = iters + ns;
     c->active = active;
     c->max_cell_chunks = maxchunks;
   }
@@ -422,6 +433,8 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.vc_pair_chunks, M.vc_pair_chunks))) return st;
     if ((st = upload(c, D.vc_coarse_chunks, M.vc_coarse_chunks))) return st;
     if ((st = upload(c, D.vc_bot_descs, M.vc_bot_descs))) return st;
+    if ((st = upload(c, D.sweep_regions, M.sweep_regions))) return st;
+    if ((st = upload(c, D.vc_sweep_regions, M.vc_sweep_regions))) return st;
   }
   {
     const TailHost& T = c->tail;
@@ -461,6 +474,7 @@ gmg_status upload_tables(gmg_ctx* c) {
   std::vector<int> ones(c->ns(), 1);
   gmg_status st = upload(c, c->active, ones);
   if (st) return st;
+  CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return GMG_OK;
 }
@@ -583,7 +597,26 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
   if (prof) record_timing_event(c, ev[1], s);
 }
 
-void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, cudaStream_t s) {
+// nsweep red-black sweeps on level m.  Levels with sweep regions (and fused_sweep set) run
+// each sweep as: black ghosts, fused region pass, red ghosts, fix-up of the regions'
+// boundary black cells -- the same updates as red pass + black pass, in one pass over the
+// coefficients.
+void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s) {
+  if (p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0) {
+    const LevelBufs& B = c->buf[m];
+    const Coefs k = coefs_of(c, m, dt);
+    for (int it = 0; it < nsweep; ++it) {
+      launch_fill(dt, D, B.e[dt], 1, 0, s);
+      const bool prof = c->profiling && m == 0;
+      cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
+      if (prof) record_timing_event(c, ev[0], s);
+      launch_sweep(dt, D, B.e[dt], B.r[dt], k, c->dev_err, s);
+      if (prof) record_timing_event(c, ev[1], s);
+      launch_fill(dt, D, B.e[dt], 0, 0, s);
+      launch_sweep_fixup(dt, D, B.e[dt], B.r[dt], k, s);
+    }
+    return;
+  }
   for (int it = 0; it < nsweep; ++it) {
     smooth_colour(c, D, dt, m, 0, s);
     smooth_colour(c, D, dt, m, 1, s);
@@ -602,6 +635,8 @@ LevelDev vc_view(const gmg_ctx* c, int m) {
   D.n_coarse_chunks = D.n_vc_coarse_chunks;
   D.bot_descs = D.vc_bot_descs;
   D.n_bot = D.n_vc_bot;
+  D.sweep_regions = D.vc_sweep_regions;
+  D.n_sweep_regions = D.n_vc_sweep_regions;
   return D;
 }
 
@@ -651,13 +686,13 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
     launch_bottom(dt, D, B.r[dt], B.e[dt], coefs64(c, m), a, s);
   }
   if (m + 1 >= nlev(c) || D.n_pair_chunks == 0) return;
-  smooth_sweeps(c, D, dt, m, p.nu1, s);
+  smooth_sweeps(c, D, dt, m, p.nu1, p, s);
   launch_fill(dt, D, B.e[dt], -1, 0, s);
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
   launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
   vcycle(c, dt, m + 1, p, s);
   launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s);
-  smooth_sweeps(c, D, dt, m, p.nu2, s);
+  smooth_sweeps(c, D, dt, m, p.nu2, p, s);
 }
 
 // One outer iteration: e = V(r); phi += e; r = rhs - A phi with per-problem ||r||_inf into
@@ -700,6 +735,7 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
     SETERR(c, GMG_ERR_BAD_INPUT, "invalid parameters");
   if (p.precision < GMG_FP64 || p.precision > GMG_MIXED_BF16) SETERR(c, GMG_ERR_BAD_INPUT, "invalid precision");
   if (p.fused_coarse != 0 && p.fused_coarse != 1) SETERR(c, GMG_ERR_BAD_INPUT, "fused_coarse must be 0 or 1");
+  if (p.fused_sweep != 0 && p.fused_sweep != 1) SETERR(c, GMG_ERR_BAD_INPUT, "fused_sweep must be 0 or 1");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
   return GMG_OK;
 }
@@ -785,13 +821,13 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   int sm_n = 0, rs_n = 0;
   if (p.use_graph && nlive) {
     auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
-                               p.bottom_tol, p.profile, p.fused_coarse);
+                               p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep);
     auto itg = c->graphs.find(key);
     if (itg != c->graphs.end()) {
-      gexec = itg->second.first;
-      per_iter = itg->second.second;
-      c->n_ev_smooth = 2 * (p.nu1 + p.nu2);
-      c->n_ev_resid = 1;
+      gexec = itg->second.exec;
+      per_iter = itg->second.launches;
+      c->n_ev_smooth = itg->second.n_ev_smooth;
+      c->n_ev_resid = itg->second.n_ev_resid;
     } else {
       cudaGraph_t g;
       const int64_t l0 = kernel_launch_count();
@@ -805,7 +841,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
       if (e2 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
       per_iter = kernel_launch_count() - l0;
       count_launches((int)-per_iter);  // captured, not launched
-      c->graphs[key] = {gexec, per_iter};
+      c->graphs[key] = {gexec, per_iter, c->n_ev_smooth, c->n_ev_resid};
     }
   }
   int64_t launched = 0;
@@ -859,11 +895,16 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
     launch_add_scalar(D0, phi, c->scal + ns, -1.0, s);
     CK(c, cudaGetLastError());
   }
-  CK(c, cudaMemcpyAsync(c->h_iters, c->bot_iters, 4 * (size_t)ns, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaMemcpyAsync(c->h_iters, c->bot_iters, 4 * (size_t)(ns + 1), cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
   gmg_status worst = GMG_OK;
   for (int q = 0; q < ns; ++q)
     if (status[q] != GMG_OK && (worst == GMG_OK || status[q] == GMG_ERR_DIVERGED)) worst = (gmg_status)status[q];
+  if (c->h_iters[ns]) {  // a staging wait in a fused sweep gave up: results are not trustworthy
+    CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), s));
+    for (int q = 0; q < ns; ++q) status[q] = GMG_ERR_DEVICE_TIMEOUT;
+    worst = GMG_ERR_DEVICE_TIMEOUT;
+  }
   if (infos) {
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     const int64_t tot = launched + prologue_launches + (kernel_launch_count() - l_epi);
@@ -887,6 +928,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   }
   if (worst == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
   if (worst == GMG_ERR_DIVERGED) c->err = "residual is not finite";
+  if (worst == GMG_ERR_DEVICE_TIMEOUT) c->err = "a bounded device wait gave up (fused sweep staging)";
   return worst;
 }
 
@@ -1313,6 +1355,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->use_graph = 1;
   p->profile = 0;
   p->fused_coarse = 1;
+  p->fused_sweep = 0;
   return GMG_OK;
 }
 

@@ -78,6 +78,18 @@ struct BotDesc {
   int solve;
 };
 
+// One region of a fused red-black sweep (sweep.cu): full x extent of a box, rows
+// [y0, y0 + ny) and planes [z0, z0 + nz).  The black cells on the region's boundary
+// (x faces, first/last row, first/last plane) are updated by the fix-up pass.
+struct SweepRegion {
+  int box;
+  int y0, ny;
+  int z0, nz;
+  int pad;
+};
+constexpr int SWEEP_MIN_CELLS = 1 << 20;  // levels with fewer smoothed cells keep one pass per colour
+constexpr int SWEEP_MAX_CAP = 2304;       // staged elements per plane: 4 slots x 24 B fit 220 KB
+
 // The coarse end of one problem's V-cycle run by one thread block (tail.cu): levels
 // m0..mb of that problem, mb its bottom.  Cell and ghost lists reuse BotCell / BotGhost.
 constexpr int TAIL_MAXLEV = 20;       // MG levels addressable by the tail kernel

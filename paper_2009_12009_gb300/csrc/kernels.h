@@ -49,6 +49,12 @@ struct LevelDev {
   int n_vc_coarse_chunks = 0;
   const BotDesc* vc_bot_descs = nullptr;
   int n_vc_bot = 0;
+  // fused red-black sweep regions (sweep.cu); empty: one pass per colour on this level
+  const SweepRegion* sweep_regions = nullptr;
+  int n_sweep_regions = 0;
+  const SweepRegion* vc_sweep_regions = nullptr;
+  int n_vc_sweep_regions = 0;
+  int sweep_cap = 0;  // max (rows + 2) * row stride over the regions: staged elements per plane
 };
 
 // Coefficients of one level in one element type (double for FP64 fields, float for
@@ -129,6 +135,17 @@ struct BottomArgs {
 };
 void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Coefs& c64, const BottomArgs& a,
                    cudaStream_t s);
+
+// ---- fused red-black sweep (sweep.cu) ----
+// red cells of every region and the black cells inside each region, one pass (the black
+// ghosts of phi must hold the old black values); float and bfloat16 fields only (returns
+// false, launching nothing, otherwise).  err: device flag raised if a staging wait gave up
+bool launch_sweep(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int* err, cudaStream_t s);
+// shared memory of one sweep block for regions of at most cap staged elements per plane
+size_t sweep_smem_bytes(int dt, int cap);
+// the black cells on the regions' boundaries (the red ghosts of phi must hold the new red
+// values); launch_sweep then launch_sweep_fixup = one red and one black half-sweep
+void launch_sweep_fixup(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, cudaStream_t s);
 
 // ---- coarse end of the V-cycle, one block per problem (tail.cu) ----
 struct TailArgs {

@@ -184,6 +184,50 @@ static void build_bottom(LevelMeta& L) {
   }
 }
 
+// Regions of the fused sweep: each box of a smoothing solve is cut into slabs of full x
+// extent, ry rows and rz planes.  A staged plane of a region holds (ry + 2) rows of the
+// box's row stride, at most SWEEP_MAX_CAP elements; rows are split evenly.  Boxes are then
+// cut in z until the level has at least two regions per SM of a 152-SM part (each block
+// loops over regions), keeping at least 8 planes per region.  Levels below SWEEP_MIN_CELLS
+// smoothed cells, or with a row too wide to stage 4 rows, get no regions.
+static void build_sweep_regions(LevelMeta& L) {
+  L.sweep_regions.clear();
+  L.sweep_cap = 0;
+  int64_t cells = 0;
+  for (int b = 0; b < (int)L.boxes.size(); ++b)
+    if (!L.solve_bottom[L.box_solve[b]]) cells += L.boxes[b].volume();
+  if (cells < SWEEP_MIN_CELLS) return;
+  std::vector<int> ry(L.boxes.size(), 0);
+  int64_t nreg = 0;
+  for (int b = 0; b < (int)L.boxes.size(); ++b) {
+    if (L.solve_bottom[L.box_solve[b]]) continue;
+    const DevBox& D = L.dbox[b];
+    const int rmax = std::min(D.ny, SWEEP_MAX_CAP / D.sx - 2);
+    if (rmax < 4) return;
+    const int parts = (D.ny + rmax - 1) / rmax;
+    ry[b] = (D.ny + parts - 1) / parts;
+    nreg += parts;
+  }
+  const int64_t want = 2 * 152;
+  const int zcuts = nreg >= want ? 1 : (int)((want + nreg - 1) / nreg);
+  for (int b = 0; b < (int)L.boxes.size(); ++b) {
+    if (L.solve_bottom[L.box_solve[b]]) continue;
+    const DevBox& D = L.dbox[b];
+    const int rz = std::max(std::min(D.nz, 8), (D.nz + zcuts - 1) / zcuts);
+    for (int z0 = 0; z0 < D.nz; z0 += rz)
+      for (int y0 = 0; y0 < D.ny; y0 += ry[b]) {
+        SweepRegion R{};
+        R.box = b;
+        R.y0 = y0;
+        R.ny = std::min(ry[b], D.ny - y0);
+        R.z0 = z0;
+        R.nz = std::min(rz, D.nz - z0);
+        L.sweep_regions.push_back(R);
+        L.sweep_cap = std::max(L.sweep_cap, (R.ny + 2) * D.sx);
+      }
+  }
+}
+
 std::string finalize_level(LevelMeta& L) {
   const int nb = (int)L.boxes.size();
   L.dbox.resize(nb);
@@ -234,6 +278,7 @@ std::string finalize_level(LevelMeta& L) {
     for (int64_t s = 0; s < nc; s += BLOCK) L.coarse_chunks.push_back({b, (int)s});
   }
   build_bottom(L);
+  build_sweep_regions(L);
   return "";
 }
 
@@ -429,6 +474,9 @@ std::string build_tail(std::vector<LevelMeta>& L, TailHost& T) {
     M.vc_bot_descs.clear();
     for (const BotDesc& d : M.bot_descs)
       if (!in_tail(d.solve)) M.vc_bot_descs.push_back(d);
+    M.vc_sweep_regions.clear();
+    for (const SweepRegion& r : M.sweep_regions)
+      if (!in_tail(M.box_solve[r.box])) M.vc_sweep_regions.push_back(r);
   }
   return "";
 }

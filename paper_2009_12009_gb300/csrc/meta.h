@@ -69,6 +69,11 @@ struct LevelMeta {
   // one thread block each: entries of problems whose tail covers this level are left out
   std::vector<Chunk> vc_ghost_chunks, vc_pair_chunks, vc_coarse_chunks;
   std::vector<BotDesc> vc_bot_descs;
+
+  // fused red-black sweeps: regions of the boxes of solves that smooth on this level
+  // (empty when the level has fewer than SWEEP_MIN_CELLS smoothed cells)
+  std::vector<SweepRegion> sweep_regions, vc_sweep_regions;
+  int sweep_cap = 0;
 };
 
 // Tail tables: for every problem whose bottom level is small, the levels from the first

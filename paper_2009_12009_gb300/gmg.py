@@ -37,7 +37,8 @@ EXPORTS = [
 class Params(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_iter", C.c_int), ("bottom_max_iter", C.c_int),
                 ("bottom_tol", C.c_double), ("precision", C.c_int), ("project_mean", C.c_int),
-                ("use_graph", C.c_int), ("profile", C.c_int), ("fused_coarse", C.c_int)]
+                ("use_graph", C.c_int), ("profile", C.c_int), ("fused_coarse", C.c_int),
+                ("fused_sweep", C.c_int)]
 
 
 class SolveInfo(C.Structure):

@@ -335,3 +335,45 @@ def test_fused_coarse_launches_fewer_kernels():
     a, b = out[1][0], out[0][0]
     assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
     assert out[1][1] < out[0][1]
+
+
+def _ctx_of(cfg, precision=gmg.MIXED_FP32):
+    C = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"],
+                    prob_hi=cfg.get("prob_hi", (1.0, 1.0, 1.0)), stream=torch.cuda.current_stream().cuda_stream)
+    C.allocate(precision)
+    C.set_scalars(cfg["a"], cfg["b"])
+    C.set_beta(torch.from_numpy(cfg["beta"]))
+    return C
+
+
+def _sweep_cases():
+    from paper_2009_12009_gb300 import inputs as I
+
+    rng = np.random.default_rng(77)
+    uneven_dom = ((0, 0, 0), (129, 99, 89))  # boxes 64/64/2 x 64/36 x 64/26: x-faces 2 cells apart
+    shape = (90, 100, 130)
+    uneven = dict(name="uneven_large", domain=uneven_dom, boxes=I.chop(*uneven_dom, 64), bc_lo=[I.DIRICHLET] * 3,
+                  bc_hi=[I.DIRICHLET] * 3, a=0.0, b=1.0, beta=I.lognormal_beta(rng, shape, periodic=False),
+                  rhs=rng.standard_normal(shape), prob_hi=(130 / 128, 100 / 128, 90 / 128))
+    return [I.abec(128, 64, 4343, name="abec128"), I.abec(128, 32, 4344, bc=I.PERIODIC, name="per128"), uneven]
+
+
+@pytest.mark.parametrize("case", [0, 1, 2], ids=["abec128", "periodic128_boxes32", "uneven_large"])
+def test_fused_sweep_is_bitwise_two_half_sweeps(case):
+    """Levels of >= 2^20 cells: the fused red-black sweep (region pass + fix-up of the
+    regions' boundary black cells) gives bit for bit the V-cycle and the solve of the two
+    half-sweeps, in FP64, FP32 and BF16."""
+    cfg = _sweep_cases()[case]
+    C = _ctx_of(cfg)
+    r = torch.from_numpy(cfg["rhs"] - (cfg["rhs"].mean() if cfg["bc_lo"][0] == gmg.PERIODIC else 0.0))
+    for dt in DTS:
+        rb = C.pack(r, 0, dt)
+        e1 = C.vcycle(rb, dt, fused_sweep=1)
+        e0 = C.vcycle(rb, dt, fused_sweep=0)
+        assert torch.equal(C.unpack(e1, 0, dt), C.unpack(e0, 0, dt)), dt
+    rhs = C.pack(r)
+    p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=1, project_mean=1)
+    a1 = C.unpack(p1).clone()
+    p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=0, project_mean=1)
+    assert torch.equal(a1, C.unpack(p0))
+    assert i1.kernel_launches == i0.kernel_launches
