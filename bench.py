@@ -258,6 +258,25 @@ def _form_batch64(stream, barrier):
                      "value": sum(u * k for u, k in zip(upd_s, its)) / (ms * 1e-3) / 1e6, "unit": UNIT}
     del bctx, brhs, bphi
     torch.cuda.empty_cache()
+    # the same 64 problems solved one after another, each in its own context (FP64)
+    ctxs = []
+    for p in probs:
+        c1 = gmg.Context(p["domain"], p["bc_lo"], p["bc_hi"], prob_hi=p["prob_hi"], boxes=p["boxes"],
+                         stream=stream.cuda_stream)
+        c1.allocate(gmg.FP64)
+        c1.set_scalars(0.0, 1.0)
+        c1.set_beta(torch.from_numpy(p["beta"]))
+        ctxs.append((c1, c1.pack(torch.from_numpy(p["rhs"])), c1.field(0)))
+
+    def one_by_one():
+        return [c1.solve(r1, f1, tol_rel=TOL)[1] for c1, r1, f1 in ctxs]
+
+    ms_seq, infos_seq = _timed(one_by_one, 2, 1, stream, barrier)
+    res["sequential_fp64"] = {"time_to_tol_ms": ms_seq,
+                              "all_converged": all(i.status == gmg.OK for i in infos_seq),
+                              "batched_speedup": ms_seq / res["fp64"]["time_to_tol_ms"]}
+    del ctxs
+    torch.cuda.empty_cache()
     return res
 
 

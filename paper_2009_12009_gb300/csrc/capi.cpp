@@ -587,9 +587,9 @@ void record_timing_event(gmg_ctx* c, cudaEvent_t e, cudaStream_t s) {
   else cudaEventRecord(e, s);
 }
 
-void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cudaStream_t s) {
+void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cudaStream_t s, bool fill = true) {
   const LevelBufs& B = c->buf[m];
-  launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
+  if (fill) launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
   const bool prof = c->profiling && m == 0;
   cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
   if (prof) record_timing_event(c, ev[0], s);
@@ -601,12 +601,15 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
 // each sweep as: black ghosts, fused region pass, red ghosts, fix-up of the regions'
 // boundary black cells -- the same updates as red pass + black pass, in one pass over the
 // coefficients.
-void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s) {
+// e_zero: e is zero including its ghosts (just cleared), so the first ghost fill would
+// copy zeros and is skipped.
+void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s,
+                   bool e_zero = false) {
   if (p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0) {
     const LevelBufs& B = c->buf[m];
     const Coefs k = coefs_of(c, m, dt);
     for (int it = 0; it < nsweep; ++it) {
-      launch_fill(dt, D, B.e[dt], 1, 0, s);
+      if (!(e_zero && it == 0)) launch_fill(dt, D, B.e[dt], 1, 0, s);
       const bool prof = c->profiling && m == 0;
       cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
       if (prof) record_timing_event(c, ev[0], s);
@@ -618,7 +621,7 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
     return;
   }
   for (int it = 0; it < nsweep; ++it) {
-    smooth_colour(c, D, dt, m, 0, s);
+    smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0));
     smooth_colour(c, D, dt, m, 1, s);
   }
 }
@@ -686,8 +689,8 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
     launch_bottom(dt, D, B.r[dt], B.e[dt], coefs64(c, m), a, s);
   }
   if (m + 1 >= nlev(c) || D.n_pair_chunks == 0) return;
-  smooth_sweeps(c, D, dt, m, p.nu1, p, s);
-  launch_fill(dt, D, B.e[dt], -1, 0, s);
+  smooth_sweeps(c, D, dt, m, p.nu1, p, s, true);
+  if (p.nu1 > 0) launch_fill(dt, D, B.e[dt], -1, 0, s);  // (nu1 = 0: e and its ghosts are still zero)
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
   launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
   vcycle(c, dt, m + 1, p, s);
