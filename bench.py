@@ -151,6 +151,13 @@ def cpu_baseline(cfg, iters=2):
             "sample": f"{it} V-cycle iterations of the abec256 solve (FP64 oracle, 1 thread), {dt:.1f} s"}
 
 
+def summarize_tuning(t):
+    """ghost push chosen per MG level (1 push, 0 exchange, -1 not eligible) and the fused
+    coarse end (1 on), as gmg_autotune measured them"""
+    return {"ghost_push_per_level": [lv[0] for lv in t["levels"]], "fused_coarse": t["fused_coarse"],
+            "vcycle_ms_fused_vs_levels": [round(x, 4) for x in t["vcycle_ms"]]}
+
+
 def _timed(fn, steps, warmup, stream, barrier):
     """device time (ms) per call of fn over `steps` calls after `warmup`; returns (ms, last)"""
     import torch
@@ -214,7 +221,9 @@ def _form_abec512(stream, barrier):
     del cfg
     phi = ctx.field(0)
     upd = mcell_updates_per_vcycle(ctx, 4)
-    res = {"workload": "abec512: 512^3 Dirichlet, 64 boxes of 128^3, abec recipe seed 12012, tol 1e-10"}
+    res = {"workload": "abec512: 512^3 Dirichlet, 64 boxes of 128^3, abec recipe seed 12012, tol 1e-10",
+           "autotuned": {name: summarize_tuning(ctx.autotune(rhs, prec))
+                         for name, prec in (("fp64", gmg.FP64), ("fp32", gmg.MIXED_FP32), ("bf16", gmg.MIXED_BF16))}}
     ref = None
     for name, prec in (("fp64", gmg.FP64), ("fp32", gmg.MIXED_FP32), ("bf16", gmg.MIXED_BF16)):
         ms, info = _timed(lambda: ctx.solve(rhs, phi, tol_rel=TOL, precision=prec)[1], 3, 1, stream, barrier)
@@ -248,7 +257,9 @@ def _form_batch64(stream, barrier):
     cells = sum(int(np.prod(p["rhs"].shape)) for p in probs)
     upd_s = [_updates_per_vcycle_problem(bctx, s) for s in range(len(probs))]
     bphi = bctx.field(0)
-    res = {"workload": f"batch64: 64 problems, edges from {{32,...,160}}, boxes <= 32^3, {cells} cells, "
+    tuned = {name: summarize_tuning(bctx.autotune(brhs, prec)) for name, prec in (("fp64", gmg.FP64),
+                                                                                 ("fp32", gmg.MIXED_FP32))}
+    res = {"autotuned": tuned, "workload": f"batch64: 64 problems, edges from {{32,...,160}}, boxes <= 32^3, {cells} cells, "
                        f"{bctx.level_info(0)[0]} boxes, abec recipe seeds 12014+i (i = 0..63), tol 1e-10 each"}
     for name, prec in (("fp64", gmg.FP64), ("fp32", gmg.MIXED_FP32)):
         ms, infos = _timed(lambda: bctx.batch_solve(brhs, bphi, tol_rel=TOL, precision=prec)[1], 3, 1, stream, barrier)
@@ -292,6 +303,7 @@ def _form_amr2(stream, barrier, dev):
     actx.allocate(gmg.FP64)
     actx.set_coeffs(0.0, 1.0, beta_c=torch.from_numpy(a["beta_c"]), beta_f=torch.from_numpy(a["beta_f"]))
     rc, rf = actx.pack_level(0, torch.from_numpy(a["rhs_c"])), actx.pack_level(1, torch.from_numpy(a["rhs_f"]))
+    tuned = summarize_tuning(actx.autotune(rc, gmg.FP64))
     ms_f, (pc, pf, info_f) = _timed(lambda: actx.solve2(rc, rf, tol_rel=TOL), 3, 1, stream, barrier)
     # dL/dphi of L = 0.5 |phi - phi_target|^2 over the composite cells
     keep = torch.as_tensor(~a["covered"], device=dev, dtype=torch.float64)
@@ -303,7 +315,7 @@ def _form_amr2(stream, barrier, dev):
                         "coarse cells (128^3 fine cells, 8 boxes), seed 12014, tol 1e-10",
             "forward": {"time_to_tol_ms": ms_f, "iterations": info_f.iterations, "status": info_f.status},
             "adjoint": {"time_to_tol_ms": ms_a, "iterations": info_a.iterations, "status": info_a.status},
-            "beta_grad_ms": ms_g}
+            "beta_grad_ms": ms_g, "autotuned_level0_hierarchy": tuned}
 
 
 def run_reference(args):
@@ -380,6 +392,10 @@ def main():
     phi = ctx.field(0)
     ncells = int(np.prod(ctx.level_shape(0)))
     nu = 4
+    tuned = {"fp64": ctx.autotune(rhs, gmg.FP64)}
+    if not args.no_mixed:
+        tuned["fp32"] = ctx.autotune(rhs, gmg.MIXED_FP32)
+        tuned["bf16"] = ctx.autotune(rhs, gmg.MIXED_BF16)
     upd_per_vc = mcell_updates_per_vcycle(ctx, nu)
 
     def barrier():
@@ -433,7 +449,8 @@ def main():
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "cells": ncells, "mg_levels": ctx.nlevels,
                       "cell_updates_per_vcycle": upd_per_vc, "parallelism": f"replicas x{world}",
-                      "l2": "inputs larger than L2 (finest-level working set ~1.2 GB of fields and coefficients)"},
+                      "l2": "inputs larger than L2 (finest-level working set ~1.2 GB of fields and coefficients)",
+                      "autotuned": {k: summarize_tuning(v) for k, v in tuned.items()}},
            "gpu_launches": int(sum(i.kernel_launches for i in infos)),
            "roofline": {"bound": "hbm", "kernel": "k_smooth<double> (finest level, one colour)",
                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -86,12 +86,12 @@ typedef struct {
   int profile;          /* record CUDA events around every finest-level smoother and
                            outer-residual launch (inside the graph too; with fused sweeps
                            the region pass of each sweep); default 0 */
-  int fused_coarse;     /* 1 (default): each problem's V-cycle levels from the first one
-                           with at most 4096 of its cells (never level 0) down to its
-                           bottom run as ONE thread block per problem (same arithmetic as
-                           the per-level launches; only the bottom solve's dot products
-                           add in another order); 0: one grid launch per step on every
-                           level */
+  int fused_coarse;     /* 1: each problem's V-cycle levels from the first one with at most
+                           512 of its cells (never level 0) down to its bottom run as ONE
+                           thread block per problem (same arithmetic as the per-level
+                           launches; only the bottom solve's dot products add in another
+                           order); 0: one grid launch per step on every level; 2 (default):
+                           the gmg_autotune choice, 1 before tuning */
   int fused_sweep;      /* 1: in the float and bfloat16 V-cycles, on levels with at least
                            2^20 smoothed cells, each red-black sweep stages the planes of a
                            box region in shared memory with TMA bulk copies and updates the
@@ -101,6 +101,15 @@ typedef struct {
                            half-sweeps.  0 (default): one pass per colour, measured faster
                            on GB300 (the fix-up pass costs more than the halved traffic
                            saves).  FP64 sweeps always use one pass per colour. */
+  int ghost_push;       /* 1: in the V-cycle the smoother and the interpolation write every
+                           new value also into the ghost cells that copy it, so the ghost
+                           exchanges before each colour and before the restriction are not
+                           needed (levels whose every box face is copied whole into one
+                           ghost rectangle and whose periodic lengths are all even, so a
+                           ghost has its source's colour); same values as the exchange.
+                           0: ghost exchange before every colour.  2 (default): per level,
+                           the gmg_autotune choice; before tuning, push on levels of fewer
+                           than 2^22 cells (where the exchange is launch-latency bound) */
 } gmg_params;
 
 typedef struct {
@@ -299,6 +308,26 @@ gmg_status gmg_bottom_solve(gmg_ctx* ctx, int dt, const void* rhs, void* x, cons
 
 /* One V-cycle on the correction equation of MG level 0: e = V(r), element type dt. */
 gmg_status gmg_vcycle(gmg_ctx* ctx, int dt, void* e, const void* r, const gmg_params* p);
+
+/* -------------------------------------------------------------- autotuning */
+
+/* Launch-shape autotuner (no counterpart in the paper).  For the V-cycle of the given
+   precision it times, on this context's own levels and buffers (CUDA events, a few
+   repetitions each), (1) per MG level: a red-black sweep with the ghost push against the
+   ghost exchange before each colour, and (2) whole V-cycles with the fused coarse end
+   against per-level launches, and keeps the faster of each.  Solves and V-cycles whose
+   params have ghost_push = 2 / fused_coarse = 2 (the defaults) use the choices; the
+   results do not depend on them.  rhs: FP64 level-0 boxed right-hand side (device), used
+   to fill the correction equation.  Clobbers the V-cycle work buffers only; drops cached
+   graphs. */
+gmg_status gmg_autotune(gmg_ctx* ctx, int precision, const void* rhs, const gmg_params* p);
+
+/* The tuned choice for MG level m and precision: *push = 1 push, 0 exchange, -1 not tuned
+   (or not eligible); the measured ms per sweep both ways; *fused_coarse = 1/0/-1 and the
+   measured ms per V-cycle with (fused) and without (levels) the fused coarse end.  Any
+   output pointer may be NULL. */
+gmg_status gmg_tuned(const gmg_ctx* ctx, int precision, int m, int* push, double* ms_push, double* ms_pull,
+                     int* fused_coarse, double* ms_vcycle_fused, double* ms_vcycle_levels);
 
 /* ------------------------------------------------------------ batched form */
 

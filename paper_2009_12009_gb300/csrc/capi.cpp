@@ -106,7 +106,7 @@ struct gmg_ctx {
     int64_t launches;
     int n_ev_smooth, n_ev_resid;  // profiling event pairs recorded per replay
   };
-  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int>, GraphEntry> graphs;
+  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int>, GraphEntry> graphs;
 
   // profiling events (pairs around finest-level smoother / outer residual launches)
   bool profiling = false;
@@ -115,6 +115,13 @@ struct gmg_ctx {
 
   // cell beta of level 0 as last set (ghosts filled), for beta gradients
   double* betac_cell = nullptr;
+
+  // autotuned choices (gmg_autotune), per element type: ghost push per MG level (-1: not
+  // tuned), fused coarse end (-1: not tuned); graphs are rebuilt after tuning
+  std::vector<signed char> push_choice[NDT];
+  int tail_choice[NDT] = {-1, -1, -1};
+  std::vector<double> tune_ms_push[NDT], tune_ms_pull[NDT];
+  double tune_ms_tail[NDT][2] = {{0, 0}, {0, 0}, {0, 0}};
 
   // coarse ends of the problems' V-cycles, one thread block each (tail.cu)
   TailHost tail;
@@ -256,6 +263,8 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.vc_sweep_regions = (const SweepRegion*)cv.take(sizeof(SweepRegion) * M.vc_sweep_regions.size());
     D.n_vc_sweep_regions = (int)M.vc_sweep_regions.size();
     D.sweep_cap = M.sweep_cap;
+    D.push_faces = (const PushFace*)cv.take(sizeof(PushFace) * M.push_faces.size());
+    D.push_ok = M.push_ok ? 1 : 0;
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
     B.acoef = (double*)cv.take(8 * ne);
     B.wx = (double*)cv.take(8 * ne);
@@ -435,6 +444,7 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.vc_bot_descs, M.vc_bot_descs))) return st;
     if ((st = upload(c, D.sweep_regions, M.sweep_regions))) return st;
     if ((st = upload(c, D.vc_sweep_regions, M.vc_sweep_regions))) return st;
+    if ((st = upload(c, D.push_faces, M.push_faces))) return st;
   }
   {
     const TailHost& T = c->tail;
@@ -492,6 +502,12 @@ void reset_problem(gmg_ctx* c) {
   c->have_beta_f = c->have_alpha_f = false;
   c->tail = TailHost();
   c->tail_ok = false;
+  for (int d = 0; d < NDT; ++d) {
+    c->push_choice[d].clear();
+    c->tail_choice[d] = -1;
+    c->tune_ms_push[d].clear();
+    c->tune_ms_pull[d].clear();
+  }
 }
 
 // Build the multigrid hierarchy from level-0 boxes (stored problem by problem).
@@ -587,13 +603,16 @@ void record_timing_event(gmg_ctx* c, cudaEvent_t e, cudaStream_t s) {
   else cudaEventRecord(e, s);
 }
 
-void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cudaStream_t s, bool fill = true) {
+// push: the smoother writes its new values into the ghost cells that copy them, so no
+// ghost exchange precedes a colour (the ghosts are kept current since e was cleared)
+void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cudaStream_t s, bool fill = true,
+                   bool push = false) {
   const LevelBufs& B = c->buf[m];
-  if (fill) launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
+  if (fill && !push) launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
   const bool prof = c->profiling && m == 0;
   cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
   if (prof) record_timing_event(c, ev[0], s);
-  launch_smooth(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s);
+  launch_smooth(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s, push);
   if (prof) record_timing_event(c, ev[1], s);
 }
 
@@ -604,7 +623,7 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
 // e_zero: e is zero including its ghosts (just cleared), so the first ghost fill would
 // copy zeros and is skipped.
 void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s,
-                   bool e_zero = false) {
+                   bool e_zero = false, bool push = false) {
   if (p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0) {
     const LevelBufs& B = c->buf[m];
     const Coefs k = coefs_of(c, m, dt);
@@ -621,8 +640,8 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
     return;
   }
   for (int it = 0; it < nsweep; ++it) {
-    smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0));
-    smooth_colour(c, D, dt, m, 1, s);
+    smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0), push);
+    smooth_colour(c, D, dt, m, 1, s, true, push);
   }
 }
 
@@ -678,8 +697,23 @@ void launch_tails(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s
 // recurse, interpolate and smooth again.  With fused_coarse, each problem's levels from
 // its first level of at most TAIL_MAX_CELLS cells down to its bottom run in one thread
 // block (launched when the descent reaches that level) and the grid launches skip them.
+// ghost push on level m: 1 always (where the level allows it), 2 the tuned choice (before
+// tuning: levels below 2^22 cells, whose ghost exchanges are launch-latency bound)
+bool push_on(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
+  if (p.ghost_push == 0) return false;
+  if (p.ghost_push == 1) return true;
+  const auto& ch = c->push_choice[dt];
+  if (m < (int)ch.size() && ch[m] >= 0) return ch[m] == 1;
+  return c->L[m].ncells < (1 << 22);
+}
+
+bool tail_on(const gmg_ctx* c, const gmg_params& p, int dt) {
+  if (p.fused_coarse == 2) return c->tail_choice[dt] != 0;  // untuned: on
+  return p.fused_coarse == 1;
+}
+
 void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
-  const bool fused = p.fused_coarse && c->tail_ok;
+  const bool fused = tail_on(c, p, dt) && c->tail_ok;
   const LevelDev D = fused ? vc_view(c, m) : c->dev[m];
   const LevelBufs& B = c->buf[m];
   cudaMemsetAsync(B.e[dt], 0, dt_size(dt) * (size_t)c->L[m].nelem, s);
@@ -689,13 +723,17 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
     launch_bottom(dt, D, B.r[dt], B.e[dt], coefs64(c, m), a, s);
   }
   if (m + 1 >= nlev(c) || D.n_pair_chunks == 0) return;
-  smooth_sweeps(c, D, dt, m, p.nu1, p, s, true);
-  if (p.nu1 > 0) launch_fill(dt, D, B.e[dt], -1, 0, s);  // (nu1 = 0: e and its ghosts are still zero)
+  // ghost push (every value written also lands in the ghosts that copy it) on levels whose
+  // ghosts share their source's colour, when the sweep is the two-pass one
+  const bool push =
+      push_on(c, p, dt, m) && D.push_ok && !(p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0);
+  smooth_sweeps(c, D, dt, m, p.nu1, p, s, true, push);
+  if (p.nu1 > 0 && !push) launch_fill(dt, D, B.e[dt], -1, 0, s);  // (nu1 = 0: e and its ghosts are still zero)
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
   launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
   vcycle(c, dt, m + 1, p, s);
-  launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s);
-  smooth_sweeps(c, D, dt, m, p.nu2, p, s);
+  launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
+  smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push);
 }
 
 // One outer iteration: e = V(r); phi += e; r = rhs - A phi with per-problem ||r||_inf into
@@ -737,8 +775,9 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.nu1 < 0 || p.nu2 < 0 || p.nu1 + p.nu2 == 0 || p.max_iter < 0 || p.bottom_max_iter < 1 || !(p.bottom_tol > 0))
     SETERR(c, GMG_ERR_BAD_INPUT, "invalid parameters");
   if (p.precision < GMG_FP64 || p.precision > GMG_MIXED_BF16) SETERR(c, GMG_ERR_BAD_INPUT, "invalid precision");
-  if (p.fused_coarse != 0 && p.fused_coarse != 1) SETERR(c, GMG_ERR_BAD_INPUT, "fused_coarse must be 0 or 1");
+  if (p.fused_coarse < 0 || p.fused_coarse > 2) SETERR(c, GMG_ERR_BAD_INPUT, "fused_coarse must be 0, 1 or 2");
   if (p.fused_sweep != 0 && p.fused_sweep != 1) SETERR(c, GMG_ERR_BAD_INPUT, "fused_sweep must be 0 or 1");
+  if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
   return GMG_OK;
 }
@@ -824,7 +863,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   int sm_n = 0, rs_n = 0;
   if (p.use_graph && nlive) {
     auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
-                               p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep);
+                               p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep, p.ghost_push);
     auto itg = c->graphs.find(key);
     if (itg != c->graphs.end()) {
       gexec = itg->second.exec;
@@ -1344,6 +1383,29 @@ gmg_status set_domain_geom(gmg_ctx* c, SolveGeom& G, const int lo[3], const int 
 
 // ====================================================================== C ABI
 
+namespace {
+
+// Time `body` (stream-ordered launches) reps times with CUDA events on the context stream;
+// returns ms per rep.
+template <class F>
+double time_reps(gmg_ctx* c, int reps, F body) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  body();  // warm-up
+  cudaEventRecord(a, c->stream);
+  for (int i = 0; i < reps; ++i) body();
+  cudaEventRecord(b, c->stream);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return (double)ms / reps;
+}
+
+}  // namespace
+
 extern "C" {
 
 gmg_status gmg_default_params(gmg_params* p) {
@@ -1357,8 +1419,9 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->project_mean = 0;
   p->use_graph = 1;
   p->profile = 0;
-  p->fused_coarse = 1;
+  p->fused_coarse = 2;
   p->fused_sweep = 0;
+  p->ghost_push = 2;
   return GMG_OK;
 }
 
@@ -1851,6 +1914,78 @@ gmg_status gmg_bottom_solve(gmg_ctx* c, int dt, const void* rhs, void* x, const 
     CK(c, cudaStreamSynchronize(c->stream));
     *iters = c->h_iters[0];
   }
+  return GMG_OK;
+}
+
+gmg_status gmg_autotune(gmg_ctx* c, int precision, const void* rhs, const gmg_params* pp) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_params p;
+  gmg_default_params(&p);
+  if (pp) p = *pp;
+  gmg_status st;
+  if ((st = params_ok(c, p))) return st;
+  const int dt = dt_of_precision(precision);
+  if ((st = check_level(c, 0, dt))) return st;
+  if (!rhs) SETERR(c, GMG_ERR_BAD_INPUT, "autotune needs a level-0 right-hand side");
+  if ((st = build_coefs(c))) return st;
+  drop_graphs(c);
+  cudaStream_t s = c->stream;
+  const int n = nlev(c);
+  const int reps = 5;
+  // a realistic level-0 correction equation: r = rhs (its mean removed for singular problems
+  // does not matter for timing), and one V-cycle to populate every level's r
+  launch_convert(DT_F64, dt, rhs, c->buf[0].r[dt], c->L[0].nelem, s);
+  gmg_params q = p;
+  q.fused_coarse = 1;
+  q.ghost_push = 0;
+  q.fused_sweep = 0;
+  vcycle(c, dt, 0, q, s);
+  // ghost push vs exchange per level: two colour passes each way on the level's own buffers
+  c->push_choice[dt].assign(n, -1);
+  c->tune_ms_push[dt].assign(n, 0.0);
+  c->tune_ms_pull[dt].assign(n, 0.0);
+  for (int m = 0; m < n; ++m) {
+    const LevelDev& D = c->dev[m];
+    if (!D.push_ok || D.n_pair_chunks == 0) continue;
+    const LevelBufs& B = c->buf[m];
+    const Coefs k = coefs_of(c, m, dt);
+    const double pull = time_reps(c, reps, [&] {
+      for (int colour = 0; colour < 2; ++colour) {
+        launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
+        launch_smooth(dt, D, B.e[dt], B.r[dt], k, colour, s, false);
+      }
+    });
+    const double push = time_reps(c, reps, [&] {
+      for (int colour = 0; colour < 2; ++colour) launch_smooth(dt, D, B.e[dt], B.r[dt], k, colour, s, true);
+    });
+    c->tune_ms_pull[dt][m] = pull;
+    c->tune_ms_push[dt][m] = push;
+    c->push_choice[dt][m] = push < pull ? 1 : 0;
+  }
+  // fused coarse end vs per-level launches, whole V-cycles with the choices above
+  q.ghost_push = 2;
+  for (int f = 0; f < 2; ++f) {
+    q.fused_coarse = f;
+    c->tune_ms_tail[dt][f] = time_reps(c, reps, [&] { vcycle(c, dt, 0, q, s); });
+  }
+  c->tail_choice[dt] = c->tune_ms_tail[dt][1] <= c->tune_ms_tail[dt][0] ? 1 : 0;
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_tuned(const gmg_ctx* c, int precision, int m, int* push, double* ms_push, double* ms_pull,
+                     int* fused_coarse, double* ms_vcycle_fused, double* ms_vcycle_levels) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  const int dt = dt_of_precision(precision);
+  if (dt < 0 || dt >= NDT || m < 0 || m >= (int)c->L.size()) return GMG_ERR_BAD_INPUT;
+  const auto& ch = c->push_choice[dt];
+  if (push) *push = m < (int)ch.size() ? ch[m] : -1;
+  if (ms_push) *ms_push = m < (int)c->tune_ms_push[dt].size() ? c->tune_ms_push[dt][m] : 0.0;
+  if (ms_pull) *ms_pull = m < (int)c->tune_ms_pull[dt].size() ? c->tune_ms_pull[dt][m] : 0.0;
+  if (fused_coarse) *fused_coarse = c->tail_choice[dt];
+  if (ms_vcycle_fused) *ms_vcycle_fused = c->tune_ms_tail[dt][1];
+  if (ms_vcycle_levels) *ms_vcycle_levels = c->tune_ms_tail[dt][0];
   return GMG_OK;
 }
 

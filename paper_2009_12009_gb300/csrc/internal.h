@@ -38,6 +38,15 @@ struct DevBox {
   int solve;     // index of the independent solve this box belongs to (batched form)
 };
 
+// Ghost push target of one box face (2 * axis + side): the cells of the face are copied,
+// times sign, into box `box` at the same cell shifted by (dx, dy, dz); box < 0: none.
+struct PushFace {
+  int box;
+  int sign;
+  int dx, dy, dz;
+  int pad;
+};
+
 // One rectangle of face ghost cells of box dst_box and where its values come from.
 struct GhostRect {
   int dst_box, src_box;

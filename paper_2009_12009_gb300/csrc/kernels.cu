@@ -109,6 +109,29 @@ __device__ __forceinline__ void pair_decode(const DevBox& B, int t, int& i0, int
   i0 = 2 * p;
 }
 
+// Ghost push: the new value v of cell (i, j, k) of box B (index b) is also written into
+// the ghost cells that copy it -- one per face of B the cell lies on, the whole face being
+// copied to a translate in one box (walls: into B's own ghost, negated) -- so the next step
+// needs no ghost exchange.  The values a pull exchange would copy land in the same places;
+// the caller uses it only where a ghost has its source's colour (even periodic lengths),
+// so a colour pass never reads a ghost it writes.
+template <class T, class A>
+__device__ __forceinline__ void push_ghosts(const DevBox& B, int b, const DevBox* __restrict__ boxes,
+                                            const PushFace* __restrict__ faces, T* f, int i, int j, int k, A v) {
+  if (i != 0 && i != B.nx - 1 && j != 0 && j != B.ny - 1 && k != 0 && k != B.nz - 1) return;
+#pragma unroll
+  for (int fc = 0; fc < 6; ++fc) {
+    const int d = fc >> 1;
+    const int c = d == 0 ? i : (d == 1 ? j : k);
+    const int nd = d == 0 ? B.nx : (d == 1 ? B.ny : B.nz);
+    if (c != ((fc & 1) ? nd - 1 : 0)) continue;
+    const PushFace P = faces[6 * b + fc];
+    if (P.box < 0) continue;
+    const DevBox Bd = boxes[P.box];
+    st(f + elem_index(Bd, i + P.dx, j + P.dy, k + P.dz), P.sign < 0 ? -v : v);
+  }
+}
+
 // ------------------------------------------------------------ red-black smoother
 
 // One colour of Gauss-Seidel: each thread owns a pair of x-adjacent cells and updates
@@ -121,7 +144,8 @@ __global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ box
                                                   const typename CoefOf<T>::type* __restrict__ wy,
                                                   const typename CoefOf<T>::type* __restrict__ wz,
                                                   const typename CoefOf<T>::type* __restrict__ invD, int colour,
-                                                  const int* __restrict__ active) {
+                                                  const int* __restrict__ active,
+                                                  const PushFace* __restrict__ push) {
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
@@ -141,7 +165,9 @@ __global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ box
   s = fma((A)ldg(wy + q + sx), (A)ld(phi + q + sx), s);
   s = fma((A)ldg(wz + q), (A)ld(phi + q - sy), s);
   s = fma((A)ldg(wz + q + sy), (A)ld(phi + q + sy), s);
-  st(phi + q, s * (A)ldg(invD + q));
+  s = s * (A)ldg(invD + q);
+  st(phi + q, s);
+  if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, s);
 }
 
 // ------------------------------------------------------------------- residual
@@ -250,7 +276,7 @@ template <class T>
 __global__ void __launch_bounds__(BLOCK)
     k_prolong_add(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes, const int* __restrict__ parent,
                   const Chunk* __restrict__ chunks, const T* __restrict__ coarse, T* fine,
-                  const int* __restrict__ active) {
+                  const int* __restrict__ active, const PushFace* __restrict__ push) {
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox F = fboxes[ch.item];
@@ -267,8 +293,13 @@ __global__ void __launch_bounds__(BLOCK)
   for (int dk = 0; dk < 2; ++dk)
     for (int dj = 0; dj < 2; ++dj) {
       const int64_t q = elem_index(F, 2 * ci, 2 * cj + dj, 2 * ck + dk);
-      st(fine + q, (A)ld(fine + q) + e);
-      st(fine + q + 1, (A)ld(fine + q + 1) + e);
+      const A v0 = (A)ld(fine + q) + e, v1 = (A)ld(fine + q + 1) + e;
+      st(fine + q, v0);
+      st(fine + q + 1, v1);
+      if (push) {
+        push_ghosts(F, ch.item, fboxes, push, fine, 2 * ci, 2 * cj + dj, 2 * ck + dk, v0);
+        push_ghosts(F, ch.item, fboxes, push, fine, 2 * ci + 1, 2 * cj + dj, 2 * ck + dk, v1);
+      }
     }
 }
 
@@ -539,13 +570,15 @@ void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, 
                                                                            (T*)f, colour, copy_mode, L.active)));
 }
 
-void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour, cudaStream_t s) {
+void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour, cudaStream_t s,
+                   bool push) {
   if (!L.n_pair_chunks) return;
   ++g_launches;
+  const PushFace* pf = push ? L.push_faces : nullptr;
   GMG_DISPATCH(dt, (k_smooth<T><<<grid_of(L.n_pair_chunks), BLOCK, 0, s>>>(
                        L.boxes, L.pair_chunks, (T*)phi, (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
                        (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
-                       (const typename CoefOf<T>::type*)c.invD, colour, L.active)));
+                       (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf)));
 }
 
 // residual work list: pair items over every box (the bottom level included)
@@ -586,12 +619,13 @@ void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* f
                                                                                  (T*)coarse)));
 }
 
-void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine, cudaStream_t s) {
+void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine, cudaStream_t s,
+                        bool push) {
   if (!f.n_coarse_chunks) return;
   ++g_launches;
-  GMG_DISPATCH(dt, (k_prolong_add<T><<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(f.boxes, c.boxes, f.parent,
-                                                                                    f.coarse_chunks, (const T*)coarse,
-                                                                                    (T*)fine, f.active)));
+  const PushFace* pf = push ? f.push_faces : nullptr;
+  GMG_DISPATCH(dt, (k_prolong_add<T><<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(
+                       f.boxes, c.boxes, f.parent, f.coarse_chunks, (const T*)coarse, (T*)fine, f.active, pf)));
 }
 
 void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s) {

@@ -55,6 +55,8 @@ struct LevelDev {
   const SweepRegion* vc_sweep_regions = nullptr;
   int n_vc_sweep_regions = 0;
   int sweep_cap = 0;  // max (rows + 2) * row stride over the regions: staged elements per plane
+  const PushFace* push_faces = nullptr;  // 6 per box (ghost push targets)
+  int push_ok = 0;                       // push_faces usable for every box of the level
 };
 
 // Coefficients of one level in one element type (double for FP64 fields, float for
@@ -71,9 +73,10 @@ struct Coefs {
 // ghost exchange; colour -1 = all ghosts; copy_mode: skip wall rectangles (coefficient
 // fills, where the wall face is handled by the face kernel)
 void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, cudaStream_t s);
-// one red-black colour (no ghost fill)
+// one red-black colour (no ghost fill); push: also write each new value into the ghost
+// cells that copy it (L.push_ok levels only)
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour,
-                   cudaStream_t s);
+                   cudaStream_t s, bool push = false);
 // r = (rhs - shift[solve]) - A phi on valid cells (ghosts of phi must be filled); rdt =
 // type of r; maxbits (may be null): per-solve atomic max of |r| as IEEE bits; shift (may be
 // null): per-solve device scalars
@@ -84,7 +87,7 @@ void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const v
                            const Coefs& cf, void* rc, cudaStream_t s);
 void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s);
 void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine,
-                        cudaStream_t s);
+                        cudaStream_t s, bool push = false);
 // phi (double) += e (type dt) on valid cells
 void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s);
 // dense (nz,ny,nx) double over the level's (single-solve) domain <-> boxed type dt

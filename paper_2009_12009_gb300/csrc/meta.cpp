@@ -249,6 +249,31 @@ std::string finalize_level(LevelMeta& L) {
   if (L.parent.size() != (size_t)nb) L.parent.assign(nb, -1);
   std::string err = build_ghosts(L);
   if (!err.empty()) return err;
+  // push faces: each ghost rectangle copies one face of its source box (its source layer is
+  // the box's first or last layer along the normal) to a translate in the destination box
+  L.push_faces.assign((size_t)nb * 6, PushFace{-1, 1, 0, 0, 0, 0});
+  L.push_ok = true;
+  for (const GhostRect& g : L.ghosts) {
+    const int d = 3 - g.d1 - g.d2;
+    const DevBox& S = L.dbox[g.src_box];
+    const int n[3] = {S.nx, S.ny, S.nz};
+    if (n[d] < 2 || (g.src[d] != 0 && g.src[d] != n[d] - 1) || g.n1 != n[g.d1] || g.n2 != n[g.d2] ||
+        g.src[g.d1] != 0 || g.src[g.d2] != 0) {
+      L.push_ok = false;  // a face split over several rectangles, or a one-cell-thick box
+      continue;
+    }
+    PushFace& P = L.push_faces[(size_t)g.src_box * 6 + 2 * d + (g.src[d] == 0 ? 0 : 1)];
+    if (P.box >= 0) L.push_ok = false;  // two rectangles from one face
+    P.box = g.dst_box;
+    P.sign = g.sign;
+    P.dx = g.dst[0] - g.src[0];
+    P.dy = g.dst[1] - g.src[1];
+    P.dz = g.dst[2] - g.src[2];
+  }
+  for (int q = 0; q < (int)L.geoms.size(); ++q)
+    if (L.solve_present[q])
+      for (int d = 0; d < 3; ++d)
+        if (L.geoms[q].periodic(d) && L.geoms[q].domain.n(d) % 2 != 0) L.push_ok = false;
   L.pair_chunks.clear();
   L.pair_all_chunks.clear();
   L.cell_chunks.clear();

@@ -54,6 +54,9 @@ struct LevelMeta {
 
   // cached tables
   std::vector<GhostRect> ghosts;
+  std::vector<PushFace> push_faces;  // 6 per box: where each face's cells are copied
+  bool push_ok = false;  // every face copied whole into one ghost rectangle, every periodic
+                         // length even (a ghost has its source's colour)
   std::vector<Chunk> ghost_chunks;
   std::vector<Chunk> pair_chunks;    // boxes of solves that smooth on this level, 2 cells per item
   std::vector<Chunk> pair_all_chunks;  // every box, 2 cells per item

@@ -30,7 +30,7 @@ EXPORTS = [
     "gmg_smooth", "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_bottom_solve", "gmg_vcycle",
     "gmg_box_bicgstab_noalloc", "gmg_define_batch", "gmg_num_solves", "gmg_solve_boxes", "gmg_pack_solve",
     "gmg_unpack_solve", "gmg_batch_solve", "gmg_amr_level_boxes", "gmg_pack_amr", "gmg_unpack_amr",
-    "gmg_apply_transpose", "gmg_solve_adjoint", "gmg_beta_grad",
+    "gmg_apply_transpose", "gmg_solve_adjoint", "gmg_beta_grad", "gmg_autotune", "gmg_tuned",
 ]
 
 
@@ -38,7 +38,7 @@ class Params(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_iter", C.c_int), ("bottom_max_iter", C.c_int),
                 ("bottom_tol", C.c_double), ("precision", C.c_int), ("project_mean", C.c_int),
                 ("use_graph", C.c_int), ("profile", C.c_int), ("fused_coarse", C.c_int),
-                ("fused_sweep", C.c_int)]
+                ("fused_sweep", C.c_int), ("ghost_push", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -122,6 +122,9 @@ def _declare(L):
         "gmg_solve_adjoint": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_double, C.POINTER(Params),
                               C.POINTER(SolveInfo)],
         "gmg_beta_grad": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)],
+        "gmg_autotune": [vp, C.c_int, vp, C.POINTER(Params)],
+        "gmg_tuned": [vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                      C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -362,6 +365,26 @@ class Context:
         it = C.c_int()
         self._check(self.L.gmg_bottom_solve(self.h, dt, _ptr(rhs), _ptr(x), C.byref(p), C.byref(it)))
         return x, it.value
+
+    def autotune(self, rhs, precision=FP64, **params):
+        """Time ghost push vs exchange per level and the fused coarse end (gmg_autotune) for
+        this precision; later solves with the default params use the faster choices.
+        Returns {"levels": [(push, ms_push, ms_pull), ...], "fused_coarse": f,
+        "vcycle_ms": (fused, per-level)}."""
+        if isinstance(precision, str):
+            precision = PRECISION[precision]
+        p = default_params(**params)
+        self._check(self.L.gmg_autotune(self.h, precision, _ptr(rhs), C.byref(p)))
+        out = []
+        f = C.c_int()
+        vf, vl = C.c_double(), C.c_double()
+        for m in range(self.nlevels):
+            ps = C.c_int()
+            a, b = C.c_double(), C.c_double()
+            self._check(self.L.gmg_tuned(self.h, precision, m, C.byref(ps), C.byref(a), C.byref(b), C.byref(f),
+                                         C.byref(vf), C.byref(vl)))
+            out.append((ps.value, a.value, b.value))
+        return {"levels": out, "fused_coarse": f.value, "vcycle_ms": (vf.value, vl.value)}
 
     def vcycle(self, r, dt=DT_F64, **params):
         e = self.field(0, dt)

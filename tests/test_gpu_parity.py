@@ -377,3 +377,51 @@ def test_fused_sweep_is_bitwise_two_half_sweeps(case):
     p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=0, project_mean=1)
     assert torch.equal(a1, C.unpack(p0))
     assert i1.kernel_launches == i0.kernel_launches
+
+
+@pytest.mark.parametrize("name", ["uneven", "periodic", "helmholtz", "poisson32"])
+def test_ghost_push_is_bitwise_ghost_exchange(name):
+    """The smoother and interpolation writing their new values into the ghosts that copy
+    them gives bit for bit the V-cycle and the solve of the ghost exchange before every
+    colour, in FP64, FP32 and BF16 (walls, periodic images and uneven boxes)."""
+    cfg = cases.make(name)
+    C = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], prob_hi=cfg.get("prob_hi", (1.0, 1.0, 1.0)),
+                    boxes=cfg["boxes"], stream=torch.cuda.current_stream().cuda_stream)
+    C.allocate(gmg.MIXED_FP32)
+    C.set_scalars(cfg["a"], cfg["b"])
+    if cfg["alpha"] is not None:
+        C.set_alpha(torch.from_numpy(cfg["alpha"]))
+    C.set_beta(torch.from_numpy(cfg["beta"]) if cfg["beta"] is not None else None)
+    r = cfg["rhs"] - (cfg["rhs"].mean() if name in ("periodic", "poisson32") else 0.0)
+    for dt in DTS:
+        rb = C.pack(torch.from_numpy(r), 0, dt)
+        e1 = C.unpack(C.vcycle(rb, dt, ghost_push=1), 0, dt)
+        e0 = C.unpack(C.vcycle(rb, dt, ghost_push=0), 0, dt)
+        assert torch.equal(e1, e0), dt
+    rhs = C.pack(torch.from_numpy(r))
+    p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=3, ghost_push=1, project_mean=1)
+    a1 = C.unpack(p1).clone()
+    p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=3, ghost_push=0, project_mean=1)
+    assert torch.equal(a1, C.unpack(p0))
+    assert i1.kernel_launches < i0.kernel_launches
+
+
+def test_autotune_keeps_results():
+    """gmg_autotune measures push vs exchange per level and the fused coarse end, records a
+    choice for every eligible level, and solves with the tuned defaults give the iterates of
+    the untuned per-level path (the fused bottom adds its dot products in another order)."""
+    from paper_2009_12009_gb300 import inputs as I
+
+    cfg = I.abec(64, 16, 4545, name="abec64_16")
+    C = _ctx_of(cfg, gmg.MIXED_FP32)
+    rhs = C.pack(torch.from_numpy(cfg["rhs"]))
+    for prec in (gmg.FP64, gmg.MIXED_FP32):
+        t = C.autotune(rhs, prec)
+        assert t["fused_coarse"] in (0, 1) and min(t["vcycle_ms"]) > 0
+        smoothed = [lv for lv in t["levels"] if lv[0] >= 0]
+        assert smoothed and all(a > 0 and b > 0 for _, a, b in smoothed)
+        p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=4, precision=prec)
+        a1 = C.unpack(p1).cpu().numpy()
+        p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=4, precision=prec, ghost_push=0, fused_coarse=0)
+        a0 = C.unpack(p0).cpu().numpy()
+        assert np.abs(a1 - a0).max() <= 1e-12 * np.abs(a0).max()
