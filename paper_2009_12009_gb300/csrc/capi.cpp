@@ -741,8 +741,10 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
 void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const gmg_params& p, cudaStream_t s) {
   const int ns = c->ns();
   vcycle(c, dt, 0, p, s);
-  launch_add_correction(dt, c->dev[0], phi, c->buf[0].e[dt], s);
-  launch_fill(DT_F64, c->dev[0], phi, -1, 0, s);
+  // phi's ghosts stay current by push (they were filled, or zero, before the first update)
+  const bool push = p.ghost_push != 0 && c->dev[0].push_ok;
+  launch_add_correction(dt, c->dev[0], phi, c->buf[0].e[dt], s, push);
+  if (!push) launch_fill(DT_F64, c->dev[0], phi, -1, 0, s);
   cudaMemsetAsync(c->normbits, 0, 8 * (size_t)ns, s);
   cudaEvent_t* ev = c->profiling ? ev_pair(c->ev_resid, c->n_ev_resid++) : nullptr;
   if (ev) record_timing_event(c, ev[0], s);

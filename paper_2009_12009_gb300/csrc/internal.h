@@ -44,7 +44,8 @@ struct PushFace {
   int box;
   int sign;
   int dx, dy, dz;
-  int pad;
+  int direct;     // 1: same row and plane strides, the ghost of element q is q + delta
+  int64_t delta;
 };
 
 // One rectangle of face ghost cells of box dst_box and where its values come from.

@@ -127,8 +127,13 @@ __device__ __forceinline__ void push_ghosts(const DevBox& B, int b, const DevBox
     if (c != ((fc & 1) ? nd - 1 : 0)) continue;
     const PushFace P = faces[6 * b + fc];
     if (P.box < 0) continue;
-    const DevBox Bd = boxes[P.box];
-    st(f + elem_index(Bd, i + P.dx, j + P.dy, k + P.dz), P.sign < 0 ? -v : v);
+    const A w = P.sign < 0 ? -v : v;
+    if (P.direct) {
+      st(f + elem_index(B, i, j, k) + P.delta, w);
+    } else {
+      const DevBox Bd = boxes[P.box];
+      st(f + elem_index(Bd, i + P.dx, j + P.dy, k + P.dz), w);
+    }
   }
 }
 
@@ -308,7 +313,8 @@ __global__ void __launch_bounds__(BLOCK)
 template <class T>
 __global__ void __launch_bounds__(BLOCK) k_add_correction(const DevBox* __restrict__ boxes,
                                                           const Chunk* __restrict__ chunks, double* phi,
-                                                          const T* __restrict__ e, const int* __restrict__ active) {
+                                                          const T* __restrict__ e, const int* __restrict__ active,
+                                                          const PushFace* __restrict__ push) {
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
   if (active && !active[B.solve]) return;
@@ -316,7 +322,9 @@ __global__ void __launch_bounds__(BLOCK) k_add_correction(const DevBox* __restri
   if (t >= B.nx * B.ny * B.nz) return;
   const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
   const int64_t q = elem_index(B, i, j, k);
-  phi[q] += (double)ld(e + q);
+  const double v = phi[q] + (double)ld(e + q);
+  phi[q] = v;
+  if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, v);
 }
 
 template <class T>
@@ -628,11 +636,12 @@ void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void
                        f.boxes, c.boxes, f.parent, f.coarse_chunks, (const T*)coarse, (T*)fine, f.active, pf)));
 }
 
-void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s) {
+void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s, bool push) {
   if (!L.n_cell_chunks) return;
   ++g_launches;
+  const PushFace* pf = push ? L.push_faces : nullptr;
   GMG_DISPATCH(dt, (k_add_correction<T><<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, phi,
-                                                                                     (const T*)e, L.active)));
+                                                                                     (const T*)e, L.active, pf)));
 }
 
 void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const double* dense, void* boxed,

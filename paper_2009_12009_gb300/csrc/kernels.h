@@ -89,7 +89,9 @@ void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* f
 void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine,
                         cudaStream_t s, bool push = false);
 // phi (double) += e (type dt) on valid cells
-void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s);
+// (push: also write the new phi into the ghost cells that copy it, L.push_ok levels only)
+void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s,
+                           bool push = false);
 // dense (nz,ny,nx) double over the level's (single-solve) domain <-> boxed type dt
 void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const double* dense, void* boxed,
                  cudaStream_t s);
