@@ -152,9 +152,9 @@ def cpu_baseline(cfg, iters=2):
 
 
 def summarize_tuning(t):
-    """ghost push chosen per MG level (1 push, 0 exchange, -1 not eligible) and the fused
-    coarse end (1 on), as gmg_autotune measured them"""
-    return {"ghost_push_per_level": [lv[0] for lv in t["levels"]], "fused_coarse": t["fused_coarse"],
+    """sweep variant chosen per MG level (bit 0: ghost push, bit 1: one thread per 4 cells;
+    -1: no smoothing there) and the fused coarse end (1 on), as gmg_autotune measured them"""
+    return {"sweep_variant_per_level": [lv[0] for lv in t["levels"]], "fused_coarse": t["fused_coarse"],
             "vcycle_ms_fused_vs_levels": [round(x, 4) for x in t["vcycle_ms"]]}
 
 

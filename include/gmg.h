@@ -110,6 +110,11 @@ typedef struct {
                            0: ghost exchange before every colour.  2 (default): per level,
                            the gmg_autotune choice; before tuning, push on levels of fewer
                            than 2^22 cells (where the exchange is launch-latency bound) */
+  int vector_smooth;    /* 1: float and bfloat16 colour sweeps on levels whose box widths
+                           are multiples of 4 run one thread per 4 consecutive cells with
+                           128-bit (float) / 64-bit (bfloat16) loads; bitwise the same results
+                           as one thread per cell pair (0).  2 (default): per level, the
+                           gmg_autotune choice; before tuning, bfloat16 only */
 } gmg_params;
 
 typedef struct {
@@ -313,17 +318,19 @@ gmg_status gmg_vcycle(gmg_ctx* ctx, int dt, void* e, const void* r, const gmg_pa
 
 /* Launch-shape autotuner (no counterpart in the paper).  For the V-cycle of the given
    precision it times, on this context's own levels and buffers (CUDA events, a few
-   repetitions each), (1) per MG level: a red-black sweep with the ghost push against the
-   ghost exchange before each colour, and (2) whole V-cycles with the fused coarse end
-   against per-level launches, and keeps the faster of each.  Solves and V-cycles whose
-   params have ghost_push = 2 / fused_coarse = 2 (the defaults) use the choices; the
-   results do not depend on them.  rhs: FP64 level-0 boxed right-hand side (device), used
+   repetitions each), (1) per MG level: a red-black sweep four ways -- ghost exchange before
+   each colour or ghost push, one thread per cell pair or per 4 cells (float/bfloat16) --
+   and (2) whole V-cycles with the fused coarse end against per-level launches, and keeps
+   the fastest of each.  Solves and V-cycles whose params have ghost_push = 2,
+   vector_smooth = 2, fused_coarse = 2 (the defaults) use the choices; the results do not
+   depend on them.  rhs: FP64 level-0 boxed right-hand side (device), used
    to fill the correction equation.  Clobbers the V-cycle work buffers only; drops cached
    graphs. */
 gmg_status gmg_autotune(gmg_ctx* ctx, int precision, const void* rhs, const gmg_params* p);
 
-/* The tuned choice for MG level m and precision: *push = 1 push, 0 exchange, -1 not tuned
-   (or not eligible); the measured ms per sweep both ways; *fused_coarse = 1/0/-1 and the
+/* The tuned choice for MG level m and precision: *push = bit 0 ghost push, bit 1 4-cell
+   threads, -1 not tuned (no smoothing there); the best measured ms per sweep with push and
+   with the exchange (0 if push is not possible there); *fused_coarse = 1/0/-1 and the
    measured ms per V-cycle with (fused) and without (levels) the fused coarse end.  Any
    output pointer may be NULL. */
 gmg_status gmg_tuned(const gmg_ctx* ctx, int precision, int m, int* push, double* ms_push, double* ms_pull,

@@ -106,7 +106,7 @@ struct gmg_ctx {
     int64_t launches;
     int n_ev_smooth, n_ev_resid;  // profiling event pairs recorded per replay
   };
-  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int>, GraphEntry> graphs;
+  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int>, GraphEntry> graphs;
 
   // profiling events (pairs around finest-level smoother / outer residual launches)
   bool profiling = false;
@@ -237,6 +237,8 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.n_ghost_chunks = (int)M.ghost_chunks.size();
     D.pair_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.pair_chunks.size());
     D.n_pair_chunks = (int)M.pair_chunks.size();
+    D.quad_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.quad_chunks.size());
+    D.n_quad_chunks = (int)M.quad_chunks.size();
     D.pair_all_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.pair_all_chunks.size());
     D.n_pair_all_chunks = (int)M.pair_all_chunks.size();
     D.cell_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.cell_chunks.size());
@@ -254,6 +256,8 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.n_vc_ghost_chunks = (int)M.vc_ghost_chunks.size();
     D.vc_pair_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.vc_pair_chunks.size());
     D.n_vc_pair_chunks = (int)M.vc_pair_chunks.size();
+    D.vc_quad_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.vc_quad_chunks.size());
+    D.n_vc_quad_chunks = (int)M.vc_quad_chunks.size();
     D.vc_coarse_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.vc_coarse_chunks.size());
     D.n_vc_coarse_chunks = (int)M.vc_coarse_chunks.size();
     D.vc_bot_descs = (const BotDesc*)cv.take(sizeof(BotDesc) * M.vc_bot_descs.size());
@@ -429,6 +433,7 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.ghosts, M.ghosts))) return st;
     if ((st = upload(c, D.ghost_chunks, M.ghost_chunks))) return st;
     if ((st = upload(c, D.pair_chunks, M.pair_chunks))) return st;
+    if ((st = upload(c, D.quad_chunks, M.quad_chunks))) return st;
     if ((st = upload(c, D.pair_all_chunks, M.pair_all_chunks))) return st;
     if ((st = upload(c, D.cell_chunks, M.cell_chunks))) return st;
     if ((st = upload(c, D.coarse_chunks, M.coarse_chunks))) return st;
@@ -440,6 +445,7 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.inv_count, M.inv_count))) return st;
     if ((st = upload(c, D.vc_ghost_chunks, M.vc_ghost_chunks))) return st;
     if ((st = upload(c, D.vc_pair_chunks, M.vc_pair_chunks))) return st;
+    if ((st = upload(c, D.vc_quad_chunks, M.vc_quad_chunks))) return st;
     if ((st = upload(c, D.vc_coarse_chunks, M.vc_coarse_chunks))) return st;
     if ((st = upload(c, D.vc_bot_descs, M.vc_bot_descs))) return st;
     if ((st = upload(c, D.sweep_regions, M.sweep_regions))) return st;
@@ -603,16 +609,40 @@ void record_timing_event(gmg_ctx* c, cudaEvent_t e, cudaStream_t s) {
   else cudaEventRecord(e, s);
 }
 
+// ghost push on level m: 1 always (where the level allows it), 2 the tuned choice (before
+// tuning: levels below 2^22 cells, whose ghost exchanges are launch-latency bound)
+bool push_on(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
+  if (p.ghost_push == 0) return false;
+  if (p.ghost_push == 1) return true;
+  const auto& ch = c->push_choice[dt];
+  if (m < (int)ch.size() && ch[m] >= 0) return (ch[m] & 1) != 0;
+  return c->L[m].ncells < (1 << 22);
+}
+
+// 4-cell sweep threads on level m: 1 always (where possible), 2 the tuned choice (before
+// tuning: bfloat16 only)
+bool vec_on(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
+  if (p.vector_smooth != 2) return p.vector_smooth == 1;
+  const auto& ch = c->push_choice[dt];
+  if (m < (int)ch.size() && ch[m] >= 0) return (ch[m] & 2) != 0;
+  return dt == DT_BF16;
+}
+
+bool tail_on(const gmg_ctx* c, const gmg_params& p, int dt) {
+  if (p.fused_coarse == 2) return c->tail_choice[dt] != 0;  // untuned: on
+  return p.fused_coarse == 1;
+}
+
 // push: the smoother writes its new values into the ghost cells that copy them, so no
 // ghost exchange precedes a colour (the ghosts are kept current since e was cleared)
 void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cudaStream_t s, bool fill = true,
-                   bool push = false) {
+                   bool push = false, bool vec = true) {
   const LevelBufs& B = c->buf[m];
   if (fill && !push) launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
   const bool prof = c->profiling && m == 0;
   cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
   if (prof) record_timing_event(c, ev[0], s);
-  launch_smooth(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s, push);
+  launch_smooth(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s, push, vec);
   if (prof) record_timing_event(c, ev[1], s);
 }
 
@@ -640,8 +670,8 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
     return;
   }
   for (int it = 0; it < nsweep; ++it) {
-    smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0), push);
-    smooth_colour(c, D, dt, m, 1, s, true, push);
+    smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
+    smooth_colour(c, D, dt, m, 1, s, true, push, vec_on(c, p, dt, m));
   }
 }
 
@@ -653,6 +683,10 @@ LevelDev vc_view(const gmg_ctx* c, int m) {
   D.n_ghost_chunks = D.n_vc_ghost_chunks;
   D.pair_chunks = D.vc_pair_chunks;
   D.n_pair_chunks = D.n_vc_pair_chunks;
+  if (D.quad_chunks) {  // (null when the level's widths are not all multiples of 4)
+    D.quad_chunks = D.vc_quad_chunks;
+    D.n_quad_chunks = D.n_vc_quad_chunks;
+  }
   D.coarse_chunks = D.vc_coarse_chunks;
   D.n_coarse_chunks = D.n_vc_coarse_chunks;
   D.bot_descs = D.vc_bot_descs;
@@ -697,21 +731,6 @@ void launch_tails(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s
 // recurse, interpolate and smooth again.  With fused_coarse, each problem's levels from
 // its first level of at most TAIL_MAX_CELLS cells down to its bottom run in one thread
 // block (launched when the descent reaches that level) and the grid launches skip them.
-// ghost push on level m: 1 always (where the level allows it), 2 the tuned choice (before
-// tuning: levels below 2^22 cells, whose ghost exchanges are launch-latency bound)
-bool push_on(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
-  if (p.ghost_push == 0) return false;
-  if (p.ghost_push == 1) return true;
-  const auto& ch = c->push_choice[dt];
-  if (m < (int)ch.size() && ch[m] >= 0) return ch[m] == 1;
-  return c->L[m].ncells < (1 << 22);
-}
-
-bool tail_on(const gmg_ctx* c, const gmg_params& p, int dt) {
-  if (p.fused_coarse == 2) return c->tail_choice[dt] != 0;  // untuned: on
-  return p.fused_coarse == 1;
-}
-
 void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
   const bool fused = tail_on(c, p, dt) && c->tail_ok;
   const LevelDev D = fused ? vc_view(c, m) : c->dev[m];
@@ -780,6 +799,7 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.fused_coarse < 0 || p.fused_coarse > 2) SETERR(c, GMG_ERR_BAD_INPUT, "fused_coarse must be 0, 1 or 2");
   if (p.fused_sweep != 0 && p.fused_sweep != 1) SETERR(c, GMG_ERR_BAD_INPUT, "fused_sweep must be 0 or 1");
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
+  if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
   return GMG_OK;
 }
@@ -865,7 +885,8 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   int sm_n = 0, rs_n = 0;
   if (p.use_graph && nlive) {
     auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
-                               p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep, p.ghost_push);
+                               p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep, p.ghost_push,
+                               p.vector_smooth);
     auto itg = c->graphs.find(key);
     if (itg != c->graphs.end()) {
       gexec = itg->second.exec;
@@ -1424,6 +1445,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->fused_coarse = 2;
   p->fused_sweep = 0;
   p->ghost_push = 2;
+  p->vector_smooth = 2;
   return GMG_OK;
 }
 
@@ -1942,27 +1964,39 @@ gmg_status gmg_autotune(gmg_ctx* c, int precision, const void* rhs, const gmg_pa
   q.ghost_push = 0;
   q.fused_sweep = 0;
   vcycle(c, dt, 0, q, s);
-  // ghost push vs exchange per level: two colour passes each way on the level's own buffers
+  // per level, a red-black sweep (two colour passes) four ways on the level's own buffers:
+  // ghost exchange or push, one thread per cell pair or per 4 cells (float / bfloat16)
   c->push_choice[dt].assign(n, -1);
   c->tune_ms_push[dt].assign(n, 0.0);
   c->tune_ms_pull[dt].assign(n, 0.0);
   for (int m = 0; m < n; ++m) {
     const LevelDev& D = c->dev[m];
-    if (!D.push_ok || D.n_pair_chunks == 0) continue;
+    if (D.n_pair_chunks == 0) continue;
     const LevelBufs& B = c->buf[m];
     const Coefs k = coefs_of(c, m, dt);
-    const double pull = time_reps(c, reps, [&] {
-      for (int colour = 0; colour < 2; ++colour) {
-        launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
-        launch_smooth(dt, D, B.e[dt], B.r[dt], k, colour, s, false);
+    const bool can_vec = dt != DT_F64 && D.quad_chunks && D.n_quad_chunks > 0;
+    double best = 1e30;
+    int best_v = 0;
+    double best_push = 1e30, best_pull = 1e30;
+    for (int v = 0; v < 4; ++v) {
+      const bool push = v & 1, vec = (v & 2) != 0;
+      if ((push && !D.push_ok) || (vec && !can_vec)) continue;
+      const double ms = time_reps(c, reps, [&] {
+        for (int colour = 0; colour < 2; ++colour) {
+          if (!push) launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
+          launch_smooth(dt, D, B.e[dt], B.r[dt], k, colour, s, push, vec);
+        }
+      });
+      if (push) best_push = std::min(best_push, ms);
+      else best_pull = std::min(best_pull, ms);
+      if (ms < best) {
+        best = ms;
+        best_v = v;
       }
-    });
-    const double push = time_reps(c, reps, [&] {
-      for (int colour = 0; colour < 2; ++colour) launch_smooth(dt, D, B.e[dt], B.r[dt], k, colour, s, true);
-    });
-    c->tune_ms_pull[dt][m] = pull;
-    c->tune_ms_push[dt][m] = push;
-    c->push_choice[dt][m] = push < pull ? 1 : 0;
+    }
+    c->tune_ms_pull[dt][m] = best_pull;
+    c->tune_ms_push[dt][m] = best_push < 1e30 ? best_push : 0.0;
+    c->push_choice[dt][m] = (signed char)best_v;
   }
   // fused coarse end vs per-level launches, whole V-cycles with the choices above
   q.ghost_push = 2;
@@ -1982,7 +2016,7 @@ gmg_status gmg_tuned(const gmg_ctx* c, int precision, int m, int* push, double* 
   const int dt = dt_of_precision(precision);
   if (dt < 0 || dt >= NDT || m < 0 || m >= (int)c->L.size()) return GMG_ERR_BAD_INPUT;
   const auto& ch = c->push_choice[dt];
-  if (push) *push = m < (int)ch.size() ? ch[m] : -1;
+  if (push) *push = m < (int)ch.size() ? ch[m] : -1;  // bit 0: push, bit 1: 4-cell threads
   if (ms_push) *ms_push = m < (int)c->tune_ms_push[dt].size() ? c->tune_ms_push[dt][m] : 0.0;
   if (ms_pull) *ms_pull = m < (int)c->tune_ms_pull[dt].size() ? c->tune_ms_pull[dt][m] : 0.0;
   if (fused_coarse) *fused_coarse = c->tail_choice[dt];

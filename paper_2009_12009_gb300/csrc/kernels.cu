@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -173,6 +174,83 @@ __global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ box
   s = s * (A)ldg(invD + q);
   st(phi + q, s);
   if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, s);
+}
+
+// Four consecutive cells (x), 16-byte aligned: 128-bit loads for float, 64-bit for bfloat16.
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ldg4(const float* p, float v[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const bf16* p, float v[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ldg4(const bf16* p, float v[4]) { ld4(p, v); }
+
+// One red-black colour with one thread per 4 consecutive cells of a row (boxes whose width
+// is a multiple of 4; float and bfloat16 fields): the thread reads the 4-cell segments of
+// phi (with its four neighbour segments), rhs and the coefficients with vector loads and
+// updates the two cells of the colour -- the arithmetic and order of k_smooth, so the
+// results are bitwise the same.
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_smooth4(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                   T* phi, const T* __restrict__ rhs, const float* __restrict__ wx,
+                                                   const float* __restrict__ wy, const float* __restrict__ wz,
+                                                   const float* __restrict__ invD, int colour,
+                                                   const int* __restrict__ active, const PushFace* __restrict__ push) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  if (active && !active[B.solve]) return;
+  const int nq = B.nx >> 2;
+  const int t = ch.start + threadIdx.x;
+  if (t >= nq * B.ny * B.nz) return;
+  const int g = t % nq, r = t / nq;
+  const int j = r % B.ny, k = r / B.ny, i0 = 4 * g;
+  const int64_t q0 = elem_index(B, i0, j, k);
+  const int64_t sx = B.sx, sy = B.sy;
+  float p[4], pym[4], pyp[4], pzm[4], pzp[4], rh[4], wxl[4], wyl[4], wyh[4], wzl[4], wzh[4], id[4];
+  ld4(phi + q0, p);
+  ld4(phi + q0 - sx, pym);
+  ld4(phi + q0 + sx, pyp);
+  ld4(phi + q0 - sy, pzm);
+  ld4(phi + q0 + sy, pzp);
+  const float pl = ld(phi + q0 - 1), pr = ld(phi + q0 + 4);
+  ldg4(rhs + q0, rh);
+  ldg4(wx + q0, wxl);
+  const float wx4 = __ldg(wx + q0 + 4);
+  ldg4(wy + q0, wyl);
+  ldg4(wy + q0 + sx, wyh);
+  ldg4(wz + q0, wzl);
+  ldg4(wz + q0 + sy, wzh);
+  ldg4(invD + q0, id);
+  const int c0 = (B.lo[0] + B.lo[1] + B.lo[2] + i0 + j + k + colour) & 1;
+  // cells m and m + 2 of the segment, m = c0 (constant indices keep the arrays in registers)
+  auto update = [&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    float s = rh[m];
+    s = fmaf(wxl[m], m == 0 ? pl : p[m == 0 ? 0 : m - 1], s);
+    s = fmaf(m == 3 ? wx4 : wxl[m == 3 ? 3 : m + 1], m == 3 ? pr : p[m == 3 ? 3 : m + 1], s);
+    s = fmaf(wyl[m], pym[m], s);
+    s = fmaf(wyh[m], pyp[m], s);
+    s = fmaf(wzl[m], pzm[m], s);
+    s = fmaf(wzh[m], pzp[m], s);
+    s = s * id[m];
+    st(phi + q0 + m, s);
+    if (push) push_ghosts(B, ch.item, boxes, push, phi, i0 + m, j, k, s);
+  };
+  if (c0 == 0) {
+    update(std::integral_constant<int, 0>());
+    update(std::integral_constant<int, 2>());
+  } else {
+    update(std::integral_constant<int, 1>());
+    update(std::integral_constant<int, 3>());
+  }
 }
 
 // ------------------------------------------------------------------- residual
@@ -579,10 +657,22 @@ void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, 
 }
 
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour, cudaStream_t s,
-                   bool push) {
+                   bool push, bool vec) {
   if (!L.n_pair_chunks) return;
   ++g_launches;
   const PushFace* pf = push ? L.push_faces : nullptr;
+  if (vec && dt != DT_F64 && L.quad_chunks && L.n_quad_chunks > 0) {
+    const float *wx = (const float*)c.wx, *wy = (const float*)c.wy, *wz = (const float*)c.wz;
+    const float* invD = (const float*)c.invD;
+    if (dt == DT_F32)
+      k_smooth4<float><<<grid_of(L.n_quad_chunks), BLOCK, 0, s>>>(L.boxes, L.quad_chunks, (float*)phi,
+                                                                  (const float*)rhs, wx, wy, wz, invD, colour,
+                                                                  L.active, pf);
+    else
+      k_smooth4<bf16><<<grid_of(L.n_quad_chunks), BLOCK, 0, s>>>(L.boxes, L.quad_chunks, (bf16*)phi, (const bf16*)rhs,
+                                                                 wx, wy, wz, invD, colour, L.active, pf);
+    return;
+  }
   GMG_DISPATCH(dt, (k_smooth<T><<<grid_of(L.n_pair_chunks), BLOCK, 0, s>>>(
                        L.boxes, L.pair_chunks, (T*)phi, (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
                        (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,

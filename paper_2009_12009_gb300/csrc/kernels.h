@@ -23,6 +23,8 @@ struct LevelDev {
   int n_ghost_chunks = 0;
   const Chunk* pair_chunks = nullptr;  // boxes that smooth on this level, 2 cells per item
   int n_pair_chunks = 0;
+  const Chunk* quad_chunks = nullptr;  // the same, 4 cells per item (null: a width is not a multiple of 4)
+  int n_quad_chunks = 0;
   const Chunk* pair_all_chunks = nullptr;  // every box, 2 cells per item
   int n_pair_all_chunks = 0;
   const Chunk* cell_chunks = nullptr;
@@ -45,6 +47,8 @@ struct LevelDev {
   int n_vc_ghost_chunks = 0;
   const Chunk* vc_pair_chunks = nullptr;
   int n_vc_pair_chunks = 0;
+  const Chunk* vc_quad_chunks = nullptr;
+  int n_vc_quad_chunks = 0;
   const Chunk* vc_coarse_chunks = nullptr;
   int n_vc_coarse_chunks = 0;
   const BotDesc* vc_bot_descs = nullptr;
@@ -76,7 +80,7 @@ void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, 
 // one red-black colour (no ghost fill); push: also write each new value into the ghost
 // cells that copy it (L.push_ok levels only)
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour,
-                   cudaStream_t s, bool push = false);
+                   cudaStream_t s, bool push = false, bool vec = false);
 // r = (rhs - shift[solve]) - A phi on valid cells (ghosts of phi must be filled); rdt =
 // type of r; maxbits (may be null): per-solve atomic max of |r| as IEEE bits; shift (may be
 // null): per-solve device scalars

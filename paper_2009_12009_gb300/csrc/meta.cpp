@@ -278,8 +278,10 @@ std::string finalize_level(LevelMeta& L) {
       for (int d = 0; d < 3; ++d)
         if (L.geoms[q].periodic(d) && L.geoms[q].domain.n(d) % 2 != 0) L.push_ok = false;
   L.pair_chunks.clear();
+  L.quad_chunks.clear();
   L.pair_all_chunks.clear();
   L.cell_chunks.clear();
+  L.quad_ok = true;
   for (int b = 0; b < nb; ++b) {
     const DevBox& D = L.dbox[b];
     int64_t ncell = (int64_t)D.nx * D.ny * D.nz;
@@ -288,7 +290,11 @@ std::string finalize_level(LevelMeta& L) {
     for (int64_t s = 0; s < npair; s += BLOCK) L.pair_all_chunks.push_back({b, (int)s});
     if (L.solve_bottom[L.box_solve[b]]) continue;
     for (int64_t s = 0; s < npair; s += BLOCK) L.pair_chunks.push_back({b, (int)s});
+    if (D.nx % 4 != 0) L.quad_ok = false;
+    const int64_t nquad = (int64_t)(D.nx / 4) * D.ny * D.nz;
+    for (int64_t s = 0; s < nquad; s += BLOCK) L.quad_chunks.push_back({b, (int)s});
   }
+  if (!L.quad_ok) L.quad_chunks.clear();
   // boxes are stored solve by solve, so each solve's cell chunks are contiguous
   const int ns = (int)L.geoms.size();
   L.solve_chunk_range.assign(ns + 1, 0);
@@ -496,6 +502,9 @@ std::string build_tail(std::vector<LevelMeta>& L, TailHost& T) {
     M.vc_pair_chunks.clear();
     for (const Chunk& ch : M.pair_chunks)
       if (!in_tail(M.box_solve[ch.item])) M.vc_pair_chunks.push_back(ch);
+    M.vc_quad_chunks.clear();
+    for (const Chunk& ch : M.quad_chunks)
+      if (!in_tail(M.box_solve[ch.item])) M.vc_quad_chunks.push_back(ch);
     M.vc_coarse_chunks.clear();
     for (const Chunk& ch : M.coarse_chunks)
       if (!in_tail(M.box_solve[ch.item])) M.vc_coarse_chunks.push_back(ch);

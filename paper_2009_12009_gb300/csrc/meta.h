@@ -59,6 +59,8 @@ struct LevelMeta {
                          // length even (a ghost has its source's colour)
   std::vector<Chunk> ghost_chunks;
   std::vector<Chunk> pair_chunks;    // boxes of solves that smooth on this level, 2 cells per item
+  std::vector<Chunk> quad_chunks;    // the same boxes, 4 cells per item (all widths multiples of 4)
+  bool quad_ok = false;              // every smoothing box has a width that is a multiple of 4
   std::vector<Chunk> pair_all_chunks;  // every box, 2 cells per item
   std::vector<Chunk> cell_chunks;    // every box, 1 cell per item
   std::vector<Chunk> coarse_chunks;  // boxes with a parent, 1 coarse cell per item
@@ -70,7 +72,7 @@ struct LevelMeta {
 
   // work lists of the V-cycle's grid launches when the coarse ends of the problems run as
   // one thread block each: entries of problems whose tail covers this level are left out
-  std::vector<Chunk> vc_ghost_chunks, vc_pair_chunks, vc_coarse_chunks;
+  std::vector<Chunk> vc_ghost_chunks, vc_pair_chunks, vc_coarse_chunks, vc_quad_chunks;
   std::vector<BotDesc> vc_bot_descs;
 
   // fused red-black sweeps: regions of the boxes of solves that smooth on this level

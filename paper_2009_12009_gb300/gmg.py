@@ -38,7 +38,8 @@ class Params(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_iter", C.c_int), ("bottom_max_iter", C.c_int),
                 ("bottom_tol", C.c_double), ("precision", C.c_int), ("project_mean", C.c_int),
                 ("use_graph", C.c_int), ("profile", C.c_int), ("fused_coarse", C.c_int),
-                ("fused_sweep", C.c_int), ("ghost_push", C.c_int)]
+                ("fused_sweep", C.c_int), ("ghost_push", C.c_int),
+                ("vector_smooth", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -367,10 +368,10 @@ class Context:
         return x, it.value
 
     def autotune(self, rhs, precision=FP64, **params):
-        """Time ghost push vs exchange per level and the fused coarse end (gmg_autotune) for
-        this precision; later solves with the default params use the faster choices.
-        Returns {"levels": [(push, ms_push, ms_pull), ...], "fused_coarse": f,
-        "vcycle_ms": (fused, per-level)}."""
+        """Time the sweep variants per level (ghost push / exchange, 2- / 4-cell threads) and
+        the fused coarse end (gmg_autotune) for this precision; later solves with the default
+        params use the fastest.  Returns {"levels": [(variant bits, best ms with push, best ms
+        with exchange), ...], "fused_coarse": f, "vcycle_ms": (fused, per-level)}."""
         if isinstance(precision, str):
             precision = PRECISION[precision]
         p = default_params(**params)

@@ -419,9 +419,40 @@ def test_autotune_keeps_results():
         t = C.autotune(rhs, prec)
         assert t["fused_coarse"] in (0, 1) and min(t["vcycle_ms"]) > 0
         smoothed = [lv for lv in t["levels"] if lv[0] >= 0]
-        assert smoothed and all(a > 0 and b > 0 for _, a, b in smoothed)
+        assert smoothed and all(0 <= v <= 3 and a >= 0 and b > 0 for v, a, b in smoothed)
         p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=4, precision=prec)
         a1 = C.unpack(p1).cpu().numpy()
         p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=4, precision=prec, ghost_push=0, fused_coarse=0)
         a0 = C.unpack(p0).cpu().numpy()
         assert np.abs(a1 - a0).max() <= 1e-12 * np.abs(a0).max()
+
+
+@pytest.mark.parametrize("case", ["abec64_boxes16", "helmholtz", "periodic"])
+def test_vector_smooth_is_bitwise_pair_smooth(case):
+    """One thread per 4 cells with vector loads gives bit for bit the V-cycle and the solve
+    of one thread per cell pair (float and bfloat16; FP64 always uses pairs)."""
+    from paper_2009_12009_gb300 import inputs as I
+
+    cfg = I.abec(64, 16, 4646, name=case) if case == "abec64_boxes16" else cases.make(case)
+    C = _ctx_of(cfg) if case == "abec64_boxes16" else None
+    if C is None:
+        C = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], prob_hi=cfg.get("prob_hi", (1.0, 1.0, 1.0)),
+                        boxes=cfg["boxes"], stream=torch.cuda.current_stream().cuda_stream)
+        C.allocate(gmg.MIXED_FP32)
+        C.set_scalars(cfg["a"], cfg["b"])
+        if cfg["alpha"] is not None:
+            C.set_alpha(torch.from_numpy(cfg["alpha"]))
+        C.set_beta(torch.from_numpy(cfg["beta"]) if cfg["beta"] is not None else None)
+    r = cfg["rhs"] - (cfg["rhs"].mean() if cfg["bc_lo"][0] == gmg.PERIODIC and cfg["a"] == 0 else 0.0)
+    for dt in (gmg.DT_F32, gmg.DT_BF16):
+        rb = C.pack(torch.from_numpy(r), 0, dt)
+        for push in (0, 1):
+            e1 = C.unpack(C.vcycle(rb, dt, vector_smooth=1, ghost_push=push), 0, dt)
+            e0 = C.unpack(C.vcycle(rb, dt, vector_smooth=0, ghost_push=push), 0, dt)
+            assert torch.equal(e1, e0), (dt, push)
+    rhs = C.pack(torch.from_numpy(r))
+    for prec in (gmg.MIXED_FP32, gmg.MIXED_BF16):
+        p1, _ = C.solve(rhs, tol_rel=0.0, max_iter=3, precision=prec, vector_smooth=1, project_mean=1)
+        a1 = C.unpack(p1).clone()
+        p0, _ = C.solve(rhs, tol_rel=0.0, max_iter=3, precision=prec, vector_smooth=0, project_mean=1)
+        assert torch.equal(a1, C.unpack(p0)), prec
