@@ -199,7 +199,7 @@ __device__ __forceinline__ void ldg4(const bf16* p, float v[4]) { ld4(p, v); }
 // updates the two cells of the colour -- the arithmetic and order of k_smooth, so the
 // results are bitwise the same.
 template <class T>
-__global__ void __launch_bounds__(BLOCK) k_smooth4(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+__global__ void __launch_bounds__(BLOCK, 4) k_smooth4(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
                                                    T* phi, const T* __restrict__ rhs, const float* __restrict__ wx,
                                                    const float* __restrict__ wy, const float* __restrict__ wz,
                                                    const float* __restrict__ invD, int colour,
