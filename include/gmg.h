@@ -115,6 +115,11 @@ typedef struct {
                            128-bit (float) / 64-bit (bfloat16) loads; bitwise the same results
                            as one thread per cell pair (0).  2 (default): per level, the
                            gmg_autotune choice; before tuning, bfloat16 only */
+  int pdl;              /* 1: the V-cycle kernels are launched for programmatic dependent
+                           launch -- each may be scheduled while its predecessor finishes
+                           and waits for it on the device before touching memory; 0: plain
+                           launches; 2 (default): dependent launch outside CUDA graph
+                           capture only.  Same results. */
 } gmg_params;
 
 typedef struct {

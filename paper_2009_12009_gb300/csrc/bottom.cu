@@ -7,6 +7,8 @@
 // result is deterministic.
 #include <cuda_bf16.h>
 
+#include <utility>
+
 #include "kernels.h"
 
 namespace gmg {
@@ -106,6 +108,9 @@ __global__ void __launch_bounds__(BT) k_bottom(const BotDesc* __restrict__ descs
                                                double* work, int64_t nelem, int maxit, double tol, int* iters,
                                                const int* __restrict__ active) {
   __shared__ double sh[BT / 32 + 1];
+  // programmatic dependent launch: wait for the predecessor before any global access
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const BotDesc P = descs[blockIdx.x];
   if (active && !active[P.solve]) return;
   BotCtx c{cells + P.cell0, ghosts + P.ghost0, P.ncell, P.nghost, wx, wy, wz, D};
@@ -188,6 +193,20 @@ __global__ void __launch_bounds__(BT) k_bottom(const BotDesc* __restrict__ descs
 
 }  // namespace
 
+template <class T, class... A>
+static void launch_bottom_kernel(int nblocks, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(BT);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k_bottom<T>, std::forward<A>(args)...);
+}
+
 void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Coefs& c, const BottomArgs& a,
                    cudaStream_t s) {
   if (!L.n_bot) return;
@@ -198,16 +217,16 @@ void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Co
   const double* D = (const double*)c.D;
   switch (dt) {
     case DT_F64:
-      k_bottom<double><<<L.n_bot, BT, 0, s>>>(L.bot_descs, L.bot_cells, L.bot_ghosts, (const double*)rhs, (double*)x, wx,
-                                              wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
+      launch_bottom_kernel<double>(L.n_bot, s, L.bot_descs, L.bot_cells, L.bot_ghosts, (const double*)rhs, (double*)x,
+                                   wx, wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
       break;
     case DT_F32:
-      k_bottom<float><<<L.n_bot, BT, 0, s>>>(L.bot_descs, L.bot_cells, L.bot_ghosts, (const float*)rhs, (float*)x, wx,
-                                             wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
+      launch_bottom_kernel<float>(L.n_bot, s, L.bot_descs, L.bot_cells, L.bot_ghosts, (const float*)rhs, (float*)x,
+                                  wx, wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
       break;
     default:
-      k_bottom<bf16><<<L.n_bot, BT, 0, s>>>(L.bot_descs, L.bot_cells, L.bot_ghosts, (const bf16*)rhs, (bf16*)x, wx, wy,
-                                            wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
+      launch_bottom_kernel<bf16>(L.n_bot, s, L.bot_descs, L.bot_cells, L.bot_ghosts, (const bf16*)rhs, (bf16*)x, wx,
+                                 wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
       break;
   }
 }

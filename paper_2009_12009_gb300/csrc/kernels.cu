@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 
 #include "kernels.h"
 
@@ -36,6 +37,15 @@ __device__ __forceinline__ void st(bf16* p, double v) { *p = __float2bfloat16_rn
 
 __device__ __forceinline__ int64_t axis_stride(const DevBox& B, int d) {
   return d == 0 ? 1 : (d == 1 ? (int64_t)B.sx : B.sy);
+}
+
+// Programmatic dependent launch: a kernel launched with the programmatic-serialization
+// attribute may start while its predecessor in the stream finishes; it waits here for the
+// predecessor's completion (and memory) before touching global memory, then lets its own
+// successor launch early.  Without the attribute both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // |v| as ordered bits: for non-negative doubles the IEEE bit pattern is monotone, and a
@@ -80,6 +90,7 @@ template <class T>
 __global__ void __launch_bounds__(BLOCK) k_fill(const DevBox* __restrict__ boxes, const GhostRect* __restrict__ rects,
                                                 const Chunk* __restrict__ chunks, T* f, int colour, int copy_mode,
                                                 const int* __restrict__ active) {
+  pdl_enter();
   const Chunk ch = chunks[blockIdx.x];
   const GhostRect g = rects[ch.item];
   if (copy_mode && g.kind == 1) return;
@@ -152,6 +163,7 @@ __global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ box
                                                   const typename CoefOf<T>::type* __restrict__ invD, int colour,
                                                   const int* __restrict__ active,
                                                   const PushFace* __restrict__ push) {
+  pdl_enter();
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
@@ -204,6 +216,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_smooth4(const DevBox* __restrict__
                                                    const float* __restrict__ wy, const float* __restrict__ wz,
                                                    const float* __restrict__ invD, int colour,
                                                    const int* __restrict__ active, const PushFace* __restrict__ push) {
+  pdl_enter();
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
   if (active && !active[B.solve]) return;
@@ -279,6 +292,7 @@ __global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ b
                                                     const typename CoefOf<T>::type* __restrict__ wz,
                                                     const typename CoefOf<T>::type* __restrict__ D, R* r,
                                                     unsigned long long* maxbits, const double* shift_p) {
+  pdl_enter();
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
@@ -308,6 +322,7 @@ __global__ void __launch_bounds__(BLOCK)
                      const T* __restrict__ rhs, const typename CoefOf<T>::type* __restrict__ wx,
                      const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
                      const typename CoefOf<T>::type* __restrict__ D, R* rc, const int* __restrict__ active) {
+  pdl_enter();
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox F = fboxes[ch.item];
@@ -360,6 +375,7 @@ __global__ void __launch_bounds__(BLOCK)
     k_prolong_add(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes, const int* __restrict__ parent,
                   const Chunk* __restrict__ chunks, const T* __restrict__ coarse, T* fine,
                   const int* __restrict__ active, const PushFace* __restrict__ push) {
+  pdl_enter();
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox F = fboxes[ch.item];
@@ -393,6 +409,7 @@ __global__ void __launch_bounds__(BLOCK) k_add_correction(const DevBox* __restri
                                                           const Chunk* __restrict__ chunks, double* phi,
                                                           const T* __restrict__ e, const int* __restrict__ active,
                                                           const PushFace* __restrict__ push) {
+  pdl_enter();
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
   if (active && !active[B.solve]) return;
@@ -634,9 +651,30 @@ __global__ void k_convert(const S* __restrict__ src, T* dst, int64_t n) {
 
 inline unsigned grid_of(int n) { return (unsigned)(n > 0 ? n : 0); }
 
+bool g_pdl = false;
+
+// <<<grid, block, smem, s>>>(args...) with the programmatic-serialization attribute when
+// dependent launch is on (the kernel must begin with pdl_enter())
+template <class... P, class... A>
+void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = g_pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
 }  // namespace
 
 static int64_t g_launches = 0;
+void set_pdl(bool on) { g_pdl = on; }
+bool pdl_enabled() { return g_pdl; }
 int64_t kernel_launch_count() { return g_launches; }
 void count_launches(int n) { g_launches += n; }
 
@@ -652,8 +690,8 @@ void count_launches(int n) { g_launches += n; }
 void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, cudaStream_t s) {
   if (!L.n_ghost_chunks) return;
   ++g_launches;
-  GMG_DISPATCH(dt, (k_fill<T><<<grid_of(L.n_ghost_chunks), BLOCK, 0, s>>>(L.boxes, L.ghosts, L.ghost_chunks,
-                                                                           (T*)f, colour, copy_mode, L.active)));
+  GMG_DISPATCH(dt, launch_pdl(k_fill<T>, grid_of(L.n_ghost_chunks), BLOCK, 0, s, L.boxes, L.ghosts, L.ghost_chunks,
+                               (T*)f, colour, copy_mode, L.active));
 }
 
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour, cudaStream_t s,
@@ -665,18 +703,17 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
     const float *wx = (const float*)c.wx, *wy = (const float*)c.wy, *wz = (const float*)c.wz;
     const float* invD = (const float*)c.invD;
     if (dt == DT_F32)
-      k_smooth4<float><<<grid_of(L.n_quad_chunks), BLOCK, 0, s>>>(L.boxes, L.quad_chunks, (float*)phi,
-                                                                  (const float*)rhs, wx, wy, wz, invD, colour,
-                                                                  L.active, pf);
+      launch_pdl(k_smooth4<float>, grid_of(L.n_quad_chunks), BLOCK, 0, s, L.boxes, L.quad_chunks, (float*)phi,
+                 (const float*)rhs, wx, wy, wz, invD, colour, L.active, pf);
     else
-      k_smooth4<bf16><<<grid_of(L.n_quad_chunks), BLOCK, 0, s>>>(L.boxes, L.quad_chunks, (bf16*)phi, (const bf16*)rhs,
-                                                                 wx, wy, wz, invD, colour, L.active, pf);
+      launch_pdl(k_smooth4<bf16>, grid_of(L.n_quad_chunks), BLOCK, 0, s, L.boxes, L.quad_chunks, (bf16*)phi,
+                 (const bf16*)rhs, wx, wy, wz, invD, colour, L.active, pf);
     return;
   }
-  GMG_DISPATCH(dt, (k_smooth<T><<<grid_of(L.n_pair_chunks), BLOCK, 0, s>>>(
-                       L.boxes, L.pair_chunks, (T*)phi, (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
-                       (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
-                       (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf)));
+  GMG_DISPATCH(dt, launch_pdl(k_smooth<T>, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks, (T*)phi,
+                              (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
+                              (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
+                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf));
 }
 
 // residual work list: pair items over every box (the bottom level included)
@@ -685,11 +722,11 @@ void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const 
   if (!L.n_pair_all_chunks) return;
   ++g_launches;
 #define GMG_RESID(TR)                                                                                     \
-  GMG_DISPATCH(dt, (k_residual<T, TR><<<grid_of(L.n_pair_all_chunks), BLOCK, 0, s>>>(                     \
-                       L.boxes, L.pair_all_chunks, (const T*)phi, (const T*)rhs,                              \
-                       (const typename CoefOf<T>::type*)c.wx, (const typename CoefOf<T>::type*)c.wy,      \
-                       (const typename CoefOf<T>::type*)c.wz, (const typename CoefOf<T>::type*)c.D, (TR*)r, \
-                       maxbits, shift)))
+  GMG_DISPATCH(dt, launch_pdl(k_residual<T, TR>, grid_of(L.n_pair_all_chunks), BLOCK, 0, s, L.boxes,           \
+                              L.pair_all_chunks, (const T*)phi, (const T*)rhs,                                  \
+                              (const typename CoefOf<T>::type*)c.wx, (const typename CoefOf<T>::type*)c.wy,     \
+                              (const typename CoefOf<T>::type*)c.wz, (const typename CoefOf<T>::type*)c.D,      \
+                              (TR*)r, maxbits, shift))
   switch (rdt) {
     case DT_F64: GMG_RESID(double); break;
     case DT_F32: GMG_RESID(float); break;
@@ -702,11 +739,11 @@ void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const v
                            const Coefs& cf, void* rc, cudaStream_t s) {
   if (!f.n_coarse_chunks) return;
   ++g_launches;
-  GMG_DISPATCH(dt, (k_resid_restrict<T, T><<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(
-                       f.boxes, c.boxes, f.parent, f.coarse_chunks, (const T*)phi, (const T*)rhs,
-                       (const typename CoefOf<T>::type*)cf.wx, (const typename CoefOf<T>::type*)cf.wy,
-                       (const typename CoefOf<T>::type*)cf.wz, (const typename CoefOf<T>::type*)cf.D, (T*)rc,
-                       f.active)));
+  GMG_DISPATCH(dt, launch_pdl(k_resid_restrict<T, T>, grid_of(f.n_coarse_chunks), BLOCK, 0, s, f.boxes, c.boxes,
+                              f.parent, f.coarse_chunks, (const T*)phi, (const T*)rhs,
+                              (const typename CoefOf<T>::type*)cf.wx, (const typename CoefOf<T>::type*)cf.wy,
+                              (const typename CoefOf<T>::type*)cf.wz, (const typename CoefOf<T>::type*)cf.D, (T*)rc,
+                              f.active));
 }
 
 void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s) {
@@ -722,16 +759,16 @@ void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void
   if (!f.n_coarse_chunks) return;
   ++g_launches;
   const PushFace* pf = push ? f.push_faces : nullptr;
-  GMG_DISPATCH(dt, (k_prolong_add<T><<<grid_of(f.n_coarse_chunks), BLOCK, 0, s>>>(
-                       f.boxes, c.boxes, f.parent, f.coarse_chunks, (const T*)coarse, (T*)fine, f.active, pf)));
+  GMG_DISPATCH(dt, launch_pdl(k_prolong_add<T>, grid_of(f.n_coarse_chunks), BLOCK, 0, s, f.boxes, c.boxes,
+                              f.parent, f.coarse_chunks, (const T*)coarse, (T*)fine, f.active, pf));
 }
 
 void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s, bool push) {
   if (!L.n_cell_chunks) return;
   ++g_launches;
   const PushFace* pf = push ? L.push_faces : nullptr;
-  GMG_DISPATCH(dt, (k_add_correction<T><<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, phi,
-                                                                                     (const T*)e, L.active, pf)));
+  GMG_DISPATCH(dt, launch_pdl(k_add_correction<T>, grid_of(L.n_cell_chunks), BLOCK, 0, s, L.boxes, L.cell_chunks,
+                              phi, (const T*)e, L.active, pf));
 }
 
 void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const double* dense, void* boxed,

@@ -131,6 +131,13 @@ void launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s);
 // copy a field of type dt into type dt2 (same layout, every element)
 void launch_convert(int dt, int dt2, const void* src, void* dst, int64_t n, cudaStream_t s);
 
+// programmatic dependent launch for the V-cycle kernels (fill, smooth, residuals,
+// restriction, interpolation, correction, coarse end, bottom): each may start while its
+// stream predecessor finishes and waits for it on the device (process-wide switch, set
+// per solve from gmg_params.pdl)
+void set_pdl(bool on);
+bool pdl_enabled();
+
 // number of kernel launches issued through these wrappers (host counter)
 int64_t kernel_launch_count();
 void count_launches(int n);

@@ -266,6 +266,9 @@ struct TailPtrs {
 template <class T>
 __global__ void __launch_bounds__(TT) k_vtail(const TailArgs a, const TailPtrs<T> P) {
   using A = typename Ar<T>::type;
+  // programmatic dependent launch: wait for the predecessor before any global access
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ double sh[TT / 32 + 1];
   const TailDesc Dd = a.descs[blockIdx.x];
   if (a.active && !a.active[Dd.solve]) return;
@@ -475,6 +478,20 @@ void fill_ptrs(TailPtrs<T>& P, const TailLevelBufs* lv, int n) {
 
 }  // namespace
 
+template <class T>
+static void launch_tail_kernel(int nblocks, const TailArgs& a, const TailPtrs<T>& P, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(TT);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k_vtail<T>, a, P);
+}
+
 void launch_vtail(int dt, int nblocks, const TailArgs& a, const TailLevelBufs* lv, int nlev, cudaStream_t s) {
   if (nblocks <= 0) return;
   count_launches(1);
@@ -482,19 +499,19 @@ void launch_vtail(int dt, int nblocks, const TailArgs& a, const TailLevelBufs* l
     case DT_F64: {
       TailPtrs<double> P;
       fill_ptrs(P, lv, nlev);
-      k_vtail<double><<<nblocks, TT, 0, s>>>(a, P);
+      launch_tail_kernel(nblocks, a, P, s);
       break;
     }
     case DT_F32: {
       TailPtrs<float> P;
       fill_ptrs(P, lv, nlev);
-      k_vtail<float><<<nblocks, TT, 0, s>>>(a, P);
+      launch_tail_kernel(nblocks, a, P, s);
       break;
     }
     default: {
       TailPtrs<bf16> P;
       fill_ptrs(P, lv, nlev);
-      k_vtail<bf16><<<nblocks, TT, 0, s>>>(a, P);
+      launch_tail_kernel(nblocks, a, P, s);
       break;
     }
   }
