@@ -151,6 +151,23 @@ def cpu_baseline(cfg, iters=2):
             "sample": f"{it} V-cycle iterations of the abec256 solve (FP64 oracle, 1 thread), {dt:.1f} s"}
 
 
+def whole_job(ms_local, updates_local, world, device):
+    """Whole-job throughput of N replicas: the timed region is the slowest rank's (max over
+    ranks), the work is every rank's (sum over ranks).  Returns (ms, updates, Mcell-upd/s)."""
+    import torch
+
+    ms, updates = float(ms_local), float(updates_local)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([updates], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, updates = float(t.item()), float(u.item())
+    return ms, updates, updates / (ms * 1e-3) / 1e6
+
+
 def summarize_tuning(t):
     """sweep variant chosen per MG level (bit 0: ghost push, bit 1: one thread per 4 cells;
     -1: no smoothing there) and the fused coarse end (1 on), as gmg_autotune measured them"""
@@ -415,12 +432,7 @@ def main():
             infos.append(info)
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, infos
+        return e0.elapsed_time(e1), infos
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -429,8 +441,7 @@ def main():
     clk = clocks.stop()
     its = [i.iterations for i in infos]
     assert all(i.status == gmg.OK for i in infos), [i.status for i in infos]
-    updates = sum(upd_per_vc * k for k in its) * world
-    value = updates / (ms * 1e-3) / 1e6
+    ms, updates, value = whole_job(ms, sum(upd_per_vc * k for k in its), world, dev)
     phi64 = ctx.unpack(phi).clone()
 
     # roofline of the dominant kernel: finest-level red-black smoother
@@ -466,9 +477,9 @@ def main():
         for name, prec in (("fp32", gmg.MIXED_FP32), ("bf16", gmg.MIXED_BF16)):
             ms_m, inf_m = timed_solves(prec, max(3, args.steps // 2), 2)
             itm = inf_m[0].iterations
-            upd = sum(upd_per_vc * i.iterations for i in inf_m) * world
+            ms_m, _, val_m = whole_job(ms_m, sum(upd_per_vc * i.iterations for i in inf_m), world, dev)
             err = float((ctx.unpack(phi) - phi64).abs().max() / phi64.abs().max())
-            mixed[name] = {"time_to_tol_ms": ms_m / len(inf_m), "value": upd / (ms_m * 1e-3) / 1e6, "unit": UNIT,
+            mixed[name] = {"time_to_tol_ms": ms_m / len(inf_m), "value": val_m, "unit": UNIT,
                            "iterations": itm, "final_rel_resid": inf_m[-1].final_resid / inf_m[-1].rhs_norm,
                            "rel_err_vs_fp64_solve": err,
                            "speedup_vs_fp64": (ms / args.steps) / (ms_m / len(inf_m))}
@@ -492,8 +503,8 @@ def main():
             tot_upd += upd_per_vc * info.iterations
         e1.record(stream)
         barrier()
-        ms_e = e0.elapsed_time(e1)
-        out["e2e"] = {"value": tot_upd * world / (ms_e * 1e-3) / 1e6, "unit": UNIT,
+        ms_e, _, val_e = whole_job(e0.elapsed_time(e1), tot_upd, world, dev)
+        out["e2e"] = {"value": val_e, "unit": UNIT,
                       "h2d_bytes_per_step": 8 * ncells, "d2h_bytes_per_step": 8 * ncells,
                       "wall_ms_per_step": 1e3 * (time.perf_counter() - t0) / nsteps}
 
