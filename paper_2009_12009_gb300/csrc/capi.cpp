@@ -340,6 +340,8 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.parent = (const int*)cv.take(sizeof(int) * M.parent.size());
     D.solve_chunk_range = (const int*)cv.take(sizeof(int) * M.solve_chunk_range.size());
     D.inv_count = (const double*)cv.take(sizeof(double) * M.inv_count.size());
+    D.push_faces = (const PushFace*)cv.take(sizeof(PushFace) * M.push_faces.size());
+    D.push_ok = M.push_ok ? 1 : 0;
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
     B.acoef = (double*)cv.take(8 * nf);
     B.wx = (double*)cv.take(8 * nf);
@@ -479,6 +481,7 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.parent, M.parent))) return st;
     if ((st = upload(c, D.solve_chunk_range, M.solve_chunk_range))) return st;
     if ((st = upload(c, D.inv_count, M.inv_count))) return st;
+    if ((st = upload(c, D.push_faces, M.push_faces))) return st;
     if ((st = upload(c, A.cf, H.cf))) return st;
     if ((st = upload(c, A.rcells, H.rcells))) return st;
     if ((st = upload(c, A.rfaces, H.rfaces))) return st;
@@ -1043,24 +1046,32 @@ void comp_correction(gmg_ctx* c, const gmg_params& p, const double* rc, const do
   double* ef = (double*)c->buff.e[DT_F64];
   double* ec = (double*)c->buf[0].e[DT_F64];
   double* crhs = (double*)c->buf[0].r[DT_F64];
+  // fine-box ghosts kept current by push (e_f starts at zero; every later write pushes);
+  // the coarse/fine ghosts depend on the fine cells inward and are refilled every colour
+  const bool push = p.ghost_push != 0 && c->devf.push_ok;
+  auto fill = [&](const double* cx) {
+    if (push) launch_cf_fill(c->amrd, ef, cx, CF_INTERP, s);
+    else fine_fill(c, ef, cx, CF_INTERP, s);
+  };
+  choose_pdl(p, s);
   cudaMemsetAsync(ef, 0, 8 * (size_t)c->F.nelem, s);
   for (int it = 0; it < p.nu1; ++it)
     for (int colour = 0; colour < 2; ++colour) {
-      fine_fill(c, ef, nullptr, CF_INTERP, s);  // coarse correction 0
-      launch_smooth(DT_F64, c->devf, ef, rf, coefs_fine(c), colour, s);
+      fill(nullptr);  // coarse correction 0
+      launch_smooth(DT_F64, c->devf, ef, rf, coefs_fine(c), colour, s, push);
     }
-  fine_fill(c, ef, nullptr, CF_INTERP, s);
+  fill(nullptr);
   cudaMemcpyAsync(crhs, rc, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, s);
   // covered cells: average of the fine correction residual r_f - A_f e_f
   launch_resid_restrict(DT_F64, c->devf, c->dev[0], ef, rf, coefs_fine(c), crhs, s);
   // uncovered cells next to the fine level: minus the fine correction's reflux
   launch_reflux(c->amrd, coefs64(c, 0), coefs_fine(c), crhs, ef, crhs, crhs, 0, s);
   vcycle(c, DT_F64, 0, p, s);
-  launch_prolong_add(DT_F64, c->devf, c->dev[0], ec, ef, s);
+  launch_prolong_add(DT_F64, c->devf, c->dev[0], ec, ef, s, push);
   for (int it = 0; it < p.nu2; ++it)
     for (int colour = 0; colour < 2; ++colour) {
-      fine_fill(c, ef, ec, CF_INTERP, s);
-      launch_smooth(DT_F64, c->devf, ef, rf, coefs_fine(c), colour, s);
+      fill(ec);
+      launch_smooth(DT_F64, c->devf, ef, rf, coefs_fine(c), colour, s, push);
     }
   launch_restrict(DT_F64, c->devf, c->dev[0], ef, ec, s);  // covered e_c := average of e_f
 }
