@@ -392,9 +392,18 @@ __global__ void __launch_bounds__(BLOCK)
   for (int dk = 0; dk < 2; ++dk)
     for (int dj = 0; dj < 2; ++dj) {
       const int64_t q = elem_index(F, 2 * ci, 2 * cj + dj, 2 * ck + dk);
-      const A v0 = (A)ld(fine + q) + e, v1 = (A)ld(fine + q + 1) + e;
-      st(fine + q, v0);
-      st(fine + q + 1, v1);
+      A v0, v1;
+      if constexpr (std::is_same<T, double>::value) {  // the pair (even element) as one 16-byte access
+        double2 f = *reinterpret_cast<const double2*>(fine + q);
+        v0 = f.x + e;
+        v1 = f.y + e;
+        *reinterpret_cast<double2*>(fine + q) = make_double2(v0, v1);
+      } else {
+        v0 = (A)ld(fine + q) + e;
+        v1 = (A)ld(fine + q + 1) + e;
+        st(fine + q, v0);
+        st(fine + q + 1, v1);
+      }
       if (push) {
         push_ghosts(F, ch.item, fboxes, push, fine, 2 * ci, 2 * cj + dj, 2 * ck + dk, v0);
         push_ghosts(F, ch.item, fboxes, push, fine, 2 * ci + 1, 2 * cj + dj, 2 * ck + dk, v1);
@@ -410,16 +419,30 @@ __global__ void __launch_bounds__(BLOCK) k_add_correction(const DevBox* __restri
                                                           const T* __restrict__ e, const int* __restrict__ active,
                                                           const PushFace* __restrict__ push) {
   pdl_enter();
+  // one thread per x-adjacent cell pair (chunks of pair items): the pair of phi is one
+  // 16-byte access (the first cell of a pair sits at an even element)
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
   if (active && !active[B.solve]) return;
   const int t = ch.start + threadIdx.x;
-  if (t >= B.nx * B.ny * B.nz) return;
-  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
-  const int64_t q = elem_index(B, i, j, k);
-  const double v = phi[q] + (double)ld(e + q);
-  phi[q] = v;
-  if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, v);
+  if (t >= ((B.nx + 1) >> 1) * B.ny * B.nz) return;
+  int i0, j, k;
+  pair_decode(B, t, i0, j, k);
+  const int64_t q = elem_index(B, i0, j, k);
+  if (i0 + 1 < B.nx) {
+    double2 p = *reinterpret_cast<const double2*>(phi + q);
+    p.x += (double)ld(e + q);
+    p.y += (double)ld(e + q + 1);
+    *reinterpret_cast<double2*>(phi + q) = p;
+    if (push) {
+      push_ghosts(B, ch.item, boxes, push, phi, i0, j, k, p.x);
+      push_ghosts(B, ch.item, boxes, push, phi, i0 + 1, j, k, p.y);
+    }
+  } else {
+    const double v = phi[q] + (double)ld(e + q);
+    phi[q] = v;
+    if (push) push_ghosts(B, ch.item, boxes, push, phi, i0, j, k, v);
+  }
 }
 
 template <class T>
@@ -764,11 +787,11 @@ void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void
 }
 
 void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s, bool push) {
-  if (!L.n_cell_chunks) return;
+  if (!L.n_pair_all_chunks) return;
   ++g_launches;
   const PushFace* pf = push ? L.push_faces : nullptr;
-  GMG_DISPATCH(dt, launch_pdl(k_add_correction<T>, grid_of(L.n_cell_chunks), BLOCK, 0, s, L.boxes, L.cell_chunks,
-                              phi, (const T*)e, L.active, pf));
+  GMG_DISPATCH(dt, launch_pdl(k_add_correction<T>, grid_of(L.n_pair_all_chunks), BLOCK, 0, s, L.boxes,
+                              L.pair_all_chunks, phi, (const T*)e, L.active, pf));
 }
 
 void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const double* dense, void* boxed,
