@@ -120,6 +120,11 @@ typedef struct {
                            and waits for it on the device before touching memory; 0: plain
                            launches; 2 (default): dependent launch outside CUDA graph
                            capture only.  Same results. */
+  int fuse_residual_sweep; /* 1 (default): the outer residual kernel also performs the
+                           first red half-sweep of the next V-cycle on level 0 (from a zero
+                           correction it is e = r / D on red cells, 0 on black), saving one
+                           pass over the finest level per iteration; 0: separate.  Same
+                           results (up to the sign of zero corrections). */
 } gmg_params;
 
 typedef struct {

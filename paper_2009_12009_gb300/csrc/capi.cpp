@@ -106,7 +106,7 @@ struct gmg_ctx {
     int64_t launches;
     int n_ev_smooth, n_ev_resid;  // profiling event pairs recorded per replay
   };
-  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int>, GraphEntry>
+  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int, int>, GraphEntry>
       graphs;
 
   // profiling events (pairs around finest-level smoother / outer residual launches)
@@ -656,8 +656,9 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
 // coefficients.
 // e_zero: e is zero including its ghosts (just cleared), so the first ghost fill would
 // copy zeros and is skipped.
+// red_done: the first red half-sweep was done by the residual kernel (level 0)
 void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s,
-                   bool e_zero = false, bool push = false) {
+                   bool e_zero = false, bool push = false, bool red_done = false) {
   if (p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0) {
     const LevelBufs& B = c->buf[m];
     const Coefs k = coefs_of(c, m, dt);
@@ -674,7 +675,7 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
     return;
   }
   for (int it = 0; it < nsweep; ++it) {
-    smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
+    if (!(red_done && it == 0)) smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
     smooth_colour(c, D, dt, m, 1, s, true, push, vec_on(c, p, dt, m));
   }
 }
@@ -744,12 +745,14 @@ void choose_pdl(const gmg_params& p, cudaStream_t s) {
   set_pdl(p.pdl == 1 || (p.pdl == 2 && cs == cudaStreamCaptureStatusNone));
 }
 
-void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
+void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool red_done = false) {
   choose_pdl(p, s);
   const bool fused = tail_on(c, p, dt) && c->tail_ok;
   const LevelDev D = fused ? vc_view(c, m) : c->dev[m];
   const LevelBufs& B = c->buf[m];
-  cudaMemsetAsync(B.e[dt], 0, dt_size(dt) * (size_t)c->L[m].nelem, s);
+  // (red_done: the residual kernel wrote e on every valid cell -- r / D on red, 0 on black
+  // -- and, with the push, its ghosts)
+  if (!red_done) cudaMemsetAsync(B.e[dt], 0, dt_size(dt) * (size_t)c->L[m].nelem, s);
   if (fused) launch_tails(c, dt, m, p, s);
   if (D.n_bot) {
     BottomArgs a{p.bottom_max_iter, p.bottom_tol, B.bot_work, c->bot_iters};
@@ -760,20 +763,33 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
   // ghosts share their source's colour, when the sweep is the two-pass one
   const bool push =
       push_on(c, p, dt, m) && D.push_ok && !(p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0);
-  smooth_sweeps(c, D, dt, m, p.nu1, p, s, true, push);
+  smooth_sweeps(c, D, dt, m, p.nu1, p, s, !red_done, push, red_done);
   if (p.nu1 > 0 && !push) launch_fill(dt, D, B.e[dt], -1, 0, s);  // (nu1 = 0: e and its ghosts are still zero)
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
   launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
-  vcycle(c, dt, m + 1, p, s);
+  vcycle(c, dt, m + 1, p, s, false);
   launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
   smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push);
+}
+
+// Whether the outer residual also performs the first red half-sweep of the next V-cycle
+// (level 0 smooths with the pair/4-cell kernels and pre-smooths at least once), and
+// whether level 0's V-cycle pushes ghosts (then that red half-sweep pushes too).
+bool resid_red(const gmg_ctx* c, const gmg_params& p, int dt) {
+  const LevelDev& D = c->dev[0];
+  return p.fuse_residual_sweep != 0 && p.nu1 > 0 && nlev(c) > 1 && D.n_pair_chunks > 0 &&
+         !(p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0);
+}
+bool level0_push(const gmg_ctx* c, const gmg_params& p, int dt) {
+  return push_on(c, p, dt, 0) && c->dev[0].push_ok;
 }
 
 // One outer iteration: e = V(r); phi += e; r = rhs - A phi with per-problem ||r||_inf into
 // normbits[0, ns), copied to the pinned host mirror.
 void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const gmg_params& p, cudaStream_t s) {
   const int ns = c->ns();
-  vcycle(c, dt, 0, p, s);  // (sets the dependent-launch switch for the launches below too)
+  const bool rr = resid_red(c, p, dt);
+  vcycle(c, dt, 0, p, s, rr);  // (sets the dependent-launch switch for the launches below too)
   // phi's ghosts stay current by push (they were filled, or zero, before the first update)
   const bool push = p.ghost_push != 0 && c->dev[0].push_ok;
   launch_add_correction(dt, c->dev[0], phi, c->buf[0].e[dt], s, push);
@@ -782,7 +798,8 @@ void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const g
   cudaEvent_t* ev = c->profiling ? ev_pair(c->ev_resid, c->n_ev_resid++) : nullptr;
   if (ev) record_timing_event(c, ev[0], s);
   launch_residual(DT_F64, dt, c->dev[0], phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits,
-                  any_singular(c) ? c->scal : nullptr, s);
+                  any_singular(c) ? c->scal : nullptr, s, rr ? c->buf[0].e[dt] : nullptr,
+                  rr ? coefs_of(c, 0, dt).invD : nullptr, rr && level0_push(c, p, dt));
   if (ev) record_timing_event(c, ev[1], s);
   cudaMemcpyAsync(c->h_bits, c->normbits, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s);
 }
@@ -815,6 +832,8 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
+  if (p.fuse_residual_sweep != 0 && p.fuse_residual_sweep != 1)
+    SETERR(c, GMG_ERR_BAD_INPUT, "fuse_residual_sweep must be 0 or 1");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
   return GMG_OK;
 }
@@ -867,7 +886,12 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   // phi = 0; r = (rhs - mean) - A 0
   CK(c, cudaMemsetAsync(phi, 0, 8 * (size_t)ne0, s));
   CK(c, cudaMemsetAsync(c->normbits, 0, 8 * (size_t)ns, s));
-  launch_residual(DT_F64, dt, D0, phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits, sing ? c->scal : nullptr, s);
+  {
+    const bool rr = resid_red(c, p, dt);
+    launch_residual(DT_F64, dt, D0, phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits, sing ? c->scal : nullptr,
+                    s, rr ? c->buf[0].e[dt] : nullptr, rr ? coefs_of(c, 0, dt).invD : nullptr,
+                    rr && level0_push(c, p, dt));
+  }
   CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
   CK(c, cudaGetLastError());
@@ -901,7 +925,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   if (p.use_graph && nlive) {
     auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
                                p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep, p.ghost_push,
-                               p.vector_smooth, p.pdl);
+                               p.vector_smooth, p.pdl, p.fuse_residual_sweep);
     auto itg = c->graphs.find(key);
     if (itg != c->graphs.end()) {
       gexec = itg->second.exec;
@@ -1470,6 +1494,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;
+  p->fuse_residual_sweep = 1;
   return GMG_OK;
 }
 

@@ -291,9 +291,12 @@ __global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ b
                                                     const typename CoefOf<T>::type* __restrict__ wy,
                                                     const typename CoefOf<T>::type* __restrict__ wz,
                                                     const typename CoefOf<T>::type* __restrict__ D, R* r,
-                                                    unsigned long long* maxbits, const double* shift_p) {
+                                                    unsigned long long* maxbits, const double* shift_p, R* e,
+                                                    const typename CoefOf<R>::type* __restrict__ invDe,
+                                                    const PushFace* __restrict__ push) {
   pdl_enter();
   using A = typename Arith<T>::type;
+  using AR = typename Arith<R>::type;
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
   const int t = ch.start + threadIdx.x;
@@ -309,6 +312,14 @@ __global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ b
       if (r) st(r + q0 + c, v);
       const unsigned long long bb = abs_bits((double)v);
       mx = bb > mx ? bb : mx;
+      if (e) {
+        // the first red half-sweep of the next V-cycle on e = 0: every neighbour term is
+        // zero, so a red cell becomes r / D (r as stored), a black cell stays 0
+        const bool red = ((B.lo[0] + B.lo[1] + B.lo[2] + i0 + c + j + k) & 1) == 0;
+        const AR ev = red ? (AR)ld(r + q0 + c) * (AR)ldg(invDe + q0 + c) : (AR)0;
+        st(e + q0 + c, ev);
+        if (push) push_ghosts(B, ch.item, boxes, push, e, i0 + c, j, k, ev);
+      }
     }
   }
   if (maxbits) block_max_atomic(mx, maxbits + B.solve);
@@ -741,15 +752,17 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
 
 // residual work list: pair items over every box (the bottom level included)
 void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const void* rhs, const Coefs& c, void* r,
-                     unsigned long long* maxbits, const double* shift, cudaStream_t s) {
+                     unsigned long long* maxbits, const double* shift, cudaStream_t s, void* e, const void* invDe,
+                     bool push) {
   if (!L.n_pair_all_chunks) return;
   ++g_launches;
+  const PushFace* pf = push ? L.push_faces : nullptr;
 #define GMG_RESID(TR)                                                                                     \
   GMG_DISPATCH(dt, launch_pdl(k_residual<T, TR>, grid_of(L.n_pair_all_chunks), BLOCK, 0, s, L.boxes,           \
                               L.pair_all_chunks, (const T*)phi, (const T*)rhs,                                  \
                               (const typename CoefOf<T>::type*)c.wx, (const typename CoefOf<T>::type*)c.wy,     \
                               (const typename CoefOf<T>::type*)c.wz, (const typename CoefOf<T>::type*)c.D,      \
-                              (TR*)r, maxbits, shift))
+                              (TR*)r, maxbits, shift, (TR*)e, (const typename CoefOf<TR>::type*)invDe, pf))
   switch (rdt) {
     case DT_F64: GMG_RESID(double); break;
     case DT_F32: GMG_RESID(float); break;

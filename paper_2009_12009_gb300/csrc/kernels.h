@@ -84,8 +84,12 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
 // r = (rhs - shift[solve]) - A phi on valid cells (ghosts of phi must be filled); rdt =
 // type of r; maxbits (may be null): per-solve atomic max of |r| as IEEE bits; shift (may be
 // null): per-solve device scalars
+// e (may be null): also the first red half-sweep of a V-cycle on this r from e = 0 --
+// e = r / D on red cells (invDe: 1/D in the coefficient type of rdt), 0 on black cells,
+// pushed into e's ghosts when push is set
 void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const void* rhs, const Coefs& c,
-                     void* r, unsigned long long* maxbits, const double* shift, cudaStream_t s);
+                     void* r, unsigned long long* maxbits, const double* shift, cudaStream_t s, void* e = nullptr,
+                     const void* invDe = nullptr, bool push = false);
 // coarse r = restriction of (rhs - A phi) (ghosts of phi filled)
 void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* phi, const void* rhs,
                            const Coefs& cf, void* rc, cudaStream_t s);

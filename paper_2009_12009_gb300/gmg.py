@@ -39,7 +39,7 @@ class Params(C.Structure):
                 ("bottom_tol", C.c_double), ("precision", C.c_int), ("project_mean", C.c_int),
                 ("use_graph", C.c_int), ("profile", C.c_int), ("fused_coarse", C.c_int),
                 ("fused_sweep", C.c_int), ("ghost_push", C.c_int),
-                ("vector_smooth", C.c_int), ("pdl", C.c_int)]
+                ("vector_smooth", C.c_int), ("pdl", C.c_int), ("fuse_residual_sweep", C.c_int)]
 
 
 class SolveInfo(C.Structure):

@@ -308,11 +308,12 @@ def test_profiled_solve_times_kernels(graph):
     launches (as timestamped graph nodes when the iteration is a captured graph)."""
     pair = Pair("uneven", mixed=False)
     rhs = pair.C.pack(torch.from_numpy(pair.cfg["rhs"]))
-    phi, info = pair.C.solve(rhs, tol_rel=0.0, max_iter=3, use_graph=graph, profile=1)
-    assert info.status == gmg.NOT_CONVERGED  # tol 0 is never reached; 3 iterations run
-    assert info.smooth0_launches == 3 * 8 and info.resid0_launches == 3
-    assert info.smooth0_ms > 0 and info.resid0_ms > 0
-    assert info.kernel_launches > 3 * 8
+    for fuse, per_iter in ((0, 8), (1, 7)):  # fused: the first red half-sweep runs in the residual
+        phi, info = pair.C.solve(rhs, tol_rel=0.0, max_iter=3, use_graph=graph, profile=1, fuse_residual_sweep=fuse)
+        assert info.status == gmg.NOT_CONVERGED  # tol 0 is never reached; 3 iterations run
+        assert info.smooth0_launches == 3 * per_iter and info.resid0_launches == 3
+        assert info.smooth0_ms > 0 and info.resid0_ms > 0
+        assert info.kernel_launches > 3 * per_iter
 
 
 def test_fused_coarse_launches_fewer_kernels():
@@ -456,3 +457,29 @@ def test_vector_smooth_is_bitwise_pair_smooth(case):
         a1 = C.unpack(p1).clone()
         p0, _ = C.solve(rhs, tol_rel=0.0, max_iter=3, precision=prec, vector_smooth=0, project_mean=1)
         assert torch.equal(a1, C.unpack(p0)), prec
+
+
+@pytest.mark.parametrize("name", ["uneven", "periodic", "helmholtz", "poisson32"])
+def test_residual_fused_first_red_sweep_is_exact(name):
+    """The outer residual also doing the first red half-sweep of the next V-cycle (e = r / D
+    on red cells from e = 0) gives the iterates of the separate sweep (equal values; only
+    the sign of exact zeros may differ), in FP64 and both mixed forms, with and without push."""
+    cfg = cases.make(name)
+    C = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], prob_hi=cfg.get("prob_hi", (1.0, 1.0, 1.0)),
+                    boxes=cfg["boxes"], stream=torch.cuda.current_stream().cuda_stream)
+    C.allocate(gmg.MIXED_FP32)
+    C.set_scalars(cfg["a"], cfg["b"])
+    if cfg["alpha"] is not None:
+        C.set_alpha(torch.from_numpy(cfg["alpha"]))
+    C.set_beta(torch.from_numpy(cfg["beta"]) if cfg["beta"] is not None else None)
+    r = cfg["rhs"] - (cfg["rhs"].mean() if name in ("periodic", "poisson32") else 0.0)
+    rhs = C.pack(torch.from_numpy(r))
+    for prec in (gmg.FP64, gmg.MIXED_FP32, gmg.MIXED_BF16):
+        for push in (0, 1):
+            p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=4, precision=prec, ghost_push=push, fuse_residual_sweep=1,
+                             project_mean=1)
+            a1 = C.unpack(p1).clone()
+            p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=4, precision=prec, ghost_push=push, fuse_residual_sweep=0,
+                             project_mean=1)
+            assert torch.equal(a1, C.unpack(p0)), (prec, push)
+            assert i1.kernel_launches < i0.kernel_launches
