@@ -20,8 +20,11 @@
  *     harmonic mean of the two cell values; at a physical wall the face takes the
  *     interior cell's beta;
  *   - ghost cells (Sec. "Operations on a level"): copied from the box at the same level
- *     that owns the cell (periodic images included); at a homogeneous Dirichlet wall the
- *     ghost is minus the adjacent interior value (the wall value 0 sits on the face);
+ *     that owns the cell (periodic images included); at a Dirichlet wall the ghost is
+ *     2g minus the adjacent interior value (the wall value g sits on the face: linear
+ *     extrapolation), at a Neumann wall the interior value plus h*g (g the outward normal
+ *     derivative); g = 0 (homogeneous walls) unless wall values are given, and always 0
+ *     in the correction equations of the V-cycle;
  *   - smoother: red-black Gauss-Seidel, colour = parity of i+j+k in the level's global
  *     index, ghosts refreshed before every colour, red first;
  *   - restriction (Sec. "Operations between levels": average of fine data): mean of the
@@ -34,9 +37,10 @@
  *     domain allows;
  *   - bottom solve (Sec. "Linear Solvers": Krylov bottom solver): unpreconditioned
  *     BiCGStab (van der Vorst 1992) from x0 = 0;
- *   - outer loop: phi += Vcycle(r); r = rhs - A phi; stop at ||r||_inf <= tol*||rhs||_inf.
- *   - singular problems (all periodic, a = 0): rhs, bottom rhs and the result are
- *     projected onto zero mean.
+ *   - outer loop: r0 = rhs - A(0) (nonzero only through wall values); phi += Vcycle(r);
+ *     r = rhs - A phi with the wall values; stop at ||r||_inf <= tol*||r0||_inf.
+ *   - singular problems (no Dirichlet wall, a = 0): the initial residual, the bottom rhs
+ *     and the result are projected onto zero mean.
  *
  * Parity pins: every function here is pinned by tests in tests/test_oracle_*.py
  * (closed-form discrete eigen-solutions, second-order convergence on a manufactured
@@ -51,6 +55,7 @@
 
 #define ORC_PERIODIC 0
 #define ORC_DIRICHLET 1
+#define ORC_NEUMANN 2
 #define ORC_MAXLEV 32
 
 typedef struct {
@@ -66,6 +71,10 @@ typedef struct {
   int64_t ng;
   int64_t *gdst, *gsrc;
   double *gfac;
+  /* per ghost-map entry at a physical wall: the wall face (2*d + side) and the index of
+     the ghost's tangential position in that face's value array; gwall = -1 elsewhere */
+  int *gwall;
+  int64_t *gtan;
   int *parent;           /* box on the next coarser level that contains coarsen(box), or NULL */
   /* coefficients on this level (ghosted layout; face slot i holds the face at i-1/2) */
   double *alpha, *bx, *by, *bz;
@@ -81,6 +90,7 @@ typedef struct {
   int nu1, nu2, bot_maxit;
   double bot_tol;
   int last_bottom_iters;
+  double* bcval[6];  /* level-0 wall values per face (2*d + side), or NULL (g = 0) */
 } oprob;
 
 /* ------------------------------------------------------------------ layout */
@@ -138,6 +148,8 @@ static void build_ghost_map(olev* l) {
   l->gdst = (int64_t*)malloc(sizeof(int64_t) * (cap + 1));
   l->gsrc = (int64_t*)malloc(sizeof(int64_t) * (cap + 1));
   l->gfac = (double*)malloc(sizeof(double) * (cap + 1));
+  l->gwall = (int*)malloc(sizeof(int) * (cap + 1));
+  l->gtan = (int64_t*)malloc(sizeof(int64_t) * (cap + 1));
   int64_t n = 0;
   for (int b = 0; b < l->nb; ++b) {
     for (int d = 0; d < 3; ++d) {
@@ -159,13 +171,21 @@ static void build_ghost_map(olev* l) {
               g[d] = l->dlo[d] + pmod(g[d] - l->dlo[d], len);
               outside = 0;
             }
+            l->gwall[n] = -1;
+            l->gtan[n] = 0;
             if (outside) {
-              /* homogeneous Dirichlet: ghost = -(adjacent interior cell) */
+              /* wall: ghost = -(adjacent interior cell) at a Dirichlet wall, +(adjacent
+                 interior cell) at a Neumann wall; the wall value's part is added by
+                 fill_ghosts_bc.  Tangential axes of the face in increasing order, the
+                 lower one fastest. */
               int in[3] = {loc[0], loc[1], loc[2]};
+              int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
               in[d] = side ? bn(l, b, d) - 1 : 0;
               l->gdst[n] = dst;
               l->gsrc[n] = IX(l, b, in[0], in[1], in[2]);
-              l->gfac[n] = -1.0;
+              l->gfac[n] = bc == ORC_NEUMANN ? 1.0 : -1.0;
+              l->gwall[n] = 2 * d + side;
+              l->gtan[n] = (int64_t)(g[t1] - l->dlo[t1]) + (int64_t)(l->dhi[t1] - l->dlo[t1] + 1) * (g[t2] - l->dlo[t2]);
             } else {
               int ob = find_box(l, g);
               l->gdst[n] = dst;
@@ -194,6 +214,13 @@ static void fill_ghosts(const olev* l, double* f) {
     if (l->gsrc[q] >= 0) f[l->gdst[q]] = l->gfac[q] * f[l->gsrc[q]];
 }
 
+/* a level with no Dirichlet wall has the constants in the null space of A when a = 0 */
+static int has_dirichlet(const olev* l) {
+  for (int d = 0; d < 3; ++d)
+    if (l->bclo[d] == ORC_DIRICHLET || l->bchi[d] == ORC_DIRICHLET) return 1;
+  return 0;
+}
+
 static int covers_domain(const olev* l) {
   int64_t vol = 0, dvol = 1;
   for (int b = 0; b < l->nb; ++b) vol += (int64_t)bn(l, b, 0) * bn(l, b, 1) * bn(l, b, 2);
@@ -204,7 +231,7 @@ static int covers_domain(const olev* l) {
 /* ------------------------------------------------------------- hierarchy */
 
 static void free_level(olev* l) {
-  free(l->lo); free(l->hi); free(l->off); free(l->gdst); free(l->gsrc); free(l->gfac);
+  free(l->lo); free(l->hi); free(l->off); free(l->gdst); free(l->gsrc); free(l->gfac); free(l->gwall); free(l->gtan);
   free(l->parent); free(l->alpha); free(l->bx); free(l->by); free(l->bz);
   free(l->e); free(l->r); free(l->t);
   memset(l, 0, sizeof(*l));
@@ -285,7 +312,10 @@ void* orc_create(const int* dlo, const int* dhi, const int* bclo, const int* bch
   }
   /* validity: boxes inside the domain and pairwise disjoint; periodic on both sides */
   for (int d = 0; d < 3; ++d)
-    if ((bclo[d] == ORC_PERIODIC) != (bchi[d] == ORC_PERIODIC)) { free(l->lo); free(l->hi); free(p); return NULL; }
+    if ((bclo[d] == ORC_PERIODIC) != (bchi[d] == ORC_PERIODIC) || bclo[d] < 0 || bclo[d] > 2 || bchi[d] < 0 ||
+        bchi[d] > 2) {
+      free(l->lo); free(l->hi); free(p); return NULL;
+    }
   for (int b = 0; b < nb; ++b) {
     for (int d = 0; d < 3; ++d)
       if (l->lo[3 * b + d] < dlo[d] || l->hi[3 * b + d] > dhi[d] || l->lo[3 * b + d] > l->hi[3 * b + d]) {
@@ -308,9 +338,7 @@ void* orc_create(const int* dlo, const int* dhi, const int* bclo, const int* bch
   p->nu2 = 2;
   p->bot_maxit = 200;
   p->bot_tol = 1e-4;
-  int allper = 1;
-  for (int d = 0; d < 3; ++d) allper &= (bclo[d] == ORC_PERIODIC);
-  p->singular = allper; /* until a != 0 is set */
+  p->singular = !has_dirichlet(l); /* until a != 0 is set */
   return p;
 }
 
@@ -318,6 +346,7 @@ void orc_destroy(void* vp) {
   oprob* p = (oprob*)vp;
   if (!p) return;
   for (int m = 0; m < p->nlev; ++m) free_level(&p->L[m]);
+  for (int f = 0; f < 6; ++f) free(p->bcval[f]);
   free(p);
 }
 
@@ -391,9 +420,7 @@ int orc_set_coeffs(void* vp, double a, double bsc, const double* alpha_dense, co
   olev* l = &p->L[0];
   p->a = a;
   p->b = bsc;
-  int allper = 1;
-  for (int d = 0; d < 3; ++d) allper &= (l->bclo[d] == ORC_PERIODIC);
-  p->singular = allper && (a == 0.0);
+  p->singular = !has_dirichlet(l) && (a == 0.0);
   memset(l->alpha, 0, sizeof(double) * l->ntot);
   memset(l->bx, 0, sizeof(double) * l->ntot);
   memset(l->by, 0, sizeof(double) * l->ntot);
@@ -747,11 +774,169 @@ void orc_vcycle(void* vp, int m, double* e, const double* r) {
   }
 }
 
+/* ------------------------------------------------------------ wall values */
+
+/* Values g on a level-0 wall face (face = 2*d + side): phi on the face for a Dirichlet
+   wall, the outward normal derivative for a Neumann wall.  `values` is a dense array over
+   the face's two tangential axes in increasing order, the lower one fastest (NULL: g = 0).
+   Returns -1 for a periodic face or a bad face index. */
+int orc_set_bc_values(void* vp, int face, const double* values) {
+  oprob* p = (oprob*)vp;
+  olev* l = &p->L[0];
+  if (face < 0 || face > 5) return -1;
+  int d = face / 2, side = face % 2;
+  int bc = side ? l->bchi[d] : l->bclo[d];
+  if (bc == ORC_PERIODIC) return -1;
+  free(p->bcval[face]);
+  p->bcval[face] = NULL;
+  if (!values) return 0;
+  int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  int64_t n = (int64_t)(l->dhi[t1] - l->dlo[t1] + 1) * (l->dhi[t2] - l->dlo[t2] + 1);
+  p->bcval[face] = (double*)malloc(sizeof(double) * n);
+  memcpy(p->bcval[face], values, sizeof(double) * n);
+  return 0;
+}
+
+/* level-0 ghosts with the wall values: the homogeneous ghost plus 2g (Dirichlet: the
+   line through the interior value and g on the face) or h*g (Neumann: the one-sided
+   difference across the face equals g) */
+static void fill_ghosts_bc(const oprob* p, double* f) {
+  const olev* l = &p->L[0];
+  fill_ghosts(l, f);
+  for (int64_t q = 0; q < l->ng; ++q) {
+    int w = l->gwall[q];
+    if (w < 0 || !p->bcval[w]) continue;
+    int d = w / 2, side = w % 2;
+    double g = p->bcval[w][l->gtan[q]];
+    int bc = side ? l->bchi[d] : l->bclo[d];
+    f[l->gdst[q]] += bc == ORC_NEUMANN ? l->h[d] * g : 2.0 * g;
+  }
+}
+
+/* r = rhs - A phi on level 0 with the wall values in the ghosts */
+static void residual_bc(oprob* p, double* phi, const double* rhs, double* r) {
+  olev* l = &p->L[0];
+  fill_ghosts_bc(p, phi);
+  for (int b = 0; b < l->nb; ++b)
+    for (int k = 0; k < bn(l, b, 2); ++k)
+      for (int j = 0; j < bn(l, b, 1); ++j)
+        for (int i = 0; i < bn(l, b, 0); ++i)
+          r[IX(l, b, i, j, k)] = rhs[IX(l, b, i, j, k)] - op_cell(p, l, phi, b, i, j, k);
+}
+
+/* out = A phi with the wall values (an affine map unless every g is 0), dense arrays */
+void orc_apply_bc(void* vp, const double* phi_dense, double* out_dense) {
+  oprob* p = (oprob*)vp;
+  olev* l = &p->L[0];
+  double* phi = (double*)calloc(l->ntot, sizeof(double));
+  double* out = (double*)calloc(l->ntot, sizeof(double));
+  orc_dense_to_boxed(vp, 0, phi_dense, phi);
+  fill_ghosts_bc(p, phi);
+  for (int b = 0; b < l->nb; ++b)
+    for (int k = 0; k < bn(l, b, 2); ++k)
+      for (int j = 0; j < bn(l, b, 1); ++j)
+        for (int i = 0; i < bn(l, b, 0); ++i) out[IX(l, b, i, j, k)] = op_cell(p, l, phi, b, i, j, k);
+  orc_boxed_to_dense(vp, 0, out, out_dense);
+  free(phi); free(out);
+}
+
+/* ------------------------------------------------- gradients (one level) */
+
+/* Gradient of a loss L(phi) with respect to the cell-centred beta of level 0, given the
+   solution phi of A phi = rhs (wall values in A) and the adjoint lambda (A^T lambda =
+   dL/dphi).  dL/dbeta = lambda^T d(rhs - A phi)/dbeta: the row of cell q holds, per face
+   f, -b beta_f (phi_nbr - phi_q) / h^2, so face f adds lambda_q b (phi_nbr - phi_q) / h^2
+   for each of its (one or two) rows, with phi_nbr the neighbour or, at a wall, the ghost
+   of the wall rule (wall values included).  The face sum then goes to the cells through
+   the rule that made beta_f: harmonic mean 2 bL bR / (bL + bR), derivative 2 bR^2 /
+   (bL + bR)^2 for bL; a wall face takes the interior cell's beta, derivative 1.
+   Dense arrays over the domain (x fastest); beta_dense is the cell beta given to
+   orc_set_coeffs (NULL: beta = 1). */
+void orc_grad_beta_cells(void* vp, const double* phi_dense, const double* lam_dense, const double* beta_dense,
+                         double* out_dense) {
+  oprob* p = (oprob*)vp;
+  olev* l = &p->L[0];
+  int n[3] = {l->dhi[0] - l->dlo[0] + 1, l->dhi[1] - l->dlo[1] + 1, l->dhi[2] - l->dlo[2] + 1};
+  int64_t N = (int64_t)n[0] * n[1] * n[2];
+  for (int64_t q = 0; q < N; ++q) out_dense[q] = 0.0;
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        int c[3] = {i, j, k};
+        int64_t q = i + (int64_t)n[0] * (j + (int64_t)n[1] * k);
+        double bq = beta_dense ? beta_dense[q] : 1.0;
+        for (int d = 0; d < 3; ++d) {
+          double w = p->b / (l->h[d] * l->h[d]);
+          int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+          for (int side = 0; side < 2; ++side) {
+            int nb[3] = {c[0], c[1], c[2]};
+            nb[d] += side ? 1 : -1;
+            int outside = nb[d] < 0 || nb[d] >= n[d];
+            int bc = side ? l->bchi[d] : l->bclo[d];
+            if (outside && bc == ORC_PERIODIC) {
+              nb[d] = pmod(nb[d], n[d]);
+              outside = 0;
+            }
+            if (outside) {
+              double ghost = bc == ORC_NEUMANN ? phi_dense[q] : -phi_dense[q];
+              const double* gv = p->bcval[2 * d + side];
+              if (gv) {
+                double g = gv[(int64_t)c[t1] + (int64_t)n[t1] * c[t2]];
+                ghost += bc == ORC_NEUMANN ? l->h[d] * g : 2.0 * g;
+              }
+              out_dense[q] += lam_dense[q] * w * (ghost - phi_dense[q]);
+              continue;
+            }
+            int64_t r = nb[0] + (int64_t)n[0] * (nb[1] + (int64_t)n[1] * nb[2]);
+            double br = beta_dense ? beta_dense[r] : 1.0;
+            double s = bq + br;
+            /* this row's share of face f, passed to both cells of the face */
+            double gf = lam_dense[q] * w * (phi_dense[r] - phi_dense[q]);
+            out_dense[q] += gf * 2.0 * br * br / (s * s);
+            out_dense[r] += gf * 2.0 * bq * bq / (s * s);
+          }
+        }
+      }
+}
+
+/* dL/dg on wall face `face` (= 2*d + side): the wall values enter rhs - A 0 of the wall
+   cell q as +2 b beta_f g / h^2 (Dirichlet) or +b beta_f g / h (Neumann), so
+   dL/dg = lambda_q times that factor.  out: the face's value layout (tangential axes in
+   increasing order, the lower one fastest). */
+int orc_grad_wall_values(void* vp, const double* lam_dense, int face, double* out) {
+  oprob* p = (oprob*)vp;
+  olev* l = &p->L[0];
+  if (face < 0 || face > 5) return -1;
+  int d = face / 2, side = face % 2;
+  int bc = side ? l->bchi[d] : l->bclo[d];
+  if (bc == ORC_PERIODIC) return -1;
+  int n[3] = {l->dhi[0] - l->dlo[0] + 1, l->dhi[1] - l->dlo[1] + 1, l->dhi[2] - l->dlo[2] + 1};
+  int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  double* fa = d == 0 ? l->bx : (d == 1 ? l->by : l->bz);
+  for (int v = 0; v < n[t2]; ++v)
+    for (int u = 0; u < n[t1]; ++u) {
+      int c[3], fl[3];
+      c[d] = side ? n[d] - 1 : 0;
+      c[t1] = u;
+      c[t2] = v;
+      int g[3] = {l->dlo[0] + c[0], l->dlo[1] + c[1], l->dlo[2] + c[2]};
+      int b = find_box(l, g);
+      for (int e = 0; e < 3; ++e) fl[e] = g[e] - l->lo[3 * b + e];
+      if (side) fl[d] += 1; /* the wall face's slot */
+      double beta_f = fa[IX(l, b, fl[0], fl[1], fl[2])];
+      double h = l->h[d];
+      double fac = bc == ORC_NEUMANN ? p->b * beta_f / h : 2.0 * p->b * beta_f / (h * h);
+      out[u + (int64_t)n[t1] * v] = lam_dense[c[0] + (int64_t)n[0] * (c[1] + (int64_t)n[1] * c[2])] * fac;
+    }
+  return 0;
+}
+
 /* ------------------------------------------------------------ outer loop */
 
-/* Solve A phi = rhs (dense arrays over the level-0 domain) from phi = 0:
-   phi += Vcycle(r), r = rhs - A phi, until ||r||_inf <= max(tol_rel*||rhs||_inf, tol_abs)
-   or maxit iterations.  hist[0..iters] receives ||r||_inf after each iteration.
+/* Solve A phi = rhs (dense arrays over the level-0 domain, wall values in A) from
+   phi = 0: r0 = rhs - A 0; phi += Vcycle(r), r = rhs - A phi, until
+   ||r||_inf <= max(tol_rel*||r0||_inf, tol_abs) or maxit iterations (without wall values
+   r0 = rhs).  The V-cycle solves the correction equation with homogeneous walls.  hist[0..iters] receives ||r||_inf after each iteration.
    status: 0 converged, -1 bad input (nonzero-mean rhs of a singular problem without
    project_mean), -2 not converged, -3 diverged (non-finite residual). */
 int orc_solve(void* vp, const double* rhs_dense, double* phi_dense, double tol_rel, double tol_abs, int maxit,
@@ -764,18 +949,19 @@ int orc_solve(void* vp, const double* rhs_dense, double* phi_dense, double tol_r
   double* r = (double*)calloc(n, sizeof(double));
   double* e = (double*)calloc(n, sizeof(double));
   orc_dense_to_boxed(vp, 0, rhs_dense, rhs);
-  double rhsnorm = lev_norminf(l, rhs);
+  residual_bc(p, phi, rhs, r); /* r0 = rhs - A 0 */
+  double rhsnorm = lev_norminf(l, r);
   *status = 0;
   if (p->singular) {
-    double mean = lev_sum(l, rhs) / (double)lev_ncells(l);
+    double mean = lev_sum(l, r) / (double)lev_ncells(l);
     if (fabs(mean) > 1e-12 * rhsnorm && !project_mean) {
       *status = -1;
       free(rhs); free(phi); free(r); free(e);
       return 0;
     }
     lev_add_const(l, rhs, -mean);
+    lev_add_const(l, r, -mean);
   }
-  memcpy(r, rhs, sizeof(double) * n);
   double target = tol_rel * rhsnorm;
   if (tol_abs > target) target = tol_abs;
   double rn = lev_norminf(l, r);
@@ -784,7 +970,7 @@ int orc_solve(void* vp, const double* rhs_dense, double* phi_dense, double tol_r
   while (!(rn <= target) && it < maxit) {
     orc_vcycle(vp, 0, e, r);
     for (int64_t q = 0; q < n; ++q) phi[q] += e[q];
-    orc_residual(vp, 0, phi, rhs, r);
+    residual_bc(p, phi, rhs, r);
     rn = lev_norminf(l, r);
     ++it;
     if (hist) hist[it] = rn;
@@ -1200,8 +1386,12 @@ static void coarse_row(const oamr* A, orow* R, int b, int i, int j, int k) {
       int64_t fs = IX(c, b, fl[0], fl[1], fl[2]);
       double w = A->b / (hc * hc);
       term(A, R, 0, q, w, 0, d, fs);
-      if (nq < 0) term(A, R, 0, q, w, 0, d, fs); /* homogeneous Dirichlet: ghost = -phi */
-      else term(A, R, 0, nq, -w, 0, d, fs);
+      if (nq < 0) { /* wall: ghost = -phi (homogeneous Dirichlet) or +phi (homogeneous Neumann) */
+        int bc = side ? c->bchi[d] : c->bclo[d];
+        term(A, R, 0, q, bc == ORC_NEUMANN ? -w : w, 0, d, fs);
+      } else {
+        term(A, R, 0, nq, -w, 0, d, fs);
+      }
     }
   }
 }

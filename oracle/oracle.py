@@ -22,6 +22,7 @@ LIB = os.path.join(BUILD, "liboracle.so")
 
 PERIODIC = 0
 DIRICHLET = 1
+NEUMANN = 2
 
 # status codes of orc_solve
 OK, BAD_INPUT, NOT_CONVERGED, DIVERGED = 0, -1, -2, -3
@@ -95,6 +96,12 @@ def _declare(L):
     L.orc_solve.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_double, C.c_int, C.c_int, _f64p, _i32p]
     L.orc_solve.restype = C.c_int
     L.orc_apply.argtypes = [C.c_void_p, _f64p, _f64p]
+    L.orc_apply_bc.argtypes = [C.c_void_p, _f64p, _f64p]
+    L.orc_set_bc_values.argtypes = [C.c_void_p, C.c_int, _f64p]
+    L.orc_set_bc_values.restype = C.c_int
+    L.orc_grad_beta_cells.argtypes = [C.c_void_p, _f64p, _f64p, _f64p, _f64p]
+    L.orc_grad_wall_values.argtypes = [C.c_void_p, _f64p, C.c_int, _f64p]
+    L.orc_grad_wall_values.restype = C.c_int
 
 
 def _ip(a):
@@ -117,7 +124,8 @@ class Problem:
     """Single-level problem on a BoxArray with its multigrid hierarchy.
 
     domain: (lo[3], hi[3]) inclusive; boxes: list of (lo[3], hi[3]) inclusive;
-    bc_lo/bc_hi: PERIODIC or DIRICHLET per direction; prob_lo/prob_hi: physical extent.
+    bc_lo/bc_hi: PERIODIC, DIRICHLET or NEUMANN per direction; prob_lo/prob_hi: physical
+    extent.  Walls are homogeneous unless set_bc_values gives them values.
     """
 
     def __init__(self, domain, boxes, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0), prob_hi=(1.0, 1.0, 1.0)):
@@ -260,9 +268,54 @@ class Problem:
         return phi, int(it), hist[:it + 1].copy(), int(status[0])
 
     def apply(self, phi):
+        """A phi with homogeneous walls (linear)."""
         phi = _f64(phi)
         out = np.zeros(self.level_shape(0))
         lib().orc_apply(self.h, _dp(phi), _dp(out))
+        return out
+
+    # wall values ----------------------------------------------------------------
+    def face_shape(self, face):
+        """Shape of face (2*d + side)'s value array: its two tangential axes in increasing
+        order, the lower one fastest (numpy shape (n_t2, n_t1))."""
+        d = face // 2
+        t1, t2 = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
+        lo, hi = self.domain
+        return (hi[t2] - lo[t2] + 1, hi[t1] - lo[t1] + 1)
+
+    def set_bc_values(self, face, values):
+        """Wall values of level-0 face `face` = 2*d + side: phi on the face (Dirichlet) or the
+        outward normal derivative (Neumann); None clears them (g = 0)."""
+        if values is None:
+            st = lib().orc_set_bc_values(self.h, face, None)
+        else:
+            v = _f64(values)
+            if v.shape != self.face_shape(face):
+                raise ValueError(f"face {face}: values of shape {v.shape}, expected {self.face_shape(face)}")
+            st = lib().orc_set_bc_values(self.h, face, _dp(v))
+        if st != 0:
+            raise ValueError(f"face {face} is periodic or out of range")
+
+    def grad_beta(self, phi, lam, beta=None):
+        """dL/dbeta at the cells (dense) from the solution phi (wall values of this problem)
+        and the adjoint lambda; beta: the cell beta of set_coeffs (None: 1)."""
+        out = np.zeros(self.level_shape(0))
+        b = None if beta is None else _f64(beta)
+        lib().orc_grad_beta_cells(self.h, _dp(_f64(phi)), _dp(_f64(lam)), _dp(b), _dp(out))
+        return out
+
+    def grad_wall_values(self, lam, face):
+        """dL/dg on wall face `face` for the adjoint lambda (dense)."""
+        out = np.zeros(self.face_shape(face))
+        if lib().orc_grad_wall_values(self.h, _dp(_f64(lam)), face, _dp(out)) != 0:
+            raise ValueError(f"face {face} is periodic or out of range")
+        return out
+
+    def apply_bc(self, phi):
+        """A phi with the wall values in the ghosts (affine in phi)."""
+        phi = _f64(phi)
+        out = np.zeros(self.level_shape(0))
+        lib().orc_apply_bc(self.h, _dp(phi), _dp(out))
         return out
 
 

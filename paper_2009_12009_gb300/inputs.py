@@ -20,6 +20,7 @@ import numpy as np
 
 PERIODIC = 0
 DIRICHLET = 1
+NEUMANN = 2
 
 SEEDS = {"poisson32": 12010, "abec256": 12011, "abec512": 12012, "batch64": 12013, "amr2": 12014}
 BATCH_EDGES = (32, 48, 64, 96, 128, 160)

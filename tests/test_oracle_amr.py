@@ -13,7 +13,7 @@ import pytest
 
 from paper_2009_12009_gb300 import inputs as I
 
-P_, D_ = I.PERIODIC, I.DIRICHLET
+P_, D_, N_ = I.PERIODIC, I.DIRICHLET, I.NEUMANN
 
 
 def two_level(orc, n=8, patch=(2, 6), bc=P_, nfb=1, L=1.0):
@@ -43,12 +43,13 @@ def rand_coeffs(P, rng, a=0.0, sigma=1.0):
     return bc, bf
 
 
-@pytest.mark.parametrize("nfb", [1, 8])
-def test_constants_and_conservation(orc, nfb):
-    """Periodic, a = 0: constants are in the null space (interpolation weights and the
-    quadratic's weights 8/15 + 2/3 - 1/5 sum to 1) and the operator is conservative,
-    sum of volume x (A x) = 0, which fixes the reflux weights and signs."""
-    P = two_level(orc, nfb=nfb)
+@pytest.mark.parametrize("nfb,bc", [(1, P_), (8, P_), (8, N_)])
+def test_constants_and_conservation(orc, nfb, bc):
+    """Periodic or zero-flux (Neumann) walls, a = 0: constants are in the null space
+    (interpolation weights and the quadratic's weights 8/15 + 2/3 - 1/5 sum to 1) and the
+    operator is conservative, sum of volume x (A x) = 0, which fixes the reflux weights and
+    signs (and, with Neumann walls, the wall rows)."""
+    P = two_level(orc, nfb=nfb, bc=bc)
     rng = np.random.default_rng(1)
     rand_coeffs(P, rng)
     yc, yf = P.apply(np.full(P.coarse_shape, 3.0), np.full(P.fine_shape, 3.0))
@@ -88,7 +89,7 @@ def test_quadratic_exactness(orc):
     assert (sel & np.roll(P.covered, 1, 0)).any()
 
 
-@pytest.mark.parametrize("bc", [P_, D_])
+@pytest.mark.parametrize("bc", [P_, D_, N_])
 def test_transpose(orc, bc):
     P = two_level(orc, bc=bc, nfb=8)
     rng = np.random.default_rng(2)
@@ -121,14 +122,14 @@ def lapack_solve(P, rhs, transpose=False):
     return np.linalg.solve(B, np.concatenate([rhs, [0.0]]))[:n]
 
 
-@pytest.mark.parametrize("bc,nfb", [(P_, 1), (P_, 8), (D_, 8)])
+@pytest.mark.parametrize("bc,nfb", [(P_, 1), (P_, 8), (D_, 8), (N_, 8)])
 def test_mlmg_matches_lapack(orc, bc, nfb):
     P = two_level(orc, bc=bc, nfb=nfb)
     rng = np.random.default_rng(3)
     rand_coeffs(P, rng)
     rc, rf = rng.standard_normal(P.coarse_shape), rng.standard_normal(P.fine_shape)
     rhs = P.pack(rc, rf)
-    if bc == P_:
+    if bc != D_:
         V = P.volumes()
         rhs = rhs - (V @ rhs) / V.sum()
         rc, rf = P.unpack(rhs)
@@ -186,7 +187,7 @@ def adjoint_case(orc, bc, seed=4):
     bc_, bf_ = rand_coeffs(P, rng, sigma=0.5)
     rhs = rng.standard_normal(P.pack(np.zeros(P.coarse_shape), np.zeros(P.fine_shape)).size)
     V = P.volumes()
-    if bc == P_:
+    if bc != D_:
         rhs -= (V @ rhs) / V.sum()
     target = rng.standard_normal(rhs.size)
     return P, rng, bc_, bf_, rhs, target
@@ -199,7 +200,7 @@ def loss(P, rhs, target, tol=1e-13):
     return 0.5 * np.sum((phi - target) ** 2), phi
 
 
-@pytest.mark.parametrize("bc", [P_, D_])
+@pytest.mark.parametrize("bc", [P_, D_, N_])
 def test_adjoint_rhs_gradient_finite_differences(orc, bc):
     """dL/d(rhs) = lambda with A^T lambda = (phi - phi_t) (projected for the periodic case):
     central differences of L = 0.5 ||phi - phi_t||^2 in random rhs directions."""
@@ -210,7 +211,7 @@ def test_adjoint_rhs_gradient_finite_differences(orc, bc):
     lam = lapack_solve(P, g, transpose=True)
     for _ in range(3):
         d = rng.standard_normal(rhs.size)
-        if bc == P_:
+        if bc != D_:
             d -= (V @ d) / V.sum()
         eps = 1e-3
         Lp, _ = loss(P, rhs + eps * d, target)
@@ -219,7 +220,7 @@ def test_adjoint_rhs_gradient_finite_differences(orc, bc):
         assert abs(fd - lam @ d) <= 1e-6 * abs(fd) + 1e-10
 
 
-@pytest.mark.parametrize("bc", [P_, D_])
+@pytest.mark.parametrize("bc", [P_, D_, N_])
 def test_adjoint_beta_gradient_finite_differences(orc, bc):
     """dL/dbeta at cells from the face gradient -(lambda^T dA/dbeta_face phi) through the
     harmonic face mean: central differences of L in random beta directions, coarse and

@@ -11,7 +11,7 @@ import pytest
 
 from paper_2009_12009_gb300 import inputs as I
 
-P_, D_ = I.PERIODIC, I.DIRICHLET
+P_, D_, N_ = I.PERIODIC, I.DIRICHLET, I.NEUMANN
 
 
 def cube(n):
@@ -202,7 +202,7 @@ def test_dense_direct_8cubed(orc, case, boxsz):
 # Sec. "Operations on a level": ghost cells hold the owning box's values
 
 
-@pytest.mark.parametrize("bc", [P_, D_])
+@pytest.mark.parametrize("bc", [P_, D_, N_])
 def test_fill_ghosts_matches_global_array(orc, bc):
     nx, ny, nz = 12, 10, 14
     boxes = I.chop(*dom3(nx, ny, nz), 5)
@@ -229,7 +229,7 @@ def test_fill_ghosts_matches_global_array(orc, bc):
                     want = g[np.ix_(idx[2], idx[1], idx[0])]
                 else:
                     idx[d] = np.array([lo[d] if side == 0 else hi[d]])
-                    want = -g[np.ix_(idx[2], idx[1], idx[0])]
+                    want = (1.0 if bc == N_ else -1.0) * g[np.ix_(idx[2], idx[1], idx[0])]
                 np.testing.assert_array_equal(ghost, want.reshape(ghost.shape))
                 checked += ghost.size
     assert checked > 0
@@ -271,7 +271,7 @@ def test_box_layout_invariance(orc):
 # Operator identities
 
 
-@pytest.mark.parametrize("bc", [P_, D_])
+@pytest.mark.parametrize("bc", [P_, D_, N_])
 def test_operator_symmetric(orc, bc):
     """Flux form with one beta per face and reflected Dirichlet ghosts gives a symmetric
     matrix: <Ax, y> = <x, Ay>.  A beta read from the wrong face breaks this."""
@@ -354,7 +354,7 @@ def test_positive_definite_dirichlet(orc):
 # Red-black Gauss-Seidel
 
 
-@pytest.mark.parametrize("bc", [P_, D_])
+@pytest.mark.parametrize("bc", [P_, D_, N_])
 def test_gauss_seidel_zeroes_colour_residual(orc, bc):
     """After one colour, every updated cell satisfies its own row of A phi = rhs (its
     neighbours have the other colour and did not move); the other colour is untouched."""
