@@ -60,8 +60,15 @@ typedef enum {
   GMG_ERR_STATE = -7           /* call out of order (e.g. solve before coefficients) */
 } gmg_status;
 
-/* Boundary condition of one domain side (Sec. "Basic data structures": BCRec). */
-typedef enum { GMG_BC_PERIODIC = 0, GMG_BC_DIRICHLET0 = 1 } gmg_bc;
+/* Boundary condition of one domain side (Sec. "Basic data structures": BCRec; Sec.
+   "Linear Solvers": the operator equation's boundary conditions).  Walls are homogeneous
+   inside the solver: a Dirichlet ghost is minus the adjacent interior value (phi = 0 on the
+   face), a Neumann ghost equals it (zero normal derivative); the face beta of a wall is the
+   interior cell's.  Nonzero wall values (phi = g on a Dirichlet face, outward normal
+   derivative g on a Neumann face) enter through gmg_wall_values_rhs.  A problem without a
+   Dirichlet wall and with a = 0 is singular (constants in the null space).
+   GMG_BC_DIRICHLET0 is the older name of GMG_BC_DIRICHLET. */
+typedef enum { GMG_BC_PERIODIC = 0, GMG_BC_DIRICHLET = 1, GMG_BC_DIRICHLET0 = 1, GMG_BC_NEUMANN = 2 } gmg_bc;
 
 /* Arithmetic of the V-cycle.  FP64: everything in double.  MIXED_FP32: the V-cycle
    (smoothing, residual, restriction, interpolation) runs in float inside an FP64
@@ -80,7 +87,7 @@ typedef struct {
   int bottom_max_iter;  /* BiCGStab iterations, default 200 */
   double bottom_tol;    /* BiCGStab relative L-inf tolerance, default 1e-4 */
   int precision;        /* gmg_precision, default GMG_FP64 */
-  int project_mean;     /* singular (all periodic, a = 0): project a nonzero-mean rhs
+  int project_mean;     /* singular (no Dirichlet wall, a = 0): project a nonzero-mean rhs
                            instead of returning GMG_ERR_BAD_INPUT; default 0 */
   int use_graph;        /* replay the V-cycle as a captured CUDA graph, default 1 */
   int profile;          /* record CUDA events around every finest-level smoother and
@@ -276,7 +283,7 @@ gmg_status gmg_apply_transpose(gmg_ctx* ctx, void* const* out, void* const* y);
 /* Adjoint solve A^T lambda = g (FP64), so that lambda = dL/d(rhs) for a loss L(phi) with
    dL/dphi = g.  One level: a forward solve (A symmetric).  Two levels: BiCGStab on A^T,
    right-preconditioned by the composite multigrid correction of A, to ||g - A^T lambda||_inf
-   <= tol_rel ||g||_inf (max_iter Krylov iterations).  Singular problems (all periodic,
+   <= tol_rel ||g||_inf (max_iter Krylov iterations).  Singular problems (no Dirichlet wall,
    a = 0): g is projected onto the range of A^T (g - V sum(g)/sum(V), V the cell volumes;
    one level: g minus its mean) and lambda returned with zero sum.  lambda, g as in
    gmg_solve; covered coarse entries of g are ignored and those of lambda are 0. */
@@ -293,13 +300,47 @@ gmg_status gmg_solve_adjoint(gmg_ctx* ctx, void* const* lambda, const void* cons
    lambda's ghosts are overwritten. */
 gmg_status gmg_beta_grad(gmg_ctx* ctx, void* const* dbeta, void* const* phi, void* const* lambda);
 
+/* ------------------------------------------------------------- wall values */
+/* Nonzero values on the level-0 walls of a single-level, single-problem context.  A wall
+   value g makes the wall's ghost rule affine -- Dirichlet: ghost = 2g - interior (the line
+   through the interior value and g on the face); Neumann: ghost = interior + h g (h the cell
+   size normal to the face) -- and its phi-independent part is a constant of the operator:
+   A_g phi = A_0 phi + A_g(0).  Solving A_0 phi = rhs - A_g(0) (gmg_solve, homogeneous walls)
+   gives the solution with the wall values; the stopping test is then relative to
+   ||rhs - A_g(0)||_inf, the initial residual.
+
+   values[f], f = 2*d + side (x-, x+, y-, y+, z-, z+): FP64 device array over face f's two
+   tangential axes in increasing order, the lower one fastest (n_t1 * n_t2 values; for a
+   face normal to y: x fastest, then z), or NULL for g = 0.  A periodic face must be NULL;
+   a context with several problems or two levels accepts only NULLs (GMG_ERR_BAD_INPUT).
+   All work is enqueued on the context stream; nothing is synchronised. */
+
+/* out = rhs - A_g(0): rhs plus, in each cell next to a wall face with a value, 2 w g
+   (Dirichlet) or w h g (Neumann), w = b beta_face / h^2 the face's weight; faces are added
+   in the order x-, x+, y-, y+, z-, z+.  rhs, out: FP64 level-0 boxed device arrays; out may
+   equal rhs (in place); otherwise rhs is copied first. */
+gmg_status gmg_wall_values_rhs(gmg_ctx* ctx, void* out, const void* rhs, const void* const* values);
+
+/* The transpose of the map g -> rhs - A_g(0): dvalues[f][t] = c * lambda[q] for the wall
+   cell q behind face position t, c = 2 w (Dirichlet) or w h (Neumann); with lambda the
+   adjoint (gmg_solve_adjoint of dL/dphi) this is dL/dg.  dvalues[f]: FP64 device arrays in
+   the layout of values above, written whole; NULL entries are skipped. */
+gmg_status gmg_wall_values_grad(gmg_ctx* ctx, const void* lambda, void* const* dvalues);
+
+/* gmg_beta_grad for a solution with wall values: phi's wall ghosts take the affine rule
+   (values as above, NULL entries g = 0) before the face terms, so a wall face adds
+   lambda_q w (ghost - phi_q) / beta_face to its cell.  values == NULL: gmg_beta_grad. */
+gmg_status gmg_beta_grad_walls(gmg_ctx* ctx, void* const* dbeta, void* const* phi, void* const* lambda,
+                               const void* const* values);
+
 /* ------------------------------------------------ individual hot-path steps */
 /* Each step acts on MG level m with caller buffers of element type dt in that level's
    boxed layout.  Coefficients come from the last gmg_set_bcoef_* call (float copies
    for GMG_DT_F32 / GMG_DT_BF16 fields need a mixed-precision workspace). */
 
 /* FillBoundary: copy every face ghost cell from the box that owns it (periodic images
-   included) or apply the homogeneous Dirichlet reflection.  colour = 0 or 1 fills only
+   included) or apply the homogeneous wall rule (Dirichlet: minus, Neumann: plus the
+   adjacent interior value).  colour = 0 or 1 fills only
    the ghosts whose global (i+j+k) parity is that colour; -1 fills all. */
 gmg_status gmg_fill_boundary(gmg_ctx* ctx, int m, int dt, void* field, int colour);
 
@@ -401,8 +442,8 @@ gmg_status gmg_batch_solve(gmg_ctx* ctx, void* phi, const void* rhs, double tol_
      wy: nx*(ny+1)*nz, face j-1/2 at i + nx*(j + (ny+1)*k);
      wz: nx*ny*(nz+1), face k-1/2 at i + nx*(j + ny*k);
      diag, rhs, x: nx*ny*nz.  All device pointers; x is written.
-   bc_lo/bc_hi: GMG_BC_PERIODIC (both sides; wraps inside the box) or GMG_BC_DIRICHLET0
-   (ghost = minus the adjacent cell).  singular != 0 projects rhs and x onto zero mean.
+   bc_lo/bc_hi: GMG_BC_PERIODIC (both sides; wraps inside the box), GMG_BC_DIRICHLET
+   (ghost = minus the adjacent cell) or GMG_BC_NEUMANN (ghost = the adjacent cell).  singular != 0 projects rhs and x onto zero mean.
    iters: device int receiving the iteration count, or NULL.
 
    Limit: (nx+2)(ny+2)(nz+2) <= 65536; larger boxes return GMG_ERR_BAD_INPUT.  The static

@@ -4,10 +4,11 @@ Forward:  phi = A(beta)^-1 rhs by the multigrid solve (one level, or the two-lev
           composite form of Sec. "Operations between levels").
 Backward: lambda = A^-T dL/dphi by the adjoint solve (gmg_solve_adjoint), then
           dL/drhs = lambda and dL/dbeta = -lambda^T (dA/dbeta) phi by the face-flux gradient
-          kernel (gmg_beta_grad), through the harmonic face mean to the cell beta.
+          kernel (gmg_beta_grad), through the harmonic face mean to the cell beta; with
+          wall values g (one level), dL/dg = lambda^T d(rhs - A_g 0)/dg (gmg_wall_values_grad).
 Both run in the library's kernels; this module only marshals tensors.
 
-Singular problems (all periodic, a = 0): the forward projects rhs onto the operator's range
+Singular problems (no Dirichlet wall, a = 0): the forward projects rhs onto the operator's range
 and returns phi with zero (volume-weighted) mean; the backward projects accordingly, so the
 gradients are those of that projected map.  Two levels: phi on coarse cells under the fine
 level is returned as 0 (those cells are not unknowns of the composite problem), and the
@@ -72,14 +73,17 @@ class AmrSolve:
 
 class _Solve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, solver, rhs, beta):
+    def forward(ctx, solver, rhs, beta, *walls):
         C = solver.ctx
         C.set_beta(beta.detach())
-        phi, info = C.solve(C.pack(rhs.detach()), tol_rel=solver.tol, max_iter=solver.max_iter, project_mean=1)
+        wv = None if all(w is None for w in walls) else [None if w is None else w.detach() for w in walls]
+        phi, info = C.solve(C.pack(rhs.detach()), tol_rel=solver.tol, max_iter=solver.max_iter, project_mean=1,
+                            wall_values=wv)
         if info.status != gmg.OK:
             raise gmg.GmgError(info.status, "forward solve did not converge")
         ctx.solver = solver
         ctx.phi = phi
+        ctx.wv = wv
         return C.unpack(phi)
 
     @staticmethod
@@ -89,22 +93,42 @@ class _Solve(torch.autograd.Function):
         lam, info = C.solve_adjoint(C.pack(g.contiguous()), tol_rel=solver.tol, max_iter=solver.max_iter)
         if info.status != gmg.OK:
             raise gmg.GmgError(info.status, "adjoint solve did not converge")
-        d = C.beta_grad(ctx.phi, lam)
-        return None, C.unpack(lam), C.unpack(d)
+        d = C.beta_grad(ctx.phi, lam, wall_values=ctx.wv)
+        dwalls = [None] * 6
+        if ctx.wv is not None:
+            faces = [f for f in range(6) if ctx.wv[f] is not None and ctx.needs_input_grad[3 + f]]
+            if faces:
+                got = C.wall_values_grad(lam, faces)
+                for f in faces:
+                    dwalls[f] = got[f]
+        return (None, C.unpack(lam), C.unpack(d), *dwalls)
+
+
+_BC = {"periodic": gmg.PERIODIC, "dirichlet": gmg.DIRICHLET, "neumann": gmg.NEUMANN}
 
 
 class Solve:
-    """phi = Solve(...)(rhs, beta) on one level, differentiable in rhs and beta."""
+    """phi = Solve(...)(rhs, beta, wall_values) on one level, differentiable in rhs, beta and
+    the wall values.  bc: "periodic", "dirichlet" or "neumann" on every side, or a pair of
+    per-axis lists (bc_lo, bc_hi) of those names or codes.  wall_values: None, or a dict
+    face -> (n_t2, n_t1) tensor (face = 2*d + side; see gmg.Context.face_shape)."""
 
     def __init__(self, shape_xyz, bc="dirichlet", max_grid_size=64, prob_hi=(1.0, 1.0, 1.0), a=0.0, b=1.0,
                  tol=1e-10, max_iter=100):
         nx, ny, nz = shape_xyz
-        bcv = gmg.PERIODIC if bc == "periodic" else gmg.DIRICHLET0
-        self.ctx = gmg.Context(((0, 0, 0), (nx - 1, ny - 1, nz - 1)), [bcv] * 3, [bcv] * 3, prob_hi=prob_hi,
+        if isinstance(bc, str):
+            lo = hi = [_BC[bc]] * 3
+        else:
+            lo, hi = ([_BC[v] if isinstance(v, str) else int(v) for v in side] for side in bc)
+        self.ctx = gmg.Context(((0, 0, 0), (nx - 1, ny - 1, nz - 1)), lo, hi, prob_hi=prob_hi,
                                max_grid_size=max_grid_size, stream=torch.cuda.current_stream().cuda_stream)
         self.ctx.allocate(gmg.FP64)
         self.ctx.set_scalars(a, b)
         self.tol, self.max_iter = tol, max_iter
 
-    def __call__(self, rhs, beta):
-        return _Solve.apply(self, rhs, beta)
+    def __call__(self, rhs, beta, wall_values=None):
+        walls = [None] * 6
+        if wall_values is not None:
+            for f, v in wall_values.items():
+                walls[f] = v
+        return _Solve.apply(self, rhs, beta, *walls)

@@ -122,7 +122,8 @@ __device__ __forceinline__ int64_t ax_stride(const DevBox& B, int d) {
 // dL/dbeta_face = -lambda^T (dA/dbeta_face) phi, through the face rule that made the face
 // beta (harmonic mean of two cells of the level; the one adjacent cell at a wall or at a
 // coarse/fine face).  Ghosts of phi, lambda and beta must be filled; C/F ghosts of phi hold
-// the interpolated values.  cfidx (fine level): per element, the C/F ghost index or -1.
+// the interpolated values; wall ghosts of phi hold the wall rule (with the wall values, if
+// any), so a wall face contributes lambda_q w (phi_ghost - phi_q) to its one row.  cfidx (fine level): per element, the C/F ghost index or -1.
 // covered (coarse level): per element, 1 if covered.  lamc: coarse lambda (fine level: the
 // coarse cell of a C/F ghost takes the reflux part).
 __global__ void __launch_bounds__(AT)
@@ -155,8 +156,8 @@ __global__ void __launch_bounds__(AT)
       const int gface = B.lo[d] + loc[d] + side;  // global index of the face
       const bool wall = (side == 0 && G.wall_lo[d] && gface == G.dlo[d]) ||
                         (side == 1 && G.wall_hi[d] && gface == G.dhi[d] + 1);
-      if (wall) {  // row q: w (phi_q - phi_g), phi_g = -phi_q
-        acc += -lq * ih2 * 2.0 * pq;
+      if (wall) {  // one row: q's, with w (phi_q - phi_g); beta_face = beta_q
+        acc += lq * ih2 * (phi[nq] - pq);
         continue;
       }
       if (ghost && cfidx && cfidx[nq] >= 0) {  // fine coarse/fine face: fine row + reflux row

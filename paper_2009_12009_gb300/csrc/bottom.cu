@@ -2,7 +2,7 @@
 // solver): unpreconditioned BiCGStab (van der Vorst 1992) in FP64, x0 = 0, one thread
 // block per bottom problem running the whole iteration on the device (no host round
 // trip per iteration).  Stops at ||r||_inf <= tol * ||r0||_inf, after maxit iterations,
-// or on breakdown.  Singular problems (all periodic, a = 0) project the right-hand side
+// or on breakdown.  Singular problems (no Dirichlet wall, a = 0) project the right-hand side
 // and the result onto zero mean.  Dot products are reduced in a fixed order, so the
 // result is deterministic.
 #include <cuda_bf16.h>

@@ -181,7 +181,8 @@ cudaEvent_t* ev_pair(std::vector<cudaEvent_t>& v, int k) {
   return &v[2 * k];
 }
 
-bool singular(const gmg_ctx* c, int s) { return c->geoms[s].all_periodic() && c->a == 0.0; }
+// no Dirichlet wall and a = 0: the constants span the null space of A
+bool singular(const gmg_ctx* c, int s) { return !c->geoms[s].has_dirichlet() && c->a == 0.0; }
 bool any_singular(const gmg_ctx* c) {
   for (int s = 0; s < c->ns(); ++s)
     if (singular(c, s)) return true;
@@ -418,8 +419,8 @@ std::vector<DevGeom> dev_geoms(const LevelMeta& M) {
     for (int d = 0; d < 3; ++d) {
       g[s].dlo[d] = G.domain.lo[d];
       g[s].dhi[d] = G.domain.hi[d];
-      g[s].wall_lo[d] = G.bclo[d] != 0;
-      g[s].wall_hi[d] = G.bchi[d] != 0;
+      g[s].wall_lo[d] = G.bclo[d];  // the boundary codes: 0 periodic, 1 Dirichlet, 2 Neumann
+      g[s].wall_hi[d] = G.bchi[d];
       g[s].ih2[d] = 1.0 / (G.h[d] * G.h[d]);
     }
   }
@@ -1435,8 +1436,7 @@ gmg_status set_domain_geom(gmg_ctx* c, SolveGeom& G, const int lo[3], const int 
   for (int d = 0; d < 3; ++d) {
     if (hi[d] < lo[d]) SETERR(c, GMG_ERR_BAD_INPUT, "empty domain");
     if (!(phi[d] > plo[d])) SETERR(c, GMG_ERR_BAD_INPUT, "prob_hi must exceed prob_lo");
-    if ((bclo[d] != GMG_BC_PERIODIC && bclo[d] != GMG_BC_DIRICHLET0) ||
-        (bchi[d] != GMG_BC_PERIODIC && bchi[d] != GMG_BC_DIRICHLET0))
+    if (bclo[d] < GMG_BC_PERIODIC || bclo[d] > GMG_BC_NEUMANN || bchi[d] < GMG_BC_PERIODIC || bchi[d] > GMG_BC_NEUMANN)
       SETERR(c, GMG_ERR_BAD_INPUT, "unknown boundary condition");
     if ((bclo[d] == GMG_BC_PERIODIC) != (bchi[d] == GMG_BC_PERIODIC))
       SETERR(c, GMG_ERR_BAD_INPUT, "a periodic direction must be periodic on both sides");
@@ -1472,6 +1472,42 @@ double time_reps(gmg_ctx* c, int reps, F body) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   return (double)ms / reps;
+}
+
+// Wall values are for single-level contexts holding one problem; a periodic face takes none.
+gmg_status wall_values_check(gmg_ctx* c, const void* const* values) {
+  bool any = false;
+  for (int f = 0; f < 6; ++f) any |= values[f] != nullptr;
+  if (!any) return GMG_OK;
+  if (c->amr || c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "wall values: single-level, single-problem contexts only");
+  const SolveGeom& G = c->geoms[0];
+  for (int f = 0; f < 6; ++f) {
+    const int d = f / 2, bc = f % 2 ? G.bchi[d] : G.bclo[d];
+    if (values[f] && bc == GMG_BC_PERIODIC)
+      SETERR(c, GMG_ERR_BAD_INPUT, "wall values given for periodic face " + std::to_string(f));
+  }
+  if (c->L[0].boxes.size() > 65535u) SETERR(c, GMG_ERR_BAD_INPUT, "wall values: more than 65535 level-0 boxes");
+  return GMG_OK;
+}
+
+// One k_wall_values launch per face with values, in face order (walls.cu).
+gmg_status wall_values_pass(gmg_ctx* c, const void* const* values, int mode, double* f, const double* lam,
+                            void* const* dg) {
+  const LevelMeta& M = c->L[0];
+  const SolveGeom& G = c->geoms[0];
+  const Coefs k = coefs64(c, 0);
+  const double* w[3] = {(const double*)k.wx, (const double*)k.wy, (const double*)k.wz};
+  for (int face = 0; face < 6; ++face) {
+    if (!values[face]) continue;
+    const int d = face / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const int kind = face % 2 ? G.bchi[d] : G.bclo[d];
+    int maxf = 0;
+    for (const Box& B : M.boxes) maxf = std::max(maxf, B.n(t1) * B.n(t2));
+    launch_wall_values(c->dev[0], (int)M.boxes.size(), maxf, face, kind, G.h[d], w[d], (const double*)values[face],
+                       mode, f, lam, mode == 2 ? (double*)dg[face] : nullptr, c->stream);
+  }
+  CK(c, cudaGetLastError());
+  return GMG_OK;
 }
 
 }  // namespace
@@ -2178,11 +2214,17 @@ gmg_status gmg_solve_adjoint(gmg_ctx* c, void* const* lambda, const void* const*
 }
 
 gmg_status gmg_beta_grad(gmg_ctx* c, void* const* dbeta, void* const* phi, void* const* lambda) {
+  return gmg_beta_grad_walls(c, dbeta, phi, lambda, nullptr);
+}
+
+gmg_status gmg_beta_grad_walls(gmg_ctx* c, void* const* dbeta, void* const* phi, void* const* lambda,
+                               const void* const* values) {
   if (!c || !dbeta || !phi || !lambda || !dbeta[0] || !phi[0] || !lambda[0]) return GMG_ERR_BAD_INPUT;
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
   if ((st = build_coefs(c))) return st;
   if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "beta gradient: single-problem contexts only");
+  if (values && (st = wall_values_check(c, values))) return st;
   cudaStream_t s = c->stream;
   double* pc = (double*)phi[0];
   double* lc = (double*)lambda[0];
@@ -2202,11 +2244,32 @@ gmg_status gmg_beta_grad(gmg_ctx* c, void* const* dbeta, void* const* phi, void*
   } else {
     launch_fill(DT_F64, c->dev[0], pc, -1, 0, s);
     launch_fill(DT_F64, c->dev[0], lc, -1, 0, s);
+    if (values && (st = wall_values_pass(c, values, 1, pc, nullptr, nullptr))) return st;
     launch_grad_beta(c->dev[0], pc, lc, c->betac_cell, c->b, nullptr, nullptr, nullptr, 0.5, nullptr,
                      (double*)dbeta[0], s);
   }
   CK(c, cudaGetLastError());
   return GMG_OK;
+}
+
+gmg_status gmg_wall_values_rhs(gmg_ctx* c, void* out, const void* rhs, const void* const* values) {
+  if (!c || !out || !rhs || !values) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if ((st = build_coefs(c))) return st;
+  if ((st = wall_values_check(c, values))) return st;
+  if (out != rhs)
+    CK(c, cudaMemcpyAsync(out, rhs, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, c->stream));
+  return wall_values_pass(c, values, 0, (double*)out, nullptr, nullptr);
+}
+
+gmg_status gmg_wall_values_grad(gmg_ctx* c, const void* lambda, void* const* dvalues) {
+  if (!c || !lambda || !dvalues) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, 0, DT_F64);
+  if (st) return st;
+  if ((st = build_coefs(c))) return st;
+  if ((st = wall_values_check(c, (const void* const*)dvalues))) return st;
+  return wall_values_pass(c, (const void* const*)dvalues, 2, nullptr, (const double*)lambda, dvalues);
 }
 
 }  // extern "C"

@@ -55,7 +55,7 @@ struct GhostRect {
   int src[3];    // local coordinates (in src_box) of its source cell
   int d1, d2;    // tangential axes iterated by u (fastest) and v
   int n1, n2;    // extents along d1, d2
-  int sign;      // +1: copy; -1: homogeneous Dirichlet reflection
+  int sign;      // +1: copy (or homogeneous Neumann mirror); -1: homogeneous Dirichlet reflection
   int par0;      // global (i+j+k) parity of the first ghost cell
   int kind;      // 0: copy from a box of the same level (periodic images included); 1: wall
 };

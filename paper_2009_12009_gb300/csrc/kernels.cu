@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(BLOCK) k_acoef(const DevBox* __restrict__ boxe
 }
 
 // Face beta from cell beta (Sec. "Linear Solvers": beta on faces): harmonic mean of the
-// two cells; on a Dirichlet wall face the interior cell's value.  Each thread writes the
+// two cells; on a wall face (Dirichlet or Neumann) the interior cell's value.  Each thread writes the
 // low face of its cell in every direction and, for the last cell of a row/column, the
 // high face too.  The ghosts of beta must hold the neighbouring boxes' values.
 __global__ void __launch_bounds__(BLOCK)

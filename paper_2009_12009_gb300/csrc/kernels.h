@@ -10,7 +10,7 @@ namespace gmg {
 // Per-solve geometry of one level, as the coefficient kernels see it.
 struct DevGeom {
   int dlo[3], dhi[3];
-  int wall_lo[3], wall_hi[3];  // 1: homogeneous Dirichlet wall on that side
+  int wall_lo[3], wall_hi[3];  // wall on that side: 0 none (periodic), 1 Dirichlet, 2 Neumann
   double ih2[3];               // 1 / h_d^2
 };
 
@@ -193,5 +193,12 @@ struct TailLevelBufs {
   const void *wx = nullptr, *wy = nullptr, *wz = nullptr, *D = nullptr, *invD = nullptr;
 };
 void launch_vtail(int dt, int nblocks, const TailArgs& a, const TailLevelBufs* lv, int nlev, cudaStream_t s);
+
+// Wall values on level 0 (walls.cu), one launch per face: mode 0 f[q] += c g, mode 1
+// f[ghost] += (2 or h) g, mode 2 dg = c lam[q]; c = 2 w (kind 1, Dirichlet) or w h (kind 2,
+// Neumann), w the FP64 face weight array of the face's direction.
+void launch_wall_values(const LevelDev& L, int nboxes, int max_face_cells, int face, int kind, double h,
+                        const double* w, const double* g, int mode, double* f, const double* lam, double* dg,
+                        cudaStream_t s);
 
 }  // namespace gmg

@@ -66,8 +66,9 @@ std::vector<Box> chop(const Box& dom, int mgs) {
 
 // Face ghost rectangles of every box (Sec. "Operations on a level").  For each face slab
 // of each box, the slab is intersected with every box of the same solve (and with its
-// periodic images along the face normal); the part outside a Dirichlet wall becomes a
-// reflection rectangle.  Edge and corner ghosts are not needed by the 7-point stencil.
+// periodic images along the face normal); the part outside a wall becomes a reflection
+// rectangle: minus the adjacent interior value at a Dirichlet wall, plus it at a Neumann
+// wall (the homogeneous wall rules; wall values enter the right-hand side).  Edge and corner ghosts are not needed by the 7-point stencil.
 static std::string build_ghosts(LevelMeta& L) {
   L.ghosts.clear();
   L.cf_slabs.clear();
@@ -95,7 +96,7 @@ static std::string build_ghosts(LevelMeta& L) {
           r.src[d] = side ? B.n(d) - 1 : 0;
           r.d1 = d1; r.d2 = d2;
           r.n1 = B.n(d1); r.n2 = B.n(d2);
-          r.sign = -1;
+          r.sign = bc == 2 ? 1 : -1;
           r.par0 = pmod2(B.lo[0] + B.lo[1] + B.lo[2] + r.dst[0] + r.dst[1] + r.dst[2]);
           r.kind = 1;
           L.ghosts.push_back(r);

@@ -30,6 +30,11 @@ struct SolveGeom {
   int bchi[3] = {0, 0, 0};
   bool periodic(int d) const { return bclo[d] == 0; }
   bool all_periodic() const { return bclo[0] == 0 && bclo[1] == 0 && bclo[2] == 0; }
+  bool has_dirichlet() const {
+    for (int d = 0; d < 3; ++d)
+      if (bclo[d] == 1 || bchi[d] == 1) return true;
+    return false;
+  }
 };
 
 // One multigrid level of one or several independent problems.

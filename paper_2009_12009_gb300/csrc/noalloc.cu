@@ -31,7 +31,8 @@ static __device__ __align__(256) double g_noalloc_scratch[7 * NOALLOC_MAX_ELEMS]
 
 struct NBox {
   int nx, ny, nz;
-  int per[3];      // 1: periodic along d (wrap inside the box); 0: homogeneous Dirichlet
+  int per[3];      // 1: periodic along d (wrap inside the box); 0: walls
+  double wsign[3][2];  // wall ghost = wsign * adjacent cell: -1 homogeneous Dirichlet, +1 homogeneous Neumann
   int ncell;
   int64_t sx, sy;  // ghosted strides
 };
@@ -74,7 +75,7 @@ __device__ __forceinline__ void cell_ijk(const NBox& b, int c, int& i, int& j, i
   k = c / (b.nx * b.ny);
 }
 
-// face ghosts of `in`: periodic wrap inside the box, or minus the adjacent cell
+// face ghosts of `in`: periodic wrap inside the box, or the wall rule on the adjacent cell
 __device__ void nfill(const NBox& b, double* in) {
   const int n[3] = {b.nx, b.ny, b.nz};
   for (int d = 0; d < 3; ++d) {
@@ -88,7 +89,7 @@ __device__ void nfill(const NBox& b, double* in) {
       g[d] = side ? n[d] : -1;
       double sign;
       if (b.per[d]) { s[d] = side ? 0 : n[d] - 1; sign = 1.0; }
-      else { s[d] = side ? n[d] - 1 : 0; sign = -1.0; }
+      else { s[d] = side ? n[d] - 1 : 0; sign = b.wsign[d][side]; }
       in[gq(b, g[0], g[1], g[2])] = sign * in[gq(b, s[0], s[1], s[2])];
     }
   }
@@ -295,11 +296,14 @@ extern "C" gmg_status gmg_box_bicgstab_noalloc(void* stream, int nx, int ny, int
   b.nx = nx; b.ny = ny; b.nz = nz;
   for (int d = 0; d < 3; ++d) {
     const bool pl = bc_lo[d] == GMG_BC_PERIODIC, ph = bc_hi[d] == GMG_BC_PERIODIC;
-    if (pl != ph || (!pl && bc_lo[d] != GMG_BC_DIRICHLET0) || (!ph && bc_hi[d] != GMG_BC_DIRICHLET0)) {
+    if (pl != ph || bc_lo[d] < GMG_BC_PERIODIC || bc_lo[d] > GMG_BC_NEUMANN || bc_hi[d] < GMG_BC_PERIODIC ||
+        bc_hi[d] > GMG_BC_NEUMANN) {
       set_thread_error("gmg_box_bicgstab_noalloc: bad boundary conditions");
       return GMG_ERR_BAD_INPUT;
     }
     b.per[d] = pl ? 1 : 0;
+    b.wsign[d][0] = bc_lo[d] == GMG_BC_NEUMANN ? 1.0 : -1.0;
+    b.wsign[d][1] = bc_hi[d] == GMG_BC_NEUMANN ? 1.0 : -1.0;
   }
   b.ncell = nx * ny * nz;
   b.sx = nx + 2;

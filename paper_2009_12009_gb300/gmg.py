@@ -14,7 +14,8 @@ import numpy as np
 from . import build as _build
 
 OK, BAD_INPUT, NOT_CONVERGED, DIVERGED, CUDA_ERR, DEVICE_TIMEOUT, NO_WORKSPACE, STATE = 0, -1, -2, -3, -4, -5, -6, -7
-PERIODIC, DIRICHLET0 = 0, 1
+PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
+DIRICHLET0 = DIRICHLET
 FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 GX = 8  # first valid cell of a row sits at element GX (16-byte aligned for every type)
@@ -31,6 +32,7 @@ EXPORTS = [
     "gmg_box_bicgstab_noalloc", "gmg_define_batch", "gmg_num_solves", "gmg_solve_boxes", "gmg_pack_solve",
     "gmg_unpack_solve", "gmg_batch_solve", "gmg_amr_level_boxes", "gmg_pack_amr", "gmg_unpack_amr",
     "gmg_apply_transpose", "gmg_solve_adjoint", "gmg_beta_grad", "gmg_autotune", "gmg_tuned",
+    "gmg_wall_values_rhs", "gmg_wall_values_grad", "gmg_beta_grad_walls",
 ]
 
 
@@ -123,6 +125,10 @@ def _declare(L):
         "gmg_solve_adjoint": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_double, C.POINTER(Params),
                               C.POINTER(SolveInfo)],
         "gmg_beta_grad": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)],
+        "gmg_wall_values_rhs": [vp, vp, vp, C.POINTER(C.c_void_p)],
+        "gmg_wall_values_grad": [vp, vp, C.POINTER(C.c_void_p)],
+        "gmg_beta_grad_walls": [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                C.POINTER(C.c_void_p)],
         "gmg_autotune": [vp, C.c_int, vp, C.POINTER(Params)],
         "gmg_tuned": [vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                       C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)],
@@ -304,8 +310,11 @@ class Context:
         return wx, wy, wz, d
 
     # ---- solve ------------------------------------------------------------------------
-    def solve(self, rhs, phi=None, tol_rel=1e-10, tol_abs=0.0, raise_on_error=True, **params):
-        """rhs, phi: FP64 boxed-layout tensors of level 0.  Returns (phi, info)."""
+    def solve(self, rhs, phi=None, tol_rel=1e-10, tol_abs=0.0, raise_on_error=True, wall_values=None, **params):
+        """rhs, phi: FP64 boxed-layout tensors of level 0.  wall_values: nonzero wall values
+        (see wall_values_rhs), folded into a copy of rhs first.  Returns (phi, info)."""
+        if wall_values is not None:
+            rhs = self.wall_values_rhs(rhs, wall_values)
         phi = self.field(0) if phi is None else phi
         p = default_params(**params)
         info = SolveInfo()
@@ -332,10 +341,58 @@ class Context:
             self._check(st)
         return lam, info
 
-    def beta_grad(self, phi, lam):
+    def beta_grad(self, phi, lam, wall_values=None):
         d = self.field(0)
-        self._check(self.L.gmg_beta_grad(self.h, _pp(d), _pp(phi), _pp(lam)))
+        if wall_values is None:
+            self._check(self.L.gmg_beta_grad(self.h, _pp(d), _pp(phi), _pp(lam)))
+        else:
+            arr, keep = self._wall_ptrs(wall_values)
+            self._check(self.L.gmg_beta_grad_walls(self.h, _pp(d), _pp(phi), _pp(lam), arr))
         return d
+
+    # ---- wall values ----------------------------------------------------------------
+    def face_shape(self, face):
+        """Shape (n_t2, n_t1) of face `face` (= 2*d + side)'s value array: its tangential axes
+        in increasing order, the lower one fastest."""
+        d = face // 2
+        t1, t2 = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
+        lo, hi = self.domain
+        return (hi[t2] - lo[t2] + 1, hi[t1] - lo[t1] + 1)
+
+    def _wall_ptrs(self, values):
+        """values: dict face -> array, or a sequence of 6 (None: g = 0).  Returns the pointer
+        array and the FP64 device tensors it points into."""
+        import torch
+        arr = (C.c_void_p * 6)()
+        keep = []
+        for f in range(6):
+            v = values.get(f) if isinstance(values, dict) else values[f]
+            if v is None:
+                continue
+            t = torch.as_tensor(v, dtype=torch.float64, device="cuda").contiguous()
+            if tuple(t.shape) != self.face_shape(f):
+                raise ValueError(f"face {f}: values of shape {tuple(t.shape)}, expected {self.face_shape(f)}")
+            arr[f] = t.data_ptr()
+            keep.append(t)
+        return arr, keep
+
+    def wall_values_rhs(self, rhs, values, out=None):
+        """rhs - A_g(0): rhs with the flux the wall values drive into the wall cells."""
+        out = self.field(0) if out is None else out
+        arr, keep = self._wall_ptrs(values)
+        self._check(self.L.gmg_wall_values_rhs(self.h, _ptr(out), _ptr(rhs), arr))
+        return out
+
+    def wall_values_grad(self, lam, faces):
+        """dL/dg on the given faces for the adjoint lam: {face: (n_t2, n_t1) tensor}."""
+        import torch
+        arr = (C.c_void_p * 6)()
+        out = {}
+        for f in faces:
+            out[f] = torch.zeros(self.face_shape(f), dtype=torch.float64, device="cuda")
+            arr[f] = out[f].data_ptr()
+        self._check(self.L.gmg_wall_values_grad(self.h, _ptr(lam), arr))
+        return out
 
     # ---- individual steps ----------------------------------------------------------------
     def fill_boundary(self, f, m=0, dt=DT_F64, colour=-1):

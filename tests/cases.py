@@ -9,7 +9,7 @@ import numpy as np
 
 from paper_2009_12009_gb300 import inputs as I
 
-P_, D_ = I.PERIODIC, I.DIRICHLET
+P_, D_, N_ = I.PERIODIC, I.DIRICHLET, I.NEUMANN
 
 
 def dom3(nx, ny, nz):
@@ -42,6 +42,14 @@ def make(name):
         n = (64, 64, 64)
         bc_lo = bc_hi = [D_] * 3
         a, b, mgs = 0.0, 1.0, 16
+    elif name == "neumann":  # singular: zero-flux walls everywhere, a = 0; tails of 4
+        n = (20, 16, 12)
+        bc_lo = bc_hi = [N_] * 3
+        a, b, mgs = 0.0, 1.0, 8
+    elif name == "mixedwalls":  # Neumann/Dirichlet per side, y periodic, a*alpha term, anisotropic h
+        n = (24, 16, 20)
+        bc_lo, bc_hi = [N_, P_, D_], [D_, P_, N_]
+        a, b, mgs = 0.5, 1.3, 6
     else:
         raise KeyError(name)
     shape = (n[2], n[1], n[0])
@@ -49,12 +57,13 @@ def make(name):
     beta = I.lognormal_beta(rng, shape, periodic=(bc_lo[0] == P_ and bc_lo[1] == P_))
     alpha = np.exp(rng.standard_normal(shape)) if a != 0.0 else None
     rhs = rng.standard_normal(shape)
-    if all(x == P_ for x in bc_lo) and a == 0.0:
+    if D_ not in bc_lo + bc_hi and a == 0.0:  # singular: a zero-mean rhs
         rhs -= rhs.mean()
-    prob_hi = (1.0, 1.0, 1.0) if name != "helmholtz" else (1.0, 0.5, 2.0)
+    prob_hi = {"helmholtz": (1.0, 0.5, 2.0), "mixedwalls": (1.2, 0.8, 1.0)}.get(name, (1.0, 1.0, 1.0))
     return dict(name=name, domain=dom, boxes=I.chop(*dom, mgs), bc_lo=list(bc_lo), bc_hi=list(bc_hi), a=a, b=b,
                 alpha=alpha, beta=beta, rhs=rhs, prob_hi=prob_hi)
 
 
-SEEDS = {"uneven": 101, "periodic": 102, "helmholtz": 103, "oddlo": 104, "abec64": 105}
-NAMES = ["uneven", "periodic", "helmholtz", "oddlo", "poisson32"]
+SEEDS = {"uneven": 101, "periodic": 102, "helmholtz": 103, "oddlo": 104, "abec64": 105, "neumann": 106,
+         "mixedwalls": 107}
+NAMES = ["uneven", "periodic", "helmholtz", "oddlo", "poisson32", "neumann", "mixedwalls"]

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2009_12009_gb300 import gmg  # noqa: E402
 
-P_, D_ = I.PERIODIC, I.DIRICHLET
+P_, D_, N_ = I.PERIODIC, I.DIRICHLET, I.NEUMANN
 
 
 def average_down(xf, cshape):
@@ -45,7 +45,7 @@ class AmrPair:
         self.P.set_coeffs(0.0, 1.0, beta_c=self.bc, beta_f=self.bf)
         self.C.set_coeffs(0.0, 1.0, beta_c=torch.from_numpy(self.bc), beta_f=torch.from_numpy(self.bf[self.sl]))
         self.rng = rng
-        self.periodic = per
+        self.singular = bc != D_  # periodic or zero-flux walls with a = 0
 
     def to_gpu(self, xc, xf):
         return self.C.pack_level(0, torch.from_numpy(xc)), self.C.pack_level(1, torch.from_numpy(xf[self.sl].copy()))
@@ -63,14 +63,14 @@ class AmrPair:
 
     def rand_rhs(self):
         rc, rf = self.rand_composite()
-        if self.periodic:
+        if self.singular:
             v = self.P.pack(rc, rf)
             V = self.P.volumes()
             rc, rf = self.P.unpack(v - (V @ v) / V.sum())
         return rc, rf
 
 
-@pytest.fixture(scope="module", params=[P_, D_], ids=["periodic", "dirichlet"])
+@pytest.fixture(scope="module", params=[P_, D_, N_], ids=["periodic", "dirichlet", "neumann"])
 def amr(request):
     return AmrPair(bc=request.param)
 
@@ -127,7 +127,7 @@ def test_adjoint_solve_residual(amr):
     assert info.status == gmg.OK, (info.status, info.history()[-3:])
     lam = amr.P.pack(*amr.from_gpu(lc, lf))
     g = amr.P.pack(gcn, gfn)
-    if amr.periodic:
+    if amr.singular:
         V = amr.P.volumes()
         g = g - V * g.sum() / V.sum()
         assert abs(lam.sum()) <= 1e-10 * np.abs(lam).sum()

@@ -380,7 +380,7 @@ def test_fused_sweep_is_bitwise_two_half_sweeps(case):
     assert i1.kernel_launches == i0.kernel_launches
 
 
-@pytest.mark.parametrize("name", ["uneven", "periodic", "helmholtz", "poisson32"])
+@pytest.mark.parametrize("name", ["uneven", "periodic", "helmholtz", "poisson32", "neumann", "mixedwalls"])
 def test_ghost_push_is_bitwise_ghost_exchange(name):
     """The smoother and interpolation writing their new values into the ghosts that copy
     them gives bit for bit the V-cycle and the solve of the ghost exchange before every
@@ -459,7 +459,7 @@ def test_vector_smooth_is_bitwise_pair_smooth(case):
         assert torch.equal(a1, C.unpack(p0)), prec
 
 
-@pytest.mark.parametrize("name", ["uneven", "periodic", "helmholtz", "poisson32"])
+@pytest.mark.parametrize("name", ["uneven", "periodic", "helmholtz", "poisson32", "neumann", "mixedwalls"])
 def test_residual_fused_first_red_sweep_is_exact(name):
     """The outer residual also doing the first red half-sweep of the next V-cycle (e = r / D
     on red cells from e = 0) gives the iterates of the separate sweep (equal values; only

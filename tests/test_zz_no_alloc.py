@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 from paper_2009_12009_gb300 import gmg  # noqa: E402
 from paper_2009_12009_gb300 import inputs as I  # noqa: E402
 
-P_, D_ = I.PERIODIC, I.DIRICHLET
+P_, D_, N_ = I.PERIODIC, I.DIRICHLET, I.NEUMANN
 
 # single boxes with an odd edge: nothing coarsens, so the whole box is the bottom level
 CASES = [
@@ -31,6 +31,8 @@ CASES = [
     dict(n=(9, 7, 5), bc=[P_, P_, P_], a=0.0, seed=2),      # singular: zero-mean projection
     dict(n=(11, 9, 7), bc=[P_, D_, D_], a=1.0, seed=3),     # a*alpha term, mixed walls
     dict(n=(30, 31, 29), bc=[D_, D_, D_], a=0.0, seed=4),   # near the static limit
+    dict(n=(9, 5, 7), bc=[N_, N_, N_], a=0.0, seed=5),      # singular: zero-flux walls
+    dict(n=(7, 9, 5), bc=[N_, P_, D_], bc_hi=[D_, P_, N_], a=0.5, seed=6),  # Neumann/Dirichlet per side
 ]
 
 
@@ -48,7 +50,8 @@ def test_noalloc_matches_workspace_bottom(case):
     shape = (nz, ny, nx)
     dom = ((0, 0, 0), (nx - 1, ny - 1, nz - 1))
     stream = torch.cuda.current_stream().cuda_stream
-    ctx = gmg.Context(dom, case["bc"], case["bc"], boxes=[dom], stream=stream)
+    bc_hi = case.get("bc_hi", case["bc"])
+    ctx = gmg.Context(dom, case["bc"], bc_hi, boxes=[dom], stream=stream)
     assert ctx.nlevels == 1
     ctx.allocate(gmg.FP64)
     ctx.set_scalars(case["a"], 1.0)
@@ -56,18 +59,19 @@ def test_noalloc_matches_workspace_bottom(case):
         ctx.set_alpha(torch.from_numpy(np.exp(rng.standard_normal(shape))))
     ctx.set_beta(torch.from_numpy(I.lognormal_beta(rng, shape, periodic=False)))
     rhs = rng.standard_normal(shape)
-    singular = int(all(b == P_ for b in case["bc"]) and case["a"] == 0.0)
+    singular = int(D_ not in case["bc"] + bc_hi and case["a"] == 0.0)
     # existing entry point: the bottom solve with the context's workspace
     xref_b, it_ref = ctx.bottom_solve(ctx.pack(torch.from_numpy(rhs)))
     xref = ctx.unpack(xref_b).cpu().numpy()
     wx, wy, wz, dg = _dense_coeffs(ctx)
     rhs_d = torch.from_numpy(rhs).cuda()
     bc = (C.c_int * 3)(*case["bc"])
+    bch = (C.c_int * 3)(*bc_hi)
     iters = torch.zeros(1, dtype=torch.int32, device="cuda")
     L = gmg.lib()
     for call in range(2):
         x = torch.full(shape, float("nan"), dtype=torch.float64, device="cuda")
-        st = L.gmg_box_bicgstab_noalloc(C.c_void_p(stream), nx, ny, nz, bc, bc, singular,
+        st = L.gmg_box_bicgstab_noalloc(C.c_void_p(stream), nx, ny, nz, bc, bch, singular,
                                         C.c_void_p(wx.data_ptr()), C.c_void_p(wy.data_ptr()),
                                         C.c_void_p(wz.data_ptr()), C.c_void_p(dg.data_ptr()),
                                         C.c_void_p(rhs_d.data_ptr()), C.c_void_p(x.data_ptr()), 200, 1e-4,
