@@ -220,6 +220,8 @@ def measure_forms(stream, barrier, dev, only=None):
         forms["batch64"] = _form_batch64(stream, barrier)
     if only in (None, "amr2"):
         forms["amr2"] = _form_amr2(stream, barrier, dev)
+    if only in (None, "walls256"):
+        forms["walls256"] = _form_walls256(stream, barrier)
     return forms
 
 
@@ -254,6 +256,40 @@ def _form_abec512(stream, barrier):
     res["mixed_speedup_fp32"] = res["fp64"]["time_to_tol_ms"] / res["fp32"]["time_to_tol_ms"]
     res["mixed_speedup_bf16"] = res["fp64"]["time_to_tol_ms"] / res["bf16"]["time_to_tol_ms"]
     del ctx, rhs, phi, ref, sol
+    torch.cuda.empty_cache()
+    return res
+
+
+def _form_walls256(stream, barrier):
+    import torch
+
+    from paper_2009_12009_gb300 import gmg
+    from paper_2009_12009_gb300 import inputs as I
+
+    cfg = I.walls256()
+    ctx = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"], stream=stream.cuda_stream)
+    ctx.allocate(gmg.MIXED_FP32)
+    ctx.set_scalars(0.0, 1.0)
+    ctx.set_beta(torch.from_numpy(cfg["beta"]))
+    rhs = ctx.pack(torch.from_numpy(cfg["rhs"]))
+    vals = {f: torch.from_numpy(v).cuda() for f, v in cfg["wall_values"].items()}
+    del cfg
+    phi = ctx.field(0)
+    folded = ctx.field(0)
+    upd = mcell_updates_per_vcycle(ctx, 4)
+    ms_fold, _ = _timed(lambda: ctx.wall_values_rhs(rhs, vals, out=folded), 5, 2, stream, barrier)
+    res = {"workload": "walls256: the abec256 recipe (seed 12015) with Neumann x-, y+, z- and Dirichlet x+, y-, "
+                       "z+ walls, N(0,1) values on every wall face; tol 1e-10 of the initial residual",
+           "wall_values_rhs_ms": ms_fold,
+           "autotuned": {name: summarize_tuning(ctx.autotune(folded, prec))
+                         for name, prec in (("fp64", gmg.FP64), ("fp32", gmg.MIXED_FP32), ("bf16", gmg.MIXED_BF16))}}
+    for name, prec in (("fp64", gmg.FP64), ("fp32", gmg.MIXED_FP32), ("bf16", gmg.MIXED_BF16)):
+        ms, info = _timed(lambda: ctx.solve(rhs, phi, tol_rel=TOL, precision=prec, wall_values=vals)[1], 3, 1,
+                          stream, barrier)
+        res[name] = {"time_to_tol_ms": ms, "iterations": info.iterations, "status": info.status,
+                     "value": upd * info.iterations / (ms * 1e-3) / 1e6, "unit": UNIT,
+                     "final_rel_resid": info.final_resid / info.rhs_norm}
+    del ctx, rhs, phi, folded
     torch.cuda.empty_cache()
     return res
 
@@ -373,7 +409,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the 512^3, batched and two-level workloads")
-    ap.add_argument("--only", choices=["abec512", "batch64", "amr2"], default=None,
+    ap.add_argument("--only", choices=["abec512", "batch64", "amr2", "walls256"], default=None,
                     help="run and print only this one of the other workloads (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -312,9 +312,12 @@ class Context:
     # ---- solve ------------------------------------------------------------------------
     def solve(self, rhs, phi=None, tol_rel=1e-10, tol_abs=0.0, raise_on_error=True, wall_values=None, **params):
         """rhs, phi: FP64 boxed-layout tensors of level 0.  wall_values: nonzero wall values
-        (see wall_values_rhs), folded into a copy of rhs first.  Returns (phi, info)."""
+        (see wall_values_rhs), folded into a copy of rhs first (one buffer per context, so
+        repeated solves reuse one captured graph).  Returns (phi, info)."""
         if wall_values is not None:
-            rhs = self.wall_values_rhs(rhs, wall_values)
+            if getattr(self, "_wall_rhs", None) is None:
+                self._wall_rhs = self.field(0)
+            rhs = self.wall_values_rhs(rhs, wall_values, out=self._wall_rhs)
         phi = self.field(0) if phi is None else phi
         p = default_params(**params)
         info = SolveInfo()

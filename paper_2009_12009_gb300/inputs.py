@@ -22,7 +22,8 @@ PERIODIC = 0
 DIRICHLET = 1
 NEUMANN = 2
 
-SEEDS = {"poisson32": 12010, "abec256": 12011, "abec512": 12012, "batch64": 12013, "amr2": 12014}
+SEEDS = {"poisson32": 12010, "abec256": 12011, "abec512": 12012, "batch64": 12013, "amr2": 12014,
+         "walls256": 12015}
 BATCH_EDGES = (32, 48, 64, 96, 128, 160)
 
 
@@ -117,6 +118,27 @@ def abec256():
 
 def abec512():
     return abec(512, 128, SEEDS["abec512"], name="abec512")
+
+
+def face_shape(domain, face):
+    """(n_t2, n_t1) of a wall face (2*d + side): its tangential axes in increasing order, the
+    lower one fastest."""
+    d = face // 2
+    t1, t2 = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
+    lo, hi = domain
+    return (hi[t2] - lo[t2] + 1, hi[t1] - lo[t1] + 1)
+
+
+def walls256():
+    """The abec256 recipe with mixed walls and nonzero wall values: x- Neumann, x+ Dirichlet,
+    y- Dirichlet, y+ Neumann, z- Neumann, z+ Dirichlet; every wall face carries N(0,1) values
+    (Dirichlet: phi on the face; Neumann: the outward normal derivative)."""
+    cfg = abec(256, 64, SEEDS["walls256"], name="walls256")
+    cfg["bc_lo"] = [NEUMANN, DIRICHLET, NEUMANN]
+    cfg["bc_hi"] = [DIRICHLET, NEUMANN, DIRICHLET]
+    rng = np.random.default_rng(SEEDS["walls256"] + 1)
+    cfg["wall_values"] = {f: rng.standard_normal(face_shape(cfg["domain"], f)) for f in range(6)}
+    return cfg
 
 
 def batch_sizes(nsolves=64, seed=None):

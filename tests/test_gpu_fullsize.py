@@ -10,6 +10,9 @@ the oracle.
   * batch64 (64 problems, 42.3M cells, one batched context): every problem's residual by
     the oracle's operator, in FP64 and mixed FP32; three problems (smallest, median,
     largest) solved by the oracle alone: same iteration count, solutions within 1e-10.
+  * walls256 (the abec256 recipe with Neumann and Dirichlet walls carrying N(0,1) values):
+    two iterations element by element against the oracle (values in its ghosts); the
+    converged FP64 and mixed solutions' residuals by the oracle's affine operator.
   * amr2 (two levels, 128^3 + 128^3): two composite iterations element by element; the
     converged forward and adjoint solves' residuals by the oracle's composite operator and
     its transpose; the beta gradient of the GPU's phi and lambda against the oracle's.
@@ -72,6 +75,38 @@ def test_abec256_converged_residual(abec256):
     rel = oracle_rel_residual(P, C.unpack(phi).cpu().numpy(), cfg["rhs"])
     assert rel <= RES_BOUND
     # the library's own final residual is the one the oracle's operator gives
+    assert abs(rel - info.final_resid / info.rhs_norm) <= 1e-3 * rel
+
+
+@pytest.fixture(scope="module")
+def walls256():
+    cfg = I.walls256()
+    C, P = make_pair(cfg, gmg.MIXED_FP32)
+    for f, v in cfg["wall_values"].items():
+        P.set_bc_values(f, v)
+    vals = {f: torch.from_numpy(v) for f, v in cfg["wall_values"].items()}
+    return cfg, C, P, vals
+
+
+def test_walls256_two_iterations_match_oracle(walls256):
+    cfg, C, P, vals = walls256
+    want, it, hist, _ = P.solve(cfg["rhs"], tol_rel=0.0, maxit=2)
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=0.0, max_iter=2, wall_values=vals)
+    assert info.iterations == it == 2
+    got = C.unpack(phi).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    np.testing.assert_allclose(info.history(), hist, rtol=1e-8)
+
+
+@pytest.mark.parametrize("prec", [gmg.FP64, gmg.MIXED_FP32, gmg.MIXED_BF16])
+def test_walls256_converged_residual(walls256, prec):
+    cfg, C, P, vals = walls256
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=TOL, precision=prec, wall_values=vals)
+    assert info.status == gmg.OK
+    got = C.unpack(phi).cpu().numpy()
+    r0 = np.abs(cfg["rhs"] - P.apply_bc(np.zeros_like(got))).max()
+    rel = np.abs(cfg["rhs"] - P.apply_bc(got)).max() / r0
+    assert rel <= RES_BOUND
     assert abs(rel - info.final_resid / info.rhs_norm) <= 1e-3 * rel
 
 
