@@ -110,16 +110,18 @@ class ClockSampler:
 
 
 def kernel_traffic(kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the kernel
-    source it was measured on is the current one (else None)."""
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the sources it
+    was measured on (the kernel and the workspace placement) are the current ones (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
-    src = os.path.join(ROOT, "paper_2009_12009_gb300", "csrc", rec.get("source", "kernels.cu"))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if h != rec.get("source_sha256_16"):
+    h = hashlib.sha256()
+    for name in rec.get("sources", []):
+        with open(os.path.join(ROOT, "paper_2009_12009_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    if not rec.get("sources") or h.hexdigest()[:16] != rec.get("sources_sha256_16"):
         return None
     return rec.get("dram_bytes_per_launch_full_size")
 
