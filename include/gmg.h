@@ -28,7 +28,7 @@
  *         box_offset + (gx + i) + sx * ((j + 1) + (ny + 2) * (k + 1)),
  *     with gx = 8 for every element type (so the first valid cell of a row is 16-byte
  *     aligned for bfloat16, 32-byte for float, 64-byte for double) and sx = the row
- *     stride returned by gmg_mg_layout (a multiple of 16 elements).  Offsets count
+ *     stride returned by gmg_mg_layout (a multiple of 32 elements).  Offsets count
  *     elements, so buffers of different element types on one level share offsets.  Ghost cells sit at
  *     i = -1, i = nx, j = -1, ... .  Face arrays use the same layout: slot i holds the
  *     face at i - 1/2, i in [0, nx].  gmg_pack / gmg_unpack convert to and from a dense

@@ -55,14 +55,15 @@ struct Carver {
     off += bytes;
     return p;
   }
-  // An FP64 level array that kernels read without its x ghosts (coefficients, right-hand
-  // sides): 64 bytes past a 256-byte boundary.  Rows of the boxed layout start on 128-byte
-  // boundaries and their first valid cell sits at element 8, so here the valid cells of a
-  // row begin on a 128-byte line: 64 cells are 4 lines instead of 5.  DRAM traffic follows
-  // whole lines (abec256 level-0 sweep: 1.02 -> 0.87 GB per colour); fields read with
-  // their x ghosts (phi, e) keep the plain placement, where the ghosts share the end lines.
-  void* take_rows(size_t bytes) {
-    off = ((off + 255) & ~(size_t)255) + 64;
+  // A level array of elem-byte elements that kernels read without its x ghosts
+  // (coefficients, right-hand sides): 128 - 8 elem bytes past a 256-byte boundary.  Rows of
+  // the boxed layout start on 128-byte lines (float, double) and their first valid cell sits
+  // at element 8, so here the valid cells of a row begin on a line: 64 doubles are 4 lines
+  // instead of 5, 64 floats 2 instead of 3.  DRAM traffic follows whole lines (abec256
+  // level-0 FP64 sweep: 1.02 -> 0.87 GB per colour); fields read with their x ghosts (phi,
+  // e) keep the plain placement, where the ghosts share the end lines.
+  void* take_rows(size_t bytes, size_t elem) {
+    off = ((off + 255) & ~(size_t)255) + ((128 - 8 * elem) & 127);
     void* p = base ? base + off : nullptr;
     off += bytes;
     return p;
@@ -284,24 +285,24 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.push_faces = (const PushFace*)cv.take(sizeof(PushFace) * M.push_faces.size());
     D.push_ok = M.push_ok ? 1 : 0;
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
-    B.acoef = (double*)cv.take_rows(8 * ne);
-    B.wx = (double*)cv.take_rows(8 * ne);
-    B.wy = (double*)cv.take_rows(8 * ne);
-    B.wz = (double*)cv.take_rows(8 * ne);
-    B.D = (double*)cv.take_rows(8 * ne);
-    B.invD = (double*)cv.take_rows(8 * ne);
+    B.acoef = (double*)cv.take_rows(8 * ne, 8);
+    B.wx = (double*)cv.take_rows(8 * ne, 8);
+    B.wy = (double*)cv.take_rows(8 * ne, 8);
+    B.wz = (double*)cv.take_rows(8 * ne, 8);
+    B.D = (double*)cv.take_rows(8 * ne, 8);
+    B.invD = (double*)cv.take_rows(8 * ne, 8);
     B.e[DT_F64] = cv.take(8 * ne);
-    B.r[DT_F64] = cv.take_rows(8 * ne);
+    B.r[DT_F64] = cv.take_rows(8 * ne, 8);
     if (mixed) {
-      B.fwx = (float*)cv.take(4 * ne);
-      B.fwy = (float*)cv.take(4 * ne);
-      B.fwz = (float*)cv.take(4 * ne);
-      B.fD = (float*)cv.take(4 * ne);
-      B.finvD = (float*)cv.take(4 * ne);
+      B.fwx = (float*)cv.take_rows(4 * ne, 4);
+      B.fwy = (float*)cv.take_rows(4 * ne, 4);
+      B.fwz = (float*)cv.take_rows(4 * ne, 4);
+      B.fD = (float*)cv.take_rows(4 * ne, 4);
+      B.finvD = (float*)cv.take_rows(4 * ne, 4);
       B.e[DT_F32] = cv.take(4 * ne);
-      B.r[DT_F32] = cv.take(4 * ne);
+      B.r[DT_F32] = cv.take_rows(4 * ne, 4);
       B.e[DT_BF16] = cv.take(2 * ne);
-      B.r[DT_BF16] = cv.take(2 * ne);
+      B.r[DT_BF16] = cv.take_rows(2 * ne, 2);
     }
     if (!M.bot_descs.empty()) B.bot_work = (double*)cv.take(8 * 7 * ne);
     if (fill) {
@@ -356,14 +357,14 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.push_faces = (const PushFace*)cv.take(sizeof(PushFace) * M.push_faces.size());
     D.push_ok = M.push_ok ? 1 : 0;
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
-    B.acoef = (double*)cv.take_rows(8 * nf);
-    B.wx = (double*)cv.take_rows(8 * nf);
-    B.wy = (double*)cv.take_rows(8 * nf);
-    B.wz = (double*)cv.take_rows(8 * nf);
-    B.D = (double*)cv.take_rows(8 * nf);
-    B.invD = (double*)cv.take_rows(8 * nf);
+    B.acoef = (double*)cv.take_rows(8 * nf, 8);
+    B.wx = (double*)cv.take_rows(8 * nf, 8);
+    B.wy = (double*)cv.take_rows(8 * nf, 8);
+    B.wz = (double*)cv.take_rows(8 * nf, 8);
+    B.D = (double*)cv.take_rows(8 * nf, 8);
+    B.invD = (double*)cv.take_rows(8 * nf, 8);
     B.e[DT_F64] = cv.take(8 * nf);
-    B.r[DT_F64] = cv.take_rows(8 * nf);
+    B.r[DT_F64] = cv.take_rows(8 * nf, 8);
     AmrDev A;
     A.cf = (const CfGhost*)cv.take(sizeof(CfGhost) * H.cf.size());
     A.ncf = (int)H.cf.size();

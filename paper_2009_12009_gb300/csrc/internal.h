@@ -19,8 +19,9 @@ enum { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2, NDT = 3 };
 // Valid cell i of a row sits at element GX + i; GX elements = 16 B for bfloat16, 32 B for
 // float, 64 B for double, so the first valid cell of every row is 16-byte aligned.
 constexpr int GX = 8;
-// Row strides are multiples of this many elements (32 B for bfloat16).
-constexpr int ROW_ALIGN = 16;
+// Row strides are multiples of this many elements: 128 B (one DRAM line) for float, 256 B
+// for double, so every row of a float or double array starts on a line boundary.
+constexpr int ROW_ALIGN = 32;
 // Box offsets are multiples of this many elements.
 constexpr int BOX_ALIGN = 64;
 
