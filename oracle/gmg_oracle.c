@@ -91,6 +91,8 @@ typedef struct {
   double bot_tol;
   int last_bottom_iters;
   double* bcval[6];  /* level-0 wall values per face (2*d + side), or NULL (g = 0) */
+  int bot_cg;        /* bottom solver: 0 BiCGStab, 1 conjugate gradients */
+  int post_rev;      /* post-smoothing colour order: 0 red then black, 1 black then red */
 } oprob;
 
 /* ------------------------------------------------------------------ layout */
@@ -375,6 +377,15 @@ void orc_set_params(void* vp, int nu1, int nu2, int bot_maxit, double bot_tol) {
   p->nu1 = nu1; p->nu2 = nu2; p->bot_maxit = bot_maxit; p->bot_tol = bot_tol;
 }
 int orc_last_bottom_iters(void* vp) { return ((oprob*)vp)->last_bottom_iters; }
+/* bottom_cg: the bottom solve by conjugate gradients instead of BiCGStab; post_reverse: the
+   post-smoothing sweeps take black before red, the reverse of the pre-smoothing order, which
+   makes the V-cycle a symmetric operator when A is (the preconditioner of the top-level
+   conjugate gradients) */
+void orc_set_cycle(void* vp, int bottom_cg, int post_reverse) {
+  oprob* p = (oprob*)vp;
+  p->bot_cg = bottom_cg;
+  p->post_rev = post_reverse;
+}
 
 /* dense array over the level's domain (x fastest) <-> ghosted per-box layout */
 void orc_dense_to_boxed(void* vp, int m, const double* dense, double* boxed) {
@@ -690,8 +701,11 @@ double orc_level_norminf(void* vp, int m, const double* x) { return lev_norminf(
    or on breakdown (|rho| or |(rhat, v)| below 1e-300, or (t,t) = 0), keeping the
    current iterate.  For a singular problem the right-hand side is first projected onto
    zero mean and so is the result.  Returns the number of iterations taken. */
+static int bottom_cg(oprob* p, const double* rhs_in, double* x);
+
 int orc_bottom(void* vp, const double* rhs_in, double* x) {
   oprob* p = (oprob*)vp;
+  if (p->bot_cg) return bottom_cg(p, rhs_in, x);
   int m = p->nlev - 1;
   olev* l = &p->L[m];
   int64_t n = l->ntot;
@@ -746,6 +760,50 @@ int orc_bottom(void* vp, const double* rhs_in, double* x) {
   return it;
 }
 
+/* Conjugate gradients (Hestenes and Stiefel 1952) for A x = rhs on the bottom level (A
+   symmetric positive definite, or semi-definite with the constants as null space for a
+   singular problem), x0 = 0:  p = r;  alpha = (r,r)/(p,Ap);  x += alpha p;  r -= alpha Ap;
+   beta = (r',r')/(r,r);  p = r' + beta p.  Stops when ||r||_inf <= bot_tol * ||r0||_inf,
+   after bot_maxit iterations, or on breakdown ((p,Ap) not positive), keeping the current
+   iterate.  Singular problems: rhs and result projected onto zero mean, as for BiCGStab. */
+static int bottom_cg(oprob* p, const double* rhs_in, double* x) {
+  int m = p->nlev - 1;
+  olev* l = &p->L[m];
+  int64_t n = l->ntot;
+  double* r = (double*)calloc(n, sizeof(double));
+  double* pp = (double*)calloc(n, sizeof(double));
+  double* q = (double*)calloc(n, sizeof(double));
+  memcpy(r, rhs_in, sizeof(double) * n);
+  if (p->singular) lev_add_const(l, r, -lev_sum(l, r) / (double)lev_ncells(l));
+  memset(x, 0, sizeof(double) * n);
+  double r0 = lev_norminf(l, r);
+  int it = 0;
+  if (r0 > 0.0) {
+    memcpy(pp, r, sizeof(double) * n);
+    double rho = lev_dot(l, r, r);
+    for (it = 1; it <= p->bot_maxit; ++it) {
+      orc_apply_level(p, m, pp, q);
+      double pq = lev_dot(l, pp, q);
+      if (!(pq > 0.0)) { it--; break; }
+      double alpha = rho / pq;
+      for (int64_t k = 0; k < n; ++k) {
+        x[k] += alpha * pp[k];
+        r[k] -= alpha * q[k];
+      }
+      if (lev_norminf(l, r) <= p->bot_tol * r0) break;
+      double rho_new = lev_dot(l, r, r);
+      double beta = rho_new / rho;
+      rho = rho_new;
+      for (int64_t k = 0; k < n; ++k) pp[k] = r[k] + beta * pp[k];
+    }
+    if (it > p->bot_maxit) it = p->bot_maxit;
+  }
+  if (p->singular) lev_add_const(l, x, -lev_sum(l, x) / (double)lev_ncells(l));
+  free(r); free(pp); free(q);
+  p->last_bottom_iters = it;
+  return it;
+}
+
 /* --------------------------------------------------------------- V-cycle */
 
 /* V-cycle on the correction equation A_m e = r at MG level m, e = 0 on entry:
@@ -769,8 +827,8 @@ void orc_vcycle(void* vp, int m, double* e, const double* r) {
   orc_vcycle(vp, m + 1, c->e, c->r);
   orc_prolong_add(vp, m, c->e, e);
   for (int s = 0; s < p->nu2; ++s) {
-    orc_smooth_colour(vp, m, e, r, 0);
-    orc_smooth_colour(vp, m, e, r, 1);
+    orc_smooth_colour(vp, m, e, r, p->post_rev ? 1 : 0);
+    orc_smooth_colour(vp, m, e, r, p->post_rev ? 0 : 1);
   }
 }
 
@@ -980,6 +1038,130 @@ int orc_solve(void* vp, const double* rhs_dense, double* phi_dense, double tol_r
   if (p->singular) lev_add_const(l, phi, -lev_sum(l, phi) / (double)lev_ncells(l));
   orc_boxed_to_dense(vp, 0, phi, phi_dense);
   free(rhs); free(phi); free(r); free(e);
+  return it;
+}
+
+/* ------------------------------------------------- Krylov-accelerated multigrid */
+
+/* z = M v: one V-cycle on the correction equation A e = v from e = 0 (the multigrid
+   preconditioner); singular problems: z projected onto zero mean */
+static void mg_precond(oprob* p, const double* v, double* z) {
+  olev* l = &p->L[0];
+  orc_vcycle(p, 0, z, v);
+  if (p->singular) lev_add_const(l, z, -lev_sum(l, z) / (double)lev_ncells(l));
+}
+
+/* q = A v on level 0 with homogeneous walls (v's ghosts refreshed) */
+static void apply0(oprob* p, double* v, double* q) { orc_apply_level(p, 0, v, q); }
+
+/* Solve A phi = rhs from phi = 0 by a Krylov method preconditioned with one V-cycle per
+   application (Sec. "Linear Solvers": native Krylov solvers next to multigrid):
+     method 1: BiCGStab (van der Vorst 1992) preconditioned on the right, x += alpha M p +
+               omega M s;
+     method 2: conjugate gradients preconditioned by M (use orc_set_cycle(.., 1) for a
+               symmetric V-cycle).
+   The wall values enter as for orc_solve: b = rhs - A_g(0), solve A_0 x = b.  Stops when the
+   recursive residual ||r||_inf <= max(tol_rel ||b||_inf, tol_abs), after maxit iterations,
+   or on breakdown.  hist[0..it]: ||r||_inf.  status as orc_solve.  Singular problems: b
+   and every preconditioned vector projected onto zero mean, phi returned with zero mean. */
+int orc_solve_krylov(void* vp, const double* rhs_dense, double* phi_dense, double tol_rel, double tol_abs, int maxit,
+                     int method, int project_mean, double* hist, int* status) {
+  oprob* p = (oprob*)vp;
+  olev* l = &p->L[0];
+  int64_t n = l->ntot;
+  double* V[10];
+  for (int k = 0; k < 10; ++k) V[k] = (double*)calloc(n, sizeof(double));
+  double *x = V[0], *b = V[1], *r = V[2], *rh = V[3], *pp = V[4], *v = V[5], *y = V[6], *sv = V[7], *t = V[8],
+         *z = V[9];
+  double* rhs = (double*)calloc(n, sizeof(double));
+  orc_dense_to_boxed(vp, 0, rhs_dense, rhs);
+  residual_bc(p, x, rhs, b); /* b = rhs - A_g 0 */
+  double bnorm = lev_norminf(l, b);
+  *status = 0;
+  int it = 0;
+  if (p->singular) {
+    double mean = lev_sum(l, b) / (double)lev_ncells(l);
+    if (fabs(mean) > 1e-12 * bnorm && !project_mean) {
+      *status = -1;
+      goto done;
+    }
+    lev_add_const(l, b, -mean);
+  }
+  {
+    double target = tol_rel * bnorm;
+    if (tol_abs > target) target = tol_abs;
+    memcpy(r, b, sizeof(double) * n);
+    double rn = lev_norminf(l, r);
+    if (hist) hist[0] = rn;
+    if (method == 1) {
+      memcpy(rh, r, sizeof(double) * n);
+      double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+      while (!(rn <= target) && it < maxit) {
+        ++it;
+        double rho = lev_dot(l, rh, r);
+        if (fabs(rho) < 1e-300) { --it; break; }
+        double beta = (rho / rho_old) * (alpha / omega);
+        for (int64_t k = 0; k < n; ++k) pp[k] = r[k] + beta * (pp[k] - omega * v[k]);
+        mg_precond(p, pp, y);
+        apply0(p, y, v);
+        double rv = lev_dot(l, rh, v);
+        if (fabs(rv) < 1e-300) { --it; break; }
+        alpha = rho / rv;
+        for (int64_t k = 0; k < n; ++k) sv[k] = r[k] - alpha * v[k];
+        double sn = lev_norminf(l, sv);
+        if (sn <= target) {
+          for (int64_t k = 0; k < n; ++k) x[k] += alpha * y[k];
+          memcpy(r, sv, sizeof(double) * n);
+          rn = sn;
+          if (hist) hist[it] = rn;
+          break;
+        }
+        mg_precond(p, sv, z);
+        apply0(p, z, t);
+        double tt = lev_dot(l, t, t);
+        if (tt == 0.0) { --it; break; }
+        omega = lev_dot(l, t, sv) / tt;
+        for (int64_t k = 0; k < n; ++k) {
+          x[k] += alpha * y[k] + omega * z[k];
+          r[k] = sv[k] - omega * t[k];
+        }
+        rn = lev_norminf(l, r);
+        if (hist) hist[it] = rn;
+        if (!(rn == rn) || isinf(rn)) { *status = -3; break; }
+        rho_old = rho;
+      }
+    } else {
+      mg_precond(p, r, z);
+      memcpy(pp, z, sizeof(double) * n);
+      double rho = lev_dot(l, r, z);
+      while (!(rn <= target) && it < maxit) {
+        ++it;
+        apply0(p, pp, v);
+        double pv = lev_dot(l, pp, v);
+        if (!(pv > 0.0)) { --it; break; }
+        double alpha = rho / pv;
+        for (int64_t k = 0; k < n; ++k) {
+          x[k] += alpha * pp[k];
+          r[k] -= alpha * v[k];
+        }
+        rn = lev_norminf(l, r);
+        if (hist) hist[it] = rn;
+        if (!(rn == rn) || isinf(rn)) { *status = -3; break; }
+        if (rn <= target) break;
+        mg_precond(p, r, z);
+        double rho_new = lev_dot(l, r, z);
+        double beta = rho_new / rho;
+        rho = rho_new;
+        for (int64_t k = 0; k < n; ++k) pp[k] = z[k] + beta * pp[k];
+      }
+    }
+    if (*status == 0 && !(rn <= target)) *status = -2;
+  }
+  if (p->singular) lev_add_const(l, x, -lev_sum(l, x) / (double)lev_ncells(l));
+  orc_boxed_to_dense(vp, 0, x, phi_dense);
+done:
+  for (int k = 0; k < 10; ++k) free(V[k]);
+  free(rhs);
   return it;
 }
 

@@ -96,6 +96,10 @@ def _declare(L):
     L.orc_solve.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_double, C.c_int, C.c_int, _f64p, _i32p]
     L.orc_solve.restype = C.c_int
     L.orc_apply.argtypes = [C.c_void_p, _f64p, _f64p]
+    L.orc_set_cycle.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.orc_solve_krylov.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+                                   _f64p, _i32p]
+    L.orc_solve_krylov.restype = C.c_int
     L.orc_apply_bc.argtypes = [C.c_void_p, _f64p, _f64p]
     L.orc_set_bc_values.argtypes = [C.c_void_p, C.c_int, _f64p]
     L.orc_set_bc_values.restype = C.c_int
@@ -174,6 +178,11 @@ class Problem:
 
     def level_size(self, m):
         return int(lib().orc_level_size(self.h, m))
+
+    def set_cycle(self, bottom_cg=False, post_reverse=False):
+        """bottom solver CG instead of BiCGStab; post-smoothing black before red (symmetric
+        V-cycle)."""
+        lib().orc_set_cycle(self.h, int(bottom_cg), int(post_reverse))
 
     def set_params(self, nu1=2, nu2=2, bot_maxit=200, bot_tol=1e-4):
         lib().orc_set_params(self.h, nu1, nu2, bot_maxit, bot_tol)
@@ -265,6 +274,18 @@ class Problem:
         status = np.zeros(1, dtype=np.int32)
         it = lib().orc_solve(self.h, _dp(rhs), _dp(phi), tol_rel, tol_abs, maxit, int(project_mean),
                              _dp(hist), _ip(status))
+        return phi, int(it), hist[:it + 1].copy(), int(status[0])
+
+    def solve_krylov(self, rhs, method, tol_rel=1e-10, tol_abs=0.0, maxit=100, project_mean=False):
+        """Krylov solve preconditioned by one V-cycle per application: method 1 BiCGStab
+        (right preconditioned), 2 conjugate gradients.  Returns (phi, iterations,
+        recursive-residual history, status)."""
+        rhs = _f64(rhs)
+        phi = np.zeros(self.level_shape(0))
+        hist = np.zeros(maxit + 1)
+        status = np.zeros(1, dtype=np.int32)
+        it = lib().orc_solve_krylov(self.h, _dp(rhs), _dp(phi), tol_rel, tol_abs, maxit, int(method),
+                                    int(project_mean), _dp(hist), _ip(status))
         return phi, int(it), hist[:it + 1].copy(), int(status[0])
 
     def apply(self, phi):
