@@ -132,6 +132,20 @@ typedef struct {
                            correction it is e = r / D on red cells, 0 on black), saving one
                            pass over the finest level per iteration; 0: separate.  Same
                            results (up to the sign of zero corrections). */
+  int krylov;           /* top-level method of gmg_solve (Sec. "Linear Solvers": native
+                           Krylov solvers next to multigrid).  0 (default): the multigrid
+                           iteration phi += V(rhs - A phi).  1: BiCGStab preconditioned on the
+                           right by one V-cycle per application.  2: conjugate gradients
+                           preconditioned by the symmetric V-cycle (post-smoothing colours
+                           reversed, whatever post_reverse says; A must be symmetric, which
+                           it is for one level).  Krylov vectors are FP64 and need a
+                           workspace sized with krylov != 0; the V-cycle runs in `precision`.
+                           One-level, single-problem contexts.  The stopping test uses the
+                           recursive residual of the Krylov recurrence. */
+  int bottom_solver;    /* 0 (default): BiCGStab bottom; 1: conjugate gradients (the bottom
+                           operator is symmetric) */
+  int post_reverse;     /* 1: post-smoothing sweeps take black before red, the reverse of
+                           pre-smoothing (a symmetric V-cycle); 0 (default): red first */
 } gmg_params;
 
 typedef struct {

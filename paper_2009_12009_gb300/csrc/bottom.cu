@@ -1,7 +1,7 @@
 // bottom.cu -- bottom solve of the V-cycle (Sec. "Linear Solvers": Krylov bottom
-// solver): unpreconditioned BiCGStab (van der Vorst 1992) in FP64, x0 = 0, one thread
-// block per bottom problem running the whole iteration on the device (no host round
-// trip per iteration).  Stops at ||r||_inf <= tol * ||r0||_inf, after maxit iterations,
+// solver): unpreconditioned BiCGStab (van der Vorst 1992) or conjugate gradients (Hestenes
+// and Stiefel 1952) in FP64, x0 = 0, one thread block per bottom problem running the whole
+// iteration on the device (no host round trip per iteration).  Stops at ||r||_inf <= tol * ||r0||_inf, after maxit iterations,
 // or on breakdown.  Singular problems (no Dirichlet wall, a = 0) project the right-hand side
 // and the result onto zero mean.  Dot products are reduced in a fixed order, so the
 // result is deterministic.
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(BT) k_bottom(const BotDesc* __restrict__ descs
                                                const double* __restrict__ wx, const double* __restrict__ wy,
                                                const double* __restrict__ wz, const double* __restrict__ D,
                                                double* work, int64_t nelem, int maxit, double tol, int* iters,
-                                               const int* __restrict__ active) {
+                                               const int* __restrict__ active, int cg) {
   __shared__ double sh[BT / 32 + 1];
   // programmatic dependent launch: wait for the predecessor before any global access
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -139,7 +139,35 @@ __global__ void __launch_bounds__(BT) k_bottom(const BotDesc* __restrict__ descs
   const double r0 = bot_norm(c, r, sh);
   double rho_old = 1.0, alpha = 1.0, omega = 1.0;
   int it = 0;
-  if (r0 > 0.0) {
+  if (cg && r0 > 0.0) {
+    // conjugate gradients: p = r; alpha = (r,r)/(p,Ap); x += alpha p; r -= alpha Ap;
+    // beta = (r',r')/(r,r); p = r' + beta p; breakdown when (p,Ap) is not positive
+    for (int i = threadIdx.x; i < c.ncell; i += BT) p[c.cells[i].q] = r[c.cells[i].q];
+    __syncthreads();
+    double rho = bot_dot(c, r, r, sh);
+    for (it = 1; it <= maxit; ++it) {
+      bot_apply(c, p, v);
+      const double pv = bot_dot(c, p, v, sh);
+      if (!(pv > 0.0)) { --it; break; }
+      const double al = rho / pv;
+      for (int i = threadIdx.x; i < c.ncell; i += BT) {
+        const int64_t q = c.cells[i].q;
+        x[q] += al * p[q];
+        r[q] -= al * v[q];
+      }
+      __syncthreads();
+      if (bot_norm(c, r, sh) <= tol * r0) break;
+      const double rho_new = bot_dot(c, r, r, sh);
+      const double be = rho_new / rho;
+      rho = rho_new;
+      for (int i = threadIdx.x; i < c.ncell; i += BT) {
+        const int64_t q = c.cells[i].q;
+        p[q] = r[q] + be * p[q];
+      }
+      __syncthreads();
+    }
+    if (it > maxit) it = maxit;
+  } else if (r0 > 0.0) {
     for (it = 1; it <= maxit; ++it) {
       const double rho = bot_dot(c, rh, r, sh);
       if (fabs(rho) < 1e-300) { --it; break; }
@@ -218,15 +246,15 @@ void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Co
   switch (dt) {
     case DT_F64:
       launch_bottom_kernel<double>(L.n_bot, s, L.bot_descs, L.bot_cells, L.bot_ghosts, (const double*)rhs, (double*)x,
-                                   wx, wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
+                                   wx, wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active, a.cg);
       break;
     case DT_F32:
       launch_bottom_kernel<float>(L.n_bot, s, L.bot_descs, L.bot_cells, L.bot_ghosts, (const float*)rhs, (float*)x,
-                                  wx, wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
+                                  wx, wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active, a.cg);
       break;
     default:
       launch_bottom_kernel<bf16>(L.n_bot, s, L.bot_descs, L.bot_cells, L.bot_ghosts, (const bf16*)rhs, (bf16*)x, wx,
-                                 wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active);
+                                 wy, wz, D, a.work, L.nelem, a.maxit, a.tol, a.iters, L.active, a.cg);
       break;
   }
 }

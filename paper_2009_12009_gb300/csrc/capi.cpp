@@ -94,6 +94,10 @@ struct gmg_ctx {
   std::vector<LevelDev> dev;
   std::vector<LevelBufs> buf;
   double *alpha0 = nullptr, *bx0 = nullptr, *by0 = nullptr, *bz0 = nullptr, *tmp0 = nullptr;
+  // top-level Krylov vectors (level-0 FP64, after everything else in the workspace when it
+  // was sized for them): b, r, rhat, p, v, y, s, t, z, zero
+  static constexpr int NKV = 10;
+  double* kv[NKV] = {};
   // per-problem device scalars
   unsigned long long* normbits = nullptr;  // [0, ns): outer residual norms; [ns, 2ns): rhs / step norms
   double* partials = nullptr;
@@ -119,7 +123,8 @@ struct gmg_ctx {
     int64_t launches;
     int n_ev_smooth, n_ev_resid;  // profiling event pairs recorded per replay
   };
-  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int, int>, GraphEntry>
+  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int, int, int, int>,
+           GraphEntry>
       graphs;
 
   // profiling events (pairs around finest-level smoother / outer residual launches)
@@ -671,8 +676,17 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
 // e_zero: e is zero including its ghosts (just cleared), so the first ghost fill would
 // copy zeros and is skipped.
 // red_done: the first red half-sweep was done by the residual kernel (level 0)
+// reverse: black before red in every sweep (post-smoothing of the symmetric V-cycle; the
+// fused sweep, red first by construction, is not used then)
 void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s,
-                   bool e_zero = false, bool push = false, bool red_done = false) {
+                   bool e_zero = false, bool push = false, bool red_done = false, bool reverse = false) {
+  if (reverse) {
+    for (int it = 0; it < nsweep; ++it) {
+      smooth_colour(c, D, dt, m, 1, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
+      smooth_colour(c, D, dt, m, 0, s, true, push, vec_on(c, p, dt, m));
+    }
+    return;
+  }
   if (p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0) {
     const LevelBufs& B = c->buf[m];
     const Coefs k = coefs_of(c, m, dt);
@@ -693,6 +707,10 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
     smooth_colour(c, D, dt, m, 1, s, true, push, vec_on(c, p, dt, m));
   }
 }
+
+// the symmetric V-cycle: post-smoothing black before red (asked for, or implied by the
+// conjugate-gradient top level)
+bool post_reversed(const gmg_params& p) { return p.post_reverse != 0 || p.krylov == 2; }
 
 // Level m's tables with the V-cycle's work lists of the fused coarse ends: the grid
 // launches leave out the problems whose tail covers level m.
@@ -740,6 +758,8 @@ void launch_tails(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s
   a.nu2 = p.nu2;
   a.maxit = p.bottom_max_iter;
   a.tol = p.bottom_tol;
+  a.cg = p.bottom_solver;
+  a.post_rev = post_reversed(p) ? 1 : 0;
   a.iters = c->bot_iters;
   a.active = c->active;
   launch_vtail(dt, T.count_at[m], a, lv, std::min(nlev(c), TAIL_MAXLEV), s);
@@ -769,7 +789,7 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   if (!red_done) cudaMemsetAsync(B.e[dt], 0, dt_size(dt) * (size_t)c->L[m].nelem, s);
   if (fused) launch_tails(c, dt, m, p, s);
   if (D.n_bot) {
-    BottomArgs a{p.bottom_max_iter, p.bottom_tol, B.bot_work, c->bot_iters};
+    BottomArgs a{p.bottom_max_iter, p.bottom_tol, B.bot_work, c->bot_iters, p.bottom_solver};
     launch_bottom(dt, D, B.r[dt], B.e[dt], coefs64(c, m), a, s);
   }
   if (m + 1 >= nlev(c) || D.n_pair_chunks == 0) return;
@@ -783,7 +803,7 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
   vcycle(c, dt, m + 1, p, s, false);
   launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
-  smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push);
+  smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, post_reversed(p));
 }
 
 // Whether the outer residual also performs the first red half-sweep of the next V-cycle
@@ -848,6 +868,9 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
   if (p.fuse_residual_sweep != 0 && p.fuse_residual_sweep != 1)
     SETERR(c, GMG_ERR_BAD_INPUT, "fuse_residual_sweep must be 0 or 1");
+  if (p.krylov < 0 || p.krylov > 2) SETERR(c, GMG_ERR_BAD_INPUT, "krylov must be 0, 1 or 2");
+  if (p.bottom_solver != 0 && p.bottom_solver != 1) SETERR(c, GMG_ERR_BAD_INPUT, "bottom_solver must be 0 or 1");
+  if (p.post_reverse != 0 && p.post_reverse != 1) SETERR(c, GMG_ERR_BAD_INPUT, "post_reverse must be 0 or 1");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
   return GMG_OK;
 }
@@ -939,7 +962,8 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   if (p.use_graph && nlive) {
     auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
                                p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep, p.ghost_push,
-                               p.vector_smooth, p.pdl, p.fuse_residual_sweep);
+                               p.vector_smooth, p.pdl, p.fuse_residual_sweep, p.bottom_solver,
+                               p.post_reverse);
     auto itg = c->graphs.find(key);
     if (itg != c->graphs.end()) {
       gexec = itg->second.exec;
@@ -1468,6 +1492,197 @@ gmg_status set_domain_geom(gmg_ctx* c, SolveGeom& G, const int lo[3], const int 
 
 namespace {
 
+// workspace bytes of the top-level Krylov vectors
+size_t krylov_bytes(const gmg_ctx* c) {
+  const size_t ne0 = c->L.empty() ? 0 : (size_t)c->L[0].nelem;
+  return 256 + gmg_ctx::NKV * (((8 * ne0) + 255) & ~(size_t)255);
+}
+
+// Krylov solve of A phi = rhs from phi = 0, preconditioned by one V-cycle per application
+// (Sec. "Linear Solvers": native Krylov solvers next to multigrid): krylov = 1 BiCGStab
+// (van der Vorst 1992) preconditioned on the right, 2 conjugate gradients with the symmetric
+// V-cycle.  Vectors FP64; the V-cycle in the precision of p.  Stops on the recursive
+// residual, ||r||_inf <= max(tol_rel ||rhs||_inf, tol_abs), after max_iter iterations, or on
+// breakdown.  Singular problems: rhs, every preconditioned vector and phi projected onto
+// zero mean.  One-level, single-problem contexts.
+gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel, double tol_abs, const gmg_params& p,
+                        gmg_solve_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (c->amr || c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "krylov: one-level, single-problem contexts only");
+  if (!c->kv[0]) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for the Krylov vectors (krylov != 0)");
+  if (info) memset(info, 0, sizeof(*info));
+  cudaStream_t s = c->stream;
+  const int dt = dt_of_precision(p.precision);
+  const LevelDev& D0 = c->dev[0];
+  const int64_t ne = c->L[0].nelem;
+  const int64_t l0 = kernel_launch_count();
+  double *b = c->kv[0], *r = c->kv[1], *rh = c->kv[2], *pp = c->kv[3], *v = c->kv[4], *y = c->kv[5],
+         *sv = c->kv[6], *t = c->kv[7], *z = c->kv[8], *zero = c->kv[9];
+  const bool sing = singular(c, 0);
+  gmg_status st;
+  auto host_sync = [&]() -> gmg_status {
+    CK(c, cudaStreamSynchronize(s));
+    CK(c, cudaGetLastError());
+    return GMG_OK;
+  };
+  auto norm = [&](const double* a, double* out) -> gmg_status {
+    CK(c, cudaMemsetAsync(c->normbits, 0, 8, s));
+    launch_norm_max(D0, a, c->normbits, s);
+    CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 8, cudaMemcpyDeviceToHost, s));
+    gmg_status e = host_sync();
+    *out = bits_to_double(c->h_bits[0]);
+    return e;
+  };
+  auto dot = [&](const double* a, const double* bb, double* out) -> gmg_status {
+    launch_dot(D0, a, bb, c->partials, c->scal, s);
+    CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8, cudaMemcpyDeviceToHost, s));
+    gmg_status e = host_sync();
+    *out = c->h_scal[0];
+    return e;
+  };
+  auto project = [&](double* a) {  // a -= mean(a) on the valid cells (device only)
+    launch_sum(D0, a, c->partials, c->scal + 1, s);
+    launch_add_scalar(D0, a, c->scal + 1, -1.0, s);
+  };
+  auto axpby = [&](double al, const double* a, double be, const double* bb, double* out) {
+    launch_axpby(ne, al, a, be, bb, out, s);
+  };
+  auto precond = [&](const double* in, double* out) {  // out = V(in), e = 0 first
+    launch_convert(DT_F64, dt, in, c->buf[0].r[dt], ne, s);
+    vcycle(c, dt, 0, p, s);
+    launch_convert(dt, DT_F64, c->buf[0].e[dt], out, ne, s);
+    if (sing) project(out);
+  };
+  auto apply = [&](double* in, double* out) {  // out = A in, homogeneous walls
+    launch_fill(DT_F64, D0, in, -1, 0, s);
+    launch_residual(DT_F64, DT_F64, D0, in, zero, coefs64(c, 0), out, nullptr, nullptr, s);
+    launch_scale_valid(D0, out, -1.0, s);
+  };
+  CK(c, cudaMemsetAsync(zero, 0, 8 * (size_t)ne, s));
+  CK(c, cudaMemcpyAsync(b, rhs, 8 * (size_t)ne, cudaMemcpyDeviceToDevice, s));
+  double bnorm;
+  if ((st = norm(b, &bnorm))) return st;
+  if (!std::isfinite(bnorm)) SETERR(c, GMG_ERR_BAD_INPUT, "rhs is not finite");
+  if (sing) {
+    launch_sum(D0, b, c->partials, c->scal, s);
+    CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8, cudaMemcpyDeviceToHost, s));
+    if ((st = host_sync())) return st;
+    if (std::fabs(c->h_scal[0]) > 1e-12 * bnorm && !p.project_mean) {
+      if (info) info->status = GMG_ERR_BAD_INPUT;
+      SETERR(c, GMG_ERR_BAD_INPUT, "singular problem with a nonzero-mean rhs (set project_mean)");
+    }
+    launch_add_scalar(D0, b, c->scal, -1.0, s);
+  }
+  const double target = std::max(tol_rel * bnorm, tol_abs);
+  CK(c, cudaMemsetAsync(x, 0, 8 * (size_t)ne, s));
+  for (double* w : {pp, v, y, sv, t, z}) CK(c, cudaMemsetAsync(w, 0, 8 * (size_t)ne, s));
+  CK(c, cudaMemcpyAsync(r, b, 8 * (size_t)ne, cudaMemcpyDeviceToDevice, s));
+  double rn;
+  if ((st = norm(r, &rn))) return st;
+  std::vector<double> hist{rn};
+  int it = 0;
+  gmg_status result = GMG_OK;
+  if (p.krylov == 1) {
+    CK(c, cudaMemcpyAsync(rh, r, 8 * (size_t)ne, cudaMemcpyDeviceToDevice, s));
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    while (!(rn <= target) && it < p.max_iter) {
+      ++it;
+      double rho;
+      if ((st = dot(rh, r, &rho))) return st;
+      if (std::fabs(rho) < 1e-300) { --it; break; }
+      const double beta = (rho / rho_old) * (alpha / omega);
+      axpby(1.0, pp, -omega, v, pp);  // p = r + beta (p - omega v)
+      axpby(1.0, r, beta, pp, pp);
+      precond(pp, y);
+      apply(y, v);
+      double rv;
+      if ((st = dot(rh, v, &rv))) return st;
+      if (std::fabs(rv) < 1e-300) { --it; break; }
+      alpha = rho / rv;
+      axpby(1.0, r, -alpha, v, sv);
+      double sn;
+      if ((st = norm(sv, &sn))) return st;
+      if (sn <= target) {
+        axpby(1.0, x, alpha, y, x);
+        rn = sn;
+        hist.push_back(rn);
+        break;
+      }
+      precond(sv, z);
+      apply(z, t);
+      double tt, ts;
+      if ((st = dot(t, t, &tt))) return st;
+      if (tt == 0.0) { --it; break; }
+      if ((st = dot(t, sv, &ts))) return st;
+      omega = ts / tt;
+      axpby(1.0, x, alpha, y, x);
+      axpby(1.0, x, omega, z, x);
+      axpby(1.0, sv, -omega, t, r);
+      if ((st = norm(r, &rn))) return st;
+      hist.push_back(rn);
+      if (!std::isfinite(rn)) {
+        result = GMG_ERR_DIVERGED;
+        break;
+      }
+      rho_old = rho;
+    }
+  } else {
+    precond(r, z);
+    CK(c, cudaMemcpyAsync(pp, z, 8 * (size_t)ne, cudaMemcpyDeviceToDevice, s));
+    double rho;
+    if ((st = dot(r, z, &rho))) return st;
+    while (!(rn <= target) && it < p.max_iter) {
+      ++it;
+      apply(pp, v);
+      double pv;
+      if ((st = dot(pp, v, &pv))) return st;
+      if (!(pv > 0.0)) { --it; break; }
+      const double alpha = rho / pv;
+      axpby(1.0, x, alpha, pp, x);
+      axpby(1.0, r, -alpha, v, r);
+      if ((st = norm(r, &rn))) return st;
+      hist.push_back(rn);
+      if (!std::isfinite(rn)) {
+        result = GMG_ERR_DIVERGED;
+        break;
+      }
+      if (rn <= target) break;
+      precond(r, z);
+      double rho_new;
+      if ((st = dot(r, z, &rho_new))) return st;
+      const double beta = rho_new / rho;
+      rho = rho_new;
+      axpby(1.0, z, beta, pp, pp);
+    }
+  }
+  if (result == GMG_OK && !(rn <= target)) result = GMG_ERR_NOT_CONVERGED;
+  if (sing) project(x);
+  CK(c, cudaMemcpyAsync(c->h_iters, c->bot_iters, 4 * 2, cudaMemcpyDeviceToHost, s));
+  if ((st = host_sync())) return st;
+  if (c->h_iters[1]) {  // a staging wait in a fused sweep gave up
+    CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), s));
+    result = GMG_ERR_DEVICE_TIMEOUT;
+  }
+  if (info) {
+    info->iterations = it;
+    info->status = result;
+    info->rhs_norm = bnorm;
+    info->initial_resid = hist[0];
+    info->final_resid = rn;
+    info->bottom_iters = c->h_iters[0];
+    info->hist_len = (int)std::min<size_t>(hist.size(), 256);
+    for (int i = 0; i < info->hist_len; ++i) info->resid_hist[i] = hist[i];
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->kernel_launches = kernel_launch_count() - l0;
+  }
+  if (result == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
+  return result;
+}
+
+}  // namespace
+
+namespace {
+
 // Time `body` (stream-ordered launches) reps times with CUDA events on the context stream;
 // returns ms per rep.
 template <class F>
@@ -1544,6 +1759,9 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->vector_smooth = 2;
   p->pdl = 2;
   p->fuse_residual_sweep = 1;
+  p->krylov = 0;
+  p->bottom_solver = 0;
+  p->post_reverse = 0;
   return GMG_OK;
 }
 
@@ -1918,7 +2136,7 @@ gmg_status gmg_workspace_size(const gmg_ctx* cc, const gmg_params* p, size_t* by
   if (!c || !bytes) return GMG_ERR_BAD_INPUT;
   if (c->L.empty()) SETERR(c, GMG_ERR_STATE, "no BoxArray defined");
   const bool mixed = p && p->precision != GMG_FP64;
-  *bytes = carve(c, nullptr, mixed, false);
+  *bytes = carve(c, nullptr, mixed, false) + (p && p->krylov ? krylov_bytes(c) : 0);
   return GMG_OK;
 }
 
@@ -1939,7 +2157,13 @@ gmg_status gmg_set_workspace(gmg_ctx* c, void* dptr, size_t bytes) {
   c->ws = dptr;
   c->ws_bytes = bytes;
   c->mixed = mixed;
-  carve(c, dptr, mixed, true);
+  const size_t used = carve(c, dptr, mixed, true);
+  // the Krylov vectors, if the workspace holds them after the rest
+  const size_t ne0 = (size_t)c->L[0].nelem;
+  const bool kr = bytes >= used + krylov_bytes(c);
+  for (int q = 0; q < gmg_ctx::NKV; ++q)
+    c->kv[q] = kr ? (double*)((char*)dptr + ((used + 255) & ~(size_t)255) + (size_t)q * (((8 * ne0) + 255) & ~(size_t)255))
+                  : nullptr;
   CK(c, cudaMemsetAsync(c->ws, 0, c->ws_bytes, c->stream));
   st = upload_tables(c);
   if (st) return st;
@@ -2028,7 +2252,7 @@ gmg_status gmg_bottom_solve(gmg_ctx* c, int dt, const void* rhs, void* x, const 
   if ((st = build_coefs(c))) return st;
   if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "gmg_bottom_solve needs a single-problem context");
   const int m = nlev(c) - 1;
-  BottomArgs a{p.bottom_max_iter, p.bottom_tol, c->buf[m].bot_work, c->bot_iters};
+  BottomArgs a{p.bottom_max_iter, p.bottom_tol, c->buf[m].bot_work, c->bot_iters, p.bottom_solver};
   launch_bottom(dt, c->dev[m], rhs, x, coefs64(c, m), a, c->stream);
   CK(c, cudaGetLastError());
   if (iters) {
@@ -2177,6 +2401,7 @@ gmg_status gmg_solve(gmg_ctx* c, void* const* phiv, const void* const* rhsv, dou
     return solve_amr(c, (double*)phiv[0], (double*)phiv[1], (const double*)rhsv[0], (const double*)rhsv[1], tol_rel,
                      tol_abs, p, info);
   }
+  if (p.krylov) return krylov_solve(c, (double*)phiv[0], (const double*)rhsv[0], tol_rel, tol_abs, p, info);
   return solve_impl(c, (double*)phiv[0], (const double*)rhsv[0], tol_rel, tol_abs, p, info);
 }
 

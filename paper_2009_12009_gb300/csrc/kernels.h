@@ -152,6 +152,7 @@ struct BottomArgs {
   double tol;
   double* work;        // 7 double vectors of the bottom level's layout
   int* iters;          // device: iterations per bottom problem
+  int cg = 0;          // 1: conjugate gradients instead of BiCGStab
 };
 void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Coefs& c64, const BottomArgs& a,
                    cudaStream_t s);
@@ -182,6 +183,8 @@ struct TailArgs {
   int64_t nelem[TAIL_MAXLEV] = {};
   int nu1 = 2, nu2 = 2, maxit = 200;
   double tol = 1e-4;
+  int cg = 0;        // bottom by conjugate gradients instead of BiCGStab
+  int post_rev = 0;  // post-smoothing black before red
   int* iters = nullptr;         // per solve: bottom iterations
   const int* active = nullptr;  // per solve: 0 = skip (null: all)
 };

@@ -140,7 +140,7 @@ template <class T>
 __device__ void warp_bottom(const TailDesc& Dd, const BotCell* __restrict__ cells, int nc,
                             const BotGhost* __restrict__ ghosts, int ng, const double* wx, const double* wy,
                             const double* wz, const double* Dg, const T* rhs, T* e, int maxit, double tol,
-                            int* iters, WarpBottomSmem& W) {
+                            int* iters, WarpBottomSmem& W, int cg) {
   const int lane = threadIdx.x;
   const int64_t base = Dd.bot_base;
   for (int i = lane; i < nc; i += 32) {
@@ -204,7 +204,32 @@ __device__ void warp_bottom(const TailDesc& Dd, const BotCell* __restrict__ cell
   // s-values of the cells (slot order) live in W.s at the cells' element offsets
   auto sval = [&](int i) -> double& { return W.s[W.q[i]]; };
   auto pval = [&](int i) -> double& { return W.p[W.q[i]]; };
-  if (r0 > 0.0) {
+  if (cg && r0 > 0.0) {
+    // conjugate gradients (the steps of the block version): v = A p in W.v
+    __syncwarp();
+    for (int i = lane; i < nc; i += 32) pval(i) = W.r[i];
+    double rho = dot(W.r, W.r);
+    for (it = 1; it <= maxit; ++it) {
+      apply(W.p, W.v);
+      __syncwarp();
+      double pv = 0.0;
+      for (int i = lane; i < nc; i += 32) pv += pval(i) * W.v[i];
+      pv = wsum(pv);
+      if (!(pv > 0.0)) { --it; break; }
+      const double al = rho / pv;
+      for (int i = lane; i < nc; i += 32) {
+        W.x[i] += al * pval(i);
+        W.r[i] -= al * W.v[i];
+      }
+      if (norm(W.r) <= tol * r0) break;
+      const double rho_new = dot(W.r, W.r);
+      const double be = rho_new / rho;
+      rho = rho_new;
+      __syncwarp();
+      for (int i = lane; i < nc; i += 32) pval(i) = W.r[i] + be * pval(i);
+    }
+    if (it > maxit) it = maxit;
+  } else if (r0 > 0.0) {
     for (it = 1; it <= maxit; ++it) {
       const double rho = dot(W.rh, W.r);
       if (fabs(rho) < 1e-300) { --it; break; }
@@ -310,7 +335,7 @@ __global__ void __launch_bounds__(TT) k_vtail(const TailArgs a, const TailPtrs<T
     if (threadIdx.x < 32)
       warp_bottom(Dd, a.cells + Lb.cell0, Lb.ncell[0] + Lb.ncell[1], a.ghosts + Lb.ghost0,
                   Lb.nghost[0] + Lb.nghost[1], a.wx64[m], a.wy64[m], a.wz64[m], a.D64[m], P.r[m], P.e[m], a.maxit,
-                  a.tol, a.iters ? a.iters + Dd.solve : nullptr, wb);
+                  a.tol, a.iters ? a.iters + Dd.solve : nullptr, wb, a.cg);
     __syncthreads();
   } else {
     const int m = Dd.mb;
@@ -382,7 +407,33 @@ __global__ void __launch_bounds__(TT) k_vtail(const TailArgs a, const TailPtrs<T
     const double r0 = norm(r);
     double rho_old = 1.0, alpha = 1.0, omega = 1.0;
     int it = 0;
-    if (r0 > 0.0) {
+    if (a.cg && r0 > 0.0) {  // conjugate gradients, v = A p
+      for (int i = threadIdx.x; i < nc; i += TT) p[cells[i].q] = r[cells[i].q];
+      __syncthreads();
+      double rho = dot(r, r);
+      for (it = 1; it <= a.maxit; ++it) {
+        apply(p, v);
+        const double pv = dot(p, v);
+        if (!(pv > 0.0)) { --it; break; }
+        const double al = rho / pv;
+        for (int i = threadIdx.x; i < nc; i += TT) {
+          const int64_t q = cells[i].q;
+          x[q] += al * p[q];
+          r[q] -= al * v[q];
+        }
+        __syncthreads();
+        if (norm(r) <= a.tol * r0) break;
+        const double rho_new = dot(r, r);
+        const double be = rho_new / rho;
+        rho = rho_new;
+        for (int i = threadIdx.x; i < nc; i += TT) {
+          const int64_t q = cells[i].q;
+          p[q] = r[q] + be * p[q];
+        }
+        __syncthreads();
+      }
+      if (it > a.maxit) it = a.maxit;
+    } else if (r0 > 0.0) {
       for (it = 1; it <= a.maxit; ++it) {
         const double rho = dot(rh, r);
         if (fabs(rho) < 1e-300) { --it; break; }
@@ -453,7 +504,8 @@ __global__ void __launch_bounds__(TT) k_vtail(const TailArgs a, const TailPtrs<T
     }
     __syncthreads();
     for (int it = 0; it < a.nu2; ++it)
-      for (int colour = 0; colour < 2; ++colour) {
+      for (int cc = 0; cc < 2; ++cc) {
+        const int colour = a.post_rev ? 1 - cc : cc;
         t_fill(L, a.ghosts, e, 1 - colour);
         __syncthreads();
         t_smooth(L, a.cells, e, r, P.wx[m], P.wy[m], P.wz[m], P.invD[m], colour);

@@ -41,7 +41,8 @@ class Params(C.Structure):
                 ("bottom_tol", C.c_double), ("precision", C.c_int), ("project_mean", C.c_int),
                 ("use_graph", C.c_int), ("profile", C.c_int), ("fused_coarse", C.c_int),
                 ("fused_sweep", C.c_int), ("ghost_push", C.c_int),
-                ("vector_smooth", C.c_int), ("pdl", C.c_int), ("fuse_residual_sweep", C.c_int)]
+                ("vector_smooth", C.c_int), ("pdl", C.c_int), ("fuse_residual_sweep", C.c_int),
+                ("krylov", C.c_int), ("bottom_solver", C.c_int), ("post_reverse", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -238,15 +239,17 @@ class Context:
         return (hi[2] - lo[2] + 1, hi[1] - lo[1] + 1, hi[0] - lo[0] + 1)
 
     # ---- workspace ------------------------------------------------------------
-    def workspace_bytes(self, precision=FP64):
+    def workspace_bytes(self, precision=FP64, krylov=False):
         n = C.c_size_t()
-        p = default_params(precision=precision)
+        p = default_params(precision=precision, krylov=int(bool(krylov)))
         self._check(self.L.gmg_workspace_size(self.h, C.byref(p), C.byref(n)))
         return n.value
 
-    def allocate(self, precision=FP64, device="cuda"):
+    def allocate(self, precision=FP64, device="cuda", krylov=False):
+        """Workspace for solves in `precision` (mixed sizes also serve FP64); krylov=True adds
+        the top-level Krylov vectors (params krylov = 1 or 2)."""
         import torch
-        nbytes = self.workspace_bytes(precision)
+        nbytes = self.workspace_bytes(precision, krylov)
         ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
         base = ws.data_ptr()
         off = (-base) % 256
