@@ -224,6 +224,8 @@ def measure_forms(stream, barrier, dev, only=None):
         forms["amr2"] = _form_amr2(stream, barrier, dev)
     if only in (None, "walls256"):
         forms["walls256"] = _form_walls256(stream, barrier)
+    if only in (None, "krylov"):
+        forms["krylov"] = _form_krylov(stream, barrier)
     return forms
 
 
@@ -293,6 +295,44 @@ def _form_walls256(stream, barrier):
                      "final_rel_resid": info.final_resid / info.rhs_norm}
     del ctx, rhs, phi, folded
     torch.cuda.empty_cache()
+    return res
+
+
+def _form_krylov(stream, barrier):
+    """Multigrid iteration vs multigrid-preconditioned BiCGStab and CG (symmetric V-cycle)
+    on abec256 and on the high-contrast contrast256, to 1e-10."""
+    import torch
+
+    from paper_2009_12009_gb300 import gmg
+    from paper_2009_12009_gb300 import inputs as I
+
+    res = {}
+    for cfg_fn in (I.abec256, I.contrast256):
+        cfg = cfg_fn()
+        ctx = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"], stream=stream.cuda_stream)
+        ctx.allocate(gmg.MIXED_FP32, krylov=True)
+        ctx.set_scalars(0.0, 1.0)
+        ctx.set_beta(torch.from_numpy(cfg["beta"]))
+        rhs = ctx.pack(torch.from_numpy(cfg["rhs"]))
+        name = cfg["name"]
+        del cfg
+        phi = ctx.field(0)
+        ctx.autotune(rhs, gmg.FP64)
+        ctx.autotune(rhs, gmg.MIXED_FP32)
+        out = {}
+        for label, kw in (("mg_fp64", dict(krylov=0)), ("bicgstab_fp64", dict(krylov=1)),
+                          ("cg_fp64", dict(krylov=2)), ("mg_fp32", dict(krylov=0, precision=gmg.MIXED_FP32)),
+                          ("bicgstab_fp32", dict(krylov=1, precision=gmg.MIXED_FP32))):
+            ms, info = _timed(lambda: ctx.solve(rhs, phi, tol_rel=TOL, max_iter=300, **kw)[1], 3, 1, stream, barrier)
+            vc = info.iterations * (2 if kw["krylov"] == 1 else 1)
+            out[label] = {"time_to_tol_ms": ms, "iterations": info.iterations, "vcycles": vc, "status": info.status,
+                          "final_rel_resid": info.final_resid / info.rhs_norm}
+        res[name] = out
+        del ctx, rhs, phi
+        torch.cuda.empty_cache()
+    res["workload"] = ("abec256 and contrast256 (256^3, 64 boxes; beta = exp(3 N(0,1)) filtered, seed 12016), tol "
+                       "1e-10: multigrid iteration, multigrid-preconditioned BiCGStab (2 V-cycles per iteration) "
+                       "and CG (symmetric V-cycle)")
     return res
 
 
@@ -411,7 +451,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the 512^3, batched and two-level workloads")
-    ap.add_argument("--only", choices=["abec512", "batch64", "amr2", "walls256"], default=None,
+    ap.add_argument("--only", choices=["abec512", "batch64", "amr2", "walls256", "krylov"], default=None,
                     help="run and print only this one of the other workloads (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -95,8 +95,8 @@ struct gmg_ctx {
   std::vector<LevelBufs> buf;
   double *alpha0 = nullptr, *bx0 = nullptr, *by0 = nullptr, *bz0 = nullptr, *tmp0 = nullptr;
   // top-level Krylov vectors (level-0 FP64, after everything else in the workspace when it
-  // was sized for them): b, r, rhat, p, v, y, s, t, z, zero
-  static constexpr int NKV = 10;
+  // was sized for them): b, r, rhat, p, v, y, s, t, z
+  static constexpr int NKV = 9;
   double* kv[NKV] = {};
   // per-problem device scalars
   unsigned long long* normbits = nullptr;  // [0, ns): outer residual norms; [ns, 2ns): rhs / step norms
@@ -126,6 +126,9 @@ struct gmg_ctx {
   std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int, int, int, int>,
            GraphEntry>
       graphs;
+  // preconditioner V-cycles of the top-level Krylov solvers, per (input, output, params)
+  std::map<std::tuple<const void*, void*, int, int, int, int, double, int, int, int, int, int, int>, GraphEntry>
+      kgraphs;
 
   // profiling events (pairs around finest-level smoother / outer residual launches)
   bool profiling = false;
@@ -187,6 +190,8 @@ namespace {
 void drop_graphs(gmg_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   c->graphs.clear();
+  for (auto& kv : c->kgraphs) cudaGraphExecDestroy(kv.second.exec);
+  c->kgraphs.clear();
 }
 
 // event pair k of a list (created on first use, outside any capture)
@@ -1495,7 +1500,7 @@ namespace {
 // workspace bytes of the top-level Krylov vectors
 size_t krylov_bytes(const gmg_ctx* c) {
   const size_t ne0 = c->L.empty() ? 0 : (size_t)c->L[0].nelem;
-  return 256 + gmg_ctx::NKV * (((8 * ne0) + 255) & ~(size_t)255);
+  return 256 + gmg_ctx::NKV * ((((8 * ne0) + 255) & ~(size_t)255) + 256);
 }
 
 // Krylov solve of A phi = rhs from phi = 0, preconditioned by one V-cycle per application
@@ -1517,7 +1522,7 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
   const int64_t ne = c->L[0].nelem;
   const int64_t l0 = kernel_launch_count();
   double *b = c->kv[0], *r = c->kv[1], *rh = c->kv[2], *pp = c->kv[3], *v = c->kv[4], *y = c->kv[5],
-         *sv = c->kv[6], *t = c->kv[7], *z = c->kv[8], *zero = c->kv[9];
+         *sv = c->kv[6], *t = c->kv[7], *z = c->kv[8];
   const bool sing = singular(c, 0);
   gmg_status st;
   auto host_sync = [&]() -> gmg_status {
@@ -1547,18 +1552,61 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
   auto axpby = [&](double al, const double* a, double be, const double* bb, double* out) {
     launch_axpby(ne, al, a, be, bb, out, s);
   };
-  auto precond = [&](const double* in, double* out) {  // out = V(in), e = 0 first
-    launch_convert(DT_F64, dt, in, c->buf[0].r[dt], ne, s);
-    vcycle(c, dt, 0, p, s);
-    launch_convert(dt, DT_F64, c->buf[0].e[dt], out, ne, s);
-    if (sing) project(out);
+  // out = V(in) on stream st: the V-cycle runs on in and out themselves in FP64 (the
+  // level-0 buffers are swapped for the call), on float or bfloat16 copies otherwise
+  auto precond_body = [&](const double* in, double* out, cudaStream_t st) {
+    LevelBufs& B0 = c->buf[0];
+    if (dt == DT_F64) {
+      void* const sr = B0.r[DT_F64];
+      void* const se = B0.e[DT_F64];
+      B0.r[DT_F64] = (void*)in;
+      B0.e[DT_F64] = out;
+      vcycle(c, dt, 0, p, st);
+      B0.r[DT_F64] = sr;
+      B0.e[DT_F64] = se;
+    } else {
+      launch_convert(DT_F64, dt, in, B0.r[dt], ne, st);
+      vcycle(c, dt, 0, p, st);
+      launch_convert(dt, DT_F64, B0.e[dt], out, ne, st);
+    }
+    if (sing) {
+      launch_sum(D0, out, c->partials, c->scal + 1, st);
+      launch_add_scalar(D0, out, c->scal + 1, -1.0, st);
+    }
+  };
+  int64_t graph_launches = 0;
+  auto precond = [&](const double* in, double* out) -> gmg_status {
+    if (!p.use_graph) {
+      precond_body(in, out, s);
+      return GMG_OK;
+    }
+    auto key = std::make_tuple((const void*)in, (void*)out, p.precision, p.nu1, p.nu2, p.bottom_max_iter, p.bottom_tol,
+                               p.fused_coarse, p.ghost_push, p.vector_smooth, p.bottom_solver, post_reversed(p) ? 1 : 0,
+                               p.pdl);
+    auto itg = c->kgraphs.find(key);
+    if (itg == c->kgraphs.end()) {
+      cudaGraph_t g;
+      cudaGraphExec_t ge;
+      const int64_t lc = kernel_launch_count();
+      CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      precond_body(in, out, c->cap_stream);
+      cudaError_t e1 = cudaStreamEndCapture(c->cap_stream, &g);
+      if (e1 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+      cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+      const int64_t nl = kernel_launch_count() - lc;
+      count_launches((int)-nl);  // captured, not launched
+      itg = c->kgraphs.emplace(key, gmg_ctx::GraphEntry{ge, nl, 0, 0}).first;
+    }
+    CK(c, cudaGraphLaunch(itg->second.exec, s));
+    graph_launches += itg->second.launches;
+    return GMG_OK;
   };
   auto apply = [&](double* in, double* out) {  // out = A in, homogeneous walls
     launch_fill(DT_F64, D0, in, -1, 0, s);
-    launch_residual(DT_F64, DT_F64, D0, in, zero, coefs64(c, 0), out, nullptr, nullptr, s);
-    launch_scale_valid(D0, out, -1.0, s);
+    launch_apply(D0, in, coefs64(c, 0), out, s);
   };
-  CK(c, cudaMemsetAsync(zero, 0, 8 * (size_t)ne, s));
   CK(c, cudaMemcpyAsync(b, rhs, 8 * (size_t)ne, cudaMemcpyDeviceToDevice, s));
   double bnorm;
   if ((st = norm(b, &bnorm))) return st;
@@ -1591,9 +1639,8 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
       if ((st = dot(rh, r, &rho))) return st;
       if (std::fabs(rho) < 1e-300) { --it; break; }
       const double beta = (rho / rho_old) * (alpha / omega);
-      axpby(1.0, pp, -omega, v, pp);  // p = r + beta (p - omega v)
-      axpby(1.0, r, beta, pp, pp);
-      precond(pp, y);
+      launch_bicg_direction(ne, r, pp, v, beta, omega, s);  // p = r + beta (p - omega v)
+      if ((st = precond(pp, y))) return st;
       apply(y, v);
       double rv;
       if ((st = dot(rh, v, &rv))) return st;
@@ -1608,15 +1655,14 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
         hist.push_back(rn);
         break;
       }
-      precond(sv, z);
+      if ((st = precond(sv, z))) return st;
       apply(z, t);
       double tt, ts;
       if ((st = dot(t, t, &tt))) return st;
       if (tt == 0.0) { --it; break; }
       if ((st = dot(t, sv, &ts))) return st;
       omega = ts / tt;
-      axpby(1.0, x, alpha, y, x);
-      axpby(1.0, x, omega, z, x);
+      launch_add2(ne, x, alpha, y, omega, z, s);
       axpby(1.0, sv, -omega, t, r);
       if ((st = norm(r, &rn))) return st;
       hist.push_back(rn);
@@ -1627,7 +1673,7 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
       rho_old = rho;
     }
   } else {
-    precond(r, z);
+    if ((st = precond(r, z))) return st;
     CK(c, cudaMemcpyAsync(pp, z, 8 * (size_t)ne, cudaMemcpyDeviceToDevice, s));
     double rho;
     if ((st = dot(r, z, &rho))) return st;
@@ -1647,7 +1693,7 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
         break;
       }
       if (rn <= target) break;
-      precond(r, z);
+      if ((st = precond(r, z))) return st;
       double rho_new;
       if ((st = dot(r, z, &rho_new))) return st;
       const double beta = rho_new / rho;
@@ -1673,7 +1719,7 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
     info->hist_len = (int)std::min<size_t>(hist.size(), 256);
     for (int i = 0; i < info->hist_len; ++i) info->resid_hist[i] = hist[i];
     info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    info->kernel_launches = kernel_launch_count() - l0;
+    info->kernel_launches = kernel_launch_count() - l0 + graph_launches;
   }
   if (result == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
   return result;
@@ -2161,8 +2207,12 @@ gmg_status gmg_set_workspace(gmg_ctx* c, void* dptr, size_t bytes) {
   // the Krylov vectors, if the workspace holds them after the rest
   const size_t ne0 = (size_t)c->L[0].nelem;
   const bool kr = bytes >= used + krylov_bytes(c);
+  // the V-cycle outputs y (5) and z (8) are read with their ghosts (plain placement); the
+  // others start their rows' valid cells on a 128-byte line (see Carver::take_rows)
+  const size_t stride = (((8 * ne0) + 255) & ~(size_t)255) + 256;
   for (int q = 0; q < gmg_ctx::NKV; ++q)
-    c->kv[q] = kr ? (double*)((char*)dptr + ((used + 255) & ~(size_t)255) + (size_t)q * (((8 * ne0) + 255) & ~(size_t)255))
+    c->kv[q] = kr ? (double*)((char*)dptr + ((used + 255) & ~(size_t)255) + (size_t)q * stride +
+                              ((q == 5 || q == 8) ? 0 : 64))
                   : nullptr;
   CK(c, cudaMemsetAsync(c->ws, 0, c->ws_bytes, c->stream));
   st = upload_tables(c);

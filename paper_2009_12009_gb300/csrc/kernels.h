@@ -204,4 +204,11 @@ void launch_wall_values(const LevelDev& L, int nboxes, int max_face_cells, int f
                         const double* w, const double* g, int mode, double* f, const double* lam, double* dg,
                         cudaStream_t s);
 
+// Top-level Krylov vector kernels (krylov.cu): out = A in (ghosts of in filled first,
+// FP64 coefficients); p = r + beta (p - omega v); x += a y + b z (flat, n elements).
+void launch_apply(const LevelDev& L, const double* in, const Coefs& c64, double* out, cudaStream_t s);
+void launch_bicg_direction(int64_t n, const double* r, double* p, const double* v, double beta, double omega,
+                           cudaStream_t s);
+void launch_add2(int64_t n, double* x, double a, const double* y, double b, const double* z, cudaStream_t s);
+
 }  // namespace gmg

@@ -23,7 +23,7 @@ DIRICHLET = 1
 NEUMANN = 2
 
 SEEDS = {"poisson32": 12010, "abec256": 12011, "abec512": 12012, "batch64": 12013, "amr2": 12014,
-         "walls256": 12015}
+         "walls256": 12015, "contrast256": 12016}
 BATCH_EDGES = (32, 48, 64, 96, 128, 160)
 
 
@@ -118,6 +118,20 @@ def abec256():
 
 def abec512():
     return abec(512, 128, SEEDS["abec512"], name="abec512")
+
+
+def contrast256():
+    """The abec256 recipe with a high-contrast coefficient: beta = exp(3 N(0,1)) before the
+    3x3x3 mean filter (spans ~8 decades), where the multigrid iteration alone needs ~150
+    V-cycles and Krylov acceleration pays."""
+    n = 256
+    rng = np.random.default_rng(SEEDS["contrast256"])
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    shape = (n, n, n)
+    beta = box_mean_filter(np.exp(3.0 * rng.standard_normal(shape)), False)
+    rhs = rng.standard_normal(shape)
+    return dict(name="contrast256", domain=dom, boxes=chop(*dom, 64), bc_lo=[DIRICHLET] * 3, bc_hi=[DIRICHLET] * 3,
+                a=0.0, b=1.0, alpha=None, beta=beta, rhs=rhs)
 
 
 def face_shape(domain, face):
