@@ -109,6 +109,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def source_text(names):
+    """Bytes of the listed csrc sources; "file#Name" stands for the text of `struct Name`
+    in that file (up to its closing "};")."""
+    out = b""
+    for name in names:
+        fname, _, sym = name.partition("#")
+        with open(os.path.join(ROOT, "paper_2009_12009_gb300", "csrc", fname), "rb") as f:
+            text = f.read()
+        if sym:
+            start = text.index(b"struct " + sym.encode() + b" {")
+            text = text[start:text.index(b"\n};", start) + 4]
+        out += text
+    return out
+
+
 def kernel_traffic(kernel):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the sources it
     was measured on (the kernel and the workspace placement) are the current ones (else None)."""
@@ -117,10 +132,7 @@ def kernel_traffic(kernel):
         return None
     with open(path) as f:
         rec = json.load(f)
-    h = hashlib.sha256()
-    for name in rec.get("sources", []):
-        with open(os.path.join(ROOT, "paper_2009_12009_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+    h = hashlib.sha256(source_text(rec.get("sources", [])))
     if not rec.get("sources") or h.hexdigest()[:16] != rec.get("sources_sha256_16"):
         return None
     return rec.get("dram_bytes_per_launch_full_size")
