@@ -110,16 +110,17 @@ class ClockSampler:
 
 
 def source_text(names):
-    """Bytes of the listed csrc sources; "file#Name" stands for the text of `struct Name`
-    in that file (up to its closing "};")."""
+    """Bytes of the listed csrc sources; "file#text" stands for the definition in that file
+    that starts at the first occurrence of `text` and ends at the next closing brace in
+    column 0 (a function, or a struct with its ";")."""
     out = b""
     for name in names:
         fname, _, sym = name.partition("#")
         with open(os.path.join(ROOT, "paper_2009_12009_gb300", "csrc", fname), "rb") as f:
             text = f.read()
         if sym:
-            start = text.index(b"struct " + sym.encode() + b" {")
-            text = text[start:text.index(b"\n};", start) + 4]
+            start = text.index(sym.encode())
+            text = text[start:text.index(b"\n}", start) + 3]
         out += text
     return out
 
