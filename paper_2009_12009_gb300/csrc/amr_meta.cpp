@@ -51,6 +51,20 @@ std::string build_amr(const LevelMeta& C, LevelMeta& F, AmrHost& A) {
           }
         }
   }
+  // ghost elements of the coarse level take the covered flag of the cell they copy, so a
+  // kernel that looks at a neighbour across a coarse box face sees whether it is covered
+  for (const GhostRect& g : C.ghosts) {
+    if (g.kind != 0) continue;
+    const DevBox& Dd = C.dbox[g.dst_box];
+    const DevBox& Ds = C.dbox[g.src_box];
+    for (int v = 0; v < g.n2; ++v)
+      for (int u = 0; u < g.n1; ++u) {
+        int dl[3] = {g.dst[0], g.dst[1], g.dst[2]}, sl[3] = {g.src[0], g.src[1], g.src[2]};
+        dl[g.d1] += u; dl[g.d2] += v;
+        sl[g.d1] += u; sl[g.d2] += v;
+        A.covered[elem_index(Dd, dl[0], dl[1], dl[2])] = A.covered[elem_index(Ds, sl[0], sl[1], sl[2])];
+      }
+  }
   // coarse/fine ghosts of the fine level
   A.cfidx.assign(F.nelem, -1);
   for (const CfSlab& S : F.cf_slabs) {

@@ -297,3 +297,58 @@ def test_composite_iteration_contracts(orc, bc):
     rf[sl] = a["rhs_f"]
     pc, pf, it, hist, st = P.solve(a["rhs_c"], rf, tol_rel=1e-10, maxit=100)
     assert st == 0 and it <= 14, (it, hist[1:] / hist[:-1])
+
+
+# --------------------------------------------------------------- several fine patches
+
+
+def two_patches(orc, bc=P_, shifted=False):
+    """16^3 level 0 (boxes of 8^3) with two disjoint refined patches: coarse [2,6)^3 (one fine
+    box) and coarse [10,14) x [2,6) x [8,12) (two fine boxes, split along x), or, shifted,
+    the second patch moved so the two face each other across a two-cell coarse gap."""
+    n = 16
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    fb = [((4, 4, 4), (11, 11, 11))]
+    if shifted:
+        fb += [((16, 4, 4), (19, 11, 11)), ((20, 4, 4), (23, 11, 11))]
+    else:
+        fb += [((20, 4, 16), (23, 11, 23)), ((24, 4, 16), (27, 11, 23))]
+    return orc.AmrProblem(dom, I.chop(*dom, 8), fb, [bc] * 3, [bc] * 3)
+
+
+@pytest.mark.parametrize("bc", [P_, N_])
+@pytest.mark.parametrize("shifted", [False, True], ids=["apart", "facing"])
+def test_patches_constants_and_conservation(orc, bc, shifted):
+    """Two refined patches, a = 0 without Dirichlet walls: constants are in the null space
+    and sum of volume x (A x) = 0 (refluxing on every patch's coarse/fine faces)."""
+    P = two_patches(orc, bc, shifted)
+    rng = np.random.default_rng(11)
+    rand_coeffs(P, rng)
+    yc, yf = P.apply(np.full(P.coarse_shape, 2.0), np.full(P.fine_shape, 2.0))
+    assert max(np.abs(yc).max(), np.abs(yf).max()) <= 1e-10
+    V = P.volumes()
+    for _ in range(3):
+        y = P.pack(*P.apply(rng.standard_normal(P.coarse_shape), rng.standard_normal(P.fine_shape)))
+        assert abs(V @ y) <= 1e-13 * (V @ np.abs(y))
+
+
+@pytest.mark.parametrize("bc", [P_, D_, N_])
+def test_patches_transpose_and_lapack(orc, bc):
+    """Two refined patches: <A x, y> = <x, A^T y>, and the composite multigrid iteration
+    reaches LAPACK's solution of the assembled composite system."""
+    P = two_patches(orc, bc)
+    rng = np.random.default_rng(12)
+    rand_coeffs(P, rng, a=1.0 if bc == D_ else 0.0)
+    m = P.pack(np.zeros(P.coarse_shape), np.zeros(P.fine_shape)).size
+    x, y = rng.standard_normal(m), rng.standard_normal(m)
+    Ax = P.pack(*P.apply(*P.unpack(x)))
+    ATy = P.pack(*P.apply(*P.unpack(y), transpose=True))
+    assert abs(Ax @ y - x @ ATy) <= 1e-12 * np.abs(Ax).max() * np.abs(y).sum()
+    rhs = rng.standard_normal(m)
+    if bc != D_:
+        V = P.volumes()
+        rhs = rhs - (V @ rhs) / V.sum()
+    pc, pf, it, hist, st = P.solve(*P.unpack(rhs), tol_rel=1e-13, maxit=200)
+    assert st == 0
+    want = lapack_solve(P, rhs)
+    assert np.abs(P.pack(pc, pf) - want).max() <= 1e-10 * np.abs(want).max()
