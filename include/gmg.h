@@ -146,6 +146,10 @@ typedef struct {
                            operator is symmetric) */
   int post_reverse;     /* 1: post-smoothing sweeps take black before red, the reverse of
                            pre-smoothing (a symmetric V-cycle); 0 (default): red first */
+  int fuse_correction;  /* 1 (default): in the multigrid iteration, the last colour pass of
+                           the finest level's post-smoothing also adds the correction to phi
+                           (one pass over phi and e fewer per iteration); 0: separate.  Same
+                           results. */
 } gmg_params;
 
 typedef struct {

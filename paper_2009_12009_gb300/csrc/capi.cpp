@@ -123,7 +123,7 @@ struct gmg_ctx {
     int64_t launches;
     int n_ev_smooth, n_ev_resid;  // profiling event pairs recorded per replay
   };
-  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int, int, int, int>,
+  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int, int, int, int, int>,
            GraphEntry>
       graphs;
   // preconditioner V-cycles of the top-level Krylov solvers, per (input, output, params)
@@ -683,8 +683,11 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
 // red_done: the first red half-sweep was done by the residual kernel (level 0)
 // reverse: black before red in every sweep (post-smoothing of the symmetric V-cycle; the
 // fused sweep, red first by construction, is not used then)
+// phi_last (finest level, red-first order): the last (black) pass also adds e to phi
+// (k_smooth_update), pushing phi's new values into its ghosts if push_phi
 void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s,
-                   bool e_zero = false, bool push = false, bool red_done = false, bool reverse = false) {
+                   bool e_zero = false, bool push = false, bool red_done = false, bool reverse = false,
+                   double* phi_last = nullptr, bool push_phi = false) {
   if (reverse) {
     for (int it = 0; it < nsweep; ++it) {
       smooth_colour(c, D, dt, m, 1, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
@@ -709,7 +712,17 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
   }
   for (int it = 0; it < nsweep; ++it) {
     if (!(red_done && it == 0)) smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
-    smooth_colour(c, D, dt, m, 1, s, true, push, vec_on(c, p, dt, m));
+    if (phi_last && it == nsweep - 1) {
+      const LevelBufs& B = c->buf[m];
+      if (!push) launch_fill(dt, D, B.e[dt], 0, 0, s);
+      const bool prof = c->profiling && m == 0;
+      cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
+      if (prof) record_timing_event(c, ev[0], s);
+      launch_smooth_update(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, phi_last, push_phi, s);
+      if (prof) record_timing_event(c, ev[1], s);
+    } else {
+      smooth_colour(c, D, dt, m, 1, s, true, push, vec_on(c, p, dt, m));
+    }
   }
 }
 
@@ -784,7 +797,10 @@ void choose_pdl(const gmg_params& p, cudaStream_t s) {
   set_pdl(p.pdl == 1 || (p.pdl == 2 && cs == cudaStreamCaptureStatusNone));
 }
 
-void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool red_done = false) {
+// phi_update (finest level only, see fuse_correction_on): the last post-smoothing pass also
+// adds e to phi
+void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool red_done = false,
+            double* phi_update = nullptr, bool push_phi = false) {
   choose_pdl(p, s);
   const bool fused = tail_on(c, p, dt) && c->tail_ok;
   const LevelDev D = fused ? vc_view(c, m) : c->dev[m];
@@ -808,7 +824,7 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
   vcycle(c, dt, m + 1, p, s, false);
   launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
-  smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, post_reversed(p));
+  smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, post_reversed(p), phi_update, push_phi);
 }
 
 // Whether the outer residual also performs the first red half-sweep of the next V-cycle
@@ -822,16 +838,26 @@ bool resid_red(const gmg_ctx* c, const gmg_params& p, int dt) {
 bool level0_push(const gmg_ctx* c, const gmg_params& p, int dt) {
   return push_on(c, p, dt, 0) && c->dev[0].push_ok;
 }
+// Whether the last post-smoothing pass on level 0 (black, red-first order) can also add the
+// correction to phi: every level-0 box smooths there (no problem has level 0 as its
+// bottom) with the two-pass sweep.
+bool fuse_correction_on(const gmg_ctx* c, const gmg_params& p, int dt) {
+  const LevelDev& D = c->dev[0];
+  return p.fuse_correction != 0 && p.nu2 > 0 && !post_reversed(p) && nlev(c) > 1 && D.n_pair_chunks > 0 &&
+         D.n_pair_chunks == D.n_pair_all_chunks && !(p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0);
+}
 
 // One outer iteration: e = V(r); phi += e; r = rhs - A phi with per-problem ||r||_inf into
 // normbits[0, ns), copied to the pinned host mirror.
 void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const gmg_params& p, cudaStream_t s) {
   const int ns = c->ns();
   const bool rr = resid_red(c, p, dt);
-  vcycle(c, dt, 0, p, s, rr);  // (sets the dependent-launch switch for the launches below too)
   // phi's ghosts stay current by push (they were filled, or zero, before the first update)
   const bool push = p.ghost_push != 0 && c->dev[0].push_ok;
-  launch_add_correction(dt, c->dev[0], phi, c->buf[0].e[dt], s, push);
+  const bool fc = fuse_correction_on(c, p, dt);
+  // (sets the dependent-launch switch for the launches below too)
+  vcycle(c, dt, 0, p, s, rr, fc ? phi : nullptr, push);
+  if (!fc) launch_add_correction(dt, c->dev[0], phi, c->buf[0].e[dt], s, push);
   if (!push) launch_fill(DT_F64, c->dev[0], phi, -1, 0, s);
   cudaMemsetAsync(c->normbits, 0, 8 * (size_t)ns, s);
   cudaEvent_t* ev = c->profiling ? ev_pair(c->ev_resid, c->n_ev_resid++) : nullptr;
@@ -876,6 +902,8 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.krylov < 0 || p.krylov > 2) SETERR(c, GMG_ERR_BAD_INPUT, "krylov must be 0, 1 or 2");
   if (p.bottom_solver != 0 && p.bottom_solver != 1) SETERR(c, GMG_ERR_BAD_INPUT, "bottom_solver must be 0 or 1");
   if (p.post_reverse != 0 && p.post_reverse != 1) SETERR(c, GMG_ERR_BAD_INPUT, "post_reverse must be 0 or 1");
+  if (p.fuse_correction != 0 && p.fuse_correction != 1)
+    SETERR(c, GMG_ERR_BAD_INPUT, "fuse_correction must be 0 or 1");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
   return GMG_OK;
 }
@@ -968,7 +996,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
     auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
                                p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep, p.ghost_push,
                                p.vector_smooth, p.pdl, p.fuse_residual_sweep, p.bottom_solver,
-                               p.post_reverse);
+                               p.post_reverse, p.fuse_correction);
     auto itg = c->graphs.find(key);
     if (itg != c->graphs.end()) {
       gexec = itg->second.exec;
@@ -1808,6 +1836,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->krylov = 0;
   p->bottom_solver = 0;
   p->post_reverse = 0;
+  p->fuse_correction = 1;
   return GMG_OK;
 }
 

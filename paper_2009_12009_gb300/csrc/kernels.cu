@@ -188,6 +188,59 @@ __global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ box
   if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, s);
 }
 
+// The last colour pass of a V-cycle's post-smoothing on the finest level fused with the
+// solution update: the thread updates the cell of the colour as k_smooth does (storing e),
+// then adds both cells' corrections of its pair to phi -- the other cell's e is final
+// (the other colour went before) -- and pushes phi's new values into the ghosts that copy
+// them (push_phi non-null).  The same values as the colour pass followed by
+// k_add_correction (each correction added as stored), one pass fewer over phi and e.
+template <class T>
+__global__ void __launch_bounds__(BLOCK)
+    k_smooth_update(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks, T* e, const T* __restrict__ rhs,
+                    const typename CoefOf<T>::type* __restrict__ wx, const typename CoefOf<T>::type* __restrict__ wy,
+                    const typename CoefOf<T>::type* __restrict__ wz, const typename CoefOf<T>::type* __restrict__ invD,
+                    int colour, const int* __restrict__ active, double* phi, const PushFace* __restrict__ push_phi) {
+  pdl_enter();
+  using A = typename Arith<T>::type;
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  if (active && !active[B.solve]) return;
+  const int t = ch.start + threadIdx.x;
+  if (t >= ((B.nx + 1) >> 1) * B.ny * B.nz) return;
+  int i0, j, k;
+  pair_decode(B, t, i0, j, k);
+  const int par = (B.lo[0] + B.lo[1] + B.lo[2] + i0 + j + k + colour) & 1;
+  const int i = i0 + par;
+  const int64_t q0 = elem_index(B, i0, j, k);
+  const int64_t sx = B.sx, sy = B.sy;
+  if (i < B.nx) {
+    const int64_t q = q0 + par;
+    A s = ldg(rhs + q);
+    s = fma((A)ldg(wx + q), (A)ld(e + q - 1), s);
+    s = fma((A)ldg(wx + q + 1), (A)ld(e + q + 1), s);
+    s = fma((A)ldg(wy + q), (A)ld(e + q - sx), s);
+    s = fma((A)ldg(wy + q + sx), (A)ld(e + q + sx), s);
+    s = fma((A)ldg(wz + q), (A)ld(e + q - sy), s);
+    s = fma((A)ldg(wz + q + sy), (A)ld(e + q + sy), s);
+    s = s * (A)ldg(invD + q);
+    st(e + q, s);
+  }
+  if (i0 + 1 < B.nx) {
+    double2 p = *reinterpret_cast<const double2*>(phi + q0);
+    p.x += (double)ld(e + q0);
+    p.y += (double)ld(e + q0 + 1);
+    *reinterpret_cast<double2*>(phi + q0) = p;
+    if (push_phi) {
+      push_ghosts(B, ch.item, boxes, push_phi, phi, i0, j, k, p.x);
+      push_ghosts(B, ch.item, boxes, push_phi, phi, i0 + 1, j, k, p.y);
+    }
+  } else {
+    const double v = phi[q0] + (double)ld(e + q0);
+    phi[q0] = v;
+    if (push_phi) push_ghosts(B, ch.item, boxes, push_phi, phi, i0, j, k, v);
+  }
+}
+
 // Four consecutive cells (x), 16-byte aligned: 128-bit loads for float, 64-bit for bfloat16.
 __device__ __forceinline__ void ld4(const float* p, float v[4]) {
   const float4 a = *reinterpret_cast<const float4*>(p);
@@ -728,6 +781,17 @@ void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, 
   ++g_launches;
   GMG_DISPATCH(dt, launch_pdl(k_fill<T>, grid_of(L.n_ghost_chunks), BLOCK, 0, s, L.boxes, L.ghosts, L.ghost_chunks,
                                (T*)f, colour, copy_mode, L.active));
+}
+
+void launch_smooth_update(int dt, const LevelDev& L, void* e, const void* rhs, const Coefs& c, int colour,
+                          double* phi, bool push_phi, cudaStream_t s) {
+  if (!L.n_pair_chunks) return;
+  ++g_launches;
+  const PushFace* pf = push_phi ? L.push_faces : nullptr;
+  GMG_DISPATCH(dt, launch_pdl(k_smooth_update<T>, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks,
+                              (T*)e, (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
+                              (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
+                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, phi, pf));
 }
 
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour, cudaStream_t s,

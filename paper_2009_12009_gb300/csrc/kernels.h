@@ -100,6 +100,10 @@ void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void
 // (push: also write the new phi into the ghost cells that copy it, L.push_ok levels only)
 void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s,
                            bool push = false);
+// the last colour pass of the finest level's post-smoothing fused with phi += e on every
+// smoothed cell (pair work list); push_phi: also write phi's new values into its ghosts
+void launch_smooth_update(int dt, const LevelDev& L, void* e, const void* rhs, const Coefs& c, int colour,
+                          double* phi, bool push_phi, cudaStream_t s);
 // dense (nz,ny,nx) double over the level's (single-solve) domain <-> boxed type dt
 void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const double* dense, void* boxed,
                  cudaStream_t s);

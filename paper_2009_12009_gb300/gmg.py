@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("use_graph", C.c_int), ("profile", C.c_int), ("fused_coarse", C.c_int),
                 ("fused_sweep", C.c_int), ("ghost_push", C.c_int),
                 ("vector_smooth", C.c_int), ("pdl", C.c_int), ("fuse_residual_sweep", C.c_int),
-                ("krylov", C.c_int), ("bottom_solver", C.c_int), ("post_reverse", C.c_int)]
+                ("krylov", C.c_int), ("bottom_solver", C.c_int), ("post_reverse", C.c_int),
+                ("fuse_correction", C.c_int)]
 
 
 class SolveInfo(C.Structure):
