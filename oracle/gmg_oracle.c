@@ -1239,22 +1239,17 @@ static int box_of_index(const olev* l, int64_t q) {
   return b;
 }
 
-void* orc_amr_create(const int* dlo, const int* dhi, const int* bclo, const int* bchi, const double* plo,
-                     const double* phi_, int nbc, const int* cboxes, int nbf, const int* fboxes) {
-  oamr* A = (oamr*)calloc(1, sizeof(oamr));
-  A->C = (oprob*)orc_create(dlo, dhi, bclo, bchi, plo, phi_, nbc, cboxes);
-  int fdlo[3], fdhi[3];
-  for (int d = 0; d < 3; ++d) { fdlo[d] = 2 * dlo[d]; fdhi[d] = 2 * dhi[d] + 1; }
-  A->F = A->C ? (oprob*)orc_create(fdlo, fdhi, bclo, bchi, plo, phi_, nbf, fboxes) : NULL;
-  if (!A->C || !A->F) { orc_destroy(A->C); orc_destroy(A->F); free(A); return NULL; }
+/* Tables of a coarse/fine pair (A->C level 0 coarse, A->F level 0 fine, ratio 2): covered
+   coarse cells, the fine ghost-map entry of every fine ghost slot, and the coarse/fine ghosts
+   of the fine level with their interpolation stencils.  Returns -1 when the fine boxes are
+   not ratio-2 aligned and at least 2 cells wide, or when a coarse/fine ghost's stencil
+   needs a coarse cell that the coarse level lacks or that is covered. */
+static int amr_build_pair(oamr* A) {
   olev* c = &A->C->L[0];
   olev* f = &A->F->L[0];
-  /* fine boxes must be ratio-2 aligned and at least 2 cells wide */
   for (int b = 0; b < f->nb; ++b)
     for (int d = 0; d < 3; ++d)
-      if (pmod(f->lo[3 * b + d], 2) || pmod(f->hi[3 * b + d] + 1, 2) || bn(f, b, d) < 2) {
-        orc_destroy(A->C); orc_destroy(A->F); free(A); return NULL;
-      }
+      if (pmod(f->lo[3 * b + d], 2) || pmod(f->hi[3 * b + d] + 1, 2) || bn(f, b, d) < 2) return -1;
   A->covered = (char*)calloc(c->ntot, 1);
   for (int b = 0; b < c->nb; ++b)
     for (int k = 0; k < bn(c, b, 2); ++k)
@@ -1312,14 +1307,30 @@ void* orc_amr_create(const int* dlo, const int* dhi, const int* bclo, const int*
       G->cw[0] -= st * st;
     }
     for (int e2 = 0; e2 < 5; ++e2)
-      if (G->cq[e2] < 0 || A->covered[G->cq[e2]]) { /* interpolation must use uncovered coarse cells */
-        orc_destroy(A->C); orc_destroy(A->F); free(A->covered); free(A->cf); free(A->cfidx); free(A->gentry); free(A);
-        return NULL;
-      }
+      if (G->cq[e2] < 0 || A->covered[G->cq[e2]]) return -1; /* interpolation must use uncovered coarse cells */
     A->cfidx[gq] = n;
     ++n;
   }
   A->ncf = n;
+  return 0;
+}
+
+static void amr_free_tables(oamr* A) {
+  free(A->covered); free(A->cf); free(A->cfidx); free(A->gentry);
+  A->covered = NULL; A->cf = NULL; A->cfidx = NULL; A->gentry = NULL;
+}
+
+void* orc_amr_create(const int* dlo, const int* dhi, const int* bclo, const int* bchi, const double* plo,
+                     const double* phi_, int nbc, const int* cboxes, int nbf, const int* fboxes) {
+  oamr* A = (oamr*)calloc(1, sizeof(oamr));
+  A->C = (oprob*)orc_create(dlo, dhi, bclo, bchi, plo, phi_, nbc, cboxes);
+  int fdlo[3], fdhi[3];
+  for (int d = 0; d < 3; ++d) { fdlo[d] = 2 * dlo[d]; fdhi[d] = 2 * dhi[d] + 1; }
+  A->F = A->C ? (oprob*)orc_create(fdlo, fdhi, bclo, bchi, plo, phi_, nbf, fboxes) : NULL;
+  if (!A->C || !A->F || amr_build_pair(A) != 0) {
+    orc_destroy(A->C); orc_destroy(A->F); amr_free_tables(A); free(A);
+    return NULL;
+  }
   A->a = 0.0;
   A->b = 1.0;
   A->nu1 = 2;
@@ -1332,7 +1343,7 @@ void orc_amr_destroy(void* vp) {
   if (!A) return;
   orc_destroy(A->C);
   orc_destroy(A->F);
-  free(A->covered); free(A->cf); free(A->cfidx); free(A->gentry);
+  amr_free_tables(A);
   free(A);
 }
 
@@ -1922,5 +1933,398 @@ void orc_amr_grad_beta_cells(void* vp, const double* phic_d, const double* phif_
     free(v[w][0]);
     free(v[w][1]);
     for (int d = 0; d < 3; ++d) free(g[w][d]);
+  }
+}
+
+/* =====================================================================
+ * Several AMR levels (Sec. "Linear Solvers": multi-AMR-level geometric multigrid; Sec.
+ * "Operations between levels").  Level 0 covers the domain; level l (1 <= l < L) is a
+ * BoxArray at ratio 2 to level l-1, properly nested in it (its coarse/fine interpolation
+ * stencils find uncovered level-(l-1) cells).  The unknowns are the cells of every level
+ * not covered by the next finer one.  A cell's row is the level's 7-point operator with:
+ * neighbours in the level's own boxes or its periodic images; wall ghosts by the wall rule;
+ * coarse/fine ghosts interpolated from the next coarser level (the quadratic of the
+ * two-level form); and, on a face shared with a cell covered by the next finer level, the
+ * mean of the 4 fine fluxes through it (refluxing).  Each consecutive pair of levels keeps
+ * the two-level tables (oamr, built by amr_build_pair, not owning its levels).
+ * ===================================================================== */
+
+#define ORC_MAXAMR 4
+
+typedef struct {
+  int L;
+  oprob* P[ORC_MAXAMR];            /* level l as a one-level problem on its BoxArray */
+  oamr pair[ORC_MAXAMR - 1];       /* pair[l]: C = P[l], F = P[l+1] */
+  int64_t* gentry[ORC_MAXAMR];     /* level l's ghost slot -> its ghost-map entry, or -1 */
+  double a, b;
+  int nu1, nu2;
+} omlv;
+
+void orc_mlv_destroy(void* vp) {
+  omlv* M = (omlv*)vp;
+  if (!M) return;
+  for (int l = 0; l + 1 < M->L; ++l) amr_free_tables(&M->pair[l]);
+  for (int l = 0; l < M->L; ++l) {
+    orc_destroy(M->P[l]);
+    free(M->gentry[l]);
+  }
+  free(M);
+}
+
+/* L levels; nboxes[l] boxes of level l at boxes[6 * (sum of earlier nboxes) ...] in level
+   l's index space (lo[3], hi[3] inclusive).  NULL when a level's boxes are invalid or not
+   properly nested. */
+void* orc_mlv_create(const int* dlo, const int* dhi, const int* bclo, const int* bchi, const double* plo,
+                     const double* phi_, int L, const int* nboxes, const int* boxes) {
+  if (L < 1 || L > ORC_MAXAMR) return NULL;
+  omlv* M = (omlv*)calloc(1, sizeof(omlv));
+  M->L = L;
+  int off = 0;
+  int ok = 1;
+  for (int l = 0; l < L && ok; ++l) {
+    int ldlo[3], ldhi[3];
+    for (int d = 0; d < 3; ++d) {
+      ldlo[d] = dlo[d] << l;
+      ldhi[d] = ((dhi[d] + 1) << l) - 1;
+    }
+    M->P[l] = (oprob*)orc_create(ldlo, ldhi, bclo, bchi, plo, phi_, nboxes[l], boxes + 6 * off);
+    off += nboxes[l];
+    if (!M->P[l]) ok = 0;
+  }
+  for (int l = 0; l + 1 < L && ok; ++l) {
+    M->pair[l].C = M->P[l];
+    M->pair[l].F = M->P[l + 1];
+    if (amr_build_pair(&M->pair[l]) != 0) ok = 0;
+  }
+  if (!ok) {
+    orc_mlv_destroy(M);
+    return NULL;
+  }
+  for (int l = 0; l < L; ++l) {
+    olev* f = &M->P[l]->L[0];
+    M->gentry[l] = (int64_t*)malloc(sizeof(int64_t) * f->ntot);
+    for (int64_t q = 0; q < f->ntot; ++q) M->gentry[l][q] = -1;
+    for (int64_t e = 0; e < f->ng; ++e) M->gentry[l][f->gdst[e]] = e;
+  }
+  M->a = 0.0;
+  M->b = 1.0;
+  M->nu1 = 2;
+  M->nu2 = 2;
+  return M;
+}
+
+int orc_mlv_nlevels(void* vp) { return ((omlv*)vp)->L; }
+void* orc_mlv_level(void* vp, int l) { return ((omlv*)vp)->P[l]; }
+/* covered flags of level l (boxed), l < L - 1 */
+void orc_mlv_covered(void* vp, int l, char* out) {
+  omlv* M = (omlv*)vp;
+  memcpy(out, M->pair[l].covered, M->P[l]->L[0].ntot);
+}
+
+/* Coefficients per level (dense over each level's domain; NULL alpha: 1; NULL beta: 1).  A
+   face of level l on its coarse/fine boundary takes its fine cell's beta; then, from the
+   finest pair down, the faces and alphas of level l under level l + 1 are averaged from it
+   (the coefficient restriction of the two-level form). */
+int orc_mlv_set_coeffs(void* vp, double a, double bsc, const double* const* alpha, const double* const* beta) {
+  omlv* M = (omlv*)vp;
+  M->a = a;
+  M->b = bsc;
+  for (int l = 0; l < M->L; ++l) orc_set_coeffs(M->P[l], a, bsc, alpha ? alpha[l] : NULL, beta ? beta[l] : NULL);
+  for (int l = 1; l < M->L; ++l) {  /* coarse/fine faces of level l: the fine cell's beta */
+    oamr* A = &M->pair[l - 1];
+    olev* f = &A->F->L[0];
+    double* face[3] = {f->bx, f->by, f->bz};
+    const double* bf = beta ? beta[l] : NULL;
+    for (int64_t q = 0; q < A->ncf; ++q) {
+      const ocfghost* G = &A->cf[q];
+      int b = box_of_index(f, G->dst);
+      int64_t nx = bn(f, b, 0) + 2, ny = bn(f, b, 1) + 2;
+      int64_t diff = G->f1 - G->dst;
+      int d = (diff == 1 || diff == -1) ? 0 : ((diff == nx || diff == -nx) ? 1 : 2);
+      int64_t slot = diff > 0 ? G->f1 : G->dst;
+      int64_t rel = G->f1 - f->off[b];
+      int g[3] = {f->lo[3 * b] + (int)(rel % nx) - 1, f->lo[3 * b + 1] + (int)((rel / nx) % ny) - 1,
+                  f->lo[3 * b + 2] + (int)(rel / (nx * ny)) - 1};
+      face[d][slot] = bf ? dense_at(f, bf, g) : 1.0;
+    }
+  }
+  for (int l = M->L - 2; l >= 0; --l) amr_average_down_faces(&M->pair[l]);
+  return 0;
+}
+
+/* value of level l's ghost slot gq for the level fields x: a coarse/fine ghost by the
+   interpolation from level l - 1, a wall ghost by the wall rule, a copy from its source */
+static double mlv_ghost_value(const omlv* M, const double* const* x, int l, int64_t gq) {
+  if (l > 0) {
+    const oamr* A = &M->pair[l - 1];
+    int64_t cfi = A->cfidx[gq];
+    if (cfi >= 0) {
+      const ocfghost* G = &A->cf[cfi];
+      double cs = 0.0;
+      for (int e = 0; e < 5; ++e) cs += G->cw[e] * x[l - 1][G->cq[e]];
+      return (8.0 / 15.0) * cs + (2.0 / 3.0) * x[l][G->f1] - 0.2 * x[l][G->f2];
+    }
+  }
+  const olev* f = &M->P[l]->L[0];
+  int64_t e = M->gentry[l][gq];
+  return f->gfac[e] * x[l][f->gsrc[e]];
+}
+
+/* (A x) at valid cell (b; i, j, k) of level l, an uncovered cell */
+static double mlv_row(const omlv* M, const double* const* x, int l, int b, int i, int j, int k) {
+  const olev* f = &M->P[l]->L[0];
+  const int64_t q = IX(f, b, i, j, k);
+  const int loc[3] = {i, j, k};
+  double v = M->a * f->alpha[q] * x[l][q];
+  for (int d = 0; d < 3; ++d) {
+    const double* fa = d == 0 ? f->bx : (d == 1 ? f->by : f->bz);
+    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    for (int side = 0; side < 2; ++side) {
+      int nl[3] = {loc[0], loc[1], loc[2]};
+      nl[d] += side ? 1 : -1;
+      const int inside = nl[d] >= 0 && nl[d] < bn(f, b, d);
+      const int64_t nq = IX(f, b, nl[0], nl[1], nl[2]);
+      int64_t src = -1; /* the level-l cell behind the neighbour slot, if it is one */
+      if (inside) {
+        src = nq;
+      } else {
+        int64_t e = M->gentry[l][nq];
+        if (f->gsrc[e] >= 0 && f->gwall[e] < 0) src = f->gsrc[e];
+      }
+      if (l + 1 < M->L && src >= 0 && M->pair[l].covered[src]) {
+        /* reflux: the mean of the 4 fine fluxes through this face, b beta_f (x_f - x_g) / h_f
+           over h_c, the fine ghost x_g interpolated from this level */
+        const olev* fn = &M->P[l + 1]->L[0];
+        int gl[3] = {f->lo[3 * b] + i, f->lo[3 * b + 1] + j, f->lo[3 * b + 2] + k};
+        int gn[3] = {gl[0], gl[1], gl[2]};
+        gn[d] += side ? 1 : -1;
+        double cf = M->b * 0.25 / (fn->h[d] * f->h[d]);
+        const double* fna = d == 0 ? fn->bx : (d == 1 ? fn->by : fn->bz);
+        for (int u = 0; u < 2; ++u)
+          for (int w = 0; w < 2; ++w) {
+            int fg[3];
+            fg[d] = side ? 2 * gn[d] : 2 * gn[d] + 1;
+            fg[d1] = 2 * gl[d1] + u;
+            fg[d2] = 2 * gl[d2] + w;
+            wrap_periodic(fn, fg);
+            int fb = find_box(fn, fg);
+            int fl[3] = {fg[0] - fn->lo[3 * fb], fg[1] - fn->lo[3 * fb + 1], fg[2] - fn->lo[3 * fb + 2]};
+            int ghl[3] = {fl[0], fl[1], fl[2]};
+            ghl[d] += side ? -1 : 1;
+            int sl[3] = {fl[0], fl[1], fl[2]};
+            if (!side) sl[d] += 1;
+            double beta = fna[IX(fn, fb, sl[0], sl[1], sl[2])];
+            double xf = x[l + 1][IX(fn, fb, fl[0], fl[1], fl[2])];
+            double xg = mlv_ghost_value(M, x, l + 1, IX(fn, fb, ghl[0], ghl[1], ghl[2]));
+            v += cf * beta * (xg - xf);
+          }
+        continue;
+      }
+      int fl[3] = {loc[0], loc[1], loc[2]};
+      if (side) fl[d] += 1;
+      const double w = M->b * fa[IX(f, b, fl[0], fl[1], fl[2])] / (f->h[d] * f->h[d]);
+      const double xn = inside ? x[l][nq] : mlv_ghost_value(M, x, l, nq);
+      v += w * (x[l][q] - xn);
+    }
+  }
+  return v;
+}
+
+static int mlv_covered(const omlv* M, int l, int64_t q) { return l + 1 < M->L && M->pair[l].covered[q]; }
+
+/* y = A x over all levels (boxed); covered entries of y are 0 */
+static void mlv_apply(const omlv* M, const double* const* x, double* const* y) {
+  for (int l = 0; l < M->L; ++l) {
+    const olev* f = &M->P[l]->L[0];
+    memset(y[l], 0, sizeof(double) * f->ntot);
+    for (int b = 0; b < f->nb; ++b)
+      for (int k = 0; k < bn(f, b, 2); ++k)
+        for (int j = 0; j < bn(f, b, 1); ++j)
+          for (int i = 0; i < bn(f, b, 0); ++i) {
+            int64_t q = IX(f, b, i, j, k);
+            if (!mlv_covered(M, l, q)) y[l][q] = mlv_row(M, x, l, b, i, j, k);
+          }
+  }
+}
+
+static double mlv_norminf(const omlv* M, double* const* x) {
+  double m = 0.0;
+  for (int l = 0; l < M->L; ++l) {
+    const olev* f = &M->P[l]->L[0];
+    for (int b = 0; b < f->nb; ++b)
+      for (int k = 0; k < bn(f, b, 2); ++k)
+        for (int j = 0; j < bn(f, b, 1); ++j)
+          for (int i = 0; i < bn(f, b, 0); ++i) {
+            int64_t q = IX(f, b, i, j, k);
+            if (mlv_covered(M, l, q)) continue;
+            double v = fabs(x[l][q]);
+            if (v > m || v != v) m = v;
+          }
+  }
+  return m;
+}
+
+/* volume-weighted sum over the composite cells, and their volume */
+static void mlv_vsum(const omlv* M, double* const* x, double* s, double* vol) {
+  *s = 0.0;
+  *vol = 0.0;
+  for (int l = 0; l < M->L; ++l) {
+    const olev* f = &M->P[l]->L[0];
+    double v = f->h[0] * f->h[1] * f->h[2];
+    for (int b = 0; b < f->nb; ++b)
+      for (int k = 0; k < bn(f, b, 2); ++k)
+        for (int j = 0; j < bn(f, b, 1); ++j)
+          for (int i = 0; i < bn(f, b, 0); ++i) {
+            int64_t q = IX(f, b, i, j, k);
+            if (mlv_covered(M, l, q)) continue;
+            *s += v * x[l][q];
+            *vol += v;
+          }
+  }
+}
+
+/* r = rhs - A phi on the composite cells (covered 0) */
+static void mlv_residual(const omlv* M, double* const* rhs, double* const* phi, double* const* r) {
+  mlv_apply(M, (const double* const*)phi, r);
+  for (int l = 0; l < M->L; ++l) {
+    int64_t n = M->P[l]->L[0].ntot;
+    for (int64_t q = 0; q < n; ++q) r[l][q] = mlv_covered(M, l, q) ? 0.0 : rhs[l][q] - r[l][q];
+  }
+}
+
+/* covered cells of levels L-2 .. 0 := mean of their children, finest pair first */
+static void mlv_average_down(const omlv* M, double* const* x) {
+  for (int l = M->L - 1; l >= 1; --l) amr_average_down(&M->pair[l - 1], x[l], x[l - 1]);
+}
+
+/* one red-black colour on level l >= 1, coarse/fine ghosts from cx (NULL: 0) */
+static void mlv_colour(omlv* M, int l, double* e, const double* r, const double* cx, int colour) {
+  amr_fill_cf(&M->pair[l - 1], e, cx);
+  orc_smooth_colour(M->P[l], 0, e, r, colour);
+}
+
+/* Composite multigrid solve over L levels (the multi-level form of the two-level iteration):
+   r = composite residual; then, from e = 0 on every level:
+   down, for l = L-1 .. 1: nu1 red-black sweeps of e_l on the correction equation of level
+     l (right-hand side rr_l; coarse/fine ghosts with a zero coarse correction); the level's
+     correction residual s_l = rr_l - A_l e_l; the right-hand side of level l-1: on cells
+     covered by level l the average of s_l, elsewhere its composite residual minus the change
+     of its composite rows by e_l (the correction's reflux);
+   level 0: one V-cycle of its own hierarchy;
+   up, for l = 1 .. L-1: e_l += piecewise-constant interpolation of e_(l-1); nu2 sweeps with
+     coarse/fine ghosts interpolated from e_(l-1);
+   covered corrections := averages of their children (finest pair first); phi += e; covered
+   phi := averages.  With L = 2 these are the steps of orc_amr_solve.  Stops at
+   ||r||_inf <= max(tol_rel ||rhs||_inf, tol_abs) over the composite cells.  Singular (no
+   Dirichlet wall, a = 0): rhs projected to zero volume-weighted mean, phi returned so.
+   rhs_d[l], phi_d[l]: dense over level l's domain (cells outside its boxes ignored). */
+int orc_mlv_solve(void* vp, const double* const* rhs_d, double* const* phi_d, double tol_rel, double tol_abs, int maxit,
+                  double* hist, int* status) {
+  omlv* M = (omlv*)vp;
+  const int L = M->L;
+  double *rhs[ORC_MAXAMR], *phi[ORC_MAXAMR], *r[ORC_MAXAMR], *e[ORC_MAXAMR], *rr[ORC_MAXAMR], *y[ORC_MAXAMR],
+      *s[ORC_MAXAMR], *zero[ORC_MAXAMR];
+  for (int l = 0; l < L; ++l) {
+    int64_t n = M->P[l]->L[0].ntot;
+    rhs[l] = calloc(n, 8); phi[l] = calloc(n, 8); r[l] = calloc(n, 8); e[l] = calloc(n, 8);
+    rr[l] = calloc(n, 8); y[l] = calloc(n, 8); s[l] = calloc(n, 8); zero[l] = calloc(n, 8);
+    orc_dense_to_boxed(M->P[l], 0, rhs_d[l], rhs[l]);
+    for (int64_t q = 0; q < n; ++q)
+      if (mlv_covered(M, l, q)) rhs[l][q] = 0.0;
+  }
+  double rn0 = mlv_norminf(M, rhs);
+  int sing = M->P[0]->singular;
+  if (sing) {
+    double sm, v;
+    mlv_vsum(M, rhs, &sm, &v);
+    for (int l = 0; l < L; ++l) {
+      lev_add_const(&M->P[l]->L[0], rhs[l], -sm / v);
+      int64_t n = M->P[l]->L[0].ntot;
+      for (int64_t q = 0; q < n; ++q)
+        if (mlv_covered(M, l, q)) rhs[l][q] = 0.0;
+    }
+  }
+  double target = tol_rel * rn0 > tol_abs ? tol_rel * rn0 : tol_abs;
+  mlv_residual(M, rhs, phi, r);
+  double rn = mlv_norminf(M, r);
+  if (hist) hist[0] = rn;
+  int it = 0;
+  *status = 0;
+  while (!(rn <= target) && it < maxit) {
+    for (int l = 0; l < L; ++l) memset(e[l], 0, 8 * M->P[l]->L[0].ntot);
+    memcpy(rr[L - 1], r[L - 1], 8 * M->P[L - 1]->L[0].ntot);
+    for (int l = L - 1; l >= 1; --l) {
+      for (int sw = 0; sw < M->nu1; ++sw) {
+        mlv_colour(M, l, e[l], rr[l], NULL, 0);
+        mlv_colour(M, l, e[l], rr[l], NULL, 1);
+      }
+      amr_fill_cf(&M->pair[l - 1], e[l], NULL);
+      orc_residual(M->P[l], 0, e[l], rr[l], s[l]);
+      /* composite rows of level l-1 applied to (0 below l, e_l on l) */
+      const double* xs[ORC_MAXAMR];
+      for (int q = 0; q < L; ++q) xs[q] = (q == l) ? e[l] : zero[q];
+      mlv_apply(M, xs, y);
+      int64_t nc = M->P[l - 1]->L[0].ntot;
+      memset(rr[l - 1], 0, 8 * nc);
+      amr_average_down(&M->pair[l - 1], s[l], rr[l - 1]);
+      for (int64_t q = 0; q < nc; ++q)
+        if (!M->pair[l - 1].covered[q]) rr[l - 1][q] = r[l - 1][q] - y[l - 1][q];
+    }
+    orc_vcycle(M->P[0], 0, e[0], rr[0]);
+    for (int l = 1; l < L; ++l) {
+      const olev* f = &M->P[l]->L[0];
+      const olev* c = &M->P[l - 1]->L[0];
+      for (int b = 0; b < f->nb; ++b)
+        for (int k = 0; k < bn(f, b, 2); ++k)
+          for (int j = 0; j < bn(f, b, 1); ++j)
+            for (int i = 0; i < bn(f, b, 0); ++i) {
+              int G[3] = {(f->lo[3 * b] + i) >> 1, (f->lo[3 * b + 1] + j) >> 1, (f->lo[3 * b + 2] + k) >> 1};
+              e[l][IX(f, b, i, j, k)] += e[l - 1][coarse_at(c, G)];
+            }
+      for (int sw = 0; sw < M->nu2; ++sw) {
+        mlv_colour(M, l, e[l], rr[l], e[l - 1], 0);
+        mlv_colour(M, l, e[l], rr[l], e[l - 1], 1);
+      }
+    }
+    mlv_average_down(M, e);
+    for (int l = 0; l < L; ++l) {
+      int64_t n = M->P[l]->L[0].ntot;
+      for (int64_t q = 0; q < n; ++q) phi[l][q] += e[l][q];
+    }
+    mlv_average_down(M, phi);
+    mlv_residual(M, rhs, phi, r);
+    rn = mlv_norminf(M, r);
+    ++it;
+    if (hist) hist[it] = rn;
+    if (!(rn == rn) || isinf(rn)) { *status = -3; break; }
+  }
+  if (*status == 0 && !(rn <= target)) *status = -2;
+  if (sing) {
+    double sm, v;
+    mlv_vsum(M, phi, &sm, &v);
+    for (int l = 0; l < L; ++l) lev_add_const(&M->P[l]->L[0], phi[l], -sm / v);
+    mlv_average_down(M, phi);
+  }
+  for (int l = 0; l < L; ++l) {
+    orc_boxed_to_dense(M->P[l], 0, phi[l], phi_d[l]);
+    free(rhs[l]); free(phi[l]); free(r[l]); free(e[l]); free(rr[l]); free(y[l]); free(s[l]); free(zero[l]);
+  }
+  return it;
+}
+
+/* y = A x for dense level arrays (covered entries of y are 0) */
+void orc_mlv_apply(void* vp, const double* const* x_d, double* const* y_d) {
+  omlv* M = (omlv*)vp;
+  double *x[ORC_MAXAMR], *y[ORC_MAXAMR];
+  for (int l = 0; l < M->L; ++l) {
+    int64_t n = M->P[l]->L[0].ntot;
+    x[l] = calloc(n, 8);
+    y[l] = calloc(n, 8);
+    orc_dense_to_boxed(M->P[l], 0, x_d[l], x[l]);
+  }
+  mlv_apply(M, (const double* const*)x, y);
+  for (int l = 0; l < M->L; ++l) {
+    orc_boxed_to_dense(M->P[l], 0, y[l], y_d[l]);
+    free(x[l]); free(y[l]);
   }
 }

@@ -145,9 +145,9 @@ class Problem:
         self.domain = (tuple(dlo), tuple(dhi))
 
     def __del__(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and not getattr(self, "_view", False):
             lib().orc_destroy(self.h)
-            self.h = None
+        self.h = None
 
     # hierarchy -------------------------------------------------------------
     @property
@@ -459,3 +459,127 @@ class AmrProblem:
             e[j] = 1.0
             M[:, j] = self.pack(*self.apply(*self.unpack(e)))
         return M
+
+
+def _declare_mlv(L):
+    vp = C.c_void_p
+    pp = C.POINTER(_f64p)
+    L.orc_mlv_create.restype = vp
+    L.orc_mlv_create.argtypes = [_i32p, _i32p, _i32p, _i32p, _f64p, _f64p, C.c_int, _i32p, _i32p]
+    L.orc_mlv_destroy.argtypes = [vp]
+    L.orc_mlv_covered.argtypes = [vp, C.c_int, C.c_char_p]
+    L.orc_mlv_set_coeffs.argtypes = [vp, C.c_double, C.c_double, pp, pp]
+    L.orc_mlv_set_coeffs.restype = C.c_int
+    L.orc_mlv_apply.argtypes = [vp, pp, pp]
+    L.orc_mlv_solve.argtypes = [vp, pp, pp, C.c_double, C.c_double, C.c_int, _f64p, _i32p]
+    L.orc_mlv_solve.restype = C.c_int
+    L.orc_mlv_level.restype = vp
+    L.orc_mlv_level.argtypes = [vp, C.c_int]
+
+
+def _ptrs(arrays):
+    a = (_f64p * len(arrays))()
+    for i, x in enumerate(arrays):
+        a[i] = _dp(x) if x is not None else None
+    return a
+
+
+class MultiLevelProblem:
+    """Composite problem over L AMR levels (ratio 2 between consecutive levels): level 0 covers
+    the domain, level l is a BoxArray in level l's index space (the domain scaled by 2^l),
+    properly nested in level l - 1.  Dense arrays of level l are (nz, ny, nx) over the whole
+    level-l domain; only cells inside level l's boxes are used, and of those only the ones
+    not covered by level l + 1 are unknowns."""
+
+    def __init__(self, domain, level_boxes, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0), prob_hi=(1.0, 1.0, 1.0)):
+        L = lib()
+        if not hasattr(L, "_mlv_declared"):
+            _declare_mlv(L)
+            L._mlv_declared = True
+        dlo, dhi = _i32(domain[0]), _i32(domain[1])
+        nb = _i32([len(b) for b in level_boxes])
+        bx = _i32([list(b[0]) + list(b[1]) for lev in level_boxes for b in lev]).reshape(-1)
+        self._keep = [_i32(bc_lo), _i32(bc_hi), _f64(prob_lo), _f64(prob_hi)]
+        self.h = L.orc_mlv_create(_ip(dlo), _ip(dhi), _ip(self._keep[0]), _ip(self._keep[1]), _dp(self._keep[2]),
+                                  _dp(self._keep[3]), len(level_boxes), _ip(nb), _ip(bx))
+        if not self.h:
+            raise ValueError("oracle: invalid multi-level layout")
+        self.L = len(level_boxes)
+        base = tuple(int(dhi[d] - dlo[d] + 1) for d in (2, 1, 0))
+        self.shapes = [tuple(n << l for n in base) for l in range(self.L)]
+        self.level_boxes = level_boxes
+        self.inside = []
+        for l in range(self.L):
+            m = np.zeros(self.shapes[l], dtype=bool)
+            for lo, hi in level_boxes[l]:
+                m[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] = True
+            self.inside.append(m)
+        # unknowns: inside level l and not under level l + 1
+        self.masks = []
+        for l in range(self.L):
+            m = self.inside[l].copy()
+            if l + 1 < self.L:
+                s = self.shapes[l]
+                m &= ~self.inside[l + 1].reshape(s[0], 2, s[1], 2, s[2], 2).all(axis=(1, 3, 5))
+            self.masks.append(m)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_mlv_destroy(self.h)
+            self.h = None
+
+    def level(self, l):
+        """level l as a one-level Problem view (owned by this handle)"""
+        P = Problem.__new__(Problem)
+        P.h = lib().orc_mlv_level(self.h, l)
+        P._view = True
+        lo = tuple(0 for _ in range(3))
+        s = self.shapes[l]
+        P.domain = (lo, (s[2] - 1, s[1] - 1, s[0] - 1))
+        return P
+
+    def set_coeffs(self, a=0.0, b=1.0, alphas=None, betas=None):
+        self._coef = [None if alphas is None else [_f64(x) for x in alphas],
+                      None if betas is None else [_f64(x) for x in betas]]
+        lib().orc_mlv_set_coeffs(self.h, a, b, _ptrs(self._coef[0]) if alphas is not None else None,
+                                 _ptrs(self._coef[1]) if betas is not None else None)
+
+    def apply(self, xs):
+        xs = [_f64(x) for x in xs]
+        ys = [np.zeros(s) for s in self.shapes]
+        lib().orc_mlv_apply(self.h, _ptrs(xs), _ptrs(ys))
+        return [y * m for y, m in zip(ys, self.masks)]
+
+    def solve(self, rhss, tol_rel=1e-10, tol_abs=0.0, maxit=100):
+        rs = [_f64(r) for r in rhss]
+        ps = [np.zeros(s) for s in self.shapes]
+        hist = np.zeros(maxit + 1)
+        st = np.zeros(1, dtype=np.int32)
+        it = lib().orc_mlv_solve(self.h, _ptrs(rs), _ptrs(ps), tol_rel, tol_abs, maxit, _dp(hist), _ip(st))
+        return [p * m for p, m in zip(ps, self.inside)], int(it), hist[:it + 1].copy(), int(st[0])
+
+    def pack(self, xs):
+        return np.concatenate([np.asarray(x)[m] for x, m in zip(xs, self.masks)])
+
+    def unpack(self, v):
+        out, o = [], 0
+        for s, m in zip(self.shapes, self.masks):
+            x = np.zeros(s)
+            k = int(m.sum())
+            x[m] = v[o:o + k]
+            o += k
+            out.append(x)
+        return out
+
+    def volumes(self):
+        return np.concatenate([np.full(int(m.sum()), 8.0 ** (-l)) for l, m in enumerate(self.masks)])
+
+    def matrix(self):
+        n = self.pack([np.zeros(s) for s in self.shapes]).size
+        A = np.zeros((n, n))
+        e = np.zeros(n)
+        for j in range(n):
+            e[:] = 0.0
+            e[j] = 1.0
+            A[:, j] = self.pack(self.apply(self.unpack(e)))
+        return A
