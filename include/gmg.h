@@ -191,14 +191,18 @@ gmg_status gmg_define_domain(gmg_ctx* ctx, const int lo[3], const int hi[3], con
 /* BoxArray of AMR level `lev`: nboxes boxes given as box_lohi[6*b + 0..2] = lo,
    [6*b + 3..5] = hi (inclusive), disjoint.
    lev 0: the boxes cover the domain; builds the multigrid hierarchy (per-box coarsening,
-     then aggregation into one box, Sec. "Linear Solvers").  Resets any level 1.
-   lev 1 (two-level composite form, Sec. "Basic data structures": refinement ratio;
-     Sec. "Operations between levels"): ref_ratio must be 2; boxes in the fine index space,
-     aligned to the ratio, each coarsened box inside one level-0 box, faces either shared
-     with another level-1 box or wholly on the coarse/fine boundary, and at least one
-     uncovered coarse cell between the fine level and any other fine box or wall (the
-     coarse/fine interpolation reads coarse neighbours).  Call after level 0 and before
-     gmg_workspace_size; the workspace then holds both levels. */
+     then aggregation into one box, Sec. "Linear Solvers").  Resets any AMR level above.
+   lev >= 1 (composite form, Sec. "Basic data structures": refinement ratio; Sec.
+     "Operations between levels"), defined in order, up to GMG_MAX_AMR_LEVELS levels in
+     all; defining level lev drops the levels above it: ref_ratio must be 2; boxes in level
+     lev's index space (the domain scaled by 2^lev), aligned to the ratio, each coarsened
+     box inside one box of level lev - 1, faces either shared with another box of the level
+     or wholly on its coarse/fine boundary, and at least one uncovered cell of level lev - 1
+     between the level and any other of its boxes, a wall or the edge of level lev - 1 (the
+     coarse/fine interpolation reads coarse neighbours).  Single-problem contexts.  Call
+     before gmg_workspace_size; the workspace then holds every level.  The adjoint solve,
+     apply_transpose and the beta gradient take two levels at most. */
+#define GMG_MAX_AMR_LEVELS 4
 gmg_status gmg_define_level(gmg_ctx* ctx, int lev, int nboxes, const int* box_lohi, int ref_ratio);
 
 /* Convenience: BoxArray of level `lev` = the domain chopped into boxes of at most

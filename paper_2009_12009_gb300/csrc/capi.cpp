@@ -77,6 +77,21 @@ namespace gmg {
 void set_thread_error(const std::string& msg) { g_create_error = msg; }
 }  // namespace gmg
 
+// One AMR level above level 0: its boxes (one MG level whose coarse correction is the level
+// below), the tables of the pair (level below, this level), device views, coefficients and
+// work fields.
+struct AmrLevel {
+  LevelMeta M;
+  AmrHost H;  // covered cells of the level below, this level's coarse/fine ghosts, reflux, averaging
+  AmrDev A;
+  LevelDev D;
+  LevelBufs B;
+  double *alpha = nullptr, *bx = nullptr, *by = nullptr, *bz = nullptr, *beta_cell = nullptr;
+  double *rhs = nullptr, *res = nullptr, *tmp = nullptr, *zero = nullptr;  // projected rhs, residual
+  double* kf[9] = {};  // adjoint BiCGStab vectors
+  bool have_beta = false, have_alpha = false;
+};
+
 struct gmg_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
@@ -154,18 +169,13 @@ struct gmg_ctx {
   BotGhost* tghosts = nullptr;
   TailXfer* txfer = nullptr;
 
-  // two-level composite form: AMR level 1 (ratio 2) over part of level 0
+  // composite form: AMR levels 1, 2, ... (ratio 2 each) over part of the level below;
+  // amrl[l - 1] is AMR level l
   bool amr = false;
-  LevelMeta F;          // the fine level (one MG level; its coarse correction is level 0)
-  AmrHost amr_host;
-  AmrDev amrd;
-  LevelDev devf;
-  LevelBufs buff;       // fine coefficients and work fields
-  double *alphaf = nullptr, *bxf = nullptr, *byf = nullptr, *bzf = nullptr, *betaf_cell = nullptr;
-  double *crhs = nullptr, *frhs = nullptr, *cres = nullptr, *fres = nullptr;  // projected rhs, residual
-  double *ctmp = nullptr, *ftmp = nullptr, *czero = nullptr, *fzero = nullptr;
-  double *kc[9] = {}, *kf[9] = {};  // adjoint BiCGStab vectors
-  bool have_beta_f = false, have_alpha_f = false;
+  std::vector<AmrLevel> amrl;
+  double *crhs = nullptr, *cres = nullptr;  // level 0: projected rhs, composite residual
+  double *ctmp = nullptr, *czero = nullptr;
+  double* kc[9] = {};  // level 0's adjoint BiCGStab vectors
 
   int ns() const { return (int)geoms.size(); }
 };
@@ -213,6 +223,8 @@ bool any_singular(const gmg_ctx* c) {
 }
 
 int nlev(const gmg_ctx* c) { return (int)c->L.size(); }
+// AMR levels of the context (level 0 included)
+int namr(const gmg_ctx* c) { return 1 + (int)c->amrl.size(); }
 
 Coefs coefs_of(const gmg_ctx* c, int m, int dt) {
   const LevelBufs& B = c->buf[m];
@@ -339,9 +351,9 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
       c->tdescs = td; c->tlevels = tl; c->tcells = tc; c->tghosts = tg; c->txfer = tx;
     }
   }
-  if (c->amr) {
-    const LevelMeta& M = c->F;
-    const AmrHost& H = c->amr_host;
+  for (size_t al = 0; al < c->amrl.size(); ++al) {  // AMR level al + 1
+    const LevelMeta& M = c->amrl[al].M;
+    const AmrHost& H = c->amrl[al].H;
     const size_t nf = (size_t)M.nelem;
     LevelDev D;
     LevelBufs B;
@@ -392,26 +404,29 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     A.navg_cell = (int)H.avg_cells.size();
     double* f5[5];
     for (int q = 0; q < 5; ++q) f5[q] = (double*)cv.take(8 * nf);
-    double* cc[4];
-    for (int q = 0; q < 4; ++q) cc[q] = (double*)cv.take(8 * ne0);
+    double* cc[4] = {};
+    if (al == 0)
+      for (int q = 0; q < 4; ++q) cc[q] = (double*)cv.take(8 * ne0);
     double* ff[5];
     for (int q = 0; q < 5; ++q) ff[q] = (double*)cv.take(8 * nf);
-    double *kc[9], *kf[9];
-    for (int q = 0; q < 9; ++q) {
-      kc[q] = (double*)cv.take(8 * ne0);
-      kf[q] = (double*)cv.take(8 * nf);
-    }
-    if (fill) {
-      c->devf = D;
-      c->buff = B;
-      c->amrd = A;
-      c->alphaf = f5[0]; c->bxf = f5[1]; c->byf = f5[2]; c->bzf = f5[3]; c->betaf_cell = f5[4];
-      c->crhs = cc[0]; c->cres = cc[1]; c->ctmp = cc[2]; c->czero = cc[3];
-      c->frhs = ff[0]; c->fres = ff[1]; c->ftmp = ff[2]; c->fzero = ff[3];
+    double *kc[9] = {}, *kf[9] = {};
+    if (c->amrl.size() == 1)  // the adjoint solve takes two levels
       for (int q = 0; q < 9; ++q) {
-        c->kc[q] = kc[q];
-        c->kf[q] = kf[q];
+        kc[q] = (double*)cv.take(8 * ne0);
+        kf[q] = (double*)cv.take(8 * nf);
       }
+    if (fill) {
+      AmrLevel& V = c->amrl[al];
+      V.D = D;
+      V.B = B;
+      V.A = A;
+      V.alpha = f5[0]; V.bx = f5[1]; V.by = f5[2]; V.bz = f5[3]; V.beta_cell = f5[4];
+      if (al == 0) {
+        c->crhs = cc[0]; c->cres = cc[1]; c->ctmp = cc[2]; c->czero = cc[3];
+        for (int q = 0; q < 9; ++q) c->kc[q] = kc[q];
+      }
+      V.rhs = ff[0]; V.res = ff[1]; V.tmp = ff[2]; V.zero = ff[3];
+      for (int q = 0; q < 9; ++q) V.kf[q] = kf[q];
     }
   }
   unsigned long long* nb = (unsigned long long*)cv.take(8 * (2 * ns + 8));
@@ -488,11 +503,11 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, c->tghosts, T.ghosts))) return st;
     if ((st = upload(c, c->txfer, T.xfer))) return st;
   }
-  if (c->amr) {
-    const LevelMeta& M = c->F;
-    const LevelDev& D = c->devf;
-    const AmrHost& H = c->amr_host;
-    const AmrDev& A = c->amrd;
+  for (const AmrLevel& V : c->amrl) {
+    const LevelMeta& M = V.M;
+    const LevelDev& D = V.D;
+    const AmrHost& H = V.H;
+    const AmrDev& A = V.A;
     gmg_status st;
     if ((st = upload(c, D.boxes, M.dbox))) return st;
     if ((st = upload(c, D.geoms, dev_geoms(M)))) return st;
@@ -531,9 +546,7 @@ void reset_problem(gmg_ctx* c) {
   c->have_beta = c->have_alpha = false;
   c->coefs_dirty = true;
   c->amr = false;
-  c->F = LevelMeta();
-  c->amr_host = AmrHost();
-  c->have_beta_f = c->have_alpha_f = false;
+  c->amrl.clear();
   c->tail = TailHost();
   c->tail_ok = false;
   for (int d = 0; d < NDT; ++d) {
@@ -588,14 +601,20 @@ gmg_status build_coefs(gmg_ctx* c) {
   launch_acoef(c->dev[0], c->a, c->have_alpha ? c->alpha0 : nullptr, c->buf[0].acoef, s);
   launch_faces_scale(c->dev[0], c->b, c->bx0, c->by0, c->bz0, c->buf[0].wx, c->buf[0].wy, c->buf[0].wz, s);
   if (c->amr) {
-    // the fine level first: level 0 under it takes the restriction of its coefficients
-    if (!c->have_beta_f) SETERR(c, GMG_ERR_STATE, "beta of AMR level 1 not set");
-    const LevelBufs& B = c->buff;
-    const LevelBufs& B0 = c->buf[0];
-    launch_acoef(c->devf, c->a, c->have_alpha_f ? c->alphaf : nullptr, B.acoef, s);
-    launch_faces_scale(c->devf, c->b, c->bxf, c->byf, c->bzf, B.wx, B.wy, B.wz, s);
-    launch_diag(c->devf, B.acoef, B.wx, B.wy, B.wz, B.D, B.invD, s);
-    launch_avgdown_coefs(c->amrd, B.acoef, B.wx, B.wy, B.wz, B0.acoef, B0.wx, B0.wy, B0.wz, s);
+    // every AMR level's own coefficients; then, finest pair first, a level under the next
+    // finer one takes the restriction of that level's coefficients; the diagonals last
+    for (size_t al = 0; al < c->amrl.size(); ++al) {
+      const AmrLevel& V = c->amrl[al];
+      if (!V.have_beta) SETERR(c, GMG_ERR_STATE, "beta of AMR level " + std::to_string(al + 1) + " not set");
+      launch_acoef(V.D, c->a, V.have_alpha ? V.alpha : nullptr, V.B.acoef, s);
+      launch_faces_scale(V.D, c->b, V.bx, V.by, V.bz, V.B.wx, V.B.wy, V.B.wz, s);
+    }
+    for (int l = namr(c) - 1; l >= 1; --l) {
+      const LevelBufs& B = c->amrl[l - 1].B;
+      const LevelBufs& Bc = l == 1 ? c->buf[0] : c->amrl[l - 2].B;
+      launch_avgdown_coefs(c->amrl[l - 1].A, B.acoef, B.wx, B.wy, B.wz, Bc.acoef, Bc.wx, Bc.wy, Bc.wz, s);
+    }
+    for (const AmrLevel& V : c->amrl) launch_diag(V.D, V.B.acoef, V.B.wx, V.B.wy, V.B.wz, V.B.D, V.B.invD, s);
   }
   for (int m = 0; m + 1 < nlev(c); ++m) {
     const LevelBufs& F = c->buf[m];
@@ -1107,68 +1126,116 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   return worst;
 }
 
-// ------------------------------------------------------------ two-level composite
+// ------------------------------------------------------------ composite form
 
-Coefs coefs_fine(const gmg_ctx* c) {
+// per-level views of the AMR levels: level 0 is MG level 0, level l >= 1 is amrl[l - 1]
+const LevelDev& adev(const gmg_ctx* c, int l) { return l == 0 ? c->dev[0] : c->amrl[l - 1].D; }
+int64_t anelem(const gmg_ctx* c, int l) { return l == 0 ? c->L[0].nelem : c->amrl[l - 1].M.nelem; }
+Coefs acoefs(const gmg_ctx* c, int l) {
+  if (l == 0) return coefs64(c, 0);
+  const LevelBufs& B = c->amrl[l - 1].B;
   Coefs k;
-  k.wx = c->buff.wx; k.wy = c->buff.wy; k.wz = c->buff.wz; k.D = c->buff.D; k.invD = c->buff.invD;
+  k.wx = B.wx; k.wy = B.wy; k.wz = B.wz; k.D = B.D; k.invD = B.invD;
   return k;
 }
+Coefs coefs_fine(const gmg_ctx* c) { return acoefs(c, 1); }
 
-// fine ghosts: copies between fine boxes, then the coarse/fine ghosts (interpolated from
-// coarse field `cx`, or zero coarse data when cx is null)
-void fine_fill(gmg_ctx* c, double* f, const double* cx, int mode, cudaStream_t s) {
-  launch_fill(DT_F64, c->devf, f, -1, 0, s);
-  launch_cf_fill(c->amrd, f, cx, mode, s);
+// ghosts of level l >= 1: copies between its boxes, then its coarse/fine ghosts (interpolated
+// from level l - 1's field cx, or zero coarse data when cx is null)
+void level_fill(gmg_ctx* c, int l, double* f, const double* cx, int mode, cudaStream_t s) {
+  launch_fill(DT_F64, adev(c, l), f, -1, 0, s);
+  launch_cf_fill(c->amrl[l - 1].A, f, cx, mode, s);
 }
+void fine_fill(gmg_ctx* c, double* f, const double* cx, int mode, cudaStream_t s) { level_fill(c, 1, f, cx, mode, s); }
 
-// composite residual r = rhs - A phi (fine cells, uncovered coarse cells; covered 0) and
-// ||r||_inf of each level into normbits[0] (fine) and normbits[1] (coarse)
+// composite residual r_l = rhs_l - (A x)_l on every level (covered cells 0), ||r_l||_inf into
+// nb[l] (nb may be null).  x's ghosts are overwritten.
+void comp_residual_n(gmg_ctx* c, double* const* x, const double* const* rhs, double* const* r, unsigned long long* nb,
+                     cudaStream_t s) {
+  const int L = namr(c);
+  for (int l = L - 1; l >= 1; --l) level_fill(c, l, x[l], x[l - 1], CF_INTERP, s);
+  launch_fill(DT_F64, c->dev[0], x[0], -1, 0, s);
+  if (nb) cudaMemsetAsync(nb, 0, 8 * (size_t)L, s);
+  for (int l = 0; l < L; ++l) {
+    const bool finest = l + 1 == L;
+    launch_residual(DT_F64, DT_F64, adev(c, l), x[l], rhs[l], acoefs(c, l), r[l], finest && nb ? nb + l : nullptr,
+                    nullptr, s);
+    if (!finest) {
+      launch_reflux(c->amrl[l].A, acoefs(c, l), acoefs(c, l + 1), x[l], x[l + 1], r[l], r[l], 1, s);
+      launch_zero_covered(c->amrl[l].A, r[l], s);
+      if (nb) launch_norm_max(adev(c, l), r[l], nb + l, s);
+    }
+  }
+}
+// (two levels: the fine norm in nb[0], the coarse one in nb[1], as read_norms expects)
 void comp_residual(gmg_ctx* c, double* pc, double* pf, const double* rc_in, const double* rf_in, double* rc,
                    double* rf, unsigned long long* nb, cudaStream_t s) {
-  fine_fill(c, pf, pc, CF_INTERP, s);
-  launch_fill(DT_F64, c->dev[0], pc, -1, 0, s);
-  if (nb) cudaMemsetAsync(nb, 0, 16, s);
-  launch_residual(DT_F64, DT_F64, c->devf, pf, rf_in, coefs_fine(c), rf, nb, nullptr, s);
-  launch_residual(DT_F64, DT_F64, c->dev[0], pc, rc_in, coefs64(c, 0), rc, nullptr, nullptr, s);
-  launch_reflux(c->amrd, coefs64(c, 0), coefs_fine(c), pc, pf, rc, rc, 1, s);
-  launch_zero_covered(c->amrd, rc, s);
-  if (nb) launch_norm_max(c->dev[0], rc, nb + 1, s);
+  double* x[2] = {pc, pf};
+  const double* rhs[2] = {rc_in, rf_in};
+  double* r[2] = {rc, rf};
+  comp_residual_n(c, x, rhs, r, nb ? c->normbits + 2 : nullptr, s);
+  if (nb) {  // nb[0] fine, nb[1] coarse
+    cudaMemcpyAsync(nb, c->normbits + 3, 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(nb + 1, c->normbits + 2, 8, cudaMemcpyDeviceToDevice, s);
+  }
 }
 
-// one composite multigrid correction from residual (rc, rf): e_c in buf[0].e, e_f in buff.e
-void comp_correction(gmg_ctx* c, const gmg_params& p, const double* rc, const double* rf, cudaStream_t s) {
-  double* ef = (double*)c->buff.e[DT_F64];
-  double* ec = (double*)c->buf[0].e[DT_F64];
-  double* crhs = (double*)c->buf[0].r[DT_F64];
-  // fine-box ghosts kept current by push (e_f starts at zero; every later write pushes);
-  // the coarse/fine ghosts depend on the fine cells inward and are refilled every colour
-  const bool push = p.ghost_push != 0 && c->devf.push_ok;
-  auto fill = [&](const double* cx) {
-    if (push) launch_cf_fill(c->amrd, ef, cx, CF_INTERP, s);
-    else fine_fill(c, ef, cx, CF_INTERP, s);
-  };
+// One composite multigrid correction from the composite residuals r (per level): e_l in
+// level l's e buffer.  Down, for l = L-1 .. 1: pre-smoothing of level l's correction
+// equation (right-hand side rr_l; coarse/fine ghosts with a zero coarse correction); the
+// right-hand side of level l-1: its composite residual with, on cells covered by level l,
+// the average of level l's correction residual, and next to level l minus the correction's
+// reflux.  Level 0: one V-cycle of its hierarchy.  Up, for l = 1 .. L-1: interpolation of
+// e_(l-1), post-smoothing with coarse/fine ghosts from e_(l-1).  Then covered corrections
+// := averages of their children, finest pair first.
+void comp_correction_n(gmg_ctx* c, const gmg_params& p, const double* const* r, cudaStream_t s) {
+  const int L = namr(c);
+  double* e[GMG_MAX_AMR_LEVELS];
+  const double* rr[GMG_MAX_AMR_LEVELS];
+  for (int l = 0; l < L; ++l) e[l] = (double*)(l == 0 ? c->buf[0].e[DT_F64] : c->amrl[l - 1].B.e[DT_F64]);
+  // right-hand sides: level 0 in its V-cycle buffer, middle levels in their own r buffers,
+  // the finest level's is its composite residual
+  double* rbuf[GMG_MAX_AMR_LEVELS];
+  for (int l = 0; l < L; ++l) rbuf[l] = (double*)(l == 0 ? c->buf[0].r[DT_F64] : c->amrl[l - 1].B.r[DT_F64]);
+  rr[L - 1] = r[L - 1];
   choose_pdl(p, s);
-  cudaMemsetAsync(ef, 0, 8 * (size_t)c->F.nelem, s);
-  for (int it = 0; it < p.nu1; ++it)
-    for (int colour = 0; colour < 2; ++colour) {
-      fill(nullptr);  // coarse correction 0
-      launch_smooth(DT_F64, c->devf, ef, rf, coefs_fine(c), colour, s, push);
-    }
-  fill(nullptr);
-  cudaMemcpyAsync(crhs, rc, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, s);
-  // covered cells: average of the fine correction residual r_f - A_f e_f
-  launch_resid_restrict(DT_F64, c->devf, c->dev[0], ef, rf, coefs_fine(c), crhs, s);
-  // uncovered cells next to the fine level: minus the fine correction's reflux
-  launch_reflux(c->amrd, coefs64(c, 0), coefs_fine(c), crhs, ef, crhs, crhs, 0, s);
+  // level l's box ghosts kept current by push (e_l starts at zero; every later write pushes);
+  // the coarse/fine ghosts depend on the cells inward and are refilled every colour
+  auto push_of = [&](int l) { return p.ghost_push != 0 && adev(c, l).push_ok; };
+  auto fill = [&](int l, const double* cx) {
+    if (push_of(l)) launch_cf_fill(c->amrl[l - 1].A, e[l], cx, CF_INTERP, s);
+    else level_fill(c, l, e[l], cx, CF_INTERP, s);
+  };
+  for (int l = 1; l < L; ++l) cudaMemsetAsync(e[l], 0, 8 * (size_t)anelem(c, l), s);
+  for (int l = L - 1; l >= 1; --l) {
+    for (int it = 0; it < p.nu1; ++it)
+      for (int colour = 0; colour < 2; ++colour) {
+        fill(l, nullptr);  // coarse correction 0
+        launch_smooth(DT_F64, adev(c, l), e[l], rr[l], acoefs(c, l), colour, s, push_of(l));
+      }
+    fill(l, nullptr);
+    cudaMemcpyAsync(rbuf[l - 1], r[l - 1], 8 * (size_t)anelem(c, l - 1), cudaMemcpyDeviceToDevice, s);
+    // covered cells: average of level l's correction residual rr_l - A_l e_l
+    launch_resid_restrict(DT_F64, adev(c, l), adev(c, l - 1), e[l], rr[l], acoefs(c, l), rbuf[l - 1], s);
+    // cells next to level l: minus the correction's reflux
+    launch_reflux(c->amrl[l - 1].A, acoefs(c, l - 1), acoefs(c, l), rbuf[l - 1], e[l], rbuf[l - 1], rbuf[l - 1], 0,
+                  s);
+    rr[l - 1] = rbuf[l - 1];
+  }
   vcycle(c, DT_F64, 0, p, s);
-  launch_prolong_add(DT_F64, c->devf, c->dev[0], ec, ef, s, push);
-  for (int it = 0; it < p.nu2; ++it)
-    for (int colour = 0; colour < 2; ++colour) {
-      fill(ec);
-      launch_smooth(DT_F64, c->devf, ef, rf, coefs_fine(c), colour, s, push);
-    }
-  launch_restrict(DT_F64, c->devf, c->dev[0], ef, ec, s);  // covered e_c := average of e_f
+  for (int l = 1; l < L; ++l) {
+    launch_prolong_add(DT_F64, adev(c, l), adev(c, l - 1), e[l - 1], e[l], s, push_of(l));
+    for (int it = 0; it < p.nu2; ++it)
+      for (int colour = 0; colour < 2; ++colour) {
+        fill(l, e[l - 1]);
+        launch_smooth(DT_F64, adev(c, l), e[l], rr[l], acoefs(c, l), colour, s, push_of(l));
+      }
+  }
+  for (int l = L - 1; l >= 1; --l) launch_restrict(DT_F64, adev(c, l), adev(c, l - 1), e[l], e[l - 1], s);
+}
+void comp_correction(gmg_ctx* c, const gmg_params& p, const double* rc, const double* rf, cudaStream_t s) {
+  const double* r[2] = {rc, rf};
+  comp_correction_n(c, p, r, s);
 }
 
 struct CompSums {
@@ -1182,8 +1249,8 @@ CompSums comp_sizes(const gmg_ctx* c) {
   z.vc = G.h[0] * G.h[1] * G.h[2];
   z.vf = z.vc / 8.0;
   z.ncell_c = (double)c->L[0].ncells;
-  z.ncov = (double)c->amr_host.covered_list.size();
-  z.ncell_f = (double)c->F.ncells;
+  z.ncov = (double)c->amrl[0].H.covered_list.size();
+  z.ncell_f = (double)c->amrl[0].M.ncells;
   return z;
 }
 
@@ -1191,7 +1258,7 @@ CompSums comp_sizes(const gmg_ctx* c) {
 gmg_status comp_level_sums(gmg_ctx* c, const double* xc, const double* xf, double* sc, double* sf) {
   cudaStream_t s = c->stream;
   launch_sum(c->dev[0], xc, c->partials, c->scal, s);
-  launch_sum(c->devf, xf, c->partials, c->scal + 1, s);  // same stream: after the first
+  launch_sum(c->amrl[0].D, xf, c->partials, c->scal + 1, s);  // same stream: after the first
   CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 16, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
   const CompSums z = comp_sizes(c);
@@ -1207,69 +1274,111 @@ gmg_status comp_add_const(gmg_ctx* c, double* xc, double* xf, double kc, double 
   c->h_scal[3] = kf;
   CK(c, cudaMemcpyAsync(c->scal + 2, c->h_scal + 2, 16, cudaMemcpyHostToDevice, s));
   launch_add_scalar(c->dev[0], xc, c->scal + 2, 1.0, s);
-  launch_add_scalar(c->devf, xf, c->scal + 3, 1.0, s);
-  launch_zero_covered(c->amrd, xc, s);
+  launch_add_scalar(c->amrl[0].D, xf, c->scal + 3, 1.0, s);
+  launch_zero_covered(c->amrl[0].A, xc, s);
   CK(c, cudaGetLastError());
   return GMG_OK;
 }
 
-gmg_status read_norms(gmg_ctx* c, double* rn) {
-  CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 16, cudaMemcpyDeviceToHost, c->stream));
+// max over n per-level norms in normbits[0, n) (NaN if any is NaN)
+gmg_status read_norms_n(gmg_ctx* c, int n, double* rn) {
+  CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 8 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   CK(c, cudaGetLastError());
-  *rn = std::max(bits_to_double(c->h_bits[0]), bits_to_double(c->h_bits[1]));
-  if (std::isnan(bits_to_double(c->h_bits[0])) || std::isnan(bits_to_double(c->h_bits[1]))) *rn = NAN;
+  *rn = 0.0;
+  for (int l = 0; l < n; ++l) {
+    const double v = bits_to_double(c->h_bits[l]);
+    if (std::isnan(v)) {
+      *rn = NAN;
+      break;
+    }
+    *rn = std::max(*rn, v);
+  }
+  return GMG_OK;
+}
+gmg_status read_norms(gmg_ctx* c, double* rn) { return read_norms_n(c, 2, rn); }
+
+// volume-weighted mean of x over the composite cells (covered entries must be zero)
+gmg_status comp_mean_n(gmg_ctx* c, double* const* x, double* mean) {
+  cudaStream_t s = c->stream;
+  const int L = namr(c);
+  for (int l = 0; l < L; ++l) launch_sum(adev(c, l), x[l], c->partials, c->scal + l, s);
+  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8 * (size_t)L, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  const SolveGeom& G = c->geoms[0];
+  double v = G.h[0] * G.h[1] * G.h[2], num = 0.0, vol = 0.0;
+  for (int l = 0; l < L; ++l, v /= 8.0) {
+    const double ncell = (double)(l == 0 ? c->L[0].ncells : c->amrl[l - 1].M.ncells);
+    const double ncov = l + 1 < L ? (double)c->amrl[l].H.covered_list.size() : 0.0;
+    num += v * c->h_scal[l] * ncell;  // launch_sum gives the mean over every cell of the level
+    vol += v * (ncell - ncov);
+  }
+  *mean = num / vol;
   return GMG_OK;
 }
 
-// Composite multigrid solve of the two-level problem (the oracle's two-level iteration):
-// residual, fine pre-smoothing with homogeneous coarse/fine ghosts, coarse right-hand side
-// (restricted fine correction residual under the fine level, reflux-corrected residual
-// next to it), coarse V-cycle, interpolation, fine post-smoothing, average-down, update.
-gmg_status solve_amr(gmg_ctx* c, double* pc, double* pf, const double* rc_user, const double* rf_user, double tol_rel,
-                     double tol_abs, const gmg_params& p, gmg_solve_info* info) {
+// x_l -= k on every level, covered entries cleared afterwards
+gmg_status comp_shift_n(gmg_ctx* c, double* const* x, double k) {
+  cudaStream_t s = c->stream;
+  const int L = namr(c);
+  c->h_scal[0] = -k;
+  CK(c, cudaMemcpyAsync(c->scal, c->h_scal, 8, cudaMemcpyHostToDevice, s));
+  for (int l = 0; l < L; ++l) {
+    launch_add_scalar(adev(c, l), x[l], c->scal, 1.0, s);
+    if (l + 1 < L) launch_zero_covered(c->amrl[l].A, x[l], s);
+  }
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+// Composite multigrid solve over every AMR level (the oracle's multi-level iteration; with
+// two levels its two-level one): residual, composite correction, update, average-down.
+gmg_status solve_amr_n(gmg_ctx* c, double* const* phi, const double* const* rhs_user, double tol_rel, double tol_abs,
+                       const gmg_params& p, gmg_solve_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = c->stream;
+  const int L = namr(c);
   const int64_t l0 = kernel_launch_count();
   if (info) memset(info, 0, sizeof(*info));
-  const size_t nc = 8 * (size_t)c->L[0].nelem, nf = 8 * (size_t)c->F.nelem;
-  CK(c, cudaMemcpyAsync(c->crhs, rc_user, nc, cudaMemcpyDeviceToDevice, s));
-  CK(c, cudaMemcpyAsync(c->frhs, rf_user, nf, cudaMemcpyDeviceToDevice, s));
-  launch_zero_covered(c->amrd, c->crhs, s);
-  CK(c, cudaMemsetAsync(c->normbits, 0, 16, s));
-  launch_norm_max(c->devf, c->frhs, c->normbits, s);
-  launch_norm_max(c->dev[0], c->crhs, c->normbits + 1, s);
+  double *rhs[GMG_MAX_AMR_LEVELS], *res[GMG_MAX_AMR_LEVELS];
+  for (int l = 0; l < L; ++l) {
+    rhs[l] = l == 0 ? c->crhs : c->amrl[l - 1].rhs;
+    res[l] = l == 0 ? c->cres : c->amrl[l - 1].res;
+    CK(c, cudaMemcpyAsync(rhs[l], rhs_user[l], 8 * (size_t)anelem(c, l), cudaMemcpyDeviceToDevice, s));
+  }
+  CK(c, cudaMemsetAsync(c->normbits, 0, 8 * (size_t)L, s));
+  for (int l = 0; l < L; ++l) {
+    if (l + 1 < L) launch_zero_covered(c->amrl[l].A, rhs[l], s);
+    launch_norm_max(adev(c, l), rhs[l], c->normbits + l, s);
+  }
   double rhsnorm;
-  gmg_status st = read_norms(c, &rhsnorm);
+  gmg_status st = read_norms_n(c, L, &rhsnorm);
   if (st) return st;
   if (!std::isfinite(rhsnorm)) SETERR(c, GMG_ERR_BAD_INPUT, "rhs is not finite");
   const bool sing = singular(c, 0);
-  const CompSums z = comp_sizes(c);
   if (sing) {  // project onto zero volume-weighted mean (the range of the composite operator)
-    double sc, sf;
-    if ((st = comp_level_sums(c, c->crhs, c->frhs, &sc, &sf))) return st;
-    const double vol = z.vf * z.ncell_f + z.vc * (z.ncell_c - z.ncov);
-    const double mean = (z.vf * sf + z.vc * sc) / vol;
+    double mean;
+    if ((st = comp_mean_n(c, rhs, &mean))) return st;
     if (std::fabs(mean) > 1e-12 * rhsnorm && !p.project_mean)
       SETERR(c, GMG_ERR_BAD_INPUT, "singular problem with a nonzero-mean rhs (set project_mean)");
-    if ((st = comp_add_const(c, c->crhs, c->frhs, -mean, -mean))) return st;
+    if ((st = comp_shift_n(c, rhs, mean))) return st;
   }
   const double target = std::max(tol_rel * rhsnorm, tol_abs);
-  CK(c, cudaMemsetAsync(pc, 0, nc, s));
-  CK(c, cudaMemsetAsync(pf, 0, nf, s));
-  comp_residual(c, pc, pf, c->crhs, c->frhs, c->cres, c->fres, c->normbits, s);
+  for (int l = 0; l < L; ++l) CK(c, cudaMemsetAsync(phi[l], 0, 8 * (size_t)anelem(c, l), s));
+  comp_residual_n(c, phi, rhs, res, c->normbits, s);
   double rn;
-  if ((st = read_norms(c, &rn))) return st;
+  if ((st = read_norms_n(c, L, &rn))) return st;
   std::vector<double> hist{rn};
   int it = 0;
   gmg_status result = GMG_OK;
   while (!(rn <= target) && it < p.max_iter) {
-    comp_correction(c, p, c->cres, c->fres, s);
-    launch_add_correction(DT_F64, c->devf, pf, c->buff.e[DT_F64], s);
-    launch_add_correction(DT_F64, c->dev[0], pc, c->buf[0].e[DT_F64], s);
-    launch_restrict(DT_F64, c->devf, c->dev[0], pf, pc, s);  // covered := average of fine
-    comp_residual(c, pc, pf, c->crhs, c->frhs, c->cres, c->fres, c->normbits, s);
-    if ((st = read_norms(c, &rn))) return st;
+    comp_correction_n(c, p, res, s);
+    for (int l = 0; l < L; ++l)
+      launch_add_correction(DT_F64, adev(c, l), phi[l], l == 0 ? c->buf[0].e[DT_F64] : c->amrl[l - 1].B.e[DT_F64], s);
+    for (int l = L - 1; l >= 1; --l)
+      launch_restrict(DT_F64, adev(c, l), adev(c, l - 1), phi[l], phi[l - 1], s);  // covered := average
+    comp_residual_n(c, phi, rhs, res, c->normbits, s);
+    if ((st = read_norms_n(c, L, &rn))) return st;
     ++it;
     hist.push_back(rn);
     if (!std::isfinite(rn)) {
@@ -1279,13 +1388,12 @@ gmg_status solve_amr(gmg_ctx* c, double* pc, double* pf, const double* rc_user, 
   }
   if (result == GMG_OK && !(rn <= target)) result = GMG_ERR_NOT_CONVERGED;
   if (sing) {  // zero volume-weighted mean over the composite unknowns
-    launch_zero_covered(c->amrd, pc, s);
-    double sc, sf;
-    if ((st = comp_level_sums(c, pc, pf, &sc, &sf))) return st;
-    const double mean = (z.vf * sf + z.vc * sc) / (z.vf * z.ncell_f + z.vc * (z.ncell_c - z.ncov));
-    if ((st = comp_add_const(c, pc, pf, -mean, -mean))) return st;
+    for (int l = 0; l + 1 < L; ++l) launch_zero_covered(c->amrl[l].A, phi[l], s);
+    double mean;
+    if ((st = comp_mean_n(c, phi, &mean))) return st;
+    if ((st = comp_shift_n(c, phi, mean))) return st;
   }
-  launch_restrict(DT_F64, c->devf, c->dev[0], pf, pc, s);
+  for (int l = L - 1; l >= 1; --l) launch_restrict(DT_F64, adev(c, l), adev(c, l - 1), phi[l], phi[l - 1], s);
   CK(c, cudaStreamSynchronize(s));
   CK(c, cudaGetLastError());
   if (info) {
@@ -1300,17 +1408,25 @@ gmg_status solve_amr(gmg_ctx* c, double* pc, double* pf, const double* rc_user, 
     info->kernel_launches = kernel_launch_count() - l0;
   }
   if (result == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
-  if (result == GMG_ERR_DIVERGED) c->err = "residual is not finite";
   return result;
 }
 
-// out = A x (composite); x's ghosts are overwritten; covered coarse entries of out are 0
+// out = A x (composite) over every level; x's ghosts are overwritten; covered entries 0
+void comp_apply_n(gmg_ctx* c, double* const* x, double* const* out, cudaStream_t s) {
+  const int L = namr(c);
+  const double* zero[GMG_MAX_AMR_LEVELS];
+  for (int l = 0; l < L; ++l) {
+    double* z = l == 0 ? c->czero : c->amrl[l - 1].zero;
+    cudaMemsetAsync(z, 0, 8 * (size_t)anelem(c, l), s);
+    zero[l] = z;
+  }
+  comp_residual_n(c, x, zero, out, nullptr, s);
+  for (int l = 0; l < L; ++l) launch_scale_valid(adev(c, l), out[l], -1.0, s);
+}
 void comp_apply(gmg_ctx* c, double* xc, double* xf, double* outc, double* outf, cudaStream_t s) {
-  cudaMemsetAsync(c->czero, 0, 8 * (size_t)c->L[0].nelem, s);
-  cudaMemsetAsync(c->fzero, 0, 8 * (size_t)c->F.nelem, s);
-  comp_residual(c, xc, xf, c->czero, c->fzero, outc, outf, nullptr, s);
-  launch_scale_valid(c->dev[0], outc, -1.0, s);
-  launch_scale_valid(c->devf, outf, -1.0, s);
+  double* x[2] = {xc, xf};
+  double* out[2] = {outc, outf};
+  comp_apply_n(c, x, out, s);
 }
 
 // out = A^T y (composite): the level stencils (symmetric; the fine one with zero coarse/fine
@@ -1319,22 +1435,22 @@ void comp_apply(gmg_ctx* c, double* xc, double* xf, double* outc, double* outf, 
 // cleared.
 void comp_apply_transpose(gmg_ctx* c, double* yc, double* yf, double* outc, double* outf, cudaStream_t s) {
   cudaMemsetAsync(c->czero, 0, 8 * (size_t)c->L[0].nelem, s);
-  cudaMemsetAsync(c->fzero, 0, 8 * (size_t)c->F.nelem, s);
-  launch_zero_covered(c->amrd, yc, s);
+  cudaMemsetAsync(c->amrl[0].zero, 0, 8 * (size_t)c->amrl[0].M.nelem, s);
+  launch_zero_covered(c->amrl[0].A, yc, s);
   fine_fill(c, yf, nullptr, CF_ZERO, s);
   launch_fill(DT_F64, c->dev[0], yc, -1, 0, s);
-  launch_residual(DT_F64, DT_F64, c->devf, yf, c->fzero, coefs_fine(c), outf, nullptr, nullptr, s);
+  launch_residual(DT_F64, DT_F64, c->amrl[0].D, yf, c->amrl[0].zero, coefs_fine(c), outf, nullptr, nullptr, s);
   launch_residual(DT_F64, DT_F64, c->dev[0], yc, c->czero, coefs64(c, 0), outc, nullptr, nullptr, s);
   launch_scale_valid(c->dev[0], outc, -1.0, s);
-  launch_scale_valid(c->devf, outf, -1.0, s);
-  launch_composite_transpose_couplings(c->amrd, coefs64(c, 0), coefs_fine(c), yc, yf, outc, outf, s);
-  launch_zero_covered(c->amrd, outc, s);
+  launch_scale_valid(c->amrl[0].D, outf, -1.0, s);
+  launch_composite_transpose_couplings(c->amrl[0].A, coefs64(c, 0), coefs_fine(c), yc, yf, outc, outf, s);
+  launch_zero_covered(c->amrl[0].A, outc, s);
 }
 
 gmg_status comp_dot(gmg_ctx* c, const double* xc, const double* xf, const double* yc, const double* yf, double* out) {
   cudaStream_t s = c->stream;
   launch_dot(c->dev[0], xc, yc, c->partials, c->scal, s);
-  launch_dot(c->devf, xf, yf, c->partials, c->scal + 1, s);  // same stream: after the first
+  launch_dot(c->amrl[0].D, xf, yf, c->partials, c->scal + 1, s);  // same stream: after the first
   CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 16, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
   CK(c, cudaGetLastError());
@@ -1344,7 +1460,7 @@ gmg_status comp_dot(gmg_ctx* c, const double* xc, const double* xf, const double
 
 gmg_status comp_norm(gmg_ctx* c, const double* xc, const double* xf, double* out) {
   CK(c, cudaMemsetAsync(c->normbits, 0, 16, c->stream));
-  launch_norm_max(c->devf, xf, c->normbits, c->stream);
+  launch_norm_max(c->amrl[0].D, xf, c->normbits, c->stream);
   launch_norm_max(c->dev[0], xc, c->normbits + 1, c->stream);
   return read_norms(c, out);
 }
@@ -1358,12 +1474,12 @@ gmg_status solve_adjoint_amr(gmg_ctx* c, double* lc, double* lf, const double* g
   cudaStream_t s = c->stream;
   const int64_t l0 = kernel_launch_count();
   if (info) memset(info, 0, sizeof(*info));
-  const int64_t nc = c->L[0].nelem, nf = c->F.nelem;
+  const int64_t nc = c->L[0].nelem, nf = c->amrl[0].M.nelem;
   // vectors: 0 r, 1 rhat, 2 p, 3 v, 4 s, 5 t, 6 phat, 7 shat, 8 g
-  double **kc = c->kc, **kf = c->kf;
+  double **kc = c->kc, **kf = c->amrl[0].kf;
   CK(c, cudaMemcpyAsync(kc[8], gc_user, 8 * (size_t)nc, cudaMemcpyDeviceToDevice, s));
   CK(c, cudaMemcpyAsync(kf[8], gf_user, 8 * (size_t)nf, cudaMemcpyDeviceToDevice, s));
-  launch_zero_covered(c->amrd, kc[8], s);
+  launch_zero_covered(c->amrl[0].A, kc[8], s);
   const CompSums z = comp_sizes(c);
   gmg_status st;
   const bool sing = singular(c, 0);
@@ -1398,10 +1514,10 @@ gmg_status solve_adjoint_amr(gmg_ctx* c, double* lc, double* lf, const double* g
   // onto the range of A (zero volume-weighted sum) for the singular problem.
   auto precond = [&](double* inc, double* inf, double* outc, double* outf) {
     launch_axpby(nc, 1.0, inc, 0.0, inc, c->ctmp, s);
-    launch_axpby(nf, 8.0, inf, 0.0, inf, c->ftmp, s);
-    comp_correction(c, p, c->ctmp, c->ftmp, s);
+    launch_axpby(nf, 8.0, inf, 0.0, inf, c->amrl[0].tmp, s);
+    comp_correction(c, p, c->ctmp, c->amrl[0].tmp, s);
     launch_axpby(nc, 1.0, (const double*)c->buf[0].e[DT_F64], 0.0, (const double*)c->buf[0].e[DT_F64], outc, s);
-    launch_axpby(nf, 0.125, (const double*)c->buff.e[DT_F64], 0.0, (const double*)c->buff.e[DT_F64], outf, s);
+    launch_axpby(nf, 0.125, (const double*)c->amrl[0].B.e[DT_F64], 0.0, (const double*)c->amrl[0].B.e[DT_F64], outf, s);
   };
   while (!(rn <= target) && it < p.max_iter) {
     ++it;
@@ -1416,8 +1532,8 @@ gmg_status solve_adjoint_amr(gmg_ctx* c, double* lc, double* lf, const double* g
     launch_axpby(nf, 1.0, kf[0], beta, kf[2], kf[2], s);
     precond(kc[2], kf[2], kc[6], kf[6]);
     launch_axpby(nc, 1.0, kc[6], 0.0, kc[6], c->ctmp, s);
-    launch_axpby(nf, 1.0, kf[6], 0.0, kf[6], c->ftmp, s);
-    comp_apply_transpose(c, c->ctmp, c->ftmp, kc[3], kf[3], s);
+    launch_axpby(nf, 1.0, kf[6], 0.0, kf[6], c->amrl[0].tmp, s);
+    comp_apply_transpose(c, c->ctmp, c->amrl[0].tmp, kc[3], kf[3], s);
     double rv;
     if ((st = comp_dot(c, kc[1], kf[1], kc[3], kf[3], &rv))) return st;
     if (std::fabs(rv) < 1e-300) break;
@@ -1435,8 +1551,8 @@ gmg_status solve_adjoint_amr(gmg_ctx* c, double* lc, double* lf, const double* g
     }
     precond(kc[4], kf[4], kc[7], kf[7]);
     launch_axpby(nc, 1.0, kc[7], 0.0, kc[7], c->ctmp, s);
-    launch_axpby(nf, 1.0, kf[7], 0.0, kf[7], c->ftmp, s);
-    comp_apply_transpose(c, c->ctmp, c->ftmp, kc[5], kf[5], s);
+    launch_axpby(nf, 1.0, kf[7], 0.0, kf[7], c->amrl[0].tmp, s);
+    comp_apply_transpose(c, c->ctmp, c->amrl[0].tmp, kc[5], kf[5], s);
     double tt, ts;
     if ((st = comp_dot(c, kc[5], kf[5], kc[5], kf[5], &tt))) return st;
     if ((st = comp_dot(c, kc[5], kf[5], kc[4], kf[4], &ts))) return st;
@@ -1457,7 +1573,7 @@ gmg_status solve_adjoint_amr(gmg_ctx* c, double* lc, double* lf, const double* g
     rho_old = rho;
   }
   if (result == GMG_OK && !(rn <= target)) result = GMG_ERR_NOT_CONVERGED;
-  launch_zero_covered(c->amrd, lc, s);
+  launch_zero_covered(c->amrl[0].A, lc, s);
   if (sing) {  // remove the null-space component of A^T (span of V): zero plain sum
     double sc, sf;
     if ((st = comp_level_sums(c, lc, lf, &sc, &sf))) return st;
@@ -1881,7 +1997,8 @@ gmg_status gmg_define_domain(gmg_ctx* c, const int lo[3], const int hi[3], const
 gmg_status gmg_define_level(gmg_ctx* c, int lev, int nboxes, const int* lohi, int ref_ratio) {
   if (!c) return GMG_ERR_BAD_INPUT;
   if (!c->have_domain || c->ns() != 1) SETERR(c, GMG_ERR_STATE, "define one domain first (gmg_define_domain)");
-  if (lev != 0 && lev != 1) SETERR(c, GMG_ERR_BAD_INPUT, "AMR levels 0 and 1 are supported");
+  if (lev < 0 || lev >= GMG_MAX_AMR_LEVELS)
+    SETERR(c, GMG_ERR_BAD_INPUT, "AMR level out of range (0 .. " + std::to_string(GMG_MAX_AMR_LEVELS - 1) + ")");
   if (nboxes <= 0 || !lohi) SETERR(c, GMG_ERR_BAD_INPUT, "no boxes");
   std::vector<Box> boxes(nboxes);
   for (int b = 0; b < nboxes; ++b)
@@ -1890,37 +2007,41 @@ gmg_status gmg_define_level(gmg_ctx* c, int lev, int nboxes, const int* lohi, in
       boxes[b].hi[d] = lohi[6 * b + 3 + d];
     }
   if (lev == 0) return build_hierarchy(c, boxes, std::vector<int>(boxes.size(), 0));
-  // AMR level 1: ratio 2 over part of level 0 (Sec. "Basic data structures": refinement
-  // ratio between levels; proper nesting inside level 0)
+  // AMR level lev >= 1: ratio 2 over part of level lev - 1 (Sec. "Basic data structures":
+  // refinement ratio between levels; proper nesting inside the level below)
   if (c->L.empty()) SETERR(c, GMG_ERR_STATE, "define AMR level 0 first");
+  if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "AMR levels: single-problem contexts only");
+  if (lev > (int)c->amrl.size() + 1 || lev > GMG_MAX_AMR_LEVELS - 1)
+    SETERR(c, GMG_ERR_BAD_INPUT, "define AMR levels in order (at most " + std::to_string(GMG_MAX_AMR_LEVELS) + ")");
   if (ref_ratio != 2) SETERR(c, GMG_ERR_BAD_INPUT, "only refinement ratio 2 is supported");
   SolveGeom G = c->geoms[0];
   for (int d = 0; d < 3; ++d) {
-    G.domain.lo[d] = 2 * G.domain.lo[d];
-    G.domain.hi[d] = 2 * G.domain.hi[d] + 1;
-    G.h[d] *= 0.5;
+    G.domain.lo[d] = G.domain.lo[d] << lev;
+    G.domain.hi[d] = ((G.domain.hi[d] + 1) << lev) - 1;
+    G.h[d] /= (double)(1 << lev);
   }
+  const std::string tag = "level " + std::to_string(lev) + ": ";
   std::string e = validate_boxes(boxes, G.domain, false);
-  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, "level 1: " + e);
+  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, tag + e);
   drop_graphs(c);
   c->ws = nullptr;
   c->ws_bytes = 0;
-  c->have_beta = c->have_alpha = c->have_beta_f = c->have_alpha_f = false;
+  c->have_beta = c->have_alpha = false;
+  c->amrl.resize(lev - 1);  // a new level lev drops the levels above it
+  for (AmrLevel& A : c->amrl) A.have_beta = A.have_alpha = false;
   c->coefs_dirty = true;
-  LevelMeta F;
-  F.allow_cf = true;
-  F.boxes = boxes;
-  F.box_solve.assign(boxes.size(), 0);
-  F.geoms = {G};
-  F.solve_present = {1};
-  F.solve_bottom = {0};
-  e = finalize_level(F);
-  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, "level 1: " + e);
-  AmrHost H;
-  e = build_amr(c->L[0], F, H);
-  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, "level 1: " + e);
-  c->F = F;
-  c->amr_host = H;
+  AmrLevel N;
+  N.M.allow_cf = true;
+  N.M.boxes = boxes;
+  N.M.box_solve.assign(boxes.size(), 0);
+  N.M.geoms = {G};
+  N.M.solve_present = {1};
+  N.M.solve_bottom = {0};
+  e = finalize_level(N.M);
+  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, tag + e);
+  e = build_amr(lev == 1 ? c->L[0] : c->amrl[lev - 2].M, N.M, N.H);
+  if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, tag + e);
+  c->amrl.push_back(std::move(N));
   c->amr = true;
   return GMG_OK;
 }
@@ -2030,16 +2151,17 @@ gmg_status gmg_mg_layout(const gmg_ctx* c, int m, int dt, int64_t* nelems, int64
 gmg_status gmg_layout(const gmg_ctx* c, int lev, int64_t* nelems, int64_t* offs) {
   if (!c) return GMG_ERR_BAD_INPUT;
   if (lev == 0) return gmg_mg_layout(c, 0, DT_F64, nelems, offs, nullptr);
-  if (lev != 1 || !c->amr) return GMG_ERR_BAD_INPUT;
-  if (nelems) *nelems = c->F.nelem;
+  if (lev < 1 || lev > (int)c->amrl.size()) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = c->amrl[lev - 1].M;
+  if (nelems) *nelems = M.nelem;
   if (offs)
-    for (size_t b = 0; b < c->F.dbox.size(); ++b) offs[b] = c->F.dbox[b].off;
+    for (size_t b = 0; b < M.dbox.size(); ++b) offs[b] = M.dbox[b].off;
   return GMG_OK;
 }
 
 gmg_status gmg_amr_level_boxes(const gmg_ctx* c, int lev, int* nboxes, int* lohi, int* row_strides) {
-  if (!c || (lev != 0 && lev != 1) || (lev == 1 && !c->amr) || c->L.empty()) return GMG_ERR_BAD_INPUT;
-  const LevelMeta& M = lev ? c->F : c->L[0];
+  if (!c || lev < 0 || lev > (int)c->amrl.size() || c->L.empty()) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = lev ? c->amrl[lev - 1].M : c->L[0];
   if (nboxes) *nboxes = (int)M.boxes.size();
   for (size_t b = 0; b < M.boxes.size(); ++b) {
     if (lohi)
@@ -2054,37 +2176,39 @@ gmg_status gmg_amr_level_boxes(const gmg_ctx* c, int lev, int* nboxes, int* lohi
 
 // dense (nz, ny, nx) array over the bounding box of AMR level lev's boxes <-> boxed layout
 gmg_status gmg_pack_amr(gmg_ctx* c, int lev, const double* dense, double* boxed) {
-  if (!c || (lev != 0 && lev != 1)) return GMG_ERR_BAD_INPUT;
+  if (!c || lev < 0) return GMG_ERR_BAD_INPUT;
   if (lev == 0) return gmg_pack_solve(c, 0, DT_F64, 0, dense, boxed);
-  if (!c->amr) SETERR(c, GMG_ERR_STATE, "no AMR level 1");
+  if (lev > (int)c->amrl.size()) SETERR(c, GMG_ERR_STATE, "no such AMR level");
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
-  Box bb = c->F.boxes[0];
-  for (const Box& B : c->F.boxes)
+  const AmrLevel& V = c->amrl[lev - 1];
+  Box bb = V.M.boxes[0];
+  for (const Box& B : V.M.boxes)
     for (int d = 0; d < 3; ++d) {
       bb.lo[d] = std::min(bb.lo[d], B.lo[d]);
       bb.hi[d] = std::max(bb.hi[d], B.hi[d]);
     }
   int dn[3] = {bb.n(0), bb.n(1), bb.n(2)};
-  launch_pack(DT_F64, c->devf, bb.lo, dn, dense, boxed, c->stream);
+  launch_pack(DT_F64, V.D, bb.lo, dn, dense, boxed, c->stream);
   CK(c, cudaGetLastError());
   return GMG_OK;
 }
 
 gmg_status gmg_unpack_amr(gmg_ctx* c, int lev, const double* boxed, double* dense) {
-  if (!c || (lev != 0 && lev != 1)) return GMG_ERR_BAD_INPUT;
+  if (!c || lev < 0) return GMG_ERR_BAD_INPUT;
   if (lev == 0) return gmg_unpack_solve(c, 0, DT_F64, 0, boxed, dense);
-  if (!c->amr) SETERR(c, GMG_ERR_STATE, "no AMR level 1");
+  if (lev > (int)c->amrl.size()) SETERR(c, GMG_ERR_STATE, "no such AMR level");
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
-  Box bb = c->F.boxes[0];
-  for (const Box& B : c->F.boxes)
+  const AmrLevel& V = c->amrl[lev - 1];
+  Box bb = V.M.boxes[0];
+  for (const Box& B : V.M.boxes)
     for (int d = 0; d < 3; ++d) {
       bb.lo[d] = std::min(bb.lo[d], B.lo[d]);
       bb.hi[d] = std::max(bb.hi[d], B.hi[d]);
     }
   int dn[3] = {bb.n(0), bb.n(1), bb.n(2)};
-  launch_unpack(DT_F64, c->devf, bb.lo, dn, boxed, dense, c->stream);
+  launch_unpack(DT_F64, V.D, bb.lo, dn, boxed, dense, c->stream);
   CK(c, cudaGetLastError());
   return GMG_OK;
 }
@@ -2137,10 +2261,11 @@ gmg_status gmg_set_acoef(gmg_ctx* c, int lev, const double* alpha) {
   if (!c) return GMG_ERR_BAD_INPUT;
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
-  if (!alpha || lev < 0 || lev > 1 || (lev == 1 && !c->amr)) SETERR(c, GMG_ERR_BAD_INPUT, "alpha: bad level or null");
-  if (lev == 1) {
-    CK(c, cudaMemcpyAsync(c->alphaf, alpha, 8 * (size_t)c->F.nelem, cudaMemcpyDeviceToDevice, c->stream));
-    c->have_alpha_f = true;
+  if (!alpha || lev < 0 || lev > (int)c->amrl.size()) SETERR(c, GMG_ERR_BAD_INPUT, "alpha: bad level or null");
+  if (lev >= 1) {
+    AmrLevel& V = c->amrl[lev - 1];
+    CK(c, cudaMemcpyAsync(V.alpha, alpha, 8 * (size_t)V.M.nelem, cudaMemcpyDeviceToDevice, c->stream));
+    V.have_alpha = true;
     c->coefs_dirty = true;
     return GMG_OK;
   }
@@ -2154,17 +2279,24 @@ gmg_status gmg_set_bcoef_cell(gmg_ctx* c, int lev, const double* beta) {
   if (!c) return GMG_ERR_BAD_INPUT;
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
-  if (!beta || lev < 0 || lev > 1 || (lev == 1 && !c->amr)) SETERR(c, GMG_ERR_BAD_INPUT, "beta: bad level or null");
+  if (!beta || lev < 0 || lev > (int)c->amrl.size()) SETERR(c, GMG_ERR_BAD_INPUT, "beta: bad level or null");
   cudaStream_t s = c->stream;
-  if (lev == 1) {  // coarse/fine faces take the fine cell's beta: ghost := adjacent cell
-    CK(c, cudaMemcpyAsync(c->betaf_cell, beta, 8 * (size_t)c->F.nelem, cudaMemcpyDeviceToDevice, s));
-    launch_fill(DT_F64, c->devf, c->betaf_cell, -1, 1, s);
-    launch_cf_fill(c->amrd, c->betaf_cell, nullptr, CF_COPY, s);
-    launch_faces_from_cell(c->devf, c->betaf_cell, c->bxf, c->byf, c->bzf, s);
+  auto all_set = [&]() {
+    if (!c->have_beta) return false;
+    for (const AmrLevel& V : c->amrl)
+      if (!V.have_beta) return false;
+    return true;
+  };
+  if (lev >= 1) {  // coarse/fine faces take the fine cell's beta: ghost := adjacent cell
+    AmrLevel& V = c->amrl[lev - 1];
+    CK(c, cudaMemcpyAsync(V.beta_cell, beta, 8 * (size_t)V.M.nelem, cudaMemcpyDeviceToDevice, s));
+    launch_fill(DT_F64, V.D, V.beta_cell, -1, 1, s);
+    launch_cf_fill(V.A, V.beta_cell, nullptr, CF_COPY, s);
+    launch_faces_from_cell(V.D, V.beta_cell, V.bx, V.by, V.bz, s);
     CK(c, cudaGetLastError());
-    c->have_beta_f = true;
+    V.have_beta = true;
     c->coefs_dirty = true;
-    return c->have_beta ? build_coefs(c) : GMG_OK;
+    return all_set() ? build_coefs(c) : GMG_OK;
   }
   CK(c, cudaMemcpyAsync(c->betac_cell, beta, 8 * (size_t)c->L[0].nelem, cudaMemcpyDeviceToDevice, s));
   launch_fill(DT_F64, c->dev[0], c->betac_cell, -1, 1, s);
@@ -2172,7 +2304,7 @@ gmg_status gmg_set_bcoef_cell(gmg_ctx* c, int lev, const double* beta) {
   CK(c, cudaGetLastError());
   c->have_beta = true;
   c->coefs_dirty = true;
-  if (c->amr && !c->have_beta_f) return GMG_OK;  // built once level 1's beta is set
+  if (!all_set()) return GMG_OK;  // built once every AMR level's beta is set
   return build_coefs(c);
 }
 
@@ -2449,8 +2581,13 @@ gmg_status gmg_apply(gmg_ctx* c, void* const* out, void* const* phi) {
   if ((st = build_coefs(c))) return st;
   cudaStream_t s = c->stream;
   if (c->amr) {
-    if (!out[1] || !phi[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
-    comp_apply(c, (double*)phi[0], (double*)phi[1], (double*)out[0], (double*)out[1], s);
+    double *x[GMG_MAX_AMR_LEVELS], *y[GMG_MAX_AMR_LEVELS];
+    for (int l = 0; l < namr(c); ++l) {
+      if (!out[l] || !phi[l]) SETERR(c, GMG_ERR_BAD_INPUT, "composite context: pass an array for every AMR level");
+      x[l] = (double*)phi[l];
+      y[l] = (double*)out[l];
+    }
+    comp_apply_n(c, x, y, s);
     CK(c, cudaGetLastError());
     return GMG_OK;
   }
@@ -2475,10 +2612,16 @@ gmg_status gmg_solve(gmg_ctx* c, void* const* phiv, const void* const* rhsv, dou
   if ((st = params_ok(c, p))) return st;
   if ((st = build_coefs(c))) return st;
   if (c->amr) {
-    if (!phiv[1] || !rhsv[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
-    if (p.precision != GMG_FP64) SETERR(c, GMG_ERR_BAD_INPUT, "the two-level solve runs in FP64");
-    return solve_amr(c, (double*)phiv[0], (double*)phiv[1], (const double*)rhsv[0], (const double*)rhsv[1], tol_rel,
-                     tol_abs, p, info);
+    double* x[GMG_MAX_AMR_LEVELS];
+    const double* b[GMG_MAX_AMR_LEVELS];
+    for (int l = 0; l < namr(c); ++l) {
+      if (!phiv[l] || !rhsv[l]) SETERR(c, GMG_ERR_BAD_INPUT, "composite context: pass arrays for every AMR level");
+      x[l] = (double*)phiv[l];
+      b[l] = (const double*)rhsv[l];
+    }
+    if (p.precision != GMG_FP64) SETERR(c, GMG_ERR_BAD_INPUT, "the composite solve runs in FP64");
+    if (p.krylov) SETERR(c, GMG_ERR_BAD_INPUT, "krylov: one-level contexts only");
+    return solve_amr_n(c, x, b, tol_rel, tol_abs, p, info);
   }
   if (p.krylov) return krylov_solve(c, (double*)phiv[0], (const double*)rhsv[0], tol_rel, tol_abs, p, info);
   return solve_impl(c, (double*)phiv[0], (const double*)rhsv[0], tol_rel, tol_abs, p, info);
@@ -2503,6 +2646,7 @@ gmg_status gmg_apply_transpose(gmg_ctx* c, void* const* out, void* const* y) {
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
   if ((st = build_coefs(c))) return st;
+  if (namr(c) > 2) SETERR(c, GMG_ERR_BAD_INPUT, "apply_transpose: two AMR levels at most");
   if (!out[1] || !y[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
   comp_apply_transpose(c, (double*)y[0], (double*)y[1], (double*)out[0], (double*)out[1], c->stream);
   CK(c, cudaGetLastError());
@@ -2524,6 +2668,7 @@ gmg_status gmg_solve_adjoint(gmg_ctx* c, void* const* lambda, const void* const*
     p.project_mean = 1;
     return solve_impl(c, (double*)lambda[0], (const double*)g[0], tol_rel, 0.0, p, info);
   }
+  if (namr(c) > 2) SETERR(c, GMG_ERR_BAD_INPUT, "adjoint: two AMR levels at most");
   if (!lambda[1] || !g[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
   p.precision = GMG_FP64;
   return solve_adjoint_amr(c, (double*)lambda[0], (double*)lambda[1], (const double*)g[0], (const double*)g[1],
@@ -2541,6 +2686,7 @@ gmg_status gmg_beta_grad_walls(gmg_ctx* c, void* const* dbeta, void* const* phi,
   if (st) return st;
   if ((st = build_coefs(c))) return st;
   if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "beta gradient: single-problem contexts only");
+  if (c->amr && namr(c) > 2) SETERR(c, GMG_ERR_BAD_INPUT, "beta gradient: two AMR levels at most");
   if (values && (st = wall_values_check(c, values))) return st;
   cudaStream_t s = c->stream;
   double* pc = (double*)phi[0];
@@ -2549,14 +2695,14 @@ gmg_status gmg_beta_grad_walls(gmg_ctx* c, void* const* dbeta, void* const* phi,
     if (!dbeta[1] || !phi[1] || !lambda[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass both levels");
     double* pf = (double*)phi[1];
     double* lf = (double*)lambda[1];
-    launch_zero_covered(c->amrd, lc, s);
+    launch_zero_covered(c->amrl[0].A, lc, s);
     fine_fill(c, pf, pc, CF_INTERP, s);
-    launch_fill(DT_F64, c->devf, lf, -1, 0, s);
+    launch_fill(DT_F64, c->amrl[0].D, lf, -1, 0, s);
     launch_fill(DT_F64, c->dev[0], pc, -1, 0, s);
     launch_fill(DT_F64, c->dev[0], lc, -1, 0, s);
-    launch_grad_beta(c->devf, pf, lf, c->betaf_cell, c->b, c->amrd.cfidx, c->amrd.cf, lc, c->amrd.hf_over_hc,
+    launch_grad_beta(c->amrl[0].D, pf, lf, c->amrl[0].beta_cell, c->b, c->amrl[0].A.cfidx, c->amrl[0].A.cf, lc, c->amrl[0].A.hf_over_hc,
                      nullptr, (double*)dbeta[1], s);
-    launch_grad_beta(c->dev[0], pc, lc, c->betac_cell, c->b, nullptr, nullptr, nullptr, 0.5, c->amrd.covered,
+    launch_grad_beta(c->dev[0], pc, lc, c->betac_cell, c->b, nullptr, nullptr, nullptr, 0.5, c->amrl[0].A.covered,
                      (double*)dbeta[0], s);
   } else {
     launch_fill(DT_F64, c->dev[0], pc, -1, 0, s);

@@ -553,6 +553,79 @@ class AmrContext(Context):
         return dc, df
 
 
+class MultiLevelContext(Context):
+    """Composite problem over several AMR levels: level 0 covers the domain, level l
+    (ratio 2 to level l - 1) is a BoxArray in level l's index space, properly nested.  Dense
+    arrays of level l >= 1 span the bounding box of its boxes.  Forward solve and operator
+    (the adjoint and the beta gradient take two levels: AmrContext)."""
+
+    def __init__(self, domain, level_boxes, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0), prob_hi=(1.0, 1.0, 1.0),
+                 stream=None):
+        super().__init__(domain, bc_lo, bc_hi, prob_lo, prob_hi, boxes=level_boxes[0], stream=stream)
+        self.nlev_amr = len(level_boxes)
+        self.level_boxes = [list(b) for b in level_boxes]
+        self.level_lo, self.level_shape_ = [(0, 0, 0)], [self.level_shape(0)]
+        for lev in range(1, self.nlev_amr):
+            boxes = level_boxes[lev]
+            flat = [v for b in boxes for v in (list(b[0]) + list(b[1]))]
+            self._check(self.L.gmg_define_level(self.h, lev, len(boxes), _arr(flat, C.c_int), 2))
+            lo = [min(b[0][d] for b in boxes) for d in range(3)]
+            hi = [max(b[1][d] for b in boxes) for d in range(3)]
+            self.level_lo.append(tuple(lo))
+            self.level_shape_.append(tuple(hi[d] - lo[d] + 1 for d in (2, 1, 0)))
+
+    def nelem(self, lev):
+        ne = C.c_int64()
+        self._check(self.L.gmg_layout(self.h, lev, C.byref(ne), None))
+        return ne.value
+
+    def level_field(self, lev):
+        import torch
+        return torch.zeros(self.nelem(lev), dtype=torch.float64, device="cuda")
+
+    def pack_level(self, lev, dense, out=None):
+        import torch
+        dense = torch.as_tensor(dense, dtype=torch.float64, device="cuda").contiguous()
+        out = self.level_field(lev) if out is None else out
+        self._check(self.L.gmg_pack_amr(self.h, lev, _ptr(dense), _ptr(out)))
+        self._keep.append(dense)
+        return out
+
+    def unpack_level(self, lev, boxed):
+        import torch
+        out = torch.zeros(self.level_shape_[lev], dtype=torch.float64, device=boxed.device)
+        self._check(self.L.gmg_unpack_amr(self.h, lev, _ptr(boxed), _ptr(out)))
+        return out
+
+    def set_coeffs(self, a=0.0, b=1.0, alphas=None, betas=None):
+        """alphas / betas: per-level dense arrays (level 0 over the domain, level l over its
+        bounding box) or None (1)."""
+        import torch
+        self._keep = []
+        self.set_scalars(a, b)
+        for lev in range(self.nlev_amr):
+            if alphas is not None:
+                self._check(self.L.gmg_set_acoef(self.h, lev, _ptr(self.pack_level(lev, alphas[lev]))))
+        for lev in range(self.nlev_amr):
+            beta = betas[lev] if betas is not None else torch.ones(self.level_shape_[lev], dtype=torch.float64)
+            self._check(self.L.gmg_set_bcoef_cell(self.h, lev, _ptr(self.pack_level(lev, beta))))
+
+    def solve_levels(self, rhss, tol_rel=1e-10, tol_abs=0.0, **params):
+        """rhss: boxed FP64 right-hand sides per level.  Returns (phis, info)."""
+        phis = [self.level_field(lev) for lev in range(self.nlev_amr)]
+        p = default_params(**params)
+        info = SolveInfo()
+        st = self.L.gmg_solve(self.h, _pp(*phis), _pp(*rhss), tol_rel, tol_abs, C.byref(p), C.byref(info))
+        if st not in (OK, NOT_CONVERGED):
+            self._check(st)
+        return phis, info
+
+    def apply_levels(self, xs):
+        outs = [self.level_field(lev) for lev in range(self.nlev_amr)]
+        self._check(self.L.gmg_apply(self.h, _pp(*outs), _pp(*xs)))
+        return outs
+
+
 class BatchContext(Context):
     """Several independent problems solved together (one launch per step covers them all).
 
