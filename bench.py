@@ -227,7 +227,7 @@ def _updates_per_vcycle_problem(ctx, s):
 def measure_forms(stream, barrier, dev, only=None):
     """The other workloads, each at full size: abec512 in FP64 and both mixed forms, batch64
     (64 uneven problems, batched form), amr2 (two-level composite forward + adjoint +
-    beta gradient).  Device time to 1e-10 per solve."""
+    beta gradient), amr3 (three-level composite forward), walls256, krylov.  Device time to 1e-10 per solve."""
     forms = {}
     if only in (None, "abec512"):
         forms["abec512"] = _form_abec512(stream, barrier)
@@ -235,6 +235,8 @@ def measure_forms(stream, barrier, dev, only=None):
         forms["batch64"] = _form_batch64(stream, barrier)
     if only in (None, "amr2"):
         forms["amr2"] = _form_amr2(stream, barrier, dev)
+    if only in (None, "amr3"):
+        forms["amr3"] = _form_amr3(stream, barrier)
     if only in (None, "walls256"):
         forms["walls256"] = _form_walls256(stream, barrier)
     if only in (None, "krylov"):
@@ -426,6 +428,31 @@ def _form_amr2(stream, barrier, dev):
             "beta_grad_ms": ms_g, "autotuned_level0_hierarchy": tuned}
 
 
+def _form_amr3(stream, barrier):
+    import torch
+
+    from paper_2009_12009_gb300 import gmg
+    from paper_2009_12009_gb300 import inputs as I
+
+    a = I.amr3()
+    ctx = gmg.MultiLevelContext(a["domain"], a["level_boxes"], a["bc_lo"], a["bc_hi"], stream=stream.cuda_stream)
+    ctx.allocate(gmg.FP64)
+    ctx.set_coeffs(0.0, 1.0, betas=[torch.from_numpy(b) for b in a["betas"]])
+    rs = [ctx.pack_level(lev, torch.from_numpy(r)) for lev, r in enumerate(a["rhss"])]
+    tuned = summarize_tuning(ctx.autotune(rs[0], gmg.FP64))
+    ms, (phis, info) = _timed(lambda: ctx.solve_levels(rs, tol_rel=TOL), 3, 1, stream, barrier)
+    cells = sum(int((~c).sum()) for c in a["covered"])
+    res = {"workload": "amr3: 128^3 periodic level 0 (8 boxes) + ratio-2 level 1 over the central 64^3 "
+                       "level-0 cells + ratio-2 level 2 over 64^3 level-1 cells off its centre (128^3 cells "
+                       "per level; 8, 8 and 64 boxes), seed 12017, tol 1e-10",
+           "composite_cells": cells,
+           "forward": {"time_to_tol_ms": ms, "iterations": info.iterations, "status": info.status},
+           "autotuned_level0_hierarchy": tuned}
+    del ctx, rs, phis
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -464,7 +491,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the 512^3, batched and two-level workloads")
-    ap.add_argument("--only", choices=["abec512", "batch64", "amr2", "walls256", "krylov"], default=None,
+    ap.add_argument("--only", choices=["abec512", "batch64", "amr2", "amr3", "walls256", "krylov"], default=None,
                     help="run and print only this one of the other workloads (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":

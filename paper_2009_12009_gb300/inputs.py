@@ -23,7 +23,7 @@ DIRICHLET = 1
 NEUMANN = 2
 
 SEEDS = {"poisson32": 12010, "abec256": 12011, "abec512": 12012, "batch64": 12013, "amr2": 12014,
-         "walls256": 12015, "contrast256": 12016}
+         "walls256": 12015, "contrast256": 12016, "amr3": 12017}
 BATCH_EDGES = (32, 48, 64, 96, 128, 160)
 
 
@@ -207,3 +207,35 @@ def amr2(n=128, seed=None):
                 fine_slice=(lo, hi), bc_lo=[PERIODIC] * 3, bc_hi=[PERIODIC] * 3, a=0.0, b=1.0, beta_c=beta_c,
                 beta_f=beta_f, rhs_c=rhs_c, rhs_f=rhs_f, covered=covered,
                 target_c=rng.standard_normal(cshape) * ~covered, target_f=rng.standard_normal(fshape))
+
+
+def amr3(n=128, seed=None):
+    """Three-level composite workload: level 0 n^3 periodic in boxes of (n/2)^3; level 1 at
+    ratio 2 over level-0 cells [n/4, 3n/4)^3 (level-1 cells [n/2, 3n/2)^3, 8 boxes of
+    (n/2)^3); level 2 at ratio 2 over level-1 cells [5n/8, 9n/8)^3, off the centre of level 1
+    (level-2 cells [5n/4, 9n/4)^3, 64 boxes of (n/4)^3, so that each lies, coarsened, inside
+    one level-1 box).  beta log-normal smoothed per level
+    (periodic wrap on level 0, window truncated at the patch edge above), cells under a finer
+    level take the average of their children, finest pair first; rhs N(0,1) on the composite
+    cells minus its volume-weighted mean.  Arrays of level l span its patch (n^3 each);
+    `level_lo` is the patch's low corner in level l's index space."""
+    rng = np.random.default_rng(SEEDS["amr3"] if seed is None else seed)
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    los = [0, n // 2, 5 * n // 4]
+    level_boxes = [chop((lo,) * 3, (lo + n - 1,) * 3, n // 2 if l < 2 else n // 4) for l, lo in enumerate(los)]
+    shape = (n, n, n)
+    betas = [lognormal_beta(rng, shape, periodic=(l == 0)) for l in range(3)]
+    covered = [np.zeros(shape, dtype=bool) for _ in range(3)]
+    for l in (1, 0):
+        # the finer patch's footprint in level l's patch-relative indices
+        a = los[l + 1] // 2 - los[l]
+        m = n // 2
+        avg = betas[l + 1].reshape(m, 2, m, 2, m, 2).mean(axis=(1, 3, 5))
+        betas[l][a:a + m, a:a + m, a:a + m] = avg
+        covered[l][a:a + m, a:a + m, a:a + m] = True
+    rhss = [rng.standard_normal(shape) * ~c for c in covered]
+    vol = [8.0 ** (-l) for l in range(3)]
+    mean = sum(v * r.sum() for v, r in zip(vol, rhss)) / sum(v * (~c).sum() for v, c in zip(vol, covered))
+    rhss = [(r - mean) * ~c for r, c in zip(rhss, covered)]
+    return dict(name="amr3", domain=dom, level_boxes=level_boxes, level_lo=[(lo,) * 3 for lo in los],
+                bc_lo=[PERIODIC] * 3, bc_hi=[PERIODIC] * 3, a=0.0, b=1.0, betas=betas, rhss=rhss, covered=covered)

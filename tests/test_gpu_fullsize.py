@@ -16,6 +16,9 @@ the oracle.
   * amr2 (two levels, 128^3 + 128^3): two composite iterations element by element; the
     converged forward and adjoint solves' residuals by the oracle's composite operator and
     its transpose; the beta gradient of the GPU's phi and lambda against the oracle's.
+  * amr3 (three levels, 128^3 cells each, level 2 off the centre of level 1): two composite
+    iterations element by element; the converged solve's residual by the oracle's
+    composite operator.
 """
 import numpy as np
 import pytest
@@ -299,3 +302,52 @@ def test_amr2_autograd_vs_central_differences(amr2):
     pred_beta = float((bc.grad * bc0 * vc).sum() + (bf.grad * bf0 * vf).sum())
     assert abs(fd_rhs - pred_rhs) <= 1e-6 * abs(fd_rhs), (fd_rhs, pred_rhs)
     assert abs(fd_beta - pred_beta) <= 1e-6 * abs(fd_beta), (fd_beta, pred_beta)
+
+
+class Amr3:
+    def __init__(self):
+        a = self.cfg = I.amr3()
+        self.C = gmg.MultiLevelContext(a["domain"], a["level_boxes"], a["bc_lo"], a["bc_hi"], stream=stream())
+        self.C.allocate(gmg.FP64)
+        self.C.set_coeffs(0.0, 1.0, betas=[torch.from_numpy(b) for b in a["betas"]])
+        self.P = O.MultiLevelProblem(a["domain"], a["level_boxes"], a["bc_lo"], a["bc_hi"])
+        n = a["rhss"][0].shape[0]
+        self.sl = [tuple(slice(lo[d], lo[d] + n) for d in (2, 1, 0)) for lo in a["level_lo"]]
+        self.P.set_coeffs(0.0, 1.0, betas=[self.embed(lev, b, fill=1.0) for lev, b in enumerate(a["betas"])])
+
+    def embed(self, lev, x, fill=0.0):
+        out = np.full(self.P.shapes[lev], fill)
+        out[self.sl[lev]] = x
+        return out
+
+    def rhs_full(self):
+        return [self.embed(lev, r) for lev, r in enumerate(self.cfg["rhss"])]
+
+    def to_gpu(self):
+        return [self.C.pack_level(lev, torch.from_numpy(r)) for lev, r in enumerate(self.cfg["rhss"])]
+
+    def from_gpu(self, gs):
+        return [self.embed(lev, self.C.unpack_level(lev, g).cpu().numpy()) * m
+                for lev, (g, m) in enumerate(zip(gs, self.P.inside))]
+
+
+@pytest.fixture(scope="module")
+def amr3():
+    return Amr3()
+
+
+def test_amr3_two_iterations_match_oracle(amr3):
+    want, it, hist, st = amr3.P.solve(amr3.rhs_full(), tol_rel=0.0, maxit=2)
+    phis, info = amr3.C.solve_levels(amr3.to_gpu(), tol_rel=0.0, max_iter=2)
+    assert info.iterations == it == 2
+    np.testing.assert_allclose(info.history(), hist, rtol=1e-8)
+    w = amr3.P.pack(want)
+    assert np.abs(amr3.P.pack(amr3.from_gpu(phis)) - w).max() <= 1e-10 * np.abs(w).max()
+
+
+def test_amr3_converged_residual_by_oracle(amr3):
+    phis, info = amr3.C.solve_levels(amr3.to_gpu(), tol_rel=TOL)
+    assert info.status == gmg.OK
+    rhs = amr3.rhs_full()
+    r = amr3.P.pack(rhs) - amr3.P.pack(amr3.P.apply(amr3.from_gpu(phis)))
+    assert np.abs(r).max() <= RES_BOUND * np.abs(amr3.P.pack(rhs)).max()

@@ -175,3 +175,38 @@ def test_coefficients_under_finer_levels_are_restricted(orc):
     G = (7, 7, 8)  # a level-0 cell whose low x-face lies deep under level 2 ([6, 10) in level-0 units)
     want = np.mean([face_x(2, (4 * G[0], 4 * G[1] + u, 4 * G[2] + v)) for u in range(4) for v in range(4)])
     assert abs(face_x(0, G) - want) <= 1e-14 * want
+
+
+def test_amr3_recipe_small(orc):
+    """The three-level workload recipe at n = 16: covered cells of levels 0 and 1 carry the
+    average of their children, the rhs has zero volume-weighted mean and vanishes under finer
+    levels, and the oracle's composite solve reaches 1e-10 contracting steadily."""
+    a = I.amr3(16)
+    n = 16
+    M = orc.MultiLevelProblem(a["domain"], a["level_boxes"], a["bc_lo"], a["bc_hi"])
+    sl = [tuple(slice(lo[d], lo[d] + n) for d in (2, 1, 0)) for lo in a["level_lo"]]
+
+    def embed(l, x, fill=0.0):
+        out = np.full(M.shapes[l], fill)
+        out[sl[l]] = x
+        return out
+
+    for l in (1, 2):  # every box, coarsened, inside one box of the level below
+        for lo, hi in a["level_boxes"][l]:
+            assert any(all(blo[d] <= lo[d] // 2 and hi[d] // 2 <= bhi[d] for d in range(3))
+                       for blo, bhi in a["level_boxes"][l - 1])
+    for l in (0, 1):
+        cov = a["covered"][l]
+        assert (embed(l, cov.astype(float)) > 0).sum() == cov.sum() == (n // 2) ** 3
+        under = M.inside[l + 1].reshape(M.shapes[l][0], 2, M.shapes[l][1], 2, M.shapes[l][2], 2).all(axis=(1, 3, 5))
+        assert np.array_equal(embed(l, cov.astype(float)) > 0, under)
+        fine = embed(l + 1, a["betas"][l + 1], fill=np.nan)
+        want = avg_down(fine)[under]
+        assert np.allclose(embed(l, a["betas"][l])[under], want, rtol=1e-15, atol=0)
+        assert not a["rhss"][l][cov].any()
+    rs = [embed(l, r) for l, r in enumerate(a["rhss"])]
+    assert abs(M.volumes() @ M.pack(rs)) <= 1e-13 * (M.volumes() @ np.abs(M.pack(rs)))
+    M.set_coeffs(0.0, 1.0, betas=[embed(l, b, fill=1.0) for l, b in enumerate(a["betas"])])
+    ps, it, hist, st = M.solve(rs, tol_rel=1e-10, maxit=100)
+    assert st == 0 and hist[-1] <= 1e-10 * hist[0]
+    assert all(hist[i + 1] < 0.5 * hist[i] for i in range(len(hist) - 1)), hist
