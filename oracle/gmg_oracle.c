@@ -1860,6 +1860,53 @@ void orc_amr_apply(void* vp, const double* xc_d, const double* xf_d, double* yc_
   free(xc); free(xf); free(yc); free(yf);
 }
 
+/* dL/dbeta at the cells of one level (dense, zeroed first) from its per-face gradients g[d]
+   (boxed face slots): a face between two cells of the level took the harmonic mean
+   2 bL bR / (bL + bR) (d/dbL = 2 bR^2 / (bL + bR)^2); a wall face, or a face on the
+   level's coarse/fine boundary, took the one adjacent cell's beta (d = 1). */
+static void face_grads_to_cells(const olev* l, double* const* g, const double* beta_dl, double* out_dl) {
+  int64_t nx = l->dhi[0] - l->dlo[0] + 1, ny = l->dhi[1] - l->dlo[1] + 1, nz = l->dhi[2] - l->dlo[2] + 1;
+  memset(out_dl, 0, sizeof(double) * nx * ny * nz);
+  for (int b = 0; b < l->nb; ++b)
+    for (int d = 0; d < 3; ++d) {
+      int ext[3] = {bn(l, b, 0), bn(l, b, 1), bn(l, b, 2)};
+      ext[d] += 1;
+      for (int k = 0; k < ext[2]; ++k)
+        for (int j = 0; j < ext[1]; ++j)
+          for (int i = 0; i < ext[0]; ++i) {
+            int loc[3] = {i, j, k};
+            double gface = g[d][IX(l, b, i, j, k)];
+            if (gface == 0.0) continue;
+            /* a face shared by two boxes has a slot in each; each slot carries the part
+               of dL/dbeta of the rows that read it, so every slot is mapped to its cells */
+            int gR[3], gL[3];
+            for (int q = 0; q < 3; ++q) gR[q] = gL[q] = l->lo[3 * b + q] + loc[q];
+            gL[d] -= 1;
+            int per = l->bclo[d] == ORC_PERIODIC;
+            int len = l->dhi[d] - l->dlo[d] + 1;
+            int Lw[3] = {gL[0], gL[1], gL[2]}, Rw[3] = {gR[0], gR[1], gR[2]};
+            if (per) {
+              Lw[d] = l->dlo[d] + pmod(Lw[d] - l->dlo[d], len);
+              Rw[d] = l->dlo[d] + pmod(Rw[d] - l->dlo[d], len);
+            }
+            int Lin = (per || (gL[d] >= l->dlo[d])) && find_box(l, Lw) >= 0;
+            int Rin = (per || (gR[d] <= l->dhi[d])) && find_box(l, Rw) >= 0;
+            int64_t iL = (Lw[0] - l->dlo[0]) + nx * ((Lw[1] - l->dlo[1]) + ny * (int64_t)(Lw[2] - l->dlo[2]));
+            int64_t iR = (Rw[0] - l->dlo[0]) + nx * ((Rw[1] - l->dlo[1]) + ny * (int64_t)(Rw[2] - l->dlo[2]));
+            if (Lin && Rin) {
+              double bl = beta_dl[iL], br = beta_dl[iR], s2 = (bl + br) * (bl + br);
+              out_dl[iL] += gface * 2.0 * br * br / s2;
+              out_dl[iR] += gface * 2.0 * bl * bl / s2;
+            } else if (Rin) {
+              out_dl[iR] += gface;
+            } else if (Lin) {
+              out_dl[iL] += gface;
+            }
+            (void)nz;
+          }
+    }
+}
+
 /* dL/dbeta at cells (dense) from the face gradients: a face between two cells of the same
    level took the harmonic mean 2 bL bR / (bL + bR) (d/dbL = 2 bR^2 / (bL + bR)^2); a wall
    face or a coarse/fine fine face took the one adjacent cell's beta (d = 1). */
@@ -1886,49 +1933,7 @@ void orc_amr_grad_beta_cells(void* vp, const double* phic_d, const double* phif_
   orc_amr_grad_faces(A, v[0][0], v[1][0], v[0][1], v[1][1], g[0][0], g[0][1], g[0][2], g[1][0], g[1][1], g[1][2]);
   const double* beta_d[2] = {betac_d, betaf_d};
   double* out_d[2] = {gc_d, gf_d};
-  for (int w = 0; w < 2; ++w) {
-    const olev* l = &P[w]->L[0];
-    int64_t nx = l->dhi[0] - l->dlo[0] + 1, ny = l->dhi[1] - l->dlo[1] + 1, nz = l->dhi[2] - l->dlo[2] + 1;
-    memset(out_d[w], 0, sizeof(double) * nx * ny * nz);
-    for (int b = 0; b < l->nb; ++b)
-      for (int d = 0; d < 3; ++d) {
-        int ext[3] = {bn(l, b, 0), bn(l, b, 1), bn(l, b, 2)};
-        ext[d] += 1;
-        for (int k = 0; k < ext[2]; ++k)
-          for (int j = 0; j < ext[1]; ++j)
-            for (int i = 0; i < ext[0]; ++i) {
-              int loc[3] = {i, j, k};
-              double gface = g[w][d][IX(l, b, i, j, k)];
-              if (gface == 0.0) continue;
-              /* a face shared by two boxes has a slot in each; each slot carries the part
-                 of dL/dbeta of the rows that read it, so every slot is mapped to its cells */
-              int gR[3], gL[3];
-              for (int q = 0; q < 3; ++q) gR[q] = gL[q] = l->lo[3 * b + q] + loc[q];
-              gL[d] -= 1;
-              int per = l->bclo[d] == ORC_PERIODIC;
-              int len = l->dhi[d] - l->dlo[d] + 1;
-              int Lw[3] = {gL[0], gL[1], gL[2]}, Rw[3] = {gR[0], gR[1], gR[2]};
-              if (per) {
-                Lw[d] = l->dlo[d] + pmod(Lw[d] - l->dlo[d], len);
-                Rw[d] = l->dlo[d] + pmod(Rw[d] - l->dlo[d], len);
-              }
-              int Lin = (per || (gL[d] >= l->dlo[d])) && find_box(l, Lw) >= 0;
-              int Rin = (per || (gR[d] <= l->dhi[d])) && find_box(l, Rw) >= 0;
-              int64_t iL = (Lw[0] - l->dlo[0]) + nx * ((Lw[1] - l->dlo[1]) + ny * (int64_t)(Lw[2] - l->dlo[2]));
-              int64_t iR = (Rw[0] - l->dlo[0]) + nx * ((Rw[1] - l->dlo[1]) + ny * (int64_t)(Rw[2] - l->dlo[2]));
-              if (Lin && Rin) {
-                double bl = beta_d[w][iL], br = beta_d[w][iR], s2 = (bl + br) * (bl + br);
-                out_d[w][iL] += gface * 2.0 * br * br / s2;
-                out_d[w][iR] += gface * 2.0 * bl * bl / s2;
-              } else if (Rin) {
-                out_d[w][iR] += gface;
-              } else if (Lin) {
-                out_d[w][iL] += gface;
-              }
-              (void)nz;
-            }
-      }
-  }
+  for (int w = 0; w < 2; ++w) face_grads_to_cells(&P[w]->L[0], g[w], beta_d[w], out_d[w]);
   for (int w = 0; w < 2; ++w) {
     free(v[w][0]);
     free(v[w][1]);
@@ -2132,6 +2137,126 @@ static double mlv_row(const omlv* M, const double* const* x, int l, int b, int i
 
 static int mlv_covered(const omlv* M, int l, int64_t q) { return l + 1 < M->L && M->pair[l].covered[q]; }
 
+/* The row of an uncovered cell written as terms coef * x[level][q] (the row mlv_row
+   evaluates, term by term), so that one walk over the rows gives A x (mode 0), scatters
+   A^T y (mode 1: each term of row r adds coef * y_r to its column) or the face gradient
+   dL/dbeta_face = -sum_r y_r (d coef / d beta_face) x_q (mode 2).  A term whose coefficient
+   is b beta_face / h^2 names that face: level fw, direction fd, boxed slot fs (fw < 0:
+   none). */
+typedef struct {
+  int mode;
+  const double* const* x;   /* modes 0 and 2 */
+  double* const* y;         /* mode 1: output */
+  double yrow, acc;
+  double* g[ORC_MAXAMR][3]; /* mode 2: output */
+  int bad;                  /* modes 1 and 2: a term read a covered cell */
+} mterm;
+
+static void mlv_term(const omlv* M, mterm* R, int lx, int64_t q, double c, int fw, int fd, int64_t fs) {
+  double beta = 1.0;
+  if (fw >= 0) {
+    const olev* f = &M->P[fw]->L[0];
+    beta = (fd == 0 ? f->bx : (fd == 1 ? f->by : f->bz))[fs];
+  }
+  if (R->mode != 0 && mlv_covered(M, lx, q)) R->bad = 1;
+  if (R->mode == 0) R->acc += c * beta * R->x[lx][q];
+  else if (R->mode == 1) R->y[lx][q] += c * beta * R->yrow;
+  else if (fw >= 0) R->g[fw][fd][fs] -= R->yrow * c * R->x[lx][q];
+}
+
+/* the value of level l's ghost slot gq as terms, scaled by c (face tag passed through) */
+static void mlv_ghost_terms(const omlv* M, mterm* R, int l, int64_t gq, double c, int fw, int fd, int64_t fs) {
+  if (l > 0) {
+    const oamr* A = &M->pair[l - 1];
+    int64_t cfi = A->cfidx[gq];
+    if (cfi >= 0) {
+      const ocfghost* G = &A->cf[cfi];
+      for (int e = 0; e < 5; ++e) mlv_term(M, R, l - 1, G->cq[e], c * (8.0 / 15.0) * G->cw[e], fw, fd, fs);
+      mlv_term(M, R, l, G->f1, c * (2.0 / 3.0), fw, fd, fs);
+      mlv_term(M, R, l, G->f2, c * (-0.2), fw, fd, fs);
+      return;
+    }
+  }
+  const olev* f = &M->P[l]->L[0];
+  int64_t e = M->gentry[l][gq];
+  mlv_term(M, R, l, f->gsrc[e], c * f->gfac[e], fw, fd, fs);
+}
+
+static void mlv_row_terms(const omlv* M, mterm* R, int l, int b, int i, int j, int k) {
+  const olev* f = &M->P[l]->L[0];
+  const int64_t q = IX(f, b, i, j, k);
+  const int loc[3] = {i, j, k};
+  mlv_term(M, R, l, q, M->a * f->alpha[q], -1, 0, 0);
+  for (int d = 0; d < 3; ++d) {
+    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    for (int side = 0; side < 2; ++side) {
+      int nl[3] = {loc[0], loc[1], loc[2]};
+      nl[d] += side ? 1 : -1;
+      const int inside = nl[d] >= 0 && nl[d] < bn(f, b, d);
+      const int64_t nq = IX(f, b, nl[0], nl[1], nl[2]);
+      int64_t src = -1;
+      if (inside) {
+        src = nq;
+      } else {
+        int64_t e = M->gentry[l][nq];
+        if (f->gsrc[e] >= 0 && f->gwall[e] < 0) src = f->gsrc[e];
+      }
+      if (l + 1 < M->L && src >= 0 && M->pair[l].covered[src]) {
+        /* reflux: b / h_c times the mean of the 4 fine fluxes beta_f (x_g - x_f) / h_f */
+        const olev* fn = &M->P[l + 1]->L[0];
+        int gl[3] = {f->lo[3 * b] + i, f->lo[3 * b + 1] + j, f->lo[3 * b + 2] + k};
+        int gn[3] = {gl[0], gl[1], gl[2]};
+        gn[d] += side ? 1 : -1;
+        double cf = M->b * 0.25 / (fn->h[d] * f->h[d]);
+        for (int u = 0; u < 2; ++u)
+          for (int w = 0; w < 2; ++w) {
+            int fg[3];
+            fg[d] = side ? 2 * gn[d] : 2 * gn[d] + 1;
+            fg[d1] = 2 * gl[d1] + u;
+            fg[d2] = 2 * gl[d2] + w;
+            wrap_periodic(fn, fg);
+            int fb = find_box(fn, fg);
+            int fl[3] = {fg[0] - fn->lo[3 * fb], fg[1] - fn->lo[3 * fb + 1], fg[2] - fn->lo[3 * fb + 2]};
+            int ghl[3] = {fl[0], fl[1], fl[2]};
+            ghl[d] += side ? -1 : 1;
+            int sl[3] = {fl[0], fl[1], fl[2]};
+            if (!side) sl[d] += 1;
+            int64_t fs = IX(fn, fb, sl[0], sl[1], sl[2]);
+            mlv_term(M, R, l + 1, IX(fn, fb, fl[0], fl[1], fl[2]), -cf, l + 1, d, fs);
+            mlv_ghost_terms(M, R, l + 1, IX(fn, fb, ghl[0], ghl[1], ghl[2]), cf, l + 1, d, fs);
+          }
+        continue;
+      }
+      int fl[3] = {loc[0], loc[1], loc[2]};
+      if (side) fl[d] += 1;
+      const int64_t fs = IX(f, b, fl[0], fl[1], fl[2]);
+      const double w = M->b / (f->h[d] * f->h[d]);
+      mlv_term(M, R, l, q, w, l, d, fs);
+      if (inside) mlv_term(M, R, l, nq, -w, l, d, fs);
+      else mlv_ghost_terms(M, R, l, nq, -w, l, d, fs);
+    }
+  }
+}
+
+/* every uncovered row once; mode 0 stores the row value in yout, modes 1 and 2 take the
+   row's weight from yin */
+static void mlv_walk(const omlv* M, mterm* R, double* const* yout, double* const* yin) {
+  for (int l = 0; l < M->L; ++l) {
+    const olev* f = &M->P[l]->L[0];
+    for (int b = 0; b < f->nb; ++b)
+      for (int k = 0; k < bn(f, b, 2); ++k)
+        for (int j = 0; j < bn(f, b, 1); ++j)
+          for (int i = 0; i < bn(f, b, 0); ++i) {
+            int64_t q = IX(f, b, i, j, k);
+            if (mlv_covered(M, l, q)) continue;
+            R->acc = 0.0;
+            if (yin) R->yrow = yin[l][q];
+            mlv_row_terms(M, R, l, b, i, j, k);
+            if (yout) yout[l][q] = R->acc;
+          }
+  }
+}
+
 /* y = A x over all levels (boxed); covered entries of y are 0 */
 static void mlv_apply(const omlv* M, const double* const* x, double* const* y) {
   for (int l = 0; l < M->L; ++l) {
@@ -2327,4 +2452,79 @@ void orc_mlv_apply(void* vp, const double* const* x_d, double* const* y_d) {
     orc_boxed_to_dense(M->P[l], 0, y[l], y_d[l]);
     free(x[l]); free(y[l]);
   }
+}
+
+/* y = A x through the term walk (the same rows as orc_mlv_apply, summed term by term) */
+void orc_mlv_apply_terms(void* vp, const double* const* x_d, double* const* y_d) {
+  omlv* M = (omlv*)vp;
+  double *x[ORC_MAXAMR], *y[ORC_MAXAMR];
+  for (int l = 0; l < M->L; ++l) {
+    int64_t n = M->P[l]->L[0].ntot;
+    x[l] = calloc(n, 8);
+    y[l] = calloc(n, 8);
+    orc_dense_to_boxed(M->P[l], 0, x_d[l], x[l]);
+  }
+  mterm R;
+  memset(&R, 0, sizeof(R));
+  R.mode = 0;
+  R.x = (const double* const*)x;
+  mlv_walk(M, &R, y, NULL);
+  for (int l = 0; l < M->L; ++l) {
+    orc_boxed_to_dense(M->P[l], 0, y[l], y_d[l]);
+    free(x[l]); free(y[l]);
+  }
+}
+
+/* x = A^T y for dense level arrays (covered entries of y are ignored, those of x are 0).
+   Returns 0, or -1 when a term reads a cell covered by a finer level (a level closer than
+   two cells to the coarse/fine boundary of the level it refines): the covered values are
+   then averages of finer ones, and A is not a matrix over the unknowns alone. */
+int orc_mlv_apply_transpose(void* vp, const double* const* y_d, double* const* x_d) {
+  omlv* M = (omlv*)vp;
+  double *x[ORC_MAXAMR], *y[ORC_MAXAMR];
+  for (int l = 0; l < M->L; ++l) {
+    int64_t n = M->P[l]->L[0].ntot;
+    x[l] = calloc(n, 8);
+    y[l] = calloc(n, 8);
+    orc_dense_to_boxed(M->P[l], 0, y_d[l], y[l]);
+  }
+  mterm R;
+  memset(&R, 0, sizeof(R));
+  R.mode = 1;
+  R.y = x;
+  mlv_walk(M, &R, NULL, y);
+  for (int l = 0; l < M->L; ++l) {
+    orc_boxed_to_dense(M->P[l], 0, x[l], x_d[l]);
+    free(x[l]); free(y[l]);
+  }
+  return R.bad ? -1 : 0;
+}
+
+/* dL/dbeta at the cells of every level (dense; covered cells 0) for L = lambda^T (rhs - A phi):
+   -lambda^T (dA/dbeta_face) phi per face (lambda's covered entries are ignored), then through
+   the face rule of each level (face_grads_to_cells).  Faces under a finer level shape only
+   the correction operator, so they take no gradient.  Returns 0 or -1 (as the transpose). */
+int orc_mlv_grad_beta_cells(void* vp, const double* const* phi_d, const double* const* lam_d,
+                            const double* const* beta_d, double* const* out_d) {
+  omlv* M = (omlv*)vp;
+  double *phi[ORC_MAXAMR], *lam[ORC_MAXAMR];
+  mterm R;
+  memset(&R, 0, sizeof(R));
+  R.mode = 2;
+  for (int l = 0; l < M->L; ++l) {
+    int64_t n = M->P[l]->L[0].ntot;
+    phi[l] = calloc(n, 8);
+    lam[l] = calloc(n, 8);
+    orc_dense_to_boxed(M->P[l], 0, phi_d[l], phi[l]);
+    orc_dense_to_boxed(M->P[l], 0, lam_d[l], lam[l]);
+    for (int d = 0; d < 3; ++d) R.g[l][d] = calloc(n, 8);
+  }
+  R.x = (const double* const*)phi;
+  mlv_walk(M, &R, NULL, lam);
+  for (int l = 0; l < M->L; ++l) {
+    face_grads_to_cells(&M->P[l]->L[0], R.g[l], beta_d[l], out_d[l]);
+    free(phi[l]); free(lam[l]);
+    for (int d = 0; d < 3; ++d) free(R.g[l][d]);
+  }
+  return R.bad ? -1 : 0;
 }

@@ -475,6 +475,11 @@ def _declare_mlv(L):
     L.orc_mlv_solve.restype = C.c_int
     L.orc_mlv_level.restype = vp
     L.orc_mlv_level.argtypes = [vp, C.c_int]
+    L.orc_mlv_apply_terms.argtypes = [vp, pp, pp]
+    L.orc_mlv_apply_transpose.argtypes = [vp, pp, pp]
+    L.orc_mlv_apply_transpose.restype = C.c_int
+    L.orc_mlv_grad_beta_cells.argtypes = [vp, pp, pp, pp, pp]
+    L.orc_mlv_grad_beta_cells.restype = C.c_int
 
 
 def _ptrs(arrays):
@@ -544,11 +549,31 @@ class MultiLevelProblem:
         lib().orc_mlv_set_coeffs(self.h, a, b, _ptrs(self._coef[0]) if alphas is not None else None,
                                  _ptrs(self._coef[1]) if betas is not None else None)
 
-    def apply(self, xs):
+    def apply(self, xs, transpose=False, terms=False):
+        """A x (rows evaluated directly; terms=True: the same rows summed term by term), or
+        A^T x (scattered term by term; raises ValueError where a term reads a covered cell).
+        Entries outside the unknowns are 0."""
         xs = [_f64(x) for x in xs]
         ys = [np.zeros(s) for s in self.shapes]
-        lib().orc_mlv_apply(self.h, _ptrs(xs), _ptrs(ys))
+        if transpose:
+            if lib().orc_mlv_apply_transpose(self.h, _ptrs(xs), _ptrs(ys)) != 0:
+                raise ValueError("oracle: a coarse/fine term reads a covered cell (nesting closer than two cells)")
+        elif terms:
+            lib().orc_mlv_apply_terms(self.h, _ptrs(xs), _ptrs(ys))
+        else:
+            lib().orc_mlv_apply(self.h, _ptrs(xs), _ptrs(ys))
         return [y * m for y, m in zip(ys, self.masks)]
+
+    def grad_beta(self, phis, lams, betas=None):
+        """dL/dbeta per level (dense; 0 outside the unknowns) for L = lambda^T (rhs - A(beta) phi),
+        betas the cell arrays given to set_coeffs (None: 1)."""
+        phis = [_f64(x) for x in phis]
+        lams = [_f64(x) for x in lams]
+        betas = [_f64(np.ones(s) if betas is None else b) for s, b in zip(self.shapes, betas or [None] * self.L)]
+        outs = [np.zeros(s) for s in self.shapes]
+        if lib().orc_mlv_grad_beta_cells(self.h, _ptrs(phis), _ptrs(lams), _ptrs(betas), _ptrs(outs)) != 0:
+            raise ValueError("oracle: a coarse/fine term reads a covered cell (nesting closer than two cells)")
+        return [o * m for o, m in zip(outs, self.masks)]
 
     def solve(self, rhss, tol_rel=1e-10, tol_abs=0.0, maxit=100):
         rs = [_f64(r) for r in rhss]

@@ -210,3 +210,122 @@ def test_amr3_recipe_small(orc):
     ps, it, hist, st = M.solve(rs, tol_rel=1e-10, maxit=100)
     assert st == 0 and hist[-1] <= 1e-10 * hist[0]
     assert all(hist[i + 1] < 0.5 * hist[i] for i in range(len(hist) - 1)), hist
+
+
+# --------------------------------------------------------------- transpose and beta gradient
+
+@pytest.mark.parametrize("bc", [P_, D_, N_])
+def test_term_walk_equals_the_rows(orc, bc):
+    """The term-by-term walk that the transpose and the gradient scatter through sums to the
+    rows evaluated directly (three levels, variable alpha and beta)."""
+    dom, lb = three_levels(8)
+    M = orc.MultiLevelProblem(dom, lb, [bc] * 3, [bc] * 3)
+    rng = np.random.default_rng(35)
+    rand_coeffs(M, rng, bc == P_, a=0.7)
+    xs = [rng.standard_normal(s) for s in M.shapes]
+    y0 = M.pack(M.apply(xs))
+    y1 = M.pack(M.apply(xs, terms=True))
+    assert np.abs(y1 - y0).max() <= 1e-13 * np.abs(y0).max()
+
+
+@pytest.mark.parametrize("bc", [P_, D_, N_])
+def test_two_level_transpose_and_gradient_are_the_two_level_form(orc, bc):
+    """L = 2: A^T and dL/dbeta equal the two-level oracle's (separate code: row functions
+    of the two-level form)."""
+    n = 8
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    fb = I.chop((4, 4, 4), (11, 11, 11), 4)
+    M = orc.MultiLevelProblem(dom, [I.chop(*dom, 4), fb], [bc] * 3, [bc] * 3)
+    A = orc.AmrProblem(dom, I.chop(*dom, 4), fb, [bc] * 3, [bc] * 3)
+    rng = np.random.default_rng(36)
+    alphas, betas = rand_coeffs(M, rng, bc == P_, a=0.5)
+    A.set_coeffs(0.5, 1.0, alpha_c=alphas[0], beta_c=betas[0], alpha_f=alphas[1], beta_f=betas[1])
+    ys = [rng.standard_normal(s) * m for s, m in zip(M.shapes, M.masks)]
+    xm = M.apply(ys, transpose=True)
+    xc, xf = A.apply(ys[0], ys[1], transpose=True)
+    sc = max(np.abs(xc).max(), np.abs(xf).max())
+    assert np.abs(xm[0] - xc).max() <= 1e-13 * sc and np.abs(xm[1] - xf).max() <= 1e-13 * sc
+    phis = [rng.standard_normal(s) for s in M.shapes]
+    lams = [rng.standard_normal(s) * m for s, m in zip(M.shapes, M.masks)]
+    gm = M.grad_beta(phis, lams, betas)
+    gc, gf = A.grad_beta(phis[0], phis[1], lams[0], lams[1], betas[0], betas[1])
+    gf = gf * M.masks[1]
+    sc = max(np.abs(gc).max(), np.abs(gf).max())
+    assert np.abs(gm[0] - gc).max() <= 1e-13 * sc and np.abs(gm[1] - gf).max() <= 1e-13 * sc
+
+
+@pytest.mark.parametrize("bc", [P_, D_, N_])
+def test_three_level_transpose_by_inner_products(orc, bc):
+    """<A x, y> = <x, A^T y> over the composite unknowns: A x from the rows evaluated
+    directly, A^T y scattered term by term."""
+    dom, lb = three_levels(8)
+    M = orc.MultiLevelProblem(dom, lb, [bc] * 3, [bc] * 3)
+    rng = np.random.default_rng(37)
+    rand_coeffs(M, rng, bc == P_, a=0.0 if bc != D_ else 1.0)
+    for _ in range(3):
+        xs = [rng.standard_normal(s) * m for s, m in zip(M.shapes, M.masks)]
+        ys = [rng.standard_normal(s) * m for s, m in zip(M.shapes, M.masks)]
+        ax = M.pack(M.apply(xs))
+        aty = M.pack(M.apply(ys, transpose=True))
+        lhs, rhs = ax @ M.pack(ys), M.pack(xs) @ aty
+        assert abs(lhs - rhs) <= 1e-13 * (np.abs(ax) @ np.abs(M.pack(ys)))
+    # and the assembled matrix's transpose, column by column, on one level-2 and one level-0 unknown
+    A = M.matrix() if M.pack([np.zeros(s) for s in M.shapes]).size <= 2000 else None
+    if A is not None:
+        m = A.shape[0]
+        for j in (0, m - 1):
+            e = np.zeros(m)
+            e[j] = 1.0
+            assert np.abs(M.pack(M.apply(M.unpack(e), transpose=True)) - A[j]).max() <= 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("bc", [P_, D_, N_])
+def test_three_level_gradient_by_central_differences(orc, bc):
+    """dL/dbeta for L = lambda^T (rhs - A(beta) phi) against central differences of
+    <lambda, A(beta (1 + eps v)) phi> in random relative directions v (all cells of every
+    level, covered ones included: their beta shapes only the correction operator, so their
+    gradient is 0), eps = 1e-5."""
+    dom, lb = three_levels(8)
+    M = orc.MultiLevelProblem(dom, lb, [bc] * 3, [bc] * 3)
+    rng = np.random.default_rng(38)
+    alphas, betas = rand_coeffs(M, rng, bc == P_, a=0.4)
+    phis = [rng.standard_normal(s) for s in M.shapes]
+    lams = [rng.standard_normal(s) * m for s, m in zip(M.shapes, M.masks)]
+    g = M.grad_beta(phis, lams, betas)
+    for l in range(M.L - 1):
+        under = M.inside[l + 1].reshape(M.shapes[l][0], 2, M.shapes[l][1], 2, M.shapes[l][2], 2).all(axis=(1, 3, 5))
+        assert not g[l][under].any()
+
+    def F(bs):
+        M.set_coeffs(0.4, 1.0, alphas=alphas, betas=bs)
+        return M.pack(lams) @ M.pack(M.apply(phis))
+
+    for _ in range(3):
+        vs = [rng.standard_normal(s) * I_ for s, I_ in zip(M.shapes, M.inside)]
+        eps = 1e-5
+        fd = (F([b * (1 + eps * v) for b, v in zip(betas, vs)]) - F([b * (1 - eps * v) for b, v in zip(betas, vs)])) / (2 * eps)
+        pred = -sum((gl * b * v).sum() for gl, b, v in zip(g, betas, vs))
+        assert abs(fd - pred) <= 1e-7 * abs(fd), (fd, pred)
+    M.set_coeffs(0.4, 1.0, alphas=alphas, betas=betas)
+
+
+def test_transpose_refuses_nesting_closer_than_two_cells(orc):
+    """Level 2 one level-1 cell inside level 1's low x boundary: the fine ghost interpolation
+    of level 1 reads a covered cell, so A is not a matrix over the unknowns; the transpose
+    and the gradient refuse, the forward operator runs."""
+    n = 16
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    l1 = I.chop((8, 8, 8), (23, 23, 23), 8)
+    l2 = [((18, 20, 20), (29, 27, 27))]
+    M = orc.MultiLevelProblem(dom, [I.chop(*dom, 8), l1, l2], [D_] * 3, [D_] * 3)
+    M.set_coeffs(0.0, 1.0)
+    xs = [np.ones(s) for s in M.shapes]
+    M.apply(xs)
+    with pytest.raises(ValueError):
+        M.apply(xs, transpose=True)
+    with pytest.raises(ValueError):
+        M.grad_beta(xs, xs)
+    # two cells in: accepted
+    M2 = orc.MultiLevelProblem(dom, [I.chop(*dom, 8), l1, [((20, 20, 20), (29, 27, 27))]], [D_] * 3, [D_] * 3)
+    M2.set_coeffs(0.0, 1.0)
+    M2.apply(xs, transpose=True)
