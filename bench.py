@@ -227,7 +227,8 @@ def _updates_per_vcycle_problem(ctx, s):
 def measure_forms(stream, barrier, dev, only=None):
     """The other workloads, each at full size: abec512 in FP64 and both mixed forms, batch64
     (64 uneven problems, batched form), amr2 (two-level composite forward + adjoint +
-    beta gradient), amr3 (three-level composite forward), walls256, krylov.  Device time to 1e-10 per solve."""
+    beta gradient), amr3 (the same over three levels), walls256, krylov.  Device time to
+    1e-10 per solve."""
     forms = {}
     if only in (None, "abec512"):
         forms["abec512"] = _form_abec512(stream, barrier)
@@ -441,14 +442,19 @@ def _form_amr3(stream, barrier):
     rs = [ctx.pack_level(lev, torch.from_numpy(r)) for lev, r in enumerate(a["rhss"])]
     tuned = summarize_tuning(ctx.autotune(rs[0], gmg.FP64))
     ms, (phis, info) = _timed(lambda: ctx.solve_levels(rs, tol_rel=TOL), 3, 1, stream, barrier)
+    # adjoint of L = 0.5 |phi|^2 over the composite cells: g = phi (zero volume-weighted mean),
+    # projected by the solver onto the range of A^T
+    ms_a, (lams, info_a) = _timed(lambda: ctx.solve_adjoint_levels(phis, tol_rel=TOL), 3, 1, stream, barrier)
+    ms_g, _ = _timed(lambda: ctx.beta_grad_levels(phis, lams), 5, 1, stream, barrier)
     cells = sum(int((~c).sum()) for c in a["covered"])
     res = {"workload": "amr3: 128^3 periodic level 0 (8 boxes) + ratio-2 level 1 over the central 64^3 "
                        "level-0 cells + ratio-2 level 2 over 64^3 level-1 cells off its centre (128^3 cells "
                        "per level; 8, 8 and 64 boxes), seed 12017, tol 1e-10",
            "composite_cells": cells,
            "forward": {"time_to_tol_ms": ms, "iterations": info.iterations, "status": info.status},
-           "autotuned_level0_hierarchy": tuned}
-    del ctx, rs, phis
+           "adjoint": {"time_to_tol_ms": ms_a, "iterations": info_a.iterations, "status": info_a.status},
+           "beta_grad_ms": ms_g, "autotuned_level0_hierarchy": tuned}
+    del ctx, rs, phis, lams
     torch.cuda.empty_cache()
     return res
 

@@ -201,7 +201,10 @@ gmg_status gmg_define_domain(gmg_ctx* ctx, const int lo[3], const int hi[3], con
      between the level and any other of its boxes, a wall or the edge of level lev - 1 (the
      coarse/fine interpolation reads coarse neighbours).  Single-problem contexts.  Call
      before gmg_workspace_size; the workspace then holds every level.  The adjoint solve,
-     apply_transpose and the beta gradient take two levels at most. */
+     apply_transpose and the beta gradient over three or more levels also need every level
+     at least two of its cells inside the coarse/fine boundary of the level it refines (the
+     two fine cells a coarse/fine ghost reads must not be covered): GMG_ERR_BAD_INPUT
+     otherwise. */
 #define GMG_MAX_AMR_LEVELS 4
 gmg_status gmg_define_level(gmg_ctx* ctx, int lev, int nboxes, const int* box_lohi, int ref_ratio);
 
@@ -297,18 +300,19 @@ gmg_status gmg_solve(gmg_ctx* ctx, void* const* phi, const void* const* rhs, dou
    operator; covered coarse entries of out are 0. */
 gmg_status gmg_apply(gmg_ctx* ctx, void* const* out, void* const* phi);
 
-/* out = A^T y.  One level: A is symmetric (same as gmg_apply).  Two levels: the transpose
-   of the composite operator (the transposed interpolation and reflux couplings); covered
-   coarse entries of y are taken as 0 and those of out are 0. */
+/* out = A^T y.  One level: A is symmetric (same as gmg_apply).  Several AMR levels: the
+   transpose of the composite operator (the level stencils plus, for each pair of
+   consecutive levels, the transposed interpolation and reflux couplings); covered entries
+   of y are taken as 0 and those of out are 0; y's ghosts are overwritten. */
 gmg_status gmg_apply_transpose(gmg_ctx* ctx, void* const* out, void* const* y);
 
 /* Adjoint solve A^T lambda = g (FP64), so that lambda = dL/d(rhs) for a loss L(phi) with
-   dL/dphi = g.  One level: a forward solve (A symmetric).  Two levels: BiCGStab on A^T,
+   dL/dphi = g.  One level: a forward solve (A symmetric).  Several AMR levels: BiCGStab on A^T,
    right-preconditioned by the composite multigrid correction of A, to ||g - A^T lambda||_inf
    <= tol_rel ||g||_inf (max_iter Krylov iterations).  Singular problems (no Dirichlet wall,
    a = 0): g is projected onto the range of A^T (g - V sum(g)/sum(V), V the cell volumes;
    one level: g minus its mean) and lambda returned with zero sum.  lambda, g as in
-   gmg_solve; covered coarse entries of g are ignored and those of lambda are 0. */
+   gmg_solve; covered entries of g are ignored and those of lambda are 0. */
 gmg_status gmg_solve_adjoint(gmg_ctx* ctx, void* const* lambda, const void* const* g, double tol_rel,
                              const gmg_params* p, gmg_solve_info* info);
 
@@ -318,8 +322,8 @@ gmg_status gmg_solve_adjoint(gmg_ctx* ctx, void* const* lambda, const void* cons
    also the reflux row's share), then through the rule that made the face value from cell
    beta (harmonic mean: d/dbeta_L = 2 beta_R^2 / (beta_L + beta_R)^2; wall and coarse/fine
    faces: 1 for the adjacent cell).  Uses the beta last passed to gmg_set_bcoef_cell.
-   dbeta[l]: FP64 output in level l's layout (covered coarse cells get 0).  phi's and
-   lambda's ghosts are overwritten. */
+   dbeta[l]: FP64 output in level l's layout for every AMR level (covered cells get 0: their
+   beta shapes only the correction operator).  phi's and lambda's ghosts are overwritten. */
 gmg_status gmg_beta_grad(gmg_ctx* ctx, void* const* dbeta, void* const* phi, void* const* lambda);
 
 /* ------------------------------------------------------------- wall values */

@@ -1,7 +1,7 @@
 """Differentiable solves: torch.autograd.Function wrappers of the library's solve.
 
-Forward:  phi = A(beta)^-1 rhs by the multigrid solve (one level, or the two-level
-          composite form of Sec. "Operations between levels").
+Forward:  phi = A(beta)^-1 rhs by the multigrid solve (one level, or the composite form
+          over two or more AMR levels of Sec. "Operations between levels").
 Backward: lambda = A^-T dL/dphi by the adjoint solve (gmg_solve_adjoint), then
           dL/drhs = lambda and dL/dbeta = -lambda^T (dA/dbeta) phi by the face-flux gradient
           kernel (gmg_beta_grad), through the harmonic face mean to the cell beta; with
@@ -10,9 +10,9 @@ Both run in the library's kernels; this module only marshals tensors.
 
 Singular problems (no Dirichlet wall, a = 0): the forward projects rhs onto the operator's range
 and returns phi with zero (volume-weighted) mean; the backward projects accordingly, so the
-gradients are those of that projected map.  Two levels: phi on coarse cells under the fine
+gradients are those of that projected map.  Several levels: phi on cells under a finer
 level is returned as 0 (those cells are not unknowns of the composite problem), and the
-rhs of those cells does not influence phi (its gradient is 0).
+rhs and beta of those cells do not influence phi (their gradients are 0).
 """
 from __future__ import annotations
 
@@ -132,3 +132,49 @@ class Solve:
             for f, v in wall_values.items():
                 walls[f] = v
         return _Solve.apply(self, rhs, beta, *walls)
+
+
+class _MultiLevelSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, solver, *args):
+        C = solver.ctx
+        L = C.nlev_amr
+        rhss, betas = args[:L], args[L:]
+        C.set_coeffs(solver.a, solver.b, betas=[b.detach() for b in betas])
+        rs = [C.pack_level(lev, r.detach()) for lev, r in enumerate(rhss)]
+        phis, info = C.solve_levels(rs, tol_rel=solver.tol, max_iter=solver.max_iter, project_mean=1)
+        if info.status != gmg.OK:
+            raise gmg.GmgError(info.status, "forward solve did not converge")
+        masks = [torch.as_tensor(~cov, device=rhss[0].device, dtype=torch.float64) for cov in C.covered]
+        ctx.solver, ctx.state, ctx.masks = solver, phis, masks
+        solver.last_info = info
+        return tuple(C.unpack_level(lev, p) * m for lev, (p, m) in enumerate(zip(phis, masks)))
+
+    @staticmethod
+    def backward(ctx, *gs):
+        solver = ctx.solver
+        C = solver.ctx
+        g = [C.pack_level(lev, (x * m).contiguous()) for lev, (x, m) in enumerate(zip(gs, ctx.masks))]
+        lams, info = C.solve_adjoint_levels(g, tol_rel=solver.tol, max_iter=solver.max_iter)
+        if info.status != gmg.OK:
+            raise gmg.GmgError(info.status, "adjoint solve did not converge")
+        solver.last_adjoint_info = info
+        ds = C.beta_grad_levels(ctx.state, lams)
+        dr = [C.unpack_level(lev, lam) * m for lev, (lam, m) in enumerate(zip(lams, ctx.masks))]
+        return (None, *dr, *[C.unpack_level(lev, d) for lev, d in enumerate(ds)])
+
+
+class MultiLevelSolve:
+    """phis = MultiLevelSolve(...)(rhss, betas): the composite solve over several AMR levels,
+    differentiable in every level's rhs and beta.  Dense float64 CUDA tensors per level:
+    level 0 over the domain (nz, ny, nx), level l over the bounding box of its boxes."""
+
+    def __init__(self, domain, level_boxes, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0), prob_hi=(1.0, 1.0, 1.0),
+                 a=0.0, b=1.0, tol=1e-10, max_iter=100):
+        self.ctx = gmg.MultiLevelContext(domain, level_boxes, bc_lo, bc_hi, prob_lo, prob_hi,
+                                         stream=torch.cuda.current_stream().cuda_stream)
+        self.ctx.allocate(gmg.FP64)
+        self.a, self.b, self.tol, self.max_iter = a, b, tol, max_iter
+
+    def __call__(self, rhss, betas):
+        return _MultiLevelSolve.apply(self, *rhss, *betas)

@@ -409,12 +409,11 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
       for (int q = 0; q < 4; ++q) cc[q] = (double*)cv.take(8 * ne0);
     double* ff[5];
     for (int q = 0; q < 5; ++q) ff[q] = (double*)cv.take(8 * nf);
-    double *kc[9] = {}, *kf[9] = {};
-    if (c->amrl.size() == 1)  // the adjoint solve takes two levels
-      for (int q = 0; q < 9; ++q) {
-        kc[q] = (double*)cv.take(8 * ne0);
-        kf[q] = (double*)cv.take(8 * nf);
-      }
+    double *kc[9] = {}, *kf[9] = {};  // the adjoint solve's vectors
+    for (int q = 0; q < 9; ++q) {
+      if (al == 0) kc[q] = (double*)cv.take(8 * ne0);
+      kf[q] = (double*)cv.take(8 * nf);
+    }
     if (fill) {
       AmrLevel& V = c->amrl[al];
       V.D = D;
@@ -1138,7 +1137,6 @@ Coefs acoefs(const gmg_ctx* c, int l) {
   k.wx = B.wx; k.wy = B.wy; k.wz = B.wz; k.D = B.D; k.invD = B.invD;
   return k;
 }
-Coefs coefs_fine(const gmg_ctx* c) { return acoefs(c, 1); }
 
 // ghosts of level l >= 1: copies between its boxes, then its coarse/fine ghosts (interpolated
 // from level l - 1's field cx, or zero coarse data when cx is null)
@@ -1146,7 +1144,6 @@ void level_fill(gmg_ctx* c, int l, double* f, const double* cx, int mode, cudaSt
   launch_fill(DT_F64, adev(c, l), f, -1, 0, s);
   launch_cf_fill(c->amrl[l - 1].A, f, cx, mode, s);
 }
-void fine_fill(gmg_ctx* c, double* f, const double* cx, int mode, cudaStream_t s) { level_fill(c, 1, f, cx, mode, s); }
 
 // composite residual r_l = rhs_l - (A x)_l on every level (covered cells 0), ||r_l||_inf into
 // nb[l] (nb may be null).  x's ghosts are overwritten.
@@ -1167,19 +1164,6 @@ void comp_residual_n(gmg_ctx* c, double* const* x, const double* const* rhs, dou
     }
   }
 }
-// (two levels: the fine norm in nb[0], the coarse one in nb[1], as read_norms expects)
-void comp_residual(gmg_ctx* c, double* pc, double* pf, const double* rc_in, const double* rf_in, double* rc,
-                   double* rf, unsigned long long* nb, cudaStream_t s) {
-  double* x[2] = {pc, pf};
-  const double* rhs[2] = {rc_in, rf_in};
-  double* r[2] = {rc, rf};
-  comp_residual_n(c, x, rhs, r, nb ? c->normbits + 2 : nullptr, s);
-  if (nb) {  // nb[0] fine, nb[1] coarse
-    cudaMemcpyAsync(nb, c->normbits + 3, 8, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(nb + 1, c->normbits + 2, 8, cudaMemcpyDeviceToDevice, s);
-  }
-}
-
 // One composite multigrid correction from the composite residuals r (per level): e_l in
 // level l's e buffer.  Down, for l = L-1 .. 1: pre-smoothing of level l's correction
 // equation (right-hand side rr_l; coarse/fine ghosts with a zero coarse correction); the
@@ -1233,49 +1217,47 @@ void comp_correction_n(gmg_ctx* c, const gmg_params& p, const double* const* r, 
   }
   for (int l = L - 1; l >= 1; --l) launch_restrict(DT_F64, adev(c, l), adev(c, l - 1), e[l], e[l - 1], s);
 }
-void comp_correction(gmg_ctx* c, const gmg_params& p, const double* rc, const double* rf, cudaStream_t s) {
-  const double* r[2] = {rc, rf};
-  comp_correction_n(c, p, r, s);
-}
-
-struct CompSums {
-  double vc, vf;  // cell volumes
-  double ncell_c, ncov, ncell_f;
+// volume of a cell of each AMR level and the number of its composite cells (not covered)
+struct CompLevels {
+  double v[GMG_MAX_AMR_LEVELS], n[GMG_MAX_AMR_LEVELS];
 };
 
-CompSums comp_sizes(const gmg_ctx* c) {
-  CompSums z;
+CompLevels comp_levels(const gmg_ctx* c) {
+  CompLevels z;
+  const int L = namr(c);
   const SolveGeom& G = c->geoms[0];
-  z.vc = G.h[0] * G.h[1] * G.h[2];
-  z.vf = z.vc / 8.0;
-  z.ncell_c = (double)c->L[0].ncells;
-  z.ncov = (double)c->amrl[0].H.covered_list.size();
-  z.ncell_f = (double)c->amrl[0].M.ncells;
+  double v = G.h[0] * G.h[1] * G.h[2];
+  for (int l = 0; l < L; ++l, v /= 8.0) {
+    z.v[l] = v;
+    const double ncell = (double)(l == 0 ? c->L[0].ncells : c->amrl[l - 1].M.ncells);
+    const double ncov = l + 1 < L ? (double)c->amrl[l].H.covered_list.size() : 0.0;
+    z.n[l] = ncell - ncov;
+  }
   return z;
 }
 
-// per-level sums of the valid cells of (xc, xf) (covered coarse entries must be zero)
-gmg_status comp_level_sums(gmg_ctx* c, const double* xc, const double* xf, double* sc, double* sf) {
+// per-level plain sums of the valid cells of x (covered entries must be zero)
+gmg_status comp_sums_n(gmg_ctx* c, double* const* x, double* sums) {
   cudaStream_t s = c->stream;
-  launch_sum(c->dev[0], xc, c->partials, c->scal, s);
-  launch_sum(c->amrl[0].D, xf, c->partials, c->scal + 1, s);  // same stream: after the first
-  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 16, cudaMemcpyDeviceToHost, s));
+  const int L = namr(c);
+  for (int l = 0; l < L; ++l) launch_sum(adev(c, l), x[l], c->partials, c->scal + l, s);  // in stream order
+  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8 * (size_t)L, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
-  const CompSums z = comp_sizes(c);
-  *sc = c->h_scal[0] * z.ncell_c;  // launch_sum returns means over every cell of the level
-  *sf = c->h_scal[1] * z.ncell_f;
+  for (int l = 0; l < L; ++l)  // launch_sum returns the mean over every cell of the level
+    sums[l] = c->h_scal[l] * (double)(l == 0 ? c->L[0].ncells : c->amrl[l - 1].M.ncells);
   return GMG_OK;
 }
 
-// x_c (uncovered) += kc, x_f += kf  (covered coarse entries cleared afterwards)
-gmg_status comp_add_const(gmg_ctx* c, double* xc, double* xf, double kc, double kf) {
+// x_l += k[l] on every level (covered entries cleared afterwards)
+gmg_status comp_add_const_n(gmg_ctx* c, double* const* x, const double* k) {
   cudaStream_t s = c->stream;
-  c->h_scal[2] = kc;
-  c->h_scal[3] = kf;
-  CK(c, cudaMemcpyAsync(c->scal + 2, c->h_scal + 2, 16, cudaMemcpyHostToDevice, s));
-  launch_add_scalar(c->dev[0], xc, c->scal + 2, 1.0, s);
-  launch_add_scalar(c->amrl[0].D, xf, c->scal + 3, 1.0, s);
-  launch_zero_covered(c->amrl[0].A, xc, s);
+  const int L = namr(c);
+  for (int l = 0; l < L; ++l) c->h_scal[4 + l] = k[l];
+  CK(c, cudaMemcpyAsync(c->scal + 4, c->h_scal + 4, 8 * (size_t)L, cudaMemcpyHostToDevice, s));
+  for (int l = 0; l < L; ++l) {
+    launch_add_scalar(adev(c, l), x[l], c->scal + 4 + l, 1.0, s);
+    if (l + 1 < L) launch_zero_covered(c->amrl[l].A, x[l], s);
+  }
   CK(c, cudaGetLastError());
   return GMG_OK;
 }
@@ -1296,7 +1278,6 @@ gmg_status read_norms_n(gmg_ctx* c, int n, double* rn) {
   }
   return GMG_OK;
 }
-gmg_status read_norms(gmg_ctx* c, double* rn) { return read_norms_n(c, 2, rn); }
 
 // volume-weighted mean of x over the composite cells (covered entries must be zero)
 gmg_status comp_mean_n(gmg_ctx* c, double* const* x, double* mean) {
@@ -1423,148 +1404,175 @@ void comp_apply_n(gmg_ctx* c, double* const* x, double* const* out, cudaStream_t
   comp_residual_n(c, x, zero, out, nullptr, s);
   for (int l = 0; l < L; ++l) launch_scale_valid(adev(c, l), out[l], -1.0, s);
 }
-void comp_apply(gmg_ctx* c, double* xc, double* xf, double* outc, double* outf, cudaStream_t s) {
-  double* x[2] = {xc, xf};
-  double* out[2] = {outc, outf};
-  comp_apply_n(c, x, out, s);
+// out = A^T y (composite) over every level: the level stencils (symmetric; coarse/fine
+// ghosts zero, covered entries of y zero) plus, for each pair of consecutive levels, the
+// transposed interpolation and reflux couplings.  y's ghosts are overwritten; its covered
+// entries are cleared.
+void comp_apply_transpose_n(gmg_ctx* c, double* const* y, double* const* out, cudaStream_t s) {
+  const int L = namr(c);
+  double* zero[GMG_MAX_AMR_LEVELS];
+  for (int l = 0; l < L; ++l) {
+    zero[l] = l == 0 ? c->czero : c->amrl[l - 1].zero;
+    cudaMemsetAsync(zero[l], 0, 8 * (size_t)anelem(c, l), s);
+    if (l + 1 < L) launch_zero_covered(c->amrl[l].A, y[l], s);
+  }
+  for (int l = 1; l < L; ++l) level_fill(c, l, y[l], nullptr, CF_ZERO, s);
+  launch_fill(DT_F64, c->dev[0], y[0], -1, 0, s);
+  for (int l = L - 1; l >= 0; --l) {
+    launch_residual(DT_F64, DT_F64, adev(c, l), y[l], zero[l], acoefs(c, l), out[l], nullptr, nullptr, s);
+    launch_scale_valid(adev(c, l), out[l], -1.0, s);
+  }
+  for (int l = 0; l + 1 < L; ++l)
+    launch_composite_transpose_couplings(c->amrl[l].A, acoefs(c, l), acoefs(c, l + 1), y[l], y[l + 1], out[l],
+                                         out[l + 1], s);
+  for (int l = 0; l + 1 < L; ++l) launch_zero_covered(c->amrl[l].A, out[l], s);
 }
 
-// out = A^T y (composite): the level stencils (symmetric; the fine one with zero coarse/fine
-// ghosts, the coarse one with covered entries of y zero) plus the transposed
-// interpolation and reflux couplings.  y's ghosts are overwritten; yc's covered entries are
-// cleared.
-void comp_apply_transpose(gmg_ctx* c, double* yc, double* yf, double* outc, double* outf, cudaStream_t s) {
-  cudaMemsetAsync(c->czero, 0, 8 * (size_t)c->L[0].nelem, s);
-  cudaMemsetAsync(c->amrl[0].zero, 0, 8 * (size_t)c->amrl[0].M.nelem, s);
-  launch_zero_covered(c->amrl[0].A, yc, s);
-  fine_fill(c, yf, nullptr, CF_ZERO, s);
-  launch_fill(DT_F64, c->dev[0], yc, -1, 0, s);
-  launch_residual(DT_F64, DT_F64, c->amrl[0].D, yf, c->amrl[0].zero, coefs_fine(c), outf, nullptr, nullptr, s);
-  launch_residual(DT_F64, DT_F64, c->dev[0], yc, c->czero, coefs64(c, 0), outc, nullptr, nullptr, s);
-  launch_scale_valid(c->dev[0], outc, -1.0, s);
-  launch_scale_valid(c->amrl[0].D, outf, -1.0, s);
-  launch_composite_transpose_couplings(c->amrl[0].A, coefs64(c, 0), coefs_fine(c), yc, yf, outc, outf, s);
-  launch_zero_covered(c->amrl[0].A, outc, s);
-}
-
-gmg_status comp_dot(gmg_ctx* c, const double* xc, const double* xf, const double* yc, const double* yf, double* out) {
+// sum over the levels of <x_l, y_l> (covered entries zero in one of the two)
+gmg_status comp_dot_n(gmg_ctx* c, double* const* x, double* const* y, double* out) {
   cudaStream_t s = c->stream;
-  launch_dot(c->dev[0], xc, yc, c->partials, c->scal, s);
-  launch_dot(c->amrl[0].D, xf, yf, c->partials, c->scal + 1, s);  // same stream: after the first
-  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 16, cudaMemcpyDeviceToHost, s));
+  const int L = namr(c);
+  for (int l = 0; l < L; ++l) launch_dot(adev(c, l), x[l], y[l], c->partials, c->scal + l, s);  // in stream order
+  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8 * (size_t)L, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
   CK(c, cudaGetLastError());
-  *out = c->h_scal[0] + c->h_scal[1];
+  double sum = 0.0;
+  for (int l = 0; l < L; ++l) sum += c->h_scal[l];
+  *out = sum;
   return GMG_OK;
 }
 
-gmg_status comp_norm(gmg_ctx* c, const double* xc, const double* xf, double* out) {
-  CK(c, cudaMemsetAsync(c->normbits, 0, 16, c->stream));
-  launch_norm_max(c->amrl[0].D, xf, c->normbits, c->stream);
-  launch_norm_max(c->dev[0], xc, c->normbits + 1, c->stream);
-  return read_norms(c, out);
+// max over the levels of ||x_l||_inf
+gmg_status comp_norm_n(gmg_ctx* c, double* const* x, double* out) {
+  const int L = namr(c);
+  CK(c, cudaMemsetAsync(c->normbits, 0, 8 * (size_t)L, c->stream));
+  for (int l = 0; l < L; ++l) launch_norm_max(adev(c, l), x[l], c->normbits + l, c->stream);
+  return read_norms_n(c, L, out);
 }
 
-// Adjoint solve A^T lambda = g of the composite operator: BiCGStab preconditioned on the
-// right by the composite multigrid correction of A.  Singular problems: g is projected
-// onto the range of A^T (g - V sum(g)/sum(V), V = cell volumes) and lambda onto zero sum.
-gmg_status solve_adjoint_amr(gmg_ctx* c, double* lc, double* lf, const double* gc_user, const double* gf_user,
-                             double tol_rel, const gmg_params& p, gmg_solve_info* info) {
+// The transpose, the adjoint solve and the beta gradient treat the composite operator as a
+// matrix over the unknowns.  That holds while no coarse/fine ghost of a level reads, through
+// its two inward cells, a cell covered by the next finer level (whose value is then an
+// average of finer data): every level must lie at least two cells inside the coarse/fine
+// boundary of the level it refines.
+gmg_status adjoint_layout_ok(gmg_ctx* c) {
+  const int L = namr(c);
+  for (int l = 0; l + 2 < L; ++l) {
+    const std::vector<unsigned char>& cov = c->amrl[l + 1].H.covered;  // level l+1 under level l+2
+    for (const CfGhost& G : c->amrl[l].H.cf)                          // level l+1's coarse/fine ghosts
+      if (cov[G.f1] || cov[G.f2])
+        SETERR(c, GMG_ERR_BAD_INPUT,
+               "transpose/adjoint/gradient: a level lies closer than two cells to the coarse/fine boundary of the "
+               "level it refines");
+  }
+  return GMG_OK;
+}
+
+// Adjoint solve A^T lambda = g of the composite operator over every AMR level: BiCGStab
+// preconditioned on the right by the composite multigrid correction of A.  Singular
+// problems: g is projected onto the range of A^T (g - V sum(g) / sum(V), V = cell volumes)
+// and lambda onto zero plain sum.
+gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* const* g_user, double tol_rel,
+                               const gmg_params& p, gmg_solve_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = c->stream;
+  const int L = namr(c);
   const int64_t l0 = kernel_launch_count();
   if (info) memset(info, 0, sizeof(*info));
-  const int64_t nc = c->L[0].nelem, nf = c->amrl[0].M.nelem;
-  // vectors: 0 r, 1 rhat, 2 p, 3 v, 4 s, 5 t, 6 phat, 7 shat, 8 g
-  double **kc = c->kc, **kf = c->amrl[0].kf;
-  CK(c, cudaMemcpyAsync(kc[8], gc_user, 8 * (size_t)nc, cudaMemcpyDeviceToDevice, s));
-  CK(c, cudaMemcpyAsync(kf[8], gf_user, 8 * (size_t)nf, cudaMemcpyDeviceToDevice, s));
-  launch_zero_covered(c->amrl[0].A, kc[8], s);
-  const CompSums z = comp_sizes(c);
+  // vectors per level: 0 r, 1 rhat, 2 p, 3 v, 4 s, 5 t, 6 phat, 7 shat, 8 g
+  double* k[9][GMG_MAX_AMR_LEVELS];
+  double *tmp[GMG_MAX_AMR_LEVELS], *e[GMG_MAX_AMR_LEVELS];
+  int64_t ne[GMG_MAX_AMR_LEVELS];
+  for (int l = 0; l < L; ++l) {
+    for (int q = 0; q < 9; ++q) k[q][l] = l == 0 ? c->kc[q] : c->amrl[l - 1].kf[q];
+    tmp[l] = l == 0 ? c->ctmp : c->amrl[l - 1].tmp;
+    e[l] = (double*)(l == 0 ? c->buf[0].e[DT_F64] : c->amrl[l - 1].B.e[DT_F64]);
+    ne[l] = anelem(c, l);
+  }
+  // out = a x + b y on every level
+  auto axpby = [&](double a, double* const* x, double b, double* const* y, double* const* out) {
+    for (int l = 0; l < L; ++l) launch_axpby(ne[l], a, x[l], b, y[l], out[l], s);
+  };
+  for (int l = 0; l < L; ++l) {
+    CK(c, cudaMemcpyAsync(k[8][l], g_user[l], 8 * (size_t)ne[l], cudaMemcpyDeviceToDevice, s));
+    if (l + 1 < L) launch_zero_covered(c->amrl[l].A, k[8][l], s);
+  }
+  const CompLevels z = comp_levels(c);
+  double vol = 0.0;
+  for (int l = 0; l < L; ++l) vol += z.v[l] * z.n[l];
   gmg_status st;
   const bool sing = singular(c, 0);
+  double sums[GMG_MAX_AMR_LEVELS], shift[GMG_MAX_AMR_LEVELS];
   if (sing) {
-    double sc, sf;
-    if ((st = comp_level_sums(c, kc[8], kf[8], &sc, &sf))) return st;
-    const double mu = (sc + sf) / (z.vf * z.ncell_f + z.vc * (z.ncell_c - z.ncov));
-    if ((st = comp_add_const(c, kc[8], kf[8], -mu * z.vc, -mu * z.vf))) return st;
+    if ((st = comp_sums_n(c, k[8], sums))) return st;
+    double tot = 0.0;
+    for (int l = 0; l < L; ++l) tot += sums[l];
+    for (int l = 0; l < L; ++l) shift[l] = -(tot / vol) * z.v[l];
+    if ((st = comp_add_const_n(c, k[8], shift))) return st;
   }
   double gnorm;
-  if ((st = comp_norm(c, kc[8], kf[8], &gnorm))) return st;
-  CK(c, cudaMemsetAsync(lc, 0, 8 * (size_t)nc, s));
-  CK(c, cudaMemsetAsync(lf, 0, 8 * (size_t)nf, s));
-  for (int q = 0; q < 8; ++q) {
-    CK(c, cudaMemsetAsync(kc[q], 0, 8 * (size_t)nc, s));
-    CK(c, cudaMemsetAsync(kf[q], 0, 8 * (size_t)nf, s));
+  if ((st = comp_norm_n(c, k[8], &gnorm))) return st;
+  for (int l = 0; l < L; ++l) {
+    CK(c, cudaMemsetAsync(lam[l], 0, 8 * (size_t)ne[l], s));
+    for (int q = 0; q < 8; ++q) CK(c, cudaMemsetAsync(k[q][l], 0, 8 * (size_t)ne[l], s));
   }
-  launch_axpby(nc, 1.0, kc[8], 0.0, kc[8], kc[0], s);
-  launch_axpby(nf, 1.0, kf[8], 0.0, kf[8], kf[0], s);
-  launch_axpby(nc, 1.0, kc[8], 0.0, kc[8], kc[1], s);
-  launch_axpby(nf, 1.0, kf[8], 0.0, kf[8], kf[1], s);
+  axpby(1.0, k[8], 0.0, k[8], k[0]);
+  axpby(1.0, k[8], 0.0, k[8], k[1]);
   const double target = tol_rel * gnorm;
   double rho_old = 1.0, alpha = 1.0, omega = 1.0, rn = gnorm;
   std::vector<double> hist{rn};
   int it = 0;
   gmg_status result = GMG_OK;
   // Preconditioner for A^T.  The composite operator is a flux divergence per cell volume,
-  // A = V^-1 K with K nearly symmetric, so A^T = K V^-1 = V A V^-1 (exactly so away from
-  // the coarse/fine couplings).  With M the composite multigrid correction (M ~ A^-1), the
-  // preconditioner is V M V^-1: scale the fine part of the input by V_c / V_f = 8, apply M,
-  // scale the fine part of the output by 1/8.  V^-1 also maps the range of A^T (zero sum)
-  // onto the range of A (zero volume-weighted sum) for the singular problem.
-  auto precond = [&](double* inc, double* inf, double* outc, double* outf) {
-    launch_axpby(nc, 1.0, inc, 0.0, inc, c->ctmp, s);
-    launch_axpby(nf, 8.0, inf, 0.0, inf, c->amrl[0].tmp, s);
-    comp_correction(c, p, c->ctmp, c->amrl[0].tmp, s);
-    launch_axpby(nc, 1.0, (const double*)c->buf[0].e[DT_F64], 0.0, (const double*)c->buf[0].e[DT_F64], outc, s);
-    launch_axpby(nf, 0.125, (const double*)c->amrl[0].B.e[DT_F64], 0.0, (const double*)c->amrl[0].B.e[DT_F64], outf, s);
+  // A = V^-1 K with K nearly symmetric, so A^T = K V^-1 = V A V^-1 (exactly so away from the
+  // coarse/fine couplings).  With M the composite multigrid correction (M ~ A^-1), the
+  // preconditioner is V M V^-1: scale level l of the input by V_0 / V_l = 8^l, apply M,
+  // scale level l of the output by 8^-l.  V^-1 also maps the range of A^T (zero sum) onto
+  // the range of A (zero volume-weighted sum) for the singular problem.
+  auto precond = [&](double* const* in, double* const* out) {
+    for (int l = 0; l < L; ++l) launch_axpby(ne[l], z.v[0] / z.v[l], in[l], 0.0, in[l], tmp[l], s);
+    comp_correction_n(c, p, tmp, s);
+    for (int l = 0; l < L; ++l) launch_axpby(ne[l], z.v[l] / z.v[0], e[l], 0.0, e[l], out[l], s);
+  };
+  // out = A^T x with x copied first (the transpose overwrites its input's ghosts)
+  auto apply_t = [&](double* const* x, double* const* out) {
+    axpby(1.0, x, 0.0, x, tmp);
+    comp_apply_transpose_n(c, tmp, out, s);
   };
   while (!(rn <= target) && it < p.max_iter) {
     ++it;
     double rho;
-    if ((st = comp_dot(c, kc[1], kf[1], kc[0], kf[0], &rho))) return st;
+    if ((st = comp_dot_n(c, k[1], k[0], &rho))) return st;
     if (std::fabs(rho) < 1e-300) break;
     const double beta = (rho / rho_old) * (alpha / omega);
-    // p = r + beta (p - omega v)
-    launch_axpby(nc, 1.0, kc[2], -omega, kc[3], kc[2], s);
-    launch_axpby(nf, 1.0, kf[2], -omega, kf[3], kf[2], s);
-    launch_axpby(nc, 1.0, kc[0], beta, kc[2], kc[2], s);
-    launch_axpby(nf, 1.0, kf[0], beta, kf[2], kf[2], s);
-    precond(kc[2], kf[2], kc[6], kf[6]);
-    launch_axpby(nc, 1.0, kc[6], 0.0, kc[6], c->ctmp, s);
-    launch_axpby(nf, 1.0, kf[6], 0.0, kf[6], c->amrl[0].tmp, s);
-    comp_apply_transpose(c, c->ctmp, c->amrl[0].tmp, kc[3], kf[3], s);
+    axpby(1.0, k[2], -omega, k[3], k[2]);  // p = r + beta (p - omega v)
+    axpby(1.0, k[0], beta, k[2], k[2]);
+    precond(k[2], k[6]);
+    apply_t(k[6], k[3]);
     double rv;
-    if ((st = comp_dot(c, kc[1], kf[1], kc[3], kf[3], &rv))) return st;
+    if ((st = comp_dot_n(c, k[1], k[3], &rv))) return st;
     if (std::fabs(rv) < 1e-300) break;
     alpha = rho / rv;
-    launch_axpby(nc, 1.0, kc[0], -alpha, kc[3], kc[4], s);
-    launch_axpby(nf, 1.0, kf[0], -alpha, kf[3], kf[4], s);
+    axpby(1.0, k[0], -alpha, k[3], k[4]);
     double sn;
-    if ((st = comp_norm(c, kc[4], kf[4], &sn))) return st;
+    if ((st = comp_norm_n(c, k[4], &sn))) return st;
     if (sn <= target) {
-      launch_axpby(nc, 1.0, lc, alpha, kc[6], lc, s);
-      launch_axpby(nf, 1.0, lf, alpha, kf[6], lf, s);
+      axpby(1.0, lam, alpha, k[6], lam);
       rn = sn;
       hist.push_back(rn);
       break;
     }
-    precond(kc[4], kf[4], kc[7], kf[7]);
-    launch_axpby(nc, 1.0, kc[7], 0.0, kc[7], c->ctmp, s);
-    launch_axpby(nf, 1.0, kf[7], 0.0, kf[7], c->amrl[0].tmp, s);
-    comp_apply_transpose(c, c->ctmp, c->amrl[0].tmp, kc[5], kf[5], s);
+    precond(k[4], k[7]);
+    apply_t(k[7], k[5]);
     double tt, ts;
-    if ((st = comp_dot(c, kc[5], kf[5], kc[5], kf[5], &tt))) return st;
-    if ((st = comp_dot(c, kc[5], kf[5], kc[4], kf[4], &ts))) return st;
+    if ((st = comp_dot_n(c, k[5], k[5], &tt))) return st;
+    if ((st = comp_dot_n(c, k[5], k[4], &ts))) return st;
     if (tt == 0.0) break;
     omega = ts / tt;
-    launch_axpby(nc, 1.0, lc, alpha, kc[6], lc, s);
-    launch_axpby(nf, 1.0, lf, alpha, kf[6], lf, s);
-    launch_axpby(nc, 1.0, lc, omega, kc[7], lc, s);
-    launch_axpby(nf, 1.0, lf, omega, kf[7], lf, s);
-    launch_axpby(nc, 1.0, kc[4], -omega, kc[5], kc[0], s);
-    launch_axpby(nf, 1.0, kf[4], -omega, kf[5], kf[0], s);
-    if ((st = comp_norm(c, kc[0], kf[0], &rn))) return st;
+    axpby(1.0, lam, alpha, k[6], lam);
+    axpby(1.0, lam, omega, k[7], lam);
+    axpby(1.0, k[4], -omega, k[5], k[0]);
+    if ((st = comp_norm_n(c, k[0], &rn))) return st;
     hist.push_back(rn);
     if (!std::isfinite(rn)) {
       result = GMG_ERR_DIVERGED;
@@ -1573,12 +1581,13 @@ gmg_status solve_adjoint_amr(gmg_ctx* c, double* lc, double* lf, const double* g
     rho_old = rho;
   }
   if (result == GMG_OK && !(rn <= target)) result = GMG_ERR_NOT_CONVERGED;
-  launch_zero_covered(c->amrl[0].A, lc, s);
+  for (int l = 0; l + 1 < L; ++l) launch_zero_covered(c->amrl[l].A, lam[l], s);
   if (sing) {  // remove the null-space component of A^T (span of V): zero plain sum
-    double sc, sf;
-    if ((st = comp_level_sums(c, lc, lf, &sc, &sf))) return st;
-    const double a = (sc + sf) / (z.vf * z.ncell_f + z.vc * (z.ncell_c - z.ncov));
-    if ((st = comp_add_const(c, lc, lf, -a * z.vc, -a * z.vf))) return st;
+    if ((st = comp_sums_n(c, lam, sums))) return st;
+    double tot = 0.0;
+    for (int l = 0; l < L; ++l) tot += sums[l];
+    for (int l = 0; l < L; ++l) shift[l] = -(tot / vol) * z.v[l];
+    if ((st = comp_add_const_n(c, lam, shift))) return st;
   }
   CK(c, cudaStreamSynchronize(s));
   CK(c, cudaGetLastError());
@@ -2646,9 +2655,14 @@ gmg_status gmg_apply_transpose(gmg_ctx* c, void* const* out, void* const* y) {
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
   if ((st = build_coefs(c))) return st;
-  if (namr(c) > 2) SETERR(c, GMG_ERR_BAD_INPUT, "apply_transpose: two AMR levels at most");
-  if (!out[1] || !y[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
-  comp_apply_transpose(c, (double*)y[0], (double*)y[1], (double*)out[0], (double*)out[1], c->stream);
+  double *yy[GMG_MAX_AMR_LEVELS], *oo[GMG_MAX_AMR_LEVELS];
+  for (int l = 0; l < namr(c); ++l) {
+    if (!out[l] || !y[l]) SETERR(c, GMG_ERR_BAD_INPUT, "composite context: pass arrays for every AMR level");
+    yy[l] = (double*)y[l];
+    oo[l] = (double*)out[l];
+  }
+  if ((st = adjoint_layout_ok(c))) return st;
+  comp_apply_transpose_n(c, yy, oo, c->stream);
   CK(c, cudaGetLastError());
   return GMG_OK;
 }
@@ -2668,11 +2682,16 @@ gmg_status gmg_solve_adjoint(gmg_ctx* c, void* const* lambda, const void* const*
     p.project_mean = 1;
     return solve_impl(c, (double*)lambda[0], (const double*)g[0], tol_rel, 0.0, p, info);
   }
-  if (namr(c) > 2) SETERR(c, GMG_ERR_BAD_INPUT, "adjoint: two AMR levels at most");
-  if (!lambda[1] || !g[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass level-0 and level-1 arrays");
+  double* lam[GMG_MAX_AMR_LEVELS];
+  const double* gg[GMG_MAX_AMR_LEVELS];
+  for (int l = 0; l < namr(c); ++l) {
+    if (!lambda[l] || !g[l]) SETERR(c, GMG_ERR_BAD_INPUT, "composite context: pass arrays for every AMR level");
+    lam[l] = (double*)lambda[l];
+    gg[l] = (const double*)g[l];
+  }
+  if ((st = adjoint_layout_ok(c))) return st;
   p.precision = GMG_FP64;
-  return solve_adjoint_amr(c, (double*)lambda[0], (double*)lambda[1], (const double*)g[0], (const double*)g[1],
-                           tol_rel, p, info);
+  return solve_adjoint_amr_n(c, lam, gg, tol_rel, p, info);
 }
 
 gmg_status gmg_beta_grad(gmg_ctx* c, void* const* dbeta, void* const* phi, void* const* lambda) {
@@ -2686,24 +2705,35 @@ gmg_status gmg_beta_grad_walls(gmg_ctx* c, void* const* dbeta, void* const* phi,
   if (st) return st;
   if ((st = build_coefs(c))) return st;
   if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "beta gradient: single-problem contexts only");
-  if (c->amr && namr(c) > 2) SETERR(c, GMG_ERR_BAD_INPUT, "beta gradient: two AMR levels at most");
   if (values && (st = wall_values_check(c, values))) return st;
   cudaStream_t s = c->stream;
   double* pc = (double*)phi[0];
   double* lc = (double*)lambda[0];
   if (c->amr) {
-    if (!dbeta[1] || !phi[1] || !lambda[1]) SETERR(c, GMG_ERR_BAD_INPUT, "two-level context: pass both levels");
-    double* pf = (double*)phi[1];
-    double* lf = (double*)lambda[1];
-    launch_zero_covered(c->amrl[0].A, lc, s);
-    fine_fill(c, pf, pc, CF_INTERP, s);
-    launch_fill(DT_F64, c->amrl[0].D, lf, -1, 0, s);
+    // level l's faces: its own rows, the reflux rows of level l - 1 on its coarse/fine faces
+    // (lambda of level l - 1), none under level l + 1 (covered cells: 0)
+    const int L = namr(c);
+    double *ph[GMG_MAX_AMR_LEVELS], *la[GMG_MAX_AMR_LEVELS];
+    for (int l = 0; l < L; ++l) {
+      if (!dbeta[l] || !phi[l] || !lambda[l]) SETERR(c, GMG_ERR_BAD_INPUT, "composite context: pass every AMR level");
+      ph[l] = (double*)phi[l];
+      la[l] = (double*)lambda[l];
+    }
+    if ((st = adjoint_layout_ok(c))) return st;
+    for (int l = 0; l + 1 < L; ++l) launch_zero_covered(c->amrl[l].A, la[l], s);
+    for (int l = L - 1; l >= 1; --l) {
+      level_fill(c, l, ph[l], ph[l - 1], CF_INTERP, s);
+      launch_fill(DT_F64, adev(c, l), la[l], -1, 0, s);
+    }
     launch_fill(DT_F64, c->dev[0], pc, -1, 0, s);
     launch_fill(DT_F64, c->dev[0], lc, -1, 0, s);
-    launch_grad_beta(c->amrl[0].D, pf, lf, c->amrl[0].beta_cell, c->b, c->amrl[0].A.cfidx, c->amrl[0].A.cf, lc, c->amrl[0].A.hf_over_hc,
-                     nullptr, (double*)dbeta[1], s);
-    launch_grad_beta(c->dev[0], pc, lc, c->betac_cell, c->b, nullptr, nullptr, nullptr, 0.5, c->amrl[0].A.covered,
-                     (double*)dbeta[0], s);
+    for (int l = L - 1; l >= 0; --l) {
+      const AmrDev* below = l > 0 ? &c->amrl[l - 1].A : nullptr;  // pair (l - 1, l)
+      const AmrDev* above = l + 1 < L ? &c->amrl[l].A : nullptr;  // pair (l, l + 1)
+      launch_grad_beta(adev(c, l), ph[l], la[l], l == 0 ? c->betac_cell : c->amrl[l - 1].beta_cell, c->b,
+                       below ? below->cfidx : nullptr, below ? below->cf : nullptr, l > 0 ? la[l - 1] : nullptr,
+                       below ? below->hf_over_hc : 0.5, above ? above->covered : nullptr, (double*)dbeta[l], s);
+    }
   } else {
     launch_fill(DT_F64, c->dev[0], pc, -1, 0, s);
     launch_fill(DT_F64, c->dev[0], lc, -1, 0, s);

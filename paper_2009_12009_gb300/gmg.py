@@ -553,11 +553,26 @@ class AmrContext(Context):
         return dc, df
 
 
+def covered_masks(level_boxes, level_lo, level_shape):
+    """Per AMR level, the cells of its dense array (shape level_shape[l], low corner
+    level_lo[l] in level l's index space) under a box of level l + 1 (ratio 2)."""
+    out = []
+    for lev, shape in enumerate(level_shape):
+        cov = np.zeros(shape, dtype=bool)
+        if lev + 1 < len(level_shape):
+            o = level_lo[lev]
+            for blo, bhi in level_boxes[lev + 1]:
+                cov[tuple(slice(blo[d] // 2 - o[d], (bhi[d] + 1) // 2 - o[d]) for d in (2, 1, 0))] = True
+        out.append(cov)
+    return out
+
+
 class MultiLevelContext(Context):
     """Composite problem over several AMR levels: level 0 covers the domain, level l
     (ratio 2 to level l - 1) is a BoxArray in level l's index space, properly nested.  Dense
-    arrays of level l >= 1 span the bounding box of its boxes.  Forward solve and operator
-    (the adjoint and the beta gradient take two levels: AmrContext)."""
+    arrays of level l >= 1 span the bounding box of its boxes.  Forward solve and operator,
+    transpose, adjoint solve and beta gradient (these three need every level at least two
+    cells inside the coarse/fine boundary of the level it refines)."""
 
     def __init__(self, domain, level_boxes, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0), prob_hi=(1.0, 1.0, 1.0),
                  stream=None):
@@ -573,6 +588,7 @@ class MultiLevelContext(Context):
             hi = [max(b[1][d] for b in boxes) for d in range(3)]
             self.level_lo.append(tuple(lo))
             self.level_shape_.append(tuple(hi[d] - lo[d] + 1 for d in (2, 1, 0)))
+        self.covered = covered_masks(level_boxes, self.level_lo, self.level_shape_)
 
     def nelem(self, lev):
         ne = C.c_int64()
@@ -620,9 +636,28 @@ class MultiLevelContext(Context):
             self._check(st)
         return phis, info
 
-    def apply_levels(self, xs):
+    def apply_levels(self, xs, transpose=False):
+        """A x, or A^T x (transpose: x's ghosts are overwritten, its covered entries cleared)."""
         outs = [self.level_field(lev) for lev in range(self.nlev_amr)]
-        self._check(self.L.gmg_apply(self.h, _pp(*outs), _pp(*xs)))
+        fn = self.L.gmg_apply_transpose if transpose else self.L.gmg_apply
+        self._check(fn(self.h, _pp(*outs), _pp(*xs)))
+        return outs
+
+    def solve_adjoint_levels(self, gs, tol_rel=1e-10, **params):
+        """A^T lambda = g over every level.  Returns (lambdas, info)."""
+        lams = [self.level_field(lev) for lev in range(self.nlev_amr)]
+        p = default_params(**params)
+        info = SolveInfo()
+        st = self.L.gmg_solve_adjoint(self.h, _pp(*lams), _pp(*gs), tol_rel, C.byref(p), C.byref(info))
+        if st not in (OK, NOT_CONVERGED):
+            self._check(st)
+        return lams, info
+
+    def beta_grad_levels(self, phis, lams):
+        """dL/dbeta per level (boxed) for L = lambda^T (rhs - A(beta) phi); the ghosts of phi
+        and lambda are overwritten."""
+        outs = [self.level_field(lev) for lev in range(self.nlev_amr)]
+        self._check(self.L.gmg_beta_grad(self.h, _pp(*outs), _pp(*phis), _pp(*lams)))
         return outs
 
 

@@ -18,7 +18,8 @@ the oracle.
     its transpose; the beta gradient of the GPU's phi and lambda against the oracle's.
   * amr3 (three levels, 128^3 cells each, level 2 off the centre of level 1): two composite
     iterations element by element; the converged solve's residual by the oracle's
-    composite operator.
+    composite operator; the adjoint solve's residual by the oracle's transpose and the beta
+    gradient of the GPU's phi and lambda against the oracle's.
 """
 import numpy as np
 import pytest
@@ -351,3 +352,28 @@ def test_amr3_converged_residual_by_oracle(amr3):
     rhs = amr3.rhs_full()
     r = amr3.P.pack(rhs) - amr3.P.pack(amr3.P.apply(amr3.from_gpu(phis)))
     assert np.abs(r).max() <= RES_BOUND * np.abs(amr3.P.pack(rhs)).max()
+
+
+def test_amr3_adjoint_and_gradient(amr3):
+    P = amr3.P
+    phis, info = amr3.C.solve_levels(amr3.to_gpu(), tol_rel=TOL)
+    assert info.status == gmg.OK
+    phi = amr3.from_gpu(phis)
+    rng = np.random.default_rng(12017 + 100)
+    gs = [rng.standard_normal(s) * m for s, m in zip(P.shapes, P.masks)]
+    v = P.pack(gs)
+    gs = P.unpack(v - v.sum() / v.size)  # zero plain sum: the range of A^T (periodic, a = 0)
+    g_gpu = [amr3.C.pack_level(lev, torch.from_numpy(np.ascontiguousarray(x[amr3.sl[lev]])))
+             for lev, x in enumerate(gs)]
+    lams, ainfo = amr3.C.solve_adjoint_levels(g_gpu, tol_rel=TOL)
+    assert ainfo.status == gmg.OK
+    lam = amr3.from_gpu(lams)
+    g = P.pack(gs)
+    res = g - P.pack(P.apply(lam, transpose=True))
+    res -= res.mean()
+    assert np.abs(res).max() <= RES_BOUND * np.abs(g).max()
+    betas = [amr3.embed(lev, b, fill=1.0) for lev, b in enumerate(amr3.cfg["betas"])]
+    want = P.grad_beta(phi, lam, betas)
+    got = amr3.from_gpu(amr3.C.beta_grad_levels(phis, lams))
+    sc = max(np.abs(w).max() for w in want)
+    assert max(np.abs(gg - w).max() for gg, w in zip(got, want)) <= 1e-10 * sc

@@ -1,7 +1,8 @@
 """Composite form over three AMR levels on the GPU against the oracle (MultiLevelProblem):
-the composite operator (1e-12 of scale), the composite multigrid solve at a fixed iteration
-count (1e-10, same residual history) and to tolerance (1e-12 on both sides, 1e-10), for
-periodic, Dirichlet and Neumann walls."""
+the composite operator and its transpose (1e-12 of scale), the composite multigrid solve at
+a fixed iteration count (1e-10, same residual history) and to tolerance (1e-12 on both
+sides, 1e-10), the adjoint solve (A^T lambda = g by the oracle's transpose, 1e-10) and the
+beta gradient (1e-10 of scale), for periodic, Dirichlet and Neumann walls."""
 import numpy as np
 import pytest
 
@@ -111,16 +112,118 @@ def test_three_level_solve_to_tolerance(mp):
     assert max(np.abs(x).max() for x in r) <= 1.01e-12 * max(np.abs(x).max() for x in rs) * 10
 
 
-def test_three_levels_refuse_adjoint():
-    dom, lb = three_levels(16)
+def test_three_level_transpose(mp):
+    ys = [mp.rng.standard_normal(s) * m for s, m in zip(mp.P.shapes, mp.P.masks)]
+    want = mp.P.apply(ys, transpose=True)
+    got = mp.from_gpu(mp.C.apply_levels(mp.to_gpu(ys), transpose=True))
+    sc = max(np.abs(w).max() for w in want)
+    assert max(np.abs(g - w).max() for g, w in zip(got, want)) <= 1e-12 * sc
+
+
+def test_three_level_adjoint_and_gradient(mp):
+    """A^T lambda = g solved on the GPU, checked with the oracle's transpose; the beta
+    gradient from the oracle's phi and the GPU's lambda against the oracle's gradient of the
+    same."""
+    rs = mp.rand_rhs()
+    want, it, hist, st = mp.P.solve(rs, tol_rel=1e-12, maxit=100)
+    assert st == 0
+    gs = [mp.rng.standard_normal(s) * m for s, m in zip(mp.P.shapes, mp.P.masks)]
+    if mp.singular:
+        v = mp.P.pack(gs)
+        gs = mp.P.unpack(v - v.sum() / v.size)  # zero plain sum: the range of A^T
+    lams, info = mp.C.solve_adjoint_levels(mp.to_gpu(gs), tol_rel=1e-11)
+    assert info.status == gmg.OK
+    lam = mp.from_gpu(lams)
+    g = mp.P.pack(gs)
+    res = g - mp.P.pack(mp.P.apply(lam, transpose=True))
+    if mp.singular:
+        res -= res.mean()
+        assert abs(mp.P.pack(lam).sum()) <= 1e-10 * np.abs(mp.P.pack(lam)).sum()
+    assert np.abs(res).max() <= 1e-10 * np.abs(g).max()
+    want_g = mp.P.grad_beta(want, lam, mp.betas)
+    outs = mp.C.beta_grad_levels(mp.to_gpu(want), mp.to_gpu(lam))
+    got = mp.from_gpu(outs)
+    sc = max(np.abs(w).max() for w in want_g)
+    assert max(np.abs(gg - w).max() for gg, w in zip(got, want_g)) <= 1e-10 * sc
+
+
+def test_close_nesting_refuses_transpose():
+    """Level 2 one level-1 cell inside level 1's low x edge: a level-1 coarse/fine ghost reads a
+    covered cell, so the transpose, the adjoint solve and the gradient refuse; the forward
+    operator and solve run."""
+    import ctypes as C_
+
+    n = 16
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    lb = [I.chop(*dom, 8), I.chop((8, 8, 8), (23, 23, 23), 8), [((18, 20, 20), (29, 27, 27))]]
     C = gmg.MultiLevelContext(dom, lb, [D_] * 3, [D_] * 3, stream=torch.cuda.current_stream().cuda_stream)
     C.allocate(gmg.FP64)
     C.set_coeffs(0.0, 1.0)
     z = [C.level_field(l) for l in range(3)]
-    import ctypes as C_
-
+    C.apply_levels(z)
+    with pytest.raises(gmg.GmgError) as e:
+        C.apply_levels(z, transpose=True)
+    assert e.value.status == gmg.BAD_INPUT
     arr = (C_.c_void_p * 3)(*[t.data_ptr() for t in z])
     info = gmg.SolveInfo()
     p = gmg.default_params()
-    st = C.L.gmg_solve_adjoint(C.h, arr, arr, 1e-10, C_.byref(p), C_.byref(info))
-    assert st == gmg.BAD_INPUT
+    assert C.L.gmg_solve_adjoint(C.h, arr, arr, 1e-10, C_.byref(p), C_.byref(info)) == gmg.BAD_INPUT
+    assert C.L.gmg_beta_grad(C.h, arr, arr, arr) == gmg.BAD_INPUT
+
+
+def test_three_level_autograd_vs_central_differences():
+    """dL/d(rhs) and dL/d(beta) of every level from MultiLevelSolve (adjoint solve + beta
+    gradient behind torch.autograd) against Richardson-extrapolated central differences of
+    GPU forward solves to 1e-12 (eps = 1e-3, 5e-4) in random directions, L = 0.5 sum over
+    composite cells (phi - phi_t)^2; periodic (singular) and Dirichlet."""
+    from paper_2009_12009_gb300.autograd import MultiLevelSolve
+
+    for bc in (P_, D_):
+        dom, lb = three_levels(16)
+        solver = MultiLevelSolve(dom, lb, [bc] * 3, [bc] * 3, tol=1e-12, max_iter=100)
+        C = solver.ctx
+        gen = torch.Generator(device="cpu").manual_seed(9)
+
+        def randn(shape):
+            return torch.randn(shape, generator=gen, dtype=torch.float64).cuda()
+
+        keep = [torch.as_tensor(~cov, device="cuda", dtype=torch.float64) for cov in C.covered]
+        shapes = C.level_shape_
+        vol = [8.0 ** (-l) for l in range(3)]
+
+        def zero_mean(xs):  # composite cells, zero volume-weighted mean (needed if singular)
+            xs = [x * k for x, k in zip(xs, keep)]
+            if bc == P_:
+                m = sum(v * x.sum() for v, x in zip(vol, xs)) / sum(v * k.sum() for v, k in zip(vol, keep))
+                xs = [(x - m) * k for x, k in zip(xs, keep)]
+            return xs
+
+        r0 = zero_mean([randn(s) for s in shapes])
+        b0 = [torch.exp(0.5 * randn(s)) for s in shapes]
+        tgt = [randn(s) * k for s, k in zip(shapes, keep)]
+
+        def loss_of(phis):
+            return sum(0.5 * (((p - t) * k) ** 2).sum() for p, t, k in zip(phis, tgt, keep))
+
+        rs = [r.clone().requires_grad_(True) for r in r0]
+        bs = [b.clone().requires_grad_(True) for b in b0]
+        loss_of(solver(rs, bs)).backward()
+        assert solver.last_adjoint_info.status == gmg.OK
+        dr = zero_mean([randn(s) for s in shapes])
+        vb = [0.1 * randn(s) * k for s, k in zip(shapes, keep)]
+
+        def central(solve_at, eps):
+            pp, pm = solve_at(eps), solve_at(-eps)
+            d = sum(0.5 * ((a - b) * (a + b - 2 * t) * k).sum() for a, b, t, k in zip(pp, pm, tgt, keep))
+            return float(d) / (2 * eps)
+
+        def richardson(solve_at):
+            return (4 * central(solve_at, 5e-4) - central(solve_at, 1e-3)) / 3
+
+        with torch.no_grad():
+            fd_r = richardson(lambda e: solver([r + e * d for r, d in zip(r0, dr)], b0))
+            fd_b = richardson(lambda e: solver(r0, [b * (1 + e * v) for b, v in zip(b0, vb)]))
+        pred_r = float(sum((r.grad * d).sum() for r, d in zip(rs, dr)))
+        pred_b = float(sum((b.grad * b0_ * v).sum() for b, b0_, v in zip(bs, b0, vb)))
+        assert abs(fd_r - pred_r) <= 1e-6 * abs(fd_r), (bc, fd_r, pred_r)
+        assert abs(fd_b - pred_b) <= 1e-6 * abs(fd_b), (bc, fd_b, pred_b)

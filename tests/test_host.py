@@ -102,3 +102,19 @@ def test_bad_input_refused():
     st = Cx.L.gmg_set_workspace(Cx.h, C.c_void_p(257), C.c_size_t(1 << 40))
     assert st == gmg.BAD_INPUT
     assert Cx.L.gmg_set_scalars(Cx.h, 0.0, 0.0) == gmg.BAD_INPUT
+
+
+def test_covered_masks_match_oracle(orc):
+    """The host's per-level covered masks (bounding-box arrays) are the oracle's cells inside a
+    level and not among its unknowns, for the three-level recipe at n = 16."""
+    import numpy as np
+
+    a = I.amr3(16)
+    M = orc.MultiLevelProblem(a["domain"], a["level_boxes"], a["bc_lo"], a["bc_hi"])
+    n = 16
+    shapes = [(n, n, n)] * 3
+    got = gmg.covered_masks(a["level_boxes"], a["level_lo"], shapes)
+    for lev in range(3):
+        sl = tuple(slice(a["level_lo"][lev][d], a["level_lo"][lev][d] + n) for d in (2, 1, 0))
+        assert np.array_equal(got[lev], (M.inside[lev] & ~M.masks[lev])[sl])
+        assert np.array_equal(got[lev], a["covered"][lev])
