@@ -150,6 +150,13 @@ typedef struct {
                            the finest level's post-smoothing also adds the correction to phi
                            (one pass over phi and e fewer per iteration); 0: separate.  Same
                            results. */
+  int settled_zero;     /* 1 (default): an FP64 residual taken right after a Gauss-Seidel
+                           half-sweep (the restriction after pre-smoothing; the multigrid
+                           iteration's residual after post-smoothing) on a single problem stores
+                           0 for the cells of the colour updated last, except on wall faces:
+                           such a cell reads only the other colour, unchanged since the update
+                           made its residual zero up to rounding.  0: every residual is
+                           computed.  Results differ by rounding. */
 } gmg_params;
 
 typedef struct {

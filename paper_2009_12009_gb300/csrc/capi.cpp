@@ -138,11 +138,12 @@ struct gmg_ctx {
     int64_t launches;
     int n_ev_smooth, n_ev_resid;  // profiling event pairs recorded per replay
   };
-  std::map<std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int, int, int, int, int>,
-           GraphEntry>
+  std::map<
+      std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int, int, int, int, int, int>,
+      GraphEntry>
       graphs;
   // preconditioner V-cycles of the top-level Krylov solvers, per (input, output, params)
-  std::map<std::tuple<const void*, void*, int, int, int, int, double, int, int, int, int, int, int>, GraphEntry>
+  std::map<std::tuple<const void*, void*, int, int, int, int, double, int, int, int, int, int, int, int>, GraphEntry>
       kgraphs;
 
   // profiling events (pairs around finest-level smoother / outer residual launches)
@@ -839,7 +840,9 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   smooth_sweeps(c, D, dt, m, p.nu1, p, s, !red_done, push, red_done);
   if (p.nu1 > 0 && !push) launch_fill(dt, D, B.e[dt], -1, 0, s);  // (nu1 = 0: e and its ghosts are still zero)
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
-  launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s);
+  // (pre-smoothing ends with a black half-sweep: black residuals vanish away from walls)
+  const bool settled = dt == DT_F64 && p.nu1 > 0 && p.settled_zero != 0 && c->ns() == 1 && D.push_ok;
+  launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s, settled);
   vcycle(c, dt, m + 1, p, s, false);
   launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
   smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, post_reversed(p), phi_update, push_phi);
@@ -865,6 +868,18 @@ bool fuse_correction_on(const gmg_ctx* c, const gmg_params& p, int dt) {
          D.n_pair_chunks == D.n_pair_all_chunks && !(p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0);
 }
 
+// The colour whose residual vanishes away from walls after an outer iteration (-1: none):
+// the level-0 colour smoothed last, when the correction was computed in FP64 (r - A e = 0
+// there up to rounding, and rhs - A (phi + e) = r - A e) on a single problem whose level-0
+// boxes are all smoothed and whose ghosts have their source's colour.
+int outer_settled(const gmg_ctx* c, const gmg_params& p, int dt) {
+  const LevelDev& D = c->dev[0];
+  if (!p.settled_zero || dt != DT_F64 || p.nu2 <= 0 || c->ns() != 1 || nlev(c) <= 1 || D.n_pair_chunks == 0 ||
+      D.n_pair_chunks != D.n_pair_all_chunks || !D.push_ok)
+    return -1;
+  return post_reversed(p) ? 0 : 1;
+}
+
 // One outer iteration: e = V(r); phi += e; r = rhs - A phi with per-problem ||r||_inf into
 // normbits[0, ns), copied to the pinned host mirror.
 void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const gmg_params& p, cudaStream_t s) {
@@ -882,7 +897,7 @@ void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const g
   if (ev) record_timing_event(c, ev[0], s);
   launch_residual(DT_F64, dt, c->dev[0], phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits,
                   any_singular(c) ? c->scal : nullptr, s, rr ? c->buf[0].e[dt] : nullptr,
-                  rr ? coefs_of(c, 0, dt).invD : nullptr, rr && level0_push(c, p, dt));
+                  rr ? coefs_of(c, 0, dt).invD : nullptr, rr && level0_push(c, p, dt), outer_settled(c, p, dt));
   if (ev) record_timing_event(c, ev[1], s);
   cudaMemcpyAsync(c->h_bits, c->normbits, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s);
 }
@@ -922,6 +937,7 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.post_reverse != 0 && p.post_reverse != 1) SETERR(c, GMG_ERR_BAD_INPUT, "post_reverse must be 0 or 1");
   if (p.fuse_correction != 0 && p.fuse_correction != 1)
     SETERR(c, GMG_ERR_BAD_INPUT, "fuse_correction must be 0 or 1");
+  if (p.settled_zero != 0 && p.settled_zero != 1) SETERR(c, GMG_ERR_BAD_INPUT, "settled_zero must be 0 or 1");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
   return GMG_OK;
 }
@@ -1014,7 +1030,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
     auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
                                p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep, p.ghost_push,
                                p.vector_smooth, p.pdl, p.fuse_residual_sweep, p.bottom_solver,
-                               p.post_reverse, p.fuse_correction);
+                               p.post_reverse, p.fuse_correction, p.settled_zero);
     auto itg = c->graphs.find(key);
     if (itg != c->graphs.end()) {
       gexec = itg->second.exec;
@@ -1735,7 +1751,7 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
     }
     auto key = std::make_tuple((const void*)in, (void*)out, p.precision, p.nu1, p.nu2, p.bottom_max_iter, p.bottom_tol,
                                p.fused_coarse, p.ghost_push, p.vector_smooth, p.bottom_solver, post_reversed(p) ? 1 : 0,
-                               p.pdl);
+                               p.pdl, p.settled_zero);
     auto itg = c->kgraphs.find(key);
     if (itg == c->kgraphs.end()) {
       cudaGraph_t g;
@@ -1962,6 +1978,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->bottom_solver = 0;
   p->post_reverse = 0;
   p->fuse_correction = 1;
+  p->settled_zero = 1;
   return GMG_OK;
 }
 

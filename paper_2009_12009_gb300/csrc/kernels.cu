@@ -321,6 +321,13 @@ __global__ void __launch_bounds__(BLOCK, 4) k_smooth4(const DevBox* __restrict__
 
 // ------------------------------------------------------------------- residual
 
+// whether global cell g of a level lies next to one of its problem's walls
+__device__ __forceinline__ bool next_to_wall(const DevGeom& G, int g0, int g1, int g2) {
+  return (G.wall_lo[0] && g0 == G.dlo[0]) || (G.wall_hi[0] && g0 == G.dhi[0]) || (G.wall_lo[1] && g1 == G.dlo[1]) ||
+         (G.wall_hi[1] && g1 == G.dhi[1]) || (G.wall_lo[2] && g2 == G.dlo[2]) || (G.wall_hi[2] && g2 == G.dhi[2]);
+}
+
+
 template <class T, class C>
 __device__ __forceinline__ typename Arith<T>::type resid_at(const T* phi, const T* rhs, const C* wx, const C* wy,
                                                            const C* wz, const C* D, int64_t q, int64_t sx, int64_t sy,
@@ -338,7 +345,8 @@ __device__ __forceinline__ typename Arith<T>::type resid_at(const T* phi, const 
 }
 
 template <class T, class R>
-__global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+__global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ boxes, const DevGeom* __restrict__ geoms,
+                                                    const Chunk* __restrict__ chunks,
                                                     const T* __restrict__ phi, const T* __restrict__ rhs,
                                                     const typename CoefOf<T>::type* __restrict__ wx,
                                                     const typename CoefOf<T>::type* __restrict__ wy,
@@ -346,7 +354,7 @@ __global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ b
                                                     const typename CoefOf<T>::type* __restrict__ D, R* r,
                                                     unsigned long long* maxbits, const double* shift_p, R* e,
                                                     const typename CoefOf<R>::type* __restrict__ invDe,
-                                                    const PushFace* __restrict__ push) {
+                                                    const PushFace* __restrict__ push, int settled) {
   pdl_enter();
   using A = typename Arith<T>::type;
   using AR = typename Arith<R>::type;
@@ -355,7 +363,41 @@ __global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ b
   const int t = ch.start + threadIdx.x;
   const A shift = shift_p ? (A)shift_p[B.solve] : (A)0;
   unsigned long long mx = 0;
-  if (t < ((B.nx + 1) >> 1) * B.ny * B.nz) {
+  if (settled >= 0 && t < ((B.nx + 1) >> 1) * B.ny * B.nz) {
+    // the cell of the pair not of the settled colour is computed; the settled one's r is 0
+    // unless it lies next to a wall.  e: r / D on red, 0 on black.
+    int i0, j, k;
+    pair_decode(B, t, i0, j, k);
+    const int64_t q0 = elem_index(B, i0, j, k);
+    const int c0 = (B.lo[0] + B.lo[1] + B.lo[2] + i0 + j + k) & 1;  // colour of the pair's first cell
+    const int cc = c0 == settled ? 1 : 0;                          // offset of the computed cell
+    const int cs = 1 - cc;                                          // offset of the settled cell
+    if (i0 + cc < B.nx) {
+      const A v = shift_p ? resid_at(phi, rhs, wx, wy, wz, D, q0 + cc, B.sx, B.sy, shift)
+                          : resid_at(phi, rhs, wx, wy, wz, D, q0 + cc, B.sx, B.sy, (A)0);
+      st(r + q0 + cc, v);
+      mx = abs_bits((double)v);
+    }
+    if (i0 + cs < B.nx) {
+      A v = 0;
+      if (next_to_wall(geoms[B.solve], B.lo[0] + i0 + cs, B.lo[1] + j, B.lo[2] + k)) {
+        v = shift_p ? resid_at(phi, rhs, wx, wy, wz, D, q0 + cs, B.sx, B.sy, shift)
+                    : resid_at(phi, rhs, wx, wy, wz, D, q0 + cs, B.sx, B.sy, (A)0);
+        const unsigned long long bb = abs_bits((double)v);
+        mx = bb > mx ? bb : mx;
+      }
+      st(r + q0 + cs, v);
+    }
+    if (e) {
+      for (int c = 0; c < 2; ++c) {
+        if (i0 + c >= B.nx) break;
+        const bool red = ((c0 + c) & 1) == 0;
+        const AR ev = red ? (AR)ld(r + q0 + c) * (AR)ldg(invDe + q0 + c) : (AR)0;
+        st(e + q0 + c, ev);
+        if (push) push_ghosts(B, ch.item, boxes, push, e, i0 + c, j, k, ev);
+      }
+    }
+  } else if (t < ((B.nx + 1) >> 1) * B.ny * B.nz) {
     int i0, j, k;
     pair_decode(B, t, i0, j, k);
     const int64_t q0 = elem_index(B, i0, j, k);
@@ -380,14 +422,35 @@ __global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ b
   if (maxbits) block_max_atomic(mx, maxbits + B.solve);
 }
 
+// the restriction of the residual of the 8 children of coarse cell (ci, cj, ck) of fine box F
+template <class T>
+__device__ __forceinline__ typename Arith<T>::type resid_sum8(const DevBox& F, const T* phi, const T* rhs,
+                                                              const typename CoefOf<T>::type* wx,
+                                                              const typename CoefOf<T>::type* wy,
+                                                              const typename CoefOf<T>::type* wz,
+                                                              const typename CoefOf<T>::type* D, int ci, int cj,
+                                                              int ck) {
+  using A = typename Arith<T>::type;
+  A s = 0;
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj) {
+      const int64_t q = elem_index(F, 2 * ci, 2 * cj + dj, 2 * ck + dk);
+      s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0);
+      s += resid_at(phi, rhs, wx, wy, wz, D, q + 1, F.sx, F.sy, (A)0);
+    }
+  return s;
+}
+
 // residual of the 8 children of one coarse cell, averaged into the coarse level
 template <class T, class R>
 __global__ void __launch_bounds__(BLOCK)
-    k_resid_restrict(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes,
+    k_resid_restrict(const DevBox* __restrict__ fboxes, const DevGeom* __restrict__ fgeoms,
+                     const DevBox* __restrict__ cboxes,
                      const int* __restrict__ parent, const Chunk* __restrict__ chunks, const T* __restrict__ phi,
                      const T* __restrict__ rhs, const typename CoefOf<T>::type* __restrict__ wx,
                      const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
-                     const typename CoefOf<T>::type* __restrict__ D, R* rc, const int* __restrict__ active) {
+                     const typename CoefOf<T>::type* __restrict__ D, R* rc, const int* __restrict__ active,
+                     int settled_black) {
   pdl_enter();
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[blockIdx.x];
@@ -399,12 +462,29 @@ __global__ void __launch_bounds__(BLOCK)
   if (t >= ncx * ncy * ncz) return;
   const int ci = t % ncx, cj = (t / ncx) % ncy, ck = t / (ncx * ncy);
   A s = 0;
-  for (int dk = 0; dk < 2; ++dk)
-    for (int dj = 0; dj < 2; ++dj) {
-      const int64_t q = elem_index(F, 2 * ci, 2 * cj + dj, 2 * ck + dk);
-      s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0);
-      s += resid_at(phi, rhs, wx, wy, wz, D, q + 1, F.sx, F.sy, (A)0);
+  if (settled_black) {
+    // the 4 red children; the black ones count 0 (see launch_resid_restrict) unless the
+    // coarse cell's children touch a wall
+    const int par = (F.lo[0] + F.lo[1] + F.lo[2]) & 1;  // colour of the box's first cell
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj) {
+        const int dx = (par + dj + dk) & 1;  // the red child of the row pair
+        const int64_t q = elem_index(F, 2 * ci + dx, 2 * cj + dj, 2 * ck + dk);
+        s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0);
+      }
+    const DevGeom G = fgeoms[F.solve];
+    const int g0 = F.lo[0] + 2 * ci, g1 = F.lo[1] + 2 * cj, g2 = F.lo[2] + 2 * ck;
+    if (next_to_wall(G, g0, g1, g2) || next_to_wall(G, g0 + 1, g1 + 1, g2 + 1)) {
+      for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj) {
+          const int dx = 1 - ((par + dj + dk) & 1);  // the black child
+          const int64_t q = elem_index(F, 2 * ci + dx, 2 * cj + dj, 2 * ck + dk);
+          s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0);
+        }
     }
+  } else {
+    s = resid_sum8(F, phi, rhs, wx, wy, wz, D, ci, cj, ck);
+  }
   const int I = (F.lo[0] >> 1) + ci - P.lo[0];
   const int J = (F.lo[1] >> 1) + cj - P.lo[1];
   const int K = (F.lo[2] >> 1) + ck - P.lo[2];
@@ -819,33 +899,36 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
 // residual work list: pair items over every box (the bottom level included)
 void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const void* rhs, const Coefs& c, void* r,
                      unsigned long long* maxbits, const double* shift, cudaStream_t s, void* e, const void* invDe,
-                     bool push) {
+                     bool push, int settled) {
+  if (settled >= 0 && (dt != DT_F64 || rdt != DT_F64 || !r)) settled = -1;  // (defined for FP64 only)
   if (!L.n_pair_all_chunks) return;
   ++g_launches;
   const PushFace* pf = push ? L.push_faces : nullptr;
 #define GMG_RESID(TR)                                                                                     \
-  GMG_DISPATCH(dt, launch_pdl(k_residual<T, TR>, grid_of(L.n_pair_all_chunks), BLOCK, 0, s, L.boxes,           \
+  GMG_DISPATCH(dt, launch_pdl(k_residual<T, TR>, grid_of(L.n_pair_all_chunks), BLOCK, 0, s, L.boxes, L.geoms, \
                               L.pair_all_chunks, (const T*)phi, (const T*)rhs,                                  \
                               (const typename CoefOf<T>::type*)c.wx, (const typename CoefOf<T>::type*)c.wy,     \
                               (const typename CoefOf<T>::type*)c.wz, (const typename CoefOf<T>::type*)c.D,      \
-                              (TR*)r, maxbits, shift, (TR*)e, (const typename CoefOf<TR>::type*)invDe, pf))
+                              (TR*)r, maxbits, shift, (TR*)e, (const typename CoefOf<TR>::type*)invDe, pf, settled))
   switch (rdt) {
     case DT_F64: GMG_RESID(double); break;
     case DT_F32: GMG_RESID(float); break;
     default: GMG_RESID(bf16); break;
   }
 #undef GMG_RESID
+
 }
 
 void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* phi, const void* rhs,
-                           const Coefs& cf, void* rc, cudaStream_t s) {
+                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black) {
   if (!f.n_coarse_chunks) return;
   ++g_launches;
-  GMG_DISPATCH(dt, launch_pdl(k_resid_restrict<T, T>, grid_of(f.n_coarse_chunks), BLOCK, 0, s, f.boxes, c.boxes,
+  GMG_DISPATCH(dt, launch_pdl(k_resid_restrict<T, T>, grid_of(f.n_coarse_chunks), BLOCK, 0, s, f.boxes, f.geoms, c.boxes,
                               f.parent, f.coarse_chunks, (const T*)phi, (const T*)rhs,
                               (const typename CoefOf<T>::type*)cf.wx, (const typename CoefOf<T>::type*)cf.wy,
                               (const typename CoefOf<T>::type*)cf.wz, (const typename CoefOf<T>::type*)cf.D, (T*)rc,
-                              f.active));
+                              f.active, settled_black ? 1 : 0));
+
 }
 
 void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s) {

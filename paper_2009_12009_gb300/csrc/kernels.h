@@ -87,12 +87,19 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
 // e (may be null): also the first red half-sweep of a V-cycle on this r from e = 0 --
 // e = r / D on red cells (invDe: 1/D in the coefficient type of rdt), 0 on black cells,
 // pushed into e's ghosts when push is set
+// settled (0 red, 1 black, -1 none; FP64 phi and r, one problem, a level whose ghosts have
+// their source's colour): the colour a Gauss-Seidel half-sweep updated last.  A cell of that
+// colour reads only cells of the other colour, unchanged since its update made its residual
+// zero up to rounding -- except next to a wall, whose ghost is the cell's own image (those
+// cells are computed).  Its r is stored as 0 without being computed.
 void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const void* rhs, const Coefs& c,
                      void* r, unsigned long long* maxbits, const double* shift, cudaStream_t s, void* e = nullptr,
-                     const void* invDe = nullptr, bool push = false);
-// coarse r = restriction of (rhs - A phi) (ghosts of phi filled)
+                     const void* invDe = nullptr, bool push = false, int settled = -1);
+// coarse r = restriction of (rhs - A phi) (ghosts of phi filled); settled_black: the last
+// half-sweep on phi was black (as for launch_residual: black children count 0 unless they
+// lie next to a wall)
 void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* phi, const void* rhs,
-                           const Coefs& cf, void* rc, cudaStream_t s);
+                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black = false);
 void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s);
 void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine,
                         cudaStream_t s, bool push = false);

@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("fused_sweep", C.c_int), ("ghost_push", C.c_int),
                 ("vector_smooth", C.c_int), ("pdl", C.c_int), ("fuse_residual_sweep", C.c_int),
                 ("krylov", C.c_int), ("bottom_solver", C.c_int), ("post_reverse", C.c_int),
-                ("fuse_correction", C.c_int)]
+                ("fuse_correction", C.c_int), ("settled_zero", C.c_int)]
 
 
 class SolveInfo(C.Structure):
