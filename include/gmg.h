@@ -152,8 +152,8 @@ typedef struct {
                            results. */
   int settled_zero;     /* 1 (default): an FP64 residual taken right after a Gauss-Seidel
                            half-sweep (the restriction after pre-smoothing; the multigrid
-                           iteration's residual after post-smoothing) on a single problem stores
-                           0 for the cells of the colour updated last, except on wall faces:
+                           iteration's residual after post-smoothing) stores 0 for the cells of
+                           the colour updated last, except next to walls:
                            such a cell reads only the other colour, unchanged since the update
                            made its residual zero up to rounding.  0: every residual is
                            computed.  Results differ by rounding. */

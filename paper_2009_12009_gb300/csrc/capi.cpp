@@ -841,7 +841,7 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   if (p.nu1 > 0 && !push) launch_fill(dt, D, B.e[dt], -1, 0, s);  // (nu1 = 0: e and its ghosts are still zero)
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
   // (pre-smoothing ends with a black half-sweep: black residuals vanish away from walls)
-  const bool settled = dt == DT_F64 && p.nu1 > 0 && p.settled_zero != 0 && c->ns() == 1 && D.push_ok;
+  const bool settled = dt == DT_F64 && p.nu1 > 0 && p.settled_zero != 0 && D.push_ok;
   launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s, settled);
   vcycle(c, dt, m + 1, p, s, false);
   launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
@@ -870,11 +870,12 @@ bool fuse_correction_on(const gmg_ctx* c, const gmg_params& p, int dt) {
 
 // The colour whose residual vanishes away from walls after an outer iteration (-1: none):
 // the level-0 colour smoothed last, when the correction was computed in FP64 (r - A e = 0
-// there up to rounding, and rhs - A (phi + e) = r - A e) on a single problem whose level-0
-// boxes are all smoothed and whose ghosts have their source's colour.
+// there up to rounding, and rhs - A (phi + e) = r - A e), every level-0 box is smoothed and
+// ghosts have their source's colour.  (In the batched form the residual of a problem that
+// has stopped is not used again.)
 int outer_settled(const gmg_ctx* c, const gmg_params& p, int dt) {
   const LevelDev& D = c->dev[0];
-  if (!p.settled_zero || dt != DT_F64 || p.nu2 <= 0 || c->ns() != 1 || nlev(c) <= 1 || D.n_pair_chunks == 0 ||
+  if (!p.settled_zero || dt != DT_F64 || p.nu2 <= 0 || nlev(c) <= 1 || D.n_pair_chunks == 0 ||
       D.n_pair_chunks != D.n_pair_all_chunks || !D.push_ok)
     return -1;
   return post_reversed(p) ? 0 : 1;

@@ -87,8 +87,8 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
 // e (may be null): also the first red half-sweep of a V-cycle on this r from e = 0 --
 // e = r / D on red cells (invDe: 1/D in the coefficient type of rdt), 0 on black cells,
 // pushed into e's ghosts when push is set
-// settled (0 red, 1 black, -1 none; FP64 phi and r, one problem, a level whose ghosts have
-// their source's colour): the colour a Gauss-Seidel half-sweep updated last.  A cell of that
+// settled (0 red, 1 black, -1 none; FP64 phi and r, a level whose ghosts have their
+// source's colour): the colour a Gauss-Seidel half-sweep updated last.  A cell of that
 // colour reads only cells of the other colour, unchanged since its update made its residual
 // zero up to rounding -- except next to a wall, whose ghost is the cell's own image (those
 // cells are computed).  Its r is stored as 0 without being computed.

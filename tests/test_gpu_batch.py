@@ -96,3 +96,16 @@ def test_batch_mixed_precision(batch, prec):
         got = ctx.unpack_solve(s, phi).cpu().numpy()
         r = (p["rhs"] - (p["rhs"].mean() if s == len(probs) - 1 else 0.0)) - P.apply(got)
         assert np.abs(r).max() <= 1.01e-10 * np.abs(p["rhs"]).max(), s
+
+
+def test_batch_settled_residuals_change_only_rounding(batch):
+    """The settled-colour residuals (the default) against computing every residual: every
+    problem takes the same iterations to 1e-10 and reaches the same iterate to 1e-12."""
+    probs, ctx, rhs, oracles = batch
+    p1, i1 = ctx.batch_solve(rhs, tol_rel=1e-10, settled_zero=1)
+    a1 = [ctx.unpack_solve(s, p1).cpu().numpy() for s in range(len(probs))]
+    p0, i0 = ctx.batch_solve(rhs, tol_rel=1e-10, settled_zero=0)
+    for s in range(len(probs)):
+        a0 = ctx.unpack_solve(s, p0).cpu().numpy()
+        assert i1[s].iterations == i0[s].iterations
+        assert np.abs(a1[s] - a0).max() <= 1e-12 * np.abs(a0).max()
