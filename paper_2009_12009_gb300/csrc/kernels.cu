@@ -443,7 +443,7 @@ __device__ __forceinline__ typename Arith<T>::type resid_sum8(const DevBox& F, c
 
 // residual of the 8 children of one coarse cell, averaged into the coarse level
 template <class T, class R>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, 5)
     k_resid_restrict(const DevBox* __restrict__ fboxes, const DevGeom* __restrict__ fgeoms,
                      const DevBox* __restrict__ cboxes,
                      const int* __restrict__ parent, const Chunk* __restrict__ chunks, const T* __restrict__ phi,
@@ -477,7 +477,8 @@ __global__ void __launch_bounds__(BLOCK)
     if (next_to_wall(G, g0, g1, g2) || next_to_wall(G, g0 + 1, g1 + 1, g2 + 1)) {
       for (int dk = 0; dk < 2; ++dk)
         for (int dj = 0; dj < 2; ++dj) {
-          const int dx = 1 - ((par + dj + dk) & 1);  // the black child
+          const int dx = 1 - ((par + dj + dk) & 1);  // the black child of the row pair
+          if (!next_to_wall(G, g0 + dx, g1 + dj, g2 + dk)) continue;  // (its residual is 0)
           const int64_t q = elem_index(F, 2 * ci + dx, 2 * cj + dj, 2 * ck + dk);
           s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0);
         }

@@ -16,6 +16,8 @@ the oracle.
   * amr2 (two levels, 128^3 + 128^3): two composite iterations element by element; the
     converged forward and adjoint solves' residuals by the oracle's composite operator and
     its transpose; the beta gradient of the GPU's phi and lambda against the oracle's.
+  * abec256 and contrast256 (beta = exp(3 N(0,1)) filtered): the multigrid-preconditioned
+    BiCGStab and CG solves of the benchmark, their true residuals by the oracle's operator.
   * amr3 (three levels, 128^3 cells each, level 2 off the centre of level 1): two composite
     iterations element by element; the converged solve's residual by the oracle's
     composite operator; the adjoint solve's residual by the oracle's transpose and the beta
@@ -377,3 +379,35 @@ def test_amr3_adjoint_and_gradient(amr3):
     got = amr3.from_gpu(amr3.C.beta_grad_levels(phis, lams))
     sc = max(np.abs(w).max() for w in want)
     assert max(np.abs(gg - w).max() for gg, w in zip(got, want)) <= 1e-10 * sc
+
+
+@pytest.fixture(scope="module")
+def krylov256():
+    out = {}
+    for name in ("abec256", "contrast256"):
+        cfg = getattr(I, name)()
+        C = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"], stream=stream())
+        C.allocate(gmg.MIXED_FP32, krylov=True)
+        C.set_scalars(cfg["a"], cfg["b"])
+        C.set_beta(torch.from_numpy(cfg["beta"]))
+        P = O.Problem(cfg["domain"], cfg["boxes"], cfg["bc_lo"], cfg["bc_hi"])
+        P.set_coeffs(cfg["a"], cfg["b"], alpha=cfg["alpha"], beta=cfg["beta"])
+        out[name] = (cfg, C, P)
+    return out
+
+
+@pytest.mark.parametrize("name,method,prec", [("abec256", 1, gmg.FP64), ("abec256", 2, gmg.FP64),
+                                              ("contrast256", 1, gmg.FP64), ("contrast256", 2, gmg.FP64),
+                                              ("contrast256", 1, gmg.MIXED_FP32)],
+                         ids=["abec256-bicgstab", "abec256-cg", "contrast256-bicgstab", "contrast256-cg",
+                              "contrast256-bicgstab-fp32"])
+def test_krylov_converged_residual(krylov256, name, method, prec):
+    """The multigrid-preconditioned Krylov solves of the benchmark, to 1e-10 of the recursive
+    residual: the true residual by the oracle's operator is within 1.5e-10 (the recurrence
+    and the true residual drift apart by rounding over the iterations)."""
+    cfg, C, P = krylov256[name]
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=TOL, max_iter=200, krylov=method,
+                        precision=prec)
+    assert info.status == gmg.OK
+    rel = oracle_rel_residual(P, C.unpack(phi).cpu().numpy(), cfg["rhs"])
+    assert rel <= 1.5e-10, rel
