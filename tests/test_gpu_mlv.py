@@ -2,7 +2,8 @@
 the composite operator and its transpose (1e-12 of scale), the composite multigrid solve at
 a fixed iteration count (1e-10, same residual history) and to tolerance (1e-12 on both
 sides, 1e-10), the adjoint solve (A^T lambda = g by the oracle's transpose, 1e-10) and the
-beta gradient (1e-10 of scale), for periodic, Dirichlet and Neumann walls."""
+beta gradient (1e-10 of scale), for periodic, Dirichlet and Neumann walls; and over four
+levels (the maximum), periodic and Dirichlet."""
 import numpy as np
 import pytest
 
@@ -29,9 +30,15 @@ def three_levels(n=16):
     return dom, [I.chop(*dom, n // 2), l1, l2]
 
 
+def four_levels(n=8):
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    h = n // 2
+    return dom, [I.chop(*dom, h)] + [I.chop((lo,) * 3, (lo + n - 1,) * 3, h) for lo in (n // 2, 3 * n // 2, 7 * n // 2)]
+
+
 class MlvPair:
-    def __init__(self, bc, seed=40, n=16):
-        dom, lb = three_levels(n)
+    def __init__(self, bc, seed=40, n=16, nlev=3):
+        dom, lb = three_levels(n) if nlev == 3 else four_levels(n)
         self.P = O.MultiLevelProblem(dom, lb, [bc] * 3, [bc] * 3)
         self.C = gmg.MultiLevelContext(dom, lb, [bc] * 3, [bc] * 3, stream=torch.cuda.current_stream().cuda_stream)
         self.C.allocate(gmg.FP64)
@@ -75,12 +82,14 @@ class MlvPair:
         return rs
 
 
-@pytest.fixture(scope="module", params=[P_, D_, N_], ids=["periodic", "dirichlet", "neumann"])
+@pytest.fixture(scope="module", params=[(P_, 3), (D_, 3), (N_, 3), (P_, 4), (D_, 4)],
+                ids=["periodic", "dirichlet", "neumann", "periodic-4lev", "dirichlet-4lev"])
 def mp(request):
-    return MlvPair(request.param)
+    bc, nlev = request.param
+    return MlvPair(bc, nlev=nlev, n=16 if nlev == 3 else 8)
 
 
-def test_three_level_apply(mp):
+def test_multilevel_apply(mp):
     xs = [mp.rng.standard_normal(s) * m for s, m in zip(mp.P.shapes, mp.P.masks)]
     want = mp.P.apply(xs)
     got = mp.from_gpu(mp.C.apply_levels(mp.to_gpu(xs)))
@@ -88,7 +97,7 @@ def test_three_level_apply(mp):
     assert max(np.abs(g - w).max() for g, w in zip(got, want)) <= 1e-12 * sc
 
 
-def test_three_level_solve_fixed_iterations(mp):
+def test_multilevel_solve_fixed_iterations(mp):
     rs = mp.rand_rhs()
     want, it, hist, st = mp.P.solve(rs, tol_rel=0.0, maxit=3)
     phis, info = mp.C.solve_levels(mp.to_gpu(rs), tol_rel=0.0, max_iter=3)
@@ -99,7 +108,7 @@ def test_three_level_solve_fixed_iterations(mp):
     assert max(np.abs((g - w) * m).max() for g, w, m in zip(got, want, mp.P.masks)) <= 1e-10 * sc
 
 
-def test_three_level_solve_to_tolerance(mp):
+def test_multilevel_solve_to_tolerance(mp):
     rs = mp.rand_rhs()
     want, it, hist, st = mp.P.solve(rs, tol_rel=1e-12, maxit=100)
     phis, info = mp.C.solve_levels(mp.to_gpu(rs), tol_rel=1e-12, max_iter=100)
@@ -112,7 +121,7 @@ def test_three_level_solve_to_tolerance(mp):
     assert max(np.abs(x).max() for x in r) <= 1.01e-12 * max(np.abs(x).max() for x in rs) * 10
 
 
-def test_three_level_transpose(mp):
+def test_multilevel_transpose(mp):
     ys = [mp.rng.standard_normal(s) * m for s, m in zip(mp.P.shapes, mp.P.masks)]
     want = mp.P.apply(ys, transpose=True)
     got = mp.from_gpu(mp.C.apply_levels(mp.to_gpu(ys), transpose=True))
@@ -120,7 +129,7 @@ def test_three_level_transpose(mp):
     assert max(np.abs(g - w).max() for g, w in zip(got, want)) <= 1e-12 * sc
 
 
-def test_three_level_adjoint_and_gradient(mp):
+def test_multilevel_adjoint_and_gradient(mp):
     """A^T lambda = g solved on the GPU, checked with the oracle's transpose; the beta
     gradient from the oracle's phi and the GPU's lambda against the oracle's gradient of the
     same."""

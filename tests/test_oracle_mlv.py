@@ -329,3 +329,42 @@ def test_transpose_refuses_nesting_closer_than_two_cells(orc):
     M2 = orc.MultiLevelProblem(dom, [I.chop(*dom, 8), l1, [((20, 20, 20), (29, 27, 27))]], [D_] * 3, [D_] * 3)
     M2.set_coeffs(0.0, 1.0)
     M2.apply(xs, transpose=True)
+
+
+def four_levels(n=8):
+    """four levels: level 0 is n^3 in boxes of n/2; level l >= 1 is a cube of n of its own
+    cells from n/2, 3n/2, 7n/2 (in boxes of n/2), i.e. two or more cells inside the level below
+    it, each box coarsened inside one box of that level"""
+    dom = ((0, 0, 0), (n - 1, n - 1, n - 1))
+    h = n // 2
+    los = [0, n // 2, 3 * n // 2, 7 * n // 2]  # low corner of level l in its own index space
+    lbs = [I.chop(*dom, h)] + [I.chop((lo,) * 3, (lo + n - 1,) * 3, h) for lo in los[1:]]
+    return dom, lbs
+
+
+@pytest.mark.parametrize("bc", [P_, D_])
+def test_four_levels_reach_lapack_and_transpose(orc, bc):
+    """The maximum of four levels: the composite iteration reaches LAPACK's solution of the
+    assembled system, and the transpose scatters the assembled matrix's rows."""
+    dom, lb = four_levels(8)
+    M = orc.MultiLevelProblem(dom, lb, [bc] * 3, [bc] * 3)
+    rng = np.random.default_rng(39)
+    rand_coeffs(M, rng, bc == P_, a=1.0 if bc == D_ else 0.0)
+    A = M.matrix()
+    m = A.shape[0]
+    r = M.pack([rng.standard_normal(s) for s in M.shapes])
+    if bc != D_:
+        V = M.volumes()
+        r = r - (V @ r) / V.sum()
+        B = np.zeros((m + 1, m + 1))
+        B[:m, :m] = A
+        B[:m, m] = 1.0
+        B[m, :m] = V
+        want = np.linalg.solve(B, np.concatenate([r, [0.0]]))[:m]
+    else:
+        want = np.linalg.solve(A, r)
+    ps, it, hist, st = M.solve(M.unpack(r), tol_rel=1e-13, maxit=200)
+    assert st == 0
+    assert np.abs(M.pack(ps) - want).max() <= 1e-10 * np.abs(want).max()
+    y = rng.standard_normal(m)
+    assert np.abs(M.pack(M.apply(M.unpack(y), transpose=True)) - A.T @ y).max() <= 1e-12 * np.abs(A).max() * np.abs(y).max() * 10
