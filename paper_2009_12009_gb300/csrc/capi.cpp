@@ -89,6 +89,7 @@ struct AmrLevel {
   double *alpha = nullptr, *bx = nullptr, *by = nullptr, *bz = nullptr, *beta_cell = nullptr;
   double *rhs = nullptr, *res = nullptr, *tmp = nullptr, *zero = nullptr;  // projected rhs, residual
   double* kf[9] = {};  // adjoint BiCGStab vectors
+  double* phi = nullptr;  // the composite solve's iterate on this level
   bool have_beta = false, have_alpha = false;
 };
 
@@ -177,6 +178,7 @@ struct gmg_ctx {
   double *crhs = nullptr, *cres = nullptr;  // level 0: projected rhs, composite residual
   double *ctmp = nullptr, *czero = nullptr;
   double* kc[9] = {};  // level 0's adjoint BiCGStab vectors
+  double* cphi = nullptr;  // level 0's iterate of the composite solve
 
   int ns() const { return (int)geoms.size(); }
 };
@@ -405,9 +407,9 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     A.navg_cell = (int)H.avg_cells.size();
     double* f5[5];
     for (int q = 0; q < 5; ++q) f5[q] = (double*)cv.take(8 * nf);
-    double* cc[4] = {};
+    double* cc[5] = {};
     if (al == 0)
-      for (int q = 0; q < 4; ++q) cc[q] = (double*)cv.take(8 * ne0);
+      for (int q = 0; q < 5; ++q) cc[q] = (double*)cv.take(8 * ne0);
     double* ff[5];
     for (int q = 0; q < 5; ++q) ff[q] = (double*)cv.take(8 * nf);
     double *kc[9] = {}, *kf[9] = {};  // the adjoint solve's vectors
@@ -422,10 +424,10 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
       V.A = A;
       V.alpha = f5[0]; V.bx = f5[1]; V.by = f5[2]; V.bz = f5[3]; V.beta_cell = f5[4];
       if (al == 0) {
-        c->crhs = cc[0]; c->cres = cc[1]; c->ctmp = cc[2]; c->czero = cc[3];
+        c->crhs = cc[0]; c->cres = cc[1]; c->ctmp = cc[2]; c->czero = cc[3]; c->cphi = cc[4];
         for (int q = 0; q < 9; ++q) c->kc[q] = kc[q];
       }
-      V.rhs = ff[0]; V.res = ff[1]; V.tmp = ff[2]; V.zero = ff[3];
+      V.rhs = ff[0]; V.res = ff[1]; V.tmp = ff[2]; V.zero = ff[3]; V.phi = ff[4];
       for (int q = 0; q < 9; ++q) V.kf[q] = kf[q];
     }
   }
@@ -1331,17 +1333,20 @@ gmg_status comp_shift_n(gmg_ctx* c, double* const* x, double k) {
 
 // Composite multigrid solve over every AMR level (the oracle's multi-level iteration; with
 // two levels its two-level one): residual, composite correction, update, average-down.
-gmg_status solve_amr_n(gmg_ctx* c, double* const* phi, const double* const* rhs_user, double tol_rel, double tol_abs,
-                       const gmg_params& p, gmg_solve_info* info) {
+// (the iterate lives in the context's own buffers, so one captured iteration serves every
+// call with the same parameters; it is copied to the caller's arrays at the end)
+gmg_status solve_amr_n(gmg_ctx* c, double* const* phi_user, const double* const* rhs_user, double tol_rel,
+                       double tol_abs, const gmg_params& p, gmg_solve_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = c->stream;
   const int L = namr(c);
   const int64_t l0 = kernel_launch_count();
   if (info) memset(info, 0, sizeof(*info));
-  double *rhs[GMG_MAX_AMR_LEVELS], *res[GMG_MAX_AMR_LEVELS];
+  double *rhs[GMG_MAX_AMR_LEVELS], *res[GMG_MAX_AMR_LEVELS], *phi[GMG_MAX_AMR_LEVELS];
   for (int l = 0; l < L; ++l) {
     rhs[l] = l == 0 ? c->crhs : c->amrl[l - 1].rhs;
     res[l] = l == 0 ? c->cres : c->amrl[l - 1].res;
+    phi[l] = l == 0 ? c->cphi : c->amrl[l - 1].phi;
     CK(c, cudaMemcpyAsync(rhs[l], rhs_user[l], 8 * (size_t)anelem(c, l), cudaMemcpyDeviceToDevice, s));
   }
   CK(c, cudaMemsetAsync(c->normbits, 0, 8 * (size_t)L, s));
@@ -1369,13 +1374,49 @@ gmg_status solve_amr_n(gmg_ctx* c, double* const* phi, const double* const* rhs_
   std::vector<double> hist{rn};
   int it = 0;
   gmg_status result = GMG_OK;
-  while (!(rn <= target) && it < p.max_iter) {
-    comp_correction_n(c, p, res, s);
+  // one iteration: correction, update, covered := average, composite residual and its norms
+  auto iteration = [&](cudaStream_t st_) {
+    comp_correction_n(c, p, res, st_);
     for (int l = 0; l < L; ++l)
-      launch_add_correction(DT_F64, adev(c, l), phi[l], l == 0 ? c->buf[0].e[DT_F64] : c->amrl[l - 1].B.e[DT_F64], s);
-    for (int l = L - 1; l >= 1; --l)
-      launch_restrict(DT_F64, adev(c, l), adev(c, l - 1), phi[l], phi[l - 1], s);  // covered := average
-    comp_residual_n(c, phi, rhs, res, c->normbits, s);
+      launch_add_correction(DT_F64, adev(c, l), phi[l], l == 0 ? c->buf[0].e[DT_F64] : c->amrl[l - 1].B.e[DT_F64],
+                            st_);
+    for (int l = L - 1; l >= 1; --l) launch_restrict(DT_F64, adev(c, l), adev(c, l - 1), phi[l], phi[l - 1], st_);
+    comp_residual_n(c, phi, rhs, res, c->normbits, st_);
+  };
+  cudaGraphExec_t gexec = nullptr;
+  int64_t per_iter = 0;
+  if (p.use_graph && !(rn <= target) && p.max_iter > 0) {
+    // keyed by the context's own buffers (no caller pointer is captured) and the parameters
+    // the iteration reads
+    auto key = std::make_tuple((void*)phi[0], (const void*)rhs[0], L, p.nu1, p.nu2, p.bottom_max_iter, p.bottom_tol,
+                               0, p.fused_coarse, 0, p.ghost_push, p.vector_smooth, p.pdl, 0, p.bottom_solver,
+                               p.post_reverse, 0, p.settled_zero);
+    auto itg = c->graphs.find(key);
+    if (itg != c->graphs.end()) {
+      gexec = itg->second.exec;
+      per_iter = itg->second.launches;
+    } else {
+      cudaGraph_t g;
+      const int64_t lc0 = kernel_launch_count();
+      CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      iteration(c->cap_stream);
+      cudaError_t e1 = cudaStreamEndCapture(c->cap_stream, &g);
+      if (e1 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+      cudaError_t e2 = cudaGraphInstantiate(&gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+      per_iter = kernel_launch_count() - lc0;
+      count_launches((int)-per_iter);  // captured, not launched
+      c->graphs[key] = {gexec, per_iter, 0, 0};
+    }
+  }
+  while (!(rn <= target) && it < p.max_iter) {
+    if (gexec) {
+      CK(c, cudaGraphLaunch(gexec, s));
+      count_launches((int)per_iter);
+    } else {
+      iteration(s);
+    }
     if ((st = read_norms_n(c, L, &rn))) return st;
     ++it;
     hist.push_back(rn);
@@ -1392,6 +1433,8 @@ gmg_status solve_amr_n(gmg_ctx* c, double* const* phi, const double* const* rhs_
     if ((st = comp_shift_n(c, phi, mean))) return st;
   }
   for (int l = L - 1; l >= 1; --l) launch_restrict(DT_F64, adev(c, l), adev(c, l - 1), phi[l], phi[l - 1], s);
+  for (int l = 0; l < L; ++l)
+    CK(c, cudaMemcpyAsync(phi_user[l], phi[l], 8 * (size_t)anelem(c, l), cudaMemcpyDeviceToDevice, s));
   CK(c, cudaStreamSynchronize(s));
   CK(c, cudaGetLastError());
   if (info) {
@@ -1546,15 +1589,43 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
   // preconditioner is V M V^-1: scale level l of the input by V_0 / V_l = 8^l, apply M,
   // scale level l of the output by 8^-l.  V^-1 also maps the range of A^T (zero sum) onto
   // the range of A (zero volume-weighted sum) for the singular problem.
-  auto precond = [&](double* const* in, double* const* out) {
-    for (int l = 0; l < L; ++l) launch_axpby(ne[l], z.v[0] / z.v[l], in[l], 0.0, in[l], tmp[l], s);
-    comp_correction_n(c, p, tmp, s);
-    for (int l = 0; l < L; ++l) launch_axpby(ne[l], z.v[l] / z.v[0], e[l], 0.0, e[l], out[l], s);
+  // mid = V M V^-1 in, then out = A^T mid (mid copied first: the transpose overwrites its
+  // input's ghosts).  With use_graph each of the two (in, mid, out) triples of the iteration
+  // is captured once and replayed.
+  auto prec_apply = [&](double* const* in, double* const* mid, double* const* out, cudaStream_t st_) {
+    for (int l = 0; l < L; ++l) launch_axpby(ne[l], z.v[0] / z.v[l], in[l], 0.0, in[l], tmp[l], st_);
+    comp_correction_n(c, p, tmp, st_);
+    for (int l = 0; l < L; ++l) launch_axpby(ne[l], z.v[l] / z.v[0], e[l], 0.0, e[l], mid[l], st_);
+    for (int l = 0; l < L; ++l) launch_axpby(ne[l], 1.0, mid[l], 0.0, mid[l], tmp[l], st_);
+    comp_apply_transpose_n(c, tmp, out, st_);
   };
-  // out = A^T x with x copied first (the transpose overwrites its input's ghosts)
-  auto apply_t = [&](double* const* x, double* const* out) {
-    axpby(1.0, x, 0.0, x, tmp);
-    comp_apply_transpose_n(c, tmp, out, s);
+  auto run_pa = [&](double* const* in, double* const* mid, double* const* out) -> gmg_status {
+    if (!p.use_graph) {
+      prec_apply(in, mid, out, s);
+      return GMG_OK;
+    }
+    auto key = std::make_tuple((void*)mid[0], (const void*)in[0], L, p.nu1, p.nu2, p.bottom_max_iter, p.bottom_tol, 1,
+                               p.fused_coarse, 1, p.ghost_push, p.vector_smooth, p.pdl, 1, p.bottom_solver,
+                               p.post_reverse, 1, p.settled_zero);
+    auto itg = c->graphs.find(key);
+    if (itg == c->graphs.end()) {
+      cudaGraph_t g;
+      cudaGraphExec_t ge;
+      const int64_t lc0 = kernel_launch_count();
+      CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      prec_apply(in, mid, out, c->cap_stream);
+      cudaError_t e1 = cudaStreamEndCapture(c->cap_stream, &g);
+      if (e1 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+      cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+      const int64_t n = kernel_launch_count() - lc0;
+      count_launches((int)-n);  // captured, not launched
+      itg = c->graphs.emplace(key, gmg_ctx::GraphEntry{ge, n, 0, 0}).first;
+    }
+    CK(c, cudaGraphLaunch(itg->second.exec, s));
+    count_launches((int)itg->second.launches);
+    return GMG_OK;
   };
   while (!(rn <= target) && it < p.max_iter) {
     ++it;
@@ -1564,8 +1635,7 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
     const double beta = (rho / rho_old) * (alpha / omega);
     axpby(1.0, k[2], -omega, k[3], k[2]);  // p = r + beta (p - omega v)
     axpby(1.0, k[0], beta, k[2], k[2]);
-    precond(k[2], k[6]);
-    apply_t(k[6], k[3]);
+    if ((st = run_pa(k[2], k[6], k[3]))) return st;
     double rv;
     if ((st = comp_dot_n(c, k[1], k[3], &rv))) return st;
     if (std::fabs(rv) < 1e-300) break;
@@ -1579,8 +1649,7 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
       hist.push_back(rn);
       break;
     }
-    precond(k[4], k[7]);
-    apply_t(k[7], k[5]);
+    if ((st = run_pa(k[4], k[7], k[5]))) return st;
     double tt, ts;
     if ((st = comp_dot_n(c, k[5], k[5], &tt))) return st;
     if ((st = comp_dot_n(c, k[5], k[4], &ts))) return st;
