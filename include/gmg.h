@@ -290,21 +290,24 @@ gmg_status gmg_set_workspace(gmg_ctx* ctx, void* dptr, size_t bytes);
 /* Solve A phi = rhs from phi = 0 (phi's input content is ignored) until
    ||rhs - A phi||_inf <= max(tol_rel * ||rhs||_inf, tol_abs) or p->max_iter outer
    iterations.  phi[l], rhs[l]: FP64 device arrays in AMR level l's layout.  One level:
-   the multigrid V-cycle iteration.  Two levels: A is the composite operator on the fine
-   cells and the uncovered coarse cells (fine ghosts on the coarse/fine boundary by
-   quadratic interpolation, coarse cells next to the fine level refluxed: the mean of the 4
-   fine fluxes replaces the coarse flux on a shared face), solved by the two-level
-   composite multigrid iteration (fine smoothing, coarse V-cycle on level 0's hierarchy);
-   on return covered coarse cells of phi[0] hold the average of the fine solution, and the
-   rhs entries of covered cells are ignored; FP64 only.  info may be NULL.  Returns GMG_OK,
-   GMG_ERR_NOT_CONVERGED (phi holds the last iterate), GMG_ERR_DIVERGED or
-   GMG_ERR_BAD_INPUT (nonzero-mean rhs of a singular problem without project_mean; for
-   two levels the mean is volume-weighted over the composite cells). */
+   the multigrid V-cycle iteration.  Several AMR levels: A is the composite operator on the
+   cells not covered by a finer level (fine ghosts on each coarse/fine boundary by quadratic
+   interpolation from the level below, cells next to a finer level refluxed: the mean of
+   the 4 fine fluxes replaces the coarse flux on a shared face), solved by the composite
+   multigrid iteration (down the levels: smoothing of each refined level's correction,
+   restriction of its correction residual and reflux into the level below; a V-cycle of
+   level 0's hierarchy; up: interpolation and smoothing); with use_graph one captured
+   iteration is replayed.  On return covered cells of phi[l] hold the average of the finer
+   solution, and the rhs entries of covered cells are ignored; FP64 only.  info may be
+   NULL.  Returns GMG_OK, GMG_ERR_NOT_CONVERGED (phi holds the last iterate),
+   GMG_ERR_DIVERGED or GMG_ERR_BAD_INPUT (nonzero-mean rhs of a singular problem without
+   project_mean; with several levels the mean is volume-weighted over the composite
+   cells). */
 gmg_status gmg_solve(gmg_ctx* ctx, void* const* phi, const void* const* rhs, double tol_rel, double tol_abs,
                      const gmg_params* p, gmg_solve_info* info);
 
-/* out = A phi (FP64; phi's ghost cells are overwritten).  Two levels: the composite
-   operator; covered coarse entries of out are 0. */
+/* out = A phi (FP64; phi's ghost cells are overwritten).  Several AMR levels: the
+   composite operator; covered entries of out are 0. */
 gmg_status gmg_apply(gmg_ctx* ctx, void* const* out, void* const* phi);
 
 /* out = A^T y.  One level: A is symmetric (same as gmg_apply).  Several AMR levels: the
@@ -345,7 +348,7 @@ gmg_status gmg_beta_grad(gmg_ctx* ctx, void* const* dbeta, void* const* phi, voi
    values[f], f = 2*d + side (x-, x+, y-, y+, z-, z+): FP64 device array over face f's two
    tangential axes in increasing order, the lower one fastest (n_t1 * n_t2 values; for a
    face normal to y: x fastest, then z), or NULL for g = 0.  A periodic face must be NULL;
-   a context with several problems or two levels accepts only NULLs (GMG_ERR_BAD_INPUT).
+   a context with several problems or several AMR levels accepts only NULLs (GMG_ERR_BAD_INPUT).
    All work is enqueued on the context stream; nothing is synchronised. */
 
 /* out = rhs - A_g(0): rhs plus, in each cell next to a wall face with a value, 2 w g
