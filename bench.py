@@ -594,6 +594,9 @@ def main():
                         "launches_timed": sm_n},
            "outer_residual": {"kernel": "k_residual<double> (finest level, FP64)", "avg_launch_us":
                               1e3 * rs_ms / max(rs_n, 1), "launches_timed": rs_n},
+           # per V-cycle iteration, and the finest level's share of the cell updates
+           "ms_per_iteration": ms / args.steps / max(its[0], 1),
+           "finest_level_value": ncells * nu * sum(its) * world / (ms * 1e-3) / 1e6,
            "clocks": clk}
 
     if not args.no_mixed:
