@@ -1502,6 +1502,26 @@ gmg_status comp_dot_n(gmg_ctx* c, double* const* x, double* const* y, double* ou
   return GMG_OK;
 }
 
+// two such sums with one read-back: out1 = sum <x1_l, y1_l>, out2 = sum <x2_l, y2_l>
+gmg_status comp_dot2_n(gmg_ctx* c, double* const* x1, double* const* y1, double* const* x2, double* const* y2,
+                       double* out1, double* out2) {
+  cudaStream_t s = c->stream;
+  const int L = namr(c);
+  for (int l = 0; l < L; ++l) launch_dot(adev(c, l), x1[l], y1[l], c->partials, c->scal + l, s);  // in stream order
+  for (int l = 0; l < L; ++l) launch_dot(adev(c, l), x2[l], y2[l], c->partials, c->scal + L + l, s);
+  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 16 * (size_t)L, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  double a = 0.0, b = 0.0;
+  for (int l = 0; l < L; ++l) {
+    a += c->h_scal[l];
+    b += c->h_scal[L + l];
+  }
+  *out1 = a;
+  *out2 = b;
+  return GMG_OK;
+}
+
 // max over the levels of ||x_l||_inf
 gmg_status comp_norm_n(gmg_ctx* c, double* const* x, double* out) {
   const int L = namr(c);
@@ -1633,8 +1653,8 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
     if ((st = comp_dot_n(c, k[1], k[0], &rho))) return st;
     if (std::fabs(rho) < 1e-300) break;
     const double beta = (rho / rho_old) * (alpha / omega);
-    axpby(1.0, k[2], -omega, k[3], k[2]);  // p = r + beta (p - omega v)
-    axpby(1.0, k[0], beta, k[2], k[2]);
+    for (int l = 0; l < L; ++l)  // p = r + beta (p - omega v), one pass
+      launch_bicg_direction(ne[l], k[0][l], k[2][l], k[3][l], beta, omega, s);
     if ((st = run_pa(k[2], k[6], k[3]))) return st;
     double rv;
     if ((st = comp_dot_n(c, k[1], k[3], &rv))) return st;
@@ -1651,12 +1671,10 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
     }
     if ((st = run_pa(k[4], k[7], k[5]))) return st;
     double tt, ts;
-    if ((st = comp_dot_n(c, k[5], k[5], &tt))) return st;
-    if ((st = comp_dot_n(c, k[5], k[4], &ts))) return st;
+    if ((st = comp_dot2_n(c, k[5], k[5], k[5], k[4], &tt, &ts))) return st;
     if (tt == 0.0) break;
     omega = ts / tt;
-    axpby(1.0, lam, alpha, k[6], lam);
-    axpby(1.0, lam, omega, k[7], lam);
+    for (int l = 0; l < L; ++l) launch_add2(ne[l], lam[l], alpha, k[6][l], omega, k[7][l], s);  // one pass
     axpby(1.0, k[4], -omega, k[5], k[0]);
     if ((st = comp_norm_n(c, k[0], &rn))) return st;
     hist.push_back(rn);
