@@ -344,8 +344,11 @@ __device__ __forceinline__ typename Arith<T>::type resid_at(const T* phi, const 
   return v;
 }
 
-template <class T, class R>
-__global__ void __launch_bounds__(BLOCK) k_residual(const DevBox* __restrict__ boxes, const DevGeom* __restrict__ geoms,
+// (MINB: resident blocks per SM the register count must allow; 6 for the FP64 residual,
+// whose loads then have more warps to overlap them; 0, no bound, elsewhere)
+template <class T, class R, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_residual(const DevBox* __restrict__ boxes,
+                                                          const DevGeom* __restrict__ geoms,
                                                     const Chunk* __restrict__ chunks,
                                                     const T* __restrict__ phi, const T* __restrict__ rhs,
                                                     const typename CoefOf<T>::type* __restrict__ wx,
@@ -906,7 +909,8 @@ void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const 
   ++g_launches;
   const PushFace* pf = push ? L.push_faces : nullptr;
 #define GMG_RESID(TR)                                                                                     \
-  GMG_DISPATCH(dt, launch_pdl(k_residual<T, TR>, grid_of(L.n_pair_all_chunks), BLOCK, 0, s, L.boxes, L.geoms, \
+  GMG_DISPATCH(dt, launch_pdl(k_residual<T, TR, std::is_same<T, double>::value && std::is_same<TR, double>::value ? 6 : 0>, \
+                              grid_of(L.n_pair_all_chunks), BLOCK, 0, s, L.boxes, L.geoms,                        \
                               L.pair_all_chunks, (const T*)phi, (const T*)rhs,                                  \
                               (const typename CoefOf<T>::type*)c.wx, (const typename CoefOf<T>::type*)c.wy,     \
                               (const typename CoefOf<T>::type*)c.wz, (const typename CoefOf<T>::type*)c.D,      \
