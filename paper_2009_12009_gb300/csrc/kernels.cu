@@ -520,8 +520,9 @@ __global__ void __launch_bounds__(BLOCK)
   st(coarse + elem_index(P, I, J, K), s * (A)0.125);
 }
 
-template <class T>
-__global__ void __launch_bounds__(BLOCK)
+// (MINB as for k_residual: 8 for FP64, no bound otherwise)
+template <class T, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
     k_prolong_add(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes, const int* __restrict__ parent,
                   const Chunk* __restrict__ chunks, const T* __restrict__ coarse, T* fine,
                   const int* __restrict__ active, const PushFace* __restrict__ push) {
@@ -949,7 +950,8 @@ void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void
   if (!f.n_coarse_chunks) return;
   ++g_launches;
   const PushFace* pf = push ? f.push_faces : nullptr;
-  GMG_DISPATCH(dt, launch_pdl(k_prolong_add<T>, grid_of(f.n_coarse_chunks), BLOCK, 0, s, f.boxes, c.boxes,
+  GMG_DISPATCH(dt, launch_pdl(k_prolong_add<T, std::is_same<T, double>::value ? 8 : 0>, grid_of(f.n_coarse_chunks),
+                              BLOCK, 0, s, f.boxes, c.boxes,
                               f.parent, f.coarse_chunks, (const T*)coarse, (T*)fine, f.active, pf));
 }
 
