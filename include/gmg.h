@@ -89,7 +89,10 @@ typedef struct {
   int precision;        /* gmg_precision, default GMG_FP64 */
   int project_mean;     /* singular (no Dirichlet wall, a = 0): project a nonzero-mean rhs
                            instead of returning GMG_ERR_BAD_INPUT; default 0 */
-  int use_graph;        /* replay the V-cycle as a captured CUDA graph, default 1 */
+  int use_graph;        /* 1 (default): replay one outer iteration as a captured CUDA graph
+                           (one level and batched: the V-cycle, update and residual; several
+                           AMR levels: the composite iteration, and in the adjoint solve its
+                           two preconditioner-and-transpose steps); 0: direct launches */
   int profile;          /* record CUDA events around every finest-level smoother and
                            outer-residual launch (inside the graph too; with fused sweeps
                            the region pass of each sweep); default 0 */
