@@ -118,3 +118,30 @@ def test_covered_masks_match_oracle(orc):
         sl = tuple(slice(a["level_lo"][lev][d], a["level_lo"][lev][d] + n) for d in (2, 1, 0))
         assert np.array_equal(got[lev], (M.inside[lev] & ~M.masks[lev])[sl])
         assert np.array_equal(got[lev], a["covered"][lev])
+
+
+def _header_struct(name):
+    """(type, field) pairs of `typedef struct { ... } name;` in include/gmg.h, in order"""
+    src = open(os.path.join(ROOT, "include", "gmg.h")).read()
+    end = src.index("} " + name + ";")
+    start = src.rindex("typedef struct {", 0, end)
+    body = re.sub(r"/\*.*?\*/", "", src[start:end], flags=re.S)
+    return re.findall(r"\b(int|double|int64_t)\s+([a-z_0-9]+)(?:\[[0-9A-Z_]+\])?\s*;", body)
+
+
+def test_params_struct_matches_header():
+    """The Python mirror of gmg_params has the header's fields, in order and of the same C
+    types (the struct crosses the ABI by pointer)."""
+    want = _header_struct("gmg_params")
+    ct = {"int": C.c_int, "double": C.c_double, "int64_t": C.c_int64}
+    got = [(n, t) for n, t in gmg.Params._fields_]
+    assert [n for n, _ in got] == [n for _, n in want]
+    assert all(t == ct[w] for (_, t), (w, _) in zip(got, want))
+    p = gmg.default_params()
+    assert p.settled_zero == 1 and p.use_graph == 1 and p.nu1 == 2 and p.nu2 == 2
+
+
+def test_solve_info_struct_matches_header():
+    want = [n for _, n in _header_struct("gmg_solve_info")]
+    assert [n for n, _ in gmg.SolveInfo._fields_] == want
+    assert C.sizeof(gmg.SolveInfo) >= 8 * 256
