@@ -126,14 +126,14 @@ def _header_struct(name):
     end = src.index("} " + name + ";")
     start = src.rindex("typedef struct {", 0, end)
     body = re.sub(r"/\*.*?\*/", "", src[start:end], flags=re.S)
-    return re.findall(r"\b(int|double|int64_t)\s+([a-z_0-9]+)(?:\[[0-9A-Z_]+\])?\s*;", body)
+    return re.findall(r"\b(long long|int|double|int64_t)\s+([a-z_0-9]+)(?:\[[0-9A-Z_]+\])?\s*;", body)
 
 
 def test_params_struct_matches_header():
     """The Python mirror of gmg_params has the header's fields, in order and of the same C
     types (the struct crosses the ABI by pointer)."""
     want = _header_struct("gmg_params")
-    ct = {"int": C.c_int, "double": C.c_double, "int64_t": C.c_int64}
+    ct = {"int": C.c_int, "double": C.c_double, "int64_t": C.c_int64, "long long": C.c_longlong}
     got = [(n, t) for n, t in gmg.Params._fields_]
     assert [n for n, _ in got] == [n for _, n in want]
     assert all(t == ct[w] for (_, t), (w, _) in zip(got, want))
