@@ -102,15 +102,20 @@ typedef struct {
                            launches; only the bottom solve's dot products add in another
                            order); 0: one grid launch per step on every level; 2 (default):
                            the gmg_autotune choice, 1 before tuning */
-  int fused_sweep;      /* 1: in the float and bfloat16 V-cycles, on levels with at least
-                           2^20 smoothed cells, each red-black sweep stages the planes of a
-                           box region in shared memory with TMA bulk copies and updates the
-                           red cells and the region's inner black cells in one pass; the
-                           regions' boundary black cells follow after the red ghost
-                           exchange.  Updates and results are bitwise those of the two
-                           half-sweeps.  0 (default): one pass per colour, measured faster
-                           on GB300 (the fix-up pass costs more than the halved traffic
-                           saves).  FP64 sweeps always use one pass per colour. */
+  int fused_sweep;      /* 1 or 2: on MG levels of at least 2^17 smoothed cells whose ghosts are
+                           pushed, the colour passes of each smoothing step (up to 4, e.g.
+                           black, red, black after the residual's red half-sweep) run as ONE
+                           dataflow launch: items of ~128 cells (box, plane, rows) of every
+                           pass are handed out to warps in an order where an item starts once
+                           the previous pass has finished on the z-slabs it reads, so the
+                           second colour's reads can come from L2.  Every value is computed
+                           from the operands of the two-pass sweep: results are bitwise those
+                           of fused_sweep = 0.  0 (default): one launch per colour -- measured
+                           faster on GB300 (abec256 level 0: 165 us per colour pass in FP64,
+                           115 in float, against ~270 for the dataflow launch, whose per-item
+                           GPU-scope release/acquire dominates).  A dependency wait that gives up
+                           (it cannot in a correct build) makes the call return
+                           GMG_ERR_DEVICE_TIMEOUT. */
   int ghost_push;       /* 1: in the V-cycle the smoother and the interpolation write every
                            new value also into the ghost cells that copy it, so the ghost
                            exchanges before each colour and before the restriction are not
@@ -160,6 +165,13 @@ typedef struct {
                            such a cell reads only the other colour, unchanged since the update
                            made its residual zero up to rounding.  0: every residual is
                            computed.  Results differ by rounding. */
+  int flow_warps;       /* resident warps per SM of the dataflow sweep launches (each warp
+                           takes one work item at a time); 0 (default): 32.  Same results. */
+  int flow_lag_kcells;  /* dataflow sweeps: in the hand-out order, the items of colour pass
+                           c trail those of pass c - 1 they depend on by this many x 1024
+                           cells of the level (more lag: fewer waits, more data between the
+                           passes that L2 must hold); 0 (default): 1024 (2^20 cells).  Same
+                           results. */
 } gmg_params;
 
 typedef struct {
@@ -177,6 +189,8 @@ typedef struct {
   int smooth0_launches;  /* ... and their number */
   double resid0_ms;      /* with profile: summed device time of the outer FP64 residual launches */
   int resid0_launches;
+  int smooth0_passes;    /* colour passes (red or black half-sweeps) covered by the timed
+                            smoother launches (a dataflow launch covers several) */
 } gmg_solve_info;
 
 /* ---------------------------------------------------------------- context */

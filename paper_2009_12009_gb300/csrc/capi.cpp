@@ -138,19 +138,21 @@ struct gmg_ctx {
     cudaGraphExec_t exec;
     int64_t launches;
     int n_ev_smooth, n_ev_resid;  // profiling event pairs recorded per replay
+    std::vector<int> passes;      // colour passes of each smoother event pair
   };
   std::map<
       std::tuple<void*, const void*, int, int, int, int, double, int, int, int, int, int, int, int, int, int, int, int>,
       GraphEntry>
       graphs;
   // preconditioner V-cycles of the top-level Krylov solvers, per (input, output, params)
-  std::map<std::tuple<const void*, void*, int, int, int, int, double, int, int, int, int, int, int, int>, GraphEntry>
+  std::map<std::tuple<const void*, void*, int, int, int, int, double, int, int, int, int, int, int, int, int>, GraphEntry>
       kgraphs;
 
   // profiling events (pairs around finest-level smoother / outer residual launches)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_smooth, ev_resid;
   int n_ev_smooth = 0, n_ev_resid = 0;
+  std::vector<int> ev_smooth_passes;  // colour passes covered by each smoother event pair
 
   // cell beta of level 0 as last set (ghosts filled), for beta gradients
   double* betac_cell = nullptr;
@@ -161,6 +163,9 @@ struct gmg_ctx {
   int tail_choice[NDT] = {-1, -1, -1};
   std::vector<double> tune_ms_push[NDT], tune_ms_pull[NDT];
   double tune_ms_tail[NDT][2] = {{0, 0}, {0, 0}, {0, 0}};
+
+  // per MG level: the vc_flow_skip table on the device (the V-cycle's view of the flow sweep)
+  std::vector<const int*> vc_flow_skip;
 
   // coarse ends of the problems' V-cycles, one thread block each (tail.cu)
   TailHost tail;
@@ -262,6 +267,7 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
   }
   int* active = (int*)cv.take(4 * ns);
   int maxchunks = 1;
+  std::vector<const int*> vc_skip(n, nullptr);
   for (int m = 0; m < n; ++m) {
     const LevelMeta& M = c->L[m];
     const size_t ne = (size_t)M.nelem;
@@ -302,11 +308,18 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.n_vc_coarse_chunks = (int)M.vc_coarse_chunks.size();
     D.vc_bot_descs = (const BotDesc*)cv.take(sizeof(BotDesc) * M.vc_bot_descs.size());
     D.n_vc_bot = (int)M.vc_bot_descs.size();
-    D.sweep_regions = (const SweepRegion*)cv.take(sizeof(SweepRegion) * M.sweep_regions.size());
-    D.n_sweep_regions = (int)M.sweep_regions.size();
-    D.vc_sweep_regions = (const SweepRegion*)cv.take(sizeof(SweepRegion) * M.vc_sweep_regions.size());
-    D.n_vc_sweep_regions = (int)M.vc_sweep_regions.size();
-    D.sweep_cap = M.sweep_cap;
+    D.flow_items = (const FlowItem*)cv.take(sizeof(FlowItem) * M.flow_items.size());
+    D.flow_slabs = (const FlowSlab*)cv.take(sizeof(FlowSlab) * M.flow_slabs.size());
+    D.n_flow_slabs = (int)M.flow_slabs.size();
+    for (int q = 0; q < FLOW_MAX_PHASES; ++q) {
+      D.flow_order[q] = (const FlowChunk*)cv.take(sizeof(FlowChunk) * M.flow_order[q].size());
+      D.n_flow_order[q] = (int)M.flow_order[q].size();
+    }
+    D.flow_cnt = M.flow_slabs.empty()
+                     ? nullptr
+                     : (int*)cv.take(sizeof(int) * FLOW_CNT_STRIDE *
+                                     (FLOW_QUEUES + 1 + FLOW_MAX_PHASES * M.flow_slabs.size()));
+    vc_skip[m] = (const int*)cv.take(sizeof(int) * M.vc_flow_skip.size());
     D.push_faces = (const PushFace*)cv.take(sizeof(PushFace) * M.push_faces.size());
     D.push_ok = M.push_ok ? 1 : 0;
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
@@ -335,6 +348,7 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
       c->buf[m] = B;
     }
   }
+  if (fill) c->vc_flow_skip = vc_skip;
   const size_t ne0 = c->L.empty() ? 0 : (size_t)c->L[0].nelem;
   double* alpha0 = (double*)cv.take(8 * ne0);
   double* bx0 = (double*)cv.take(8 * ne0);
@@ -492,8 +506,15 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.vc_quad_chunks, M.vc_quad_chunks))) return st;
     if ((st = upload(c, D.vc_coarse_chunks, M.vc_coarse_chunks))) return st;
     if ((st = upload(c, D.vc_bot_descs, M.vc_bot_descs))) return st;
-    if ((st = upload(c, D.sweep_regions, M.sweep_regions))) return st;
-    if ((st = upload(c, D.vc_sweep_regions, M.vc_sweep_regions))) return st;
+    if ((st = upload(c, D.flow_items, M.flow_items))) return st;
+    if ((st = upload(c, D.flow_slabs, M.flow_slabs))) return st;
+    for (int q = 0; q < FLOW_MAX_PHASES; ++q)
+      if ((st = upload(c, D.flow_order[q], M.flow_order[q]))) return st;
+    if (D.flow_cnt)
+      CK(c, cudaMemsetAsync(D.flow_cnt, 0,
+                            sizeof(int) * FLOW_CNT_STRIDE * (FLOW_QUEUES + 1 + FLOW_MAX_PHASES * M.flow_slabs.size()),
+                            c->stream));
+    if ((st = upload(c, c->vc_flow_skip[m], M.vc_flow_skip))) return st;
     if ((st = upload(c, D.push_faces, M.push_faces))) return st;
   }
   {
@@ -658,11 +679,13 @@ void record_timing_event(gmg_ctx* c, cudaEvent_t e, cudaStream_t s) {
   else cudaEventRecord(e, s);
 }
 
-// ghost push on level m: 1 always (where the level allows it), 2 the tuned choice (before
-// tuning: levels below 2^22 cells, whose ghost exchanges are launch-latency bound)
+// ghost push on level m: 1 always (where the level allows it), 2 on levels that run the
+// dataflow sweep, elsewhere the tuned choice (before tuning: levels below 2^22 cells, whose
+// ghost exchanges are launch-latency bound)
 bool push_on(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
   if (p.ghost_push == 0) return false;
   if (p.ghost_push == 1) return true;
+  if (p.fused_sweep != 0 && flow_ok(c->dev[m])) return true;  // the dataflow sweep needs pushed ghosts
   const auto& ch = c->push_choice[dt];
   if (m < (int)ch.size() && ch[m] >= 0) return (ch[m] & 1) != 0;
   return c->L[m].ncells < (1 << 22);
@@ -682,6 +705,21 @@ bool tail_on(const gmg_ctx* c, const gmg_params& p, int dt) {
   return p.fused_coarse == 1;
 }
 
+// whether the sweeps of level m run as dataflow launches (flow.cu): fused_sweep 1 or 2 on
+// levels with flow tables whose ghosts are pushed (default 0: one launch per colour)
+bool flow_on(const gmg_ctx* c, const gmg_params& p, const LevelDev& D, bool push) {
+  (void)c;
+  return p.fused_sweep != 0 && push && flow_ok(D);
+}
+
+// a profiling event pair around a finest-level smoother launch covering `passes` colour passes
+cudaEvent_t* smooth_event(gmg_ctx* c, int passes) {
+  const int k = c->n_ev_smooth++;
+  if ((int)c->ev_smooth_passes.size() <= k) c->ev_smooth_passes.resize(k + 1, 0);
+  c->ev_smooth_passes[k] = passes;
+  return ev_pair(c->ev_smooth, k);
+}
+
 // push: the smoother writes its new values into the ghost cells that copy them, so no
 // ghost exchange precedes a colour (the ghosts are kept current since e was cleared)
 void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cudaStream_t s, bool fill = true,
@@ -689,45 +727,51 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
   const LevelBufs& B = c->buf[m];
   if (fill && !push) launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
   const bool prof = c->profiling && m == 0;
-  cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
+  cudaEvent_t* ev = prof ? smooth_event(c, 1) : nullptr;
   if (prof) record_timing_event(c, ev[0], s);
   launch_smooth(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s, push, vec);
   if (prof) record_timing_event(c, ev[1], s);
 }
 
-// nsweep red-black sweeps on level m.  Levels with sweep regions (and fused_sweep set) run
-// each sweep as: black ghosts, fused region pass, red ghosts, fix-up of the regions'
-// boundary black cells -- the same updates as red pass + black pass, in one pass over the
-// coefficients.
+// nsweep red-black sweeps on level m.
 // e_zero: e is zero including its ghosts (just cleared), so the first ghost fill would
 // copy zeros and is skipped.
 // red_done: the first red half-sweep was done by the residual kernel (level 0)
-// reverse: black before red in every sweep (post-smoothing of the symmetric V-cycle; the
-// fused sweep, red first by construction, is not used then)
+// reverse: black before red in every sweep (post-smoothing of the symmetric V-cycle)
 // phi_last (finest level, red-first order): the last (black) pass also adds e to phi
 // (k_smooth_update), pushing phi's new values into its ghosts if push_phi
+// On levels with flow tables and pushed ghosts (fused_sweep != 0) the colour passes run
+// as dataflow launches of up to FLOW_MAX_PHASES passes each, with the same values.
 void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s,
                    bool e_zero = false, bool push = false, bool red_done = false, bool reverse = false,
                    double* phi_last = nullptr, bool push_phi = false) {
+  if (nsweep <= 0) return;
+  if (flow_on(c, p, D, push)) {
+    int first = reverse ? 1 : 0;
+    int n = 2 * nsweep;
+    if (red_done && !reverse) {
+      first = 1;
+      --n;
+    }
+    const LevelBufs& B = c->buf[m];
+    const Coefs k = coefs_of(c, m, dt);
+    for (int done = 0; done < n;) {
+      const int np = std::min(FLOW_MAX_PHASES, n - done);
+      const bool last = done + np == n;
+      const bool prof = c->profiling && m == 0;
+      cudaEvent_t* ev = prof ? smooth_event(c, np) : nullptr;
+      if (prof) record_timing_event(c, ev[0], s);
+      launch_flow(dt, D, B.e[dt], B.r[dt], k, (first + done) & 1, np, last && !reverse ? phi_last : nullptr,
+                  push_phi, c->dev_err, s, p.flow_warps);
+      if (prof) record_timing_event(c, ev[1], s);
+      done += np;
+    }
+    return;
+  }
   if (reverse) {
     for (int it = 0; it < nsweep; ++it) {
       smooth_colour(c, D, dt, m, 1, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
       smooth_colour(c, D, dt, m, 0, s, true, push, vec_on(c, p, dt, m));
-    }
-    return;
-  }
-  if (p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0) {
-    const LevelBufs& B = c->buf[m];
-    const Coefs k = coefs_of(c, m, dt);
-    for (int it = 0; it < nsweep; ++it) {
-      if (!(e_zero && it == 0)) launch_fill(dt, D, B.e[dt], 1, 0, s);
-      const bool prof = c->profiling && m == 0;
-      cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
-      if (prof) record_timing_event(c, ev[0], s);
-      launch_sweep(dt, D, B.e[dt], B.r[dt], k, c->dev_err, s);
-      if (prof) record_timing_event(c, ev[1], s);
-      launch_fill(dt, D, B.e[dt], 0, 0, s);
-      launch_sweep_fixup(dt, D, B.e[dt], B.r[dt], k, s);
     }
     return;
   }
@@ -737,7 +781,7 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
       const LevelBufs& B = c->buf[m];
       if (!push) launch_fill(dt, D, B.e[dt], 0, 0, s);
       const bool prof = c->profiling && m == 0;
-      cudaEvent_t* ev = prof ? ev_pair(c->ev_smooth, c->n_ev_smooth++) : nullptr;
+      cudaEvent_t* ev = prof ? smooth_event(c, 1) : nullptr;
       if (prof) record_timing_event(c, ev[0], s);
       launch_smooth_update(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, phi_last, push_phi, s);
       if (prof) record_timing_event(c, ev[1], s);
@@ -746,6 +790,9 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
     }
   }
 }
+
+// the graph-cache value of the sweep choices: fused_sweep and the flow launch width
+int sweep_key(const gmg_params& p) { return p.fused_sweep + 4 * p.flow_warps; }
 
 // the symmetric V-cycle: post-smoothing black before red (asked for, or implied by the
 // conjugate-gradient top level)
@@ -767,8 +814,7 @@ LevelDev vc_view(const gmg_ctx* c, int m) {
   D.n_coarse_chunks = D.n_vc_coarse_chunks;
   D.bot_descs = D.vc_bot_descs;
   D.n_bot = D.n_vc_bot;
-  D.sweep_regions = D.vc_sweep_regions;
-  D.n_sweep_regions = D.n_vc_sweep_regions;
+  if (m < (int)c->vc_flow_skip.size()) D.flow_skip = c->vc_flow_skip[m];
   return D;
 }
 
@@ -837,8 +883,7 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   if (m + 1 >= nlev(c) || D.n_pair_chunks == 0) return;
   // ghost push (every value written also lands in the ghosts that copy it) on levels whose
   // ghosts share their source's colour, when the sweep is the two-pass one
-  const bool push =
-      push_on(c, p, dt, m) && D.push_ok && !(p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0);
+  const bool push = push_on(c, p, dt, m) && D.push_ok;
   smooth_sweeps(c, D, dt, m, p.nu1, p, s, !red_done, push, red_done);
   if (p.nu1 > 0 && !push) launch_fill(dt, D, B.e[dt], -1, 0, s);  // (nu1 = 0: e and its ghosts are still zero)
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
@@ -855,8 +900,7 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
 // whether level 0's V-cycle pushes ghosts (then that red half-sweep pushes too).
 bool resid_red(const gmg_ctx* c, const gmg_params& p, int dt) {
   const LevelDev& D = c->dev[0];
-  return p.fuse_residual_sweep != 0 && p.nu1 > 0 && nlev(c) > 1 && D.n_pair_chunks > 0 &&
-         !(p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0);
+  return p.fuse_residual_sweep != 0 && p.nu1 > 0 && nlev(c) > 1 && D.n_pair_chunks > 0;
 }
 bool level0_push(const gmg_ctx* c, const gmg_params& p, int dt) {
   return push_on(c, p, dt, 0) && c->dev[0].push_ok;
@@ -867,7 +911,7 @@ bool level0_push(const gmg_ctx* c, const gmg_params& p, int dt) {
 bool fuse_correction_on(const gmg_ctx* c, const gmg_params& p, int dt) {
   const LevelDev& D = c->dev[0];
   return p.fuse_correction != 0 && p.nu2 > 0 && !post_reversed(p) && nlev(c) > 1 && D.n_pair_chunks > 0 &&
-         D.n_pair_chunks == D.n_pair_all_chunks && !(p.fused_sweep && dt != DT_F64 && D.n_sweep_regions > 0);
+         D.n_pair_chunks == D.n_pair_all_chunks;
 }
 
 // The colour whose residual vanishes away from walls after an outer iteration (-1: none):
@@ -922,6 +966,17 @@ double bits_to_double(unsigned long long b) {
   return d;
 }
 
+// Read and clear the device error flag (raised by a flow-sweep dependency wait that gave up);
+// synchronises s.  GMG_ERR_DEVICE_TIMEOUT if it was raised.
+gmg_status take_dev_err(gmg_ctx* c, cudaStream_t s) {
+  int flag = 0;
+  CK(c, cudaMemcpyAsync(&flag, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  if (!flag) return GMG_OK;
+  CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), s));
+  SETERR(c, GMG_ERR_DEVICE_TIMEOUT, "a bounded device wait gave up (flow sweep dependency)");
+}
+
 int dt_of_precision(int prec) { return prec == GMG_MIXED_FP32 ? DT_F32 : (prec == GMG_MIXED_BF16 ? DT_BF16 : DT_F64); }
 
 gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
@@ -929,7 +984,9 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
     SETERR(c, GMG_ERR_BAD_INPUT, "invalid parameters");
   if (p.precision < GMG_FP64 || p.precision > GMG_MIXED_BF16) SETERR(c, GMG_ERR_BAD_INPUT, "invalid precision");
   if (p.fused_coarse < 0 || p.fused_coarse > 2) SETERR(c, GMG_ERR_BAD_INPUT, "fused_coarse must be 0, 1 or 2");
-  if (p.fused_sweep != 0 && p.fused_sweep != 1) SETERR(c, GMG_ERR_BAD_INPUT, "fused_sweep must be 0 or 1");
+  if (p.fused_sweep < 0 || p.fused_sweep > 2) SETERR(c, GMG_ERR_BAD_INPUT, "fused_sweep must be 0, 1 or 2");
+  if (p.flow_warps < 0 || p.flow_warps > 64) SETERR(c, GMG_ERR_BAD_INPUT, "flow_warps must be in [0, 64]");
+  if (p.flow_lag_kcells < 0) SETERR(c, GMG_ERR_BAD_INPUT, "flow_lag_kcells must be >= 0");
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
@@ -942,6 +999,27 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
     SETERR(c, GMG_ERR_BAD_INPUT, "fuse_correction must be 0 or 1");
   if (p.settled_zero != 0 && p.settled_zero != 1) SETERR(c, GMG_ERR_BAD_INPUT, "settled_zero must be 0 or 1");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
+  return GMG_OK;
+}
+
+// Dispense orders of the flow sweeps for the lag the parameters ask for (flow_lag_kcells x
+// 1024 cells; 0: FLOW_LAG_CELLS): rebuilt and uploaded (same sizes) when it changes.  Not
+// during stream capture: called by the entry points before they launch anything.
+gmg_status ensure_flow_lag(gmg_ctx* c, const gmg_params& p) {
+  const int64_t lag = p.flow_lag_kcells > 0 ? 1024 * (int64_t)p.flow_lag_kcells : (int64_t)FLOW_LAG_CELLS;
+  bool any = false;
+  for (int m = 0; m < nlev(c); ++m) {
+    LevelMeta& M = c->L[m];
+    if (M.flow_slabs.empty() || M.flow_lag == lag) continue;
+    build_flow_order(M, lag);
+    const LevelDev& D = c->dev[m];
+    for (int q = 0; q < FLOW_MAX_PHASES; ++q) {
+      gmg_status st = upload(c, D.flow_order[q], M.flow_order[q]);
+      if (st) return st;
+    }
+    any = true;
+  }
+  if (any) CK(c, cudaStreamSynchronize(c->stream));
   return GMG_OK;
 }
 
@@ -1028,10 +1106,10 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
     ev_pair(c->ev_resid, 0);
   }
   double sm_ms = 0.0, rs_ms = 0.0;
-  int sm_n = 0, rs_n = 0;
+  int sm_n = 0, rs_n = 0, sm_passes = 0;
   if (p.use_graph && nlive) {
     auto key = std::make_tuple((void*)phi, (const void*)rhs, p.precision, p.nu1, p.nu2, p.bottom_max_iter,
-                               p.bottom_tol, p.profile, p.fused_coarse, p.fused_sweep, p.ghost_push,
+                               p.bottom_tol, p.profile, p.fused_coarse, sweep_key(p), p.ghost_push,
                                p.vector_smooth, p.pdl, p.fuse_residual_sweep, p.bottom_solver,
                                p.post_reverse, p.fuse_correction, p.settled_zero);
     auto itg = c->graphs.find(key);
@@ -1040,6 +1118,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
       per_iter = itg->second.launches;
       c->n_ev_smooth = itg->second.n_ev_smooth;
       c->n_ev_resid = itg->second.n_ev_resid;
+      c->ev_smooth_passes = itg->second.passes;
     } else {
       cudaGraph_t g;
       const int64_t l0 = kernel_launch_count();
@@ -1053,7 +1132,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
       if (e2 != cudaSuccess) SETERR(c, GMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
       per_iter = kernel_launch_count() - l0;
       count_launches((int)-per_iter);  // captured, not launched
-      c->graphs[key] = {gexec, per_iter, c->n_ev_smooth, c->n_ev_resid};
+      c->graphs[key] = {gexec, per_iter, c->n_ev_smooth, c->n_ev_resid, c->ev_smooth_passes};
     }
   }
   int64_t launched = 0;
@@ -1072,6 +1151,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
     if (c->profiling) {
       sm_ms += pair_ms(c->ev_smooth, c->n_ev_smooth);
       sm_n += c->n_ev_smooth;
+      for (int k = 0; k < c->n_ev_smooth && k < (int)c->ev_smooth_passes.size(); ++k) sm_passes += c->ev_smooth_passes[k];
       rs_ms += pair_ms(c->ev_resid, c->n_ev_resid);
       rs_n += c->n_ev_resid;
     }
@@ -1112,7 +1192,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
   gmg_status worst = GMG_OK;
   for (int q = 0; q < ns; ++q)
     if (status[q] != GMG_OK && (worst == GMG_OK || status[q] == GMG_ERR_DIVERGED)) worst = (gmg_status)status[q];
-  if (c->h_iters[ns]) {  // a staging wait in a fused sweep gave up: results are not trustworthy
+  if (c->h_iters[ns]) {  // a dependency wait of a flow sweep gave up: results are not trustworthy
     CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), s));
     for (int q = 0; q < ns; ++q) status[q] = GMG_ERR_DEVICE_TIMEOUT;
     worst = GMG_ERR_DEVICE_TIMEOUT;
@@ -1134,13 +1214,14 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
       I.kernel_launches = tot;
       I.smooth0_ms = sm_ms;
       I.smooth0_launches = sm_n;
+      I.smooth0_passes = sm_passes;
       I.resid0_ms = rs_ms;
       I.resid0_launches = rs_n;
     }
   }
   if (worst == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
   if (worst == GMG_ERR_DIVERGED) c->err = "residual is not finite";
-  if (worst == GMG_ERR_DEVICE_TIMEOUT) c->err = "a bounded device wait gave up (fused sweep staging)";
+  if (worst == GMG_ERR_DEVICE_TIMEOUT) c->err = "a bounded device wait gave up (flow sweep dependency)";
   return worst;
 }
 
@@ -1389,7 +1470,7 @@ gmg_status solve_amr_n(gmg_ctx* c, double* const* phi_user, const double* const*
     // keyed by the context's own buffers (no caller pointer is captured) and the parameters
     // the iteration reads
     auto key = std::make_tuple((void*)phi[0], (const void*)rhs[0], L, p.nu1, p.nu2, p.bottom_max_iter, p.bottom_tol,
-                               0, p.fused_coarse, 0, p.ghost_push, p.vector_smooth, p.pdl, 0, p.bottom_solver,
+                               0, p.fused_coarse, sweep_key(p), p.ghost_push, p.vector_smooth, p.pdl, 0, p.bottom_solver,
                                p.post_reverse, 0, p.settled_zero);
     auto itg = c->graphs.find(key);
     if (itg != c->graphs.end()) {
@@ -1449,6 +1530,10 @@ gmg_status solve_amr_n(gmg_ctx* c, double* const* phi_user, const double* const*
     info->kernel_launches = kernel_launch_count() - l0;
   }
   if (result == GMG_ERR_NOT_CONVERGED) c->err = "not converged within max_iter";
+  if (gmg_status e = take_dev_err(c, s)) {
+    if (info) info->status = e;
+    return e;
+  }
   return result;
 }
 
@@ -1625,7 +1710,8 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
       return GMG_OK;
     }
     auto key = std::make_tuple((void*)mid[0], (const void*)in[0], L, p.nu1, p.nu2, p.bottom_max_iter, p.bottom_tol, 1,
-                               p.fused_coarse, 1, p.ghost_push, p.vector_smooth, p.pdl, 1, p.bottom_solver,
+                               p.fused_coarse, 1 + 256 * sweep_key(p), p.ghost_push, p.vector_smooth, p.pdl, 1,
+                               p.bottom_solver,
                                p.post_reverse, 1, p.settled_zero);
     auto itg = c->graphs.find(key);
     if (itg == c->graphs.end()) {
@@ -1707,6 +1793,10 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
     info->kernel_launches = kernel_launch_count() - l0;
   }
   if (result == GMG_ERR_NOT_CONVERGED) c->err = "adjoint solve not converged within max_iter";
+  if (gmg_status e = take_dev_err(c, s)) {
+    if (info) info->status = e;
+    return e;
+  }
   return result;
 }
 
@@ -1839,7 +1929,7 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
     }
     auto key = std::make_tuple((const void*)in, (void*)out, p.precision, p.nu1, p.nu2, p.bottom_max_iter, p.bottom_tol,
                                p.fused_coarse, p.ghost_push, p.vector_smooth, p.bottom_solver, post_reversed(p) ? 1 : 0,
-                               p.pdl, p.settled_zero);
+                               p.pdl, p.settled_zero, sweep_key(p));
     auto itg = c->kgraphs.find(key);
     if (itg == c->kgraphs.end()) {
       cudaGraph_t g;
@@ -1962,7 +2052,7 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
   if (sing) project(x);
   CK(c, cudaMemcpyAsync(c->h_iters, c->bot_iters, 4 * 2, cudaMemcpyDeviceToHost, s));
   if ((st = host_sync())) return st;
-  if (c->h_iters[1]) {  // a staging wait in a fused sweep gave up
+  if (c->h_iters[1]) {  // a dependency wait of a flow sweep gave up
     CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), s));
     result = GMG_ERR_DEVICE_TIMEOUT;
   }
@@ -2058,6 +2148,8 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->profile = 0;
   p->fused_coarse = 2;
   p->fused_sweep = 0;
+  p->flow_warps = 0;
+  p->flow_lag_kcells = 0;
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;
@@ -2595,6 +2687,7 @@ gmg_status gmg_autotune(gmg_ctx* c, int precision, const void* rhs, const gmg_pa
   if (pp) p = *pp;
   gmg_status st;
   if ((st = params_ok(c, p))) return st;
+  if ((st = ensure_flow_lag(c, p))) return st;
   const int dt = dt_of_precision(precision);
   if ((st = check_level(c, 0, dt))) return st;
   if (!rhs) SETERR(c, GMG_ERR_BAD_INPUT, "autotune needs a level-0 right-hand side");
@@ -2680,12 +2773,13 @@ gmg_status gmg_vcycle(gmg_ctx* c, int dt, void* e, const void* r, const gmg_para
   gmg_status st = check_level(c, 0, dt);
   if (st) return st;
   if ((st = build_coefs(c))) return st;
+  if ((st = ensure_flow_lag(c, p))) return st;
   const size_t n = dt_size(dt) * (size_t)c->L[0].nelem;
   CK(c, cudaMemcpyAsync(c->buf[0].r[dt], r, n, cudaMemcpyDeviceToDevice, c->stream));
   vcycle(c, dt, 0, p, c->stream);
   CK(c, cudaGetLastError());
   CK(c, cudaMemcpyAsync(e, c->buf[0].e[dt], n, cudaMemcpyDeviceToDevice, c->stream));
-  return GMG_OK;
+  return take_dev_err(c, c->stream);
 }
 
 gmg_status gmg_apply(gmg_ctx* c, void* const* out, void* const* phi) {
@@ -2724,6 +2818,7 @@ gmg_status gmg_solve(gmg_ctx* c, void* const* phiv, const void* const* rhsv, dou
   if (st) return st;
   if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "context holds several problems: use gmg_batch_solve");
   if ((st = params_ok(c, p))) return st;
+  if ((st = ensure_flow_lag(c, p))) return st;
   if ((st = build_coefs(c))) return st;
   if (c->amr) {
     double* x[GMG_MAX_AMR_LEVELS];
@@ -2750,6 +2845,7 @@ gmg_status gmg_batch_solve(gmg_ctx* c, void* phi, const void* rhs, double tol_re
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
   if ((st = params_ok(c, p))) return st;
+  if ((st = ensure_flow_lag(c, p))) return st;
   if ((st = build_coefs(c))) return st;
   return solve_impl(c, (double*)phi, (const double*)rhs, tol_rel, tol_abs, p, infos);
 }
@@ -2782,6 +2878,7 @@ gmg_status gmg_solve_adjoint(gmg_ctx* c, void* const* lambda, const void* const*
   if (st) return st;
   if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "adjoint: single-problem contexts only");
   if ((st = params_ok(c, p))) return st;
+  if ((st = ensure_flow_lag(c, p))) return st;
   if ((st = build_coefs(c))) return st;
   if (!c->amr) {  // symmetric operator: the adjoint solve is a forward solve (mean projected)
     p.project_mean = 1;

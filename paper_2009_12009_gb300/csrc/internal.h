@@ -89,17 +89,43 @@ struct BotDesc {
   int solve;
 };
 
-// One region of a fused red-black sweep (sweep.cu): full x extent of a box, rows
-// [y0, y0 + ny) and planes [z0, z0 + nz).  The black cells on the region's boundary
-// (x faces, first/last row, first/last plane) are updated by the fix-up pass.
-struct SweepRegion {
+// Dataflow red-black sweep (flow.cu).  A smoothed level is cut, per independent problem,
+// into z-slabs of whole planes of the problem's domain (about FLOW_SLAB_CELLS cells each);
+// every box is cut into work items of its full x extent and about FLOW_ITEM_CELLS cells
+// inside one slab (one warp's work).  One launch runs
+// several colour phases (red, black, red, ...): an item of phase c may start once every item
+// of phase c - 1 in its own slab and the two slabs next to it (periodic images included) has
+// finished, which is exactly when the values it reads are those of the two-pass sweep and no
+// value it overwrites is still to be read.
+struct FlowItem {
   int box;
-  int y0, ny;
-  int z0, nz;
-  int pad;
+  int slab;      // index into the level's FlowSlab table
+  int z0, z1;    // planes [z0, z1) of the box
+  int y0, y1;    // rows [y0, y1) of the box
 };
-constexpr int SWEEP_MIN_CELLS = 1 << 20;  // levels with fewer smoothed cells keep one pass per colour
-constexpr int SWEEP_MAX_CAP = 2304;       // staged elements per plane: 4 slots x 24 B fit 220 KB
+
+struct FlowSlab {
+  int first, count;  // the slab's items: [first, first + count) of the item list
+  int dep[3];        // slabs whose previous-phase items must be complete (-1: none)
+  int solve;
+};
+
+// One entry of a dispense order: one item (box, planes, rows) of one slab in one phase.
+struct FlowChunk {
+  int phase_slab;  // phase << 24 | slab
+  int box;
+  int z0, z1, y0, y1;
+};
+
+constexpr int FLOW_MAX_PHASES = 4;          // colour phases one launch can run
+constexpr int FLOW_SLAB_CELLS = 1 << 18;    // target cells per slab (whole planes, at most 16)
+constexpr int FLOW_ITEM_CELLS = 128;        // target cells per work item (one warp: two updates per lane)
+constexpr int FLOW_LAG_CELLS = 1 << 20;     // default dispense lag of phase c behind phase c - 1
+constexpr int FLOW_MIN_CELLS = 1 << 17;     // levels with fewer smoothed cells keep one launch per colour
+constexpr int FLOW_BLOCK = 128;             // threads per block of the flow kernel (4 warps)
+constexpr int FLOW_WARPS_PER_SM = 32;       // default resident warps per SM
+constexpr int FLOW_QUEUES = 16;             // hand-out counters (chunk k is handed out by queue k % FLOW_QUEUES)
+constexpr int FLOW_CNT_STRIDE = 32;         // ints between completion counters (one 128-byte line each)
 
 // The coarse end of one problem's V-cycle run by one thread block (tail.cu): levels
 // m0..mb of that problem, mb its bottom.  Cell and ghost lists reuse BotCell / BotGhost.

@@ -53,12 +53,15 @@ struct LevelDev {
   int n_vc_coarse_chunks = 0;
   const BotDesc* vc_bot_descs = nullptr;
   int n_vc_bot = 0;
-  // fused red-black sweep regions (sweep.cu); empty: one pass per colour on this level
-  const SweepRegion* sweep_regions = nullptr;
-  int n_sweep_regions = 0;
-  const SweepRegion* vc_sweep_regions = nullptr;
-  int n_vc_sweep_regions = 0;
-  int sweep_cap = 0;  // max (rows + 2) * row stride over the regions: staged elements per plane
+  // dataflow red-black sweep (flow.cu); n_flow_slabs == 0: one launch per colour here
+  const FlowItem* flow_items = nullptr;
+  const FlowSlab* flow_slabs = nullptr;
+  int n_flow_slabs = 0;
+  const FlowChunk* flow_order[FLOW_MAX_PHASES] = {};  // per number of phases n: [n - 1]
+  int n_flow_order[FLOW_MAX_PHASES] = {};
+  int* flow_cnt = nullptr;  // (FLOW_QUEUES + 1 + FLOW_MAX_PHASES * n_flow_slabs) * FLOW_CNT_STRIDE ints,
+                            // zero between launches
+  const int* flow_skip = nullptr;  // per solve: 1 = leave its items out (null: none)
   const PushFace* push_faces = nullptr;  // 6 per box (ghost push targets)
   int push_ok = 0;                       // push_faces usable for every box of the level
 };
@@ -168,16 +171,18 @@ struct BottomArgs {
 void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Coefs& c64, const BottomArgs& a,
                    cudaStream_t s);
 
-// ---- fused red-black sweep (sweep.cu) ----
-// red cells of every region and the black cells inside each region, one pass (the black
-// ghosts of phi must hold the old black values); float and bfloat16 fields only (returns
-// false, launching nothing, otherwise).  err: device flag raised if a staging wait gave up
-bool launch_sweep(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int* err, cudaStream_t s);
-// shared memory of one sweep block for regions of at most cap staged elements per plane
-size_t sweep_smem_bytes(int dt, int cap);
-// the black cells on the regions' boundaries (the red ghosts of phi must hold the new red
-// values); launch_sweep then launch_sweep_fixup = one red and one black half-sweep
-void launch_sweep_fixup(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, cudaStream_t s);
+// ---- dataflow red-black sweeps (flow.cu) ----
+// whether level L has flow tables and pushes its ghosts (the flow kernel keeps every ghost
+// current by push; it cannot run a ghost exchange between phases)
+bool flow_ok(const LevelDev& L);
+// nphase alternating colour phases starting with colour0 (0 red, 1 black), in one launch,
+// in place on e; the same values as nphase launches of launch_smooth with push.  phi
+// non-null: the last phase also adds both cells' e to phi on every pair (launch_smooth_update),
+// pushing phi's new values into its ghosts if push_phi.  err: device flag raised if a
+// dependency wait gave up.  Returns false (nothing launched) if the level has no flow tables.
+// warps: resident warps per SM (0: the default).
+bool launch_flow(int dt, const LevelDev& L, void* e, const void* rhs, const Coefs& c, int colour0, int nphase,
+                 double* phi, bool push_phi, int* err, cudaStream_t s, int warps = 0);
 
 // ---- coarse end of the V-cycle, one block per problem (tail.cu) ----
 struct TailArgs {

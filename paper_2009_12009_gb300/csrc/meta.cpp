@@ -185,47 +185,128 @@ static void build_bottom(LevelMeta& L) {
   }
 }
 
-// Regions of the fused sweep: each box of a smoothing solve is cut into slabs of full x
-// extent, ry rows and rz planes.  A staged plane of a region holds (ry + 2) rows of the
-// box's row stride, at most SWEEP_MAX_CAP elements; rows are split evenly.  Boxes are then
-// cut in z until the level has at least two regions per SM of a 152-SM part (each block
-// loops over regions), keeping at least 8 planes per region.  Levels below SWEEP_MIN_CELLS
-// smoothed cells, or with a row too wide to stage 4 rows, get no regions.
-static void build_sweep_regions(LevelMeta& L) {
-  L.sweep_regions.clear();
-  L.sweep_cap = 0;
+// Tables of the dataflow sweep (flow.cu).  Per independent problem the level's z extent is
+// cut into slabs of whole planes (about FLOW_SLAB_CELLS cells, 1 to 16 planes); every
+// smoothed box is cut into items of its full x extent and about FLOW_ITEM_CELLS cells
+// (a range of rows of one plane, or whole planes), inside the planes it shares with one slab.  An item of phase c waits for phase
+// c - 1 in slabs s - 1, s, s + 1 (periodic in z where the problem is): a colour phase on
+// planes Q reads the other colour on planes Q - 1, Q and Q + 1 (the 7-point stencil), as the
+// previous phase left them, and overwrites values that the previous phase read there.
+static void build_flow(LevelMeta& L) {
+  L.flow_items.clear();
+  L.flow_slabs.clear();
+  for (auto& o : L.flow_order) o.clear();
+  L.vc_flow_skip.assign(L.geoms.size(), 0);
+  if (L.allow_cf || !L.push_ok) return;
+  const int nb = (int)L.boxes.size();
+  const int ns = (int)L.geoms.size();
   int64_t cells = 0;
-  for (int b = 0; b < (int)L.boxes.size(); ++b)
+  for (int b = 0; b < nb; ++b)
     if (!L.solve_bottom[L.box_solve[b]]) cells += L.boxes[b].volume();
-  if (cells < SWEEP_MIN_CELLS) return;
-  std::vector<int> ry(L.boxes.size(), 0);
-  int64_t nreg = 0;
-  for (int b = 0; b < (int)L.boxes.size(); ++b) {
-    if (L.solve_bottom[L.box_solve[b]]) continue;
-    const DevBox& D = L.dbox[b];
-    const int rmax = std::min(D.ny, SWEEP_MAX_CAP / D.sx - 2);
-    if (rmax < 4) return;
-    const int parts = (D.ny + rmax - 1) / rmax;
-    ry[b] = (D.ny + parts - 1) / parts;
-    nreg += parts;
-  }
-  const int64_t want = 2 * 152;
-  const int zcuts = nreg >= want ? 1 : (int)((want + nreg - 1) / nreg);
-  for (int b = 0; b < (int)L.boxes.size(); ++b) {
-    if (L.solve_bottom[L.box_solve[b]]) continue;
-    const DevBox& D = L.dbox[b];
-    const int rz = std::max(std::min(D.nz, 8), (D.nz + zcuts - 1) / zcuts);
-    for (int z0 = 0; z0 < D.nz; z0 += rz)
-      for (int y0 = 0; y0 < D.ny; y0 += ry[b]) {
-        SweepRegion R{};
-        R.box = b;
-        R.y0 = y0;
-        R.ny = std::min(ry[b], D.ny - y0);
-        R.z0 = z0;
-        R.nz = std::min(rz, D.nz - z0);
-        L.sweep_regions.push_back(R);
-        L.sweep_cap = std::max(L.sweep_cap, (R.ny + 2) * D.sx);
+  if (cells < FLOW_MIN_CELLS) return;
+  std::vector<FlowItem> items;
+  std::vector<FlowSlab> slabs;
+  for (int q = 0; q < ns; ++q) {
+    if (!L.solve_present[q] || L.solve_bottom[q]) continue;
+    const Box& dom = L.geoms[q].domain;
+    const int nzd = dom.n(2);
+    const int64_t area = (int64_t)dom.n(0) * dom.n(1);
+    const int planes = (int)std::max<int64_t>(1, std::min<int64_t>(16, FLOW_SLAB_CELLS / std::max<int64_t>(1, area)));
+    const int nsl = (nzd + planes - 1) / planes;
+    const int base = (int)slabs.size();
+    for (int sl = 0; sl < nsl; ++sl) {
+      FlowSlab S{};
+      S.first = (int)items.size();
+      S.solve = q;
+      const int g0 = dom.lo[2] + sl * planes, g1 = std::min(g0 + planes, dom.lo[2] + nzd);
+      for (int b = 0; b < nb; ++b) {
+        if (L.box_solve[b] != q) continue;
+        const Box& B = L.boxes[b];
+        const int z0 = std::max(g0, B.lo[2]) - B.lo[2], z1 = std::min(g1, B.hi[2] + 1) - B.lo[2];
+        if (z1 <= z0) continue;
+        const int nx = B.n(0), ny = B.n(1);
+        if (nx * ny >= FLOW_ITEM_CELLS) {  // items of one plane and a range of rows
+          const int rows = std::max(1, FLOW_ITEM_CELLS / nx);
+          for (int z = z0; z < z1; ++z)
+            for (int y0 = 0; y0 < ny; y0 += rows) items.push_back({b, base + sl, z, z + 1, y0, std::min(ny, y0 + rows)});
+        } else {  // items of whole planes
+          const int np = std::max(1, FLOW_ITEM_CELLS / (nx * ny));
+          for (int z = z0; z < z1; z += np) items.push_back({b, base + sl, z, std::min(z1, z + np), 0, ny});
+        }
       }
+      S.count = (int)items.size() - S.first;
+      int k = 0;
+      for (int d = -1; d <= 1; ++d) {
+        int t = sl + d;
+        if (t < 0 || t >= nsl) {
+          if (!L.geoms[q].periodic(2)) continue;
+          t = (t + nsl) % nsl;
+        }
+        bool dup = false;
+        for (int u = 0; u < k; ++u) dup |= S.dep[u] == base + t;
+        if (!dup) S.dep[k++] = base + t;
+      }
+      for (; k < 3; ++k) S.dep[k] = -1;
+      slabs.push_back(S);
+    }
+  }
+  if (items.empty() || slabs.size() >= (1u << 24)) return;
+  L.flow_items = items;
+  L.flow_slabs = slabs;
+  build_flow_order(L, FLOW_LAG_CELLS);
+}
+
+// The dispense order: (phase, slab) groups sorted by a position tau, in cells of the whole
+// level: tau(0, s) = the level's cells times the fraction of its problem's slabs up to and
+// including s (every problem advances at the same pace), tau(c, s) = lag + the largest
+// tau(c - 1, .) of the slabs it waits for.  Every item comes after the items it waits for.
+void build_flow_order(LevelMeta& L, int64_t lag) {
+  for (auto& o : L.flow_order) o.clear();
+  const int nsl = (int)L.flow_slabs.size();
+  if (!nsl) return;
+  L.flow_lag = lag;
+  int64_t total = 0;
+  std::vector<int> nsl_of(L.geoms.size(), 0), first_of(L.geoms.size(), -1);
+  for (int s = 0; s < nsl; ++s) {
+    const FlowSlab& S = L.flow_slabs[s];
+    if (first_of[S.solve] < 0) first_of[S.solve] = s;
+    nsl_of[S.solve]++;
+  }
+  for (const FlowItem& it : L.flow_items) {
+    const DevBox& B = L.dbox[it.box];
+    total += (int64_t)B.nx * (it.y1 - it.y0) * (it.z1 - it.z0);
+  }
+  std::vector<double> tau(nsl), prev(nsl);
+  for (int n = 1; n <= FLOW_MAX_PHASES; ++n) {
+    struct G { double t; int c, s; };
+    std::vector<G> groups;
+    for (int s = 0; s < nsl; ++s) {
+      const FlowSlab& S = L.flow_slabs[s];
+      tau[s] = (double)total * (double)(s - first_of[S.solve] + 1) / (double)nsl_of[S.solve];
+    }
+    for (int c = 0; c < n; ++c) {
+      if (c > 0) {
+        prev = tau;
+        for (int s = 0; s < nsl; ++s) {
+          double m = 0;
+          for (int u = 0; u < 3; ++u)
+            if (L.flow_slabs[s].dep[u] >= 0) m = std::max(m, prev[L.flow_slabs[s].dep[u]]);
+          tau[s] = m + (double)std::max<int64_t>(lag, 1);
+        }
+      }
+      for (int s = 0; s < nsl; ++s) groups.push_back({tau[s], c, s});
+    }
+    std::stable_sort(groups.begin(), groups.end(), [](const G& x, const G& y) {
+      return x.t != y.t ? x.t < y.t : (x.c != y.c ? x.c < y.c : x.s < y.s);
+    });
+    std::vector<FlowChunk>& o = L.flow_order[n - 1];
+    for (const G& g : groups) {
+      const FlowSlab& S = L.flow_slabs[g.s];
+      for (int i = S.first; i < S.first + S.count; ++i) {
+        const FlowItem& I = L.flow_items[i];
+        o.push_back({(g.c << 24) | g.s, I.box, I.z0, I.z1, I.y0, I.y1});
+      }
+    }
   }
 }
 
@@ -313,7 +394,7 @@ std::string finalize_level(LevelMeta& L) {
     for (int64_t s = 0; s < nc; s += BLOCK) L.coarse_chunks.push_back({b, (int)s});
   }
   build_bottom(L);
-  build_sweep_regions(L);
+  build_flow(L);
   return "";
 }
 
@@ -512,9 +593,8 @@ std::string build_tail(std::vector<LevelMeta>& L, TailHost& T) {
     M.vc_bot_descs.clear();
     for (const BotDesc& d : M.bot_descs)
       if (!in_tail(d.solve)) M.vc_bot_descs.push_back(d);
-    M.vc_sweep_regions.clear();
-    for (const SweepRegion& r : M.sweep_regions)
-      if (!in_tail(M.box_solve[r.box])) M.vc_sweep_regions.push_back(r);
+    M.vc_flow_skip.assign(M.geoms.size(), 0);
+    for (int q = 0; q < (int)M.geoms.size(); ++q) M.vc_flow_skip[q] = in_tail(q) ? 1 : 0;
   }
   return "";
 }

@@ -80,10 +80,16 @@ struct LevelMeta {
   std::vector<Chunk> vc_ghost_chunks, vc_pair_chunks, vc_coarse_chunks, vc_quad_chunks;
   std::vector<BotDesc> vc_bot_descs;
 
-  // fused red-black sweeps: regions of the boxes of solves that smooth on this level
-  // (empty when the level has fewer than SWEEP_MIN_CELLS smoothed cells)
-  std::vector<SweepRegion> sweep_regions, vc_sweep_regions;
-  int sweep_cap = 0;
+  // dataflow red-black sweep (empty when the level has fewer than FLOW_MIN_CELLS smoothed
+  // cells or its ghosts cannot be pushed): items grouped by slab, the slab table, and per
+  // number of phases n the dispense order (flow_order[n - 1]: chunks of one slab's items)
+  std::vector<FlowItem> flow_items;
+  std::vector<FlowSlab> flow_slabs;
+  std::vector<FlowChunk> flow_order[FLOW_MAX_PHASES];
+  int64_t flow_lag = 0;  // the dispense lag (cells) flow_order was built with
+  // per solve: 1 if the problem's coarse end (tail.cu) covers this level, so the V-cycle's
+  // flow launches skip its items
+  std::vector<int> vc_flow_skip;
 };
 
 // Tail tables: for every problem whose bottom level is small, the levels from the first
@@ -112,6 +118,9 @@ std::vector<Box> chop(const Box& dom, int max_grid_size);
 // Layout, ghost rectangles and work tables of a level whose boxes, box_solve, geoms and
 // solve_present/solve_bottom are set.  Returns "" or an error message.
 std::string finalize_level(LevelMeta& L);
+
+// Rebuild a level's flow dispense orders for a dispense lag of `lag` cells (same sizes).
+void build_flow_order(LevelMeta& L, int64_t lag);
 
 // Multigrid coarsening with aggregation (Sec. "Linear Solvers"), per solve:
 //  - every box of the solve has even lo, even size and size >= 4: coarsen each box;

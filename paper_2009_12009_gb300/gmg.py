@@ -43,7 +43,8 @@ class Params(C.Structure):
                 ("fused_sweep", C.c_int), ("ghost_push", C.c_int),
                 ("vector_smooth", C.c_int), ("pdl", C.c_int), ("fuse_residual_sweep", C.c_int),
                 ("krylov", C.c_int), ("bottom_solver", C.c_int), ("post_reverse", C.c_int),
-                ("fuse_correction", C.c_int), ("settled_zero", C.c_int)]
+                ("fuse_correction", C.c_int), ("settled_zero", C.c_int), ("flow_warps", C.c_int),
+                ("flow_lag_kcells", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -51,7 +52,7 @@ class SolveInfo(C.Structure):
                 ("initial_resid", C.c_double), ("final_resid", C.c_double), ("hist_len", C.c_int),
                 ("resid_hist", C.c_double * 256), ("bottom_iters", C.c_int), ("solve_ms", C.c_double),
                 ("kernel_launches", C.c_longlong), ("smooth0_ms", C.c_double), ("smooth0_launches", C.c_int),
-                ("resid0_ms", C.c_double), ("resid0_launches", C.c_int)]
+                ("resid0_ms", C.c_double), ("resid0_launches", C.c_int), ("smooth0_passes", C.c_int)]
 
     def history(self):
         return [self.resid_hist[i] for i in range(self.hist_len)]

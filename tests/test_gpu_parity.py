@@ -361,9 +361,9 @@ def _sweep_cases():
 
 @pytest.mark.parametrize("case", [0, 1, 2], ids=["abec128", "periodic128_boxes32", "uneven_large"])
 def test_fused_sweep_is_bitwise_two_half_sweeps(case):
-    """Levels of >= 2^20 cells: the fused red-black sweep (region pass + fix-up of the
-    regions' boundary black cells) gives bit for bit the V-cycle and the solve of the two
-    half-sweeps, in FP64, FP32 and BF16."""
+    """Levels of >= 2^17 cells: the dataflow sweep (every colour pass of a smoothing step in
+    one launch) gives bit for bit the V-cycle and the solve of one launch per colour, in
+    FP64, FP32 and BF16, with fewer launches."""
     cfg = _sweep_cases()[case]
     C = _ctx_of(cfg)
     r = torch.from_numpy(cfg["rhs"] - (cfg["rhs"].mean() if cfg["bc_lo"][0] == gmg.PERIODIC else 0.0))
@@ -377,7 +377,7 @@ def test_fused_sweep_is_bitwise_two_half_sweeps(case):
     a1 = C.unpack(p1).clone()
     p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=0, project_mean=1)
     assert torch.equal(a1, C.unpack(p0))
-    assert i1.kernel_launches == i0.kernel_launches
+    assert i1.kernel_launches < i0.kernel_launches
 
 
 @pytest.mark.parametrize("name", ["uneven", "periodic", "helmholtz", "poisson32", "neumann", "mixedwalls"])
