@@ -172,6 +172,11 @@ typedef struct {
                            cells of the level (more lag: fewer waits, more data between the
                            passes that L2 must hold); 0 (default): 1024 (2^20 cells).  Same
                            results. */
+  int serpentine;       /* 1 (default): the level-sweep kernels of a level (smoothers, residual,
+                           residual-restriction, interpolation) alternate the direction in
+                           which they walk the level's boxes, so each starts on the data the
+                           previous one touched last (still in L2); 0: always first box first.
+                           Same results. */
 } gmg_params;
 
 typedef struct {

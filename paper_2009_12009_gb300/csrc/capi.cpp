@@ -164,6 +164,11 @@ struct gmg_ctx {
   std::vector<double> tune_ms_push[NDT], tune_ms_pull[NDT];
   double tune_ms_tail[NDT][2] = {{0, 0}, {0, 0}, {0, 0}};
 
+  // serpentine order (gmg_params.serpentine, set per call): per MG level, the direction the
+  // last level-sweep launch took its work list in
+  bool serp = true;
+  std::vector<int> dir;
+
   // per MG level: the vc_flow_skip table on the device (the V-cycle's view of the flow sweep)
   std::vector<const int*> vc_flow_skip;
 
@@ -705,6 +710,19 @@ bool tail_on(const gmg_ctx* c, const gmg_params& p, int dt) {
   return p.fused_coarse == 1;
 }
 
+// Serpentine order: a copy of D whose level-sweep kernels take their work list in the
+// direction opposite to the previous such launch on level m (the first boxes they touch are
+// the last ones the previous kernel touched, still in L2).  Forward if serpentine is off.
+LevelDev dir_view(gmg_ctx* c, const LevelDev& D, int m) {
+  LevelDev V = D;
+  V.rev = 0;
+  if (!c->serp) return V;
+  if ((int)c->dir.size() <= m) c->dir.resize(m + 1, 0);
+  c->dir[m] ^= 1;
+  V.rev = c->dir[m];
+  return V;
+}
+
 // whether the sweeps of level m run as dataflow launches (flow.cu): fused_sweep 1 or 2 on
 // levels with flow tables whose ghosts are pushed (default 0: one launch per colour)
 bool flow_on(const gmg_ctx* c, const gmg_params& p, const LevelDev& D, bool push) {
@@ -729,7 +747,7 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
   const bool prof = c->profiling && m == 0;
   cudaEvent_t* ev = prof ? smooth_event(c, 1) : nullptr;
   if (prof) record_timing_event(c, ev[0], s);
-  launch_smooth(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s, push, vec);
+  launch_smooth(dt, dir_view(c, D, m), B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s, push, vec);
   if (prof) record_timing_event(c, ev[1], s);
 }
 
@@ -783,7 +801,7 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
       const bool prof = c->profiling && m == 0;
       cudaEvent_t* ev = prof ? smooth_event(c, 1) : nullptr;
       if (prof) record_timing_event(c, ev[0], s);
-      launch_smooth_update(dt, D, B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, phi_last, push_phi, s);
+      launch_smooth_update(dt, dir_view(c, D, m), B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, phi_last, push_phi, s);
       if (prof) record_timing_event(c, ev[1], s);
     } else {
       smooth_colour(c, D, dt, m, 1, s, true, push, vec_on(c, p, dt, m));
@@ -791,8 +809,8 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
   }
 }
 
-// the graph-cache value of the sweep choices: fused_sweep and the flow launch width
-int sweep_key(const gmg_params& p) { return p.fused_sweep + 4 * p.flow_warps; }
+// the graph-cache value of the sweep choices: fused_sweep, the flow launch width, serpentine
+int sweep_key(const gmg_params& p) { return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine; }
 
 // the symmetric V-cycle: post-smoothing black before red (asked for, or implied by the
 // conjugate-gradient top level)
@@ -869,6 +887,7 @@ void choose_pdl(const gmg_params& p, cudaStream_t s) {
 void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool red_done = false,
             double* phi_update = nullptr, bool push_phi = false) {
   choose_pdl(p, s);
+  c->serp = p.serpentine != 0;
   const bool fused = tail_on(c, p, dt) && c->tail_ok;
   const LevelDev D = fused ? vc_view(c, m) : c->dev[m];
   const LevelBufs& B = c->buf[m];
@@ -889,9 +908,10 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
   // (pre-smoothing ends with a black half-sweep: black residuals vanish away from walls)
   const bool settled = dt == DT_F64 && p.nu1 > 0 && p.settled_zero != 0 && D.push_ok;
-  launch_resid_restrict(dt, D, Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s, settled);
+  launch_resid_restrict(dt, dir_view(c, D, m), Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s,
+                        settled);
   vcycle(c, dt, m + 1, p, s, false);
-  launch_prolong_add(dt, D, Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
+  launch_prolong_add(dt, dir_view(c, D, m), Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
   smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, post_reversed(p), phi_update, push_phi);
 }
 
@@ -931,6 +951,7 @@ int outer_settled(const gmg_ctx* c, const gmg_params& p, int dt) {
 // normbits[0, ns), copied to the pinned host mirror.
 void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const gmg_params& p, cudaStream_t s) {
   const int ns = c->ns();
+  c->serp = p.serpentine != 0;
   const bool rr = resid_red(c, p, dt);
   // phi's ghosts stay current by push (they were filled, or zero, before the first update)
   const bool push = p.ghost_push != 0 && c->dev[0].push_ok;
@@ -942,7 +963,7 @@ void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const g
   cudaMemsetAsync(c->normbits, 0, 8 * (size_t)ns, s);
   cudaEvent_t* ev = c->profiling ? ev_pair(c->ev_resid, c->n_ev_resid++) : nullptr;
   if (ev) record_timing_event(c, ev[0], s);
-  launch_residual(DT_F64, dt, c->dev[0], phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits,
+  launch_residual(DT_F64, dt, dir_view(c, c->dev[0], 0), phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits,
                   any_singular(c) ? c->scal : nullptr, s, rr ? c->buf[0].e[dt] : nullptr,
                   rr ? coefs_of(c, 0, dt).invD : nullptr, rr && level0_push(c, p, dt), outer_settled(c, p, dt));
   if (ev) record_timing_event(c, ev[1], s);
@@ -987,6 +1008,7 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.fused_sweep < 0 || p.fused_sweep > 2) SETERR(c, GMG_ERR_BAD_INPUT, "fused_sweep must be 0, 1 or 2");
   if (p.flow_warps < 0 || p.flow_warps > 64) SETERR(c, GMG_ERR_BAD_INPUT, "flow_warps must be in [0, 64]");
   if (p.flow_lag_kcells < 0) SETERR(c, GMG_ERR_BAD_INPUT, "flow_lag_kcells must be >= 0");
+  if (p.serpentine != 0 && p.serpentine != 1) SETERR(c, GMG_ERR_BAD_INPUT, "serpentine must be 0 or 1");
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
@@ -2150,6 +2172,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->fused_sweep = 0;
   p->flow_warps = 0;
   p->flow_lag_kcells = 0;
+  p->serpentine = 1;
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;

@@ -91,10 +91,10 @@ __global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ box
                                                   const typename CoefOf<T>::type* __restrict__ wz,
                                                   const typename CoefOf<T>::type* __restrict__ invD, int colour,
                                                   const int* __restrict__ active,
-                                                  const PushFace* __restrict__ push) {
+                                                  const PushFace* __restrict__ push, int rev) {
   pdl_enter();
   using A = typename Arith<T>::type;
-  const Chunk ch = chunks[blockIdx.x];
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
   const DevBox B = boxes[ch.item];
   if (active && !active[B.solve]) return;
   const int t = ch.start + threadIdx.x;
@@ -128,10 +128,10 @@ __global__ void __launch_bounds__(BLOCK)
     k_smooth_update(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks, T* e, const T* __restrict__ rhs,
                     const typename CoefOf<T>::type* __restrict__ wx, const typename CoefOf<T>::type* __restrict__ wy,
                     const typename CoefOf<T>::type* __restrict__ wz, const typename CoefOf<T>::type* __restrict__ invD,
-                    int colour, const int* __restrict__ active, double* phi, const PushFace* __restrict__ push_phi) {
+                    int colour, const int* __restrict__ active, double* phi, const PushFace* __restrict__ push_phi, int rev) {
   pdl_enter();
   using A = typename Arith<T>::type;
-  const Chunk ch = chunks[blockIdx.x];
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
   const DevBox B = boxes[ch.item];
   if (active && !active[B.solve]) return;
   const int t = ch.start + threadIdx.x;
@@ -197,9 +197,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_smooth4(const DevBox* __restrict__
                                                    T* phi, const T* __restrict__ rhs, const float* __restrict__ wx,
                                                    const float* __restrict__ wy, const float* __restrict__ wz,
                                                    const float* __restrict__ invD, int colour,
-                                                   const int* __restrict__ active, const PushFace* __restrict__ push) {
+                                                   const int* __restrict__ active, const PushFace* __restrict__ push, int rev) {
   pdl_enter();
-  const Chunk ch = chunks[blockIdx.x];
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
   const DevBox B = boxes[ch.item];
   if (active && !active[B.solve]) return;
   const int nq = B.nx >> 2;
@@ -286,11 +286,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_residual(const DevBox* __restri
                                                     const typename CoefOf<T>::type* __restrict__ D, R* r,
                                                     unsigned long long* maxbits, const double* shift_p, R* e,
                                                     const typename CoefOf<R>::type* __restrict__ invDe,
-                                                    const PushFace* __restrict__ push, int settled) {
+                                                    const PushFace* __restrict__ push, int settled, int rev) {
   pdl_enter();
   using A = typename Arith<T>::type;
   using AR = typename Arith<R>::type;
-  const Chunk ch = chunks[blockIdx.x];
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
   const DevBox B = boxes[ch.item];
   const int t = ch.start + threadIdx.x;
   const A shift = shift_p ? (A)shift_p[B.solve] : (A)0;
@@ -382,10 +382,10 @@ __global__ void __launch_bounds__(BLOCK, 5)
                      const T* __restrict__ rhs, const typename CoefOf<T>::type* __restrict__ wx,
                      const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
                      const typename CoefOf<T>::type* __restrict__ D, R* rc, const int* __restrict__ active,
-                     int settled_black) {
+                     int settled_black, int rev) {
   pdl_enter();
   using A = typename Arith<T>::type;
-  const Chunk ch = chunks[blockIdx.x];
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
   const DevBox F = fboxes[ch.item];
   if (active && !active[F.solve]) return;
   const DevBox P = cboxes[parent[ch.item]];
@@ -454,10 +454,10 @@ template <class T, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB)
     k_prolong_add(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes, const int* __restrict__ parent,
                   const Chunk* __restrict__ chunks, const T* __restrict__ coarse, T* fine,
-                  const int* __restrict__ active, const PushFace* __restrict__ push) {
+                  const int* __restrict__ active, const PushFace* __restrict__ push, int rev) {
   pdl_enter();
   using A = typename Arith<T>::type;
-  const Chunk ch = chunks[blockIdx.x];
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
   const DevBox F = fboxes[ch.item];
   if (active && !active[F.solve]) return;
   const DevBox P = cboxes[parent[ch.item]];
@@ -805,7 +805,7 @@ void launch_smooth_update(int dt, const LevelDev& L, void* e, const void* rhs, c
   GMG_DISPATCH(dt, launch_pdl(k_smooth_update<T>, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks,
                               (T*)e, (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
                               (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
-                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, phi, pf));
+                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, phi, pf, L.rev));
 }
 
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour, cudaStream_t s,
@@ -818,16 +818,16 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
     const float* invD = (const float*)c.invD;
     if (dt == DT_F32)
       launch_pdl(k_smooth4<float>, grid_of(L.n_quad_chunks), BLOCK, 0, s, L.boxes, L.quad_chunks, (float*)phi,
-                 (const float*)rhs, wx, wy, wz, invD, colour, L.active, pf);
+                 (const float*)rhs, wx, wy, wz, invD, colour, L.active, pf, L.rev);
     else
       launch_pdl(k_smooth4<bf16>, grid_of(L.n_quad_chunks), BLOCK, 0, s, L.boxes, L.quad_chunks, (bf16*)phi,
-                 (const bf16*)rhs, wx, wy, wz, invD, colour, L.active, pf);
+                 (const bf16*)rhs, wx, wy, wz, invD, colour, L.active, pf, L.rev);
     return;
   }
   GMG_DISPATCH(dt, launch_pdl(k_smooth<T>, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks, (T*)phi,
                               (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
                               (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
-                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf));
+                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf, L.rev));
 }
 
 // residual work list: pair items over every box (the bottom level included)
@@ -844,7 +844,8 @@ void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const 
                               L.pair_all_chunks, (const T*)phi, (const T*)rhs,                                  \
                               (const typename CoefOf<T>::type*)c.wx, (const typename CoefOf<T>::type*)c.wy,     \
                               (const typename CoefOf<T>::type*)c.wz, (const typename CoefOf<T>::type*)c.D,      \
-                              (TR*)r, maxbits, shift, (TR*)e, (const typename CoefOf<TR>::type*)invDe, pf, settled))
+                              (TR*)r, maxbits, shift, (TR*)e, (const typename CoefOf<TR>::type*)invDe, pf, settled, \
+                              L.rev))
   switch (rdt) {
     case DT_F64: GMG_RESID(double); break;
     case DT_F32: GMG_RESID(float); break;
@@ -862,7 +863,7 @@ void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const v
                               f.parent, f.coarse_chunks, (const T*)phi, (const T*)rhs,
                               (const typename CoefOf<T>::type*)cf.wx, (const typename CoefOf<T>::type*)cf.wy,
                               (const typename CoefOf<T>::type*)cf.wz, (const typename CoefOf<T>::type*)cf.D, (T*)rc,
-                              f.active, settled_black ? 1 : 0));
+                              f.active, settled_black ? 1 : 0, f.rev));
 
 }
 
@@ -881,7 +882,7 @@ void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void
   const PushFace* pf = push ? f.push_faces : nullptr;
   GMG_DISPATCH(dt, launch_pdl(k_prolong_add<T, std::is_same<T, double>::value ? 8 : 0>, grid_of(f.n_coarse_chunks),
                               BLOCK, 0, s, f.boxes, c.boxes,
-                              f.parent, f.coarse_chunks, (const T*)coarse, (T*)fine, f.active, pf));
+                              f.parent, f.coarse_chunks, (const T*)coarse, (T*)fine, f.active, pf, f.rev));
 }
 
 void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s, bool push) {

@@ -64,6 +64,10 @@ struct LevelDev {
   const int* flow_skip = nullptr;  // per solve: 1 = leave its items out (null: none)
   const PushFace* push_faces = nullptr;  // 6 per box (ghost push targets)
   int push_ok = 0;                       // push_faces usable for every box of the level
+  // 1: the level-sweep kernels (smoothers, residual, residual-restriction, interpolation)
+  // take their work list last entry first.  Consecutive kernels on a level that alternate it
+  // start on the boxes the previous one touched last, still in L2.  Same results.
+  int rev = 0;
 };
 
 // Coefficients of one level in one element type (double for FP64 fields, float for

@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("vector_smooth", C.c_int), ("pdl", C.c_int), ("fuse_residual_sweep", C.c_int),
                 ("krylov", C.c_int), ("bottom_solver", C.c_int), ("post_reverse", C.c_int),
                 ("fuse_correction", C.c_int), ("settled_zero", C.c_int), ("flow_warps", C.c_int),
-                ("flow_lag_kcells", C.c_int)]
+                ("flow_lag_kcells", C.c_int), ("serpentine", C.c_int)]
 
 
 class SolveInfo(C.Structure):
