@@ -16,12 +16,17 @@ prolongation, BiCGStab bottom) and the outer FP64 residual loop.
   mixed  = the same solve with the float and bfloat16-storage V-cycles inside FP64
            iterative refinement (time, Mcell-updates/s, error against the FP64 solve);
   roofline: the finest-level smoother kernel (dominant), its algorithmic bytes per launch
-           over its average launch time, CUDA events recorded around each launch inside
-           the timed solves;
-  cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload.
+           (28 B per cell per colour pass: 56 B per cell per red+black sweep) over its average
+           launch time, CUDA events recorded around each launch inside the timed solves; beside
+           it, the same launches' FP64-pipe rate (7 operations per updated cell) over the FP64
+           ceiling measured in this run (fp64_peak: the library's DFMA probe);
+  cpu_baseline: the FP64 CPU oracle solving the same workload to 1e-10 on the host cores
+           (OpenMP over boxes), plus one V-cycle on one thread; rel_err_vs_oracle: every
+           precision's solution against the oracle's;
+  summary: the headline figures of every workload, last in the line.
 
 --impl reference times the oracle itself (each step: one V-cycle iteration of the
-workload on the host cores).  Multi-GPU: independent replicas (the solve does not shard
+workload, OpenMP over boxes on the host cores).  Multi-GPU: independent replicas (the solve does not shard
 in this version), weak scaling.
 """
 from __future__ import annotations
@@ -44,7 +49,12 @@ UNIT = "Mcell-updates/s"
 WORKLOAD = ("abec256: 256^3 ABecLaplacian a=0 b=1, Dirichlet walls, 64 boxes of 64^3, beta log-normal "
             "(3x3x3 mean filter, harmonic faces), rhs N(0,1) seed 12011; V(2,2) red-black GS, "
             "BiCGStab bottom at 2^3, FP64, tol 1e-10")
-SMOOTH_BYTES_PER_CELL = 56  # one colour pass: phi, rhs, 3 face weights, 1/D read, phi written (8 B each)
+# algorithmic bytes of the red-black smoother: 56 B per cell per full sweep (phi, rhs, 3 face
+# weights, 1/D read and phi written once, 8 B each), so 28 B per cell per colour pass
+SWEEP_BYTES_PER_CELL = 56
+PASS_BYTES_PER_CELL = SWEEP_BYTES_PER_CELL // 2
+# FP64-pipe operations of one Gauss-Seidel update: 6 fused multiply-adds and 1 multiply
+UPDATE_FP64_OPS = 7
 TOL = 1e-10
 
 
@@ -133,7 +143,10 @@ def kernel_traffic(kernel):
         return None
     with open(path) as f:
         rec = json.load(f)
-    h = hashlib.sha256(source_text(rec.get("sources", [])))
+    try:
+        h = hashlib.sha256(source_text(rec.get("sources", [])))
+    except (OSError, ValueError):  # a hashed definition moved or is gone: the record is stale
+        return None
     if not rec.get("sources") or h.hexdigest()[:16] != rec.get("sources_sha256_16"):
         return None
     return rec.get("dram_bytes_per_launch_full_size")
@@ -148,9 +161,10 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(cfg, iters=2):
-    """The FP64 oracle, single-threaded, on the full workload for `iters` V-cycle
-    iterations (a bounded sample of the solve)."""
+def cpu_baseline(cfg):
+    """The FP64 oracle on the host cores: the whole abec256 solve to 1e-10 with OpenMP over
+    boxes on every core this process may use (its solution is the reference of the error
+    figures), and one V-cycle iteration on one thread.  Returns (record, oracle solution)."""
     from oracle import oracle as O
 
     P = O.Problem(cfg["domain"], cfg["boxes"], cfg["bc_lo"], cfg["bc_hi"])
@@ -159,11 +173,51 @@ def cpu_baseline(cfg, iters=2):
     for m in range(P.nlevels - 1):
         nz, ny, nx = P.level_shape(m)
         cells += nx * ny * nz * 4
+    ncores = len(os.sched_getaffinity(0))
+    O.set_threads(1)
     t0 = time.perf_counter()
-    _, it, _, _ = P.solve(cfg["rhs"], tol_rel=0.0, maxit=iters)
+    _, it1, _, _ = P.solve(cfg["rhs"], tol_rel=0.0, maxit=1)
+    dt1 = time.perf_counter() - t0
+    O.set_threads(ncores)
+    t0 = time.perf_counter()
+    sol, it, _, st = P.solve(cfg["rhs"], tol_rel=TOL, maxit=100)
     dt = time.perf_counter() - t0
-    return {"value": cells * it / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{it} V-cycle iterations of the abec256 solve (FP64 oracle, 1 thread), {dt:.1f} s"}
+    O.set_threads(1)
+    rec = {"value": cells * it / dt / 1e6, "unit": UNIT, "cores": ncores, "kind": "oracle",
+           "time_to_tol_ms": 1e3 * dt, "iterations": it, "status": st,
+           "sample": f"the whole abec256 solve to 1e-10 ({it} V-cycles, FP64 oracle, OpenMP over boxes on "
+                     f"{ncores} threads), {dt:.1f} s",
+           "single_thread": {"value": cells * it1 / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                             "sample": f"{it1} V-cycle iteration of the same solve, {dt1:.1f} s"}}
+    return rec, sol
+
+
+def fp64_peak(stream, clocks_index):
+    """FP64 ceiling of this GPU: the library's DFMA probe (independent FMA chains) timed with
+    CUDA events on the bench stream, best over 4, 8 and 16 blocks of 256 threads per SM."""
+    import torch
+
+    from paper_2009_12009_gb300 import gmg
+
+    clk = ClockSampler(clocks_index)
+    clk.start()
+    time.sleep(0.2)
+    best = (0.0, 0)
+    for bps in (4, 8, 16):
+        gmg.dfma_probe(stream.cuda_stream, bps, 1 << 12)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = sum(gmg.dfma_probe(stream.cuda_stream, bps, 1 << 15) for _ in range(3))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tf = fl / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        if tf > best[0]:
+            best = (tf, bps)
+    c = clk.stop()
+    return {"tflops": best[0], "fma_per_s": best[0] * 1e12 / 2, "blocks_per_sm": best[1],
+            "how": "gmg_dfma_probe: 16 independent FP64 FMA chains per thread, 256-thread blocks, CUDA events",
+            "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")}
 
 
 def whole_job(ms_local, updates_local, world, device):
@@ -459,6 +513,39 @@ def _form_amr3(stream, barrier):
     return res
 
 
+def summary(out):
+    """The headline figures in one small record, printed last in the JSON line."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return round(d, 4) if isinstance(d, float) else d
+
+    f = out.get("forms", {})
+    return {
+        "abec256_ms": {"fp64": g(out, "time_to_tol_ms"), "fp32": g(out, "mixed", "fp32", "time_to_tol_ms"),
+                       "bf16": g(out, "mixed", "bf16", "time_to_tol_ms")},
+        "abec256_mixed_speedup": {"fp32": g(out, "mixed", "fp32", "speedup_vs_fp64"),
+                                  "bf16": g(out, "mixed", "bf16", "speedup_vs_fp64")},
+        "abec256_rel_err_vs_oracle": out.get("rel_err_vs_oracle"),
+        "abec512_ms": {k: g(f, "abec512", k, "time_to_tol_ms") for k in ("fp64", "fp32", "bf16")},
+        "abec512_mixed_speedup": {"fp32": g(f, "abec512", "mixed_speedup_fp32"),
+                                  "bf16": g(f, "abec512", "mixed_speedup_bf16")},
+        "batch64_ms": {"fp64": g(f, "batch64", "fp64", "time_to_tol_ms"),
+                       "fp32": g(f, "batch64", "fp32", "time_to_tol_ms"),
+                       "fp64_one_by_one": g(f, "batch64", "sequential_fp64", "time_to_tol_ms")},
+        "amr2_ms": {"forward": g(f, "amr2", "forward", "time_to_tol_ms"),
+                    "adjoint": g(f, "amr2", "adjoint", "time_to_tol_ms"), "beta_grad": g(f, "amr2", "beta_grad_ms")},
+        "amr3_ms": {"forward": g(f, "amr3", "forward", "time_to_tol_ms"),
+                    "adjoint": g(f, "amr3", "adjoint", "time_to_tol_ms")},
+        "smoother_frac": {"hbm_algorithmic": g(out, "roofline", "frac"),
+                          "fp64_pipe": g(out, "roofline", "fp64_pipe", "frac")},
+        "fp64_peak_tflops": g(out, "fp64_peak", "tflops"),
+        "oracle_ms": g(out, "cpu_baseline", "time_to_tol_ms"), "oracle_cores": g(out, "cpu_baseline", "cores"),
+    }
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -470,6 +557,8 @@ def run_reference(args):
     P = O.Problem(cfg["domain"], cfg["boxes"], cfg["bc_lo"], cfg["bc_hi"])
     P.set_coeffs(cfg["a"], cfg["b"], alpha=cfg["alpha"], beta=cfg["beta"])
     cells = sum(P.level_shape(m)[0] * P.level_shape(m)[1] * P.level_shape(m)[2] * 4 for m in range(P.nlevels - 1))
+    ncores = len(os.sched_getaffinity(0))
+    O.set_threads(ncores)
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -478,12 +567,12 @@ def run_reference(args):
             times.append(time.perf_counter() - t0)
     tot = sum(times)
     val = cells * len(times) / tot / 1e6
-    sample = f"each step: 1 V-cycle iteration of the abec256 solve (FP64 oracle, 1 thread)"
+    sample = f"each step: 1 V-cycle iteration of the abec256 solve (FP64 oracle, OpenMP over boxes, {ncores} threads)"
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-                      "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "cpu_baseline": {"value": val, "unit": UNIT, "cores": ncores, "kind": "oracle", "sample": sample},
                       "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -558,6 +647,7 @@ def main():
         barrier()
         return e0.elapsed_time(e1), infos
 
+    fp64pk = fp64_peak(stream, local)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -568,13 +658,19 @@ def main():
     ms, updates, value = whole_job(ms, sum(upd_per_vc * k for k in its), world, dev)
     phi64 = ctx.unpack(phi).clone()
 
-    # roofline of the dominant kernel: finest-level red-black smoother
+    # roofline of the dominant kernel: finest-level red-black smoother, one colour pass per
+    # launch; algorithmic bytes 28 B/cell per pass (56 B/cell per red+black sweep)
     sm_ms = sum(i.smooth0_ms for i in infos)
     sm_n = sum(i.smooth0_launches for i in infos)
+    sm_passes = sum(i.smooth0_passes for i in infos)
     launch_s = sm_ms * 1e-3 / max(sm_n, 1)
-    alg_bytes = SMOOTH_BYTES_PER_CELL * ncells
+    alg_bytes = PASS_BYTES_PER_CELL * ncells * sm_passes / max(sm_n, 1)
     achieved = alg_bytes / launch_s / 1e9
     peak, peak_kind = peaks()
+    # the same launches against the FP64 pipe: 7 operations per updated cell (half the
+    # cells per pass), over the probe's FMA rate
+    fp64_ops = UPDATE_FP64_OPS * (ncells / 2) * sm_passes / max(sm_n, 1)
+    fp64_rate = fp64_ops / launch_s
     rs_ms = sum(i.resid0_ms for i in infos)
     rs_n = sum(i.resid0_launches for i in infos)
 
@@ -587,11 +683,16 @@ def main():
                       "l2": "inputs larger than L2 (finest-level working set ~1.2 GB of fields and coefficients)",
                       "autotuned": {k: summarize_tuning(v) for k, v in tuned.items()}},
            "gpu_launches": int(sum(i.kernel_launches for i in infos)),
-           "roofline": {"bound": "hbm", "kernel": "k_smooth<double> (finest level, one colour)",
+           "roofline": {"bound": "hbm", "kernel": "k_smooth<double> (finest level, one colour pass)",
                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_kind": peak_kind, "traffic": kernel_traffic("k_smooth_f64"),
-                        "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": launch_s * 1e6,
-                        "launches_timed": sm_n},
+                        "algorithmic_bytes_per_launch": alg_bytes,
+                        "bytes_rule": "56 B/cell per red+black sweep = 28 B/cell per colour pass",
+                        "avg_launch_us": launch_s * 1e6, "launches_timed": sm_n, "passes_timed": sm_passes,
+                        "fp64_pipe": {"ops_per_launch": fp64_ops, "achieved_gops": fp64_rate / 1e9,
+                                      "peak_gops": fp64pk["fma_per_s"] / 1e9,
+                                      "frac": fp64_rate / fp64pk["fma_per_s"],
+                                      "peak_kind": "measured in this run (gmg_dfma_probe)"}},
            "outer_residual": {"kernel": "k_residual<double> (finest level, FP64)", "avg_launch_us":
                               1e3 * rs_ms / max(rs_n, 1), "launches_timed": rs_n},
            # per V-cycle iteration, and the finest level's share of the cell updates
@@ -599,13 +700,16 @@ def main():
            "finest_level_value": ncells * nu * sum(its) * world / (ms * 1e-3) / 1e6,
            "clocks": clk}
 
+    sols = {"fp64": phi64.cpu().numpy()}
     if not args.no_mixed:
         mixed = {}
         for name, prec in (("fp32", gmg.MIXED_FP32), ("bf16", gmg.MIXED_BF16)):
             ms_m, inf_m = timed_solves(prec, max(3, args.steps // 2), 2)
             itm = inf_m[0].iterations
             ms_m, _, val_m = whole_job(ms_m, sum(upd_per_vc * i.iterations for i in inf_m), world, dev)
-            err = float((ctx.unpack(phi) - phi64).abs().max() / phi64.abs().max())
+            sol_m = ctx.unpack(phi)
+            err = float((sol_m - phi64).abs().max() / phi64.abs().max())
+            sols[name] = sol_m.cpu().numpy()
             mixed[name] = {"time_to_tol_ms": ms_m / len(inf_m), "value": val_m, "unit": UNIT,
                            "iterations": itm, "final_rel_resid": inf_m[-1].final_resid / inf_m[-1].rhs_norm,
                            "rel_err_vs_fp64_solve": err,
@@ -641,8 +745,12 @@ def main():
         out["forms"] = measure_forms(stream, barrier, dev)
 
     if not args.no_cpu and rank == 0 and world == 1:
-        out["cpu_baseline"] = cpu_baseline(cfg)
+        out["cpu_baseline"], ref = cpu_baseline(cfg)
+        den = float(np.abs(ref).max())
+        out["rel_err_vs_oracle"] = {k: float(np.abs(v - ref).max() / den) for k, v in sols.items()}
+    out["fp64_peak"] = fp64pk
     if rank == 0:
+        out["summary"] = summary(out)
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

@@ -517,6 +517,16 @@ gmg_status gmg_box_bicgstab_noalloc(void* cuda_stream, int nx, int ny, int nz, c
                                     const double* diag, const double* rhs, double* x, int max_iter, double tol,
                                     int* iters);
 
+/* ---------------------------------------------------------------- diagnostics */
+
+/* FP64 throughput probe (no counterpart in the paper; a measurement helper for the roofline
+   of the FP64-pipe-bound kernels): enqueues on cuda_stream one kernel of SMs x blocks_per_sm
+   blocks of 256 threads, each thread running 16 independent chains of `iters` FP64 fused
+   multiply-adds, and returns in *flops the floating-point operations it performs (2 per
+   FMA).  The caller times it (events on the same stream).  Allocates nothing.
+   GMG_ERR_BAD_INPUT for blocks_per_sm outside [1, 64], iters < 1 or flops NULL. */
+gmg_status gmg_dfma_probe(void* cuda_stream, int blocks_per_sm, int iters, double* flops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,10 +9,14 @@
  * smoke check and by the benchmark's CPU-baseline leg, never by the product path.
  * It shares no code, header, table or constant with the CUDA library.
  *
- * Everything here is written for clarity, not speed: single thread, one ghosted
- * array per box (Sec. "Containers for mesh data": the FAB's array includes its
- * ghost cells), brute-force box intersections for the ghost-cell exchange, and the
- * V-cycle steps in the order the method states them.
+ * Everything here is written for clarity, not speed: one ghosted array per box (Sec.
+ * "Containers for mesh data": the FAB's array includes its ghost cells), brute-force box
+ * intersections for the ghost-cell exchange, and the V-cycle steps in the order the method
+ * states them.  By default one thread; orc_set_threads(n) lets the loops over boxes whose
+ * iterations write disjoint cells and compute each cell exactly as one thread does (colour
+ * sweeps, residuals, operator applications, restriction, interpolation, ghost copies,
+ * max-norms) run on n OpenMP threads -- the results are bitwise those of one thread.  Sums
+ * stay sequential.
  *
  * Readings of the paper used here (the paper names the components but not their
  * exact form):
@@ -96,6 +100,11 @@ typedef struct {
 } oprob;
 
 /* ------------------------------------------------------------------ layout */
+
+/* OpenMP threads of the box loops (1: sequential) */
+static int g_threads = 1;
+void orc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+int orc_get_threads(void) { return g_threads; }
 
 static int bn(const olev* l, int b, int d) { return l->hi[3 * b + d] - l->lo[3 * b + d] + 1; }
 
@@ -212,6 +221,7 @@ static void build_ghost_map(olev* l) {
 /* Sec. "Operations on a level": fill ghost cells from the owning box at the same level
    (or the physical boundary condition). */
 static void fill_ghosts(const olev* l, double* f) {
+  #pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
   for (int64_t q = 0; q < l->ng; ++q)
     if (l->gsrc[q] >= 0) f[l->gdst[q]] = l->gfac[q] * f[l->gsrc[q]];
 }
@@ -561,6 +571,7 @@ void orc_apply_level(void* vp, int m, double* phi, double* out) {
   oprob* p = (oprob*)vp;
   olev* l = &p->L[m];
   fill_ghosts(l, phi);
+  #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1)
   for (int b = 0; b < l->nb; ++b)
     for (int k = 0; k < bn(l, b, 2); ++k)
       for (int j = 0; j < bn(l, b, 1); ++j)
@@ -579,6 +590,7 @@ void orc_smooth_colour(void* vp, int m, double* phi, const double* rhs, int colo
   olev* l = &p->L[m];
   fill_ghosts(l, phi);
   double ihx2 = 1.0 / (l->h[0] * l->h[0]), ihy2 = 1.0 / (l->h[1] * l->h[1]), ihz2 = 1.0 / (l->h[2] * l->h[2]);
+  #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1)
   for (int b = 0; b < l->nb; ++b)
     for (int k = 0; k < bn(l, b, 2); ++k)
       for (int j = 0; j < bn(l, b, 1); ++j)
@@ -602,6 +614,7 @@ void orc_residual(void* vp, int m, double* phi, const double* rhs, double* r) {
   oprob* p = (oprob*)vp;
   olev* l = &p->L[m];
   fill_ghosts(l, phi);
+  #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1)
   for (int b = 0; b < l->nb; ++b)
     for (int k = 0; k < bn(l, b, 2); ++k)
       for (int j = 0; j < bn(l, b, 1); ++j)
@@ -614,6 +627,7 @@ void orc_restrict(void* vp, int m, const double* fine, double* coarse) {
   oprob* p = (oprob*)vp;
   olev* f = &p->L[m];
   olev* c = &p->L[m + 1];
+  #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1)
   for (int fb = 0; fb < f->nb; ++fb) {
     int P = f->parent[fb];
     for (int K = f->lo[3 * fb + 2] / 2; K <= (f->hi[3 * fb + 2] + 1) / 2 - 1; ++K)
@@ -635,6 +649,7 @@ void orc_prolong_add(void* vp, int m, const double* coarse, double* fine) {
   oprob* p = (oprob*)vp;
   olev* f = &p->L[m];
   olev* c = &p->L[m + 1];
+  #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1)
   for (int fb = 0; fb < f->nb; ++fb) {
     int P = f->parent[fb];
     for (int k = 0; k < bn(f, fb, 2); ++k)
@@ -659,14 +674,17 @@ static double lev_dot(const olev* l, const double* x, const double* y) {
 
 static double lev_norminf(const olev* l, const double* x) {
   double s = 0.0;
+  int nan = 0;
+  #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1) reduction(max : s) reduction(| : nan)
   for (int b = 0; b < l->nb; ++b)
     for (int k = 0; k < bn(l, b, 2); ++k)
       for (int j = 0; j < bn(l, b, 1); ++j)
         for (int i = 0; i < bn(l, b, 0); ++i) {
           double v = fabs(x[IX(l, b, i, j, k)]);
-          if (v > s || v != v) s = v;
+          if (v != v) nan = 1;
+          else if (v > s) s = v;
         }
-  return s;
+  return nan ? NAN : s;
 }
 
 static double lev_sum(const olev* l, const double* x) {
@@ -875,6 +893,7 @@ static void fill_ghosts_bc(const oprob* p, double* f) {
 static void residual_bc(oprob* p, double* phi, const double* rhs, double* r) {
   olev* l = &p->L[0];
   fill_ghosts_bc(p, phi);
+  #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1)
   for (int b = 0; b < l->nb; ++b)
     for (int k = 0; k < bn(l, b, 2); ++k)
       for (int j = 0; j < bn(l, b, 1); ++j)
@@ -890,6 +909,7 @@ void orc_apply_bc(void* vp, const double* phi_dense, double* out_dense) {
   double* out = (double*)calloc(l->ntot, sizeof(double));
   orc_dense_to_boxed(vp, 0, phi_dense, phi);
   fill_ghosts_bc(p, phi);
+  #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1)
   for (int b = 0; b < l->nb; ++b)
     for (int k = 0; k < bn(l, b, 2); ++k)
       for (int j = 0; j < bn(l, b, 1); ++j)
@@ -1027,6 +1047,7 @@ int orc_solve(void* vp, const double* rhs_dense, double* phi_dense, double tol_r
   int it = 0;
   while (!(rn <= target) && it < maxit) {
     orc_vcycle(vp, 0, e, r);
+    #pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
     for (int64_t q = 0; q < n; ++q) phi[q] += e[q];
     residual_bc(p, phi, rhs, r);
     rn = lev_norminf(l, r);

@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
            "-o", tmp] + srcs + ["-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
@@ -54,11 +54,22 @@ def lib():
     return _lib
 
 
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's box loops (1: sequential; results are bitwise the same)."""
+    lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return lib().orc_get_threads()
+
+
 _i32p = C.POINTER(C.c_int)
 _f64p = C.POINTER(C.c_double)
 
 
 def _declare(L):
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_get_threads.restype = C.c_int
     L.orc_create.restype = C.c_void_p
     L.orc_create.argtypes = [_i32p, _i32p, _i32p, _i32p, _f64p, _f64p, C.c_int, _i32p]
     L.orc_destroy.argtypes = [C.c_void_p]

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgmg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["kernels.cu", "bottom.cu", "meta.cpp", "capi.cpp", "noalloc.cu", "amr_meta.cpp", "amr_kernels.cu", "tail.cu", "flow.cu",
+SOURCES = ["kernels.cu", "bottom.cu", "meta.cpp", "capi.cpp", "noalloc.cu", "amr_meta.cpp", "amr_kernels.cu", "tail.cu", "flow.cu", "diag.cu",
            "walls.cu", "krylov.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -84,6 +84,7 @@ def _declare(L):
     vp, i32p, i64p, f64p = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_double)
     sig = {
         "gmg_default_params": [C.POINTER(Params)],
+        "gmg_dfma_probe": [vp, C.c_int, C.c_int, f64p],
         "gmg_create": [C.POINTER(C.c_void_p), vp],
         "gmg_destroy": [vp],
         "gmg_define_domain": [vp, i32p, i32p, f64p, f64p, i32p, i32p],
@@ -142,6 +143,16 @@ def _declare(L):
         f.restype = C.c_int
     L.gmg_last_error.argtypes = [vp]
     L.gmg_last_error.restype = C.c_char_p
+
+
+def dfma_probe(stream, blocks_per_sm=8, iters=1 << 15):
+    """Enqueue the FP64 throughput probe kernel on `stream` (a cudaStream_t as int); returns
+    the flops it performs (the caller times it with events on that stream)."""
+    f = C.c_double()
+    st = lib().gmg_dfma_probe(C.c_void_p(stream or 0), int(blocks_per_sm), int(iters), C.byref(f))
+    if st != OK:
+        raise GmgError(st, (lib().gmg_last_error(None) or b"").decode())
+    return f.value
 
 
 def default_params(**kw) -> Params:

@@ -543,3 +543,23 @@ def test_bicgstab_singular_bottom(orc):
     bp = b - b.mean()
     r = bp - P.to_dense(mb, P.apply_level(mb, P.to_boxed(mb, xd)))
     assert np.abs(r).max() <= 1e-4 * np.abs(bp).max()
+
+
+def test_threaded_oracle_is_bitwise_sequential():
+    """OpenMP over boxes (colour sweeps, residuals, restriction, interpolation, ghost copies,
+    max-norms) changes no operation of any cell: a threaded solve equals the sequential one
+    bit for bit, iteration count and residual history included."""
+    from oracle import oracle as O
+
+    cfg = I.abec(32, 8, 5151, name="abec32")
+    P = O.Problem(cfg["domain"], cfg["boxes"], cfg["bc_lo"], cfg["bc_hi"])
+    P.set_coeffs(0.0, 1.0, beta=cfg["beta"])
+    out = {}
+    try:
+        for th in (1, 3):
+            O.set_threads(th)
+            out[th] = P.solve(cfg["rhs"], tol_rel=1e-10, maxit=50)
+    finally:
+        O.set_threads(1)
+    assert np.array_equal(out[1][0], out[3][0])
+    assert out[1][1] == out[3][1] and list(out[1][2]) == list(out[3][2])
