@@ -32,7 +32,7 @@ EXPORTS = [
     "gmg_box_bicgstab_noalloc", "gmg_define_batch", "gmg_num_solves", "gmg_solve_boxes", "gmg_pack_solve",
     "gmg_unpack_solve", "gmg_batch_solve", "gmg_amr_level_boxes", "gmg_pack_amr", "gmg_unpack_amr",
     "gmg_apply_transpose", "gmg_solve_adjoint", "gmg_beta_grad", "gmg_autotune", "gmg_tuned",
-    "gmg_wall_values_rhs", "gmg_wall_values_grad", "gmg_beta_grad_walls",
+    "gmg_wall_values_rhs", "gmg_wall_values_grad", "gmg_beta_grad_walls", "gmg_dfma_probe",
 ]
 
 
