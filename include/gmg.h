@@ -200,13 +200,26 @@ typedef struct {
 
 /* ---------------------------------------------------------------- context */
 
+/* Default parameters of the solve (Sec. "Linear Solvers": the multigrid solver's settings --
+   2 + 2 red-black Gauss-Seidel sweeps per V-cycle, BiCGStab bottom to 1e-4 in at most 200
+   iterations -- and the launch options of this implementation, which change no result
+   unless documented otherwise).  p: host pointer, written. */
 gmg_status gmg_default_params(gmg_params* p);
 
 /* Create a context bound to a CUDA stream (cudaStream_t passed as void*; NULL = the
-   legacy default stream).  *out receives the context. */
+   legacy default stream).  *out receives the context.  A context is one problem of the
+   operator equation of Sec. "Linear Solvers" posed on the data model of Sec. "Basic data
+   structures" (Geometry, BoxArray, BCRec) with one ghosted array per box (Sec.
+   "Containers for mesh data"); it owns host metadata only (device memory is the caller's,
+   see gmg_set_workspace).  GMG_ERR_BAD_INPUT if out is NULL. */
 gmg_status gmg_create(gmg_ctx** out, void* cuda_stream);
+/* Destroy a context (its cached tables and CUDA graphs; not the caller's device memory):
+   the problem of Sec. "Linear Solvers" on the data model of Sec. "Basic data structures",
+   as made by gmg_create.  NULL is accepted. */
 gmg_status gmg_destroy(gmg_ctx* ctx);
-/* Message of the last error on ctx ("" if none).  ctx may be NULL (creation errors). */
+/* Message of the last error on ctx ("" if none); no counterpart in the paper (the error
+   model of this library: a status code and a message, never an abort).  ctx may be NULL
+   (creation errors).  The returned string lives until the next call on ctx. */
 const char* gmg_last_error(const gmg_ctx* ctx);
 
 /* ---------------------------------------------------------------- geometry */
@@ -241,75 +254,95 @@ gmg_status gmg_define_level(gmg_ctx* ctx, int lev, int nboxes, const int* box_lo
    max_grid_size cells per axis (Sec. "Regridding": max_grid_size). */
 gmg_status gmg_chop_domain(gmg_ctx* ctx, int lev, int max_grid_size);
 
-/* Number of multigrid levels of the hierarchy (level 0 = the user's BoxArray). */
+/* Number of multigrid levels of the hierarchy (level 0 = the user's BoxArray; the coarser
+   levels by per-box coarsening, then aggregation, Sec. "Linear Solvers"). */
 gmg_status gmg_mg_nlevels(const gmg_ctx* ctx, int* nlevels);
 
-/* MG level m: number of boxes and domain (dom[0..2] = lo, dom[3..5] = hi). */
+/* MG level m: number of boxes and domain (dom[0..2] = lo, dom[3..5] = hi) (Sec. "Basic
+   data structures": a level's BoxArray and Geometry). */
 gmg_status gmg_mg_level_info(const gmg_ctx* ctx, int m, int* nboxes, int* dom);
 
 /* MG level m: boxes (6 ints each) and, for each box, the box of level m+1 that holds its
-   coarsened image (-1 on the bottom level).  Either pointer may be NULL. */
+   coarsened image (-1 on the bottom level) (Sec. "Linear Solvers": the coarsened
+   BoxArrays of the multigrid hierarchy).  Either pointer may be NULL. */
 gmg_status gmg_mg_level_boxes(const gmg_ctx* ctx, int m, int* box_lohi, int* parents);
 
 /* Boxed layout of MG level m for element type dt: total elements, per-box element
    offsets (nboxes entries, may be NULL) and row strides sx (nboxes entries, may be
-   NULL). */
+   NULL) (Sec. "Containers for mesh data": one array per box, ghost cells included). */
 gmg_status gmg_mg_layout(const gmg_ctx* ctx, int m, int dt, int64_t* nelems, int64_t* box_offsets, int* row_strides);
 
-/* FP64 boxed layout of AMR level lev (0: MG level 0; 1: the fine level). */
+/* FP64 boxed layout of AMR level lev (0: MG level 0; 1: the fine level) (Sec.
+   "Containers for mesh data"). */
 gmg_status gmg_layout(const gmg_ctx* ctx, int lev, int64_t* nelems, int64_t* box_offsets);
 
-/* Boxes of AMR level lev (count, 6 ints each, row strides); NULL pointers are skipped. */
+/* Boxes of AMR level lev (count, 6 ints each, row strides); NULL pointers are skipped
+   (Sec. "Basic data structures": the BoxArray of an AMR level). */
 gmg_status gmg_amr_level_boxes(const gmg_ctx* ctx, int lev, int* nboxes, int* box_lohi, int* row_strides);
 
 /* Dense (nz, ny, nx) FP64 array over the bounding box of AMR level lev's boxes (level 0:
-   the domain) <-> FP64 boxed layout of that level (valid cells only). */
+   the domain) <-> FP64 boxed layout of that level (valid cells only) (Sec. "Containers for
+   mesh data").  Device pointers; GMG_ERR_BAD_INPUT for an undefined level. */
 gmg_status gmg_pack_amr(gmg_ctx* ctx, int lev, const double* dense, double* boxed);
 gmg_status gmg_unpack_amr(gmg_ctx* ctx, int lev, const double* boxed, double* dense);
 
 /* Dense (nz, ny, nx) FP64 device array over MG level m's domain <-> boxed layout of
-   element type dt.  pack writes valid cells only (ghosts untouched); unpack reads
-   valid cells only. */
+   element type dt (Sec. "Containers for mesh data").  pack writes valid cells only
+   (ghosts untouched); unpack reads valid cells only. */
 gmg_status gmg_pack(gmg_ctx* ctx, int m, int dt, const double* dense, void* boxed);
 gmg_status gmg_unpack(gmg_ctx* ctx, int m, int dt, const void* boxed, double* dense);
 
 /* ------------------------------------------------------------- coefficients */
 
-/* Scalars a and b of the operator equation. */
+/* Scalars a and b of the operator equation a alpha phi - b div(beta grad phi) = rhs (Sec.
+   "Linear Solvers").  Any finite values; a problem with a = 0 and no Dirichlet wall is
+   singular.  Coefficients of every level are rebuilt at the next solve. */
 gmg_status gmg_set_scalars(gmg_ctx* ctx, double a, double b);
 
-/* Cell-centred alpha of AMR level lev (FP64, that level's boxed layout, device).  Not
-   calling it means alpha = 1. */
+/* Cell-centred alpha of AMR level lev (FP64, that level's boxed layout, device), the alpha
+   of the operator equation (Sec. "Linear Solvers"; coarse levels take the mean of 8
+   children, Sec. "Operations between levels").  Not calling it means alpha = 1.  The
+   library copies it (the pointer is not kept). */
 gmg_status gmg_set_acoef(gmg_ctx* ctx, int lev, const double* alpha_cc);
 
-/* Cell-centred beta of AMR level lev (FP64, that level's boxed layout, device); face
+/* Cell-centred beta of AMR level lev (FP64, that level's boxed layout, device), from which
+   the face beta of the operator equation (Sec. "Linear Solvers") is made: face
    beta = harmonic mean of the two cells, the interior cell's value on a wall face and
    (level 1) on a coarse/fine face.  Builds the coefficients of every MG level (coarse
    alpha = mean of 8 children, coarse face beta = mean of the 4 fine faces) once every
    defined AMR level has its beta.  Needs the workspace. */
 gmg_status gmg_set_bcoef_cell(gmg_ctx* ctx, int lev, const double* beta_cc);
 
-/* Face beta given directly: three FP64 face arrays in the boxed layout (slot i = face
-   i - 1/2).  Builds every MG level's coefficients.  Needs the workspace. */
+/* Face beta given directly (the face-centred beta of the operator equation, Sec. "Linear
+   Solvers"): three FP64 face arrays in the boxed layout (slot i = face i - 1/2).  Builds
+   every MG level's coefficients.  Needs the workspace. */
 gmg_status gmg_set_bcoef_face(gmg_ctx* ctx, int lev, const double* bx, const double* by, const double* bz);
 
 /* Scaled face weights w_d = b * beta_d / h_d^2 and diagonal D = a*alpha + sum of the six
-   weights of MG level m, copied into caller buffers of element type dt (NULL to skip). */
+   weights of MG level m (the discrete operator of Sec. "Linear Solvers" on that level),
+   copied into caller buffers of element type dt (NULL to skip). */
 gmg_status gmg_get_coeffs(gmg_ctx* ctx, int m, int dt, void* wx, void* wy, void* wz, void* diag);
 
 /* ---------------------------------------------------------------- workspace */
 
 /* Bytes of device workspace needed for solves with parameters p (NULL = defaults; a
-   mixed precision needs its float buffers in addition to the FP64 ones). */
+   mixed precision needs its float buffers in addition to the FP64 ones).  The workspace
+   plays the part of the pre-allocated memory pool of Sec. "Memory management" (one large
+   block handed out in pieces), except that the caller allocates it. */
 gmg_status gmg_workspace_size(const gmg_ctx* ctx, const gmg_params* p, size_t* bytes);
 
 /* Hand the library a device buffer of at least gmg_workspace_size bytes, 256-byte
-   aligned.  Uploads the index tables.  The buffer stays in use until replaced. */
+   aligned (Sec. "Memory management": the library carves every level array and table out
+   of this one block).  Uploads the index tables.  The buffer stays in use until replaced;
+   GMG_ERR_NO_WORKSPACE if it is too small. */
 gmg_status gmg_set_workspace(gmg_ctx* ctx, void* dptr, size_t bytes);
 
 /* ------------------------------------------------------------------- solve */
 
-/* Solve A phi = rhs from phi = 0 (phi's input content is ignored) until
+/* Sec. "Linear Solvers": solve the operator equation by geometric multigrid (V-cycles with a
+   Krylov bottom solver; over several AMR levels, the multi-level solve with the coarse/fine
+   operations of Sec. "Operations between levels").
+   Solve A phi = rhs from phi = 0 (phi's input content is ignored) until
    ||rhs - A phi||_inf <= max(tol_rel * ||rhs||_inf, tol_abs) or p->max_iter outer
    iterations.  phi[l], rhs[l]: FP64 device arrays in AMR level l's layout.  One level:
    the multigrid V-cycle iteration.  Several AMR levels: A is the composite operator on the
@@ -328,17 +361,22 @@ gmg_status gmg_set_workspace(gmg_ctx* ctx, void* dptr, size_t bytes);
 gmg_status gmg_solve(gmg_ctx* ctx, void* const* phi, const void* const* rhs, double tol_rel, double tol_abs,
                      const gmg_params* p, gmg_solve_info* info);
 
-/* out = A phi (FP64; phi's ghost cells are overwritten).  Several AMR levels: the
-   composite operator; covered entries of out are 0. */
+/* out = A phi, the operator of Sec. "Linear Solvers" (FP64; phi's ghost cells are
+   overwritten).  Several AMR levels: the composite operator (coarse/fine interpolation and
+   refluxing, Sec. "Operations between levels"); covered entries of out are 0. */
 gmg_status gmg_apply(gmg_ctx* ctx, void* const* out, void* const* phi);
 
-/* out = A^T y.  One level: A is symmetric (same as gmg_apply).  Several AMR levels: the
+/* out = A^T y, the transpose of the operator of Sec. "Linear Solvers" (the transpose
+   itself has no counterpart in the paper; it serves the adjoint below).  One level: A is
+   symmetric (same as gmg_apply).  Several AMR levels: the
    transpose of the composite operator (the level stencils plus, for each pair of
    consecutive levels, the transposed interpolation and reflux couplings); covered entries
    of y are taken as 0 and those of out are 0; y's ghosts are overwritten. */
 gmg_status gmg_apply_transpose(gmg_ctx* ctx, void* const* out, void* const* y);
 
-/* Adjoint solve A^T lambda = g (FP64), so that lambda = dL/d(rhs) for a loss L(phi) with
+/* Adjoint of the solve of Sec. "Linear Solvers" (no counterpart in the paper: the
+   differentiation of its operator equation).
+   Adjoint solve A^T lambda = g (FP64), so that lambda = dL/d(rhs) for a loss L(phi) with
    dL/dphi = g.  One level: a forward solve (A symmetric).  Several AMR levels: BiCGStab on A^T,
    right-preconditioned by the composite multigrid correction of A, to ||g - A^T lambda||_inf
    <= tol_rel ||g||_inf (max_iter Krylov iterations).  Singular problems (no Dirichlet wall,
@@ -348,7 +386,9 @@ gmg_status gmg_apply_transpose(gmg_ctx* ctx, void* const* out, void* const* y);
 gmg_status gmg_solve_adjoint(gmg_ctx* ctx, void* const* lambda, const void* const* g, double tol_rel,
                              const gmg_params* p, gmg_solve_info* info);
 
-/* Gradient of a loss with respect to the cell-centred beta of each level, given the
+/* Derivative of the solve of Sec. "Linear Solvers" with respect to its beta (no counterpart
+   in the paper: the differentiation of its operator equation).
+   Gradient of a loss with respect to the cell-centred beta of each level, given the
    solution phi and the adjoint lambda:  per face, dL/dbeta_face = -lambda^T (dA/dbeta_face) phi
    (-(b/h^2)(phi_R - phi_L)(lambda_R - lambda_L) on an interior face; on a coarse/fine face
    also the reflux row's share), then through the rule that made the face value from cell
@@ -359,7 +399,9 @@ gmg_status gmg_solve_adjoint(gmg_ctx* ctx, void* const* lambda, const void* cons
 gmg_status gmg_beta_grad(gmg_ctx* ctx, void* const* dbeta, void* const* phi, void* const* lambda);
 
 /* ------------------------------------------------------------- wall values */
-/* Nonzero values on the level-0 walls of a single-level, single-problem context.  A wall
+/* Inhomogeneous boundary conditions of the operator equation (Sec. "Linear Solvers";
+   Sec. "Basic data structures": BCRec).
+   Nonzero values on the level-0 walls of a single-level, single-problem context.  A wall
    value g makes the wall's ghost rule affine -- Dirichlet: ghost = 2g - interior (the line
    through the interior value and g on the face); Neumann: ghost = interior + h g (h the cell
    size normal to the face) -- and its phi-independent part is a constant of the operator:
@@ -373,19 +415,23 @@ gmg_status gmg_beta_grad(gmg_ctx* ctx, void* const* dbeta, void* const* phi, voi
    a context with several problems or several AMR levels accepts only NULLs (GMG_ERR_BAD_INPUT).
    All work is enqueued on the context stream; nothing is synchronised. */
 
-/* out = rhs - A_g(0): rhs plus, in each cell next to a wall face with a value, 2 w g
+/* Wall values (Sec. "Linear Solvers": inhomogeneous boundary conditions of the operator
+   equation).  out = rhs - A_g(0): rhs plus, in each cell next to a wall face with a value, 2 w g
    (Dirichlet) or w h g (Neumann), w = b beta_face / h^2 the face's weight; faces are added
    in the order x-, x+, y-, y+, z-, z+.  rhs, out: FP64 level-0 boxed device arrays; out may
    equal rhs (in place); otherwise rhs is copied first. */
 gmg_status gmg_wall_values_rhs(gmg_ctx* ctx, void* out, const void* rhs, const void* const* values);
 
-/* The transpose of the map g -> rhs - A_g(0): dvalues[f][t] = c * lambda[q] for the wall
+/* Wall values, adjoint (no counterpart in the paper: the differentiation of the operator
+   equation's boundary data).  The transpose of the map g -> rhs - A_g(0): dvalues[f][t] = c * lambda[q] for the wall
    cell q behind face position t, c = 2 w (Dirichlet) or w h (Neumann); with lambda the
    adjoint (gmg_solve_adjoint of dL/dphi) this is dL/dg.  dvalues[f]: FP64 device arrays in
    the layout of values above, written whole; NULL entries are skipped. */
 gmg_status gmg_wall_values_grad(gmg_ctx* ctx, const void* lambda, void* const* dvalues);
 
-/* gmg_beta_grad for a solution with wall values: phi's wall ghosts take the affine rule
+/* Wall values, beta gradient (no counterpart in the paper: the differentiation of the
+   operator equation of Sec. "Linear Solvers").  gmg_beta_grad for a solution with wall
+   values: phi's wall ghosts take the affine rule
    (values as above, NULL entries g = 0) before the face terms, so a wall face adds
    lambda_q w (ghost - phi_q) / beta_face to its cell.  values == NULL: gmg_beta_grad. */
 gmg_status gmg_beta_grad_walls(gmg_ctx* ctx, void* const* dbeta, void* const* phi, void* const* lambda,
@@ -396,31 +442,40 @@ gmg_status gmg_beta_grad_walls(gmg_ctx* ctx, void* const* dbeta, void* const* ph
    boxed layout.  Coefficients come from the last gmg_set_bcoef_* call (float copies
    for GMG_DT_F32 / GMG_DT_BF16 fields need a mixed-precision workspace). */
 
-/* FillBoundary: copy every face ghost cell from the box that owns it (periodic images
+/* Sec. "Operations on a level" (FillBoundary; fused into one gather kernel as in Sec.
+   "Communication").
+   FillBoundary: copy every face ghost cell from the box that owns it (periodic images
    included) or apply the homogeneous wall rule (Dirichlet: minus, Neumann: plus the
    adjacent interior value).  colour = 0 or 1 fills only
    the ghosts whose global (i+j+k) parity is that colour; -1 fills all. */
 gmg_status gmg_fill_boundary(gmg_ctx* ctx, int m, int dt, void* field, int colour);
 
 /* One red-black Gauss-Seidel half sweep of colour 0 (red, i+j+k even) or 1 (black),
-   preceded by the ghost fill it needs. */
+   preceded by the ghost fill it needs (the smoother of the geometric multigrid of Sec.
+   "Linear Solvers"). */
 gmg_status gmg_smooth(gmg_ctx* ctx, int m, int dt, void* phi, const void* rhs, int colour);
 
-/* r = rhs - A phi (ghosts of phi filled first).  r has element type rdt.  If norm is
-   non-NULL, *norm receives ||r||_inf (synchronises the stream). */
+/* r = rhs - A phi (ghosts of phi filled first), the residual of the operator equation of
+   Sec. "Linear Solvers" (its max-norm is a reduction of Sec. "Parallel Reductions").  r has
+   element type rdt.  If norm is non-NULL, *norm receives ||r||_inf (synchronises the
+   stream). */
 gmg_status gmg_residual(gmg_ctx* ctx, int m, int dt, void* phi, const void* rhs, int rdt, void* r, double* norm);
 
-/* Average-down restriction of a cell field from MG level m to m+1 (mean of 8 children). */
+/* Average-down restriction of a cell field from MG level m to m+1 (mean of 8 children;
+   Sec. "Operations between levels": restriction by averaging fine data). */
 gmg_status gmg_restrict(gmg_ctx* ctx, int m, int dt, const void* fine, void* coarse);
 
-/* fine += piecewise-constant interpolation of coarse (MG level m+1 -> m). */
+/* fine += piecewise-constant interpolation of coarse (MG level m+1 -> m; Sec. "Operations
+   between levels": interpolation). */
 gmg_status gmg_prolong_add(gmg_ctx* ctx, int m, int dt, const void* coarse, void* fine);
 
 /* BiCGStab on the bottom level: x = A_bottom^-1 rhs to bottom_tol (FP64 arithmetic,
-   buffers of type dt).  *iters (host, may be NULL) receives the iteration count. */
+   buffers of type dt) (Sec. "Linear Solvers": the Krylov bottom solve of the multigrid
+   hierarchy).  *iters (host, may be NULL) receives the iteration count. */
 gmg_status gmg_bottom_solve(gmg_ctx* ctx, int dt, const void* rhs, void* x, const gmg_params* p, int* iters);
 
-/* One V-cycle on the correction equation of MG level 0: e = V(r), element type dt. */
+/* One V-cycle on the correction equation of MG level 0: e = V(r), element type dt (Sec.
+   "Linear Solvers": the geometric multigrid cycle). */
 gmg_status gmg_vcycle(gmg_ctx* ctx, int dt, void* e, const void* r, const gmg_params* p);
 
 /* -------------------------------------------------------------- autotuning */
@@ -437,7 +492,8 @@ gmg_status gmg_vcycle(gmg_ctx* ctx, int dt, void* e, const void* r, const gmg_pa
    graphs. */
 gmg_status gmg_autotune(gmg_ctx* ctx, int precision, const void* rhs, const gmg_params* p);
 
-/* The tuned choice for MG level m and precision: *push = bit 0 ghost push, bit 1 4-cell
+/* Autotuner results (no counterpart in the paper).  The tuned choice for MG level m and
+   precision: *push = bit 0 ghost push, bit 1 4-cell
    threads, -1 not tuned (no smoothing there); the best measured ms per sweep with push and
    with the exchange (0 if push is not possible there); *fused_coarse = 1/0/-1 and the
    measured ms per V-cycle with (fused) and without (levels) the fused coarse end.  Any
@@ -447,7 +503,9 @@ gmg_status gmg_tuned(const gmg_ctx* ctx, int precision, int m, int* push, double
 
 /* ------------------------------------------------------------ batched form */
 
-/* Several independent problems in one context (the batched form of the solve: many
+/* The batched form (no counterpart in the paper; each problem is a Geometry + BoxArray of
+   Sec. "Basic data structures" solved as in Sec. "Linear Solvers").
+   Several independent problems in one context (the batched form of the solve: many
    solves with boxes of uneven sizes run as one set of launches per V-cycle step).
    Problem s has domain dom_lohi[6s..6s+5] (lo, hi inclusive), physical extent
    prob_lo[3s..], prob_hi[3s..], boundary conditions bc_lo[3s..], bc_hi[3s..] and
@@ -460,19 +518,23 @@ gmg_status gmg_define_batch(gmg_ctx* ctx, int nsolves, const int* dom_lohi, cons
                             const double* prob_hi, const int* bc_lo, const int* bc_hi, const int* nboxes,
                             const int* box_lohi);
 
-/* Number of independent problems in the context (1 after gmg_define_domain). */
+/* Number of independent problems in the context (1 after gmg_define_domain) (batched form,
+   no counterpart in the paper). */
 gmg_status gmg_num_solves(const gmg_ctx* ctx, int* nsolves);
 
 /* Boxes of problem `solve` on MG level m: index of its first box and count (-1, 0 if the
-   problem has no boxes on that level). */
+   problem has no boxes on that level) (batched form; Sec. "Basic data structures"). */
 gmg_status gmg_solve_boxes(const gmg_ctx* ctx, int m, int solve, int* first, int* count);
 
-/* gmg_pack / gmg_unpack for one problem: dense (nz, ny, nx) FP64 array over that
+/* Batched form, Sec. "Containers for mesh data":
+   gmg_pack / gmg_unpack for one problem: dense (nz, ny, nx) FP64 array over that
    problem's domain on MG level m <-> its boxes in the level's boxed layout. */
 gmg_status gmg_pack_solve(gmg_ctx* ctx, int m, int dt, int solve, const double* dense, void* boxed);
 gmg_status gmg_unpack_solve(gmg_ctx* ctx, int m, int dt, int solve, const void* boxed, double* dense);
 
-/* Solve every problem of the context from phi = 0: phi and rhs are FP64 level-0 boxed
+/* Batched solve (Sec. "Linear Solvers" for each problem; the batching has no counterpart in
+   the paper).
+   Solve every problem of the context from phi = 0: phi and rhs are FP64 level-0 boxed
    buffers holding all problems.  Each problem stops at its own tolerance
    max(tol_rel * ||rhs_s||_inf, tol_abs) (or max_iter); problems that have converged are
    masked out of the remaining V-cycles, so each one performs exactly the iterations a

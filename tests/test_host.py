@@ -145,3 +145,43 @@ def test_solve_info_struct_matches_header():
     want = [n for _, n in _header_struct("gmg_solve_info")]
     assert [n for n, _ in gmg.SolveInfo._fields_] == want
     assert C.sizeof(gmg.SolveInfo) >= 8 * 256
+
+
+def test_every_declaration_cites_a_passage():
+    """Every entry point of include/gmg.h (or the group of declarations its comment covers)
+    names the paper's section that defines it, or says that the paper has no counterpart."""
+    import re
+
+    text = open(os.path.join(ROOT, "include", "gmg.h")).read()
+    body = text[text.index("/* ---------------------------------------------------------------- context */"):]
+    missing = []
+    for m in re.finditer(r"\n(?:gmg_status|const char\*) (gmg_\w+)\(", body):
+        pre = body[:m.start()]
+        # walk back over declarations that share the comment above them
+        while True:
+            cend, semi = pre.rfind("*/"), pre.rfind(";")
+            if semi > cend:
+                pre = pre[:pre.rfind("\n", 0, semi)]
+                continue
+            break
+        com = pre[pre.rfind("/*", 0, cend):cend]
+        if not re.search(r'Sec\.\s+"', com) and "no counterpart" not in com:
+            missing.append(m.group(1))
+    assert not missing, missing
+
+
+def test_noalloc_refuses_large_boxes_before_any_cuda_call():
+    """gmg_box_bicgstab_noalloc checks its size limit, (nx+2)(ny+2)(nz+2) <= 65536, on the host
+    before it touches CUDA: edges near INT_MAX (whose +2 would overflow 32 bits), a cube of
+    64^3 ghosted elements and a box one row over the limit all return GMG_ERR_BAD_INPUT
+    with the limit named, whatever the (never used) pointers."""
+    from paper_2009_12009_gb300 import gmg
+
+    L = gmg.lib()
+    bc = (C.c_int * 3)(1, 1, 1)
+    big = 2 ** 31 - 2
+    for n in [(big, 1, 1), (1, big, 1), (1, 1, big), (big, big, big), (62, 62, 62), (63, 30, 30), (62, 31, 30)]:
+        st = L.gmg_box_bicgstab_noalloc(None, n[0], n[1], n[2], bc, bc, 0, C.c_void_p(8), C.c_void_p(8),
+                                        C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), 200, 1e-4, None)
+        assert st == gmg.BAD_INPUT, n
+        assert b"static scratch limit" in L.gmg_last_error(None), n
