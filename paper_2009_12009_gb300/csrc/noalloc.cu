@@ -15,6 +15,7 @@
 // or different host threads) race on the array and must be serialised by the caller.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/gmg.h"
@@ -265,9 +266,11 @@ __global__ void __launch_bounds__(NT) k_box_bicgstab_noalloc(NBox b, const doubl
   if (threadIdx.x == 0 && iters) *iters = it;
 }
 
-// device address of the scratch, looked up once per device (with that device current)
+// device address of the scratch, looked up once per device (with that device current);
+// atomic so that host threads making their first call on a device at the same time are
+// safe (each stores the same address)
 constexpr int MAX_DEVICES = 64;
-double* g_scratch_ptr[MAX_DEVICES] = {nullptr};
+std::atomic<double*> g_scratch_ptr[MAX_DEVICES];
 
 }  // namespace
 }  // namespace gmg
@@ -286,7 +289,11 @@ extern "C" gmg_status gmg_box_bicgstab_noalloc(void* stream, int nx, int ny, int
     set_thread_error("gmg_box_bicgstab_noalloc: invalid arguments");
     return GMG_ERR_BAD_INPUT;
   }
-  const int64_t ghosted = (int64_t)(nx + 2) * (ny + 2) * (nz + 2);
+  // edges beyond the limit are refused one by one first, so the product below is formed in
+  // 64 bits from small factors (no overflow whatever the edges)
+  const int64_t ghosted = (nx > NOALLOC_MAX_ELEMS || ny > NOALLOC_MAX_ELEMS || nz > NOALLOC_MAX_ELEMS)
+                              ? (int64_t)NOALLOC_MAX_ELEMS + 1
+                              : ((int64_t)nx + 2) * ((int64_t)ny + 2) * ((int64_t)nz + 2);
   if (ghosted > NOALLOC_MAX_ELEMS) {
     set_thread_error("gmg_box_bicgstab_noalloc: (nx+2)(ny+2)(nz+2) = " + std::to_string(ghosted) +
                      " exceeds the static scratch limit of " + std::to_string(NOALLOC_MAX_ELEMS) + " elements");
@@ -314,7 +321,8 @@ extern "C" gmg_status gmg_box_bicgstab_noalloc(void* stream, int nx, int ny, int
     set_thread_error(std::string("gmg_box_bicgstab_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
     return GMG_ERR_CUDA;
   }
-  if (!g_scratch_ptr[dev]) {
+  double* scratch = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!scratch) {
     // first call on this device: resolve the scratch array's device address
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -322,9 +330,10 @@ extern "C" gmg_status gmg_box_bicgstab_noalloc(void* stream, int nx, int ny, int
       set_thread_error(std::string("gmg_box_bicgstab_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       return GMG_ERR_CUDA;
     }
-    g_scratch_ptr[dev] = (double*)ptr;
+    scratch = (double*)ptr;
+    g_scratch_ptr[dev].store(scratch, std::memory_order_release);
   }
-  k_box_bicgstab_noalloc<<<1, NT, 0, (cudaStream_t)stream>>>(b, wx, wy, wz, diag, rhs, x, g_scratch_ptr[dev],
+  k_box_bicgstab_noalloc<<<1, NT, 0, (cudaStream_t)stream>>>(b, wx, wy, wz, diag, rhs, x, scratch,
                                                               NOALLOC_MAX_ELEMS, singular ? 1 : 0, maxit, tol, iters);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
