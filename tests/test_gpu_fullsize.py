@@ -2,11 +2,15 @@
 the oracle.
 
   * abec256 (256^3, 64 boxes, FP64, graphs, V(2,2)): two V-cycle iterations element by
-    element against two oracle iterations (1e-10 relative); the converged solution's
+    element against two oracle iterations (1e-10 relative); the solve to 1e-10 against the
+    oracle's solve to 1e-10 (same algorithm): the same iteration count and the solution
+    element by element within 1e-10 relative max-norm; the float and bfloat16-storage
+    solves to 1e-10 against the same oracle solution (within 1e-9); the converged solution's
     residual recomputed by the oracle's operator (<= 1.01e-10 ||rhs||, the requested
     tolerance with room for the order of the residual's additions).
-  * abec512 (512^3, 64 boxes): one FP64 iteration element by element; FP64 and both mixed
+  * abec512 (512^3, 64 boxes): two FP64 iterations element by element; FP64 and both mixed
     solves converge to a residual that the oracle's operator confirms.
+The oracle runs its box loops on every host core (bitwise its sequential results).
   * batch64 (64 problems, 42.3M cells, one batched context): every problem's residual by
     the oracle's operator, in FP64 and mixed FP32; three problems (smallest, median,
     largest) solved by the oracle alone: same iteration count, solutions within 1e-10.
@@ -36,6 +40,15 @@ from paper_2009_12009_gb300 import gmg  # noqa: E402
 
 TOL = 1e-10
 RES_BOUND = 1.01e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def oracle_threads():
+    import os
+
+    O.set_threads(len(os.sched_getaffinity(0)))
+    yield
+    O.set_threads(1)
 
 
 def stream():
@@ -72,6 +85,42 @@ def test_abec256_two_iterations_match_oracle(abec256):
     got = C.unpack(phi).cpu().numpy()
     assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
     np.testing.assert_allclose(info.history(), hist, rtol=1e-8)
+
+
+@pytest.fixture(scope="module")
+def abec256_oracle_solution(abec256):
+    cfg, C, P = abec256
+    want, it, hist, st = P.solve(cfg["rhs"], tol_rel=TOL, maxit=100)
+    assert st == O.OK
+    return want, it, hist
+
+
+def test_abec256_converged_solution_matches_oracle(abec256, abec256_oracle_solution):
+    """The requirement at the headline size: the FP64 solve to 1e-10 and the oracle's solve to
+    1e-10 take the same V-cycles and agree within 1e-10 relative max-norm, element by element."""
+    cfg, C, P = abec256
+    want, it, hist = abec256_oracle_solution
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=TOL)
+    assert info.status == gmg.OK and info.iterations == it
+    got = C.unpack(phi).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    # residual histories agree until they reach the rounding floor of the residual sums
+    # (FMA in the kernels, separate products in the oracle): 1e-13 of the initial residual
+    np.testing.assert_allclose(info.history(), hist, rtol=1e-6, atol=1e-13 * hist[0])
+
+
+@pytest.mark.parametrize("prec", [gmg.MIXED_FP32, gmg.MIXED_BF16], ids=["fp32", "bf16"])
+def test_abec256_mixed_solution_vs_oracle(abec256_oracle_solution, prec):
+    """The float and bfloat16-storage V-cycles inside FP64 refinement reach the oracle's FP64
+    solution: relative max-norm error within 1e-9 (measured on GB300: 1.2e-15 for float,
+    2.8e-13 for bfloat16 storage)."""
+    cfg = I.abec256()
+    C, _ = make_pair(cfg, gmg.MIXED_FP32)
+    want, it, hist = abec256_oracle_solution
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=TOL, precision=prec)
+    assert info.status == gmg.OK
+    err = np.abs(C.unpack(phi).cpu().numpy() - want).max() / np.abs(want).max()
+    assert err <= 1e-9, err
 
 
 def test_abec256_converged_residual(abec256):
@@ -123,11 +172,12 @@ def abec512():
     return cfg, C, P
 
 
-def test_abec512_one_iteration_matches_oracle(abec512):
+def test_abec512_two_iterations_match_oracle(abec512):
     cfg, C, P = abec512
-    want, it, hist, _ = P.solve(cfg["rhs"], tol_rel=0.0, maxit=1)
-    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=0.0, max_iter=1)
-    assert info.iterations == it == 1
+    want, it, hist, _ = P.solve(cfg["rhs"], tol_rel=0.0, maxit=2)
+    phi, info = C.solve(C.pack(torch.from_numpy(cfg["rhs"])), tol_rel=0.0, max_iter=2)
+    assert info.iterations == it == 2
+    np.testing.assert_allclose(info.history(), hist, rtol=1e-8)
     got = C.unpack(phi).cpu().numpy()
     assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
 
