@@ -149,7 +149,12 @@ typedef struct {
                            it is for one level).  Krylov vectors are FP64 and need a
                            workspace sized with krylov != 0; the V-cycle runs in `precision`.
                            One-level, single-problem contexts.  The stopping test uses the
-                           recursive residual of the Krylov recurrence. */
+                           recursive residual of the Krylov recurrence.
+                           With krylov = 0 the multigrid iteration can stall on coefficients
+                           of very high contrast (measured: beta = exp(3 N(0,1)), 8 decades,
+                           stops near 1e-5 and returns GMG_ERR_NOT_CONVERGED after max_iter);
+                           krylov = 2 (or 1) reaches 1e-10 there -- use it when a solve reports
+                           a residual history that levels off. */
   int bottom_solver;    /* 0 (default): BiCGStab bottom; 1: conjugate gradients (the bottom
                            operator is symmetric) */
   int post_reverse;     /* 1: post-smoothing sweeps take black before red, the reverse of
