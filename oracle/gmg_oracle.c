@@ -97,6 +97,7 @@ typedef struct {
   double* bcval[6];  /* level-0 wall values per face (2*d + side), or NULL (g = 0) */
   int bot_cg;        /* bottom solver: 0 BiCGStab, 1 conjugate gradients */
   int post_rev;      /* post-smoothing colour order: 0 red then black, 1 black then red */
+  int prolong;       /* interpolation of the coarse correction: 0 piecewise constant, 1 trilinear */
 } oprob;
 
 /* ------------------------------------------------------------------ layout */
@@ -397,6 +398,10 @@ void orc_set_cycle(void* vp, int bottom_cg, int post_reverse) {
   p->post_rev = post_reverse;
 }
 
+/* Interpolation of the coarse correction (Sec. "Operations between levels": the paper names
+   interpolation without fixing its order): 0 piecewise constant (default), 1 trilinear. */
+void orc_set_prolong(void* vp, int mode) { ((oprob*)vp)->prolong = mode; }
+
 /* dense array over the level's domain (x fastest) <-> ghosted per-box layout */
 void orc_dense_to_boxed(void* vp, int m, const double* dense, double* boxed) {
   olev* l = &((oprob*)vp)->L[m];
@@ -644,11 +649,68 @@ void orc_restrict(void* vp, int m, const double* fine, double* coarse) {
   }
 }
 
-/* Piecewise-constant prolongation of a coarse correction, added to the fine one. */
+/* Value of a coarse-level field at global cell index G, which may lie one cell beyond the
+   domain: the correction's homogeneous boundary rule extends it -- a periodic axis wraps, a
+   wall mirrors the index into the domain (ghost -1 <-> cell 0) with the factor -1 for a
+   Dirichlet wall and +1 for a Neumann wall, one factor per axis crossed. */
+static double coarse_value(const olev* c, const double* e, const int G[3]) {
+  int g[3];
+  double sign = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    int n = c->dhi[d] - c->dlo[d] + 1, rel = G[d] - c->dlo[d];
+    if (rel < 0 || rel >= n) {
+      int bc = rel < 0 ? c->bclo[d] : c->bchi[d];
+      if (bc == ORC_PERIODIC) {
+        rel = pmod(rel, n);
+      } else {
+        rel = rel < 0 ? -1 - rel : 2 * n - 1 - rel;
+        if (bc == ORC_DIRICHLET) sign = -sign;
+      }
+    }
+    g[d] = c->dlo[d] + rel;
+  }
+  int b = find_box(c, g);
+  return sign * e[IX(c, b, g[0] - c->lo[3 * b], g[1] - c->lo[3 * b + 1], g[2] - c->lo[3 * b + 2])];
+}
+
+/* Trilinear interpolation at fine cell g: the fine centre lies a quarter of a coarse cell from
+   its parent's centre along each axis, towards the side s_d = +1 (odd g_d) or -1 (even g_d);
+   the weights are 3/4 on the parent's coordinate and 1/4 on the neighbour's, per axis, and
+   the eight products are summed z outermost, then y, then x. */
+static double trilinear_at(const olev* c, const double* e, const int g[3]) {
+  static const double w[2] = {0.75, 0.25};
+  int G[3], s[3];
+  for (int d = 0; d < 3; ++d) {
+    G[d] = g[d] >= 0 ? g[d] / 2 : -((1 - g[d]) / 2);
+    s[d] = (g[d] - 2 * G[d]) ? 1 : -1;
+  }
+  double v = 0.0;
+  for (int cz = 0; cz < 2; ++cz)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cx = 0; cx < 2; ++cx) {
+        int H[3] = {G[0] + cx * s[0], G[1] + cy * s[1], G[2] + cz * s[2]};
+        v += (w[cx] * w[cy] * w[cz]) * coarse_value(c, e, H);
+      }
+  return v;
+}
+
+/* Prolongation of a coarse correction, added to the fine one: piecewise constant (every
+   fine cell takes its parent's value) or trilinear (orc_set_prolong). */
 void orc_prolong_add(void* vp, int m, const double* coarse, double* fine) {
   oprob* p = (oprob*)vp;
   olev* f = &p->L[m];
   olev* c = &p->L[m + 1];
+  if (p->prolong == 1) {
+  #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1)
+    for (int fb = 0; fb < f->nb; ++fb)
+      for (int k = 0; k < bn(f, fb, 2); ++k)
+        for (int j = 0; j < bn(f, fb, 1); ++j)
+          for (int i = 0; i < bn(f, fb, 0); ++i) {
+            int g[3] = {f->lo[3 * fb] + i, f->lo[3 * fb + 1] + j, f->lo[3 * fb + 2] + k};
+            fine[IX(f, fb, i, j, k)] += trilinear_at(c, coarse, g);
+          }
+    return;
+  }
   #pragma omp parallel for schedule(dynamic) num_threads(g_threads) if (g_threads > 1)
   for (int fb = 0; fb < f->nb; ++fb) {
     int P = f->parent[fb];

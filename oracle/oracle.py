@@ -69,6 +69,7 @@ _f64p = C.POINTER(C.c_double)
 
 def _declare(L):
     L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_set_prolong.argtypes = [C.c_void_p, C.c_int]
     L.orc_get_threads.restype = C.c_int
     L.orc_create.restype = C.c_void_p
     L.orc_create.argtypes = [_i32p, _i32p, _i32p, _i32p, _f64p, _f64p, C.c_int, _i32p]
@@ -194,6 +195,10 @@ class Problem:
         """bottom solver CG instead of BiCGStab; post-smoothing black before red (symmetric
         V-cycle)."""
         lib().orc_set_cycle(self.h, int(bottom_cg), int(post_reverse))
+
+    def set_prolong(self, trilinear=False):
+        """interpolation of the coarse correction: piecewise constant (default) or trilinear"""
+        lib().orc_set_prolong(self.h, int(bool(trilinear)))
 
     def set_params(self, nu1=2, nu2=2, bot_maxit=200, bot_tol=1e-4):
         lib().orc_set_params(self.h, nu1, nu2, bot_maxit, bot_tol)
