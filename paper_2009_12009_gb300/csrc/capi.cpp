@@ -325,6 +325,8 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
                      : (int*)cv.take(sizeof(int) * FLOW_CNT_STRIDE *
                                      (FLOW_QUEUES + 1 + FLOW_MAX_PHASES * M.flow_slabs.size()));
     vc_skip[m] = (const int*)cv.take(sizeof(int) * M.vc_flow_skip.size());
+    D.ec_ghosts = (const BotGhost*)cv.take(sizeof(BotGhost) * M.ec_ghosts.size());
+    D.n_ec_ghosts = (int)M.ec_ghosts.size();
     D.push_faces = (const PushFace*)cv.take(sizeof(PushFace) * M.push_faces.size());
     D.push_ok = M.push_ok ? 1 : 0;
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
@@ -520,6 +522,7 @@ gmg_status upload_tables(gmg_ctx* c) {
                             sizeof(int) * FLOW_CNT_STRIDE * (FLOW_QUEUES + 1 + FLOW_MAX_PHASES * M.flow_slabs.size()),
                             c->stream));
     if ((st = upload(c, c->vc_flow_skip[m], M.vc_flow_skip))) return st;
+    if ((st = upload(c, D.ec_ghosts, M.ec_ghosts))) return st;
     if ((st = upload(c, D.push_faces, M.push_faces))) return st;
   }
   {
@@ -609,6 +612,7 @@ gmg_status build_hierarchy(gmg_ctx* c, const std::vector<Box>& boxes, const std:
     bool more = make_coarse(c->L[m], C);
     std::string e = finalize_level(c->L[m]);
     if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, e);
+    if (m > 0) build_ec_ghosts(c->L[m]);  // the coarse side of an interpolation (trilinear option)
     if (!more) break;
     c->L.push_back(C);
   }
@@ -706,6 +710,7 @@ bool vec_on(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
 }
 
 bool tail_on(const gmg_ctx* c, const gmg_params& p, int dt) {
+  if (p.prolongation == 1) return false;  // the one-block coarse end interpolates piecewise constant
   if (p.fused_coarse == 2) return c->tail_choice[dt] != 0;  // untuned: on
   return p.fused_coarse == 1;
 }
@@ -809,8 +814,11 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
   }
 }
 
-// the graph-cache value of the sweep choices: fused_sweep, the flow launch width, serpentine
-int sweep_key(const gmg_params& p) { return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine; }
+// the graph-cache value of the sweep choices: fused_sweep, the flow launch width, serpentine,
+// the interpolation
+int sweep_key(const gmg_params& p) {
+  return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine + 2048 * p.prolongation;
+}
 
 // the symmetric V-cycle: post-smoothing black before red (asked for, or implied by the
 // conjugate-gradient top level)
@@ -911,7 +919,13 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   launch_resid_restrict(dt, dir_view(c, D, m), Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s,
                         settled);
   vcycle(c, dt, m + 1, p, s, false);
-  launch_prolong_add(dt, dir_view(c, D, m), Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
+  if (p.prolongation == 1) {  // trilinear: the coarse correction's ghosts, edges and corners too
+    launch_fill(dt, c->dev[m + 1], c->buf[m + 1].e[dt], -1, 0, s);
+    launch_fill_ec(dt, c->dev[m + 1], c->buf[m + 1].e[dt], s);
+    launch_prolong_tri(dt, dir_view(c, D, m), Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
+  } else {
+    launch_prolong_add(dt, dir_view(c, D, m), Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
+  }
   smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, post_reversed(p), phi_update, push_phi);
 }
 
@@ -1009,6 +1023,7 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.flow_warps < 0 || p.flow_warps > 64) SETERR(c, GMG_ERR_BAD_INPUT, "flow_warps must be in [0, 64]");
   if (p.flow_lag_kcells < 0) SETERR(c, GMG_ERR_BAD_INPUT, "flow_lag_kcells must be >= 0");
   if (p.serpentine != 0 && p.serpentine != 1) SETERR(c, GMG_ERR_BAD_INPUT, "serpentine must be 0 or 1");
+  if (p.prolongation != 0 && p.prolongation != 1) SETERR(c, GMG_ERR_BAD_INPUT, "prolongation must be 0 or 1");
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
@@ -2173,6 +2188,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->flow_warps = 0;
   p->flow_lag_kcells = 0;
   p->serpentine = 1;
+  p->prolongation = 0;
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;
@@ -2678,6 +2694,18 @@ gmg_status gmg_prolong_add(gmg_ctx* c, int m, int dt, const void* coarse, void* 
   if (st) return st;
   if (m + 1 >= nlev(c)) SETERR(c, GMG_ERR_BAD_INPUT, "no coarser level");
   launch_prolong_add(dt, c->dev[m], c->dev[m + 1], coarse, fine, c->stream);
+  CK(c, cudaGetLastError());
+  return GMG_OK;
+}
+
+gmg_status gmg_prolong_add_trilinear(gmg_ctx* c, int m, int dt, void* coarse, void* fine) {
+  if (!c) return GMG_ERR_BAD_INPUT;
+  gmg_status st = check_level(c, m, dt);
+  if (st) return st;
+  if (m + 1 >= nlev(c)) SETERR(c, GMG_ERR_BAD_INPUT, "no coarser level");
+  launch_fill(dt, c->dev[m + 1], coarse, -1, 0, c->stream);
+  launch_fill_ec(dt, c->dev[m + 1], coarse, c->stream);
+  launch_prolong_tri(dt, c->dev[m], c->dev[m + 1], coarse, fine, c->stream);
   CK(c, cudaGetLastError());
   return GMG_OK;
 }

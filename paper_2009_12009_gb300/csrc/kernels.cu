@@ -491,6 +491,83 @@ __global__ void __launch_bounds__(BLOCK, MINB)
     }
 }
 
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+// Trilinear interpolation of the coarse correction, added to the fine one: one thread per
+// coarse cell reads its 3x3x3 neighbourhood (ghosts included) and writes its 8 children.  A
+// child's centre lies a quarter of a coarse cell from the parent's centre towards side
+// s_d = +1 (odd local index) or -1 per axis; weights 3/4 on the parent's coordinate and 1/4 on
+// the neighbour's, the eight terms summed z outermost, then y, then x, with unfused
+// products (the oracle's arithmetic, so FP64 results are bitwise the oracle's).
+template <class T, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
+    k_prolong_tri(const DevBox* __restrict__ fboxes, const DevBox* __restrict__ cboxes, const int* __restrict__ parent,
+                  const Chunk* __restrict__ chunks, const T* __restrict__ coarse, T* fine,
+                  const int* __restrict__ active, const PushFace* __restrict__ push, int rev) {
+  pdl_enter();
+  using A = typename Arith<T>::type;
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
+  const DevBox F = fboxes[ch.item];
+  if (active && !active[F.solve]) return;
+  const DevBox P = cboxes[parent[ch.item]];
+  const int ncx = F.nx >> 1, ncy = F.ny >> 1, ncz = F.nz >> 1;
+  const int t = ch.start + threadIdx.x;
+  if (t >= ncx * ncy * ncz) return;
+  const int ci = t % ncx, cj = (t / ncx) % ncy, ck = t / (ncx * ncy);
+  const int I = (F.lo[0] >> 1) + ci - P.lo[0];
+  const int J = (F.lo[1] >> 1) + cj - P.lo[1];
+  const int K = (F.lo[2] >> 1) + ck - P.lo[2];
+  A E[3][3][3];
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) E[dz][dy][dx] = ld(coarse + elem_index(P, I + dx - 1, J + dy - 1, K + dz - 1));
+  const A w[2] = {(A)0.75, (A)0.25};
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      A v[2];
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox) {
+        const int sx = ox ? 1 : -1, sy = oy ? 1 : -1, sz = oz ? 1 : -1;
+        A acc = 0;
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+          for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 2; ++cx)
+              acc = add_rn(acc, mul_rn(w[cx] * w[cy] * w[cz], E[1 + cz * sz][1 + cy * sy][1 + cx * sx]));
+        v[ox] = acc;
+      }
+      const int64_t q = elem_index(F, 2 * ci, 2 * cj + oy, 2 * ck + oz);
+      const A v0 = add_rn((A)ld(fine + q), v[0]), v1 = add_rn((A)ld(fine + q + 1), v[1]);
+      st(fine + q, v0);
+      st(fine + q + 1, v1);
+      if (push) {
+        push_ghosts(F, ch.item, fboxes, push, fine, 2 * ci, 2 * cj + oy, 2 * ck + oz, v0);
+        push_ghosts(F, ch.item, fboxes, push, fine, 2 * ci + 1, 2 * cj + oy, 2 * ck + oz, v1);
+      }
+    }
+}
+
+// f[dst] = sign * f[src] over a flat list (edge and corner ghosts)
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_fill_list(const BotGhost* __restrict__ g, int n, T* f) {
+  pdl_enter();
+  const int t = blockIdx.x * BLOCK + threadIdx.x;
+  if (t >= n) return;
+  const BotGhost e = g[t];
+  const auto v = ld(f + e.src);
+  st(f + e.dst, e.sign < 0 ? -v : v);
+}
+
 // ----------------------------------------------------------- cell-wise helpers
 
 template <class T>
@@ -883,6 +960,23 @@ void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void
   GMG_DISPATCH(dt, launch_pdl(k_prolong_add<T, std::is_same<T, double>::value ? 8 : 0>, grid_of(f.n_coarse_chunks),
                               BLOCK, 0, s, f.boxes, c.boxes,
                               f.parent, f.coarse_chunks, (const T*)coarse, (T*)fine, f.active, pf, f.rev));
+}
+
+void launch_prolong_tri(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine, cudaStream_t s,
+                        bool push) {
+  if (!f.n_coarse_chunks) return;
+  ++g_launches;
+  const PushFace* pf = push ? f.push_faces : nullptr;
+  GMG_DISPATCH(dt, launch_pdl(k_prolong_tri<T, std::is_same<T, double>::value ? 4 : 0>, grid_of(f.n_coarse_chunks),
+                              BLOCK, 0, s, f.boxes, c.boxes, f.parent, f.coarse_chunks, (const T*)coarse, (T*)fine,
+                              f.active, pf, f.rev));
+}
+
+void launch_fill_ec(int dt, const LevelDev& L, void* f, cudaStream_t s) {
+  if (!L.n_ec_ghosts) return;
+  ++g_launches;
+  GMG_DISPATCH(dt, launch_pdl(k_fill_list<T>, (unsigned)((L.n_ec_ghosts + BLOCK - 1) / BLOCK), BLOCK, 0, s,
+                              L.ec_ghosts, L.n_ec_ghosts, (T*)f));
 }
 
 void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s, bool push) {

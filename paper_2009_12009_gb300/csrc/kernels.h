@@ -64,6 +64,8 @@ struct LevelDev {
   const int* flow_skip = nullptr;  // per solve: 1 = leave its items out (null: none)
   const PushFace* push_faces = nullptr;  // 6 per box (ghost push targets)
   int push_ok = 0;                       // push_faces usable for every box of the level
+  const BotGhost* ec_ghosts = nullptr;  // edge and corner ghosts (levels >= 1), f[dst] = sign f[src]
+  int n_ec_ghosts = 0;
   // 1: the level-sweep kernels (smoothers, residual, residual-restriction, interpolation)
   // take their work list last entry first.  Consecutive kernels on a level that alternate it
   // start on the boxes the previous one touched last, still in L2.  Same results.
@@ -110,6 +112,13 @@ void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const v
 void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s);
 void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine,
                         cudaStream_t s, bool push = false);
+// fine += trilinear interpolation of coarse (weights 3/4, 1/4 per axis; summed z, y, x
+// outermost first, unfused products -- the oracle's order); coarse's face, edge and corner
+// ghosts must hold the homogeneous boundary rule's values (launch_fill + launch_fill_ec)
+void launch_prolong_tri(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine,
+                        cudaStream_t s, bool push = false);
+// edge and corner ghosts of a level from their owning valid cells (L.ec_ghosts)
+void launch_fill_ec(int dt, const LevelDev& L, void* f, cudaStream_t s);
 // phi (double) += e (type dt) on valid cells
 // (push: also write the new phi into the ghost cells that copy it, L.push_ok levels only)
 void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e, cudaStream_t s,

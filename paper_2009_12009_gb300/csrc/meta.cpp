@@ -2,6 +2,8 @@
 #include "meta.h"
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <cstdio>
 
 namespace gmg {
@@ -307,6 +309,79 @@ void build_flow_order(LevelMeta& L, int64_t lag) {
         o.push_back({(g.c << 24) | g.s, I.box, I.z0, I.z1, I.y0, I.y1});
       }
     }
+  }
+}
+
+void build_ec_ghosts(LevelMeta& L) {
+  L.ec_ghosts.clear();
+  L.ec_built = true;
+  const int nb = (int)L.boxes.size();
+  // per solve: buckets of side S (the largest box edge of the solve) holding the boxes that
+  // overlap them, so the owner of a cell is found among a few boxes
+  const int ns = (int)L.geoms.size();
+  std::vector<int> side(ns, 1);
+  for (int b = 0; b < nb; ++b)
+    for (int d = 0; d < 3; ++d) side[L.box_solve[b]] = std::max(side[L.box_solve[b]], L.boxes[b].n(d));
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> buckets;
+  auto bucket_of = [&](int s, const int g[3], int* k) {
+    for (int d = 0; d < 3; ++d) k[d] = (g[d] - L.geoms[s].domain.lo[d]) / side[s];
+  };
+  for (int b = 0; b < nb; ++b) {
+    const int s = L.box_solve[b];
+    int k0[3], k1[3];
+    bucket_of(s, L.boxes[b].lo, k0);
+    bucket_of(s, L.boxes[b].hi, k1);
+    for (int z = k0[2]; z <= k1[2]; ++z)
+      for (int y = k0[1]; y <= k1[1]; ++y)
+        for (int x = k0[0]; x <= k1[0]; ++x) buckets[std::make_tuple(s, x, y, z)].push_back(b);
+  }
+  for (int b = 0; b < nb; ++b) {
+    const Box& B = L.boxes[b];
+    const int s = L.box_solve[b];
+    const SolveGeom& G = L.geoms[s];
+    const DevBox& Db = L.dbox[b];
+    for (int k = -1; k <= B.n(2); ++k)
+      for (int j = -1; j <= B.n(1); ++j)
+        for (int i = -1; i <= B.n(0); ++i) {
+          const int loc[3] = {i, j, k};
+          int out = 0;
+          for (int d = 0; d < 3; ++d) out += (loc[d] < 0 || loc[d] >= B.n(d));
+          if (out < 2) continue;  // valid cells and face ghosts
+          int g[3];
+          double sign = 1.0;
+          for (int d = 0; d < 3; ++d) {
+            const int n = G.domain.n(d);
+            int rel = B.lo[d] + loc[d] - G.domain.lo[d];
+            if (rel < 0 || rel >= n) {
+              const int bc = rel < 0 ? G.bclo[d] : G.bchi[d];
+              if (bc == 0) {
+                rel = ((rel % n) + n) % n;
+              } else {
+                rel = rel < 0 ? -1 - rel : 2 * n - 1 - rel;
+                if (bc == 1) sign = -sign;
+              }
+            }
+            g[d] = G.domain.lo[d] + rel;
+          }
+          int kb[3];
+          bucket_of(s, g, kb);
+          int src = -1;
+          auto it = buckets.find(std::make_tuple(s, kb[0], kb[1], kb[2]));
+          if (it != buckets.end())
+            for (int c : it->second) {
+              const Box& C = L.boxes[c];
+              if (g[0] >= C.lo[0] && g[0] <= C.hi[0] && g[1] >= C.lo[1] && g[1] <= C.hi[1] && g[2] >= C.lo[2] &&
+                  g[2] <= C.hi[2]) {
+                src = c;
+                break;
+              }
+            }
+          if (src < 0) continue;  // (boxes cover every solve's domain on a multigrid level)
+          const DevBox& Ds = L.dbox[src];
+          const Box& S = L.boxes[src];
+          L.ec_ghosts.push_back({elem_index(Db, i, j, k),
+                                 elem_index(Ds, g[0] - S.lo[0], g[1] - S.lo[1], g[2] - S.lo[2]), sign});
+        }
   }
 }
 

@@ -90,6 +90,10 @@ struct LevelMeta {
   // per solve: 1 if the problem's coarse end (tail.cu) covers this level, so the V-cycle's
   // flow launches skip its items
   std::vector<int> vc_flow_skip;
+
+  // edge and corner ghosts (built on demand by build_ec_ghosts): f[dst] = sign * f[src]
+  std::vector<BotGhost> ec_ghosts;
+  bool ec_built = false;
 };
 
 // Tail tables: for every problem whose bottom level is small, the levels from the first
@@ -118,6 +122,13 @@ std::vector<Box> chop(const Box& dom, int max_grid_size);
 // Layout, ghost rectangles and work tables of a level whose boxes, box_solve, geoms and
 // solve_present/solve_bottom are set.  Returns "" or an error message.
 std::string finalize_level(LevelMeta& L);
+
+// Edge and corner ghost cells of every box of a level (face ghosts are the exchange's): the
+// source of ghost cell g is the valid cell that owns g under the homogeneous boundary rule
+// applied per axis -- a periodic axis wraps, a wall mirrors the index into the domain (ghost
+// -1 <-> cell 0) with the factor -1 for a Dirichlet wall and +1 for a Neumann wall.  Used by
+// the trilinear interpolation, which reads the coarse correction diagonally.
+void build_ec_ghosts(LevelMeta& L);
 
 // Rebuild a level's flow dispense orders for a dispense lag of `lag` cells (same sizes).
 void build_flow_order(LevelMeta& L, int64_t lag);

@@ -28,7 +28,8 @@ EXPORTS = [
     "gmg_chop_domain", "gmg_mg_nlevels", "gmg_mg_level_info", "gmg_mg_level_boxes", "gmg_mg_layout", "gmg_layout",
     "gmg_pack", "gmg_unpack", "gmg_set_scalars", "gmg_set_acoef", "gmg_set_bcoef_cell", "gmg_set_bcoef_face",
     "gmg_get_coeffs", "gmg_workspace_size", "gmg_set_workspace", "gmg_solve", "gmg_apply", "gmg_fill_boundary",
-    "gmg_smooth", "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_bottom_solve", "gmg_vcycle",
+    "gmg_smooth", "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_prolong_add_trilinear",
+    "gmg_bottom_solve", "gmg_vcycle",
     "gmg_box_bicgstab_noalloc", "gmg_define_batch", "gmg_num_solves", "gmg_solve_boxes", "gmg_pack_solve",
     "gmg_unpack_solve", "gmg_batch_solve", "gmg_amr_level_boxes", "gmg_pack_amr", "gmg_unpack_amr",
     "gmg_apply_transpose", "gmg_solve_adjoint", "gmg_beta_grad", "gmg_autotune", "gmg_tuned",
@@ -44,7 +45,7 @@ class Params(C.Structure):
                 ("vector_smooth", C.c_int), ("pdl", C.c_int), ("fuse_residual_sweep", C.c_int),
                 ("krylov", C.c_int), ("bottom_solver", C.c_int), ("post_reverse", C.c_int),
                 ("fuse_correction", C.c_int), ("settled_zero", C.c_int), ("flow_warps", C.c_int),
-                ("flow_lag_kcells", C.c_int), ("serpentine", C.c_int)]
+                ("flow_lag_kcells", C.c_int), ("serpentine", C.c_int), ("prolongation", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -85,6 +86,7 @@ def _declare(L):
     sig = {
         "gmg_default_params": [C.POINTER(Params)],
         "gmg_dfma_probe": [vp, C.c_int, C.c_int, f64p],
+        "gmg_prolong_add_trilinear": [vp, C.c_int, C.c_int, vp, vp],
         "gmg_create": [C.POINTER(C.c_void_p), vp],
         "gmg_destroy": [vp],
         "gmg_define_domain": [vp, i32p, i32p, f64p, f64p, i32p, i32p],

@@ -540,3 +540,79 @@ def test_settled_residuals_change_only_rounding(name):
             np.testing.assert_allclose(i1.history(), i0.history(), rtol=1e-9)
             if rev == 0 and push == 1 and C.nlevels > 1:
                 assert i1.kernel_launches >= i0.kernel_launches  # (the wall launches)
+
+
+# ------------------------------------------------------------ trilinear interpolation option
+
+
+@pytest.mark.parametrize("dt", DTS)
+def test_prolong_trilinear(pair, dt):
+    """Trilinear interpolation of a coarse field (its face, edge and corner ghosts filled by
+    the homogeneous boundary rule) added to a fine one, on every pair of MG levels: FP64 bit
+    for bit the oracle's (the same products and sums in the same order)."""
+    pair.P.set_prolong(trilinear=True)
+    try:
+        import ctypes as C
+
+        for m in range(pair.nlev - 1):
+            coarse = rand_level(pair, m + 1, 9500 + m, dt)
+            fine = rand_level(pair, m, 9600 + m, dt)
+            fb = pair.C.pack(torch.from_numpy(fine), m, dt)
+            cb = pair.C.pack(torch.from_numpy(coarse), m + 1, dt)
+            st = gmg.lib().gmg_prolong_add_trilinear(pair.C.h, m, dt, C.c_void_p(cb.data_ptr()),
+                                                     C.c_void_p(fb.data_ptr()))
+            assert st == gmg.OK
+            got = pair.C.unpack(fb, m, dt).cpu().numpy()
+            wf = pair.P.to_boxed(m, fine)
+            pair.P.prolong_add(m, pair.P.to_boxed(m + 1, coarse), wf)
+            want = pair.P.to_dense(m, wf)
+            if dt == gmg.DT_F64:
+                assert np.array_equal(got, want), m
+            else:
+                want = round_to(want, dt)
+                assert np.abs(got - want).max() <= STEP_TOL[dt] * np.abs(want).max(), m
+    finally:
+        pair.P.set_prolong(trilinear=False)
+
+
+@pytest.mark.parametrize("dt", DTS)
+def test_vcycle_trilinear(pair, dt):
+    """One V-cycle with trilinear interpolation of the coarse corrections against the oracle's."""
+    if pair.nlev < 2:
+        pytest.skip("a single level: the V-cycle is the bottom solve, nothing is interpolated")
+    r = rand_level(pair, 0, 9700, dt)
+    if pair.cfg["name"] == "periodic":
+        r = round_to(r - r.mean(), dt)
+    e = pair.C.vcycle(pair.C.pack(torch.from_numpy(r), 0, dt), dt, prolongation=1)
+    got = pair.C.unpack(e, 0, dt).cpu().numpy()
+    pair.P.set_prolong(trilinear=True)
+    try:
+        want = pair.P.to_dense(0, pair.P.vcycle(0, pair.P.to_boxed(0, r)))
+    finally:
+        pair.P.set_prolong(trilinear=False)
+    tol = {gmg.DT_F64: 1e-10, gmg.DT_F32: 2e-4, gmg.DT_BF16: 6e-2}[dt]
+    assert np.abs(got - want).max() <= tol * np.abs(want).max(), np.abs(got - want).max() / np.abs(want).max()
+
+
+def test_solve_trilinear(pair):
+    """The multigrid iteration with trilinear interpolation: the same iterates and residual
+    history as the oracle's for a fixed count, and to 1e-12 the same solution and count."""
+    if pair.nlev < 2:
+        pytest.skip("a single level: the V-cycle is the bottom solve, nothing is interpolated")
+    c = pair.cfg
+    rhs = pair.C.pack(torch.from_numpy(c["rhs"]))
+    pair.P.set_prolong(trilinear=True)
+    try:
+        phi, info = pair.C.solve(rhs, tol_rel=0.0, max_iter=4, prolongation=1)
+        got = pair.C.unpack(phi).cpu().numpy()
+        want, it, hist, st = pair.P.solve(c["rhs"], tol_rel=0.0, maxit=4)
+        assert info.iterations == it == 4
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+        np.testing.assert_allclose(np.array(info.history()), hist, rtol=1e-6, atol=1e-11 * hist[0])
+        phi, info = pair.C.solve(rhs, tol_rel=1e-12, max_iter=300, prolongation=1)
+        want, it, hist, st = pair.P.solve(c["rhs"], tol_rel=1e-12, maxit=300)
+        assert info.status == gmg.OK and st == O.OK
+        assert np.abs(pair.C.unpack(phi).cpu().numpy() - want).max() <= 1e-10 * np.abs(want).max()
+        assert abs(info.iterations - it) <= 1
+    finally:
+        pair.P.set_prolong(trilinear=False)
