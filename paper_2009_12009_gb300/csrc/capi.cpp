@@ -2382,6 +2382,83 @@ gmg_status gmg_mg_level_boxes(const gmg_ctx* c, int m, int* lohi, int* parents) 
   return GMG_OK;
 }
 
+// ------------------------------------------------------------- sharding plan (host only)
+
+namespace {
+// Morton (Z-order) key of a box's low corner: the bits of x, y, z interleaved
+uint64_t morton_key(const Box& b, const Box& dom) {
+  uint64_t k = 0;
+  const uint32_t x = (uint32_t)(b.lo[0] - dom.lo[0]), y = (uint32_t)(b.lo[1] - dom.lo[1]),
+                 z = (uint32_t)(b.lo[2] - dom.lo[2]);
+  for (int bit = 20; bit >= 0; --bit)
+    k = (k << 3) | (((z >> bit) & 1u) << 2) | (((y >> bit) & 1u) << 1) | ((x >> bit) & 1u);
+  return k;
+}
+}  // namespace
+
+gmg_status gmg_partition(const gmg_ctx* c, int m, int nranks, long long min_cells_per_rank, int* owner) {
+  if (!c || m < 0 || m >= (int)c->L.size() || nranks < 1 || !owner || min_cells_per_rank < 0)
+    return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = c->L[m];
+  const int nb = (int)M.boxes.size();
+  if (M.ncells < (int64_t)nranks * min_cells_per_rank || nranks == 1) {
+    for (int b = 0; b < nb; ++b) owner[b] = 0;  // consolidated onto rank 0
+    return GMG_OK;
+  }
+  std::vector<std::pair<std::pair<int, uint64_t>, int>> order(nb);  // ((solve, key), box)
+  for (int b = 0; b < nb; ++b)
+    order[b] = {{M.box_solve[b], morton_key(M.boxes[b], M.geoms[M.box_solve[b]].domain)}, b};
+  std::sort(order.begin(), order.end());
+  // cut the curve into nranks pieces of about equal cell counts: box i goes to the rank in
+  // whose share the middle of its cells falls
+  int64_t before = 0;
+  for (const auto& o : order) {
+    const int64_t v = M.boxes[o.second].volume();
+    const double mid = (double)before + 0.5 * (double)v;
+    owner[o.second] = std::min(nranks - 1, (int)(mid * nranks / (double)M.ncells));
+    before += v;
+  }
+  return GMG_OK;
+}
+
+gmg_status gmg_ghost_rects(const gmg_ctx* c, int m, int* n, int* rects) {
+  if (!c || m < 0 || m >= (int)c->L.size() || !n) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = c->L[m];
+  *n = (int)M.ghosts.size();
+  if (rects)
+    for (size_t r = 0; r < M.ghosts.size(); ++r) {
+      const GhostRect& g = M.ghosts[r];
+      const int v[14] = {g.dst_box, g.src_box, g.dst[0], g.dst[1], g.dst[2], g.src[0], g.src[1], g.src[2],
+                         g.d1,      g.d2,      g.n1,     g.n2,     g.sign,   g.kind};
+      for (int q = 0; q < 14; ++q) rects[14 * r + q] = v[q];
+    }
+  return GMG_OK;
+}
+
+gmg_status gmg_exchange_plan(const gmg_ctx* c, int m, const int* owner, int rank, int* nsend, int* send, int* nrecv,
+                             int* recv) {
+  if (!c || m < 0 || m >= (int)c->L.size() || !owner || !nsend || !nrecv) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = c->L[m];
+  std::vector<std::pair<int, int>> s, r;  // (peer, rectangle)
+  for (int q = 0; q < (int)M.ghosts.size(); ++q) {
+    const GhostRect& g = M.ghosts[q];
+    if (g.kind != 0) continue;  // walls are filled where their box lives
+    const int od = owner[g.dst_box], os = owner[g.src_box];
+    if (od == os) continue;
+    if (os == rank) s.push_back({od, q});
+    if (od == rank) r.push_back({os, q});
+  }
+  std::sort(s.begin(), s.end());
+  std::sort(r.begin(), r.end());
+  *nsend = (int)s.size();
+  *nrecv = (int)r.size();
+  if (send)
+    for (size_t i = 0; i < s.size(); ++i) { send[2 * i] = s[i].first; send[2 * i + 1] = s[i].second; }
+  if (recv)
+    for (size_t i = 0; i < r.size(); ++i) { recv[2 * i] = r[i].first; recv[2 * i + 1] = r[i].second; }
+  return GMG_OK;
+}
+
 gmg_status gmg_mg_layout(const gmg_ctx* c, int m, int dt, int64_t* nelems, int64_t* offs, int* sx) {
   if (!c || m < 0 || m >= (int)c->L.size() || dt < 0 || dt >= NDT) return GMG_ERR_BAD_INPUT;
   const LevelMeta& M = c->L[m];

@@ -34,6 +34,7 @@ EXPORTS = [
     "gmg_unpack_solve", "gmg_batch_solve", "gmg_amr_level_boxes", "gmg_pack_amr", "gmg_unpack_amr",
     "gmg_apply_transpose", "gmg_solve_adjoint", "gmg_beta_grad", "gmg_autotune", "gmg_tuned",
     "gmg_wall_values_rhs", "gmg_wall_values_grad", "gmg_beta_grad_walls", "gmg_dfma_probe",
+    "gmg_partition", "gmg_ghost_rects", "gmg_exchange_plan",
 ]
 
 
@@ -87,6 +88,9 @@ def _declare(L):
         "gmg_default_params": [C.POINTER(Params)],
         "gmg_dfma_probe": [vp, C.c_int, C.c_int, f64p],
         "gmg_prolong_add_trilinear": [vp, C.c_int, C.c_int, vp, vp],
+        "gmg_partition": [vp, C.c_int, C.c_int, C.c_longlong, i32p],
+        "gmg_ghost_rects": [vp, C.c_int, i32p, i32p],
+        "gmg_exchange_plan": [vp, C.c_int, i32p, C.c_int, i32p, i32p, i32p, i32p],
         "gmg_create": [C.POINTER(C.c_void_p), vp],
         "gmg_destroy": [vp],
         "gmg_define_domain": [vp, i32p, i32p, f64p, f64p, i32p, i32p],
@@ -287,6 +291,37 @@ class Context:
             blk = buf[off:off + sx * (n[1] + 2) * (n[2] + 2)].view(n[2] + 2, n[1] + 2, sx)
             out.append(blk[:, :, GX - 1:GX + n[0] + 1])
         return out
+
+    # ---- sharding plan (host tables; the solves run on one GPU) ---------------------
+    def partition(self, m, nranks, min_cells_per_rank=0):
+        """owner rank of every box of MG level m (Morton curve cut by cell counts)"""
+        nb, _ = self.level_info(m)
+        own = (C.c_int * nb)()
+        self._check(self.L.gmg_partition(self.h, m, nranks, int(min_cells_per_rank), own))
+        return list(own)
+
+    def ghost_rects(self, m):
+        """face-ghost rectangles of MG level m: list of dicts (see gmg_ghost_rects)"""
+        n = C.c_int()
+        self._check(self.L.gmg_ghost_rects(self.h, m, C.byref(n), None))
+        raw = (C.c_int * (14 * n.value))()
+        self._check(self.L.gmg_ghost_rects(self.h, m, C.byref(n), raw))
+        keys = ("dst_box", "src_box", "dst", "src", "d1", "d2", "n1", "n2", "sign", "kind")
+        out = []
+        for r in range(n.value):
+            v = raw[14 * r:14 * r + 14]
+            out.append(dict(zip(keys, (v[0], v[1], tuple(v[2:5]), tuple(v[5:8]), v[8], v[9], v[10], v[11], v[12],
+                                       v[13]))))
+        return out
+
+    def exchange_plan(self, m, owner, rank):
+        """(send, recv): lists of (peer, rectangle index) for this rank under owner[]"""
+        own = (C.c_int * len(owner))(*owner)
+        ns, nr = C.c_int(), C.c_int()
+        self._check(self.L.gmg_exchange_plan(self.h, m, own, rank, C.byref(ns), None, C.byref(nr), None))
+        s, r = (C.c_int * (2 * ns.value))(), (C.c_int * (2 * nr.value))()
+        self._check(self.L.gmg_exchange_plan(self.h, m, own, rank, C.byref(ns), s, C.byref(nr), r))
+        return ([(s[2 * i], s[2 * i + 1]) for i in range(ns.value)], [(r[2 * i], r[2 * i + 1]) for i in range(nr.value)])
 
     # ---- dense <-> boxed --------------------------------------------------------
     def pack(self, dense, m=0, dt=DT_F64, out=None):
