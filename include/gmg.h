@@ -606,20 +606,24 @@ gmg_status gmg_box_bicgstab_noalloc(void* cuda_stream, int nx, int ny, int nz, c
    Solvers": coarse multigrid levels consolidated onto fewer processes).  These calls build
    the tables only: every solve of this library runs on one GPU.  Host pointers throughout. */
 
-/* Owner rank of every box of MG level m (owner: nboxes ints): boxes sorted along a Morton
+/* Sec. "Basic data structures" (DistributionMapping by a space-filling curve) and Sec.
+   "Linear Solvers" (coarse levels consolidated):
+   Owner rank of every box of MG level m (owner: nboxes ints): boxes sorted along a Morton
    (Z-order) curve of their low corners (problem by problem), the curve cut into nranks
    pieces of about equal cell counts.  A level with fewer than nranks * min_cells_per_rank
    cells is consolidated: every box on rank 0. */
 gmg_status gmg_partition(const gmg_ctx* ctx, int m, int nranks, long long min_cells_per_rank, int* owner);
 
-/* The face-ghost rectangles of MG level m: *n receives the count; rects (may be NULL) gets
+/* Sec. "Communication" (the cached metadata of the ghost-cell exchange):
+   The face-ghost rectangles of MG level m: *n receives the count; rects (may be NULL) gets
    14 ints per rectangle: dst_box, src_box, dst[3], src[3] (local coordinates of the first
    ghost cell and of its source cell), d1, d2 (tangential axes, d1 fastest), n1, n2
    (extents), sign (+1 copy or Neumann mirror, -1 Dirichlet reflection), kind (0 copy from a
    box of the level, periodic images included; 1 wall). */
 gmg_status gmg_ghost_rects(const gmg_ctx* ctx, int m, int* n, int* rects);
 
-/* Exchange plan of rank `rank` under owner[] (nboxes ints): the copy rectangles whose
+/* Sec. "Communication" (ghost-cell exchange between processes):
+   Exchange plan of rank `rank` under owner[] (nboxes ints): the copy rectangles whose
    source box and destination box have different owners.  send (may be NULL): *nsend pairs
    (peer, rectangle) with the source on this rank; recv: *nrecv pairs with the destination
    on this rank; both sorted by (peer, rectangle), so a sender and its receiver list the
