@@ -60,6 +60,7 @@
 #define ORC_PERIODIC 0
 #define ORC_DIRICHLET 1
 #define ORC_NEUMANN 2
+#define ORC_DIRICHLET_QUAD 3 /* accepted by orc_create: a Dirichlet side whose ghosts take the quadratic rule */
 #define ORC_MAXLEV 32
 
 typedef struct {
@@ -67,6 +68,7 @@ typedef struct {
   int *lo, *hi;          /* 3*nb, inclusive cell indices in this level's index space */
   int dlo[3], dhi[3];    /* domain box at this level, inclusive */
   int bclo[3], bchi[3];  /* boundary condition per side */
+  int qlo[3], qhi[3];    /* 1: that Dirichlet side extrapolates quadratically (ghost_quad) */
   double h[3];           /* cell size */
   int64_t *off;          /* offset of box b's ghosted array inside a level field */
   int64_t ntot;          /* total length of a level field */
@@ -75,6 +77,10 @@ typedef struct {
   int64_t ng;
   int64_t *gdst, *gsrc;
   double *gfac;
+  /* quadratic Dirichlet ghosts: the second interior cell inward (the ghost is
+     -2 f[gsrc] + f[gsrc2] / 3); -1 for every other entry */
+  int64_t *gsrc2;
+  int64_t *ginv;         /* element -> ghost-map entry (-1: none), built on first use */
   /* per ghost-map entry at a physical wall: the wall face (2*d + side) and the index of
      the ghost's tangential position in that face's value array; gwall = -1 elsewhere */
   int *gwall;
@@ -162,6 +168,7 @@ static void build_ghost_map(olev* l) {
   l->gfac = (double*)malloc(sizeof(double) * (cap + 1));
   l->gwall = (int*)malloc(sizeof(int) * (cap + 1));
   l->gtan = (int64_t*)malloc(sizeof(int64_t) * (cap + 1));
+  l->gsrc2 = (int64_t*)malloc(sizeof(int64_t) * (cap + 1));
   int64_t n = 0;
   for (int b = 0; b < l->nb; ++b) {
     for (int d = 0; d < 3; ++d) {
@@ -185,6 +192,7 @@ static void build_ghost_map(olev* l) {
             }
             l->gwall[n] = -1;
             l->gtan[n] = 0;
+            l->gsrc2[n] = -1;
             if (outside) {
               /* wall: ghost = -(adjacent interior cell) at a Dirichlet wall, +(adjacent
                  interior cell) at a Neumann wall; the wall value's part is added by
@@ -198,6 +206,13 @@ static void build_ghost_map(olev* l) {
               l->gfac[n] = bc == ORC_NEUMANN ? 1.0 : -1.0;
               l->gwall[n] = 2 * d + side;
               l->gtan[n] = (int64_t)(g[t1] - l->dlo[t1]) + (int64_t)(l->dhi[t1] - l->dlo[t1] + 1) * (g[t2] - l->dlo[t2]);
+              if (bc == ORC_DIRICHLET && (side ? l->qhi[d] : l->qlo[d]) && bn(l, b, d) >= 2) {
+                /* quadratic rule: the parabola through the wall value (on the face) and the
+                   two interior cell centres, read at the ghost's centre */
+                in[d] = side ? bn(l, b, d) - 2 : 1;
+                l->gsrc2[n] = IX(l, b, in[0], in[1], in[2]);
+                l->gfac[n] = -2.0;
+              }
             } else {
               int ob = find_box(l, g);
               l->gdst[n] = dst;
@@ -223,8 +238,25 @@ static void build_ghost_map(olev* l) {
    (or the physical boundary condition). */
 static void fill_ghosts(const olev* l, double* f) {
   #pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
-  for (int64_t q = 0; q < l->ng; ++q)
-    if (l->gsrc[q] >= 0) f[l->gdst[q]] = l->gfac[q] * f[l->gsrc[q]];
+  for (int64_t q = 0; q < l->ng; ++q) {
+    if (l->gsrc2[q] >= 0)
+      f[l->gdst[q]] = -2.0 * f[l->gsrc[q]] + f[l->gsrc2[q]] / 3.0;
+    else if (l->gsrc[q] >= 0)
+      f[l->gdst[q]] = l->gfac[q] * f[l->gsrc[q]];
+  }
+}
+
+/* Dirichlet wall order, per side: the homogeneous ghost of a box's wall cell phi_0 is
+   -phi_0 (linear: the line through phi_0 and 0 on the face), or, where the side is quadratic
+   and the box has two cells along the wall normal, -2 phi_0 + phi_1 / 3 (the parabola
+   through 0 on the face, phi_0 and the next cell inward phi_1, read half a cell outside
+   the face).  A wall value g adds 2 g (linear) or 8 g / 3 (quadratic). */
+static int quad_face(const olev* l, int b, const int c[3], int d, int side) {
+  int n = bn(l, b, d);
+  if (n < 2 || c[d] != (side ? n - 1 : 0)) return 0;
+  int g = l->lo[3 * b + d] + c[d] + (side ? 1 : -1);
+  if (g >= l->dlo[d] && g <= l->dhi[d]) return 0;
+  return (side ? l->bchi[d] : l->bclo[d]) == ORC_DIRICHLET && (side ? l->qhi[d] : l->qlo[d]);
 }
 
 /* a level with no Dirichlet wall has the constants in the null space of A when a = 0 */
@@ -245,6 +277,7 @@ static int covers_domain(const olev* l) {
 
 static void free_level(olev* l) {
   free(l->lo); free(l->hi); free(l->off); free(l->gdst); free(l->gsrc); free(l->gfac); free(l->gwall); free(l->gtan);
+  free(l->gsrc2); free(l->ginv);
   free(l->parent); free(l->alpha); free(l->bx); free(l->by); free(l->bz);
   free(l->e); free(l->r); free(l->t);
   memset(l, 0, sizeof(*l));
@@ -281,6 +314,8 @@ static int make_coarse(const olev* f, olev* c) {
     c->dhi[d] = (f->dhi[d] + 1) / 2 - 1;
     c->bclo[d] = f->bclo[d];
     c->bchi[d] = f->bchi[d];
+    c->qlo[d] = f->qlo[d];
+    c->qhi[d] = f->qhi[d];
     c->h[d] = 2.0 * f->h[d];
   }
   c->nb = per_box ? nb : 1;
@@ -319,14 +354,16 @@ void* orc_create(const int* dlo, const int* dhi, const int* bclo, const int* bch
   for (int d = 0; d < 3; ++d) {
     l->dlo[d] = dlo[d];
     l->dhi[d] = dhi[d];
-    l->bclo[d] = bclo[d];
-    l->bchi[d] = bchi[d];
+    l->qlo[d] = bclo[d] == ORC_DIRICHLET_QUAD;
+    l->qhi[d] = bchi[d] == ORC_DIRICHLET_QUAD;
+    l->bclo[d] = l->qlo[d] ? ORC_DIRICHLET : bclo[d];
+    l->bchi[d] = l->qhi[d] ? ORC_DIRICHLET : bchi[d];
     l->h[d] = (phi_[d] - plo[d]) / (double)(dhi[d] - dlo[d] + 1);
   }
   /* validity: boxes inside the domain and pairwise disjoint; periodic on both sides */
   for (int d = 0; d < 3; ++d)
-    if ((bclo[d] == ORC_PERIODIC) != (bchi[d] == ORC_PERIODIC) || bclo[d] < 0 || bclo[d] > 2 || bchi[d] < 0 ||
-        bchi[d] > 2) {
+    if ((bclo[d] == ORC_PERIODIC) != (bchi[d] == ORC_PERIODIC) || bclo[d] < 0 || bclo[d] > 3 || bchi[d] < 0 ||
+        bchi[d] > 3) {
       free(l->lo); free(l->hi); free(p); return NULL;
     }
   for (int b = 0; b < nb; ++b) {
@@ -589,7 +626,11 @@ void orc_fill_ghosts(void* vp, int m, double* f) { fill_ghosts(&((oprob*)vp)->L[
    global (i+j+k) parity equals `colour`, solve its row for phi using the current
    neighbour values:
      phi = (rhs + b*sum_f h_f^-2 beta_f phi_nbr) / (a*alpha + b*sum_f h_f^-2 beta_f),
-   faces taken in the order x-, x+, y-, y+, z-, z+. */
+   faces taken in the order x-, x+, y-, y+, z-, z+.  A face on a quadratic Dirichlet wall is
+   taken into the row exactly: its ghost -2 phi + phi_1 / 3 depends on the cell itself, so
+   the face adds w_f phi_1 / 3 to the numerator and (1 - (-2)) w_f = 3 w_f to the
+   denominator (the cell's row solved exactly, as Gauss-Seidel does; the linear wall's
+   ghost -phi is taken from the ghost fill, as every other neighbour). */
 void orc_smooth_colour(void* vp, int m, double* phi, const double* rhs, int colour) {
   oprob* p = (oprob*)vp;
   olev* l = &p->L[m];
@@ -609,6 +650,26 @@ void orc_smooth_colour(void* vp, int m, double* phi, const double* rhs, int colo
                        wym * phi[IX(l, b, i, j - 1, k)] + wyp * phi[IX(l, b, i, j + 1, k)] +
                        wzm * phi[IX(l, b, i, j, k - 1)] + wzp * phi[IX(l, b, i, j, k + 1)];
           double den = wxm + wxp + wym + wyp + wzm + wzp;
+          const int c[3] = {i, j, k};
+          int quad = 0;
+          for (int d = 0; d < 3; ++d) quad |= quad_face(l, b, c, d, 0) | quad_face(l, b, c, d, 1);
+          if (quad) { /* face by face, in the same order */
+            const double w[6] = {wxm, wxp, wym, wyp, wzm, wzp};
+            num = 0.0;
+            den = 0.0;
+            for (int f = 0; f < 6; ++f) {
+              int d = f / 2, side = f % 2, nb[3] = {i, j, k}, in2[3] = {i, j, k};
+              nb[d] += side ? 1 : -1;
+              if (quad_face(l, b, c, d, side)) {
+                in2[d] += side ? -1 : 1;
+                num += w[f] * (phi[IX(l, b, in2[0], in2[1], in2[2])] / 3.0);
+                den += 3.0 * w[f];
+              } else {
+                num += w[f] * phi[IX(l, b, nb[0], nb[1], nb[2])];
+                den += w[f];
+              }
+            }
+          }
           phi[IX(l, b, i, j, k)] =
               (rhs[IX(l, b, i, j, k)] + p->b * num) / (p->a * l->alpha[IX(l, b, i, j, k)] + p->b * den);
         }
@@ -936,8 +997,8 @@ int orc_set_bc_values(void* vp, int face, const double* values) {
 }
 
 /* level-0 ghosts with the wall values: the homogeneous ghost plus 2g (Dirichlet: the
-   line through the interior value and g on the face) or h*g (Neumann: the one-sided
-   difference across the face equals g) */
+   line through the interior value and g on the face; 8g/3 for the parabola of the
+   quadratic rule) or h*g (Neumann: the one-sided difference across the face equals g) */
 static void fill_ghosts_bc(const oprob* p, double* f) {
   const olev* l = &p->L[0];
   fill_ghosts(l, f);
@@ -947,7 +1008,7 @@ static void fill_ghosts_bc(const oprob* p, double* f) {
     int d = w / 2, side = w % 2;
     double g = p->bcval[w][l->gtan[q]];
     int bc = side ? l->bchi[d] : l->bclo[d];
-    f[l->gdst[q]] += bc == ORC_NEUMANN ? l->h[d] * g : 2.0 * g;
+    f[l->gdst[q]] += bc == ORC_NEUMANN ? l->h[d] * g : (l->gsrc2[q] >= 0 ? 8.0 * g / 3.0 : 2.0 * g);
   }
 }
 
@@ -987,7 +1048,7 @@ void orc_apply_bc(void* vp, const double* phi_dense, double* out_dense) {
    dL/dphi).  dL/dbeta = lambda^T d(rhs - A phi)/dbeta: the row of cell q holds, per face
    f, -b beta_f (phi_nbr - phi_q) / h^2, so face f adds lambda_q b (phi_nbr - phi_q) / h^2
    for each of its (one or two) rows, with phi_nbr the neighbour or, at a wall, the ghost
-   of the wall rule (wall values included).  The face sum then goes to the cells through
+   of the wall rule (wall values included; the quadratic rule's ghost where it applies).  The face sum then goes to the cells through
    the rule that made beta_f: harmonic mean 2 bL bR / (bL + bR), derivative 2 bR^2 /
    (bL + bR)^2 for bL; a wall face takes the interior cell's beta, derivative 1.
    Dense arrays over the domain (x fastest); beta_dense is the cell beta given to
@@ -1019,10 +1080,18 @@ void orc_grad_beta_cells(void* vp, const double* phi_dense, const double* lam_de
             }
             if (outside) {
               double ghost = bc == ORC_NEUMANN ? phi_dense[q] : -phi_dense[q];
+              int gc[3] = {l->dlo[0] + c[0], l->dlo[1] + c[1], l->dlo[2] + c[2]}, bx = find_box(l, gc), lc[3];
+              for (int e = 0; e < 3; ++e) lc[e] = gc[e] - l->lo[3 * bx + e];
+              const int quad = quad_face(l, bx, lc, d, side);
+              if (quad) {
+                int in[3] = {c[0], c[1], c[2]};
+                in[d] += side ? -1 : 1;
+                ghost = -2.0 * phi_dense[q] + phi_dense[in[0] + (int64_t)n[0] * (in[1] + (int64_t)n[1] * in[2])] / 3.0;
+              }
               const double* gv = p->bcval[2 * d + side];
               if (gv) {
                 double g = gv[(int64_t)c[t1] + (int64_t)n[t1] * c[t2]];
-                ghost += bc == ORC_NEUMANN ? l->h[d] * g : 2.0 * g;
+                ghost += bc == ORC_NEUMANN ? l->h[d] * g : (quad ? 8.0 * g / 3.0 : 2.0 * g);
               }
               out_dense[q] += lam_dense[q] * w * (ghost - phi_dense[q]);
               continue;
@@ -1040,7 +1109,8 @@ void orc_grad_beta_cells(void* vp, const double* phi_dense, const double* lam_de
 }
 
 /* dL/dg on wall face `face` (= 2*d + side): the wall values enter rhs - A 0 of the wall
-   cell q as +2 b beta_f g / h^2 (Dirichlet) or +b beta_f g / h (Neumann), so
+   cell q as +2 b beta_f g / h^2 (Dirichlet; 8/3 in place of 2 under the quadratic rule) or
+   +b beta_f g / h (Neumann), so
    dL/dg = lambda_q times that factor.  out: the face's value layout (tangential axes in
    increasing order, the lower one fastest). */
 int orc_grad_wall_values(void* vp, const double* lam_dense, int face, double* out) {
@@ -1065,7 +1135,9 @@ int orc_grad_wall_values(void* vp, const double* lam_dense, int face, double* ou
       if (side) fl[d] += 1; /* the wall face's slot */
       double beta_f = fa[IX(l, b, fl[0], fl[1], fl[2])];
       double h = l->h[d];
-      double fac = bc == ORC_NEUMANN ? p->b * beta_f / h : 2.0 * p->b * beta_f / (h * h);
+      int lc[3] = {g[0] - l->lo[3 * b], g[1] - l->lo[3 * b + 1], g[2] - l->lo[3 * b + 2]};
+      double wg = quad_face(l, b, lc, d, side) ? 8.0 / 3.0 : 2.0;
+      double fac = bc == ORC_NEUMANN ? p->b * beta_f / h : wg * p->b * beta_f / (h * h);
       out[u + (int64_t)n[t1] * v] = lam_dense[c[0] + (int64_t)n[0] * (c[1] + (int64_t)n[1] * c[2])] * fac;
     }
   return 0;
@@ -1260,6 +1332,67 @@ void orc_apply(void* vp, const double* phi_dense, double* out_dense) {
   free(phi); free(out);
 }
 
+/* ghost-map entry that fills element e of level l, or -1 (a valid cell, or an edge or corner
+   ghost) */
+static int64_t ghost_entry(olev* l, int64_t e) {
+  if (!l->ginv) {
+    l->ginv = (int64_t*)malloc(sizeof(int64_t) * (l->ntot + 1));
+    for (int64_t q = 0; q < l->ntot; ++q) l->ginv[q] = -1;
+    for (int64_t q = 0; q < l->ng; ++q) l->ginv[l->gdst[q]] = q;
+  }
+  return l->ginv[e];
+}
+
+/* x = A^T y on level 0 with homogeneous walls, dense arrays.  Straight from the definition
+   (A^T y)_c = sum_r A[r][c] y_r: every row r of the operator (the 7-point stencil of
+   op_cell) is expanded into its matrix entries -- a neighbour that is a ghost cell stands
+   for the cells the ghost map fills it from, with the map's factors (a linear Dirichlet
+   wall's ghost -phi_0 lands on the diagonal, the quadratic rule's -2 phi_0 + phi_1 / 3 on
+   the diagonal and on the next cell inward) -- and y_r times each entry is added to x at
+   the entry's column.  Sequential (the scatter crosses boxes). */
+void orc_apply_transpose(void* vp, const double* y_dense, double* x_dense) {
+  oprob* p = (oprob*)vp;
+  olev* l = &p->L[0];
+  double* y = (double*)calloc(l->ntot, sizeof(double));
+  double* x = (double*)calloc(l->ntot, sizeof(double));
+  orc_dense_to_boxed(vp, 0, y_dense, y);
+  for (int b = 0; b < l->nb; ++b)
+    for (int k = 0; k < bn(l, b, 2); ++k)
+      for (int j = 0; j < bn(l, b, 1); ++j)
+        for (int i = 0; i < bn(l, b, 0); ++i) {
+          const int64_t r = IX(l, b, i, j, k);
+          const double yr = y[r];
+          double diag = p->a * l->alpha[r];
+          for (int d = 0; d < 3; ++d) {
+            const double* bf = d == 0 ? l->bx : (d == 1 ? l->by : l->bz);
+            for (int side = 0; side < 2; ++side) {
+              int nb[3] = {i, j, k}, up[3] = {i, j, k};
+              nb[d] += side ? 1 : -1;
+              up[d] += side ? 1 : 0; /* face slot: the face at i - 1/2 is stored at i */
+              const double w = p->b * bf[IX(l, b, up[0], up[1], up[2])] / (l->h[d] * l->h[d]);
+              diag += w; /* -b * (-beta_f phi_r) / h^2 */
+              const int64_t e = IX(l, b, nb[0], nb[1], nb[2]);
+              const int inside = nb[d] >= 0 && nb[d] < bn(l, b, d);
+              if (inside) {
+                x[e] -= w * yr;
+                continue;
+              }
+              const int64_t g = ghost_entry(l, e);
+              if (g < 0 || l->gsrc[g] < 0) continue; /* not filled from this level */
+              if (l->gsrc2[g] >= 0) {
+                x[l->gsrc[g]] -= w * (-2.0) * yr;
+                x[l->gsrc2[g]] -= w * (1.0 / 3.0) * yr;
+              } else {
+                x[l->gsrc[g]] -= w * l->gfac[g] * yr;
+              }
+            }
+          }
+          x[r] += diag * yr;
+        }
+  orc_boxed_to_dense(vp, 0, x, x_dense);
+  free(y); free(x);
+}
+
 /* =====================================================================
  * Two-level composite problem (Sec. "Operations between levels", Sec. "Linear
  * Solvers": multi-AMR-level geometric multigrid).  Level 0 (coarse) covers the domain;
@@ -1405,6 +1538,8 @@ static void amr_free_tables(oamr* A) {
 
 void* orc_amr_create(const int* dlo, const int* dhi, const int* bclo, const int* bchi, const double* plo,
                      const double* phi_, int nbc, const int* cboxes, int nbf, const int* fboxes) {
+  for (int d = 0; d < 3; ++d) /* composite operators take the linear Dirichlet rule only */
+    if (bclo[d] == ORC_DIRICHLET_QUAD || bchi[d] == ORC_DIRICHLET_QUAD) return NULL;
   oamr* A = (oamr*)calloc(1, sizeof(oamr));
   A->C = (oprob*)orc_create(dlo, dhi, bclo, bchi, plo, phi_, nbc, cboxes);
   int fdlo[3], fdhi[3];
@@ -2065,6 +2200,8 @@ void orc_mlv_destroy(void* vp) {
 void* orc_mlv_create(const int* dlo, const int* dhi, const int* bclo, const int* bchi, const double* plo,
                      const double* phi_, int L, const int* nboxes, const int* boxes) {
   if (L < 1 || L > ORC_MAXAMR) return NULL;
+  for (int d = 0; d < 3; ++d) /* composite operators take the linear Dirichlet rule only */
+    if (bclo[d] == ORC_DIRICHLET_QUAD || bchi[d] == ORC_DIRICHLET_QUAD) return NULL;
   omlv* M = (omlv*)calloc(1, sizeof(omlv));
   M->L = L;
   int off = 0;

@@ -108,6 +108,7 @@ def _declare(L):
     L.orc_solve.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_double, C.c_int, C.c_int, _f64p, _i32p]
     L.orc_solve.restype = C.c_int
     L.orc_apply.argtypes = [C.c_void_p, _f64p, _f64p]
+    L.orc_apply_transpose.argtypes = [C.c_void_p, _f64p, _f64p]
     L.orc_set_cycle.argtypes = [C.c_void_p, C.c_int, C.c_int]
     L.orc_solve_krylov.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
                                    _f64p, _i32p]
@@ -140,8 +141,8 @@ class Problem:
     """Single-level problem on a BoxArray with its multigrid hierarchy.
 
     domain: (lo[3], hi[3]) inclusive; boxes: list of (lo[3], hi[3]) inclusive;
-    bc_lo/bc_hi: PERIODIC, DIRICHLET or NEUMANN per direction; prob_lo/prob_hi: physical
-    extent.  Walls are homogeneous unless set_bc_values gives them values.
+    bc_lo/bc_hi: PERIODIC, DIRICHLET, NEUMANN or DIRICHLET_QUAD (a Dirichlet side with the
+    quadratic ghost rule) per direction; prob_lo/prob_hi: physical extent.  Walls are homogeneous unless set_bc_values gives them values.
     """
 
     def __init__(self, domain, boxes, bc_lo, bc_hi, prob_lo=(0.0, 0.0, 0.0), prob_hi=(1.0, 1.0, 1.0)):
@@ -309,6 +310,13 @@ class Problem:
         phi = _f64(phi)
         out = np.zeros(self.level_shape(0))
         lib().orc_apply(self.h, _dp(phi), _dp(out))
+        return out
+
+    def apply_transpose(self, y):
+        """A^T y with homogeneous walls, from the matrix entries of A's rows (sequential)."""
+        y = _f64(y)
+        out = np.zeros(self.level_shape(0))
+        lib().orc_apply_transpose(self.h, _dp(y), _dp(out))
         return out
 
     # wall values ----------------------------------------------------------------

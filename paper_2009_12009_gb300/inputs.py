@@ -21,6 +21,7 @@ import numpy as np
 PERIODIC = 0
 DIRICHLET = 1
 NEUMANN = 2
+DIRICHLET_QUAD = 3  # Dirichlet side whose ghosts take the quadratic rule
 
 SEEDS = {"poisson32": 12010, "abec256": 12011, "abec512": 12012, "batch64": 12013, "amr2": 12014,
          "walls256": 12015, "contrast256": 12016, "amr3": 12017}
