@@ -67,8 +67,24 @@ typedef enum {
    interior cell's.  Nonzero wall values (phi = g on a Dirichlet face, outward normal
    derivative g on a Neumann face) enter through gmg_wall_values_rhs.  A problem without a
    Dirichlet wall and with a = 0 is singular (constants in the null space).
-   GMG_BC_DIRICHLET0 is the older name of GMG_BC_DIRICHLET. */
-typedef enum { GMG_BC_PERIODIC = 0, GMG_BC_DIRICHLET = 1, GMG_BC_DIRICHLET0 = 1, GMG_BC_NEUMANN = 2 } gmg_bc;
+   GMG_BC_DIRICHLET0 is the older name of GMG_BC_DIRICHLET.
+   GMG_BC_DIRICHLET_QUAD: a Dirichlet side whose ghost is the parabola through the wall
+   value and the two nearest interior cells, read half a cell outside the face: ghost =
+   8g/3 - 2 phi_0 + phi_1 / 3 (exact for quadratics; the linear rule 2g - phi_0 is exact for
+   linear functions only).  Boxes one cell thick along the wall normal keep the linear rule.
+   The operator is then not symmetric: a wall cell's row holds the extra entry
+   -b beta_f / (3 h^2) on phi_1.  Gauss-Seidel solves each wall cell's row exactly (the
+   -2 phi_0 part is in the diagonal).  Taken on every multigrid level.  Not offered with:
+   composite (AMR) contexts, conjugate gradients (krylov = 2, bottom_solver = 1),
+   trilinear interpolation (prolongation = 1).  The transpose, adjoint solve and beta
+   gradient of a one-level context take it into account. */
+typedef enum {
+  GMG_BC_PERIODIC = 0,
+  GMG_BC_DIRICHLET = 1,
+  GMG_BC_DIRICHLET0 = 1,
+  GMG_BC_NEUMANN = 2,
+  GMG_BC_DIRICHLET_QUAD = 3
+} gmg_bc;
 
 /* Arithmetic of the V-cycle.  FP64: everything in double.  MIXED_FP32: the V-cycle
    (smoothing, residual, restriction, interpolation) runs in float inside an FP64
@@ -333,7 +349,8 @@ gmg_status gmg_set_bcoef_cell(gmg_ctx* ctx, int lev, const double* beta_cc);
 gmg_status gmg_set_bcoef_face(gmg_ctx* ctx, int lev, const double* bx, const double* by, const double* bz);
 
 /* Scaled face weights w_d = b * beta_d / h_d^2 and diagonal D = a*alpha + sum of the six
-   weights of MG level m (the discrete operator of Sec. "Linear Solvers" on that level),
+   weights (plus 2 w_f per quadratic Dirichlet wall face f of the cell) of MG level m (the
+   discrete operator of Sec. "Linear Solvers" on that level),
    copied into caller buffers of element type dt (NULL to skip). */
 gmg_status gmg_get_coeffs(gmg_ctx* ctx, int m, int dt, void* wx, void* wy, void* wz, void* diag);
 
@@ -342,7 +359,9 @@ gmg_status gmg_get_coeffs(gmg_ctx* ctx, int m, int dt, void* wx, void* wy, void*
 /* Bytes of device workspace needed for solves with parameters p (NULL = defaults; a
    mixed precision needs its float buffers in addition to the FP64 ones).  The workspace
    plays the part of the pre-allocated memory pool of Sec. "Memory management" (one large
-   block handed out in pieces), except that the caller allocates it. */
+   block handed out in pieces), except that the caller allocates it.  A context with a
+   quadratic Dirichlet side (GMG_BC_DIRICHLET_QUAD) always includes the Krylov vectors
+   (its adjoint solve is a BiCGStab on A^T). */
 gmg_status gmg_workspace_size(const gmg_ctx* ctx, const gmg_params* p, size_t* bytes);
 
 /* Hand the library a device buffer of at least gmg_workspace_size bytes, 256-byte
@@ -382,7 +401,9 @@ gmg_status gmg_apply(gmg_ctx* ctx, void* const* out, void* const* phi);
 
 /* out = A^T y, the transpose of the operator of Sec. "Linear Solvers" (the transpose
    itself has no counterpart in the paper; it serves the adjoint below).  One level: A is
-   symmetric (same as gmg_apply).  Several AMR levels: the
+   symmetric (same as gmg_apply) unless a side is GMG_BC_DIRICHLET_QUAD; then A^T moves each
+   quadratic wall cell's entry -w/3 on phi_1 (w = b beta_f / h^2) into phi_1's row (single-
+   problem contexts; y's ghosts are overwritten).  Several AMR levels: the
    transpose of the composite operator (the level stencils plus, for each pair of
    consecutive levels, the transposed interpolation and reflux couplings); covered entries
    of y are taken as 0 and those of out are 0; y's ghosts are overwritten. */
@@ -391,7 +412,9 @@ gmg_status gmg_apply_transpose(gmg_ctx* ctx, void* const* out, void* const* y);
 /* Adjoint of the solve of Sec. "Linear Solvers" (no counterpart in the paper: the
    differentiation of its operator equation).
    Adjoint solve A^T lambda = g (FP64), so that lambda = dL/d(rhs) for a loss L(phi) with
-   dL/dphi = g.  One level: a forward solve (A symmetric).  Several AMR levels: BiCGStab on A^T,
+   dL/dphi = g.  One level: a forward solve (A symmetric); with a GMG_BC_DIRICHLET_QUAD side,
+   BiCGStab on A^T right-preconditioned by the V-cycle of A (the Krylov vectors of the
+   workspace; precision of p for the V-cycle), to the same stopping test.  Several AMR levels: BiCGStab on A^T,
    right-preconditioned by the composite multigrid correction of A, to ||g - A^T lambda||_inf
    <= tol_rel ||g||_inf (max_iter Krylov iterations).  Singular problems (no Dirichlet wall,
    a = 0): g is projected onto the range of A^T (g - V sum(g)/sum(V), V the cell volumes;
@@ -431,14 +454,15 @@ gmg_status gmg_beta_grad(gmg_ctx* ctx, void* const* dbeta, void* const* phi, voi
 
 /* Wall values (Sec. "Linear Solvers": inhomogeneous boundary conditions of the operator
    equation).  out = rhs - A_g(0): rhs plus, in each cell next to a wall face with a value, 2 w g
-   (Dirichlet) or w h g (Neumann), w = b beta_face / h^2 the face's weight; faces are added
+   (Dirichlet; 8 w g / 3 under the quadratic rule) or w h g (Neumann), w = b beta_face / h^2
+   the face's weight; faces are added
    in the order x-, x+, y-, y+, z-, z+.  rhs, out: FP64 level-0 boxed device arrays; out may
    equal rhs (in place); otherwise rhs is copied first. */
 gmg_status gmg_wall_values_rhs(gmg_ctx* ctx, void* out, const void* rhs, const void* const* values);
 
 /* Wall values, adjoint (no counterpart in the paper: the differentiation of the operator
    equation's boundary data).  The transpose of the map g -> rhs - A_g(0): dvalues[f][t] = c * lambda[q] for the wall
-   cell q behind face position t, c = 2 w (Dirichlet) or w h (Neumann); with lambda the
+   cell q behind face position t, c = 2 w (Dirichlet; 8 w / 3 quadratic) or w h (Neumann); with lambda the
    adjoint (gmg_solve_adjoint of dL/dphi) this is dL/dg.  dvalues[f]: FP64 device arrays in
    the layout of values above, written whole; NULL entries are skipped. */
 gmg_status gmg_wall_values_grad(gmg_ctx* ctx, const void* lambda, void* const* dvalues);
@@ -619,7 +643,9 @@ gmg_status gmg_partition(const gmg_ctx* ctx, int m, int nranks, long long min_ce
    14 ints per rectangle: dst_box, src_box, dst[3], src[3] (local coordinates of the first
    ghost cell and of its source cell), d1, d2 (tangential axes, d1 fastest), n1, n2
    (extents), sign (+1 copy or Neumann mirror, -1 Dirichlet reflection), kind (0 copy from a
-   box of the level, periodic images included; 1 wall). */
+   box of the level, periodic images included; 1 wall; 2 quadratic Dirichlet wall, whose
+   source is the second cell inward and whose ghost holds a third of it, the rule's -2 phi_0
+   being part of the diagonal). */
 gmg_status gmg_ghost_rects(const gmg_ctx* ctx, int m, int* n, int* rects);
 
 /* Sec. "Communication" (ghost-cell exchange between processes):

@@ -104,12 +104,14 @@ class _Solve(torch.autograd.Function):
         return (None, C.unpack(lam), C.unpack(d), *dwalls)
 
 
-_BC = {"periodic": gmg.PERIODIC, "dirichlet": gmg.DIRICHLET, "neumann": gmg.NEUMANN}
+_BC = {"periodic": gmg.PERIODIC, "dirichlet": gmg.DIRICHLET, "neumann": gmg.NEUMANN,
+       "dirichlet_quad": gmg.DIRICHLET_QUAD}
 
 
 class Solve:
     """phi = Solve(...)(rhs, beta, wall_values) on one level, differentiable in rhs, beta and
-    the wall values.  bc: "periodic", "dirichlet" or "neumann" on every side, or a pair of
+    the wall values.  bc: "periodic", "dirichlet", "neumann" or "dirichlet_quad" (the quadratic
+    wall rule) on every side, or a pair of
     per-axis lists (bc_lo, bc_hi) of those names or codes.  wall_values: None, or a dict
     face -> (n_t2, n_t1) tensor (face = 2*d + side; see gmg.Context.face_shape)."""
 

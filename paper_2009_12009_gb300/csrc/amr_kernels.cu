@@ -157,7 +157,10 @@ __global__ void __launch_bounds__(AT)
       const bool wall = (side == 0 && G.wall_lo[d] && gface == G.dlo[d]) ||
                         (side == 1 && G.wall_hi[d] && gface == G.dhi[d] + 1);
       if (wall) {  // one row: q's, with w (phi_q - phi_g); beta_face = beta_q
-        acc += lq * ih2 * (phi[nq] - pq);
+        if ((side ? G.wall_hi[d] : G.wall_lo[d]) == 3 && n[d] >= 2)
+          acc += lq * ih2 * ((phi[nq] - 2.0 * pq) - pq);  // quadratic: the ghost holds phi_1 / 3 (+ 8g/3)
+        else
+          acc += lq * ih2 * (phi[nq] - pq);
         continue;
       }
       if (ghost && cfidx && cfidx[nq] >= 0) {  // fine coarse/fine face: fine row + reflux row

@@ -480,8 +480,9 @@ std::vector<DevGeom> dev_geoms(const LevelMeta& M) {
     for (int d = 0; d < 3; ++d) {
       g[s].dlo[d] = G.domain.lo[d];
       g[s].dhi[d] = G.domain.hi[d];
-      g[s].wall_lo[d] = G.bclo[d];  // the boundary codes: 0 periodic, 1 Dirichlet, 2 Neumann
-      g[s].wall_hi[d] = G.bchi[d];
+      // the boundary codes: 0 periodic, 1 Dirichlet, 2 Neumann, 3 quadratic Dirichlet
+      g[s].wall_lo[d] = G.qlo[d] ? 3 : G.bclo[d];
+      g[s].wall_hi[d] = G.qhi[d] ? 3 : G.bchi[d];
       g[s].ih2[d] = 1.0 / (G.h[d] * G.h[d]);
     }
   }
@@ -709,8 +710,16 @@ bool vec_on(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
   return dt == DT_BF16;
 }
 
+// a problem of the context has a quadratic Dirichlet side
+bool any_quad(const gmg_ctx* c) {
+  for (const SolveGeom& G : c->geoms)
+    if (G.has_quad()) return true;
+  return false;
+}
+
 bool tail_on(const gmg_ctx* c, const gmg_params& p, int dt) {
   if (p.prolongation == 1) return false;  // the one-block coarse end interpolates piecewise constant
+  if (any_quad(c)) return false;          // its ghost lists copy or negate only
   if (p.fused_coarse == 2) return c->tail_choice[dt] != 0;  // untuned: on
   return p.fused_coarse == 1;
 }
@@ -1036,6 +1045,14 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
     SETERR(c, GMG_ERR_BAD_INPUT, "fuse_correction must be 0 or 1");
   if (p.settled_zero != 0 && p.settled_zero != 1) SETERR(c, GMG_ERR_BAD_INPUT, "settled_zero must be 0 or 1");
   if (p.precision != GMG_FP64 && !c->mixed) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for mixed precision");
+  if (any_quad(c)) {
+    if (p.krylov == 2 || p.bottom_solver == 1)
+      SETERR(c, GMG_ERR_BAD_INPUT,
+             "quadratic Dirichlet walls make the operator non-symmetric: conjugate gradients (krylov = 2, "
+             "bottom_solver = 1) are not offered");
+    if (p.prolongation == 1)
+      SETERR(c, GMG_ERR_BAD_INPUT, "quadratic Dirichlet walls: trilinear interpolation is not offered");
+  }
   return GMG_OK;
 }
 
@@ -1862,14 +1879,18 @@ gmg_status set_domain_geom(gmg_ctx* c, SolveGeom& G, const int lo[3], const int 
   for (int d = 0; d < 3; ++d) {
     if (hi[d] < lo[d]) SETERR(c, GMG_ERR_BAD_INPUT, "empty domain");
     if (!(phi[d] > plo[d])) SETERR(c, GMG_ERR_BAD_INPUT, "prob_hi must exceed prob_lo");
-    if (bclo[d] < GMG_BC_PERIODIC || bclo[d] > GMG_BC_NEUMANN || bchi[d] < GMG_BC_PERIODIC || bchi[d] > GMG_BC_NEUMANN)
+    if (bclo[d] < GMG_BC_PERIODIC || bclo[d] > GMG_BC_DIRICHLET_QUAD || bchi[d] < GMG_BC_PERIODIC ||
+        bchi[d] > GMG_BC_DIRICHLET_QUAD)
       SETERR(c, GMG_ERR_BAD_INPUT, "unknown boundary condition");
     if ((bclo[d] == GMG_BC_PERIODIC) != (bchi[d] == GMG_BC_PERIODIC))
       SETERR(c, GMG_ERR_BAD_INPUT, "a periodic direction must be periodic on both sides");
     G.domain.lo[d] = lo[d];
     G.domain.hi[d] = hi[d];
-    G.bclo[d] = bclo[d];
-    G.bchi[d] = bchi[d];
+    // a quadratic Dirichlet side is a Dirichlet side with the quadratic flag
+    G.qlo[d] = bclo[d] == GMG_BC_DIRICHLET_QUAD;
+    G.qhi[d] = bchi[d] == GMG_BC_DIRICHLET_QUAD;
+    G.bclo[d] = G.qlo[d] ? GMG_BC_DIRICHLET : bclo[d];
+    G.bchi[d] = G.qhi[d] ? GMG_BC_DIRICHLET : bchi[d];
     G.h[d] = (phi[d] - plo[d]) / (double)(hi[d] - lo[d] + 1);
   }
   return GMG_OK;
@@ -1893,9 +1914,12 @@ size_t krylov_bytes(const gmg_ctx* c) {
 // V-cycle.  Vectors FP64; the V-cycle in the precision of p.  Stops on the recursive
 // residual, ||r||_inf <= max(tol_rel ||rhs||_inf, tol_abs), after max_iter iterations, or on
 // breakdown.  Singular problems: rhs, every preconditioned vector and phi projected onto
-// zero mean.  One-level, single-problem contexts.
+// zero mean.  One-level, single-problem contexts.  transpose: solve A^T x = rhs instead (the
+// adjoint of a context with quadratic walls; BiCGStab, still preconditioned by the V-cycle
+// of A, which differs from A^T only in the wall couplings).
+void apply_transpose_one(gmg_ctx* c, double* y, double* out, cudaStream_t s);
 gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel, double tol_abs, const gmg_params& p,
-                        gmg_solve_info* info) {
+                        gmg_solve_info* info, bool transpose = false) {
   const auto t0 = std::chrono::steady_clock::now();
   if (c->amr || c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "krylov: one-level, single-problem contexts only");
   if (!c->kv[0]) SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace was not sized for the Krylov vectors (krylov != 0)");
@@ -1987,7 +2011,11 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
     graph_launches += itg->second.launches;
     return GMG_OK;
   };
-  auto apply = [&](double* in, double* out) {  // out = A in, homogeneous walls
+  auto apply = [&](double* in, double* out) {  // out = A in (A^T in), homogeneous walls
+    if (transpose) {
+      apply_transpose_one(c, in, out, s);
+      return;
+    }
     launch_fill(DT_F64, D0, in, -1, 0, s);
     launch_apply(D0, in, coefs64(c, 0), out, s);
   };
@@ -2158,7 +2186,7 @@ gmg_status wall_values_pass(gmg_ctx* c, const void* const* values, int mode, dou
   for (int face = 0; face < 6; ++face) {
     if (!values[face]) continue;
     const int d = face / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    const int kind = face % 2 ? G.bchi[d] : G.bclo[d];
+    const int kind = (face % 2 ? G.qhi[d] : G.qlo[d]) ? 3 : (face % 2 ? G.bchi[d] : G.bclo[d]);
     int maxf = 0;
     for (const Box& B : M.boxes) maxf = std::max(maxf, B.n(t1) * B.n(t2));
     launch_wall_values(c->dev[0], (int)M.boxes.size(), maxf, face, kind, G.h[d], w[d], (const double*)values[face],
@@ -2166,6 +2194,30 @@ gmg_status wall_values_pass(gmg_ctx* c, const void* const* values, int mode, dou
   }
   CK(c, cudaGetLastError());
   return GMG_OK;
+}
+
+// out = A^T y on level 0 of a one-level context with homogeneous walls (y's ghosts are
+// overwritten).  Without quadratic walls A is symmetric and this is A y.  A quadratic wall
+// cell's row holds, besides its symmetric entries, -w/3 on phi_1 (the cell next to it
+// inward): A y with the quadratic ghosts 0 gives every other entry of A^T, then one
+// k_wall_values pass per quadratic face adds -w/3 y_0 to the row of phi_1.
+void apply_transpose_one(gmg_ctx* c, double* y, double* out, cudaStream_t s) {
+  const LevelDev& D0 = c->dev[0];
+  const bool quad = any_quad(c);
+  launch_fill(DT_F64, D0, y, -1, quad ? 2 : 0, s);
+  launch_apply(D0, y, coefs64(c, 0), out, s);
+  if (!quad) return;
+  const LevelMeta& M = c->L[0];
+  const SolveGeom& G = c->geoms[0];
+  const Coefs k = coefs64(c, 0);
+  const double* w[3] = {(const double*)k.wx, (const double*)k.wy, (const double*)k.wz};
+  for (int face = 0; face < 6; ++face) {
+    const int d = face / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    if (!(face % 2 ? G.qhi[d] : G.qlo[d])) continue;
+    int maxf = 0;
+    for (const Box& B : M.boxes) maxf = std::max(maxf, B.n(t1) * B.n(t2));
+    launch_wall_values(D0, (int)M.boxes.size(), maxf, face, 3, G.h[d], w[d], nullptr, 3, out, y, nullptr, s);
+  }
 }
 
 }  // namespace
@@ -2255,6 +2307,8 @@ gmg_status gmg_define_level(gmg_ctx* c, int lev, int nboxes, const int* lohi, in
   // AMR level lev >= 1: ratio 2 over part of level lev - 1 (Sec. "Basic data structures":
   // refinement ratio between levels; proper nesting inside the level below)
   if (c->L.empty()) SETERR(c, GMG_ERR_STATE, "define AMR level 0 first");
+  if (c->geoms[0].has_quad())
+    SETERR(c, GMG_ERR_BAD_INPUT, "quadratic Dirichlet walls: composite (AMR) contexts take the linear rule only");
   if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "AMR levels: single-problem contexts only");
   if (lev > (int)c->amrl.size() + 1 || lev > GMG_MAX_AMR_LEVELS - 1)
     SETERR(c, GMG_ERR_BAD_INPUT, "define AMR levels in order (at most " + std::to_string(GMG_MAX_AMR_LEVELS) + ")");
@@ -2665,7 +2719,8 @@ gmg_status gmg_workspace_size(const gmg_ctx* cc, const gmg_params* p, size_t* by
   if (!c || !bytes) return GMG_ERR_BAD_INPUT;
   if (c->L.empty()) SETERR(c, GMG_ERR_STATE, "no BoxArray defined");
   const bool mixed = p && p->precision != GMG_FP64;
-  *bytes = carve(c, nullptr, mixed, false) + (p && p->krylov ? krylov_bytes(c) : 0);
+  // Krylov vectors: asked for, or needed by the adjoint solve of quadratic walls
+  *bytes = carve(c, nullptr, mixed, false) + ((p && p->krylov) || any_quad(c) ? krylov_bytes(c) : 0);
   return GMG_OK;
 }
 
@@ -2675,8 +2730,13 @@ gmg_status gmg_set_workspace(gmg_ctx* c, void* dptr, size_t bytes) {
   if (!dptr || ((uintptr_t)dptr & 255)) SETERR(c, GMG_ERR_BAD_INPUT, "workspace must be non-null and 256-byte aligned");
   const size_t need64 = carve(c, nullptr, false, false);
   const size_t needmx = carve(c, nullptr, true, false);
+  const size_t kb = krylov_bytes(c);
+  // the sizes gmg_workspace_size gives, largest first: mixed with the Krylov vectors, FP64
+  // with them (when that is more than mixed alone), mixed, FP64
   bool mixed;
-  if (bytes >= needmx) mixed = true;
+  if (bytes >= needmx + kb) mixed = true;
+  else if (needmx < need64 + kb && bytes >= need64 + kb) mixed = false;
+  else if (bytes >= needmx) mixed = true;
   else if (bytes >= need64) mixed = false;
   else SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace too small");
   drop_graphs(c);
@@ -2689,7 +2749,7 @@ gmg_status gmg_set_workspace(gmg_ctx* c, void* dptr, size_t bytes) {
   const size_t used = carve(c, dptr, mixed, true);
   // the Krylov vectors, if the workspace holds them after the rest
   const size_t ne0 = (size_t)c->L[0].nelem;
-  const bool kr = bytes >= used + krylov_bytes(c);
+  const bool kr = bytes >= used + kb;
   // the V-cycle outputs y (5) and z (8) are read with their ghosts (plain placement); the
   // others start their rows' valid cells on a 128-byte line (see Carver::take_rows)
   const size_t stride = (((8 * ne0) + 255) & ~(size_t)255) + 256;
@@ -2980,7 +3040,16 @@ gmg_status gmg_batch_solve(gmg_ctx* c, void* phi, const void* rhs, double tol_re
 
 gmg_status gmg_apply_transpose(gmg_ctx* c, void* const* out, void* const* y) {
   if (!c || !out || !y || !out[0] || !y[0]) return GMG_ERR_BAD_INPUT;
-  if (!c->amr) return gmg_apply(c, out, y);  // one level: A is symmetric
+  if (!c->amr && !any_quad(c)) return gmg_apply(c, out, y);  // one level, linear walls: A is symmetric
+  if (!c->amr) {
+    gmg_status st = check_level(c, 0, DT_F64);
+    if (st) return st;
+    if (c->ns() != 1) SETERR(c, GMG_ERR_BAD_INPUT, "transpose with quadratic walls: single-problem contexts only");
+    if ((st = build_coefs(c))) return st;
+    apply_transpose_one(c, (double*)y[0], (double*)out[0], c->stream);
+    CK(c, cudaGetLastError());
+    return GMG_OK;
+  }
   gmg_status st = check_level(c, 0, DT_F64);
   if (st) return st;
   if ((st = build_coefs(c))) return st;
@@ -3008,6 +3077,10 @@ gmg_status gmg_solve_adjoint(gmg_ctx* c, void* const* lambda, const void* const*
   if ((st = params_ok(c, p))) return st;
   if ((st = ensure_flow_lag(c, p))) return st;
   if ((st = build_coefs(c))) return st;
+  if (!c->amr && any_quad(c)) {  // non-symmetric operator: BiCGStab on A^T
+    p.krylov = 1;
+    return krylov_solve(c, (double*)lambda[0], (const double*)g[0], tol_rel, 0.0, p, info, true);
+  }
   if (!c->amr) {  // symmetric operator: the adjoint solve is a forward solve (mean projected)
     p.project_mean = 1;
     return solve_impl(c, (double*)lambda[0], (const double*)g[0], tol_rel, 0.0, p, info);

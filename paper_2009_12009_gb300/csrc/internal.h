@@ -58,8 +58,13 @@ struct GhostRect {
   int n1, n2;    // extents along d1, d2
   int sign;      // +1: copy (or homogeneous Neumann mirror); -1: homogeneous Dirichlet reflection
   int par0;      // global (i+j+k) parity of the first ghost cell
-  int kind;      // 0: copy from a box of the same level (periodic images included); 1: wall
+  int kind;      // 0: copy from a box of the same level (periodic images included); 1: wall;
+                 // 2: quadratic Dirichlet wall -- the source is the second cell inward and the
+                 //    ghost holds a third of it (the rule's -2 phi_0 sits in the diagonal D)
 };
+
+// the factor from a ghost rectangle's source value to its ghost value
+inline double ghost_factor(const GhostRect& g) { return g.kind == 2 ? 1.0 / 3.0 : (double)g.sign; }
 
 // Generic work-list entry: block b handles items [start, start + per-block) of `item`.
 struct Chunk {

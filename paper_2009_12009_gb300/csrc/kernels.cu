@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(BLOCK) k_fill(const DevBox* __restrict__ boxes
   pdl_enter();
   const Chunk ch = chunks[blockIdx.x];
   const GhostRect g = rects[ch.item];
-  if (copy_mode && g.kind == 1) return;
+  if (copy_mode == 1 && g.kind != 0) return;
   const DevBox Bd = boxes[g.dst_box];
   if (active && !active[Bd.solve]) return;
   const DevBox Bs = boxes[g.src_box];
@@ -74,7 +74,10 @@ __global__ void __launch_bounds__(BLOCK) k_fill(const DevBox* __restrict__ boxes
     const int u = e % g.n1, v = e / g.n1;
     if (colour >= 0 && ((g.par0 + u + v) & 1) != colour) continue;
     const auto val = ld(f + s0 + u * su + v * sv);
-    st(f + d0 + u * du + v * dv, g.sign < 0 ? -val : val);
+    if (g.kind == 2)  // quadratic wall: a third of the second cell inward (0 for the transpose)
+      st(f + d0 + u * du + v * dv, copy_mode == 2 ? (decltype(val))0 : val * (decltype(val))(1.0 / 3.0));
+    else
+      st(f + d0 + u * du + v * dv, g.sign < 0 ? -val : val);
   }
 }
 
@@ -807,7 +810,11 @@ __global__ void __launch_bounds__(BLOCK)
   }
 }
 
-__global__ void __launch_bounds__(BLOCK) k_diag(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+// D = a alpha + sum_f w_f, plus 2 w_f for each face on a quadratic Dirichlet wall (the
+// rule's -2 phi_0 term of the ghost, moved into the row's diagonal; the box must have two
+// cells along the normal, else the linear rule holds there)
+__global__ void __launch_bounds__(BLOCK) k_diag(const DevBox* __restrict__ boxes, const DevGeom* __restrict__ geoms,
+                                                const Chunk* __restrict__ chunks,
                                                 const double* __restrict__ acoef, const double* __restrict__ wx,
                                                 const double* __restrict__ wy, const double* __restrict__ wz,
                                                 double* D, double* invD) {
@@ -818,7 +825,16 @@ __global__ void __launch_bounds__(BLOCK) k_diag(const DevBox* __restrict__ boxes
   const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
   const int64_t q = elem_index(B, i, j, k);
   const double s = ((wx[q] + wx[q + 1]) + (wy[q] + wy[q + B.sx])) + (wz[q] + wz[q + B.sy]);
-  const double d = acoef[q] + s;
+  double d = acoef[q] + s;
+  const DevGeom G = geoms[B.solve];
+  const int c[3] = {i, j, k}, n[3] = {B.nx, B.ny, B.nz};
+  const double* w[3] = {wx, wy, wz};
+  for (int a = 0; a < 3; ++a) {
+    if (n[a] < 2) continue;
+    const int64_t sa = axis_stride(B, a);
+    if (G.wall_lo[a] == 3 && c[a] == 0 && B.lo[a] == G.dlo[a]) d += 2.0 * w[a][q];
+    if (G.wall_hi[a] == 3 && c[a] == n[a] - 1 && B.lo[a] + n[a] - 1 == G.dhi[a]) d += 2.0 * w[a][q + sa];
+  }
   D[q] = d;
   invD[q] = 1.0 / d;
 }
@@ -1070,7 +1086,7 @@ void launch_diag(const LevelDev& L, const double* acoef, const double* wx, const
                  double* D, double* invD, cudaStream_t s) {
   if (!L.n_cell_chunks) return;
   ++g_launches;
-  k_diag<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, acoef, wx, wy, wz, D, invD);
+  k_diag<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.geoms, L.cell_chunks, acoef, wx, wy, wz, D, invD);
 }
 
 void launch_convert(int dt, int dt2, const void* src, void* dst, int64_t n, cudaStream_t s) {

@@ -10,7 +10,8 @@ namespace gmg {
 // Per-solve geometry of one level, as the coefficient kernels see it.
 struct DevGeom {
   int dlo[3], dhi[3];
-  int wall_lo[3], wall_hi[3];  // wall on that side: 0 none (periodic), 1 Dirichlet, 2 Neumann
+  int wall_lo[3], wall_hi[3];  // wall on that side: 0 none (periodic), 1 Dirichlet, 2 Neumann,
+                               // 3 Dirichlet with the quadratic ghost rule
   double ih2[3];               // 1 / h_d^2
 };
 
@@ -83,8 +84,9 @@ struct Coefs {
   const void* invD = nullptr;
 };
 
-// ghost exchange; colour -1 = all ghosts; copy_mode: skip wall rectangles (coefficient
-// fills, where the wall face is handled by the face kernel)
+// ghost exchange; colour -1 = all ghosts; copy_mode 1: skip wall rectangles (coefficient
+// fills, where the wall face is handled by the face kernel); 2: quadratic wall ghosts 0
+// (the transposed operator: the rule's entry on phi_1 moves to phi_1's row)
 void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, cudaStream_t s);
 // one red-black colour (no ghost fill); push: also write each new value into the ghost
 // cells that copy it (L.push_ok levels only)

@@ -101,6 +101,14 @@ static std::string build_ghosts(LevelMeta& L) {
           r.sign = bc == 2 ? 1 : -1;
           r.par0 = pmod2(B.lo[0] + B.lo[1] + B.lo[2] + r.dst[0] + r.dst[1] + r.dst[2]);
           r.kind = 1;
+          if (bc == 1 && (side ? G.qhi[d] : G.qlo[d]) && B.n(d) >= 2) {
+            // quadratic rule: ghost = -2 phi_0 + phi_1 / 3; the rectangle fills phi_1 / 3 and
+            // the diagonal takes the -2 phi_0 part (so the ghost holds no value of the cell
+            // next to it, and the row of that cell stays exact under Gauss-Seidel)
+            r.src[d] = side ? B.n(d) - 2 : 1;
+            r.sign = 1;
+            r.kind = 2;
+          }
           L.ghosts.push_back(r);
           continue;
         }
@@ -177,7 +185,7 @@ static void build_bottom(LevelMeta& L) {
           int sl[3] = {g.src[0], g.src[1], g.src[2]};
           dl[g.d1] += u; dl[g.d2] += v;
           sl[g.d1] += u; sl[g.d2] += v;
-          L.bot_ghosts.push_back({elem_index(Bd, dl[0], dl[1], dl[2]), elem_index(Bs, sl[0], sl[1], sl[2]), (double)g.sign});
+          L.bot_ghosts.push_back({elem_index(Bd, dl[0], dl[1], dl[2]), elem_index(Bs, sl[0], sl[1], sl[2]), ghost_factor(g)});
         }
     }
     D.ncell = (int)L.bot_cells.size() - D.cell0;
@@ -414,6 +422,10 @@ std::string finalize_level(LevelMeta& L) {
     const int d = 3 - g.d1 - g.d2;
     const DevBox& S = L.dbox[g.src_box];
     const int n[3] = {S.nx, S.ny, S.nz};
+    if (g.kind == 2) {  // a quadratic wall's source is not on the box face
+      L.push_ok = false;
+      continue;
+    }
     if (n[d] < 2 || (g.src[d] != 0 && g.src[d] != n[d] - 1) || g.n1 != n[g.d1] || g.n2 != n[g.d2] ||
         g.src[g.d1] != 0 || g.src[g.d2] != 0) {
       L.push_ok = false;  // a face split over several rectangles, or a one-cell-thick box
@@ -605,7 +617,7 @@ std::string build_tail(std::vector<LevelMeta>& L, TailHost& T) {
               dl[g.d1] += u; dl[g.d2] += v;
               sl[g.d1] += u; sl[g.d2] += v;
               T.ghosts.push_back({elem_index(Bd, dl[0], dl[1], dl[2]), elem_index(Bs, sl[0], sl[1], sl[2]),
-                                  (double)g.sign});
+                                  ghost_factor(g)});
             }
         }
         TL.nghost[parity] = (int)T.ghosts.size() - g0;

@@ -28,7 +28,14 @@ struct SolveGeom {
   double h[3] = {1, 1, 1};
   int bclo[3] = {0, 0, 0};
   int bchi[3] = {0, 0, 0};
+  int qlo[3] = {0, 0, 0};  // 1: that Dirichlet side takes the quadratic ghost rule
+  int qhi[3] = {0, 0, 0};
   bool periodic(int d) const { return bclo[d] == 0; }
+  bool has_quad() const {
+    for (int d = 0; d < 3; ++d)
+      if (qlo[d] || qhi[d]) return true;
+    return false;
+  }
   bool all_periodic() const { return bclo[0] == 0 && bclo[1] == 0 && bclo[2] == 0; }
   bool has_dirichlet() const {
     for (int d = 0; d < 3; ++d)

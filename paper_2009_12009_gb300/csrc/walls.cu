@@ -10,11 +10,18 @@
 // (Neumann); so rhs - A_g(0) = rhs + c g with c = 2w or w h, and solving A_0 phi =
 // rhs - A_g(0) with homogeneous walls gives the solution with the wall values.
 //
-// One kernel does the three uses of that map, one launch per wall face (faces in the order
+// A quadratic Dirichlet side (kind 3; boxes of two or more cells along the normal) has the
+// ghost 8g/3 - 2 phi_0 + phi_1 / 3: the constant is 8g/3 and c = 8w/3.  Its homogeneous
+// part puts the entry -w/3 on phi_1 into the wall cell's row, which the transpose moves
+// into phi_1's row.
+//
+// One kernel does the four uses of that map, one launch per wall face (faces in the order
 // x-, x+, y-, y+, z-, z+, so a corner cell's sum has a fixed order):
-//   mode 0: f[q] += c g           (fold the values into a right-hand side)
-//   mode 1: f[ghost] += (2 or h) g (complete homogeneous ghosts of phi to the affine rule)
-//   mode 2: dg = c lambda[q]       (the transpose: dL/dg for an adjoint lambda)
+//   mode 0: f[q] += c g             (fold the values into a right-hand side)
+//   mode 1: f[ghost] += (2, 8/3 or h) g (complete homogeneous ghosts of phi to the affine rule)
+//   mode 2: dg = c lambda[q]         (the transpose: dL/dg for an adjoint lambda)
+//   mode 3: f[q1] -= (w / 3) lam[q]  (quadratic sides: the transposed operator's entry, q1 the
+//                                     cell next to q inward; f = A^T lam without it)
 // A block row (blockIdx.y) takes one box; boxes without a face on the wall return at once.
 #include "kernels.h"
 
@@ -45,14 +52,16 @@ __global__ void __launch_bounds__(WT)
     const int64_t qf = side ? q + sd : q;  // the wall face's slot (slot i holds face i - 1/2)
     const int64_t qg = side ? q + sd : q - sd;
     const int64_t tt = (int64_t)(B.lo[t1] + loc[t1] - G.dlo[t1]) + nt1 * (int64_t)(B.lo[t2] + loc[t2] - G.dlo[t2]);
+    const bool quad = kind == 3 && n[d] >= 2;
+    const double gf = kind == 2 ? h : (quad ? 8.0 / 3.0 : 2.0);  // ghost = homogeneous part + gf g
     if (mode == 0) {
-      const double c = kind == 1 ? 2.0 * w[qf] : w[qf] * h;
-      f[q] += c * g[tt];
+      f[q] += (kind == 2 ? w[qf] * h : gf * w[qf]) * g[tt];
     } else if (mode == 1) {
-      f[qg] += (kind == 1 ? 2.0 : h) * g[tt];
-    } else {
-      const double c = kind == 1 ? 2.0 * w[qf] : w[qf] * h;
-      dg[tt] = c * lam[q];
+      f[qg] += gf * g[tt];
+    } else if (mode == 2) {
+      dg[tt] = (kind == 2 ? w[qf] * h : gf * w[qf]) * lam[q];
+    } else if (quad) {
+      f[side ? q - sd : q + sd] -= (w[qf] / 3.0) * lam[q];
     }
   }
 }

@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 OK, BAD_INPUT, NOT_CONVERGED, DIVERGED, CUDA_ERR, DEVICE_TIMEOUT, NO_WORKSPACE, STATE = 0, -1, -2, -3, -4, -5, -6, -7
-PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
+PERIODIC, DIRICHLET, NEUMANN, DIRICHLET_QUAD = 0, 1, 2, 3
 DIRICHLET0 = DIRICHLET
 FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
@@ -381,11 +381,13 @@ class Context:
             self._check(st)
         return phi, info
 
-    def apply(self, phi, out=None):
+    def apply(self, phi, out=None, transpose=False):
+        """A phi with homogeneous walls, or A^T phi (transpose; phi's ghosts are overwritten)."""
         out = self.field(0) if out is None else out
         pa = (C.c_void_p * 1)(phi.data_ptr())
         oa = (C.c_void_p * 1)(out.data_ptr())
-        self._check(self.L.gmg_apply(self.h, oa, pa))
+        fn = self.L.gmg_apply_transpose if transpose else self.L.gmg_apply
+        self._check(fn(self.h, oa, pa))
         return out
 
     def solve_adjoint(self, g, tol_rel=1e-10, **params):
