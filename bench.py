@@ -513,6 +513,130 @@ def _form_amr3(stream, barrier):
     return res
 
 
+def oracle_table(stream, barrier, dev):
+    """GPU time to 1e-10 next to the oracle's (all host cores) and the largest relative
+    difference of the GPU result from the oracle's, for the small periodic case, the 512^3
+    mixed forms, the 64 batched solves and the two-level adjoint (the 256^3 case is the main
+    line).  Prints one JSON record; used to fill the GPU table of the baseline notes."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2009_12009_gb300 import gmg
+    from paper_2009_12009_gb300 import inputs as I
+
+    ncores = len(os.sched_getaffinity(0))
+    O.set_threads(ncores)
+
+    def ms_of(fn):
+        t0 = time.perf_counter()
+        out = fn()
+        return (time.perf_counter() - t0) * 1e3, out
+
+    def rel(a, b):
+        return float(np.abs(a - b).max() / np.abs(b).max())
+
+    res = {"oracle_cores": ncores}
+    # poisson32: periodic, singular (projected), FP64
+    c = I.poisson32()
+    ctx = gmg.Context(c["domain"], c["bc_lo"], c["bc_hi"], boxes=c["boxes"], stream=stream.cuda_stream)
+    ctx.allocate(gmg.FP64)
+    ctx.set_scalars(0.0, 1.0)
+    ctx.set_beta(None)
+    rhs = ctx.pack(torch.from_numpy(c["rhs"]))
+    ms, (phi, info) = _timed(lambda: ctx.solve(rhs, tol_rel=TOL, project_mean=1), 5, 2, stream, barrier)
+    P = O.Problem(c["domain"], c["boxes"], c["bc_lo"], c["bc_hi"])
+    P.set_coeffs(0.0, 1.0)
+    oms, (want, it, hist, st) = ms_of(lambda: P.solve(c["rhs"], tol_rel=TOL, project_mean=True))
+    res["poisson32"] = {"gpu_ms": ms, "iterations": info.iterations, "value": mcell_updates_per_vcycle(ctx, 4) *
+                        info.iterations / (ms * 1e-3) / 1e6, "oracle_ms": oms, "oracle_iterations": it,
+                        "rel_err_vs_oracle": rel(ctx.unpack(phi).cpu().numpy(), want)}
+    del ctx
+    # abec512: FP64 oracle solve; the GPU's FP32 and BF16 forms
+    c = I.abec512()
+    P = O.Problem(c["domain"], c["boxes"], c["bc_lo"], c["bc_hi"])
+    P.set_coeffs(c["a"], c["b"], alpha=c["alpha"], beta=c["beta"])
+    oms, (want, it, hist, st) = ms_of(lambda: P.solve(c["rhs"], tol_rel=TOL))
+    del P
+    ctx = gmg.Context(c["domain"], c["bc_lo"], c["bc_hi"], boxes=c["boxes"], stream=stream.cuda_stream)
+    ctx.allocate(gmg.MIXED_FP32)
+    ctx.set_scalars(c["a"], c["b"])
+    ctx.set_beta(torch.from_numpy(c["beta"]))
+    rhs = ctx.pack(torch.from_numpy(c["rhs"]))
+    ctx.autotune(rhs, gmg.MIXED_FP32)
+    ctx.autotune(rhs, gmg.MIXED_BF16)
+    r = {"oracle_ms": oms, "oracle_iterations": it}
+    for name, prec in (("fp32", gmg.MIXED_FP32), ("bf16", gmg.MIXED_BF16)):
+        ms, (phi, info) = _timed(lambda: ctx.solve(rhs, tol_rel=TOL, precision=prec), 2, 1, stream, barrier)
+        r[name] = {"gpu_ms": ms, "iterations": info.iterations, "value": mcell_updates_per_vcycle(ctx, 4) *
+                   info.iterations / (ms * 1e-3) / 1e6, "rel_err_vs_oracle": rel(ctx.unpack(phi).cpu().numpy(), want)}
+    res["abec512_mixed"] = r
+    del ctx, rhs, want
+    torch.cuda.empty_cache()
+    # batch64: every problem on the oracle, one after another
+    probs = I.batch64()
+    wants, oms = [], 0.0
+    for p in probs:
+        P = O.Problem(p["domain"], p["boxes"], p["bc_lo"], p["bc_hi"], (0, 0, 0), p["prob_hi"])
+        P.set_coeffs(0.0, 1.0, beta=p["beta"])
+        t, (w, it, hist, st) = ms_of(lambda: P.solve(p["rhs"], tol_rel=TOL))
+        oms += t
+        wants.append(w)
+    B = gmg.BatchContext(probs, stream=stream.cuda_stream)
+    B.allocate(gmg.FP64)
+    B.set_scalars(0.0, 1.0)
+    B.set_beta_all([torch.from_numpy(p["beta"]) for p in probs])
+    brhs = B.pack_all([torch.from_numpy(p["rhs"]) for p in probs])
+    B.autotune(brhs, gmg.FP64)
+    ms, (phi, infos) = _timed(lambda: B.batch_solve(brhs, tol_rel=TOL), 3, 1, stream, barrier)
+    upd = sum(_updates_per_vcycle_problem(B, s) * i.iterations for s, i in enumerate(infos))
+    res["batch64"] = {"gpu_ms": ms, "value": upd / (ms * 1e-3) / 1e6, "oracle_ms": oms,
+                      "rel_err_vs_oracle": max(rel(B.unpack_solve(s, phi).cpu().numpy(), w)
+                                               for s, w in enumerate(wants))}
+    del B, brhs, phi
+    torch.cuda.empty_cache()
+    # amr2: the oracle's composite forward solve; the GPU's forward and adjoint solves
+    a = I.amr2()
+    P = O.AmrProblem(a["domain"], a["coarse_boxes"], a["fine_boxes"], a["bc_lo"], a["bc_hi"])
+    lo, hi = a["fine_slice"]
+    sl = (slice(lo, hi + 1),) * 3
+
+    def full_fine(x):
+        out = np.zeros(P.fine_shape)
+        out[sl] = x
+        return out
+
+    bf = np.ones(P.fine_shape)
+    bf[sl] = a["beta_f"]
+    P.set_coeffs(0.0, 1.0, beta_c=a["beta_c"], beta_f=bf)
+    oms, (oc, of, it, hist, st) = ms_of(lambda: P.solve(a["rhs_c"], full_fine(a["rhs_f"]), tol_rel=TOL))
+    actx = gmg.AmrContext(a["domain"], a["coarse_boxes"], a["fine_boxes"], a["bc_lo"], a["bc_hi"],
+                          stream=stream.cuda_stream)
+    actx.allocate(gmg.FP64)
+    actx.set_coeffs(0.0, 1.0, beta_c=torch.from_numpy(a["beta_c"]), beta_f=torch.from_numpy(a["beta_f"]))
+    rc, rf = actx.pack_level(0, torch.from_numpy(a["rhs_c"])), actx.pack_level(1, torch.from_numpy(a["rhs_f"]))
+    actx.autotune(rc, gmg.FP64)
+    ms_f, (pc, pf, info_f) = _timed(lambda: actx.solve2(rc, rf, tol_rel=TOL), 3, 1, stream, barrier)
+    phi_c = actx.unpack_level(0, pc).cpu().numpy() * P.coarse_mask
+    phi_f = full_fine(actx.unpack_level(1, pf).cpu().numpy())
+    gcn = (phi_c - a["target_c"]) * P.coarse_mask
+    gfn = phi_f[sl] - a["target_f"]
+    gc, gf = actx.pack_level(0, torch.from_numpy(gcn)), actx.pack_level(1, torch.from_numpy(gfn))
+    ms_a, (lc, lf, info_a) = _timed(lambda: actx.solve_adjoint2(gc, gf, tol_rel=TOL), 3, 1, stream, barrier)
+    lam = (actx.unpack_level(0, lc).cpu().numpy() * P.coarse_mask, full_fine(actx.unpack_level(1, lf).cpu().numpy()))
+    g = P.pack(gcn, full_fine(gfn))
+    V = P.volumes()
+    g = g - V * g.sum() / V.sum()
+    res["amr2_adjoint"] = {"gpu_forward_ms": ms_f, "gpu_adjoint_ms": ms_a, "forward_iterations": info_f.iterations,
+                           "adjoint_iterations": info_a.iterations, "oracle_forward_ms": oms,
+                           "oracle_forward_iterations": it,
+                           "forward_rel_err_vs_oracle": rel(P.pack(phi_c, phi_f), P.pack(oc, of)),
+                           "adjoint_rel_resid_by_oracle_transpose":
+                               float(np.abs(g - P.pack(*P.apply(*lam, transpose=True))).max() / np.abs(g).max())}
+    O.set_threads(1)
+    return res
+
+
 def summary(out):
     """The headline figures in one small record, printed last in the JSON line."""
     def g(d, *ks):
@@ -586,6 +710,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the 512^3, batched and two-level workloads")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="print only GPU and oracle times and differences for the other workloads")
     ap.add_argument("--only", choices=["abec512", "batch64", "amr2", "amr3", "walls256", "krylov"], default=None,
                     help="run and print only this one of the other workloads (for profiling)")
     args = ap.parse_args()
@@ -608,6 +734,9 @@ def main():
     from paper_2009_12009_gb300 import inputs as I
 
     stream = torch.cuda.current_stream()
+    if args.oracle_table:
+        print(json.dumps({"oracle_table": oracle_table(stream, torch.cuda.synchronize, dev)}))
+        return
     if args.only:
         def sync():
             torch.cuda.synchronize()
