@@ -787,18 +787,25 @@ def main():
     ms, updates, value = whole_job(ms, sum(upd_per_vc * k for k in its), world, dev)
     phi64 = ctx.unpack(phi).clone()
 
-    # roofline of the dominant kernel: finest-level red-black smoother, one colour pass per
-    # launch; algorithmic bytes 28 B/cell per pass (56 B/cell per red+black sweep)
+    # roofline of the dominant kernel: the finest-level red-black smoother.  Wavefront
+    # launches cover a whole sweep (two colour passes): 56 B/cell, except the first
+    # pre-smoothing sweep of each V-cycle, which starts from a zero correction and does not
+    # read it (48 B/cell); the two-pass form covers one colour pass per launch (28 B/cell).
     sm_ms = sum(i.smooth0_ms for i in infos)
     sm_n = sum(i.smooth0_launches for i in infos)
     sm_passes = sum(i.smooth0_passes for i in infos)
     launch_s = sm_ms * 1e-3 / max(sm_n, 1)
-    alg_bytes = PASS_BYTES_PER_CELL * ncells * sm_passes / max(sm_n, 1)
+    wave = sm_n > 0 and sm_passes == 2 * sm_n
+    sweeps = nu  # level-0 sweeps per V-cycle (nu1 + nu2)
+    if wave:
+        alg_bytes = ncells * (SWEEP_BYTES_PER_CELL * sweeps - 8) / sweeps
+        # 7 FP64-pipe operations per updated cell; the zero-start sweep's red cells take 2
+        fp64_ops = ncells * (UPDATE_FP64_OPS * sweeps - 2.5) / sweeps
+    else:
+        alg_bytes = PASS_BYTES_PER_CELL * ncells * sm_passes / max(sm_n, 1)
+        fp64_ops = UPDATE_FP64_OPS * (ncells / 2) * sm_passes / max(sm_n, 1)
     achieved = alg_bytes / launch_s / 1e9
     peak, peak_kind = peaks()
-    # the same launches against the FP64 pipe: 7 operations per updated cell (half the
-    # cells per pass), over the probe's FMA rate
-    fp64_ops = UPDATE_FP64_OPS * (ncells / 2) * sm_passes / max(sm_n, 1)
     fp64_rate = fp64_ops / launch_s
     rs_ms = sum(i.resid0_ms for i in infos)
     rs_n = sum(i.resid0_launches for i in infos)
@@ -812,11 +819,16 @@ def main():
                       "l2": "inputs larger than L2 (finest-level working set ~1.2 GB of fields and coefficients)",
                       "autotuned": {k: summarize_tuning(v) for k, v in tuned.items()}},
            "gpu_launches": int(sum(i.kernel_launches for i in infos)),
-           "roofline": {"bound": "hbm", "kernel": "k_smooth<double> (finest level, one colour pass)",
+           "roofline": {"bound": "hbm",
+                        "kernel": ("k_wave<double> (finest level, one red+black sweep per launch)" if wave
+                                   else "k_smooth<double> (finest level, one colour pass)"),
                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "peak_kind": peak_kind, "traffic": kernel_traffic("k_smooth_f64"),
+                        "peak_kind": peak_kind,
+                        "traffic": kernel_traffic("k_wave_f64" if wave else "k_smooth_f64"),
                         "algorithmic_bytes_per_launch": alg_bytes,
-                        "bytes_rule": "56 B/cell per red+black sweep = 28 B/cell per colour pass",
+                        "bytes_rule": ("56 B/cell per red+black sweep (48 for the sweep from a zero "
+                                       "correction, once per V-cycle), averaged over the launches" if wave
+                                       else "56 B/cell per red+black sweep = 28 B/cell per colour pass"),
                         "avg_launch_us": launch_s * 1e6, "launches_timed": sm_n, "passes_timed": sm_passes,
                         "fp64_pipe": {"ops_per_launch": fp64_ops, "achieved_gops": fp64_rate / 1e9,
                                       "peak_gops": fp64pk["fma_per_s"] / 1e9,

@@ -207,6 +207,22 @@ typedef struct {
                            wrapped.  Trilinear turns the one-block coarse end (fused_coarse) off
                            and, with this smoother, needs more V-cycles (abec64: 12 against 9).
                            The interpolation between AMR levels is not affected. */
+  int wave_sweep;       /* 1 (default): on MG levels whose ghosts are pushed, whose box widths are
+                           even and whose boxes meet face to face (every face copied whole from
+                           one box, or a wall; z-neighbours given opposite marching directions),
+                           each red-first Gauss-Seidel sweep runs as ONE wavefront launch:
+                           thread blocks take bands of rows of a box and march through its
+                           planes, updating the red cells of a plane and then the black cells
+                           of the plane before it; a block waits (bounded) for the bands beside
+                           it to report a plane's red cells before that plane's black cells.
+                           Each array is read from HBM about once per sweep instead of once per
+                           colour.  Bitwise the results of 0 (one launch per colour); the first
+                           pre-smoothing sweep from a zero correction computes its red cells as
+                           r / D itself (the outer residual then skips that half-sweep).
+                           Levels whose problems have more bands than the device holds at once,
+                           and the black-first post-smoothing of the symmetric V-cycle, keep
+                           one launch per colour.  A wait that gives up (it cannot in a correct
+                           build) makes the call return GMG_ERR_DEVICE_TIMEOUT.  0: off. */
 } gmg_params;
 
 typedef struct {
@@ -296,6 +312,16 @@ gmg_status gmg_mg_level_info(const gmg_ctx* ctx, int m, int* nboxes, int* dom);
    coarsened image (-1 on the bottom level) (Sec. "Linear Solvers": the coarsened
    BoxArrays of the multigrid hierarchy).  Either pointer may be NULL. */
 gmg_status gmg_mg_level_boxes(const gmg_ctx* ctx, int m, int* box_lohi, int* parents);
+
+/* The work tiles of the wavefront red-black sweep on MG level m (the smoother of Sec. "Linear
+   Solvers"; the tiling itself has no counterpart in the paper): *ntiles receives their number
+   and *ppt the cell pairs per thread (0: the level keeps one launch per colour).  out (may be
+   NULL) receives, for at most cap tiles in hand-out order, 13 ints each: box, first row y0,
+   end row y1, marching direction (0: planes upward), the tiles across the x-, x+, y-, y+ sides
+   and the z-, z+ faces (-1: a wall), the red planes the two z tiles must have reported before
+   the black cells of the first (z-) and last (z+) plane, and the tile's problem (batched
+   form).  Host only (no device work). */
+gmg_status gmg_wave_tiles(const gmg_ctx* ctx, int m, int* ntiles, int* ppt, int* out, int cap);
 
 /* Boxed layout of MG level m for element type dt: total elements, per-box element
    offsets (nboxes entries, may be NULL) and row strides sx (nboxes entries, may be

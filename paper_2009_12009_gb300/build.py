@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgmg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["kernels.cu", "bottom.cu", "meta.cpp", "capi.cpp", "noalloc.cu", "amr_meta.cpp", "amr_kernels.cu", "tail.cu", "flow.cu", "diag.cu",
-           "walls.cu", "krylov.cu"]
+           "walls.cu", "krylov.cu", "wave.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

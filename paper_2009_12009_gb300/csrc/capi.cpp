@@ -329,6 +329,11 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.n_ec_ghosts = (int)M.ec_ghosts.size();
     D.push_faces = (const PushFace*)cv.take(sizeof(PushFace) * M.push_faces.size());
     D.push_ok = M.push_ok ? 1 : 0;
+    D.wave_tiles = (const WaveTile*)cv.take(sizeof(WaveTile) * M.wave_tiles.size());
+    D.n_wave_tiles = (int)M.wave_tiles.size();
+    D.wave_ppt = M.wave_ppt;
+    D.wave_max_solve_tiles = M.wave_max_solve_tiles;
+    D.wave_cnt = M.wave_tiles.empty() ? nullptr : (unsigned*)cv.take(sizeof(unsigned) * (64 + M.wave_tiles.size()));
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
     B.acoef = (double*)cv.take_rows(8 * ne, 8);
     B.wx = (double*)cv.take_rows(8 * ne, 8);
@@ -402,6 +407,11 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.inv_count = (const double*)cv.take(sizeof(double) * M.inv_count.size());
     D.push_faces = (const PushFace*)cv.take(sizeof(PushFace) * M.push_faces.size());
     D.push_ok = M.push_ok ? 1 : 0;
+    D.wave_tiles = (const WaveTile*)cv.take(sizeof(WaveTile) * M.wave_tiles.size());
+    D.n_wave_tiles = (int)M.wave_tiles.size();
+    D.wave_ppt = M.wave_ppt;
+    D.wave_max_solve_tiles = M.wave_max_solve_tiles;
+    D.wave_cnt = M.wave_tiles.empty() ? nullptr : (unsigned*)cv.take(sizeof(unsigned) * (64 + M.wave_tiles.size()));
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
     B.acoef = (double*)cv.take_rows(8 * nf, 8);
     B.wx = (double*)cv.take_rows(8 * nf, 8);
@@ -525,6 +535,8 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, c->vc_flow_skip[m], M.vc_flow_skip))) return st;
     if ((st = upload(c, D.ec_ghosts, M.ec_ghosts))) return st;
     if ((st = upload(c, D.push_faces, M.push_faces))) return st;
+    if ((st = upload(c, D.wave_tiles, M.wave_tiles))) return st;
+    if (D.wave_cnt) CK(c, cudaMemsetAsync(D.wave_cnt, 0, sizeof(unsigned) * (64 + M.wave_tiles.size()), c->stream));
   }
   {
     const TailHost& T = c->tail;
@@ -601,6 +613,14 @@ gmg_status build_hierarchy(gmg_ctx* c, const std::vector<Box>& boxes, const std:
     if (!e.empty()) SETERR(c, GMG_ERR_BAD_INPUT, (ns > 1 ? "problem " + std::to_string(s) + ": " : std::string()) + e);
   }
   reset_problem(c);
+  {  // wavefront tiles: at most 8 blocks of the sweep per SM are assumed resident
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) ==
+                                                  cudaSuccess && nsm > 0)
+      set_wave_capacity(8 * nsm);
+    else
+      cudaGetLastError();
+  }
   LevelMeta L0;
   L0.boxes = boxes;
   L0.box_solve = box_solve;
@@ -696,6 +716,7 @@ bool push_on(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
   if (p.ghost_push == 0) return false;
   if (p.ghost_push == 1) return true;
   if (p.fused_sweep != 0 && flow_ok(c->dev[m])) return true;  // the dataflow sweep needs pushed ghosts
+  if (p.wave_sweep != 0 && wave_ok(c->dev[m])) return true;    // and so does the wavefront sweep
   const auto& ch = c->push_choice[dt];
   if (m < (int)ch.size() && ch[m] >= 0) return (ch[m] & 1) != 0;
   return c->L[m].ncells < (1 << 22);
@@ -765,6 +786,32 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
   if (prof) record_timing_event(c, ev[1], s);
 }
 
+// whether the sweeps of level m run as wavefront launches (wave.cu): wave_sweep on, the level
+// has wavefront tables and pushes its ghosts (red-first sweeps only)
+bool wave_on(const gmg_params& p, const LevelDev& D, bool push) { return p.wave_sweep != 0 && push && wave_ok(D); }
+
+// One red-black sweep (red, then black) of level m as two launches; phi_last: the black pass
+// also adds e to phi (k_smooth_update).
+void black_pass(gmg_ctx* c, const LevelDev& D, int dt, int m, cudaStream_t s, bool push, bool vec, double* phi_last,
+                bool push_phi) {
+  if (!phi_last) {
+    smooth_colour(c, D, dt, m, 1, s, true, push, vec);
+    return;
+  }
+  const LevelBufs& B = c->buf[m];
+  if (!push) launch_fill(dt, D, B.e[dt], 0, 0, s);
+  const bool prof = c->profiling && m == 0;
+  cudaEvent_t* ev = prof ? smooth_event(c, 1) : nullptr;
+  if (prof) record_timing_event(c, ev[0], s);
+  launch_smooth_update(dt, dir_view(c, D, m), B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, phi_last, push_phi, s);
+  if (prof) record_timing_event(c, ev[1], s);
+}
+void two_pass_sweep(gmg_ctx* c, const LevelDev& D, int dt, int m, cudaStream_t s, bool fill_red, bool push, bool vec,
+                    double* phi_last, bool push_phi) {
+  smooth_colour(c, D, dt, m, 0, s, fill_red, push, vec);
+  black_pass(c, D, dt, m, s, push, vec, phi_last, push_phi);
+}
+
 // nsweep red-black sweeps on level m.
 // e_zero: e is zero including its ghosts (just cleared), so the first ghost fill would
 // copy zeros and is skipped.
@@ -778,6 +825,28 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
                    bool e_zero = false, bool push = false, bool red_done = false, bool reverse = false,
                    double* phi_last = nullptr, bool push_phi = false) {
   if (nsweep <= 0) return;
+  if (!reverse && wave_on(p, D, push)) {
+    const LevelBufs& B = c->buf[m];
+    const Coefs k = coefs_of(c, m, dt);
+    for (int it = 0; it < nsweep; ++it) {
+      double* ph = (phi_last && it == nsweep - 1) ? phi_last : nullptr;
+      if (red_done && it == 0) {  // the residual kernel did this sweep's red cells
+        black_pass(c, D, dt, m, s, push, vec_on(c, p, dt, m), ph, push_phi);
+        continue;
+      }
+      const bool zero = e_zero && it == 0 && !ph;
+      const bool prof = c->profiling && m == 0;
+      cudaEvent_t* ev = prof ? smooth_event(c, 2) : nullptr;
+      if (prof) record_timing_event(c, ev[0], s);
+      const bool ran = launch_wave(dt, D, B.e[dt], B.r[dt], k, zero, ph, push_phi, c->dev_err, s);
+      if (prof) record_timing_event(c, ev[1], s);
+      if (!ran) {  // (a problem's tiles do not fit on the device at once)
+        if (prof) --c->n_ev_smooth;
+        two_pass_sweep(c, D, dt, m, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m), ph, push_phi);
+      }
+    }
+    return;
+  }
   if (flow_on(c, p, D, push)) {
     int first = reverse ? 1 : 0;
     int n = 2 * nsweep;
@@ -826,7 +895,7 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
 // the graph-cache value of the sweep choices: fused_sweep, the flow launch width, serpentine,
 // the interpolation
 int sweep_key(const gmg_params& p) {
-  return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine + 2048 * p.prolongation;
+  return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine + 2048 * p.prolongation + 4096 * p.wave_sweep;
 }
 
 // the symmetric V-cycle: post-smoothing black before red (asked for, or implied by the
@@ -943,6 +1012,9 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
 // whether level 0's V-cycle pushes ghosts (then that red half-sweep pushes too).
 bool resid_red(const gmg_ctx* c, const gmg_params& p, int dt) {
   const LevelDev& D = c->dev[0];
+  // (with the wavefront sweep on level 0, its first pre-smoothing sweep starts from e = 0
+  // itself: r / D on red cells, then the black cells, in one launch)
+  if (p.wave_sweep != 0 && push_on(c, p, dt, 0) && D.push_ok && wave_ok(D)) return false;
   return p.fuse_residual_sweep != 0 && p.nu1 > 0 && nlev(c) > 1 && D.n_pair_chunks > 0;
 }
 bool level0_push(const gmg_ctx* c, const gmg_params& p, int dt) {
@@ -1033,6 +1105,7 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.flow_lag_kcells < 0) SETERR(c, GMG_ERR_BAD_INPUT, "flow_lag_kcells must be >= 0");
   if (p.serpentine != 0 && p.serpentine != 1) SETERR(c, GMG_ERR_BAD_INPUT, "serpentine must be 0 or 1");
   if (p.prolongation != 0 && p.prolongation != 1) SETERR(c, GMG_ERR_BAD_INPUT, "prolongation must be 0 or 1");
+  if (p.wave_sweep != 0 && p.wave_sweep != 1) SETERR(c, GMG_ERR_BAD_INPUT, "wave_sweep must be 0 or 1");
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
@@ -2241,6 +2314,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->flow_lag_kcells = 0;
   p->serpentine = 1;
   p->prolongation = 0;
+  p->wave_sweep = 1;
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;
@@ -2433,6 +2507,21 @@ gmg_status gmg_mg_level_boxes(const gmg_ctx* c, int m, int* lohi, int* parents) 
       }
     if (parents) parents[b] = M.parent[b];
   }
+  return GMG_OK;
+}
+
+gmg_status gmg_wave_tiles(const gmg_ctx* c, int m, int* ntiles, int* ppt, int* out, int cap) {
+  if (!c || m < 0 || m >= (int)c->L.size() || cap < 0) return GMG_ERR_BAD_INPUT;
+  const LevelMeta& M = c->L[m];
+  if (ntiles) *ntiles = (int)M.wave_tiles.size();
+  if (ppt) *ppt = M.wave_ppt;
+  if (out)
+    for (int t = 0; t < (int)M.wave_tiles.size() && t < cap; ++t) {
+      const WaveTile& W = M.wave_tiles[t];
+      const int row[13] = {W.box,   W.y0,    W.y1,    W.dir,      W.nb[0],    W.nb[1],   W.nb[2],
+                           W.nb[3], W.zb[0], W.zb[1], W.zneed[0], W.zneed[1], W.solve};
+      for (int u = 0; u < 13; ++u) out[13 * t + u] = row[u];
+    }
   return GMG_OK;
 }
 

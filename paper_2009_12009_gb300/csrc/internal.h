@@ -132,6 +132,33 @@ constexpr int FLOW_WARPS_PER_SM = 32;       // default resident warps per SM
 constexpr int FLOW_QUEUES = 16;             // hand-out counters (chunk k is handed out by queue k % FLOW_QUEUES)
 constexpr int FLOW_CNT_STRIDE = 32;         // ints between completion counters (one 128-byte line each)
 
+// Wavefront red-black sweep (wave.cu): one launch performs one whole Gauss-Seidel sweep
+// (red then black) of a level, in place.  The level is cut into tiles -- a band of rows
+// [y0, y1) of one box, all its x and all its planes -- and one thread block per tile marches
+// through the tile's planes: at step m it updates the red cells of plane m (in the tile's
+// marching order), then the black cells of plane m - 1.  A black cell on the tile's border
+// reads red cells of the tile next to it, so before the black cells of a plane the block
+// waits until each neighbouring tile has reported its red cells of that plane done; a red
+// cell reads black cells of the neighbours, which they update only after this tile's report.
+// Boxes next to each other along z march in opposite directions (their shared face is the
+// first plane of both, or the last of both), and boxes next to each other along x or y march
+// alike, so every wait is for a step the other tile reaches earlier: no wait can deadlock.
+struct WaveTile {
+  int box;
+  int y0, y1;     // rows [y0, y1) of the box
+  int dir;        // 0: planes 0, 1, ..., nz - 1; 1: nz - 1, ..., 0
+  int nb[4];      // tiles across the x-, x+, y-, y+ sides whose reds of a plane this tile's blacks
+                  // of that plane wait for (same planes, same marching order); -1: a wall
+  int zb[2];      // tiles across the z- and z+ faces (-1: a wall)
+  int zneed[2];   // red planes those tiles must have reported before the blacks of plane 0
+                  // (z-) and of plane nz - 1 (z+)
+  int solve;
+};
+
+constexpr int WAVE_BLOCK = 128;       // threads per block of the wavefront sweep
+constexpr int WAVE_MAX_PPT = 4;       // cell pairs per thread (a tile holds up to WAVE_BLOCK * WAVE_MAX_PPT)
+constexpr int WAVE_MAX_PLANES = 4095; // planes of a box the sweep handles (a 12-bit count)
+
 // The coarse end of one problem's V-cycle run by one thread block (tail.cu): levels
 // m0..mb of that problem, mb its bottom.  Cell and ghost lists reuse BotCell / BotGhost.
 constexpr int TAIL_MAXLEV = 20;       // MG levels addressable by the tail kernel

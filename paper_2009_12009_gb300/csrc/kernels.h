@@ -63,6 +63,13 @@ struct LevelDev {
   int* flow_cnt = nullptr;  // (FLOW_QUEUES + 1 + FLOW_MAX_PHASES * n_flow_slabs) * FLOW_CNT_STRIDE ints,
                             // zero between launches
   const int* flow_skip = nullptr;  // per solve: 1 = leave its items out (null: none)
+  // wavefront red-black sweep (wave.cu): the level's tiles in hand-out order (problem by
+  // problem); n_wave_tiles == 0: no wavefront sweep on this level
+  const WaveTile* wave_tiles = nullptr;
+  int n_wave_tiles = 0;
+  int wave_ppt = 0;              // cell pairs per thread of the level's tiles (1, 2 or 4)
+  int wave_max_solve_tiles = 0;  // tiles of the problem that has the most
+  unsigned* wave_cnt = nullptr;  // 64 + n_wave_tiles words, zero between launches
   const PushFace* push_faces = nullptr;  // 6 per box (ghost push targets)
   int push_ok = 0;                       // push_faces usable for every box of the level
   const BotGhost* ec_ghosts = nullptr;  // edge and corner ghosts (levels >= 1), f[dst] = sign f[src]
@@ -185,6 +192,19 @@ struct BottomArgs {
 };
 void launch_bottom(int dt, const LevelDev& L, const void* rhs, void* x, const Coefs& c64, const BottomArgs& a,
                    cudaStream_t s);
+
+// ---- wavefront red-black sweep (wave.cu) ----
+// whether level L has wavefront-sweep tables (and pushed ghosts)
+bool wave_ok(const LevelDev& L);
+// One whole red-black sweep (red, then black) of level L in one launch, in place on e, with
+// the values of two launch_smooth passes with push (bitwise).  zero_start: e is zero
+// (valid cells and ghosts) before the sweep, so the red cells are rhs / D.  phi (double,
+// level 0 only, not with zero_start): also phi += e on every smoothed cell afterwards, as
+// launch_smooth_update does (push_phi: phi's new values into its ghosts).  A dependency wait
+// that gives up sets *err.  Returns false (nothing launched) when the level has no tables or
+// the problem with the most tiles cannot have them all resident at once.
+bool launch_wave(int dt, const LevelDev& L, void* e, const void* rhs, const Coefs& c, bool zero_start, double* phi,
+                 bool push_phi, int* err, cudaStream_t s);
 
 // ---- dataflow red-black sweeps (flow.cu) ----
 // whether level L has flow tables and pushes its ghosts (the flow kernel keeps every ghost

@@ -5,6 +5,7 @@
 #include <map>
 #include <tuple>
 #include <cstdio>
+#include <functional>
 
 namespace gmg {
 
@@ -266,6 +267,160 @@ static void build_flow(LevelMeta& L) {
   build_flow_order(L, FLOW_LAG_CELLS);
 }
 
+static int g_wave_capacity = 8 * 152;
+void set_wave_capacity(int blocks) { g_wave_capacity = std::max(1, blocks); }
+int wave_capacity() { return g_wave_capacity; }
+
+// Wavefront tables.  Face f = 2 d + side of box b is described by its one ghost rectangle:
+// a wall, or a copy from box Y whose face matches b's (same extents and offsets across the
+// face, so b's row bands and planes are Y's).  Marching directions come from a union-find
+// with parity over the boxes (x and y neighbours: same direction; z neighbours: opposite);
+// a contradiction -- an odd number of boxes around a periodic z, one box periodic in z --
+// leaves the level without tables.
+void build_wave(LevelMeta& L, int max_resident) {
+  L.wave_tiles.clear();
+  L.wave_ppt = 0;
+  L.wave_max_solve_tiles = 0;
+  if (L.allow_cf || !L.push_ok) return;
+  const int nb = (int)L.boxes.size();
+  std::vector<char> sm(nb, 0);
+  int max_npx = 0, max_ny = 1, nsm = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (L.solve_bottom[L.box_solve[b]]) continue;
+    const Box& B = L.boxes[b];
+    if (B.n(0) % 2 != 0 || B.n(0) < 2 || B.n(2) > WAVE_MAX_PLANES) return;
+    sm[b] = 1;
+    ++nsm;
+    max_npx = std::max(max_npx, B.n(0) / 2);
+    max_ny = std::max(max_ny, B.n(1));
+  }
+  if (!nsm) return;
+  struct Face {
+    int count = 0, kind = -1, box = -1;
+  };
+  std::vector<Face> face((size_t)nb * 6);
+  for (const GhostRect& g : L.ghosts) {
+    const int X = g.dst_box;
+    if (!sm[X]) continue;
+    const int d = 3 - g.d1 - g.d2;
+    const Box& BX = L.boxes[X];
+    const int side = g.dst[d] < 0 ? 0 : 1;
+    Face& F = face[(size_t)X * 6 + 2 * d + side];
+    F.count++;
+    F.kind = g.kind;
+    F.box = g.src_box;
+    if (g.kind == 2) return;
+    if (g.n1 != BX.n(g.d1) || g.n2 != BX.n(g.d2) || g.dst[g.d1] != 0 || g.dst[g.d2] != 0) return;
+    if (g.kind == 0) {
+      const Box& BY = L.boxes[g.src_box];
+      if (!sm[g.src_box] || g.src[g.d1] != 0 || g.src[g.d2] != 0 || BY.n(g.d1) != BX.n(g.d1) ||
+          BY.n(g.d2) != BX.n(g.d2))
+        return;
+    }
+  }
+  for (int b = 0; b < nb; ++b)
+    if (sm[b])
+      for (int f = 0; f < 6; ++f)
+        if (face[(size_t)b * 6 + f].count != 1) return;
+  // marching directions
+  std::vector<int> up(nb), rel(nb, 0);
+  for (int b = 0; b < nb; ++b) up[b] = b;
+  std::function<int(int)> find = [&](int x) {
+    if (up[x] == x) return x;
+    const int r = find(up[x]);
+    rel[x] ^= rel[up[x]];
+    up[x] = r;
+    return r;
+  };
+  for (int b = 0; b < nb; ++b) {
+    if (!sm[b]) continue;
+    for (int f = 0; f < 6; ++f) {
+      const Face& F = face[(size_t)b * 6 + f];
+      if (F.kind != 0) continue;
+      const int want = f >= 4 ? 1 : 0;  // z neighbours march the other way
+      const int ra = find(b), rb = find(F.box);
+      if (ra == rb) {
+        if ((rel[b] ^ rel[F.box]) != want) return;
+      } else {
+        up[ra] = rb;
+        rel[ra] = rel[b] ^ rel[F.box] ^ want;
+      }
+    }
+  }
+  std::vector<int> dir(nb, 0);
+  for (int b = 0; b < nb; ++b)
+    if (sm[b]) {
+      find(b);
+      dir[b] = rel[b];
+    }
+  // tile height: the fewest cell pairs per thread with every problem's tiles resident at once
+  const int ns = (int)L.geoms.size();
+  int ppt = 0, ty = 0, most = 0;
+  for (int cand : {1, 2, 4}) {
+    if (max_npx > WAVE_BLOCK * cand) continue;
+    const int h = std::max(1, std::min(max_ny, WAVE_BLOCK * cand / max_npx));
+    std::vector<int> per(ns, 0);
+    for (int b = 0; b < nb; ++b)
+      if (sm[b]) per[L.box_solve[b]] += (L.boxes[b].n(1) + h - 1) / h;
+    const int mx = *std::max_element(per.begin(), per.end());
+    if (mx <= max_resident) {
+      ppt = cand;
+      ty = h;
+      most = mx;
+      break;
+    }
+  }
+  if (!ppt) return;
+  std::vector<int> first(nb, -1), count(nb, 0);
+  std::vector<WaveTile> tiles;
+  for (int b = 0; b < nb; ++b) {  // (boxes are stored problem by problem)
+    if (!sm[b]) continue;
+    first[b] = (int)tiles.size();
+    const int ny = L.boxes[b].n(1);
+    for (int y0 = 0; y0 < ny; y0 += ty) {
+      WaveTile t{};
+      t.box = b;
+      t.y0 = y0;
+      t.y1 = std::min(ny, y0 + ty);
+      t.dir = dir[b];
+      t.solve = L.box_solve[b];
+      tiles.push_back(t);
+    }
+    count[b] = (int)tiles.size() - first[b];
+  }
+  for (int b = 0; b < nb; ++b) {
+    if (!sm[b]) continue;
+    const int nzb = L.boxes[b].n(2);
+    (void)nzb;
+    for (int u = 0; u < count[b]; ++u) {
+      WaveTile& t = tiles[first[b] + u];
+      const Face* F = &face[(size_t)b * 6];
+      for (int side = 0; side < 2; ++side)  // x: the band of the same rows in the neighbour
+        t.nb[side] = F[side].kind == 0 ? first[F[side].box] + u : -1;
+      t.nb[2] = u > 0 ? first[b] + u - 1 : (F[2].kind == 0 ? first[F[2].box] + count[F[2].box] - 1 : -1);
+      t.nb[3] = u + 1 < count[b] ? first[b] + u + 1 : (F[3].kind == 0 ? first[F[3].box] : -1);
+      for (int side = 0; side < 2; ++side) {
+        const Face& G = F[4 + side];
+        if (G.kind != 0) {
+          t.zb[side] = -1;
+          t.zneed[side] = 0;
+          continue;
+        }
+        const int Y = G.box;
+        t.zb[side] = first[Y] + u;
+        const int nzy = L.boxes[Y].n(2);
+        // the plane of Y next to this face: its last (z-) or first (z+) plane
+        const bool y_last_plane = side == 0;
+        const bool y_marches_up = dir[Y] == 0;
+        t.zneed[side] = (y_last_plane == y_marches_up) ? nzy : 1;
+      }
+    }
+  }
+  L.wave_tiles = tiles;
+  L.wave_ppt = ppt;
+  L.wave_max_solve_tiles = most;
+}
+
 // The dispense order: (phase, slab) groups sorted by a position tau, in cells of the whole
 // level: tau(0, s) = the level's cells times the fraction of its problem's slabs up to and
 // including s (every problem advances at the same pace), tau(c, s) = lag + the largest
@@ -482,6 +637,7 @@ std::string finalize_level(LevelMeta& L) {
   }
   build_bottom(L);
   build_flow(L);
+  build_wave(L, g_wave_capacity);
   return "";
 }
 

@@ -98,6 +98,13 @@ struct LevelMeta {
   // flow launches skip its items
   std::vector<int> vc_flow_skip;
 
+  // wavefront sweep (wave.cu, tables by build_wave; empty when the level cannot run it): the
+  // tiles in hand-out order (problem by problem), cell pairs per thread, and the number of
+  // tiles of the problem that has the most
+  std::vector<WaveTile> wave_tiles;
+  int wave_ppt = 0;
+  int wave_max_solve_tiles = 0;
+
   // edge and corner ghosts (built on demand by build_ec_ghosts): f[dst] = sign * f[src]
   std::vector<BotGhost> ec_ghosts;
   bool ec_built = false;
@@ -136,6 +143,20 @@ std::string finalize_level(LevelMeta& L);
 // -1 <-> cell 0) with the factor -1 for a Dirichlet wall and +1 for a Neumann wall.  Used by
 // the trilinear interpolation, which reads the coarse correction diagonally.
 void build_ec_ghosts(LevelMeta& L);
+
+// Tables of the wavefront sweep (wave.cu) for a level whose layout, ghost rectangles and push
+// faces are built.  The rows of every smoothed box are cut into bands of one height per level,
+// each a tile; tile sizes are chosen so that every problem has at most `max_resident` tiles
+// (the blocks of the sweep kernel the device holds at once).  Left empty (the level keeps one
+// launch per colour) unless the ghosts are pushed, every box width is even, every box face
+// is copied whole from one box (or is a wall) with rows and planes aligned, and the boxes of
+// each problem can be given marching directions with z-neighbours opposite and x- and
+// y-neighbours alike.
+void build_wave(LevelMeta& L, int max_resident);
+// Blocks of the wavefront sweep the device is assumed to hold at once when tables are built
+// (default 8 per SM on 152 SMs); the launch checks the real figure.
+void set_wave_capacity(int blocks);
+int wave_capacity();
 
 // Rebuild a level's flow dispense orders for a dispense lag of `lag` cells (same sizes).
 void build_flow_order(LevelMeta& L, int64_t lag);

@@ -68,8 +68,8 @@ def test_flow_tables_exist(ctx):
     smoother launches of a flow solve cover several colour passes each."""
     cfg, C = ctx
     rhs = C.pack(torch.from_numpy(cfg["rhs"]))
-    _, i1 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=1, profile=1, project_mean=1)
-    _, i0 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=0, profile=1, project_mean=1)
+    _, i1 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=1, wave_sweep=0, profile=1, project_mean=1)
+    _, i0 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=0, wave_sweep=0, profile=1, project_mean=1)
     assert i1.smooth0_passes == i0.smooth0_passes == i0.smooth0_launches
     assert i1.smooth0_launches < i1.smooth0_passes
     assert i1.kernel_launches < i0.kernel_launches
@@ -80,8 +80,8 @@ def test_flow_vcycle_is_bitwise_two_pass(ctx, dt):
     cfg, C = ctx
     r = cfg["rhs"] - (cfg["rhs"].mean() if cfg["bc_lo"] == [P_] * 3 else 0.0)
     rb = C.pack(torch.from_numpy(r), 0, dt)
-    e1 = C.unpack(C.vcycle(rb, dt, fused_sweep=1), 0, dt)
-    e0 = C.unpack(C.vcycle(rb, dt, fused_sweep=0), 0, dt)
+    e1 = C.unpack(C.vcycle(rb, dt, fused_sweep=1, wave_sweep=0), 0, dt)
+    e0 = C.unpack(C.vcycle(rb, dt, fused_sweep=0, wave_sweep=0), 0, dt)
     assert torch.equal(e1, e0)
 
 
@@ -92,9 +92,9 @@ def test_flow_solve_is_bitwise_two_pass(ctx, prec, graph):
     the last phase, CUDA-graph replay or direct launches): the same iterates and histories."""
     cfg, C = ctx
     rhs = C.pack(torch.from_numpy(cfg["rhs"]))
-    p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=3, precision=prec, use_graph=graph, fused_sweep=1, project_mean=1)
+    p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=3, precision=prec, use_graph=graph, fused_sweep=1, wave_sweep=0, project_mean=1)
     a1 = C.unpack(p1).clone()
-    p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=3, precision=prec, use_graph=graph, fused_sweep=0, project_mean=1)
+    p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=3, precision=prec, use_graph=graph, fused_sweep=0, wave_sweep=0, project_mean=1)
     assert torch.equal(a1, C.unpack(p0))
     assert i1.history() == i0.history()
 
@@ -105,9 +105,9 @@ def test_flow_more_phases_than_one_launch(ctx, nu):
     cfg, C = ctx
     rhs = C.pack(torch.from_numpy(cfg["rhs"]))
     kw = dict(tol_rel=0.0, max_iter=2, nu1=nu[0], nu2=nu[1], project_mean=1)
-    p1, _ = C.solve(rhs, fused_sweep=1, **kw)
+    p1, _ = C.solve(rhs, fused_sweep=1, wave_sweep=0, **kw)
     a1 = C.unpack(p1).clone()
-    p0, _ = C.solve(rhs, fused_sweep=0, **kw)
+    p0, _ = C.solve(rhs, fused_sweep=0, wave_sweep=0, **kw)
     assert torch.equal(a1, C.unpack(p0))
 
 
@@ -117,13 +117,13 @@ def test_flow_symmetric_vcycle_and_cg():
     cfg = _case("dir64")
     C = _ctx(cfg, krylov=True)
     rb = C.pack(torch.from_numpy(cfg["rhs"]))
-    e1 = C.unpack(C.vcycle(rb, gmg.DT_F64, fused_sweep=1, post_reverse=1))
-    e0 = C.unpack(C.vcycle(rb, gmg.DT_F64, fused_sweep=0, post_reverse=1))
+    e1 = C.unpack(C.vcycle(rb, gmg.DT_F64, fused_sweep=1, wave_sweep=0, post_reverse=1))
+    e0 = C.unpack(C.vcycle(rb, gmg.DT_F64, fused_sweep=0, wave_sweep=0, post_reverse=1))
     assert torch.equal(e1, e0)
     for kry in (1, 2):
-        p1, i1 = C.solve(rb, tol_rel=0.0, max_iter=3, krylov=kry, fused_sweep=1)
+        p1, i1 = C.solve(rb, tol_rel=0.0, max_iter=3, krylov=kry, fused_sweep=1, wave_sweep=0)
         a1 = C.unpack(p1).clone()
-        p0, i0 = C.solve(rb, tol_rel=0.0, max_iter=3, krylov=kry, fused_sweep=0)
+        p0, i0 = C.solve(rb, tol_rel=0.0, max_iter=3, krylov=kry, fused_sweep=0, wave_sweep=0)
         assert torch.equal(a1, C.unpack(p0)), kry
         assert i1.history() == i0.history()
 
@@ -150,9 +150,9 @@ def test_flow_batched_with_active_mask():
     B.set_beta_all([torch.from_numpy(p["beta"]) for p in probs])
     rhs = B.pack_all([torch.from_numpy(p["rhs"]) for p in probs])
     for prec in (gmg.FP64, gmg.MIXED_FP32):
-        p1, i1 = B.batch_solve(rhs, tol_rel=1e-10, precision=prec, fused_sweep=1)
+        p1, i1 = B.batch_solve(rhs, tol_rel=1e-10, precision=prec, fused_sweep=1, wave_sweep=0)
         a1 = [B.unpack_solve(s, p1).clone() for s in range(len(probs))]
-        p0, i0 = B.batch_solve(rhs, tol_rel=1e-10, precision=prec, fused_sweep=0)
+        p0, i0 = B.batch_solve(rhs, tol_rel=1e-10, precision=prec, fused_sweep=0, wave_sweep=0)
         its = []
         for s in range(len(probs)):
             assert i1[s].status == i0[s].status == gmg.OK

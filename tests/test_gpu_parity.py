@@ -309,7 +309,8 @@ def test_profiled_solve_times_kernels(graph):
     pair = Pair("uneven", mixed=False)
     rhs = pair.C.pack(torch.from_numpy(pair.cfg["rhs"]))
     for fuse, per_iter in ((0, 8), (1, 7)):  # fused: the first red half-sweep runs in the residual
-        phi, info = pair.C.solve(rhs, tol_rel=0.0, max_iter=3, use_graph=graph, profile=1, fuse_residual_sweep=fuse)
+        phi, info = pair.C.solve(rhs, tol_rel=0.0, max_iter=3, use_graph=graph, profile=1, fuse_residual_sweep=fuse,
+                                 wave_sweep=0)
         assert info.status == gmg.NOT_CONVERGED  # tol 0 is never reached; 3 iterations run
         assert info.smooth0_launches == 3 * per_iter and info.resid0_launches == 3
         assert info.smooth0_ms > 0 and info.resid0_ms > 0
@@ -369,13 +370,13 @@ def test_fused_sweep_is_bitwise_two_half_sweeps(case):
     r = torch.from_numpy(cfg["rhs"] - (cfg["rhs"].mean() if cfg["bc_lo"][0] == gmg.PERIODIC else 0.0))
     for dt in DTS:
         rb = C.pack(r, 0, dt)
-        e1 = C.vcycle(rb, dt, fused_sweep=1)
-        e0 = C.vcycle(rb, dt, fused_sweep=0)
+        e1 = C.vcycle(rb, dt, fused_sweep=1, wave_sweep=0)
+        e0 = C.vcycle(rb, dt, fused_sweep=0, wave_sweep=0)
         assert torch.equal(C.unpack(e1, 0, dt), C.unpack(e0, 0, dt)), dt
     rhs = C.pack(r)
-    p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=1, project_mean=1)
+    p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=1, project_mean=1, wave_sweep=0)
     a1 = C.unpack(p1).clone()
-    p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=0, project_mean=1)
+    p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=2, fused_sweep=0, project_mean=1, wave_sweep=0)
     assert torch.equal(a1, C.unpack(p0))
     assert i1.kernel_launches < i0.kernel_launches
 
@@ -477,10 +478,10 @@ def test_residual_fused_first_red_sweep_is_exact(name):
     for prec in (gmg.FP64, gmg.MIXED_FP32, gmg.MIXED_BF16):
         for push in (0, 1):
             p1, i1 = C.solve(rhs, tol_rel=0.0, max_iter=4, precision=prec, ghost_push=push, fuse_residual_sweep=1,
-                             project_mean=1)
+                             project_mean=1, wave_sweep=0)
             a1 = C.unpack(p1).clone()
             p0, i0 = C.solve(rhs, tol_rel=0.0, max_iter=4, precision=prec, ghost_push=push, fuse_residual_sweep=0,
-                             project_mean=1)
+                             project_mean=1, wave_sweep=0)
             assert torch.equal(a1, C.unpack(p0)), (prec, push)
             assert i1.kernel_launches < i0.kernel_launches
 
