@@ -333,6 +333,7 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.n_wave_tiles = (int)M.wave_tiles.size();
     D.wave_ppt = M.wave_ppt;
     D.wave_max_solve_tiles = M.wave_max_solve_tiles;
+    D.wave_layer_cells = M.wave_layer_cells;
     D.wave_cnt = M.wave_tiles.empty() ? nullptr : (unsigned*)cv.take(sizeof(unsigned) * (64 + M.wave_tiles.size()));
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
     B.acoef = (double*)cv.take_rows(8 * ne, 8);
@@ -411,6 +412,7 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.n_wave_tiles = (int)M.wave_tiles.size();
     D.wave_ppt = M.wave_ppt;
     D.wave_max_solve_tiles = M.wave_max_solve_tiles;
+    D.wave_layer_cells = M.wave_layer_cells;
     D.wave_cnt = M.wave_tiles.empty() ? nullptr : (unsigned*)cv.take(sizeof(unsigned) * (64 + M.wave_tiles.size()));
     maxchunks = std::max(maxchunks, D.n_cell_chunks);
     B.acoef = (double*)cv.take_rows(8 * nf, 8);
@@ -2314,7 +2316,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->flow_lag_kcells = 0;
   p->serpentine = 1;
   p->prolongation = 0;
-  p->wave_sweep = 1;
+  p->wave_sweep = 0;
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;

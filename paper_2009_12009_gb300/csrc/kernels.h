@@ -69,6 +69,7 @@ struct LevelDev {
   int n_wave_tiles = 0;
   int wave_ppt = 0;              // cell pairs per thread of the level's tiles (1, 2 or 4)
   int wave_max_solve_tiles = 0;  // tiles of the problem that has the most
+  int64_t wave_layer_cells = 0;  // cells of one plane of every tiled box
   unsigned* wave_cnt = nullptr;  // 64 + n_wave_tiles words, zero between launches
   const PushFace* push_faces = nullptr;  // 6 per box (ghost push targets)
   int push_ok = 0;                       // push_faces usable for every box of the level

@@ -281,6 +281,7 @@ void build_wave(LevelMeta& L, int max_resident) {
   L.wave_tiles.clear();
   L.wave_ppt = 0;
   L.wave_max_solve_tiles = 0;
+  L.wave_layer_cells = 0;
   if (L.allow_cf || !L.push_ok) return;
   const int nb = (int)L.boxes.size();
   std::vector<char> sm(nb, 0);
@@ -419,6 +420,9 @@ void build_wave(LevelMeta& L, int max_resident) {
   L.wave_tiles = tiles;
   L.wave_ppt = ppt;
   L.wave_max_solve_tiles = most;
+  L.wave_layer_cells = 0;
+  for (int b = 0; b < nb; ++b)
+    if (sm[b]) L.wave_layer_cells += (int64_t)L.boxes[b].n(0) * L.boxes[b].n(1);
 }
 
 // The dispense order: (phase, slab) groups sorted by a position tau, in cells of the whole

@@ -104,6 +104,7 @@ struct LevelMeta {
   std::vector<WaveTile> wave_tiles;
   int wave_ppt = 0;
   int wave_max_solve_tiles = 0;
+  int64_t wave_layer_cells = 0;  // cells of one plane of every tiled box (one step of every tile)
 
   // edge and corner ghosts (built on demand by build_ec_ghosts): f[dst] = sign * f[src]
   std::vector<BotGhost> ec_ghosts;

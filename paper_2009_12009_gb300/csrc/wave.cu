@@ -93,25 +93,58 @@ __device__ __forceinline__ void wave_wait(const unsigned* prog, int t, unsigned 
   }
 }
 
+// Ask L2 to fetch rows [j0, j1] of plane k of a field of box B (valid x extent, whole
+// 16-byte units): one bulk prefetch per row, no registers, no completion to wait for.
+template <class V>
+__device__ __forceinline__ void prefetch_rows(const V* f, const DevBox& B, int j0, int j1, int k, int lane, int nl) {
+  const unsigned bytes = ((unsigned)B.nx * (unsigned)sizeof(V)) & ~15u;
+  if (!bytes) return;
+  for (int j = j0 + lane; j <= j1; j += nl) {
+    const V* p = f + elem_index(B, 0, j, k);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+  }
+}
+
+// The 14 operands of one Gauss-Seidel update in k_smooth's order: rhs, the x-, x+, y-, y+, z-,
+// z+ face weights with their neighbours, 1/D.
+template <class A>
+struct Upd {
+  A r, d, w[6], n[6];
+};
+
+template <class A>
+__device__ __forceinline__ A gs_value(const Upd<A>& o) {
+  A s = o.r;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) s = fma(o.w[f], o.n[f], s);
+  return s * o.d;
+}
+
 // MODE 0: a sweep of e in place.  MODE 1: the first sweep from e = 0 (valid cells and ghosts):
 // the red cells are rhs / D without reading e (the two-pass sweep's products with zeros leave
 // rhs + 0).  MODE 2: a sweep of e, then phi += e on both cells of every pair (the last pass of
 // the finest level's post-smoothing, as k_smooth_update), phi's new values pushed into its
 // ghosts when push_phi is given.
-template <class T, int PPT, int MODE>
-__global__ void __launch_bounds__(WAVE_BLOCK, 8)
+//
+// A tile advances in steps of `slab` planes (in its marching order): the red cells of the
+// step's planes, a report, then the black cells of every plane whose reds on both sides are
+// done (all but the step's last plane, all of them in the last step); the next step's rows are
+// prefetched into L2 meanwhile.  A thread's updates within a pass follow one another (the
+// compiler keeps a load behind an earlier store that might alias it), so a block has one
+// update per thread in flight.
+template <class T, int PPT, int MODE, int MINB>
+__global__ void __launch_bounds__(WAVE_BLOCK, MINB)
     k_wave(const DevBox* __restrict__ boxes, const WaveTile* __restrict__ tiles, int ntiles, unsigned* cnt, T* e,
            const T* __restrict__ rhs, const typename CoefOf<T>::type* __restrict__ wx,
            const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
            const typename CoefOf<T>::type* __restrict__ invD, const int* __restrict__ active,
            const int* __restrict__ skip, const PushFace* __restrict__ push, double* phi,
-           const PushFace* __restrict__ push_phi, int* err) {
+           const PushFace* __restrict__ push_phi, int* err, int slab) {
   using A = typename Arith<T>::type;
   wv_pdl_wait();
   __shared__ int s_tile;
   __shared__ int s_last;
   __shared__ unsigned s_seen[6];
-  __shared__ A s_red[3][WAVE_BLOCK * PPT];  // red values of the last three planes, by pair
   unsigned* prog = cnt + 2 * WAVE_CTL_STRIDE;
   const int tid = threadIdx.x;
   if (tid == 0) s_tile = (int)atomicAdd(cnt, 1u);
@@ -129,12 +162,9 @@ __global__ void __launch_bounds__(WAVE_BLOCK, 8)
     const int64_t sx = B.sx, sy = B.sy;
     const int par = B.lo[0] + B.lo[1] + B.lo[2];
     const int dir = W.dir;
-    const int64_t zs = dir ? -sy : sy;  // element step to the next plane in marching order
-    int64_t q0[PPT];                    // element of cell (i0, j, 0) of the pair
+    int64_t q0[PPT];  // element of cell (i0, j, 0) of the pair
     int pj[PPT], pr[PPT], ppx[PPT];
     bool ok[PPT];
-    A pt[PPT], zn[PPT];  // black values (old) for the next red: at (red, prev plane), (black, this plane)
-    A Ra[PPT], Rb[PPT];  // red values of the pair at steps m - 2 and m - 1
 #pragma unroll
     for (int u = 0; u < PPT; ++u) {
       const int p = tid + u * WAVE_BLOCK;
@@ -144,122 +174,133 @@ __global__ void __launch_bounds__(WAVE_BLOCK, 8)
       pr[u] = r;
       pj[u] = W.y0 + r;
       q0[u] = elem_index(B, 2 * ppx[u], pj[u], 0);
-      pt[u] = zn[u] = Ra[u] = Rb[u] = (A)0;
     }
-    for (int m = 0; m <= nz; ++m) {
-      const int k = dir ? nz - 1 - m : m;  // plane of this step's red cells (m < nz)
-      A Rc[PPT];
-      if (m < nz) {
-        A* sr = s_red[m % 3];
+    const int warp = tid >> 5, lane = tid & 31;
+    int bdone = 0;  // black planes done (marching order)
+    for (int r0 = 0; r0 < nz; r0 += slab) {
+      const int r1 = min(nz, r0 + slab);  // red planes [r0, r1) of this step
+      // L2 prefetch of the next step's planes (warps 0..3, rows by lane)
+      if (r1 < nz && warp < 4) {
+        const int n1 = min(nz, r1 + slab);
+        for (int mq = r1; mq < n1; ++mq) {
+          const int kk = dir ? nz - 1 - mq : mq;
+          if (warp == 0) {
+            prefetch_rows(e, B, W.y0 - 1, W.y1, kk, lane, 32);
+          } else if (warp == 1) {
+            prefetch_rows(rhs, B, W.y0, W.y1 - 1, kk, lane, 32);
+            prefetch_rows(invD, B, W.y0, W.y1 - 1, kk, lane, 32);
+          } else if (warp == 2) {
+            prefetch_rows(wx, B, W.y0, W.y1 - 1, kk, lane, 32);
+            prefetch_rows(wy, B, W.y0, W.y1, kk, lane, 32);
+          } else {
+            prefetch_rows(wz, B, W.y0, W.y1 - 1, kk + (dir ? 0 : 1), lane, 32);
+          }
+        }
+      }
+      // red pass: planes [r0, r1); every neighbour read is a black cell not yet updated
+      for (int mq = r0; mq < r1; ++mq) {
+        const int k = dir ? nz - 1 - mq : mq;
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
-          Rc[u] = (A)0;
           if (!ok[u]) continue;
           const int off = (par + pj[u] + k) & 1;  // the red cell of the pair is i0 + off
           const int64_t q = q0[u] + (int64_t)k * sy + off;
+          Upd<A> o;
+          o.r = ldg(rhs + q);
+          o.d = ldg(invD + q);
           A s;
           if (MODE == 1) {
-            s = (A)ldg(rhs + q) + (A)0;
+            s = (o.r + (A)0) * o.d;
           } else {
-            const A partner = m == 0 ? (A)ld(e + q + (off ? -1 : 1)) : zn[u];
-            const A zprev = m == 0 ? (A)ld(e + q - zs) : pt[u];
-            const A znext = (A)ld(e + q + zs);
-            const A outer = (A)ld(e + q + (off ? 1 : -1));
-            const A xm = off ? partner : outer;
-            const A xp = off ? outer : partner;
-            const A zm = dir ? znext : zprev;
-            const A zp = dir ? zprev : znext;
-            s = ldg(rhs + q);
-            s = fma((A)ldg(wx + q), xm, s);
-            s = fma((A)ldg(wx + q + 1), xp, s);
-            s = fma((A)ldg(wy + q), (A)ld(e + q - sx), s);
-            s = fma((A)ldg(wy + q + sx), (A)ld(e + q + sx), s);
-            s = fma((A)ldg(wz + q), zm, s);
-            s = fma((A)ldg(wz + q + sy), zp, s);
-            pt[u] = partner;
-            zn[u] = znext;
+            o.w[0] = ldg(wx + q);
+            o.w[1] = ldg(wx + q + 1);
+            o.w[2] = ldg(wy + q);
+            o.w[3] = ldg(wy + q + sx);
+            o.w[4] = ldg(wz + q);
+            o.w[5] = ldg(wz + q + sy);
+            o.n[0] = ld(e + q - 1);
+            o.n[1] = ld(e + q + 1);
+            o.n[2] = ld(e + q - sx);
+            o.n[3] = ld(e + q + sx);
+            o.n[4] = ld(e + q - sy);
+            o.n[5] = ld(e + q + sy);
+            s = gs_value(o);
           }
-          s = s * (A)ldg(invD + q);
           st(e + q, s);
           if (push) push_ghosts(B, W.box, boxes, push, e, 2 * ppx[u] + off, pj[u], k, s);
-          Rc[u] = kept(s, e);
-          sr[tid + u * WAVE_BLOCK] = Rc[u];
         }
       }
-      __syncthreads();  // this step's reds stored (and in the ring) by every thread
-      if (m < nz && tid == 0) {
+      __syncthreads();  // this step's reds stored by every thread
+      if (tid == 0) {
         __threadfence();
-        wv_st_release(prog + ti, (unsigned)(m + 1));
+        wv_st_release(prog + ti, (unsigned)r1);
       }
-      if (m >= 1) {
-        const int kb = dir ? k + 1 : k - 1;  // plane of the previous step: its black cells
+      const int b1 = r1 == nz ? nz : r1 - 1;  // black planes [bdone, b1): reds on both sides done
+      if (b1 > bdone) {
         if (tid < 6) {
           int t = -1;
-          unsigned need = (unsigned)m;
+          unsigned need = (unsigned)b1;
+          const int kb_first = dir ? nz - 1 - bdone : bdone;
+          const int kb_last = dir ? nz - b1 : b1 - 1;
+          const int klo = min(kb_first, kb_last), khi = max(kb_first, kb_last);
           if (tid < 4) {
             t = tiles[ti].nb[tid];
-          } else if (tid == 4 && kb == 0) {
+          } else if (tid == 4 && klo == 0) {
             t = W.zb[0];
             need = (unsigned)W.zneed[0];
-          } else if (tid == 5 && kb == nz - 1) {
+          } else if (tid == 5 && khi == nz - 1) {
             t = W.zb[1];
             need = (unsigned)W.zneed[1];
           }
           if (t >= 0 && t != ti) wave_wait(prog, t, need, &s_seen[tid], err);
         }
-        __syncthreads();  // the neighbours' reds of plane kb are visible
-        const A* sr = s_red[(m - 1) % 3];
+        __syncthreads();  // the neighbours' reds of those planes are visible
+        // black pass: every neighbour read is a red cell already updated -- this block's
+        // (ordinary loads after the barrier) or another block's (from L2)
+        for (int mq = bdone; mq < b1; ++mq) {
+          const int kb = dir ? nz - 1 - mq : mq;
 #pragma unroll
-        for (int u = 0; u < PPT; ++u) {
-          if (!ok[u]) continue;
-          const int offr = (par + pj[u] + kb) & 1;  // red cell of the pair on plane kb
-          const int ob = 1 - offr;                  // its black cell
-          const int p = tid + u * WAVE_BLOCK;
-          const int64_t qp = q0[u] + (int64_t)kb * sy;
-          const int64_t q = qp + ob;
-          const A partner = Rb[u];
-          A outer;
-          if (ob == 0)
-            outer = ppx[u] > 0 ? sr[p - 1] : (A)ldl2(e + q - 1);
-          else
-            outer = ppx[u] < npx - 1 ? sr[p + 1] : (A)ldl2(e + q + 1);
-          const A ym = pr[u] > 0 ? sr[p - npx] : (A)ldl2(e + q - sx);
-          const A yp = pr[u] < rows - 1 ? sr[p + npx] : (A)ldl2(e + q + sx);
-          const A zprev = m >= 2 ? Ra[u] : (A)ldl2(e + q - zs);
-          const A znext = m < nz ? Rc[u] : (A)ldl2(e + q + zs);
-          const A xm = ob ? partner : outer;
-          const A xp = ob ? outer : partner;
-          const A zm = dir ? znext : zprev;
-          const A zp = dir ? zprev : znext;
-          A s = ldg(rhs + q);
-          s = fma((A)ldg(wx + q), xm, s);
-          s = fma((A)ldg(wx + q + 1), xp, s);
-          s = fma((A)ldg(wy + q), ym, s);
-          s = fma((A)ldg(wy + q + sx), yp, s);
-          s = fma((A)ldg(wz + q), zm, s);
-          s = fma((A)ldg(wz + q + sy), zp, s);
-          s = s * (A)ldg(invD + q);
-          st(e + q, s);
-          const int ib = 2 * ppx[u] + ob;
-          if (push) push_ghosts(B, W.box, boxes, push, e, ib, pj[u], kb, s);
-          if (MODE == 2) {
-            const double eb = (double)kept(s, e);
-            const double er = (double)partner;
-            double2 v = *reinterpret_cast<const double2*>(phi + qp);
-            v.x += ob == 0 ? eb : er;
-            v.y += ob == 0 ? er : eb;
-            *reinterpret_cast<double2*>(phi + qp) = v;
-            if (push_phi) {
-              push_ghosts(B, W.box, boxes, push_phi, phi, 2 * ppx[u], pj[u], kb, v.x);
-              push_ghosts(B, W.box, boxes, push_phi, phi, 2 * ppx[u] + 1, pj[u], kb, v.y);
+          for (int u = 0; u < PPT; ++u) {
+            if (!ok[u]) continue;
+            const int ob = 1 - ((par + pj[u] + kb) & 1);  // the black cell of the pair is i0 + ob
+            const int64_t qp = q0[u] + (int64_t)kb * sy;
+            const int64_t q = qp + ob;
+            Upd<A> o;
+            o.r = ldg(rhs + q);
+            o.d = ldg(invD + q);
+            o.w[0] = ldg(wx + q);
+            o.w[1] = ldg(wx + q + 1);
+            o.w[2] = ldg(wy + q);
+            o.w[3] = ldg(wy + q + sx);
+            o.w[4] = ldg(wz + q);
+            o.w[5] = ldg(wz + q + sy);
+            const A partner = (A)ld(e + qp + (1 - ob));
+            const A outer = ob ? (ppx[u] < npx - 1 ? (A)ld(e + q + 1) : (A)ldl2(e + q + 1))
+                               : (ppx[u] > 0 ? (A)ld(e + q - 1) : (A)ldl2(e + q - 1));
+            o.n[0] = ob ? partner : outer;
+            o.n[1] = ob ? outer : partner;
+            o.n[2] = pr[u] > 0 ? (A)ld(e + q - sx) : (A)ldl2(e + q - sx);
+            o.n[3] = pr[u] < rows - 1 ? (A)ld(e + q + sx) : (A)ldl2(e + q + sx);
+            o.n[4] = kb > 0 ? (A)ld(e + q - sy) : (A)ldl2(e + q - sy);
+            o.n[5] = kb < nz - 1 ? (A)ld(e + q + sy) : (A)ldl2(e + q + sy);
+            const A s = gs_value(o);
+            st(e + q, s);
+            if (push) push_ghosts(B, W.box, boxes, push, e, 2 * ppx[u] + ob, pj[u], kb, s);
+            if (MODE == 2) {
+              const double eb = (double)kept(s, e);
+              const double er = (double)partner;
+              double2 v = *reinterpret_cast<const double2*>(phi + qp);
+              v.x += ob == 0 ? eb : er;
+              v.y += ob == 0 ? er : eb;
+              *reinterpret_cast<double2*>(phi + qp) = v;
+              if (push_phi) {
+                push_ghosts(B, W.box, boxes, push_phi, phi, 2 * ppx[u], pj[u], kb, v.x);
+                push_ghosts(B, W.box, boxes, push_phi, phi, 2 * ppx[u] + 1, pj[u], kb, v.y);
+              }
             }
           }
         }
-      }
-#pragma unroll
-      for (int u = 0; u < PPT; ++u) {
-        Ra[u] = Rb[u];
-        Rb[u] = Rc[u];
+        bdone = b1;
       }
     }
   }
@@ -295,6 +336,14 @@ void launch_wave_kernel(void (*k)(P...), unsigned grid, cudaStream_t s, Args&&..
   cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
+// Planes per step: the data a step of every tile touches (its planes of the seven arrays,
+// read by the red pass and again by the black pass) should stay within a share of L2.
+constexpr double WAVE_L2_BYTES = 48.0 * (1 << 20);
+int wave_slab(const LevelDev& L, int bytes_per_cell) {
+  const double layer = (double)std::max<int64_t>(1, L.wave_layer_cells) * bytes_per_cell;
+  return std::max(2, std::min(16, (int)(WAVE_L2_BYTES / layer)));
+}
+
 // blocks of kernel k that fit on the device at once (0 if the query fails)
 template <class K>
 int resident_blocks(K k) {
@@ -305,16 +354,20 @@ int resident_blocks(K k) {
   return nsm * per;
 }
 
+// blocks per SM the register budget is held to (capacity = SMs x MINB tiles resident at once)
+constexpr int WAVE_MINB = 8;
+
 template <class T, int PPT, int MODE>
 bool wave_go(const LevelDev& L, void* e, const void* rhs, const Coefs& c, double* phi, const PushFace* pp, int* err,
              cudaStream_t s) {
   using C = typename CoefOf<T>::type;
   static int cap = -1;
-  if (cap < 0) cap = resident_blocks(k_wave<T, PPT, MODE>);
+  if (cap < 0) cap = resident_blocks(k_wave<T, PPT, MODE, WAVE_MINB>);
   if (L.wave_max_solve_tiles > cap) return false;  // a problem's tiles must be resident together
-  launch_wave_kernel(k_wave<T, PPT, MODE>, (unsigned)L.n_wave_tiles, s, L.boxes, L.wave_tiles, L.n_wave_tiles,
-                     L.wave_cnt, (T*)e, (const T*)rhs, (const C*)c.wx, (const C*)c.wy, (const C*)c.wz,
-                     (const C*)c.invD, L.active, L.flow_skip, L.push_ok ? L.push_faces : nullptr, phi, pp, err);
+  launch_wave_kernel(k_wave<T, PPT, MODE, WAVE_MINB>, (unsigned)L.n_wave_tiles, s, L.boxes, L.wave_tiles,
+                     L.n_wave_tiles, L.wave_cnt, (T*)e, (const T*)rhs, (const C*)c.wx, (const C*)c.wy, (const C*)c.wz,
+                     (const C*)c.invD, L.active, L.flow_skip, L.push_ok ? L.push_faces : nullptr, phi, pp, err,
+                     wave_slab(L, (int)(2 * sizeof(T) + 5 * sizeof(C))));
   return true;
 }
 

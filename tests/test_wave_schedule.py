@@ -1,9 +1,10 @@
 """The wavefront red-black sweep's tables and waiting rule, checked on the host (no GPU).
 
 The wavefront kernel (one launch per Gauss-Seidel sweep of Sec. "Linear Solvers") lets each
-thread block march through the planes of one tile -- a band of rows of one box -- doing the
-red cells of a plane, reporting them, and then, once the tiles beside it have reported that
-plane too, the black cells of the plane before.  These tests replay that schedule on the
+thread block march through the planes of one tile -- a band of rows of one box -- a slab of
+planes at a time: the red cells of the slab, a report, and then, once the tiles beside it
+have reported those planes too, the black cells of every plane whose reds on both sides are
+done.  These tests replay that schedule on the
 host from the library's own tile tables (gmg_wave_tiles), cell by cell, in many random and
 adversarial interleavings of the tiles' steps, and check what the two-pass sweep requires:
 every red cell reads only black cells that are not yet updated, every black cell reads only
@@ -46,15 +47,21 @@ def _nbr_versions(P, gi, gj, gk, d, sgn):
 
 
 class Replay:
-    def __init__(self, C, m, probs_of_solve):
+    """tile t's program: steps of `slab` planes (marching order): red cells of planes
+    [r0, r1), report r1, wait, black cells of planes [bdone, b1) with b1 = r1 - 1 (nz in the
+    last step) -- the kernel's schedule, replayed cell by cell"""
+
+    def __init__(self, C, m, probs_of_solve, slab):
         self.ppt, self.T = C.wave_tiles(m)
         boxes, _ = C.level_boxes(m)
         self.boxes = boxes
         self.probs = probs_of_solve
+        self.slab = slab
         self.nt = len(self.T)
-        self.iter = np.zeros(self.nt, dtype=np.int64)  # next iteration
-        self.half = np.zeros(self.nt, dtype=np.int64)  # 0: red part next, 1: black part next
-        self.count = np.zeros(self.nt, dtype=np.int64)
+        self.r0 = np.zeros(self.nt, dtype=np.int64)     # next red plane (marching order)
+        self.bdone = np.zeros(self.nt, dtype=np.int64)  # black planes done
+        self.half = np.zeros(self.nt, dtype=np.int64)   # 0: red part of a step next, 1: black part
+        self.count = np.zeros(self.nt, dtype=np.int64)  # red planes reported
         self.reds = 0
         self.blacks = 0
 
@@ -62,11 +69,11 @@ class Replay:
         lo, hi = self.boxes[self.T[t][0]]
         return hi[2] - lo[2] + 1
 
-    def plane(self, t, m):
-        return self.nz(t) - 1 - m if self.T[t][3] else m
+    def plane(self, t, q):
+        return self.nz(t) - 1 - q if self.T[t][3] else q
 
     def done(self, t):
-        return self.iter[t] > self.nz(t)
+        return self.bdone[t] >= self.nz(t)
 
     def cells(self, t, k, colour):
         b, y0, y1 = self.T[t][0], self.T[t][1], self.T[t][2]
@@ -76,30 +83,37 @@ class Replay:
         sel = ((ii + jj + gk) & 1) == colour
         return ii[sel], jj[sel], gk[sel]
 
+    def b1(self, t):
+        r1 = self.count[t]
+        return self.nz(t) if r1 == self.nz(t) else r1 - 1
+
     def waiting(self, t):
         """True if tile t's next action is a black part whose neighbours have not reported"""
         if self.half[t] == 0:
             return False
-        m = self.iter[t]
+        b1, b0 = self.b1(t), self.bdone[t]
+        if b1 <= b0:
+            return False
         row = self.T[t]
         for u in range(4, 8):
             nb = row[u]
-            if nb >= 0 and nb != t and self.count[nb] < m:
+            if nb >= 0 and nb != t and self.count[nb] < b1:
                 return True
-        kb = self.plane(t, m - 1)
-        if kb == 0 and row[8] >= 0 and self.count[row[8]] < row[10]:
+        ks = [self.plane(t, q) for q in (b0, b1 - 1)]
+        if min(ks) == 0 and row[8] >= 0 and self.count[row[8]] < row[10]:
             return True
-        if kb == self.nz(t) - 1 and row[9] >= 0 and self.count[row[9]] < row[11]:
+        if max(ks) == self.nz(t) - 1 and row[9] >= 0 and self.count[row[9]] < row[11]:
             return True
         return False
 
     def act(self, t):
         P = self.probs[self.T[t][12]]
-        m = self.iter[t]
         nz = self.nz(t)
         if self.half[t] == 0:
-            if m < nz:
-                gi, gj, gk = self.cells(t, self.plane(t, m), 0)
+            r0 = self.r0[t]
+            r1 = min(nz, r0 + self.slab)
+            for q in range(r0, r1):
+                gi, gj, gk = self.cells(t, self.plane(t, q), 0)
                 for d in range(3):
                     for sgn in (-1, 1):
                         v = _nbr_versions(P, gi, gj, gk, d, sgn)
@@ -108,32 +122,30 @@ class Replay:
                 assert not P.V[idx].any(), "a red cell updated twice"
                 P.V[idx] = 1
                 self.reds += gi.size
-                self.count[t] = m + 1
+            self.r0[t] = r1
+            self.count[t] = r1
             self.half[t] = 1
-            if m == 0:  # (no black part in the first iteration)
-                self.half[t] = 0
-                self.iter[t] = 1
             return
-        kb = self.plane(t, m - 1)
-        gi, gj, gk = self.cells(t, kb, 1)
-        for d in range(3):
-            for sgn in (-1, 1):
-                v = _nbr_versions(P, gi, gj, gk, d, sgn)
-                h = [gi - P.lo[0], gj - P.lo[1], gk - P.lo[2]][d] + sgn
-                wall = ((h < 0) | (h >= P.n[d])) & (not P.per[d])
-                assert np.all(v[~wall] == 1), f"black cell of tile {t} read a red cell not yet updated"
-                assert np.all(v[wall] == 0), "a black cell's wall image was updated before it"
-        idx = (gk - P.lo[2], gj - P.lo[1], gi - P.lo[0])
-        assert not P.V[idx].any(), "a black cell updated twice"
-        P.V[idx] = 1
-        self.blacks += gi.size
+        for q in range(self.bdone[t], self.b1(t)):
+            gi, gj, gk = self.cells(t, self.plane(t, q), 1)
+            for d in range(3):
+                for sgn in (-1, 1):
+                    v = _nbr_versions(P, gi, gj, gk, d, sgn)
+                    h = [gi - P.lo[0], gj - P.lo[1], gk - P.lo[2]][d] + sgn
+                    wall = ((h < 0) | (h >= P.n[d])) & (not P.per[d])
+                    assert np.all(v[~wall] == 1), f"black cell of tile {t} read a red cell not yet updated"
+                    assert np.all(v[wall] == 0), "a black cell's wall image was updated before it"
+            idx = (gk - P.lo[2], gj - P.lo[1], gi - P.lo[0])
+            assert not P.V[idx].any(), "a black cell updated twice"
+            P.V[idx] = 1
+            self.blacks += gi.size
+        self.bdone[t] = max(self.bdone[t], self.b1(t))
         self.half[t] = 0
-        self.iter[t] += 1
 
 
-def _run(C, m, probs, order, resident=None, rng=None):
+def _run(C, m, probs, order, resident=None, rng=None, slab=1):
     """replay one sweep of level m; order: 'random', 'low', 'high' (which runnable tile acts next)"""
-    R = Replay(C, m, probs)
+    R = Replay(C, m, probs, slab)
     slots = R.nt if resident is None else resident
     started = min(slots, R.nt)  # tiles get slots in ticket (table) order
     live = list(range(started))
@@ -194,9 +206,9 @@ def test_wave_schedule_is_the_two_pass_sweep(name):
             lo, hi = boxes[row[0]]
             assert (hi[0] - lo[0] + 1) // 2 * (row[2] - row[1]) <= 128 * ppt
         rng = np.random.default_rng(7 + m)
-        for order in ("low", "high", "random", "random", "random"):
+        for order, slab in (("low", 1), ("high", 2), ("random", 1), ("random", 3), ("random", 4), ("low", 5)):
             probs = _probs_single(C, m, bc_lo, bc_hi)
-            R = _run(C, m, probs, order, rng=rng)
+            R = _run(C, m, probs, order, rng=rng, slab=slab)
             ncell = sum(int(np.prod(P.n)) for P in probs)
             assert R.reds + R.blacks == ncell
             assert all(P.V.all() for P in probs)
@@ -228,7 +240,7 @@ def test_wave_batched_problems_with_few_resident_blocks():
             continue
         boxes, _ = C.level_boxes(m)
         per = np.bincount(T[:, 12], minlength=len(sizes))
-        for order in ("low", "random", "random"):
+        for order, slab in (("low", 1), ("random", 2), ("random", 3)):
             probs = []
             for s in range(len(sizes)):
                 mine = [boxes[row[0]] for row in T if row[12] == s]
@@ -238,7 +250,7 @@ def test_wave_batched_problems_with_few_resident_blocks():
                 lo = np.min([b[0] for b in mine], axis=0)
                 hi = np.max([b[1] for b in mine], axis=0)
                 probs.append(Prob(lo, hi, [D_] * 3, [D_] * 3))
-            R = _run(C, m, probs, order, resident=int(per.max()), rng=rng)
+            R = _run(C, m, probs, order, resident=int(per.max()), rng=rng, slab=slab)
             for s, P in enumerate(probs):
                 if per[s]:
                     assert P.V.all()
