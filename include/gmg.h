@@ -143,9 +143,11 @@ typedef struct {
                            than 2^22 cells (where the exchange is launch-latency bound) */
   int vector_smooth;    /* 1: float and bfloat16 colour sweeps on levels whose box widths
                            are multiples of 4 run one thread per 4 consecutive cells with
-                           128-bit (float) / 64-bit (bfloat16) loads; bitwise the same results
-                           as one thread per cell pair (0).  2 (default): per level, the
-                           gmg_autotune choice; before tuning, bfloat16 only */
+                           128-bit (float) / 64-bit (bfloat16) loads, and double sweeps read
+                           each cell pair of every array with one 128-bit load; bitwise the
+                           same results as one thread per cell pair with scalar loads (0).
+                           2 (default): per level, the gmg_autotune choice; before tuning,
+                           bfloat16 only */
   int pdl;              /* 1: the V-cycle kernels are launched for programmatic dependent
                            launch -- each may be scheduled while its predecessor finishes
                            and waits for it on the device before touching memory; 0: plain

@@ -465,7 +465,10 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     }
   }
   unsigned long long* nb = (unsigned long long*)cv.take(8 * (2 * ns + 8));
-  double* partials = (double*)cv.take(8 * (size_t)maxchunks);
+  // (multi-level dot products keep the partials of every composite level twice)
+  int mlchunks = c->L.empty() ? 0 : (int)c->L[0].cell_chunks.size();
+  for (const AmrLevel& V : c->amrl) mlchunks += (int)V.M.cell_chunks.size();
+  double* partials = (double*)cv.take(8 * (size_t)std::max(maxchunks, 2 * mlchunks));
   double* scal = (double*)cv.take(8 * (2 * ns + 8));
   int* iters = (int*)cv.take(4 * (ns + 1));  // bottom iterations per problem, then the device error flag
   if (fill) {
@@ -1702,11 +1705,14 @@ void comp_apply_transpose_n(gmg_ctx* c, double* const* y, double* const* out, cu
   for (int l = 0; l + 1 < L; ++l) launch_zero_covered(c->amrl[l].A, out[l], s);
 }
 
-// sum over the levels of <x_l, y_l> (covered entries zero in one of the two)
+// sum over the levels of <x_l, y_l> (covered entries zero in one of the two): one launch of
+// partial sums over every level, one of per-level sums, one read-back
 gmg_status comp_dot_n(gmg_ctx* c, double* const* x, double* const* y, double* out) {
   cudaStream_t s = c->stream;
   const int L = namr(c);
-  for (int l = 0; l < L; ++l) launch_dot(adev(c, l), x[l], y[l], c->partials, c->scal + l, s);  // in stream order
+  const LevelDev* Ls[ML_MAX_SEG];
+  for (int l = 0; l < L; ++l) Ls[l] = &adev(c, l);
+  launch_dot_ml(L, Ls, (const double* const*)x, (const double* const*)y, c->partials, c->scal, s);
   CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8 * (size_t)L, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
   CK(c, cudaGetLastError());
@@ -1716,23 +1722,38 @@ gmg_status comp_dot_n(gmg_ctx* c, double* const* x, double* const* y, double* ou
   return GMG_OK;
 }
 
-// two such sums with one read-back: out1 = sum <x1_l, y1_l>, out2 = sum <x2_l, y2_l>
-gmg_status comp_dot2_n(gmg_ctx* c, double* const* x1, double* const* y1, double* const* x2, double* const* y2,
-                       double* out1, double* out2) {
+// sums over the levels of <x1_l, y1_l> (and, with x2, of <x2_l, y2_l>) and the max over the
+// levels of ||z_l||_inf, with one read-back
+gmg_status comp_dots_norm_n(gmg_ctx* c, double* const* x1, double* const* y1, double* const* x2,
+                            double* const* y2, double* const* z, double* d1, double* d2, double* zn) {
   cudaStream_t s = c->stream;
   const int L = namr(c);
-  for (int l = 0; l < L; ++l) launch_dot(adev(c, l), x1[l], y1[l], c->partials, c->scal + l, s);  // in stream order
-  for (int l = 0; l < L; ++l) launch_dot(adev(c, l), x2[l], y2[l], c->partials, c->scal + L + l, s);
-  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 16 * (size_t)L, cudaMemcpyDeviceToHost, s));
-  CK(c, cudaStreamSynchronize(s));
-  CK(c, cudaGetLastError());
+  const int nseg = x2 ? 2 * L : L;
+  const LevelDev* Ls[ML_MAX_SEG];
+  const double *xs[ML_MAX_SEG], *ys[ML_MAX_SEG];
+  for (int l = 0; l < L; ++l) {
+    Ls[l] = &adev(c, l);
+    xs[l] = x1[l];
+    ys[l] = y1[l];
+    if (x2) {
+      Ls[L + l] = &adev(c, l);
+      xs[L + l] = x2[l];
+      ys[L + l] = y2[l];
+    }
+  }
+  launch_dot_ml(nseg, Ls, xs, ys, c->partials, c->scal, s);
+  CK(c, cudaMemsetAsync(c->normbits, 0, 8 * (size_t)L, s));
+  launch_norm_max_ml(L, Ls, (const double* const*)z, c->normbits, s);
+  CK(c, cudaMemcpyAsync(c->h_scal, c->scal, 8 * (size_t)nseg, cudaMemcpyDeviceToHost, s));
+  gmg_status st = read_norms_n(c, L, zn);  // (synchronises the stream)
+  if (st) return st;
   double a = 0.0, b = 0.0;
   for (int l = 0; l < L; ++l) {
     a += c->h_scal[l];
-    b += c->h_scal[L + l];
+    if (x2) b += c->h_scal[L + l];
   }
-  *out1 = a;
-  *out2 = b;
+  *d1 = a;
+  if (d2) *d2 = b;
   return GMG_OK;
 }
 
@@ -1740,7 +1761,9 @@ gmg_status comp_dot2_n(gmg_ctx* c, double* const* x1, double* const* y1, double*
 gmg_status comp_norm_n(gmg_ctx* c, double* const* x, double* out) {
   const int L = namr(c);
   CK(c, cudaMemsetAsync(c->normbits, 0, 8 * (size_t)L, c->stream));
-  for (int l = 0; l < L; ++l) launch_norm_max(adev(c, l), x[l], c->normbits + l, c->stream);
+  const LevelDev* Ls[ML_MAX_SEG];
+  for (int l = 0; l < L; ++l) Ls[l] = &adev(c, l);
+  launch_norm_max_ml(L, Ls, (const double* const*)x, c->normbits, c->stream);
   return read_norms_n(c, L, out);
 }
 
@@ -1783,9 +1806,14 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
     e[l] = (double*)(l == 0 ? c->buf[0].e[DT_F64] : c->amrl[l - 1].B.e[DT_F64]);
     ne[l] = anelem(c, l);
   }
-  // out = a x + b y on every level
+  // out = a x + b y on every level (one launch)
   auto axpby = [&](double a, double* const* x, double b, double* const* y, double* const* out) {
-    for (int l = 0; l < L; ++l) launch_axpby(ne[l], a, x[l], b, y[l], out[l], s);
+    double av[ML_MAX_SEG], bv[ML_MAX_SEG];
+    for (int l = 0; l < L; ++l) {
+      av[l] = a;
+      bv[l] = b;
+    }
+    launch_axpby_ml(L, ne, av, (const double* const*)x, bv, (const double* const*)y, out, s);
   };
   for (int l = 0; l < L; ++l) {
     CK(c, cudaMemcpyAsync(k[8][l], g_user[l], 8 * (size_t)ne[l], cudaMemcpyDeviceToDevice, s));
@@ -1826,11 +1854,17 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
   // mid = V M V^-1 in, then out = A^T mid (mid copied first: the transpose overwrites its
   // input's ghosts).  With use_graph each of the two (in, mid, out) triples of the iteration
   // is captured once and replayed.
+  // (the scalings are one launch over every level each; mid and its copy come from one pass)
+  double sc_in[ML_MAX_SEG], sc_out[ML_MAX_SEG], zeros[ML_MAX_SEG];
+  for (int l = 0; l < L; ++l) {
+    sc_in[l] = z.v[0] / z.v[l];
+    sc_out[l] = z.v[l] / z.v[0];
+    zeros[l] = 0.0;
+  }
   auto prec_apply = [&](double* const* in, double* const* mid, double* const* out, cudaStream_t st_) {
-    for (int l = 0; l < L; ++l) launch_axpby(ne[l], z.v[0] / z.v[l], in[l], 0.0, in[l], tmp[l], st_);
+    launch_axpby_ml(L, ne, sc_in, (const double* const*)in, zeros, (const double* const*)in, tmp, st_);
     comp_correction_n(c, p, tmp, st_);
-    for (int l = 0; l < L; ++l) launch_axpby(ne[l], z.v[l] / z.v[0], e[l], 0.0, e[l], mid[l], st_);
-    for (int l = 0; l < L; ++l) launch_axpby(ne[l], 1.0, mid[l], 0.0, mid[l], tmp[l], st_);
+    launch_scale2_ml(L, ne, sc_out, (const double* const*)e, mid, tmp, st_);
     comp_apply_transpose_n(c, tmp, out, st_);
   };
   auto run_pa = [&](double* const* in, double* const* mid, double* const* out) -> gmg_status {
@@ -1862,36 +1896,38 @@ gmg_status solve_adjoint_amr_n(gmg_ctx* c, double* const* lam, const double* con
     count_launches((int)itg->second.launches);
     return GMG_OK;
   };
+  // (read-backs per iteration: <rhat, v>; ||s|| with <t, t> and <t, s> -- t computed before
+  // ||s|| is known, so the last iteration may apply the preconditioner once for nothing;
+  // ||r|| with the next iteration's <rhat, r>)
+  double rho_next = 0.0;
   while (!(rn <= target) && it < p.max_iter) {
     ++it;
-    double rho;
-    if ((st = comp_dot_n(c, k[1], k[0], &rho))) return st;
+    double rho = rho_next;
+    if (it == 1 && (st = comp_dot_n(c, k[1], k[0], &rho))) return st;
     if (std::fabs(rho) < 1e-300) break;
     const double beta = (rho / rho_old) * (alpha / omega);
-    for (int l = 0; l < L; ++l)  // p = r + beta (p - omega v), one pass
-      launch_bicg_direction(ne[l], k[0][l], k[2][l], k[3][l], beta, omega, s);
+    // p = r + beta (p - omega v), one pass over every level
+    launch_bicg_direction_ml(L, ne, (const double* const*)k[0], k[2], (const double* const*)k[3], beta, omega, s);
     if ((st = run_pa(k[2], k[6], k[3]))) return st;
     double rv;
     if ((st = comp_dot_n(c, k[1], k[3], &rv))) return st;
     if (std::fabs(rv) < 1e-300) break;
     alpha = rho / rv;
     axpby(1.0, k[0], -alpha, k[3], k[4]);
-    double sn;
-    if ((st = comp_norm_n(c, k[4], &sn))) return st;
+    if ((st = run_pa(k[4], k[7], k[5]))) return st;
+    double sn, tt, ts;
+    if ((st = comp_dots_norm_n(c, k[5], k[5], k[5], k[4], k[4], &tt, &ts, &sn))) return st;
     if (sn <= target) {
       axpby(1.0, lam, alpha, k[6], lam);
       rn = sn;
       hist.push_back(rn);
       break;
     }
-    if ((st = run_pa(k[4], k[7], k[5]))) return st;
-    double tt, ts;
-    if ((st = comp_dot2_n(c, k[5], k[5], k[5], k[4], &tt, &ts))) return st;
     if (tt == 0.0) break;
     omega = ts / tt;
-    for (int l = 0; l < L; ++l) launch_add2(ne[l], lam[l], alpha, k[6][l], omega, k[7][l], s);  // one pass
+    launch_add2_ml(L, ne, lam, alpha, (const double* const*)k[6], omega, (const double* const*)k[7], s);  // one pass
     axpby(1.0, k[4], -omega, k[5], k[0]);
-    if ((st = comp_norm_n(c, k[0], &rn))) return st;
+    if ((st = comp_dots_norm_n(c, k[1], k[0], nullptr, nullptr, k[0], &rho_next, nullptr, &rn))) return st;
     hist.push_back(rn);
     if (!std::isfinite(rn)) {
       result = GMG_ERR_DIVERGED;
@@ -2993,7 +3029,8 @@ gmg_status gmg_autotune(gmg_ctx* c, int precision, const void* rhs, const gmg_pa
     if (D.n_pair_chunks == 0) continue;
     const LevelBufs& B = c->buf[m];
     const Coefs k = coefs_of(c, m, dt);
-    const bool can_vec = dt != DT_F64 && D.quad_chunks && D.n_quad_chunks > 0;
+    // (4-cell threads for float / bfloat16; 128-bit pair loads for double)
+    const bool can_vec = dt == DT_F64 || (D.quad_chunks && D.n_quad_chunks > 0);
     double best = 1e30;
     int best_v = 0;
     double best_push = 1e30, best_pull = 1e30;
@@ -3008,7 +3045,8 @@ gmg_status gmg_autotune(gmg_ctx* c, int precision, const void* rhs, const gmg_pa
       });
       if (push) best_push = std::min(best_push, ms);
       else best_pull = std::min(best_pull, ms);
-      if (ms < best) {
+      // (the vector-load variants must win by 2%: on launch-bound levels the order is noise)
+      if (vec ? ms < 0.98 * best : ms < best) {
         best = ms;
         best_v = v;
       }

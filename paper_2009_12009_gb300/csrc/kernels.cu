@@ -251,6 +251,52 @@ __global__ void __launch_bounds__(BLOCK, 4) k_smooth4(const DevBox* __restrict__
   }
 }
 
+// One colour of Gauss-Seidel on double fields with 128-bit loads: each thread reads the
+// aligned cell pair (i0, i0 + 1) of phi in its own row and in the rows and planes around it,
+// and the pair's rhs, 1/D and face weights, as double2 loads, and updates the pair's cell of
+// the colour with k_smooth's operands in k_smooth's order (bitwise the same values).
+__global__ void __launch_bounds__(BLOCK)
+    k_smooth_d2(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks, double* phi,
+                const double* __restrict__ rhs, const double* __restrict__ wx, const double* __restrict__ wy,
+                const double* __restrict__ wz, const double* __restrict__ invD, int colour,
+                const int* __restrict__ active, const PushFace* __restrict__ push, int rev) {
+  pdl_enter();
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  if (active && !active[B.solve]) return;
+  const int t = ch.start + threadIdx.x;
+  if (t >= ((B.nx + 1) >> 1) * B.ny * B.nz) return;
+  int i0, j, k;
+  pair_decode(B, t, i0, j, k);
+  const int off = (B.lo[0] + B.lo[1] + B.lo[2] + i0 + j + k + colour) & 1;
+  if (i0 + 1 >= B.nx) {  // (a last single cell of an odd row: the scalar kernel's path)
+    if (off) return;
+  }
+  const int64_t q0 = elem_index(B, i0, j, k);  // even: 16-byte aligned
+  const int64_t q = q0 + off;
+  const int64_t sx = B.sx, sy = B.sy;
+  auto ld2 = [](const double* p) { return *reinterpret_cast<const double2*>(p); };
+  auto ldg2 = [](const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); };
+  auto pick = [off](double2 v) { return off ? v.y : v.x; };
+  const double2 own = ld2(phi + q0);
+  const double outer = off ? phi[q0 + 2] : phi[q0 - 1];
+  const double2 ym = ld2(phi + q0 - sx), yp = ld2(phi + q0 + sx);
+  const double2 zm = ld2(phi + q0 - sy), zp = ld2(phi + q0 + sy);
+  const double2 r2 = ldg2(rhs + q0), d2 = ldg2(invD + q0), wx2 = ldg2(wx + q0);
+  const double2 wyl = ldg2(wy + q0), wyh = ldg2(wy + q0 + sx), wzl = ldg2(wz + q0), wzh = ldg2(wz + q0 + sy);
+  const double wxr = off ? __ldg(wx + q0 + 2) : wx2.y;
+  double s = pick(r2);
+  s = fma(off ? wx2.y : wx2.x, off ? own.x : outer, s);
+  s = fma(wxr, off ? outer : own.y, s);
+  s = fma(pick(wyl), pick(ym), s);
+  s = fma(pick(wyh), pick(yp), s);
+  s = fma(pick(wzl), pick(zm), s);
+  s = fma(pick(wzh), pick(zp), s);
+  s = s * pick(d2);
+  phi[q] = s;
+  if (push) push_ghosts(B, ch.item, boxes, push, phi, i0 + off, j, k, s);
+}
+
 // ------------------------------------------------------------------- residual
 
 // whether global cell g of a level lies next to one of its problem's walls
@@ -906,6 +952,12 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
   if (!L.n_pair_chunks) return;
   ++g_launches;
   const PushFace* pf = push ? L.push_faces : nullptr;
+  if (vec && dt == DT_F64) {
+    launch_pdl(k_smooth_d2, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks, (double*)phi,
+               (const double*)rhs, (const double*)c.wx, (const double*)c.wy, (const double*)c.wz,
+               (const double*)c.invD, colour, L.active, pf, L.rev);
+    return;
+  }
   if (vec && dt != DT_F64 && L.quad_chunks && L.n_quad_chunks > 0) {
     const float *wx = (const float*)c.wx, *wy = (const float*)c.wy, *wz = (const float*)c.wz;
     const float* invD = (const float*)c.invD;

@@ -263,4 +263,29 @@ void launch_bicg_direction(int64_t n, const double* r, double* p, const double* 
                            cudaStream_t s);
 void launch_add2(int64_t n, double* x, double a, const double* y, double b, const double* z, cudaStream_t s);
 
+// ---- the same vector operations over every level of a composite vector in one launch
+// (krylov.cu): nl levels of n[l] elements (ghosts included); per level the values of the
+// one-level kernels above, bitwise.  Segments (level and vectors) of the reductions: up to
+// ML_MAX_SEG.
+constexpr int ML_MAX_SEG = 8;
+// out_l = a[l] x_l + b[l] y_l
+void launch_axpby_ml(int nl, const int64_t* n, const double* a, const double* const* x, const double* b,
+                     const double* const* y, double* const* out, cudaStream_t s);
+// o1_l = a[l] x_l, o2_l = o1_l (the values of launch_axpby(a, x, 0, x, o1) then
+// launch_axpby(1, o1, 0, o1, o2))
+void launch_scale2_ml(int nl, const int64_t* n, const double* a, const double* const* x, double* const* o1,
+                      double* const* o2, cudaStream_t s);
+void launch_bicg_direction_ml(int nl, const int64_t* n, const double* const* r, double* const* p,
+                              const double* const* v, double beta, double omega, cudaStream_t s);
+void launch_add2_ml(int nl, const int64_t* n, double* const* x, double a, const double* const* y, double b,
+                    const double* const* z, cudaStream_t s);
+// out[s] = sum over the valid cells of segment s (level L[s]) of x_s y_s: deterministic
+// partial sums over groups of cell chunks, then one block per segment adds them in order
+// (partials: one per cell chunk of all segments is enough)
+void launch_dot_ml(int ns, const LevelDev* const* L, const double* const* x, const double* const* y,
+                   double* partials, double* out, cudaStream_t s);
+// maxbits[s] = max(maxbits[s], |x_s|_inf as IEEE bits) over the valid cells of segment s
+void launch_norm_max_ml(int ns, const LevelDev* const* L, const double* const* x, unsigned long long* maxbits,
+                        cudaStream_t s);
+
 }  // namespace gmg

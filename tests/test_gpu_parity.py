@@ -431,8 +431,9 @@ def test_autotune_keeps_results():
 
 @pytest.mark.parametrize("case", ["abec64_boxes16", "helmholtz", "periodic"])
 def test_vector_smooth_is_bitwise_pair_smooth(case):
-    """One thread per 4 cells with vector loads gives bit for bit the V-cycle and the solve
-    of one thread per cell pair (float and bfloat16; FP64 always uses pairs)."""
+    """One thread per 4 cells with vector loads (float and bfloat16), and one thread per pair
+    with 128-bit pair loads (FP64), give bit for bit the V-cycle and the solve of one thread
+    per cell pair with scalar loads."""
     from paper_2009_12009_gb300 import inputs as I
 
     cfg = I.abec(64, 16, 4646, name=case) if case == "abec64_boxes16" else cases.make(case)
@@ -446,14 +447,14 @@ def test_vector_smooth_is_bitwise_pair_smooth(case):
             C.set_alpha(torch.from_numpy(cfg["alpha"]))
         C.set_beta(torch.from_numpy(cfg["beta"]) if cfg["beta"] is not None else None)
     r = cfg["rhs"] - (cfg["rhs"].mean() if cfg["bc_lo"][0] == gmg.PERIODIC and cfg["a"] == 0 else 0.0)
-    for dt in (gmg.DT_F32, gmg.DT_BF16):
+    for dt in (gmg.DT_F64, gmg.DT_F32, gmg.DT_BF16):
         rb = C.pack(torch.from_numpy(r), 0, dt)
         for push in (0, 1):
             e1 = C.unpack(C.vcycle(rb, dt, vector_smooth=1, ghost_push=push), 0, dt)
             e0 = C.unpack(C.vcycle(rb, dt, vector_smooth=0, ghost_push=push), 0, dt)
             assert torch.equal(e1, e0), (dt, push)
     rhs = C.pack(torch.from_numpy(r))
-    for prec in (gmg.MIXED_FP32, gmg.MIXED_BF16):
+    for prec in (gmg.FP64, gmg.MIXED_FP32, gmg.MIXED_BF16):
         p1, _ = C.solve(rhs, tol_rel=0.0, max_iter=3, precision=prec, vector_smooth=1, project_mean=1)
         a1 = C.unpack(p1).clone()
         p0, _ = C.solve(rhs, tol_rel=0.0, max_iter=3, precision=prec, vector_smooth=0, project_mean=1)
