@@ -262,6 +262,18 @@ gmg_status check_level(gmg_ctx* c, int m, int dt) {
 }
 
 // Carve the workspace (base = nullptr: size only).  Returns bytes.
+
+// Whether the finest level of a context keeps its right-hand side and 1/D colour-split within
+// rows (split_index): every box smooths there (none has its bottom on it), every width is
+// even, and no AMR level sits above it (the composite solve writes its own right-hand sides).
+// A colour pass then reads half of each of those two arrays' sectors instead of all of them.
+bool split_level_ok(const gmg_ctx* c, const LevelMeta& M) {
+  if (c->amr || c->L.size() < 2 || !M.bot_descs.empty() || M.pair_chunks.empty()) return false;
+  for (const Box& b : M.boxes)
+    if (b.n(0) % 2 != 0) return false;
+  return true;
+}
+
 size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
   Carver cv(base);
   const int n = nlev(c);
@@ -329,6 +341,7 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.n_ec_ghosts = (int)M.ec_ghosts.size();
     D.push_faces = (const PushFace*)cv.take(sizeof(PushFace) * M.push_faces.size());
     D.push_ok = M.push_ok ? 1 : 0;
+    D.split = (m == 0 && split_level_ok(c, M)) ? (SPLIT_RHS | SPLIT_INVD) : 0;
     D.wave_tiles = (const WaveTile*)cv.take(sizeof(WaveTile) * M.wave_tiles.size());
     D.n_wave_tiles = (int)M.wave_tiles.size();
     D.wave_ppt = M.wave_ppt;
@@ -787,7 +800,7 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
   const bool prof = c->profiling && m == 0;
   cudaEvent_t* ev = prof ? smooth_event(c, 1) : nullptr;
   if (prof) record_timing_event(c, ev[0], s);
-  launch_smooth(dt, dir_view(c, D, m), B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s, push, vec);
+  launch_smooth(dt, dir_view(c, D, m), B.e[dt], B.r[dt], coefs_of(c, m, dt), colour, s, push, vec, true);
   if (prof) record_timing_event(c, ev[1], s);
 }
 
@@ -808,7 +821,8 @@ void black_pass(gmg_ctx* c, const LevelDev& D, int dt, int m, cudaStream_t s, bo
   const bool prof = c->profiling && m == 0;
   cudaEvent_t* ev = prof ? smooth_event(c, 1) : nullptr;
   if (prof) record_timing_event(c, ev[0], s);
-  launch_smooth_update(dt, dir_view(c, D, m), B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, phi_last, push_phi, s);
+  launch_smooth_update(dt, dir_view(c, D, m), B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, phi_last, push_phi, s,
+                       true);
   if (prof) record_timing_event(c, ev[1], s);
 }
 void two_pass_sweep(gmg_ctx* c, const LevelDev& D, int dt, int m, cudaStream_t s, bool fill_red, bool push, bool vec,
@@ -889,7 +903,8 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
       const bool prof = c->profiling && m == 0;
       cudaEvent_t* ev = prof ? smooth_event(c, 1) : nullptr;
       if (prof) record_timing_event(c, ev[0], s);
-      launch_smooth_update(dt, dir_view(c, D, m), B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, phi_last, push_phi, s);
+      launch_smooth_update(dt, dir_view(c, D, m), B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, phi_last, push_phi, s,
+                       true);
       if (prof) record_timing_event(c, ev[1], s);
     } else {
       smooth_colour(c, D, dt, m, 1, s, true, push, vec_on(c, p, dt, m));
@@ -1000,7 +1015,7 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   // (pre-smoothing ends with a black half-sweep: black residuals vanish away from walls)
   const bool settled = dt == DT_F64 && p.nu1 > 0 && p.settled_zero != 0 && D.push_ok;
   launch_resid_restrict(dt, dir_view(c, D, m), Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s,
-                        settled);
+                        settled, true);
   vcycle(c, dt, m + 1, p, s, false);
   if (p.prolongation == 1) {  // trilinear: the coarse correction's ghosts, edges and corners too
     launch_fill(dt, c->dev[m + 1], c->buf[m + 1].e[dt], -1, 0, s);
@@ -1065,7 +1080,7 @@ void outer_iteration(gmg_ctx* c, int dt, double* phi, const double* rhs, const g
   if (ev) record_timing_event(c, ev[0], s);
   launch_residual(DT_F64, dt, dir_view(c, c->dev[0], 0), phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits,
                   any_singular(c) ? c->scal : nullptr, s, rr ? c->buf[0].e[dt] : nullptr,
-                  rr ? coefs_of(c, 0, dt).invD : nullptr, rr && level0_push(c, p, dt), outer_settled(c, p, dt));
+                  rr ? coefs_of(c, 0, dt).invD : nullptr, rr && level0_push(c, p, dt), outer_settled(c, p, dt), true);
   if (ev) record_timing_event(c, ev[1], s);
   cudaMemcpyAsync(c->h_bits, c->normbits, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s);
 }
@@ -1207,7 +1222,7 @@ gmg_status solve_impl(gmg_ctx* c, double* phi, const double* rhs, double tol_rel
     const bool rr = resid_red(c, p, dt);
     launch_residual(DT_F64, dt, D0, phi, rhs, coefs64(c, 0), c->buf[0].r[dt], c->normbits, sing ? c->scal : nullptr,
                     s, rr ? c->buf[0].e[dt] : nullptr, rr ? coefs_of(c, 0, dt).invD : nullptr,
-                    rr && level0_push(c, p, dt));
+                    rr && level0_push(c, p, dt), -1, true);
   }
   CK(c, cudaMemcpyAsync(c->h_bits, c->normbits, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
@@ -2076,15 +2091,17 @@ gmg_status krylov_solve(gmg_ctx* c, double* x, const double* rhs, double tol_rel
   auto precond_body = [&](const double* in, double* out, cudaStream_t st) {
     LevelBufs& B0 = c->buf[0];
     if (dt == DT_F64) {
+      // (a colour-split finest level takes a split copy of in as its right-hand side)
       void* const sr = B0.r[DT_F64];
       void* const se = B0.e[DT_F64];
-      B0.r[DT_F64] = (void*)in;
+      if (D0.split & SPLIT_RHS) launch_to_rhs(DT_F64, D0, in, sr, st);
+      else B0.r[DT_F64] = (void*)in;
       B0.e[DT_F64] = out;
       vcycle(c, dt, 0, p, st);
       B0.r[DT_F64] = sr;
       B0.e[DT_F64] = se;
     } else {
-      launch_convert(DT_F64, dt, in, B0.r[dt], ne, st);
+      launch_to_rhs(dt, D0, in, B0.r[dt], st);
       vcycle(c, dt, 0, p, st);
       launch_convert(dt, DT_F64, B0.e[dt], out, ne, st);
     }
@@ -3013,7 +3030,7 @@ gmg_status gmg_autotune(gmg_ctx* c, int precision, const void* rhs, const gmg_pa
   const int reps = 5;
   // a realistic level-0 correction equation: r = rhs (its mean removed for singular problems
   // does not matter for timing), and one V-cycle to populate every level's r
-  launch_convert(DT_F64, dt, rhs, c->buf[0].r[dt], c->L[0].nelem, s);
+  launch_to_rhs(dt, c->dev[0], (const double*)rhs, c->buf[0].r[dt], s);
   gmg_params q = p;
   q.fused_coarse = 1;
   q.ghost_push = 0;
@@ -3040,7 +3057,7 @@ gmg_status gmg_autotune(gmg_ctx* c, int precision, const void* rhs, const gmg_pa
       const double ms = time_reps(c, reps, [&] {
         for (int colour = 0; colour < 2; ++colour) {
           if (!push) launch_fill(dt, D, B.e[dt], 1 - colour, 0, s);
-          launch_smooth(dt, D, B.e[dt], B.r[dt], k, colour, s, push, vec);
+          launch_smooth(dt, D, B.e[dt], B.r[dt], k, colour, s, push, vec, true);
         }
       });
       if (push) best_push = std::min(best_push, ms);
@@ -3092,7 +3109,7 @@ gmg_status gmg_vcycle(gmg_ctx* c, int dt, void* e, const void* r, const gmg_para
   if ((st = build_coefs(c))) return st;
   if ((st = ensure_flow_lag(c, p))) return st;
   const size_t n = dt_size(dt) * (size_t)c->L[0].nelem;
-  CK(c, cudaMemcpyAsync(c->buf[0].r[dt], r, n, cudaMemcpyDeviceToDevice, c->stream));
+  launch_copy_to_rhs(dt, c->dev[0], r, c->buf[0].r[dt], c->stream);
   vcycle(c, dt, 0, p, c->stream);
   CK(c, cudaGetLastError());
   CK(c, cudaMemcpyAsync(e, c->buf[0].e[dt], n, cudaMemcpyDeviceToDevice, c->stream));

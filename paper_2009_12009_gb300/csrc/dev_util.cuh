@@ -42,6 +42,25 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Colour-split storage of a row (the finest level's right-hand side and 1/D, where the
+// level allows it): the row's red cells (even global parity) at x-slots [0, nx/2), its black
+// cells at [nx/2, nx), each half in x order; nx even.  A colour pass then reads half of every
+// such row instead of every sector of it.  Ghost slots are not used (these arrays have none).
+__device__ __forceinline__ int64_t split_index(const DevBox& B, int i, int j, int k) {
+  return B.off + GX + (i >> 1) + (((B.lo[0] + B.lo[1] + B.lo[2] + i + j + k) & 1) ? (B.nx >> 1) : 0) +
+         (int64_t)B.sx * (j + 1) + B.sy * (k + 1);
+}
+// the same slot from the ordinary element q0 of an even cell i0 of the row: the cell of colour
+// c (0 red) of the pair (i0, i0 + 1) sits at q0 - i0 / 2 (+ nx / 2 if black)
+__device__ __forceinline__ int64_t split_pair_slot(int64_t q0, int i0, int c, int nx) {
+  return q0 - (i0 >> 1) + (c ? (nx >> 1) : 0);
+}
+// the element of cell (i, j, k), whose element in the ordinary layout is q, in an array that
+// is colour-split (split) or not
+__device__ __forceinline__ int64_t cell_slot(bool split, const DevBox& B, int i, int j, int k, int64_t q) {
+  return split ? split_index(B, i, j, k) : q;
+}
+
 // decode a pair item of box B into (i0, j, k); i0 even
 __device__ __forceinline__ void pair_decode(const DevBox& B, int t, int& i0, int& j, int& k) {
   const int npx = (B.nx + 1) >> 1;

@@ -65,7 +65,7 @@ __device__ __forceinline__ void flow_item(const DevBox& B, int b, const FlowItem
                                           const typename CoefOf<T>::type* __restrict__ wz,
                                           const typename CoefOf<T>::type* __restrict__ invD,
                                           const PushFace* __restrict__ push, double* __restrict__ phi,
-                                          const PushFace* __restrict__ push_phi) {
+                                          const PushFace* __restrict__ push_phi, int sp) {
   using A = typename Arith<T>::type;
   const int npx = (B.nx + 1) >> 1;
   const int ny = I.y1 - I.y0;
@@ -85,14 +85,15 @@ __device__ __forceinline__ void flow_item(const DevBox& B, int b, const FlowItem
     A s = 0;
     if (i < B.nx) {
       const int64_t q = q0 + off;
-      s = ldg(rhs + q);
+      const int64_t qs = sp ? split_index(B, i, j, k) : q;
+      s = ldg(rhs + ((sp & SPLIT_RHS) ? qs : q));
       s = fma((A)ldg(wx + q), (A)lde<L2>(ein + q - 1), s);
       s = fma((A)ldg(wx + q + 1), (A)lde<L2>(ein + q + 1), s);
       s = fma((A)ldg(wy + q), (A)lde<L2>(ein + q - sx), s);
       s = fma((A)ldg(wy + q + sx), (A)lde<L2>(ein + q + sx), s);
       s = fma((A)ldg(wz + q), (A)lde<L2>(ein + q - sy), s);
       s = fma((A)ldg(wz + q + sy), (A)lde<L2>(ein + q + sy), s);
-      s = s * (A)ldg(invD + q);
+      s = s * (A)ldg(invD + ((sp & SPLIT_INVD) ? qs : q));
       st(eout + q, s);
       if (push) push_ghosts(B, b, boxes, push, eout, i, j, k, s);
     }
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(FLOW_BLOCK)
            const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
            const typename CoefOf<T>::type* __restrict__ invD, const int* __restrict__ active,
            const int* __restrict__ skip, const PushFace* __restrict__ push, double* phi,
-           const PushFace* __restrict__ push_phi, int* err) {
+           const PushFace* __restrict__ push_phi, int* err, int sp) {
   pdl_enter();
   const int lane = threadIdx.x & 31;
   const int warp = (int)(blockIdx.x * (FLOW_BLOCK / 32) + (threadIdx.x >> 5));
@@ -212,9 +213,11 @@ __global__ void __launch_bounds__(FLOW_BLOCK)
       const int colour = (colour0 + c) & 1;
       const bool upd = update_last && c == nphase - 1;
       if (c == 0)
-        flow_item<T, false>(B, I.box, I, colour, upd, lane, boxes, e, e, rhs, wx, wy, wz, invD, push, phi, push_phi);
+        flow_item<T, false>(B, I.box, I, colour, upd, lane, boxes, e, e, rhs, wx, wy, wz, invD, push, phi, push_phi,
+                            sp);
       else
-        flow_item<T, true>(B, I.box, I, colour, upd, lane, boxes, e, e, rhs, wx, wy, wz, invD, push, phi, push_phi);
+        flow_item<T, true>(B, I.box, I, colour, upd, lane, boxes, e, e, rhs, wx, wy, wz, invD, push, phi, push_phi,
+                           sp);
     }
     if (c + 1 < nphase) {
       __syncwarp();  // the lanes' stores of the item come before its count
@@ -284,21 +287,21 @@ bool launch_flow(int dt, const LevelDev& L, void* e, const void* rhs, const Coef
       launch_flow_kernel(k_flow<double>, g, s, L.boxes, L.flow_items, L.flow_slabs, L.n_flow_slabs, order, n,
                          L.flow_cnt, colour0, nphase, upd, (double*)e, (const double*)rhs, (const double*)c.wx,
                          (const double*)c.wy, (const double*)c.wz, (const double*)c.invD, L.active, L.flow_skip,
-                         L.push_faces, phi, pp, err);
+                         L.push_faces, phi, pp, err, L.split);
     } break;
     case DT_F32: {
       const unsigned g = (unsigned)std::max(FLOW_QUEUES / 4, std::min((n + 3) / 4, flow_grid<float>(warps)));
       launch_flow_kernel(k_flow<float>, g, s, L.boxes, L.flow_items, L.flow_slabs, L.n_flow_slabs, order, n,
                          L.flow_cnt, colour0, nphase, upd, (float*)e, (const float*)rhs, (const float*)c.wx,
                          (const float*)c.wy, (const float*)c.wz, (const float*)c.invD, L.active, L.flow_skip,
-                         L.push_faces, phi, pp, err);
+                         L.push_faces, phi, pp, err, L.split);
     } break;
     default: {
       const unsigned g = (unsigned)std::max(FLOW_QUEUES / 4, std::min((n + 3) / 4, flow_grid<bf16>(warps)));
       launch_flow_kernel(k_flow<bf16>, g, s, L.boxes, L.flow_items, L.flow_slabs, L.n_flow_slabs, order, n,
                          L.flow_cnt, colour0, nphase, upd, (bf16*)e, (const bf16*)rhs, (const float*)c.wx,
                          (const float*)c.wy, (const float*)c.wz, (const float*)c.invD, L.active, L.flow_skip,
-                         L.push_faces, phi, pp, err);
+                         L.push_faces, phi, pp, err, L.split);
     } break;
   }
   return true;

@@ -83,18 +83,25 @@ __global__ void __launch_bounds__(BLOCK) k_fill(const DevBox* __restrict__ boxes
 
 // ------------------------------------------------------------ red-black smoother
 
+// resident blocks per SM the smoothers' register count must allow: 8 (32 registers) for float
+// and bfloat16, whose passes are bound by latency more than by bytes; no bound for double
+// (measured: held to 40 registers its finest-level pass took 167.8 us instead of 152.9)
+template <class T> struct SmoothMinB { static constexpr int value = 8; };
+template <> struct SmoothMinB<double> { static constexpr int value = 0; };
+
 // One colour of Gauss-Seidel: each thread owns a pair of x-adjacent cells and updates
 // the one whose global (i+j+k) parity is `colour`:
 //   phi = invD * (rhs + sum_f w_f phi_nbr)          (7 FMA-pipe operations)
 template <class T>
-__global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+__global__ void __launch_bounds__(BLOCK, SmoothMinB<T>::value)
+    k_smooth(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
                                                   T* phi, const T* __restrict__ rhs,
                                                   const typename CoefOf<T>::type* __restrict__ wx,
                                                   const typename CoefOf<T>::type* __restrict__ wy,
                                                   const typename CoefOf<T>::type* __restrict__ wz,
                                                   const typename CoefOf<T>::type* __restrict__ invD, int colour,
                                                   const int* __restrict__ active,
-                                                  const PushFace* __restrict__ push, int rev) {
+                                                  const PushFace* __restrict__ push, int rev, int sp) {
   pdl_enter();
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
@@ -108,14 +115,15 @@ __global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ box
   if (i >= B.nx) return;
   const int64_t q = elem_index(B, i, j, k);
   const int64_t sx = B.sx, sy = B.sy;
-  A s = ldg(rhs + q);
+  const int64_t qs = sp ? split_pair_slot(q - (i & 1), i & ~1, colour, B.nx) : q;
+  A s = ldg(rhs + ((sp & SPLIT_RHS) ? qs : q));
   s = fma((A)ldg(wx + q), (A)ld(phi + q - 1), s);
   s = fma((A)ldg(wx + q + 1), (A)ld(phi + q + 1), s);
   s = fma((A)ldg(wy + q), (A)ld(phi + q - sx), s);
   s = fma((A)ldg(wy + q + sx), (A)ld(phi + q + sx), s);
   s = fma((A)ldg(wz + q), (A)ld(phi + q - sy), s);
   s = fma((A)ldg(wz + q + sy), (A)ld(phi + q + sy), s);
-  s = s * (A)ldg(invD + q);
+  s = s * (A)ldg(invD + ((sp & SPLIT_INVD) ? qs : q));
   st(phi + q, s);
   if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, s);
 }
@@ -127,11 +135,12 @@ __global__ void __launch_bounds__(BLOCK) k_smooth(const DevBox* __restrict__ box
 // them (push_phi non-null).  The same values as the colour pass followed by
 // k_add_correction (each correction added as stored), one pass fewer over phi and e.
 template <class T>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, SmoothMinB<T>::value)
     k_smooth_update(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks, T* e, const T* __restrict__ rhs,
                     const typename CoefOf<T>::type* __restrict__ wx, const typename CoefOf<T>::type* __restrict__ wy,
                     const typename CoefOf<T>::type* __restrict__ wz, const typename CoefOf<T>::type* __restrict__ invD,
-                    int colour, const int* __restrict__ active, double* phi, const PushFace* __restrict__ push_phi, int rev) {
+                    int colour, const int* __restrict__ active, double* phi, const PushFace* __restrict__ push_phi, int rev,
+                    int sp) {
   pdl_enter();
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
@@ -147,14 +156,15 @@ __global__ void __launch_bounds__(BLOCK)
   const int64_t sx = B.sx, sy = B.sy;
   if (i < B.nx) {
     const int64_t q = q0 + par;
-    A s = ldg(rhs + q);
+    const int64_t qs = sp ? split_pair_slot(q0, i0, colour, B.nx) : q;
+    A s = ldg(rhs + ((sp & SPLIT_RHS) ? qs : q));
     s = fma((A)ldg(wx + q), (A)ld(e + q - 1), s);
     s = fma((A)ldg(wx + q + 1), (A)ld(e + q + 1), s);
     s = fma((A)ldg(wy + q), (A)ld(e + q - sx), s);
     s = fma((A)ldg(wy + q + sx), (A)ld(e + q + sx), s);
     s = fma((A)ldg(wz + q), (A)ld(e + q - sy), s);
     s = fma((A)ldg(wz + q + sy), (A)ld(e + q + sy), s);
-    s = s * (A)ldg(invD + q);
+    s = s * (A)ldg(invD + ((sp & SPLIT_INVD) ? qs : q));
     st(e + q, s);
   }
   if (i0 + 1 < B.nx) {
@@ -189,6 +199,17 @@ __device__ __forceinline__ void ld4(const bf16* p, float v[4]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 __device__ __forceinline__ void ldg4(const bf16* p, float v[4]) { ld4(p, v); }
+// two consecutive elements from an even element (a 64-bit load for float, 32-bit for bfloat16)
+__device__ __forceinline__ void ld2e(const float* p, float& a, float& b) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ld2e(const bf16* p, float& a, float& b) {
+  const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  a = v.x;
+  b = v.y;
+}
 
 // One red-black colour with one thread per 4 consecutive cells of a row (boxes whose width
 // is a multiple of 4; float and bfloat16 fields): the thread reads the 4-cell segments of
@@ -200,7 +221,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_smooth4(const DevBox* __restrict__
                                                    T* phi, const T* __restrict__ rhs, const float* __restrict__ wx,
                                                    const float* __restrict__ wy, const float* __restrict__ wz,
                                                    const float* __restrict__ invD, int colour,
-                                                   const int* __restrict__ active, const PushFace* __restrict__ push, int rev) {
+                                                   const int* __restrict__ active, const PushFace* __restrict__ push, int rev,
+                                                   int sp) {
   pdl_enter();
   const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
   const DevBox B = boxes[ch.item];
@@ -212,42 +234,60 @@ __global__ void __launch_bounds__(BLOCK, 4) k_smooth4(const DevBox* __restrict__
   const int j = r % B.ny, k = r / B.ny, i0 = 4 * g;
   const int64_t q0 = elem_index(B, i0, j, k);
   const int64_t sx = B.sx, sy = B.sy;
-  float p[4], pym[4], pyp[4], pzm[4], pzp[4], rh[4], wxl[4], wyl[4], wyh[4], wzl[4], wzh[4], id[4];
+  float p[4], pym[4], pyp[4], pzm[4], pzp[4], wxl[4], wyl[4], wyh[4], wzl[4], wzh[4];
   ld4(phi + q0, p);
   ld4(phi + q0 - sx, pym);
   ld4(phi + q0 + sx, pyp);
   ld4(phi + q0 - sy, pzm);
   ld4(phi + q0 + sy, pzp);
   const float pl = ld(phi + q0 - 1), pr = ld(phi + q0 + 4);
-  ldg4(rhs + q0, rh);
+  const int c0 = (B.lo[0] + B.lo[1] + B.lo[2] + i0 + j + k + colour) & 1;
+  // rhs and 1/D of the segment's two cells of the colour (c0 and c0 + 2); colour-split: two
+  // consecutive slots of the colour's half, the first at an even element (widths are
+  // multiples of 4 here)
+  float ra, rb, da, db;
+  if (sp & SPLIT_RHS) {
+    ld2e(rhs + split_pair_slot(q0, i0, colour, B.nx), ra, rb);
+  } else {
+    float rh[4];
+    ldg4(rhs + q0, rh);
+    ra = c0 ? rh[1] : rh[0];
+    rb = c0 ? rh[3] : rh[2];
+  }
   ldg4(wx + q0, wxl);
   const float wx4 = __ldg(wx + q0 + 4);
   ldg4(wy + q0, wyl);
   ldg4(wy + q0 + sx, wyh);
   ldg4(wz + q0, wzl);
   ldg4(wz + q0 + sy, wzh);
-  ldg4(invD + q0, id);
-  const int c0 = (B.lo[0] + B.lo[1] + B.lo[2] + i0 + j + k + colour) & 1;
+  if (sp & SPLIT_INVD) {
+    ld2e(invD + split_pair_slot(q0, i0, colour, B.nx), da, db);
+  } else {
+    float id[4];
+    ldg4(invD + q0, id);
+    da = c0 ? id[1] : id[0];
+    db = c0 ? id[3] : id[2];
+  }
   // cells m and m + 2 of the segment, m = c0 (constant indices keep the arrays in registers)
-  auto update = [&](auto mc) {
+  auto update = [&](auto mc, float rv, float dv) {
     constexpr int m = decltype(mc)::value;
-    float s = rh[m];
+    float s = rv;
     s = fmaf(wxl[m], m == 0 ? pl : p[m == 0 ? 0 : m - 1], s);
     s = fmaf(m == 3 ? wx4 : wxl[m == 3 ? 3 : m + 1], m == 3 ? pr : p[m == 3 ? 3 : m + 1], s);
     s = fmaf(wyl[m], pym[m], s);
     s = fmaf(wyh[m], pyp[m], s);
     s = fmaf(wzl[m], pzm[m], s);
     s = fmaf(wzh[m], pzp[m], s);
-    s = s * id[m];
+    s = s * dv;
     st(phi + q0 + m, s);
     if (push) push_ghosts(B, ch.item, boxes, push, phi, i0 + m, j, k, s);
   };
   if (c0 == 0) {
-    update(std::integral_constant<int, 0>());
-    update(std::integral_constant<int, 2>());
+    update(std::integral_constant<int, 0>(), ra, da);
+    update(std::integral_constant<int, 2>(), rb, db);
   } else {
-    update(std::integral_constant<int, 1>());
-    update(std::integral_constant<int, 3>());
+    update(std::integral_constant<int, 1>(), ra, da);
+    update(std::integral_constant<int, 3>(), rb, db);
   }
 }
 
@@ -259,7 +299,7 @@ __global__ void __launch_bounds__(BLOCK)
     k_smooth_d2(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks, double* phi,
                 const double* __restrict__ rhs, const double* __restrict__ wx, const double* __restrict__ wy,
                 const double* __restrict__ wz, const double* __restrict__ invD, int colour,
-                const int* __restrict__ active, const PushFace* __restrict__ push, int rev) {
+                const int* __restrict__ active, const PushFace* __restrict__ push, int rev, int sp) {
   pdl_enter();
   const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
   const DevBox B = boxes[ch.item];
@@ -282,17 +322,20 @@ __global__ void __launch_bounds__(BLOCK)
   const double outer = off ? phi[q0 + 2] : phi[q0 - 1];
   const double2 ym = ld2(phi + q0 - sx), yp = ld2(phi + q0 + sx);
   const double2 zm = ld2(phi + q0 - sy), zp = ld2(phi + q0 + sy);
-  const double2 r2 = ldg2(rhs + q0), d2 = ldg2(invD + q0), wx2 = ldg2(wx + q0);
+  const double2 z2 = make_double2(0.0, 0.0);
+  const double2 r2 = (sp & SPLIT_RHS) ? z2 : ldg2(rhs + q0), d2 = (sp & SPLIT_INVD) ? z2 : ldg2(invD + q0);
+  const double2 wx2 = ldg2(wx + q0);
   const double2 wyl = ldg2(wy + q0), wyh = ldg2(wy + q0 + sx), wzl = ldg2(wz + q0), wzh = ldg2(wz + q0 + sy);
   const double wxr = off ? __ldg(wx + q0 + 2) : wx2.y;
-  double s = pick(r2);
+  const int64_t qs = sp ? split_pair_slot(q0, i0, colour, B.nx) : q;
+  double s = (sp & SPLIT_RHS) ? __ldg(rhs + qs) : pick(r2);
   s = fma(off ? wx2.y : wx2.x, off ? own.x : outer, s);
   s = fma(wxr, off ? outer : own.y, s);
   s = fma(pick(wyl), pick(ym), s);
   s = fma(pick(wyh), pick(yp), s);
   s = fma(pick(wzl), pick(zm), s);
   s = fma(pick(wzh), pick(zp), s);
-  s = s * pick(d2);
+  s = s * ((sp & SPLIT_INVD) ? __ldg(invD + qs) : pick(d2));
   phi[q] = s;
   if (push) push_ghosts(B, ch.item, boxes, push, phi, i0 + off, j, k, s);
 }
@@ -309,9 +352,9 @@ __device__ __forceinline__ bool next_to_wall(const DevGeom& G, int g0, int g1, i
 template <class T, class C>
 __device__ __forceinline__ typename Arith<T>::type resid_at(const T* phi, const T* rhs, const C* wx, const C* wy,
                                                            const C* wz, const C* D, int64_t q, int64_t sx, int64_t sy,
-                                                           typename Arith<T>::type shift) {
+                                                           typename Arith<T>::type shift, int64_t rq) {
   using A = typename Arith<T>::type;
-  A v = (A)ldg(rhs + q) - shift;
+  A v = (A)ldg(rhs + rq) - shift;
   v = fma(-(A)ldg(D + q), (A)ld(phi + q), v);
   v = fma((A)ldg(wx + q), (A)ld(phi + q - 1), v);
   v = fma((A)ldg(wx + q + 1), (A)ld(phi + q + 1), v);
@@ -324,7 +367,7 @@ __device__ __forceinline__ typename Arith<T>::type resid_at(const T* phi, const 
 
 // (MINB: resident blocks per SM the register count must allow; 6 for the FP64 residual,
 // whose loads then have more warps to overlap them; 0, no bound, elsewhere)
-template <class T, class R, int MINB>
+template <class T, class R, int MINB, bool RS>
 __global__ void __launch_bounds__(BLOCK, MINB) k_residual(const DevBox* __restrict__ boxes,
                                                           const DevGeom* __restrict__ geoms,
                                                     const Chunk* __restrict__ chunks,
@@ -336,6 +379,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_residual(const DevBox* __restri
                                                     unsigned long long* maxbits, const double* shift_p, R* e,
                                                     const typename CoefOf<R>::type* __restrict__ invDe,
                                                     const PushFace* __restrict__ push, int settled, int rev) {
+  constexpr bool rsplit = RS;  // r (and invDe) colour-split
   pdl_enter();
   using A = typename Arith<T>::type;
   using AR = typename Arith<R>::type;
@@ -354,26 +398,27 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_residual(const DevBox* __restri
     const int cc = c0 == settled ? 1 : 0;                          // offset of the computed cell
     const int cs = 1 - cc;                                          // offset of the settled cell
     if (i0 + cc < B.nx) {
-      const A v = shift_p ? resid_at(phi, rhs, wx, wy, wz, D, q0 + cc, B.sx, B.sy, shift)
-                          : resid_at(phi, rhs, wx, wy, wz, D, q0 + cc, B.sx, B.sy, (A)0);
-      st(r + q0 + cc, v);
+      const A v = shift_p ? resid_at(phi, rhs, wx, wy, wz, D, q0 + cc, B.sx, B.sy, shift, q0 + cc)
+                          : resid_at(phi, rhs, wx, wy, wz, D, q0 + cc, B.sx, B.sy, (A)0, q0 + cc);
+      st(r + (rsplit ? split_pair_slot(q0, i0, (c0 + cc) & 1, B.nx) : q0 + cc), v);
       mx = abs_bits((double)v);
     }
     if (i0 + cs < B.nx) {
       A v = 0;
       if (next_to_wall(geoms[B.solve], B.lo[0] + i0 + cs, B.lo[1] + j, B.lo[2] + k)) {
-        v = shift_p ? resid_at(phi, rhs, wx, wy, wz, D, q0 + cs, B.sx, B.sy, shift)
-                    : resid_at(phi, rhs, wx, wy, wz, D, q0 + cs, B.sx, B.sy, (A)0);
+        v = shift_p ? resid_at(phi, rhs, wx, wy, wz, D, q0 + cs, B.sx, B.sy, shift, q0 + cs)
+                    : resid_at(phi, rhs, wx, wy, wz, D, q0 + cs, B.sx, B.sy, (A)0, q0 + cs);
         const unsigned long long bb = abs_bits((double)v);
         mx = bb > mx ? bb : mx;
       }
-      st(r + q0 + cs, v);
+      st(r + (rsplit ? split_pair_slot(q0, i0, (c0 + cs) & 1, B.nx) : q0 + cs), v);
     }
     if (e) {
       for (int c = 0; c < 2; ++c) {
         if (i0 + c >= B.nx) break;
         const bool red = ((c0 + c) & 1) == 0;
-        const AR ev = red ? (AR)ld(r + q0 + c) * (AR)ldg(invDe + q0 + c) : (AR)0;
+        const int64_t rs = rsplit ? split_pair_slot(q0, i0, (c0 + c) & 1, B.nx) : q0 + c;
+        const AR ev = red ? (AR)ld(r + rs) * (AR)ldg(invDe + rs) : (AR)0;
         st(e + q0 + c, ev);
         if (push) push_ghosts(B, ch.item, boxes, push, e, i0 + c, j, k, ev);
       }
@@ -385,16 +430,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_residual(const DevBox* __restri
     for (int c = 0; c < 2; ++c) {
       if (i0 + c >= B.nx) break;
       // (no shift: one FP64 operation per cell less, the kernel being bound by the FP64 pipe)
-      const A v = shift_p ? resid_at(phi, rhs, wx, wy, wz, D, q0 + c, B.sx, B.sy, shift)
-                          : resid_at(phi, rhs, wx, wy, wz, D, q0 + c, B.sx, B.sy, (A)0);
-      if (r) st(r + q0 + c, v);
+      const A v = shift_p ? resid_at(phi, rhs, wx, wy, wz, D, q0 + c, B.sx, B.sy, shift, q0 + c)
+                          : resid_at(phi, rhs, wx, wy, wz, D, q0 + c, B.sx, B.sy, (A)0, q0 + c);
+      const int64_t rs = rsplit ? split_pair_slot(q0, i0, (B.lo[0] + B.lo[1] + B.lo[2] + i0 + c + j + k) & 1, B.nx) : q0 + c;
+      if (r) st(r + rs, v);
       const unsigned long long bb = abs_bits((double)v);
       mx = bb > mx ? bb : mx;
       if (e) {
         // the first red half-sweep of the next V-cycle on e = 0: every neighbour term is
         // zero, so a red cell becomes r / D (r as stored), a black cell stays 0
         const bool red = ((B.lo[0] + B.lo[1] + B.lo[2] + i0 + c + j + k) & 1) == 0;
-        const AR ev = red ? (AR)ld(r + q0 + c) * (AR)ldg(invDe + q0 + c) : (AR)0;
+        const AR ev = red ? (AR)ld(r + rs) * (AR)ldg(invDe + rs) : (AR)0;
         st(e + q0 + c, ev);
         if (push) push_ghosts(B, ch.item, boxes, push, e, i0 + c, j, k, ev);
       }
@@ -410,14 +456,15 @@ __device__ __forceinline__ typename Arith<T>::type resid_sum8(const DevBox& F, c
                                                               const typename CoefOf<T>::type* wy,
                                                               const typename CoefOf<T>::type* wz,
                                                               const typename CoefOf<T>::type* D, int ci, int cj,
-                                                              int ck) {
+                                                              int ck, bool split) {
   using A = typename Arith<T>::type;
   A s = 0;
   for (int dk = 0; dk < 2; ++dk)
     for (int dj = 0; dj < 2; ++dj) {
-      const int64_t q = elem_index(F, 2 * ci, 2 * cj + dj, 2 * ck + dk);
-      s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0);
-      s += resid_at(phi, rhs, wx, wy, wz, D, q + 1, F.sx, F.sy, (A)0);
+      const int i = 2 * ci, j = 2 * cj + dj, k = 2 * ck + dk;
+      const int64_t q = elem_index(F, i, j, k);
+      s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0, cell_slot(split, F, i, j, k, q));
+      s += resid_at(phi, rhs, wx, wy, wz, D, q + 1, F.sx, F.sy, (A)0, cell_slot(split, F, i + 1, j, k, q + 1));
     }
   return s;
 }
@@ -431,7 +478,7 @@ __global__ void __launch_bounds__(BLOCK, 5)
                      const T* __restrict__ rhs, const typename CoefOf<T>::type* __restrict__ wx,
                      const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
                      const typename CoefOf<T>::type* __restrict__ D, R* rc, const int* __restrict__ active,
-                     int settled_black, int rev) {
+                     int settled_black, int rev, int split) {
   pdl_enter();
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
@@ -450,8 +497,9 @@ __global__ void __launch_bounds__(BLOCK, 5)
     for (int dk = 0; dk < 2; ++dk)
       for (int dj = 0; dj < 2; ++dj) {
         const int dx = (par + dj + dk) & 1;  // the red child of the row pair
-        const int64_t q = elem_index(F, 2 * ci + dx, 2 * cj + dj, 2 * ck + dk);
-        s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0);
+        const int i = 2 * ci + dx, j = 2 * cj + dj, k = 2 * ck + dk;
+        const int64_t q = elem_index(F, i, j, k);
+        s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0, cell_slot(split, F, i, j, k, q));
       }
     const DevGeom G = fgeoms[F.solve];
     const int g0 = F.lo[0] + 2 * ci, g1 = F.lo[1] + 2 * cj, g2 = F.lo[2] + 2 * ck;
@@ -460,12 +508,13 @@ __global__ void __launch_bounds__(BLOCK, 5)
         for (int dj = 0; dj < 2; ++dj) {
           const int dx = 1 - ((par + dj + dk) & 1);  // the black child of the row pair
           if (!next_to_wall(G, g0 + dx, g1 + dj, g2 + dk)) continue;  // (its residual is 0)
-          const int64_t q = elem_index(F, 2 * ci + dx, 2 * cj + dj, 2 * ck + dk);
-          s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0);
+          const int i = 2 * ci + dx, j = 2 * cj + dj, k = 2 * ck + dk;
+          const int64_t q = elem_index(F, i, j, k);
+          s += resid_at(phi, rhs, wx, wy, wz, D, q, F.sx, F.sy, (A)0, cell_slot(split, F, i, j, k, q));
         }
     }
   } else {
-    s = resid_sum8(F, phi, rhs, wx, wy, wz, D, ci, cj, ck);
+    s = resid_sum8(F, phi, rhs, wx, wy, wz, D, ci, cj, ck, split != 0);
   }
   const int I = (F.lo[0] >> 1) + ci - P.lo[0];
   const int J = (F.lo[1] >> 1) + cj - P.lo[1];
@@ -863,7 +912,7 @@ __global__ void __launch_bounds__(BLOCK) k_diag(const DevBox* __restrict__ boxes
                                                 const Chunk* __restrict__ chunks,
                                                 const double* __restrict__ acoef, const double* __restrict__ wx,
                                                 const double* __restrict__ wy, const double* __restrict__ wz,
-                                                double* D, double* invD) {
+                                                double* D, double* invD, int split) {
   const Chunk ch = chunks[blockIdx.x];
   const DevBox B = boxes[ch.item];
   const int t = ch.start + threadIdx.x;
@@ -882,7 +931,7 @@ __global__ void __launch_bounds__(BLOCK) k_diag(const DevBox* __restrict__ boxes
     if (G.wall_hi[a] == 3 && c[a] == n[a] - 1 && B.lo[a] + n[a] - 1 == G.dhi[a]) d += 2.0 * w[a][q + sa];
   }
   D[q] = d;
-  invD[q] = 1.0 / d;
+  invD[cell_slot(split & SPLIT_INVD, B, i, j, k, q)] = 1.0 / d;
 }
 
 template <class S, class T>
@@ -936,26 +985,34 @@ void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, 
                                (T*)f, colour, copy_mode, L.active));
 }
 
+// the split flags of a smoother launch: 1/D as the level keeps it, the right-hand side split
+// only when it is the level's own buffer
+int smooth_split(const LevelDev& L, bool own_rhs) {
+  return (own_rhs ? (L.split & SPLIT_RHS) : 0) | (L.split & SPLIT_INVD);
+}
+
 void launch_smooth_update(int dt, const LevelDev& L, void* e, const void* rhs, const Coefs& c, int colour,
-                          double* phi, bool push_phi, cudaStream_t s) {
+                          double* phi, bool push_phi, cudaStream_t s, bool own_rhs) {
   if (!L.n_pair_chunks) return;
   ++g_launches;
   const PushFace* pf = push_phi ? L.push_faces : nullptr;
+  const int sp = smooth_split(L, own_rhs);
   GMG_DISPATCH(dt, launch_pdl(k_smooth_update<T>, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks,
                               (T*)e, (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
                               (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
-                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, phi, pf, L.rev));
+                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, phi, pf, L.rev, sp));
 }
 
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour, cudaStream_t s,
-                   bool push, bool vec) {
+                   bool push, bool vec, bool own_rhs) {
   if (!L.n_pair_chunks) return;
   ++g_launches;
   const PushFace* pf = push ? L.push_faces : nullptr;
+  const int sp = smooth_split(L, own_rhs);
   if (vec && dt == DT_F64) {
     launch_pdl(k_smooth_d2, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks, (double*)phi,
                (const double*)rhs, (const double*)c.wx, (const double*)c.wy, (const double*)c.wz,
-               (const double*)c.invD, colour, L.active, pf, L.rev);
+               (const double*)c.invD, colour, L.active, pf, L.rev, sp);
     return;
   }
   if (vec && dt != DT_F64 && L.quad_chunks && L.n_quad_chunks > 0) {
@@ -963,52 +1020,55 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
     const float* invD = (const float*)c.invD;
     if (dt == DT_F32)
       launch_pdl(k_smooth4<float>, grid_of(L.n_quad_chunks), BLOCK, 0, s, L.boxes, L.quad_chunks, (float*)phi,
-                 (const float*)rhs, wx, wy, wz, invD, colour, L.active, pf, L.rev);
+                 (const float*)rhs, wx, wy, wz, invD, colour, L.active, pf, L.rev, sp);
     else
       launch_pdl(k_smooth4<bf16>, grid_of(L.n_quad_chunks), BLOCK, 0, s, L.boxes, L.quad_chunks, (bf16*)phi,
-                 (const bf16*)rhs, wx, wy, wz, invD, colour, L.active, pf, L.rev);
+                 (const bf16*)rhs, wx, wy, wz, invD, colour, L.active, pf, L.rev, sp);
     return;
   }
   GMG_DISPATCH(dt, launch_pdl(k_smooth<T>, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks, (T*)phi,
                               (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
                               (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
-                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf, L.rev));
+                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf, L.rev, sp));
 }
 
 // residual work list: pair items over every box (the bottom level included)
 void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const void* rhs, const Coefs& c, void* r,
                      unsigned long long* maxbits, const double* shift, cudaStream_t s, void* e, const void* invDe,
-                     bool push, int settled) {
+                     bool push, int settled, bool own_r) {
+  const int rsplit = own_r ? L.split : 0;
   if (settled >= 0 && (dt != DT_F64 || rdt != DT_F64 || !r)) settled = -1;  // (defined for FP64 only)
   if (!L.n_pair_all_chunks) return;
   ++g_launches;
   const PushFace* pf = push ? L.push_faces : nullptr;
+#define GMG_RESID_LAUNCH(TR, RS)                                                                          \
+  launch_pdl(k_residual<T, TR, std::is_same<T, double>::value && std::is_same<TR, double>::value ? 6 : 0, RS>, \
+             grid_of(L.n_pair_all_chunks), BLOCK, 0, s, L.boxes, L.geoms, L.pair_all_chunks, (const T*)phi,   \
+             (const T*)rhs, (const typename CoefOf<T>::type*)c.wx, (const typename CoefOf<T>::type*)c.wy,      \
+             (const typename CoefOf<T>::type*)c.wz, (const typename CoefOf<T>::type*)c.D, (TR*)r, maxbits,     \
+             shift, (TR*)e, (const typename CoefOf<TR>::type*)invDe, pf, settled, L.rev)
 #define GMG_RESID(TR)                                                                                     \
-  GMG_DISPATCH(dt, launch_pdl(k_residual<T, TR, std::is_same<T, double>::value && std::is_same<TR, double>::value ? 6 : 0>, \
-                              grid_of(L.n_pair_all_chunks), BLOCK, 0, s, L.boxes, L.geoms,                        \
-                              L.pair_all_chunks, (const T*)phi, (const T*)rhs,                                  \
-                              (const typename CoefOf<T>::type*)c.wx, (const typename CoefOf<T>::type*)c.wy,     \
-                              (const typename CoefOf<T>::type*)c.wz, (const typename CoefOf<T>::type*)c.D,      \
-                              (TR*)r, maxbits, shift, (TR*)e, (const typename CoefOf<TR>::type*)invDe, pf, settled, \
-                              L.rev))
+  GMG_DISPATCH(dt, rsplit ? GMG_RESID_LAUNCH(TR, true) : GMG_RESID_LAUNCH(TR, false))
   switch (rdt) {
     case DT_F64: GMG_RESID(double); break;
     case DT_F32: GMG_RESID(float); break;
     default: GMG_RESID(bf16); break;
   }
 #undef GMG_RESID
+#undef GMG_RESID_LAUNCH
 
 }
 
 void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* phi, const void* rhs,
-                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black) {
+                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black, bool own_rhs) {
   if (!f.n_coarse_chunks) return;
   ++g_launches;
+  const int split = own_rhs ? (f.split & SPLIT_RHS) : 0;
   GMG_DISPATCH(dt, launch_pdl(k_resid_restrict<T, T>, grid_of(f.n_coarse_chunks), BLOCK, 0, s, f.boxes, f.geoms, c.boxes,
                               f.parent, f.coarse_chunks, (const T*)phi, (const T*)rhs,
                               (const typename CoefOf<T>::type*)cf.wx, (const typename CoefOf<T>::type*)cf.wy,
                               (const typename CoefOf<T>::type*)cf.wz, (const typename CoefOf<T>::type*)cf.D, (T*)rc,
-                              f.active, settled_black ? 1 : 0, f.rev));
+                              f.active, settled_black ? 1 : 0, f.rev, split));
 
 }
 
@@ -1134,11 +1194,52 @@ void launch_coarsen_coefs(const LevelDev& f, const LevelDev& c, const double* ac
                                                                wyf, wzf, acc, wxc, wyc, wzc);
 }
 
+// dst (type T, the level's own right-hand side layout: colour-split if split) = src (double,
+// the ordinary layout) on every valid cell
+template <class S, class T>
+__global__ void __launch_bounds__(BLOCK) k_to_rhs(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                                  const S* __restrict__ src, T* dst, int split) {
+  const Chunk ch = chunks[blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  const int t = ch.start + threadIdx.x;
+  if (t >= B.nx * B.ny * B.nz) return;
+  const int i = t % B.nx, j = (t / B.nx) % B.ny, k = t / (B.nx * B.ny);
+  const int64_t q = elem_index(B, i, j, k);
+  if (std::is_same<S, T>::value)
+    dst[cell_slot(split & SPLIT_RHS, B, i, j, k, q)] = *reinterpret_cast<const T*>(src + q);
+  else
+    st(dst + cell_slot(split & SPLIT_RHS, B, i, j, k, q), ld(src + q));
+}
+
+void launch_to_rhs(int dt, const LevelDev& L, const double* src, void* dst, cudaStream_t s) {
+  if (!(L.split & SPLIT_RHS)) {
+    launch_convert(DT_F64, dt, src, dst, L.nelem, s);
+    return;
+  }
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  GMG_DISPATCH(dt, (k_to_rhs<double, T><<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, src,
+                                                                                     (T*)dst, L.split)));
+}
+
+void launch_copy_to_rhs(int dt, const LevelDev& L, const void* src, void* dst, cudaStream_t s) {
+  if (!(L.split & SPLIT_RHS)) {
+    cudaMemcpyAsync(dst, src, (size_t)L.nelem * (dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2)), cudaMemcpyDeviceToDevice,
+                    s);
+    return;
+  }
+  if (!L.n_cell_chunks) return;
+  ++g_launches;
+  GMG_DISPATCH(dt, (k_to_rhs<T, T><<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.cell_chunks, (const T*)src,
+                                                                                (T*)dst, L.split)));
+}
+
 void launch_diag(const LevelDev& L, const double* acoef, const double* wx, const double* wy, const double* wz,
                  double* D, double* invD, cudaStream_t s) {
   if (!L.n_cell_chunks) return;
   ++g_launches;
-  k_diag<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.geoms, L.cell_chunks, acoef, wx, wy, wz, D, invD);
+  k_diag<<<grid_of(L.n_cell_chunks), BLOCK, 0, s>>>(L.boxes, L.geoms, L.cell_chunks, acoef, wx, wy, wz, D, invD,
+                                                    L.split);
 }
 
 void launch_convert(int dt, int dt2, const void* src, void* dst, int64_t n, cudaStream_t s) {

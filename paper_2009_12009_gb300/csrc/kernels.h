@@ -75,11 +75,19 @@ struct LevelDev {
   int push_ok = 0;                       // push_faces usable for every box of the level
   const BotGhost* ec_ghosts = nullptr;  // edge and corner ghosts (levels >= 1), f[dst] = sign f[src]
   int n_ec_ghosts = 0;
+  // SPLIT_RHS | SPLIT_INVD: the level's own right-hand side buffers (r, every element type)
+  // and its 1/D are colour-split within rows; 0: the ordinary layout.  (A kernel given
+  // another right-hand side -- a caller's -- reads it in the ordinary layout.)
+  int split = 0;
   // 1: the level-sweep kernels (smoothers, residual, residual-restriction, interpolation)
   // take their work list last entry first.  Consecutive kernels on a level that alternate it
   // start on the boxes the previous one touched last, still in L2.  Same results.
   int rev = 0;
 };
+
+// Which arrays of a level are stored colour-split within rows (split_index, dev_util.cuh):
+// the level's right-hand side of the smoother, its 1/D.  Ordinary layout otherwise.
+enum { SPLIT_RHS = 1, SPLIT_INVD = 2 };
 
 // Coefficients of one level in one element type (double for FP64 fields, float for
 // float and bfloat16 fields): scaled face weights w = b*beta/h^2, diagonal
@@ -98,11 +106,15 @@ struct Coefs {
 void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, cudaStream_t s);
 // one red-black colour (no ghost fill); push: also write each new value into the ghost
 // cells that copy it (L.push_ok levels only)
+// own_rhs: rhs is the level's own right-hand side buffer (colour-split where L.split says so;
+// a caller's rhs is in the ordinary layout); 1/D is read as the level keeps it
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour,
-                   cudaStream_t s, bool push = false, bool vec = false);
+                   cudaStream_t s, bool push = false, bool vec = false, bool own_rhs = false);
 // r = (rhs - shift[solve]) - A phi on valid cells (ghosts of phi must be filled); rdt =
 // type of r; maxbits (may be null): per-solve atomic max of |r| as IEEE bits; shift (may be
 // null): per-solve device scalars
+// own_r: r is the level's own right-hand side buffer, colour-split where L.split says so
+// (and then invDe is the level's 1/D, split alike)
 // e (may be null): also the first red half-sweep of a V-cycle on this r from e = 0 --
 // e = r / D on red cells (invDe: 1/D in the coefficient type of rdt), 0 on black cells,
 // pushed into e's ghosts when push is set
@@ -113,12 +125,12 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
 // cells are computed).  Its r is stored as 0 without being computed.
 void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const void* rhs, const Coefs& c,
                      void* r, unsigned long long* maxbits, const double* shift, cudaStream_t s, void* e = nullptr,
-                     const void* invDe = nullptr, bool push = false, int settled = -1);
+                     const void* invDe = nullptr, bool push = false, int settled = -1, bool own_r = false);
 // coarse r = restriction of (rhs - A phi) (ghosts of phi filled); settled_black: the last
 // half-sweep on phi was black (as for launch_residual: black children count 0 unless they
 // lie next to a wall)
 void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* phi, const void* rhs,
-                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black = false);
+                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black = false, bool own_rhs = false);
 void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s);
 void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine,
                         cudaStream_t s, bool push = false);
@@ -136,7 +148,7 @@ void launch_add_correction(int dt, const LevelDev& L, double* phi, const void* e
 // the last colour pass of the finest level's post-smoothing fused with phi += e on every
 // smoothed cell (pair work list); push_phi: also write phi's new values into its ghosts
 void launch_smooth_update(int dt, const LevelDev& L, void* e, const void* rhs, const Coefs& c, int colour,
-                          double* phi, bool push_phi, cudaStream_t s);
+                          double* phi, bool push_phi, cudaStream_t s, bool own_rhs = false);
 // dense (nz,ny,nx) double over the level's (single-solve) domain <-> boxed type dt
 void launch_pack(int dt, const LevelDev& L, const int dlo[3], const int dn[3], const double* dense, void* boxed,
                  cudaStream_t s);
@@ -171,6 +183,11 @@ void launch_diag(const LevelDev& L, const double* acoef, const double* wx, const
 void launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s);
 // copy a field of type dt into type dt2 (same layout, every element)
 void launch_convert(int dt, int dt2, const void* src, void* dst, int64_t n, cudaStream_t s);
+// the level's own right-hand side buffer (type dt; colour-split where L.split says so) = src
+// (double, the ordinary layout) on the valid cells
+void launch_to_rhs(int dt, const LevelDev& L, const double* src, void* dst, cudaStream_t s);
+// the same from a type-dt source (a copy where the level is not split)
+void launch_copy_to_rhs(int dt, const LevelDev& L, const void* src, void* dst, cudaStream_t s);
 
 // programmatic dependent launch for the V-cycle kernels (fill, smooth, residuals,
 // restriction, interpolation, correction, coarse end, bottom): each may start while its

@@ -2,15 +2,13 @@
 //
 // The smoother of Sec. "Linear Solvers" (red-black Gauss-Seidel, colour = parity of i + j + k
 // in the level's global index) as a wavefront: every thread block takes one tile (a band of
-// rows of one box, all of its x and all of its planes) and marches through the tile's planes.
-// At step m it updates the red cells of plane m (in the tile's marching order), then the
-// black cells of plane m - 1.  Each thread owns fixed x-pairs of cells of the tile, so the
-// red values of its pair on the planes around a black cell are still in its registers, the
-// black values a red cell reads on the plane before it were loaded one step earlier, and the
-// red values the black cells of a plane read across rows or pairs of the tile come from a
-// three-plane ring in shared memory.  Every array of the level is read from HBM once per
-// sweep (the coefficient lines a black cell needs were fetched one step earlier, for the red
-// cell beside it) and phi is written once: the 56 B/cell of the sweep, not twice that.
+// rows of one box, all of its x and all of its planes) and marches through the tile's planes
+// a slab at a time: the red cells of the slab's planes, a report, then the black cells of
+// every plane whose red cells on both sides are done.  The black cells of a plane read the red
+// cells the block has just written, so the coefficient lines they need were fetched for the
+// red cells beside them a moment earlier (L1/L2), and every array of the level is read from
+// HBM about once per sweep instead of once per colour.  The next slab's rows are prefetched
+// into L2 with bulk prefetches while a slab is worked on.
 //
 // Tiles meet tiles of the same box (other row bands) and tiles of neighbouring boxes.  The
 // red cells of a plane read black cells of the tiles next to them, and their black cells read
@@ -139,7 +137,7 @@ __global__ void __launch_bounds__(WAVE_BLOCK, MINB)
            const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
            const typename CoefOf<T>::type* __restrict__ invD, const int* __restrict__ active,
            const int* __restrict__ skip, const PushFace* __restrict__ push, double* phi,
-           const PushFace* __restrict__ push_phi, int* err, int slab) {
+           const PushFace* __restrict__ push_phi, int* err, int slab, int sp) {
   using A = typename Arith<T>::type;
   wv_pdl_wait();
   __shared__ int s_tile;
@@ -205,9 +203,10 @@ __global__ void __launch_bounds__(WAVE_BLOCK, MINB)
           if (!ok[u]) continue;
           const int off = (par + pj[u] + k) & 1;  // the red cell of the pair is i0 + off
           const int64_t q = q0[u] + (int64_t)k * sy + off;
+          const int64_t qs = sp ? split_index(B, 2 * ppx[u] + off, pj[u], k) : q;
           Upd<A> o;
-          o.r = ldg(rhs + q);
-          o.d = ldg(invD + q);
+          o.r = ldg(rhs + ((sp & SPLIT_RHS) ? qs : q));
+          o.d = ldg(invD + ((sp & SPLIT_INVD) ? qs : q));
           A s;
           if (MODE == 1) {
             s = (o.r + (A)0) * o.d;
@@ -265,9 +264,10 @@ __global__ void __launch_bounds__(WAVE_BLOCK, MINB)
             const int ob = 1 - ((par + pj[u] + kb) & 1);  // the black cell of the pair is i0 + ob
             const int64_t qp = q0[u] + (int64_t)kb * sy;
             const int64_t q = qp + ob;
+            const int64_t qs = sp ? split_index(B, 2 * ppx[u] + ob, pj[u], kb) : q;
             Upd<A> o;
-            o.r = ldg(rhs + q);
-            o.d = ldg(invD + q);
+            o.r = ldg(rhs + ((sp & SPLIT_RHS) ? qs : q));
+            o.d = ldg(invD + ((sp & SPLIT_INVD) ? qs : q));
             o.w[0] = ldg(wx + q);
             o.w[1] = ldg(wx + q + 1);
             o.w[2] = ldg(wy + q);
@@ -367,7 +367,7 @@ bool wave_go(const LevelDev& L, void* e, const void* rhs, const Coefs& c, double
   launch_wave_kernel(k_wave<T, PPT, MODE, WAVE_MINB>, (unsigned)L.n_wave_tiles, s, L.boxes, L.wave_tiles,
                      L.n_wave_tiles, L.wave_cnt, (T*)e, (const T*)rhs, (const C*)c.wx, (const C*)c.wy, (const C*)c.wz,
                      (const C*)c.invD, L.active, L.flow_skip, L.push_ok ? L.push_faces : nullptr, phi, pp, err,
-                     wave_slab(L, (int)(2 * sizeof(T) + 5 * sizeof(C))));
+                     wave_slab(L, (int)(2 * sizeof(T) + 5 * sizeof(C))), L.split);
   return true;
 }
 
