@@ -227,6 +227,13 @@ typedef struct {
                            faster on GB300 (abec256 level 0: 350 us per FP64 sweep, 228 in float,
                            against 508 and 329 for the wavefront launch, whose threads each own a
                            column of cells and so have one update's loads in flight at a time). */
+  int tail_dense;       /* 1 (default): the coarse end of fused_coarse holds each problem's
+                           levels in shared memory, every level as one padded array over the
+                           problem's domain there (a problem's boxes tile it), loaded once
+                           per V-cycle, so each of its steps reads on-chip memory instead of
+                           global memory; problems whose levels do not fit keep the global-
+                           memory coarse end.  Bitwise the results of 0; 0: the coarse end
+                           reads and writes the levels' global arrays at every step. */
 } gmg_params;
 
 typedef struct {
@@ -326,6 +333,14 @@ gmg_status gmg_mg_level_boxes(const gmg_ctx* ctx, int m, int* box_lohi, int* par
    the black cells of the first (z-) and last (z+) plane, and the tile's problem (batched
    form).  Host only (no device work). */
 gmg_status gmg_wave_tiles(const gmg_ctx* ctx, int m, int* ntiles, int* ppt, int* out, int cap);
+
+/* The coarse ends that start on MG level m (fused_coarse; the coarse levels of the V-cycle
+   of Sec. "Linear Solvers" run by one thread block per problem): *nblocks receives how many
+   (one per problem; 0: none starts there) and *dense_bytes the shared memory of their dense
+   form in element type dt (gmg_dtype; 0: they keep the global-memory form, because a
+   problem's boxes do not tile its domain on one of the levels or the arrays do not fit).
+   Host only (no device work).  Either pointer may be NULL. */
+gmg_status gmg_tail_plan(const gmg_ctx* ctx, int m, int dt, int* nblocks, long long* dense_bytes);
 
 /* Boxed layout of MG level m for element type dt: total elements, per-box element
    offsets (nboxes entries, may be NULL) and row strides sx (nboxes entries, may be

@@ -180,6 +180,7 @@ struct gmg_ctx {
   BotCell* tcells = nullptr;
   BotGhost* tghosts = nullptr;
   TailXfer* txfer = nullptr;
+  BotGhost* tdghosts = nullptr;
 
   // composite form: AMR levels 1, 2, ... (ratio 2 each) over part of the level below;
   // amrl[l - 1] is AMR level l
@@ -390,8 +391,9 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     BotCell* tc = (BotCell*)cv.take(sizeof(BotCell) * T.cells.size());
     BotGhost* tg = (BotGhost*)cv.take(sizeof(BotGhost) * T.ghosts.size());
     TailXfer* tx = (TailXfer*)cv.take(sizeof(TailXfer) * T.xfer.size());
+    BotGhost* tdg = (BotGhost*)cv.take(sizeof(BotGhost) * T.dghosts.size());
     if (fill) {
-      c->tdescs = td; c->tlevels = tl; c->tcells = tc; c->tghosts = tg; c->txfer = tx;
+      c->tdescs = td; c->tlevels = tl; c->tcells = tc; c->tghosts = tg; c->txfer = tx; c->tdghosts = tdg;
     }
   }
   for (size_t al = 0; al < c->amrl.size(); ++al) {  // AMR level al + 1
@@ -564,6 +566,7 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, c->tcells, T.cells))) return st;
     if ((st = upload(c, c->tghosts, T.ghosts))) return st;
     if ((st = upload(c, c->txfer, T.xfer))) return st;
+    if ((st = upload(c, c->tdghosts, T.dghosts))) return st;
   }
   for (const AmrLevel& V : c->amrl) {
     const LevelMeta& M = V.M;
@@ -913,9 +916,10 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
 }
 
 // the graph-cache value of the sweep choices: fused_sweep, the flow launch width, serpentine,
-// the interpolation
+// the interpolation, the wavefront sweep, the coarse end's form
 int sweep_key(const gmg_params& p) {
-  return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine + 2048 * p.prolongation + 4096 * p.wave_sweep;
+  return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine + 2048 * p.prolongation + 4096 * p.wave_sweep +
+         8192 * p.tail_dense;
 }
 
 // the symmetric V-cycle: post-smoothing black before red (asked for, or implied by the
@@ -942,6 +946,22 @@ LevelDev vc_view(const gmg_ctx* c, int m) {
   return D;
 }
 
+// Shared memory (bytes) of the dense coarse end for the tails that start at level m in
+// element type dt, or 0 if one of them has no dense form or needs more than TAIL_SMEM_MAX.
+int64_t tail_dense_bytes(const gmg_ctx* c, int dt, int m) {
+  const TailHost& T = c->tail;
+  const int es = (int)dt_size(dt), cs = dt == DT_F64 ? 8 : 4;
+  int64_t most = 0;
+  for (int k = 0; k < T.count_at[m]; ++k) {
+    const TailDesc& D = T.descs[T.first_at[m] + k];
+    if (!D.dense) return 0;
+    int64_t b = 0;
+    for (int q = D.m0; q <= D.mb; ++q) b += tail_level_bytes(T.levels[D.lev0 + q - D.m0].dne, es, cs, q < D.mb);
+    most = std::max(most, b);
+  }
+  return most <= TAIL_SMEM_MAX ? most : 0;
+}
+
 // the tails that start at level m: one block per problem runs its levels m..bottom
 void launch_tails(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s) {
   const TailHost& T = c->tail;
@@ -952,6 +972,7 @@ void launch_tails(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s
   a.cells = c->tcells;
   a.ghosts = c->tghosts;
   a.xfer = c->txfer;
+  a.dghosts = c->tdghosts;
   TailLevelBufs lv[TAIL_MAXLEV];
   for (int q = 0; q < nlev(c) && q < TAIL_MAXLEV; ++q) {
     const LevelBufs& B = c->buf[q];
@@ -971,7 +992,8 @@ void launch_tails(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s
   a.post_rev = post_reversed(p) ? 1 : 0;
   a.iters = c->bot_iters;
   a.active = c->active;
-  launch_vtail(dt, T.count_at[m], a, lv, std::min(nlev(c), TAIL_MAXLEV), s);
+  const int64_t dense = p.tail_dense ? tail_dense_bytes(c, dt, m) : 0;
+  launch_vtail(dt, T.count_at[m], a, lv, std::min(nlev(c), TAIL_MAXLEV), (int)dense, s);
 }
 
 // V-cycle on the correction equation of level m: e_m = V(r_m), e_m zeroed first.  Problems
@@ -1126,6 +1148,7 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.serpentine != 0 && p.serpentine != 1) SETERR(c, GMG_ERR_BAD_INPUT, "serpentine must be 0 or 1");
   if (p.prolongation != 0 && p.prolongation != 1) SETERR(c, GMG_ERR_BAD_INPUT, "prolongation must be 0 or 1");
   if (p.wave_sweep != 0 && p.wave_sweep != 1) SETERR(c, GMG_ERR_BAD_INPUT, "wave_sweep must be 0 or 1");
+  if (p.tail_dense != 0 && p.tail_dense != 1) SETERR(c, GMG_ERR_BAD_INPUT, "tail_dense must be 0 or 1");
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
@@ -2370,6 +2393,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->serpentine = 1;
   p->prolongation = 0;
   p->wave_sweep = 0;
+  p->tail_dense = 1;
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;
@@ -2577,6 +2601,15 @@ gmg_status gmg_wave_tiles(const gmg_ctx* c, int m, int* ntiles, int* ppt, int* o
                            W.nb[3], W.zb[0], W.zb[1], W.zneed[0], W.zneed[1], W.solve};
       for (int u = 0; u < 13; ++u) out[13 * t + u] = row[u];
     }
+  return GMG_OK;
+}
+
+gmg_status gmg_tail_plan(const gmg_ctx* c, int m, int dt, int* nblocks, long long* dense_bytes) {
+  if (!c || m < 0 || m >= (int)c->L.size() || dt < 0 || dt >= NDT) return GMG_ERR_BAD_INPUT;
+  const TailHost& T = c->tail;
+  const bool any = c->tail_ok && m < (int)T.count_at.size() && T.count_at[m] > 0;
+  if (nblocks) *nblocks = any ? T.count_at[m] : 0;
+  if (dense_bytes) *dense_bytes = any ? (long long)tail_dense_bytes(c, dt, m) : 0;
   return GMG_OK;
 }
 

@@ -170,13 +170,40 @@ struct TailLevel {
   int cell0, ncell[2];   // colour-0 cells at [cell0, cell0 + ncell[0]), colour 1 after them
   int ghost0, nghost[2]; // ghosts of parity 0, then parity 1 (walls included)
   int xfer0, nxfer;      // coarse cells of level m + 1 over this level's boxes (m < mb)
+  // Dense form (the shared-memory coarse end): the problem's cells of this level tile one
+  // box, the level's domain, held as one padded array of dne = (n0+2)(n1+2)(n2+2) elements
+  // with strides 1, dsx, dsy.  A cell's slot is BotCell.pad (TAIL_SLOT_MASK bits, plus
+  // TAIL_HI_* / TAIL_LO_* flags where its high / low face lies on the domain's boundary);
+  // the ghosts outside the domain (walls, periodic images) are dense BotGhost entries of
+  // parity 0, then 1.  face[2 a + side]: the rule of the domain's face on axis a, low (0) or
+  // high (1) side -- +1 / -1 a wall whose ghost is +/- the cell inward, 2 periodic (the
+  // ghost is the cell at the other end), 0 none -- with which a boundary cell writes its
+  // new value into the ghosts that copy it.
+  int dsx, dsy, dne;
+  int dghost0, ndghost[2];
+  int face[6];
 };
+constexpr int TAIL_SLOT_MASK = (1 << 24) - 1;
+constexpr int TAIL_HI_X = 1 << 24, TAIL_HI_Y = 1 << 25, TAIL_HI_Z = 1 << 26;
+constexpr int TAIL_LO_X = 1 << 27, TAIL_LO_Y = 1 << 28, TAIL_LO_Z = 1 << 29;
+// shared-memory budget of the dense coarse end's arrays (dynamic shared memory per block)
+constexpr int TAIL_SMEM_MAX = 160 * 1024;
+
+// Bytes of one level's arrays in the dense coarse end: e and r (element size es) and, on a
+// smoothed level, wx, wy, wz, 1/D and D (coefficient size cs), each 16-byte aligned.
+__host__ __device__ inline int64_t tail_level_bytes(int dne, int es, int cs, bool smoothed) {
+  const int64_t a = ((int64_t)dne * es + 15) & ~(int64_t)15;
+  const int64_t b = ((int64_t)dne * cs + 15) & ~(int64_t)15;
+  return 2 * a + (smoothed ? 5 * b : 0);
+}
 
 // one coarse cell of the next level and its 8 children on this level:
 // qf + {0,1} + sx*{0,1} + sy*{0,1}
 struct TailXfer {
   int64_t qc, qf;
   int sx, sy;
+  int dqc, dqf;  // the same two cells' slots in the dense form
+  int dfl;       // TAIL_LO_* flags of child (0,0,0) and TAIL_HI_* flags of child (1,1,1)
 };
 
 struct TailDesc {
@@ -186,6 +213,8 @@ struct TailDesc {
   int singular;     // bottom projects onto zero mean
   int bot_span;     // elements from bot_base to the end of the problem's last bottom box
   int64_t bot_base; // first element of the problem's first bottom box
+  int dense;        // 1: every level of the tail has its dense form
+  int pad_;
 };
 
 __host__ __device__ inline int64_t elem_index(const DevBox& B, int i, int j, int k) {

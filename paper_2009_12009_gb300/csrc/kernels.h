@@ -244,6 +244,7 @@ struct TailArgs {
   const BotCell* cells = nullptr;
   const BotGhost* ghosts = nullptr;
   const TailXfer* xfer = nullptr;
+  const BotGhost* dghosts = nullptr;     // dense-form ghosts (TailLevel.dghost0)
   const double* wx64[TAIL_MAXLEV] = {};  // FP64 coefficients (bottom solve)
   const double* wy64[TAIL_MAXLEV] = {};
   const double* wz64[TAIL_MAXLEV] = {};
@@ -264,7 +265,9 @@ struct TailLevelBufs {
   void* r = nullptr;
   const void *wx = nullptr, *wy = nullptr, *wz = nullptr, *D = nullptr, *invD = nullptr;
 };
-void launch_vtail(int dt, int nblocks, const TailArgs& a, const TailLevelBufs* lv, int nlev, cudaStream_t s);
+// dense_bytes > 0: the dense coarse end (k_vtail_dense) with that much dynamic shared memory
+void launch_vtail(int dt, int nblocks, const TailArgs& a, const TailLevelBufs* lv, int nlev, int dense_bytes,
+                  cudaStream_t s);
 
 // Wall values on level 0 (walls.cu), one launch per face: mode 0 f[q] += c g, mode 1
 // f[ghost] += (2 or h) g, mode 2 dg = c lam[q]; c = 2 w (kind 1, Dirichlet) or w h (kind 2,

@@ -745,9 +745,44 @@ std::string build_tail(std::vector<LevelMeta>& L, TailHost& T) {
     D.mb = bottom[s];
     D.lev0 = (int)T.levels.size();
     D.singular = 0;  // set from the operator's scalars at coefficient time
+    // bounding box of the problem's boxes on level m; false unless they tile it
+    auto bbox = [&](int m, int lo[3], int hi[3]) {
+      int64_t vol = 0;
+      bool first = true;
+      for (int d = 0; d < 3; ++d) lo[d] = 0, hi[d] = -1;
+      for (int b = 0; b < (int)L[m].boxes.size(); ++b) {
+        if (L[m].box_solve[b] != s) continue;
+        const Box& B = L[m].boxes[b];
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = first ? B.lo[d] : std::min(lo[d], B.lo[d]);
+          hi[d] = first ? B.hi[d] : std::max(hi[d], B.hi[d]);
+        }
+        first = false;
+        vol += B.volume();
+      }
+      const int64_t bv = (int64_t)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+      return !first && vol == bv && bv <= (1 << 24);
+    };
+    D.dense = 1;
     for (int m = D.m0; m <= D.mb; ++m) {
       const LevelMeta& M = L[m];
       TailLevel TL{};
+      // the dense form: the problem's boxes of this level must tile their bounding box
+      int dlo[3], dhi[3];
+      if (!bbox(m, dlo, dhi)) D.dense = 0;
+      const int dn[3] = {dhi[0] - dlo[0] + 1, dhi[1] - dlo[1] + 1, dhi[2] - dlo[2] + 1};
+      TL.dsx = dn[0] + 2;
+      TL.dsy = (dn[0] + 2) * (dn[1] + 2);
+      TL.dne = D.dense ? TL.dsy * (dn[2] + 2) : 0;
+      // dense slot of global cell (gi, gj, gk); cells outside the domain's ghost layer: -1
+      auto dslot = [&](int gi, int gj, int gk) -> int {
+        const int u = gi - dlo[0] + 1, v = gj - dlo[1] + 1, w = gk - dlo[2] + 1;
+        if (!D.dense || u < 0 || v < 0 || w < 0 || u > dn[0] + 1 || v > dn[1] + 1 || w > dn[2] + 1) return -1;
+        return u + TL.dsx * v + TL.dsy * w;
+      };
+      auto inside = [&](int gi, int gj, int gk) {
+        return gi >= dlo[0] && gi <= dhi[0] && gj >= dlo[1] && gj <= dhi[1] && gk >= dlo[2] && gk <= dhi[2];
+      };
       TL.cell0 = (int)T.cells.size();
       for (int colour = 0; colour < 2; ++colour) {
         const int c0 = (int)T.cells.size();
@@ -757,14 +792,25 @@ std::string build_tail(std::vector<LevelMeta>& L, TailHost& T) {
           for (int k = 0; k < B.nz; ++k)
             for (int j = 0; j < B.ny; ++j)
               for (int i = 0; i < B.nx; ++i)
-                if (pmod2(B.lo[0] + B.lo[1] + B.lo[2] + i + j + k) == colour)
-                  T.cells.push_back({elem_index(B, i, j, k), B.sy, B.sx, 0});
+                if (pmod2(B.lo[0] + B.lo[1] + B.lo[2] + i + j + k) == colour) {
+                  const int gi = B.lo[0] + i, gj = B.lo[1] + j, gk = B.lo[2] + k;
+                  int slot = std::max(0, dslot(gi, gj, gk));
+                  if (gi == dhi[0]) slot |= TAIL_HI_X;
+                  if (gj == dhi[1]) slot |= TAIL_HI_Y;
+                  if (gk == dhi[2]) slot |= TAIL_HI_Z;
+                  if (gi == dlo[0]) slot |= TAIL_LO_X;
+                  if (gj == dlo[1]) slot |= TAIL_LO_Y;
+                  if (gk == dlo[2]) slot |= TAIL_LO_Z;
+                  T.cells.push_back({elem_index(B, i, j, k), B.sy, B.sx, slot});
+                }
         }
         TL.ncell[colour] = (int)T.cells.size() - c0;
       }
       TL.ghost0 = (int)T.ghosts.size();
+      TL.dghost0 = (int)T.dghosts.size();
       for (int parity = 0; parity < 2; ++parity) {
         const int g0 = (int)T.ghosts.size();
+        const int dg0 = (int)T.dghosts.size();
         for (const GhostRect& g : M.ghosts) {
           if (M.box_solve[g.dst_box] != s) continue;
           const DevBox& Bd = M.dbox[g.dst_box];
@@ -778,13 +824,49 @@ std::string build_tail(std::vector<LevelMeta>& L, TailHost& T) {
               sl[g.d1] += u; sl[g.d2] += v;
               T.ghosts.push_back({elem_index(Bd, dl[0], dl[1], dl[2]), elem_index(Bs, sl[0], sl[1], sl[2]),
                                   ghost_factor(g)});
+              // dense form: only the ghosts outside the domain (a ghost between two boxes is
+              // the neighbouring cell itself there)
+              const int gd[3] = {Bd.lo[0] + dl[0], Bd.lo[1] + dl[1], Bd.lo[2] + dl[2]};
+              const int gs[3] = {Bs.lo[0] + sl[0], Bs.lo[1] + sl[1], Bs.lo[2] + sl[2]};
+              if (D.dense && !inside(gd[0], gd[1], gd[2])) {
+                const int a = dslot(gd[0], gd[1], gd[2]), b2 = dslot(gs[0], gs[1], gs[2]);
+                if (a < 0 || b2 < 0 || !inside(gs[0], gs[1], gs[2])) D.dense = 0;
+                else T.dghosts.push_back({a, b2, ghost_factor(g)});
+                // the face's rule: a wall copies the cell inward, a periodic image the cell
+                // at the other end (one cell across: both readings give the same copy)
+                int ax = -1;
+                for (int d = 0; d < 3; ++d)
+                  if (gd[d] < dlo[d] || gd[d] > dhi[d]) ax = ax < 0 ? d : 3;
+                if (ax < 0 || ax > 2) {
+                  D.dense = 0;
+                } else {
+                  const int side = gd[ax] < dlo[ax] ? 0 : 1;
+                  const int inward = side ? dhi[ax] : dlo[ax], across = side ? dlo[ax] : dhi[ax];
+                  const int sg = ghost_factor(g) < 0 ? -1 : 1;
+                  int rule = 0;
+                  if (gs[ax] == inward && (sg < 0 || dn[ax] > 1)) rule = sg;
+                  else if (gs[ax] == across && sg > 0) rule = 2;
+                  for (int d = 0; d < 3; ++d)
+                    if (d != ax && gs[d] != gd[d]) rule = 0;
+                  // (a smoothed level pushes values into periodic images: an odd period
+                  // would make a cell's image the other colour's neighbour)
+                  if (rule == 2 && m < D.mb && (dn[ax] & 1)) rule = 0;
+                  int& f = TL.face[2 * ax + side];
+                  if (rule == 0 || (f != 0 && f != rule)) D.dense = 0;
+                  else f = rule;
+                }
+              }
             }
         }
         TL.nghost[parity] = (int)T.ghosts.size() - g0;
+        TL.ndghost[parity] = (int)T.dghosts.size() - dg0;
       }
       TL.xfer0 = (int)T.xfer.size();
       if (m < D.mb) {
         const LevelMeta& Cm = L[m + 1];
+        int clo[3], chi[3];
+        if (!bbox(m + 1, clo, chi)) D.dense = 0;
+        const int csx = chi[0] - clo[0] + 3, csy = csx * (chi[1] - clo[1] + 3);
         for (int b = 0; b < (int)M.boxes.size(); ++b) {
           if (M.box_solve[b] != s) continue;
           if (M.parent[b] < 0) return "tail: a box without a coarse parent above the bottom (internal error)";
@@ -799,6 +881,16 @@ std::string build_tail(std::vector<LevelMeta>& L, TailHost& T) {
                 x.qf = elem_index(F, 2 * ci, 2 * cj, 2 * ck);
                 x.sx = F.sx;
                 x.sy = (int)F.sy;
+                if (D.dense) {
+                  const int g[3] = {(F.lo[0] >> 1) + ci, (F.lo[1] >> 1) + cj, (F.lo[2] >> 1) + ck};
+                  x.dqc = (g[0] - clo[0] + 1) + csx * (g[1] - clo[1] + 1) + csy * (g[2] - clo[2] + 1);
+                  const int f[3] = {F.lo[0] + 2 * ci, F.lo[1] + 2 * cj, F.lo[2] + 2 * ck};
+                  x.dqf = dslot(f[0], f[1], f[2]);
+                  if (x.dqf < 0) D.dense = 0;
+                  x.dfl = (f[0] == dlo[0] ? TAIL_LO_X : 0) | (f[1] == dlo[1] ? TAIL_LO_Y : 0) |
+                          (f[2] == dlo[2] ? TAIL_LO_Z : 0) | (f[0] + 1 == dhi[0] ? TAIL_HI_X : 0) |
+                          (f[1] + 1 == dhi[1] ? TAIL_HI_Y : 0) | (f[2] + 1 == dhi[2] ? TAIL_HI_Z : 0);
+                }
                 T.xfer.push_back(x);
               }
         }

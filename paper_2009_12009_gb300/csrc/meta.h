@@ -119,6 +119,7 @@ struct TailHost {
   std::vector<BotCell> cells;
   std::vector<BotGhost> ghosts;
   std::vector<TailXfer> xfer;
+  std::vector<BotGhost> dghosts;        // dense-form ghosts (slots of the levels' dense arrays)
   std::vector<int> first_at, count_at;  // per MG level: descs whose m0 is that level
   std::vector<int> tail_from;           // per solve: m0, or -1 (no tail)
 };

@@ -25,7 +25,7 @@ PRECISION = {"fp64": FP64, "fp32": MIXED_FP32, "mixed_fp32": MIXED_FP32, "bf16":
 # every symbol declared in include/gmg.h
 EXPORTS = [
     "gmg_default_params", "gmg_create", "gmg_destroy", "gmg_last_error", "gmg_define_domain", "gmg_define_level",
-    "gmg_chop_domain", "gmg_mg_nlevels", "gmg_mg_level_info", "gmg_mg_level_boxes", "gmg_wave_tiles", "gmg_mg_layout", "gmg_layout",
+    "gmg_chop_domain", "gmg_mg_nlevels", "gmg_mg_level_info", "gmg_mg_level_boxes", "gmg_wave_tiles", "gmg_tail_plan", "gmg_mg_layout", "gmg_layout",
     "gmg_pack", "gmg_unpack", "gmg_set_scalars", "gmg_set_acoef", "gmg_set_bcoef_cell", "gmg_set_bcoef_face",
     "gmg_get_coeffs", "gmg_workspace_size", "gmg_set_workspace", "gmg_solve", "gmg_apply", "gmg_fill_boundary",
     "gmg_smooth", "gmg_residual", "gmg_restrict", "gmg_prolong_add", "gmg_prolong_add_trilinear",
@@ -47,7 +47,7 @@ class Params(C.Structure):
                 ("krylov", C.c_int), ("bottom_solver", C.c_int), ("post_reverse", C.c_int),
                 ("fuse_correction", C.c_int), ("settled_zero", C.c_int), ("flow_warps", C.c_int),
                 ("flow_lag_kcells", C.c_int), ("serpentine", C.c_int), ("prolongation", C.c_int),
-                ("wave_sweep", C.c_int)]
+                ("wave_sweep", C.c_int), ("tail_dense", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -101,6 +101,7 @@ def _declare(L):
         "gmg_mg_level_info": [vp, C.c_int, i32p, i32p],
         "gmg_mg_level_boxes": [vp, C.c_int, i32p, i32p],
         "gmg_wave_tiles": [vp, C.c_int, i32p, i32p, i32p, C.c_int],
+        "gmg_tail_plan": [vp, C.c_int, C.c_int, i32p, C.POINTER(C.c_longlong)],
         "gmg_mg_layout": [vp, C.c_int, C.c_int, i64p, i64p, i32p],
         "gmg_layout": [vp, C.c_int, i64p, i64p],
         "gmg_pack": [vp, C.c_int, C.c_int, vp, vp],
@@ -255,6 +256,13 @@ class Context:
         out = (C.c_int * max(1, 13 * n.value))()
         self._check(self.L.gmg_wave_tiles(self.h, m, None, None, out, n.value))
         return ppt.value, np.array(out[:13 * n.value], dtype=np.int64).reshape(n.value, 13)
+
+    def tail_plan(self, m, dt=DT_F64):
+        """(blocks, dense shared-memory bytes) of the coarse ends starting on level m (fused
+        coarse end; bytes 0: the global-memory form)."""
+        n, b = C.c_int(), C.c_longlong()
+        self._check(self.L.gmg_tail_plan(self.h, m, dt, C.byref(n), C.byref(b)))
+        return n.value, b.value
 
     def layout(self, m, dt=DT_F64):
         nb, _ = self.level_info(m)

@@ -185,3 +185,25 @@ def test_noalloc_refuses_large_boxes_before_any_cuda_call():
                                         C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), 200, 1e-4, None)
         assert st == gmg.BAD_INPUT, n
         assert b"static scratch limit" in L.gmg_last_error(None), n
+
+
+def test_tail_plan_dense_bytes():
+    """The coarse end's dense form (fused_coarse, tail_dense): abec256 (256^3 in 64 boxes of
+    64^3) starts its tail on level 5, 8^3 cells in 64 boxes of 2^3, then 4^3 and the 2^3 bottom.
+    One padded array per level: 10^3, 6^3 and 4^3 elements; e and r in the element type, and
+    five coefficient arrays (wx, wy, wz, 1/D, D: double for FP64, float otherwise) on the two
+    smoothed levels, each array rounded up to 16 bytes."""
+    cfg = I.abec256()
+    ctx = gmg.Context(cfg["domain"], cfg["bc_lo"], cfg["bc_hi"], boxes=cfg["boxes"])
+    al = lambda b: (b + 15) // 16 * 16  # noqa: E731
+    for dt, es, cs in ((gmg.DT_F64, 8, 8), (gmg.DT_F32, 4, 4), (gmg.DT_BF16, 2, 4)):
+        want = sum(2 * al(ne * es) + (5 * al(ne * cs) if sm else 0)
+                   for ne, sm in ((1000, True), (216, True), (64, False)))
+        assert ctx.tail_plan(5, dt) == (1, want)
+        assert all(ctx.tail_plan(m, dt) == (0, 0) for m in range(ctx.nlevels) if m != 5)
+    # batched: one block per problem, grouped by the level its tail starts on
+    sizes = [(32, 48, 16), (16, 16, 32), (48, 32, 32), (32, 16, 48), (64, 64, 64)]
+    B = gmg.BatchContext([I.batch_problem(s, i, max_grid_size=16) for i, s in enumerate(sizes)])
+    plans = [B.tail_plan(m) for m in range(B.nlevels)]
+    assert sum(n for n, _ in plans) == len(sizes)
+    assert all(b > 0 for n, b in plans if n > 0)
