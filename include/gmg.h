@@ -234,6 +234,12 @@ typedef struct {
                            global memory; problems whose levels do not fit keep the global-
                            memory coarse end.  Bitwise the results of 0; 0: the coarse end
                            reads and writes the levels' global arrays at every step. */
+  int fuse_restriction_sweep; /* 1 (default): the residual restriction into each coarse level
+                           that the grid launches smooth also performs that level's first red
+                           half-sweep from the zero correction (a red cell becomes r / D, a
+                           black one 0, every valid cell written, ghosts pushed), saving a
+                           colour pass and a zero fill per level and V-cycle; the same values
+                           as 0 (a -0.0 right-hand side aside). */
 } gmg_params;
 
 typedef struct {

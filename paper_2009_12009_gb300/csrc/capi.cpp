@@ -916,10 +916,10 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
 }
 
 // the graph-cache value of the sweep choices: fused_sweep, the flow launch width, serpentine,
-// the interpolation, the wavefront sweep, the coarse end's form
+// the interpolation, the wavefront sweep, the coarse end's form, the restriction's red pass
 int sweep_key(const gmg_params& p) {
   return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine + 2048 * p.prolongation + 4096 * p.wave_sweep +
-         8192 * p.tail_dense;
+         8192 * p.tail_dense + 16384 * p.fuse_restriction_sweep;
 }
 
 // the symmetric V-cycle: post-smoothing black before red (asked for, or implied by the
@@ -1010,6 +1010,16 @@ void choose_pdl(const gmg_params& p, cudaStream_t s) {
   set_pdl(p.pdl == 1 || (p.pdl == 2 && cs == cudaStreamCaptureStatusNone));
 }
 
+// Whether the residual restriction into level m (>= 1) also performs that level's first red
+// half-sweep of pre-smoothing: level m is smoothed by the grid launches (pair or 4-cell
+// threads, red first) and pre-smooths at least once.
+bool coarse_red(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
+  if (p.fuse_restriction_sweep == 0 || p.nu1 <= 0 || m < 1 || m + 1 >= nlev(c)) return false;
+  const bool fused = tail_on(c, p, dt) && c->tail_ok;
+  const LevelDev D = fused ? vc_view(c, m) : c->dev[m];
+  return D.n_pair_chunks > 0;
+}
+
 // phi_update (finest level only, see fuse_correction_on): the last post-smoothing pass also
 // adds e to phi
 void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool red_done = false,
@@ -1036,9 +1046,14 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
   // (pre-smoothing ends with a black half-sweep: black residuals vanish away from walls)
   const bool settled = dt == DT_F64 && p.nu1 > 0 && p.settled_zero != 0 && D.push_ok;
+  // (fuse_restriction_sweep: the coarse level's first red half-sweep from e = 0 is done by
+  // the restriction, which writes every valid coarse cell of e, so no zero fill either)
+  const bool cred = coarse_red(c, p, dt, m + 1);
+  const bool cpush = push_on(c, p, dt, m + 1) && Dc.push_ok;
   launch_resid_restrict(dt, dir_view(c, D, m), Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s,
-                        settled, true);
-  vcycle(c, dt, m + 1, p, s, false);
+                        settled, true, cred ? c->buf[m + 1].e[dt] : nullptr,
+                        cred ? coefs_of(c, m + 1, dt).invD : nullptr, cpush);
+  vcycle(c, dt, m + 1, p, s, cred);
   if (p.prolongation == 1) {  // trilinear: the coarse correction's ghosts, edges and corners too
     launch_fill(dt, c->dev[m + 1], c->buf[m + 1].e[dt], -1, 0, s);
     launch_fill_ec(dt, c->dev[m + 1], c->buf[m + 1].e[dt], s);
@@ -1149,6 +1164,8 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.prolongation != 0 && p.prolongation != 1) SETERR(c, GMG_ERR_BAD_INPUT, "prolongation must be 0 or 1");
   if (p.wave_sweep != 0 && p.wave_sweep != 1) SETERR(c, GMG_ERR_BAD_INPUT, "wave_sweep must be 0 or 1");
   if (p.tail_dense != 0 && p.tail_dense != 1) SETERR(c, GMG_ERR_BAD_INPUT, "tail_dense must be 0 or 1");
+  if (p.fuse_restriction_sweep != 0 && p.fuse_restriction_sweep != 1)
+    SETERR(c, GMG_ERR_BAD_INPUT, "fuse_restriction_sweep must be 0 or 1");
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
@@ -2394,6 +2411,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->prolongation = 0;
   p->wave_sweep = 0;
   p->tail_dense = 1;
+  p->fuse_restriction_sweep = 1;
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;

@@ -478,7 +478,8 @@ __global__ void __launch_bounds__(BLOCK, 5)
                      const T* __restrict__ rhs, const typename CoefOf<T>::type* __restrict__ wx,
                      const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
                      const typename CoefOf<T>::type* __restrict__ D, R* rc, const int* __restrict__ active,
-                     int settled_black, int rev, int split) {
+                     int settled_black, int rev, int split, R* ec, const typename CoefOf<R>::type* __restrict__ invDc,
+                     const PushFace* __restrict__ cpush) {
   pdl_enter();
   using A = typename Arith<T>::type;
   const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
@@ -519,7 +520,17 @@ __global__ void __launch_bounds__(BLOCK, 5)
   const int I = (F.lo[0] >> 1) + ci - P.lo[0];
   const int J = (F.lo[1] >> 1) + cj - P.lo[1];
   const int K = (F.lo[2] >> 1) + ck - P.lo[2];
-  st(rc + elem_index(P, I, J, K), s * (A)0.125);
+  const int64_t qc = elem_index(P, I, J, K);
+  st(rc + qc, s * (A)0.125);
+  if (ec) {
+    // the coarse level's first red half-sweep on e = 0: every neighbour term is zero, so a
+    // red cell becomes r / D (r as stored), a black cell stays 0
+    using AR = typename Arith<R>::type;
+    const bool red = ((P.lo[0] + P.lo[1] + P.lo[2] + I + J + K) & 1) == 0;
+    const AR ev = red ? (AR)ld(rc + qc) * (AR)ldg(invDc + qc) : (AR)0;
+    st(ec + qc, ev);
+    if (cpush) push_ghosts(P, parent[ch.item], cboxes, cpush, ec, I, J, K, ev);
+  }
 }
 
 template <class T>
@@ -1060,15 +1071,18 @@ void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const 
 }
 
 void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* phi, const void* rhs,
-                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black, bool own_rhs) {
+                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black, bool own_rhs, void* ec,
+                           const void* invDc, bool cpush) {
   if (!f.n_coarse_chunks) return;
   ++g_launches;
   const int split = own_rhs ? (f.split & SPLIT_RHS) : 0;
+  const PushFace* pf = (ec && cpush) ? c.push_faces : nullptr;
   GMG_DISPATCH(dt, launch_pdl(k_resid_restrict<T, T>, grid_of(f.n_coarse_chunks), BLOCK, 0, s, f.boxes, f.geoms, c.boxes,
                               f.parent, f.coarse_chunks, (const T*)phi, (const T*)rhs,
                               (const typename CoefOf<T>::type*)cf.wx, (const typename CoefOf<T>::type*)cf.wy,
                               (const typename CoefOf<T>::type*)cf.wz, (const typename CoefOf<T>::type*)cf.D, (T*)rc,
-                              f.active, settled_black ? 1 : 0, f.rev, split));
+                              f.active, settled_black ? 1 : 0, f.rev, split, (T*)ec,
+                              (const typename CoefOf<T>::type*)invDc, pf));
 
 }
 

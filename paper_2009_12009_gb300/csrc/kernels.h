@@ -128,9 +128,12 @@ void launch_residual(int dt, int rdt, const LevelDev& L, const void* phi, const 
                      const void* invDe = nullptr, bool push = false, int settled = -1, bool own_r = false);
 // coarse r = restriction of (rhs - A phi) (ghosts of phi filled); settled_black: the last
 // half-sweep on phi was black (as for launch_residual: black children count 0 unless they
-// lie next to a wall)
+// lie next to a wall).  ec non-null: also the coarse level's first red half-sweep from a zero
+// correction, ec = r / D (invDc: the coarse 1/D) on red cells and 0 on black ones, every
+// valid coarse cell written (cpush: and pushed into the coarse ghosts that copy it).
 void launch_resid_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* phi, const void* rhs,
-                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black = false, bool own_rhs = false);
+                           const Coefs& cf, void* rc, cudaStream_t s, bool settled_black = false, bool own_rhs = false,
+                           void* ec = nullptr, const void* invDc = nullptr, bool cpush = false);
 void launch_restrict(int dt, const LevelDev& f, const LevelDev& c, const void* fine, void* coarse, cudaStream_t s);
 void launch_prolong_add(int dt, const LevelDev& f, const LevelDev& c, const void* coarse, void* fine,
                         cudaStream_t s, bool push = false);

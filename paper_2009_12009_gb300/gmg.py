@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("krylov", C.c_int), ("bottom_solver", C.c_int), ("post_reverse", C.c_int),
                 ("fuse_correction", C.c_int), ("settled_zero", C.c_int), ("flow_warps", C.c_int),
                 ("flow_lag_kcells", C.c_int), ("serpentine", C.c_int), ("prolongation", C.c_int),
-                ("wave_sweep", C.c_int), ("tail_dense", C.c_int)]
+                ("wave_sweep", C.c_int), ("tail_dense", C.c_int),
+                ("fuse_restriction_sweep", C.c_int)]
 
 
 class SolveInfo(C.Structure):
