@@ -240,6 +240,17 @@ typedef struct {
                            black one 0, every valid cell written, ghosts pushed), saving a
                            colour pass and a zero fill per level and V-cycle; the same values
                            as 0 (a -0.0 right-hand side aside). */
+  int fuse_prolongation; /* 1 (default): where a level's post-smoothing starts with a red pass
+                           of the grid launches and the coarser level's ghosts are pushed
+                           (linear walls, piecewise-constant interpolation, red-first
+                           post-smoothing), that red pass reads each neighbour as the
+                           interpolation of the coarse correction would leave it (its value
+                           plus its parent's) and the interpolation pass is not launched -- the
+                           black cells it would have changed are rewritten by the black pass
+                           that follows without being read.  Bitwise the results of 0.  1
+                           leaves out FP64 levels of at least 2^22 cells, whose colour pass is
+                           bound by the FP64 pipe (the six additions per update cost more than
+                           the pass they save); 2: every level where it applies. */
 } gmg_params;
 
 typedef struct {

@@ -807,6 +807,19 @@ void smooth_colour(gmg_ctx* c, const LevelDev& D, int dt, int m, int colour, cud
   if (prof) record_timing_event(c, ev[1], s);
 }
 
+// the red pass of smooth_colour fused with the interpolation of the coarse correction ec
+// (level m + 1) that precedes it (launch_smooth_pro)
+void smooth_colour_pro(gmg_ctx* c, const LevelDev& D, const LevelDev& Dc, int dt, int m, const void* ec,
+                       cudaStream_t s, bool push) {
+  const LevelBufs& B = c->buf[m];
+  if (!push) launch_fill(dt, D, B.e[dt], 1, 0, s);
+  const bool prof = c->profiling && m == 0;
+  cudaEvent_t* ev = prof ? smooth_event(c, 1) : nullptr;
+  if (prof) record_timing_event(c, ev[0], s);
+  launch_smooth_pro(dt, dir_view(c, D, m), Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), 0, ec, s, push, true);
+  if (prof) record_timing_event(c, ev[1], s);
+}
+
 // whether the sweeps of level m run as wavefront launches (wave.cu): wave_sweep on, the level
 // has wavefront tables and pushes its ghosts (red-first sweeps only)
 bool wave_on(const gmg_params& p, const LevelDev& D, bool push) { return p.wave_sweep != 0 && push && wave_ok(D); }
@@ -845,7 +858,8 @@ void two_pass_sweep(gmg_ctx* c, const LevelDev& D, int dt, int m, cudaStream_t s
 // as dataflow launches of up to FLOW_MAX_PHASES passes each, with the same values.
 void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s,
                    bool e_zero = false, bool push = false, bool red_done = false, bool reverse = false,
-                   double* phi_last = nullptr, bool push_phi = false) {
+                   double* phi_last = nullptr, bool push_phi = false, const void* pro_ec = nullptr,
+                   const LevelDev* pro_c = nullptr) {
   if (nsweep <= 0) return;
   if (!reverse && wave_on(p, D, push)) {
     const LevelBufs& B = c->buf[m];
@@ -899,7 +913,10 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
     return;
   }
   for (int it = 0; it < nsweep; ++it) {
-    if (!(red_done && it == 0)) smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
+    if (pro_ec && it == 0)  // (the interpolation of the coarse correction, fused into the red pass)
+      smooth_colour_pro(c, D, *pro_c, dt, m, pro_ec, s, push);
+    else if (!(red_done && it == 0))
+      smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
     if (phi_last && it == nsweep - 1) {
       const LevelBufs& B = c->buf[m];
       if (!push) launch_fill(dt, D, B.e[dt], 0, 0, s);
@@ -916,10 +933,10 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
 }
 
 // the graph-cache value of the sweep choices: fused_sweep, the flow launch width, serpentine,
-// the interpolation, the wavefront sweep, the coarse end's form, the restriction's red pass
+// the interpolation, the wavefront sweep, the coarse end's form, the fused red passes
 int sweep_key(const gmg_params& p) {
   return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine + 2048 * p.prolongation + 4096 * p.wave_sweep +
-         8192 * p.tail_dense + 16384 * p.fuse_restriction_sweep;
+         8192 * p.tail_dense + 16384 * p.fuse_restriction_sweep + 32768 * p.fuse_prolongation;
 }
 
 // the symmetric V-cycle: post-smoothing black before red (asked for, or implied by the
@@ -1020,6 +1037,27 @@ bool coarse_red(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
   return D.n_pair_chunks > 0;
 }
 
+// Whether level m's first post-smoothing (red) pass also performs the interpolation of level
+// m + 1's correction before it (launch_smooth_pro): piecewise-constant interpolation, red-first
+// post-smoothing by the grid's two-pass sweeps on level m, which pushes its ghosts (push),
+// linear walls (a quadratic wall ghost is not the parent's image), and level m + 1's ghosts
+// current when its post-smoothing ends: it pushes them and every problem on it is smoothed
+// by the grid launches (no bottom solve and no coarse end starting there).
+bool prolong_fused(gmg_ctx* c, const gmg_params& p, int dt, int m, bool push, const LevelDev& D) {
+  if (p.fuse_prolongation == 0 || p.prolongation != 0 || post_reversed(p) || p.nu2 <= 0 || any_quad(c) || !push)
+    return false;
+  // (FP64 on a large level: the colour pass is bound by the FP64 pipe, and the six additions
+  // per update cost more than the interpolation pass they save -- measured on abec256)
+  if (p.fuse_prolongation == 1 && dt == DT_F64 && c->L[m].ncells >= (1 << 22)) return false;
+  if (m + 2 >= nlev(c)) return false;
+  if (wave_on(p, D, push) || flow_on(c, p, D, push)) return false;
+  const bool fused = tail_on(c, p, dt) && c->tail_ok;
+  const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
+  if (!(push_on(c, p, dt, m + 1) && Dc.push_ok) || Dc.n_pair_chunks == 0 || Dc.n_bot > 0) return false;
+  if (Dc.n_pair_chunks != c->dev[m + 1].n_pair_chunks) return false;  // (a coarse end starts there)
+  return true;
+}
+
 // phi_update (finest level only, see fuse_correction_on): the last post-smoothing pass also
 // adds e to phi
 void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool red_done = false,
@@ -1054,10 +1092,15 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
                         settled, true, cred ? c->buf[m + 1].e[dt] : nullptr,
                         cred ? coefs_of(c, m + 1, dt).invD : nullptr, cpush);
   vcycle(c, dt, m + 1, p, s, cred);
+  const bool pro = prolong_fused(c, p, dt, m, push, D);
   if (p.prolongation == 1) {  // trilinear: the coarse correction's ghosts, edges and corners too
     launch_fill(dt, c->dev[m + 1], c->buf[m + 1].e[dt], -1, 0, s);
     launch_fill_ec(dt, c->dev[m + 1], c->buf[m + 1].e[dt], s);
     launch_prolong_tri(dt, dir_view(c, D, m), Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
+  } else if (pro) {
+    // (the interpolation is done by the first post-smoothing red pass)
+    smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, false, phi_update, push_phi, c->buf[m + 1].e[dt], &Dc);
+    return;
   } else {
     launch_prolong_add(dt, dir_view(c, D, m), Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
   }
@@ -1166,6 +1209,8 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
   if (p.tail_dense != 0 && p.tail_dense != 1) SETERR(c, GMG_ERR_BAD_INPUT, "tail_dense must be 0 or 1");
   if (p.fuse_restriction_sweep != 0 && p.fuse_restriction_sweep != 1)
     SETERR(c, GMG_ERR_BAD_INPUT, "fuse_restriction_sweep must be 0 or 1");
+  if (p.fuse_prolongation < 0 || p.fuse_prolongation > 2)
+    SETERR(c, GMG_ERR_BAD_INPUT, "fuse_prolongation must be 0, 1 or 2");
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
@@ -2412,6 +2457,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->wave_sweep = 0;
   p->tail_dense = 1;
   p->fuse_restriction_sweep = 1;
+  p->fuse_prolongation = 1;
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;

@@ -99,5 +99,28 @@ __device__ __forceinline__ void push_ghosts(const DevBox& B, int b, const DevBox
   }
 }
 
+// push_ghosts restricted to the wall faces: only the cell's own images
+template <class T, class A>
+__device__ __forceinline__ void push_walls(const DevBox& B, int b, const DevBox* __restrict__ boxes,
+                                            const PushFace* __restrict__ faces, T* f, int i, int j, int k, A v) {
+  if (i != 0 && i != B.nx - 1 && j != 0 && j != B.ny - 1 && k != 0 && k != B.nz - 1) return;
+#pragma unroll
+  for (int fc = 0; fc < 6; ++fc) {
+    const int d = fc >> 1;
+    const int c = d == 0 ? i : (d == 1 ? j : k);
+    const int nd = d == 0 ? B.nx : (d == 1 ? B.ny : B.nz);
+    if (c != ((fc & 1) ? nd - 1 : 0)) continue;
+    const PushFace P = faces[6 * b + fc];
+    if (P.box < 0 || !P.wall) continue;
+    const A w = P.sign < 0 ? -v : v;
+    if (P.direct) {
+      st(f + elem_index(B, i, j, k) + P.delta, w);
+    } else {
+      const DevBox Bd = boxes[P.box];
+      st(f + elem_index(Bd, i + P.dx, j + P.dy, k + P.dz), w);
+    }
+  }
+}
+
 }  // namespace
 }  // namespace gmg

@@ -47,6 +47,8 @@ struct PushFace {
   int dx, dy, dz;
   int direct;     // 1: same row and plane strides, the ghost of element q is q + delta
   int64_t delta;
+  int wall;       // 1: a physical wall (the ghost is the cell's own image); 0: a copy
+  int pad_;
 };
 
 // One rectangle of face ghost cells of box dst_box and where its values come from.

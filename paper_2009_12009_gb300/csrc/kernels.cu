@@ -128,6 +128,72 @@ __global__ void __launch_bounds__(BLOCK, SmoothMinB<T>::value)
   if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, s);
 }
 
+// a value of type T's arithmetic type rounded as T stores it
+__device__ __forceinline__ double as_stored(double v, const double*) { return v; }
+__device__ __forceinline__ float as_stored(float v, const float*) { return v; }
+__device__ __forceinline__ float as_stored(float v, const bf16*) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// The first (red) pass of post-smoothing fused with the interpolation of the coarse
+// correction ec (piecewise constant, Sec. "Operations between levels"): a red cell reads
+// each neighbour as the interpolation would have left it -- its value plus its parent's
+// coarse value, rounded as stored, ghosts included (their parents are the coarse ghosts,
+// which must be current) -- and is updated as k_smooth does.  The black cells are not
+// written: the black pass that follows overwrites them without reading them, so the
+// interpolation pass over the level goes away and the red cells get the values of the
+// interpolation followed by the colour pass, bit for bit.  A black cell next to a wall does
+// read its own image there, so its interpolated value goes into its wall ghosts (which no
+// red cell reads); the level must push its ghosts (an exchange would copy the old value).
+template <class T>
+__global__ void __launch_bounds__(BLOCK)
+    k_smooth_pro(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks, T* phi, const T* __restrict__ rhs,
+                 const typename CoefOf<T>::type* __restrict__ wx, const typename CoefOf<T>::type* __restrict__ wy,
+                 const typename CoefOf<T>::type* __restrict__ wz, const typename CoefOf<T>::type* __restrict__ invD,
+                 int colour, const int* __restrict__ active, const PushFace* __restrict__ push, int rev, int sp,
+                 const T* __restrict__ ec, const DevBox* __restrict__ cboxes, const int* __restrict__ parent) {
+  pdl_enter();
+  using A = typename Arith<T>::type;
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  if (active && !active[B.solve]) return;
+  const int t = ch.start + threadIdx.x;
+  if (t >= ((B.nx + 1) >> 1) * B.ny * B.nz) return;
+  int i0, j, k;
+  pair_decode(B, t, i0, j, k);
+  const int par = (B.lo[0] + B.lo[1] + B.lo[2] + i0 + j + k + colour) & 1;
+  const int i = i0 + par, ib = i0 + 1 - par;  // the cell of the colour and the other one
+  const DevBox P = cboxes[parent[ch.item]];
+  // parent (coarse) element of the fine cell at global (a0, a1, a2); floor halving
+  auto pe = [&](int a0, int a1, int a2) -> A {
+    return (A)ld(ec + elem_index(P, (a0 >> 1) - P.lo[0], (a1 >> 1) - P.lo[1], (a2 >> 1) - P.lo[2]));
+  };
+  if (push && ib < B.nx) {
+    const int64_t qb = elem_index(B, ib, j, k);
+    push_walls(B, ch.item, boxes, push, phi, ib, j, k,
+               as_stored((A)ld(phi + qb) + pe(B.lo[0] + ib, B.lo[1] + j, B.lo[2] + k), phi));
+  }
+  if (i >= B.nx) return;
+  const int64_t q = elem_index(B, i, j, k);
+  const int64_t sx = B.sx, sy = B.sy;
+  const int64_t qs = sp ? split_pair_slot(q - (i & 1), i & ~1, colour, B.nx) : q;
+  const int g0 = B.lo[0] + i, g1 = B.lo[1] + j, g2 = B.lo[2] + k;
+  const A vxm = as_stored((A)ld(phi + q - 1) + pe(g0 - 1, g1, g2), phi);
+  const A vxp = as_stored((A)ld(phi + q + 1) + pe(g0 + 1, g1, g2), phi);
+  const A vym = as_stored((A)ld(phi + q - sx) + pe(g0, g1 - 1, g2), phi);
+  const A vyp = as_stored((A)ld(phi + q + sx) + pe(g0, g1 + 1, g2), phi);
+  const A vzm = as_stored((A)ld(phi + q - sy) + pe(g0, g1, g2 - 1), phi);
+  const A vzp = as_stored((A)ld(phi + q + sy) + pe(g0, g1, g2 + 1), phi);
+  A s = ldg(rhs + ((sp & SPLIT_RHS) ? qs : q));
+  s = fma((A)ldg(wx + q), vxm, s);
+  s = fma((A)ldg(wx + q + 1), vxp, s);
+  s = fma((A)ldg(wy + q), vym, s);
+  s = fma((A)ldg(wy + q + sx), vyp, s);
+  s = fma((A)ldg(wz + q), vzm, s);
+  s = fma((A)ldg(wz + q + sy), vzp, s);
+  s = s * (A)ldg(invD + ((sp & SPLIT_INVD) ? qs : q));
+  st(phi + q, s);
+  if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, s);
+}
+
 // The last colour pass of a V-cycle's post-smoothing on the finest level fused with the
 // solution update: the thread updates the cell of the colour as k_smooth does (storing e),
 // then adds both cells' corrections of its pair to phi -- the other cell's e is final
@@ -1041,6 +1107,19 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
                               (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
                               (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
                               (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf, L.rev, sp));
+}
+
+void launch_smooth_pro(int dt, const LevelDev& L, const LevelDev& Lc, void* phi, const void* rhs, const Coefs& c,
+                       int colour, const void* ec, cudaStream_t s, bool push, bool own_rhs) {
+  if (!L.n_pair_chunks) return;
+  ++g_launches;
+  const PushFace* pf = push ? L.push_faces : nullptr;
+  const int sp = smooth_split(L, own_rhs);
+  GMG_DISPATCH(dt, launch_pdl(k_smooth_pro<T>, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks, (T*)phi,
+                              (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
+                              (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
+                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf, L.rev, sp, (const T*)ec,
+                              Lc.boxes, L.parent));
 }
 
 // residual work list: pair items over every box (the bottom level included)

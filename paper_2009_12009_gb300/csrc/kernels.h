@@ -110,6 +110,12 @@ void launch_fill(int dt, const LevelDev& L, void* f, int colour, int copy_mode, 
 // a caller's rhs is in the ordinary layout); 1/D is read as the level keeps it
 void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const Coefs& c, int colour,
                    cudaStream_t s, bool push = false, bool vec = false, bool own_rhs = false);
+// One red-black colour fused with the piecewise-constant interpolation of the coarse
+// correction ec of level Lc (Lc's ghosts current) that would precede it: the cells of the
+// colour get the values of the interpolation followed by launch_smooth; the other colour's
+// cells are left as they were (the next colour pass overwrites them without reading them).
+void launch_smooth_pro(int dt, const LevelDev& L, const LevelDev& Lc, void* phi, const void* rhs, const Coefs& c,
+                       int colour, const void* ec, cudaStream_t s, bool push, bool own_rhs = false);
 // r = (rhs - shift[solve]) - A phi on valid cells (ghosts of phi must be filled); rdt =
 // type of r; maxbits (may be null): per-solve atomic max of |r| as IEEE bits; shift (may be
 // null): per-solve device scalars

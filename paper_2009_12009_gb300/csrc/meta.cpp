@@ -575,7 +575,7 @@ std::string finalize_level(LevelMeta& L) {
   if (!err.empty()) return err;
   // push faces: each ghost rectangle copies one face of its source box (its source layer is
   // the box's first or last layer along the normal) to a translate in the destination box
-  L.push_faces.assign((size_t)nb * 6, PushFace{-1, 1, 0, 0, 0, 0, 0});
+  L.push_faces.assign((size_t)nb * 6, PushFace{-1, 1, 0, 0, 0, 0, 0, 0, 0});
   L.push_ok = true;
   for (const GhostRect& g : L.ghosts) {
     const int d = 3 - g.d1 - g.d2;
@@ -600,6 +600,7 @@ std::string finalize_level(LevelMeta& L) {
     const DevBox& Dd = L.dbox[g.dst_box];
     P.direct = (Dd.sx == S.sx && Dd.sy == S.sy) ? 1 : 0;
     P.delta = elem_index(Dd, g.dst[0], g.dst[1], g.dst[2]) - elem_index(S, g.src[0], g.src[1], g.src[2]);
+    P.wall = g.kind == 1 ? 1 : 0;
   }
   for (int q = 0; q < (int)L.geoms.size(); ++q)
     if (L.solve_present[q])
