@@ -17,7 +17,8 @@ prolongation, BiCGStab bottom) and the outer FP64 residual loop.
            iterative refinement (time, Mcell-updates/s, error against the FP64 solve);
   roofline: the finest-level smoother kernel (dominant), its algorithmic bytes per launch
            (28 B per cell per colour pass: 56 B per cell per red+black sweep) over its average
-           launch time, CUDA events recorded around each launch inside the timed solves; beside
+           launch time, CUDA events recorded around each of its launches in the last timed
+           solve (inside the timed region; the other solves run without the events); beside
            it, the same launches' FP64-pipe rate (7 operations per updated cell) over the FP64
            ceiling measured in this run (fp64_peak: the library's DFMA probe);
   cpu_baseline: the FP64 CPU oracle solving the same workload to 1e-10 on the host cores
@@ -763,14 +764,20 @@ def main():
         torch.cuda.synchronize()
 
     def timed_solves(precision, steps, warmup, profile=0):
+        """profile: the last timed solve records CUDA events around its finest-level smoother
+        and outer residual launches (its captured graph, built in the warm-up, holds them);
+        the other solves replay the plain graph"""
         for _ in range(warmup):
             ctx.solve(rhs, phi, tol_rel=TOL, precision=precision)
+        if profile:
+            ctx.solve(rhs, phi, tol_rel=TOL, precision=precision, profile=profile)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         infos = []
         e0.record(stream)
-        for _ in range(steps):
-            _, info = ctx.solve(rhs, phi, tol_rel=TOL, precision=precision, profile=profile)
+        for k in range(steps):
+            _, info = ctx.solve(rhs, phi, tol_rel=TOL, precision=precision,
+                                profile=profile if k == steps - 1 else 0)
             infos.append(info)
         e1.record(stream)
         barrier()
