@@ -10,8 +10,9 @@ the same bits.  Covered: the shared parity layouts (ragged tails, aggregation, p
 Neumann singular problems, walls of every kind, anisotropic h, an a*alpha term), the abec
 layouts whose coarse levels hold many 2^3 boxes, the three element types, CUDA graphs and
 direct launches, sweep counts, the symmetric V-cycle and the conjugate-gradient bottom, the
-Krylov top levels, batched problems of uneven sizes with a per-problem active mask, and the
-abec256 workload at full size.
+Krylov top levels, batched problems of uneven sizes with a per-problem active mask, a tail
+that is its 7^3 bottom alone (solved by the block-wide BiCGStab), and the abec256 workload at
+full size.
 """
 import numpy as np
 import pytest
@@ -52,10 +53,12 @@ def _make(name):
         return I.abec(128, 32, 4602, name=name)
     if name == "per128":  # singular periodic problem, 64 boxes
         return I.abec(128, 32, 4603, bc=P_, name=name)
+    if name == "abec28":  # the tail is the 7^3 bottom alone (343 cells: the block-wide bottom solve)
+        return I.abec(28, 16, 4604, name=name)
     return cases.make(name)
 
 
-NAMES = [n for n in cases.NAMES if n != "oddlo"] + ["abec64_8", "abec128_64", "per128"]
+NAMES = [n for n in cases.NAMES if n != "oddlo"] + ["abec64_8", "abec128_64", "per128", "abec28"]
 
 
 @pytest.fixture(scope="module", params=NAMES)

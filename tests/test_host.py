@@ -201,6 +201,10 @@ def test_tail_plan_dense_bytes():
                    for ne, sm in ((1000, True), (216, True), (64, False)))
         assert ctx.tail_plan(5, dt) == (1, want)
         assert all(ctx.tail_plan(m, dt) == (0, 0) for m in range(ctx.nlevels) if m != 5)
+    # 28^3 in boxes of 16: the tail is the 7^3 bottom alone (9^3 elements, e and r only)
+    c28 = I.abec(28, 16, 1)
+    ctx28 = gmg.Context(c28["domain"], c28["bc_lo"], c28["bc_hi"], boxes=c28["boxes"])
+    assert ctx28.tail_plan(ctx28.nlevels - 1) == (1, 2 * al(729 * 8))
     # batched: one block per problem, grouped by the level its tail starts on
     sizes = [(32, 48, 16), (16, 16, 32), (48, 32, 32), (32, 16, 48), (64, 64, 64)]
     B = gmg.BatchContext([I.batch_problem(s, i, max_grid_size=16) for i, s in enumerate(sizes)])
