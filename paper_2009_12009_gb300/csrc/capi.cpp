@@ -1041,21 +1041,24 @@ bool coarse_red(const gmg_ctx* c, const gmg_params& p, int dt, int m) {
 // m + 1's correction before it (launch_smooth_pro): piecewise-constant interpolation, red-first
 // post-smoothing by the grid's two-pass sweeps on level m, which pushes its ghosts (push),
 // linear walls (a quadratic wall ghost is not the parent's image), and level m + 1's ghosts
-// current when its post-smoothing ends: it pushes them and every problem on it is smoothed
-// by the grid launches (no bottom solve and no coarse end starting there).
+// current when its post-smoothing ends: every problem on it is smoothed by grid launches that
+// push them, or by a coarse end starting there (which fills them before it returns), none
+// is solved by a bottom launch there.
 bool prolong_fused(gmg_ctx* c, const gmg_params& p, int dt, int m, bool push, const LevelDev& D) {
   if (p.fuse_prolongation == 0 || p.prolongation != 0 || post_reversed(p) || p.nu2 <= 0 || any_quad(c) || !push)
     return false;
   // (FP64 on a large level: the colour pass is bound by the FP64 pipe, and the six additions
   // per update cost more than the interpolation pass they save -- measured on abec256)
   if (p.fuse_prolongation == 1 && dt == DT_F64 && c->L[m].ncells >= (1 << 22)) return false;
-  if (m + 2 >= nlev(c)) return false;
+  if (m + 1 >= nlev(c)) return false;
   if (wave_on(p, D, push) || flow_on(c, p, D, push)) return false;
   const bool fused = tail_on(c, p, dt) && c->tail_ok;
   const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
-  if (!(push_on(c, p, dt, m + 1) && Dc.push_ok) || Dc.n_pair_chunks == 0 || Dc.n_bot > 0) return false;
-  if (Dc.n_pair_chunks != c->dev[m + 1].n_pair_chunks) return false;  // (a coarse end starts there)
-  return true;
+  if (Dc.n_bot > 0) return false;  // (a bottom solve leaves its ghosts as they were)
+  if (Dc.n_pair_chunks > 0 && !(push_on(c, p, dt, m + 1) && Dc.push_ok)) return false;
+  // (the problems not smoothed by the grid there are in coarse ends, which leave the ghosts
+  // of their first level current)
+  return Dc.n_pair_chunks > 0 || fused;
 }
 
 // phi_update (finest level only, see fuse_correction_on): the last post-smoothing pass also

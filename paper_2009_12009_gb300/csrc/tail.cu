@@ -567,6 +567,8 @@ __global__ void __launch_bounds__(TT, 1) k_vtail(const __grid_constant__ TailArg
         __syncthreads();
       }
   }
+  // the first level's ghosts current on exit (the interpolation from it may read them)
+  t_fill(a.levels[Dd.lev0], a.ghosts, P.e[Dd.m0], -1);
 }
 
 // ---------------------------------------------------------------- dense coarse end
@@ -797,6 +799,9 @@ __global__ void __launch_bounds__(TT, 1) k_vtail_dense(const __grid_constant__ T
       const BotCell C = a.cells[L.cell0 + i];
       e0[C.q] = d.e[C.pad & TAIL_SLOT_MASK];
     }
+    // and its ghosts (the box layout's), current on exit as k_vtail leaves them
+    __syncthreads();
+    t_fill(L, a.ghosts, e0, -1);
   }
 }
 
