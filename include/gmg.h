@@ -247,10 +247,13 @@ typedef struct {
                            interpolation of the coarse correction would leave it (its value
                            plus its parent's) and the interpolation pass is not launched -- the
                            black cells it would have changed are rewritten by the black pass
-                           that follows without being read.  Bitwise the results of 0.  1
-                           leaves out FP64 levels of at least 2^22 cells, whose colour pass is
-                           bound by the FP64 pipe (the six additions per update cost more than
-                           the pass they save); 2: every level where it applies. */
+                           that follows without being read.  Where that pass cannot (the fine
+                           level exchanges its ghosts), the coarser level's last post-smoothing
+                           pass adds its final values to the children instead (every coarse box
+                           with one child box of twice its extent).  Bitwise the results of 0.
+                           1 leaves out FP64 fine levels of at least 2^22 cells, whose passes
+                           are bound by the FP64 pipe (the added additions cost more than the
+                           pass they save); 2: every level where it applies. */
 } gmg_params;
 
 typedef struct {

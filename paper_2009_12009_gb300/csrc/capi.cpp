@@ -310,6 +310,7 @@ size_t carve(gmg_ctx* c, void* base, bool mixed, bool fill) {
     D.coarse_chunks = (const Chunk*)cv.take(sizeof(Chunk) * M.coarse_chunks.size());
     D.n_coarse_chunks = (int)M.coarse_chunks.size();
     D.parent = (const int*)cv.take(sizeof(int) * M.parent.size());
+    D.child = (const int*)cv.take(sizeof(int) * M.child.size());
     D.bot_cells = (const BotCell*)cv.take(sizeof(BotCell) * M.bot_cells.size());
     D.bot_ghosts = (const BotGhost*)cv.take(sizeof(BotGhost) * M.bot_ghosts.size());
     D.bot_descs = (const BotDesc*)cv.take(sizeof(BotDesc) * M.bot_descs.size());
@@ -534,6 +535,7 @@ gmg_status upload_tables(gmg_ctx* c) {
     if ((st = upload(c, D.cell_chunks, M.cell_chunks))) return st;
     if ((st = upload(c, D.coarse_chunks, M.coarse_chunks))) return st;
     if ((st = upload(c, D.parent, M.parent))) return st;
+    if ((st = upload(c, D.child, M.child))) return st;
     if ((st = upload(c, D.bot_cells, M.bot_cells))) return st;
     if ((st = upload(c, D.bot_ghosts, M.bot_ghosts))) return st;
     if ((st = upload(c, D.bot_descs, M.bot_descs))) return st;
@@ -657,6 +659,27 @@ gmg_status build_hierarchy(gmg_ctx* c, const std::vector<Box>& boxes, const std:
     if (m > 0) build_ec_ghosts(c->L[m]);  // the coarse side of an interpolation (trilinear option)
     if (!more) break;
     c->L.push_back(C);
+  }
+  // child boxes: level m's box b has exactly one child on level m - 1, of twice its extent
+  for (int m = 0; m < nlev(c); ++m) {
+    LevelMeta& M = c->L[m];
+    M.child.assign(M.boxes.size(), -1);
+    if (m == 0) continue;
+    const LevelMeta& F = c->L[m - 1];
+    std::vector<int> nchild(M.boxes.size(), 0);
+    for (int f = 0; f < (int)F.boxes.size(); ++f)
+      if (F.parent[f] >= 0) {
+        ++nchild[F.parent[f]];
+        M.child[F.parent[f]] = f;
+      }
+    for (int b = 0; b < (int)M.boxes.size(); ++b) {
+      const int f = M.child[b];
+      if (f < 0) continue;
+      bool exact = nchild[b] == 1;
+      for (int d = 0; d < 3; ++d)
+        exact = exact && F.boxes[f].lo[d] == 2 * M.boxes[b].lo[d] && F.boxes[f].n(d) == 2 * M.boxes[b].n(d);
+      if (!exact) M.child[b] = -1;
+    }
   }
   c->tail_ok = false;
   if (nlev(c) <= TAIL_MAXLEV) {
@@ -859,7 +882,8 @@ void two_pass_sweep(gmg_ctx* c, const LevelDev& D, int dt, int m, cudaStream_t s
 void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, const gmg_params& p, cudaStream_t s,
                    bool e_zero = false, bool push = false, bool red_done = false, bool reverse = false,
                    double* phi_last = nullptr, bool push_phi = false, const void* pro_ec = nullptr,
-                   const LevelDev* pro_c = nullptr) {
+                   const LevelDev* pro_c = nullptr, void* out_fine = nullptr, const LevelDev* out_f = nullptr,
+                   bool out_push = false) {
   if (nsweep <= 0) return;
   if (!reverse && wave_on(p, D, push)) {
     const LevelBufs& B = c->buf[m];
@@ -917,7 +941,12 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
       smooth_colour_pro(c, D, *pro_c, dt, m, pro_ec, s, push);
     else if (!(red_done && it == 0))
       smooth_colour(c, D, dt, m, 0, s, !(e_zero && it == 0), push, vec_on(c, p, dt, m));
-    if (phi_last && it == nsweep - 1) {
+    if (out_fine && it == nsweep - 1) {  // (the interpolation onto the finer level, fused)
+      const LevelBufs& B = c->buf[m];
+      if (!push) launch_fill(dt, D, B.e[dt], 0, 0, s);
+      launch_smooth_prolong(dt, dir_view(c, D, m), *out_f, B.e[dt], B.r[dt], coefs_of(c, m, dt), 1, out_fine, s, push,
+                            out_push);
+    } else if (phi_last && it == nsweep - 1) {
       const LevelBufs& B = c->buf[m];
       if (!push) launch_fill(dt, D, B.e[dt], 0, 0, s);
       const bool prof = c->profiling && m == 0;
@@ -1061,10 +1090,33 @@ bool prolong_fused(gmg_ctx* c, const gmg_params& p, int dt, int m, bool push, co
   return Dc.n_pair_chunks > 0 || fused;
 }
 
+// Whether level m + 1's last post-smoothing pass also performs the interpolation of its
+// correction onto level m (launch_smooth_prolong; used where the first red pass of level m
+// does not): piecewise-constant interpolation, red-first post-smoothing with at least one
+// sweep, level m + 1 smoothed for every problem by the grid's two-pass sweeps (no bottom
+// solve, no coarse end, no wavefront or dataflow sweep there), and every box of level m + 1
+// with one exact child box on level m.
+bool smooth_prolong_ok(gmg_ctx* c, const gmg_params& p, int dt, int m) {
+  if (p.fuse_prolongation == 0 || p.prolongation != 0 || post_reversed(p) || p.nu2 <= 0) return false;
+  if (m + 2 >= nlev(c)) return false;
+  // (FP64 onto a large level: the additions for the 8 children per coarse cell make the
+  // coarse pass FP64-bound, slower than the interpolation pass -- measured on abec256)
+  if (p.fuse_prolongation == 1 && dt == DT_F64 && c->L[m].ncells >= (1 << 22)) return false;
+  const bool fused = tail_on(c, p, dt) && c->tail_ok;
+  const LevelDev Dc = fused ? vc_view(c, m + 1) : c->dev[m + 1];
+  if (Dc.n_bot > 0 || Dc.n_pair_chunks == 0 || Dc.n_pair_chunks != c->dev[m + 1].n_pair_chunks) return false;
+  const bool cpush = push_on(c, p, dt, m + 1) && Dc.push_ok;
+  if (wave_on(p, Dc, cpush) || flow_on(c, p, Dc, cpush)) return false;
+  for (int b : c->L[m + 1].child)
+    if (b < 0) return false;
+  return true;
+}
+
 // phi_update (finest level only, see fuse_correction_on): the last post-smoothing pass also
 // adds e to phi
 void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool red_done = false,
-            double* phi_update = nullptr, bool push_phi = false) {
+            double* phi_update = nullptr, bool push_phi = false, void* out_fine = nullptr,
+            const LevelDev* out_f = nullptr, bool out_push = false) {
   choose_pdl(p, s);
   c->serp = p.serpentine != 0;
   const bool fused = tail_on(c, p, dt) && c->tail_ok;
@@ -1094,20 +1146,24 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   launch_resid_restrict(dt, dir_view(c, D, m), Dc, B.e[dt], B.r[dt], coefs_of(c, m, dt), c->buf[m + 1].r[dt], s,
                         settled, true, cred ? c->buf[m + 1].e[dt] : nullptr,
                         cred ? coefs_of(c, m + 1, dt).invD : nullptr, cpush);
-  vcycle(c, dt, m + 1, p, s, cred);
   const bool pro = prolong_fused(c, p, dt, m, push, D);
+  // (otherwise the coarse level's last post-smoothing pass may do the interpolation)
+  const bool sprol = !pro && smooth_prolong_ok(c, p, dt, m);
+  vcycle(c, dt, m + 1, p, s, cred, nullptr, false, sprol ? B.e[dt] : nullptr, &D, push);
   if (p.prolongation == 1) {  // trilinear: the coarse correction's ghosts, edges and corners too
     launch_fill(dt, c->dev[m + 1], c->buf[m + 1].e[dt], -1, 0, s);
     launch_fill_ec(dt, c->dev[m + 1], c->buf[m + 1].e[dt], s);
     launch_prolong_tri(dt, dir_view(c, D, m), Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
   } else if (pro) {
     // (the interpolation is done by the first post-smoothing red pass)
-    smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, false, phi_update, push_phi, c->buf[m + 1].e[dt], &Dc);
+    smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, false, phi_update, push_phi, c->buf[m + 1].e[dt], &Dc,
+                  out_fine, out_f, out_push);
     return;
-  } else {
+  } else if (!sprol) {
     launch_prolong_add(dt, dir_view(c, D, m), Dc, c->buf[m + 1].e[dt], B.e[dt], s, push);
   }
-  smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, post_reversed(p), phi_update, push_phi);
+  smooth_sweeps(c, D, dt, m, p.nu2, p, s, false, push, false, post_reversed(p), phi_update, push_phi, nullptr, nullptr,
+                out_fine, out_f, out_push);
 }
 
 // Whether the outer residual also performs the first red half-sweep of the next V-cycle

@@ -128,6 +128,69 @@ __global__ void __launch_bounds__(BLOCK, SmoothMinB<T>::value)
   if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, s);
 }
 
+// The last colour pass of a coarse level's post-smoothing fused with the piecewise-constant
+// interpolation of its correction onto the finer level (Sec. "Operations between levels"):
+// the thread updates the cell of its pair of the colour as k_smooth does, then adds both
+// cells of the pair -- the other colour's value is final -- to their 8 children each in the
+// box's one child box (child: per coarse box; the level pair is used only where every box
+// has one, of exactly twice its extent), pushing the children's new values into the fine
+// ghosts that copy them (fpush).  The values of the colour pass followed by k_prolong_add,
+// one pass over the fine level fewer.
+template <class T>
+__global__ void __launch_bounds__(BLOCK)
+    k_smooth_prolong(const DevBox* __restrict__ boxes, const Chunk* __restrict__ chunks, T* phi,
+                     const T* __restrict__ rhs, const typename CoefOf<T>::type* __restrict__ wx,
+                     const typename CoefOf<T>::type* __restrict__ wy, const typename CoefOf<T>::type* __restrict__ wz,
+                     const typename CoefOf<T>::type* __restrict__ invD, int colour, const int* __restrict__ active,
+                     const PushFace* __restrict__ push, int rev, T* fine, const DevBox* __restrict__ fboxes,
+                     const int* __restrict__ child, const PushFace* __restrict__ fpush) {
+  pdl_enter();
+  using A = typename Arith<T>::type;
+  const Chunk ch = chunks[rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x];
+  const DevBox B = boxes[ch.item];
+  if (active && !active[B.solve]) return;
+  const int t = ch.start + threadIdx.x;
+  if (t >= ((B.nx + 1) >> 1) * B.ny * B.nz) return;
+  int i0, j, k;
+  pair_decode(B, t, i0, j, k);
+  const int par = (B.lo[0] + B.lo[1] + B.lo[2] + i0 + j + k + colour) & 1;
+  const int i = i0 + par;
+  const int64_t q0 = elem_index(B, i0, j, k);
+  const int64_t sx = B.sx, sy = B.sy;
+  if (i < B.nx) {
+    const int64_t q = q0 + par;
+    A s = ldg(rhs + q);
+    s = fma((A)ldg(wx + q), (A)ld(phi + q - 1), s);
+    s = fma((A)ldg(wx + q + 1), (A)ld(phi + q + 1), s);
+    s = fma((A)ldg(wy + q), (A)ld(phi + q - sx), s);
+    s = fma((A)ldg(wy + q + sx), (A)ld(phi + q + sx), s);
+    s = fma((A)ldg(wz + q), (A)ld(phi + q - sy), s);
+    s = fma((A)ldg(wz + q + sy), (A)ld(phi + q + sy), s);
+    s = s * (A)ldg(invD + q);
+    st(phi + q, s);
+    if (push) push_ghosts(B, ch.item, boxes, push, phi, i, j, k, s);
+  }
+  const int fb = child[ch.item];
+  const DevBox F = fboxes[fb];
+  for (int c = 0; c < 2 && i0 + c < B.nx; ++c) {
+    const A e = ld(phi + q0 + c);  // (as stored)
+    const int fi = 2 * (i0 + c);
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj) {
+        const int fj = 2 * j + dj, fk = 2 * k + dk;
+        const int64_t qf = elem_index(F, fi, fj, fk);
+        const A v0 = (A)ld(fine + qf) + e;
+        const A v1 = (A)ld(fine + qf + 1) + e;
+        st(fine + qf, v0);
+        st(fine + qf + 1, v1);
+        if (fpush) {
+          push_ghosts(F, fb, fboxes, fpush, fine, fi, fj, fk, v0);
+          push_ghosts(F, fb, fboxes, fpush, fine, fi + 1, fj, fk, v1);
+        }
+      }
+  }
+}
+
 // a value of type T's arithmetic type rounded as T stores it
 __device__ __forceinline__ double as_stored(double v, const double*) { return v; }
 __device__ __forceinline__ float as_stored(float v, const float*) { return v; }
@@ -1120,6 +1183,19 @@ void launch_smooth_pro(int dt, const LevelDev& L, const LevelDev& Lc, void* phi,
                               (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
                               (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf, L.rev, sp, (const T*)ec,
                               Lc.boxes, L.parent));
+}
+
+void launch_smooth_prolong(int dt, const LevelDev& L, const LevelDev& Lf, void* phi, const void* rhs, const Coefs& c,
+                           int colour, void* fine, cudaStream_t s, bool push, bool fpush) {
+  if (!L.n_pair_chunks) return;
+  ++g_launches;
+  const PushFace* pf = push ? L.push_faces : nullptr;
+  const PushFace* ff = fpush ? Lf.push_faces : nullptr;
+  GMG_DISPATCH(dt, launch_pdl(k_smooth_prolong<T>, grid_of(L.n_pair_chunks), BLOCK, 0, s, L.boxes, L.pair_chunks,
+                              (T*)phi, (const T*)rhs, (const typename CoefOf<T>::type*)c.wx,
+                              (const typename CoefOf<T>::type*)c.wy, (const typename CoefOf<T>::type*)c.wz,
+                              (const typename CoefOf<T>::type*)c.invD, colour, L.active, pf, L.rev, (T*)fine,
+                              Lf.boxes, L.child, ff));
 }
 
 // residual work list: pair items over every box (the bottom level included)

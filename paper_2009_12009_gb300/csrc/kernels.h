@@ -33,6 +33,7 @@ struct LevelDev {
   const Chunk* coarse_chunks = nullptr;
   int n_coarse_chunks = 0;
   const int* parent = nullptr;
+  const int* child = nullptr;       // per box: its one exact child box on the finer level, or -1
   const BotCell* bot_cells = nullptr;
   const BotGhost* bot_ghosts = nullptr;
   const BotDesc* bot_descs = nullptr;
@@ -116,6 +117,13 @@ void launch_smooth(int dt, const LevelDev& L, void* phi, const void* rhs, const 
 // cells are left as they were (the next colour pass overwrites them without reading them).
 void launch_smooth_pro(int dt, const LevelDev& L, const LevelDev& Lc, void* phi, const void* rhs, const Coefs& c,
                        int colour, const void* ec, cudaStream_t s, bool push, bool own_rhs = false);
+// One red-black colour on coarse level L fused with the piecewise-constant interpolation of
+// the level's correction onto the finer level Lf that follows it (fine += parent value; L's
+// boxes each with one exact child, L.child): the values of launch_smooth followed by
+// launch_prolong_add; push / fpush: write new values into the ghosts of L / Lf too.  The other
+// colour's values must be final (this is the last pass of L's post-smoothing).
+void launch_smooth_prolong(int dt, const LevelDev& L, const LevelDev& Lf, void* phi, const void* rhs, const Coefs& c,
+                           int colour, void* fine, cudaStream_t s, bool push, bool fpush);
 // r = (rhs - shift[solve]) - A phi on valid cells (ghosts of phi must be filled); rdt =
 // type of r; maxbits (may be null): per-solve atomic max of |r| as IEEE bits; shift (may be
 // null): per-solve device scalars

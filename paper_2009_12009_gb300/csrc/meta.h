@@ -58,6 +58,8 @@ struct LevelMeta {
   std::vector<char> solve_present;  // per solve: has boxes on this level
   std::vector<char> solve_bottom;   // per solve: this level is its bottom
   std::vector<int> parent;          // per box: box on the next coarser level (-1: none)
+  std::vector<int> child;           // per box: its one child box on the next finer level, whose
+                                    // cells are exactly its own halved (-1: none or several)
 
   // layout (shared by every element type)
   std::vector<DevBox> dbox;

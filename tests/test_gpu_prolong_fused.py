@@ -10,6 +10,10 @@ both mixed forms, with ghost push and with the exchange on the fine levels, with
 and the vector smoothers on the other passes, with the coarse end fused or run level by
 level, for single problems (walls of every linear kind, periodic images, aggregated coarse
 boxes) and for batched problems with the active mask; the fused form launches fewer kernels.
+Where the fine level's red pass cannot take the interpolation (the exchange on the fine level,
+or an FP64 finest level whose pass is bound by the FP64 pipe), the coarse level's last
+post-smoothing pass adds its final values to its children instead; those cases are covered
+too (the exchange cases, and abec256 at full size).
 """
 import numpy as np
 import pytest
@@ -127,3 +131,22 @@ def test_fused_prolongation_batched(fc):
             assert torch.equal(a1[s], B.unpack_solve(s, p0)), (prec, s)
             its.append(i0[s].iterations)
         assert len(set(its)) > 1
+
+
+def test_fused_prolongation_full_size_abec256():
+    """abec256 at full size: the interpolation into the finest level done by level 1's last
+    post-smoothing pass (every level-1 box has one exact child) -- FP64 with push
+    (fuse_prolongation = 2: the default leaves that FP64-bound case out), float with the
+    exchange on the finest level (the default) -- and the default's FP64 choice.  Two
+    iterations, the same bits as no fusion."""
+    cfg = I.abec256()
+    C = _ctx(cfg)
+    rhs = C.pack(torch.from_numpy(cfg["rhs"]))
+    for prec, push, fuse in ((gmg.FP64, 0, 2), (gmg.FP64, 1, 1), (gmg.MIXED_FP32, 0, 1), (gmg.MIXED_BF16, 2, 1)):
+        kw = dict(tol_rel=0.0, max_iter=2, precision=prec, ghost_push=push)
+        p1, i1 = C.solve(rhs, fuse_prolongation=fuse, **kw)
+        a1 = C.unpack(p1).clone()
+        p0, i0 = C.solve(rhs, fuse_prolongation=0, **kw)
+        assert torch.equal(a1, C.unpack(p0)), prec
+        assert i1.history() == i0.history()
+        assert i1.kernel_launches < i0.kernel_launches
