@@ -1123,8 +1123,9 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   const LevelDev D = fused ? vc_view(c, m) : c->dev[m];
   const LevelBufs& B = c->buf[m];
   // (red_done: the residual kernel wrote e on every valid cell -- r / D on red, 0 on black
-  // -- and, with the push, its ghosts)
-  if (!red_done) cudaMemsetAsync(B.e[dt], 0, dt_size(dt) * (size_t)c->L[m].nelem, s);
+  // -- and, with the push, its ghosts; no grid smoothing here: every problem on the level is
+  // solved by a bottom launch or a coarse end, which write all its cells themselves)
+  if (!red_done && D.n_pair_chunks > 0) cudaMemsetAsync(B.e[dt], 0, dt_size(dt) * (size_t)c->L[m].nelem, s);
   if (fused) launch_tails(c, dt, m, p, s);
   if (D.n_bot) {
     BottomArgs a{p.bottom_max_iter, p.bottom_tol, B.bot_work, c->bot_iters, p.bottom_solver};
