@@ -239,12 +239,23 @@ __global__ void __launch_bounds__(BLOCK)
   const int64_t sx = B.sx, sy = B.sy;
   const int64_t qs = sp ? split_pair_slot(q - (i & 1), i & ~1, colour, B.nx) : q;
   const int g0 = B.lo[0] + i, g1 = B.lo[1] + j, g2 = B.lo[2] + k;
-  const A vxm = as_stored((A)ld(phi + q - 1) + pe(g0 - 1, g1, g2), phi);
-  const A vxp = as_stored((A)ld(phi + q + 1) + pe(g0 + 1, g1, g2), phi);
-  const A vym = as_stored((A)ld(phi + q - sx) + pe(g0, g1 - 1, g2), phi);
-  const A vyp = as_stored((A)ld(phi + q + sx) + pe(g0, g1 + 1, g2), phi);
-  const A vzm = as_stored((A)ld(phi + q - sy) + pe(g0, g1, g2 - 1), phi);
-  const A vzp = as_stored((A)ld(phi + q + sy) + pe(g0, g1, g2 + 1), phi);
+  // the cell's own parent serves the three neighbours in its 2x2x2 block; each other one is
+  // one coarse stride away (towards the side the neighbour lies on)
+  const int64_t qp = elem_index(P, (g0 >> 1) - P.lo[0], (g1 >> 1) - P.lo[1], (g2 >> 1) - P.lo[2]);
+  const int64_t psx = P.sx, psy = P.sy;
+  const A pc = ld(ec + qp);
+  const A pxm = (g0 & 1) ? pc : (A)ld(ec + qp - 1);
+  const A pxp = (g0 & 1) ? (A)ld(ec + qp + 1) : pc;
+  const A pym = (g1 & 1) ? pc : (A)ld(ec + qp - psx);
+  const A pyp = (g1 & 1) ? (A)ld(ec + qp + psx) : pc;
+  const A pzm = (g2 & 1) ? pc : (A)ld(ec + qp - psy);
+  const A pzp = (g2 & 1) ? (A)ld(ec + qp + psy) : pc;
+  const A vxm = as_stored((A)ld(phi + q - 1) + pxm, phi);
+  const A vxp = as_stored((A)ld(phi + q + 1) + pxp, phi);
+  const A vym = as_stored((A)ld(phi + q - sx) + pym, phi);
+  const A vyp = as_stored((A)ld(phi + q + sx) + pyp, phi);
+  const A vzm = as_stored((A)ld(phi + q - sy) + pzm, phi);
+  const A vzp = as_stored((A)ld(phi + q + sy) + pzp, phi);
   A s = ldg(rhs + ((sp & SPLIT_RHS) ? qs : q));
   s = fma((A)ldg(wx + q), vxm, s);
   s = fma((A)ldg(wx + q + 1), vxp, s);
