@@ -254,6 +254,11 @@ typedef struct {
                            1 leaves out FP64 fine levels of at least 2^22 cells, whose passes
                            are bound by the FP64 pipe (the added additions cost more than the
                            pass they save); 2: every level where it applies. */
+  int fork_bottoms;     /* 1 (default): in a batched context, the bottom solves of the problems
+                           whose bottom is a level other problems go below run on a second
+                           stream of the context, overlapping those problems' coarser levels,
+                           and are joined before the interpolation from that level.  Same
+                           results; 0: one stream. */
 } gmg_params;
 
 typedef struct {

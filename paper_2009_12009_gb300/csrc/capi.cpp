@@ -96,6 +96,10 @@ struct AmrLevel {
 struct gmg_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  // batched contexts: a second stream for bottom solves that overlap the other problems'
+  // coarser levels, with a fork and a join event per MG level
+  cudaStream_t side_stream = nullptr;
+  std::vector<cudaEvent_t> ev_fork, ev_join;
   std::string err;
 
   bool have_domain = false;
@@ -965,7 +969,8 @@ void smooth_sweeps(gmg_ctx* c, const LevelDev& D, int dt, int m, int nsweep, con
 // the interpolation, the wavefront sweep, the coarse end's form, the fused red passes
 int sweep_key(const gmg_params& p) {
   return p.fused_sweep + 4 * p.flow_warps + 1024 * p.serpentine + 2048 * p.prolongation + 4096 * p.wave_sweep +
-         8192 * p.tail_dense + 16384 * p.fuse_restriction_sweep + 32768 * p.fuse_prolongation;
+         8192 * p.tail_dense + 16384 * p.fuse_restriction_sweep + 32768 * p.fuse_prolongation +
+         131072 * p.fork_bottoms;
 }
 
 // the symmetric V-cycle: post-smoothing black before red (asked for, or implied by the
@@ -1127,9 +1132,31 @@ void vcycle(gmg_ctx* c, int dt, int m, const gmg_params& p, cudaStream_t s, bool
   // solved by a bottom launch or a coarse end, which write all its cells themselves)
   if (!red_done && D.n_pair_chunks > 0) cudaMemsetAsync(B.e[dt], 0, dt_size(dt) * (size_t)c->L[m].nelem, s);
   if (fused) launch_tails(c, dt, m, p, s);
+  // Bottom solves of the problems whose bottom is this level: on the side stream when other
+  // problems go on to coarser levels (the bottom touches only its problems' cells and the
+  // level's bottom scratch), joined before this call returns -- the interpolation from this
+  // level is the first step that reads their result.
+  struct Join {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    ~Join() {
+      if (ev) cudaStreamWaitEvent(s, ev, 0);
+    }
+  } join;
   if (D.n_bot) {
     BottomArgs a{p.bottom_max_iter, p.bottom_tol, B.bot_work, c->bot_iters, p.bottom_solver};
-    launch_bottom(dt, D, B.r[dt], B.e[dt], coefs64(c, m), a, s);
+    const bool fork = p.fork_bottoms != 0 && c->side_stream && m < (int)c->ev_fork.size() && D.n_pair_chunks > 0 &&
+                      m + 1 < nlev(c);
+    if (fork) {
+      cudaEventRecord(c->ev_fork[m], s);
+      cudaStreamWaitEvent(c->side_stream, c->ev_fork[m], 0);
+      launch_bottom(dt, D, B.r[dt], B.e[dt], coefs64(c, m), a, c->side_stream);
+      cudaEventRecord(c->ev_join[m], c->side_stream);
+      join.s = s;
+      join.ev = c->ev_join[m];
+    } else {
+      launch_bottom(dt, D, B.r[dt], B.e[dt], coefs64(c, m), a, s);
+    }
   }
   if (m + 1 >= nlev(c) || D.n_pair_chunks == 0) return;
   // ghost push (every value written also lands in the ghosts that copy it) on levels whose
@@ -1271,6 +1298,7 @@ gmg_status params_ok(gmg_ctx* c, const gmg_params& p) {
     SETERR(c, GMG_ERR_BAD_INPUT, "fuse_restriction_sweep must be 0 or 1");
   if (p.fuse_prolongation < 0 || p.fuse_prolongation > 2)
     SETERR(c, GMG_ERR_BAD_INPUT, "fuse_prolongation must be 0, 1 or 2");
+  if (p.fork_bottoms != 0 && p.fork_bottoms != 1) SETERR(c, GMG_ERR_BAD_INPUT, "fork_bottoms must be 0 or 1");
   if (p.ghost_push < 0 || p.ghost_push > 2) SETERR(c, GMG_ERR_BAD_INPUT, "ghost_push must be 0, 1 or 2");
   if (p.vector_smooth < 0 || p.vector_smooth > 2) SETERR(c, GMG_ERR_BAD_INPUT, "vector_smooth must be 0, 1 or 2");
   if (p.pdl < 0 || p.pdl > 2) SETERR(c, GMG_ERR_BAD_INPUT, "pdl must be 0, 1 or 2");
@@ -2518,6 +2546,7 @@ gmg_status gmg_default_params(gmg_params* p) {
   p->tail_dense = 1;
   p->fuse_restriction_sweep = 1;
   p->fuse_prolongation = 1;
+  p->fork_bottoms = 1;
   p->ghost_push = 2;
   p->vector_smooth = 2;
   p->pdl = 2;
@@ -2545,6 +2574,9 @@ gmg_status gmg_destroy(gmg_ctx* c) {
   for (cudaEvent_t e : c->ev_smooth) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_resid) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaEvent_t e : c->ev_fork) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_join) if (e) cudaEventDestroy(e);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->h_bits) cudaFreeHost(c->h_bits);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_iters) cudaFreeHost(c->h_iters);
@@ -3042,6 +3074,15 @@ gmg_status gmg_set_workspace(gmg_ctx* c, void* dptr, size_t bytes) {
   else SETERR(c, GMG_ERR_NO_WORKSPACE, "workspace too small");
   drop_graphs(c);
   if (!c->cap_stream) CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (!c->side_stream && c->ns() > 1) {
+    CK(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+    c->ev_fork.assign(nlev(c), nullptr);
+    c->ev_join.assign(nlev(c), nullptr);
+    for (int m = 0; m < nlev(c); ++m) {
+      CK(c, cudaEventCreateWithFlags(&c->ev_fork[m], cudaEventDisableTiming));
+      CK(c, cudaEventCreateWithFlags(&c->ev_join[m], cudaEventDisableTiming));
+    }
+  }
   gmg_status st = ensure_pinned(c);
   if (st) return st;
   c->ws = dptr;

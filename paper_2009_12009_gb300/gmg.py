@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("fuse_correction", C.c_int), ("settled_zero", C.c_int), ("flow_warps", C.c_int),
                 ("flow_lag_kcells", C.c_int), ("serpentine", C.c_int), ("prolongation", C.c_int),
                 ("wave_sweep", C.c_int), ("tail_dense", C.c_int),
-                ("fuse_restriction_sweep", C.c_int), ("fuse_prolongation", C.c_int)]
+                ("fuse_restriction_sweep", C.c_int), ("fuse_prolongation", C.c_int),
+                ("fork_bottoms", C.c_int)]
 
 
 class SolveInfo(C.Structure):
