@@ -9,6 +9,11 @@
 // cells down to the bottom and back.  The arithmetic of every step is that of the grid
 // kernels (kernels.cu, bottom.cu), in the same order per cell; only the order of the
 // bottom solve's dot-product additions differs.
+//
+// Two forms: k_vtail reads and writes the levels' global arrays at every step;
+// k_vtail_dense (the default where the levels fit) first copies each level into shared
+// memory as one padded array over the problem's domain and runs every step there, bitwise
+// the same values.  Both leave the ghosts of their first level current when they return.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
