@@ -211,3 +211,17 @@ def test_tail_plan_dense_bytes():
     plans = [B.tail_plan(m) for m in range(B.nlevels)]
     assert sum(n for n, _ in plans) == len(sizes)
     assert all(b > 0 for n, b in plans if n > 0)
+
+
+def test_new_launch_options_refused_out_of_range():
+    """The coarse-end and fusion options take only their documented values; a call with any
+    other value is refused (BAD_INPUT) before it touches the device, while the defaults get as
+    far as the missing workspace."""
+    Cx = gmg.Context(((0, 0, 0), (15, 15, 15)), [1] * 3, [1] * 3, max_grid_size=8)
+    for name, bad in (("tail_dense", 2), ("fuse_restriction_sweep", -1), ("fuse_prolongation", 3),
+                      ("fork_bottoms", 2)):
+        p = gmg.default_params(**{name: bad})
+        assert Cx.L.gmg_autotune(Cx.h, gmg.FP64, None, C.byref(p)) == gmg.BAD_INPUT, name
+    p = gmg.default_params()
+    assert (p.tail_dense, p.fuse_restriction_sweep, p.fuse_prolongation, p.fork_bottoms) == (1, 1, 1, 1)
+    assert Cx.L.gmg_autotune(Cx.h, gmg.FP64, None, C.byref(p)) == gmg.NO_WORKSPACE
